@@ -1,0 +1,25 @@
+"""FP64 CPU oracle for the adaptive-multigrid Wilson-Dirac solve (arXiv:0912.2186).
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path imports, calls or links this
+package: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` do.  It shares no code with the CUDA path.
+
+It is a plain, slow, obviously-correct restatement in numpy (complex128) of what the
+paper computes:
+
+* ``dirac``   -- the Wilson-Dirac operator D(U) of Sec. 2 (the equation for D_xy), the
+                 gamma matrices, the free-field closed form, a dense loop-built D.
+* ``mg``      -- blocking, block orthonormalisation of the near-null vectors (Sec. 2,
+                 the equation defining P), chirality split sigma_3 P = P gamma_5 (Sec. 3),
+                 restriction P^dag, prolongation P, the Galerkin coarse operator
+                 D^ = P^dag D P (Sec. 2) as a 9-point stencil, its application.
+* ``solvers`` -- MR smoother, CGNR coarsest solve, the multigrid cycle with post
+                 smoothing only, flexible GCR outer solver (Sec. 3) and the adaptive
+                 near-null-vector setup (Sec. 2).
+
+Parity status per function is stated in each module header.  The adaptive setup
+(``solvers.adaptive_setup``) is "parity unpinned" at the level of individual vectors:
+near-null vectors have no closed form; it is pinned only indirectly (residual
+decrease, span and orthonormality invariants).
+"""
+from . import dirac, mg, solvers  # noqa: F401
