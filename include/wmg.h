@@ -1,0 +1,199 @@
+/*
+ * wmg.h -- C ABI of libwmg: adaptive-multigrid-preconditioned solve of the
+ * Wilson-Dirac equation D(U) psi = b on one NVIDIA B300 (sm_103a).
+ *
+ * Method: Babich, Brannick, Brower, Clark, Cohen, Osborn, Rebbi, "The role of
+ * multigrid algorithms for LQCD" (arXiv:0912.2186).
+ *   Sec. 2, eq. for D_xy(U) ........ the fine operator D (wmg_apply_D)
+ *   Sec. 2, P: V^ -> S, R = P^dag .. prolongation / restriction (wmg_prolong,
+ *                                     wmg_restrict)
+ *   Sec. 2, P = orthonormal basis of theta_xhat(x) psi^(alpha)_x ... block
+ *                                     orthonormalisation inside wmg_setup
+ *   Sec. 2, D^ = R D P (Galerkin) ... the coarse operator (wmg_apply_coarse)
+ *   Sec. 2, adaptive construction .. wmg_setup
+ *   Sec. 3 ........................... chirality split sigma_3 P = P gamma_5,
+ *                                     4^4 blocks, post-smoothing cycle, GCR outer
+ *                                     solver, CG on the normal equations on the
+ *                                     coarsest level (wmg_solve)
+ *   Sec. 4 ("multiple lattices ... interpolation and prolongation operators")
+ *                                     the shape of this API.
+ *
+ * Conventions
+ * -----------
+ * * Every call returns a wmg_status; nothing throws across the ABI.  On an error
+ *   the context is left usable unless the status is WMG_ECUDA, after which only
+ *   wmg_destroy is valid.
+ * * Lattice extents dims = {X, Y, Z, T}; direction mu = 0..3 is x, y, z, t.
+ *   The lexicographic site index is x + X*(y + Y*(z + Z*t)); V = X*Y*Z*T.
+ *   Boundary conditions are periodic in all four directions.
+ * * Complex numbers are interleaved (re, im).
+ * * Canonical layouts, used by every *_host argument and by the canonical device
+ *   buffers of wmg_pack_spinor / wmg_unpack_spinor / wmg_solve_dev:
+ *     gauge field  : [t][z][y][x][mu][a][b] complex double, U_mu(x)^{ab}
+ *                    (the link leaving x in direction +mu; must be SU(3)).
+ *     fine spinor  : [rhs][t][z][y][x][spin][colour] complex double
+ *                    (component index k = 3*spin + colour).
+ *     coarse field : [rhs][site][2N] complex double, coarse sites lexicographic on
+ *                    the coarse lattice, coarse dof c = s*N + alpha with chirality
+ *                    s = 0 (sigma_3 = +1) first.
+ * * Gamma matrices (chiral basis): gamma_k = [[0, -i sigma_k], [i sigma_k, 0]]
+ *   (k = 1, 2, 3 for x, y, z), gamma_4 = [[0, 1], [1, 0]] (t), so gamma_5 =
+ *   diag(1, 1, -1, -1).  D psi(x) = (4 + m) psi(x)
+ *     - 1/2 sum_mu [(1 - gamma_mu) U_mu(x) psi(x + mu)
+ *                   + (1 + gamma_mu) U_mu(x - mu)^dag psi(x - mu)].
+ * * Native device layouts (operator entry points):
+ *     fine spinor, WMG_PREC_DOUBLE: [rhs][6][V][2] complex double
+ *     fine spinor, WMG_PREC_SINGLE: [rhs][6][V][2] complex float (float4 chunks)
+ *       chunk c of site v holds the components k = 2c and 2c + 1.
+ *     coarse vector, both precisions: [rhs][site][2N] complex.
+ *   wmg_pack_spinor / wmg_unpack_spinor convert canonical device buffers.
+ * * Device pointers passed in stay owned by the caller; work is stream-ordered on
+ *   the context's stream (wmg_create) and the call returns without synchronising
+ *   unless its comment says otherwise.  Host buffers are read or written before the
+ *   call returns.
+ * * A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef WMG_H
+#define WMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wmg_ctx wmg_ctx;
+
+typedef enum {
+  WMG_OK = 0,
+  WMG_EINVAL = 1,   /* bad argument (null pointer, size, layout, precision) */
+  WMG_ENOMEM = 2,   /* device or host allocation failed */
+  WMG_ECUDA = 3,    /* CUDA runtime error (see wmg_last_error) */
+  WMG_ENOCONV = 4,  /* solver did not reach the tolerance within max_iter */
+  WMG_ERANK = 5,    /* block Gram-Schmidt found a rank-deficient block */
+  WMG_ETIMEOUT = 6, /* a bounded device-side wait expired */
+  WMG_ESTATE = 7    /* call order (e.g. solve before setup, no gauge loaded) */
+} wmg_status;
+
+typedef enum {
+  WMG_PREC_DOUBLE = 0, /* FP64 storage and arithmetic */
+  WMG_PREC_SINGLE = 1  /* FP32 storage and arithmetic */
+} wmg_prec;
+
+#define WMG_MAX_LEVELS 3
+
+/* Parameters of the hierarchy and of the solve. */
+typedef struct {
+  int nlevels;                       /* 2 or 3 (Sec. 3 uses 3)                      */
+  int block[WMG_MAX_LEVELS - 1][4];  /* block extents {bx,by,bz,bt} per coarsening
+                                        (4^4 on the fine level, Sec. 3)             */
+  int nvec[WMG_MAX_LEVELS - 1];      /* near-null vectors N per coarsening          */
+  int setup_passes;                  /* adaptive passes (>= 1)                       */
+  int setup_relax;                   /* MR steps relaxing A psi = 0 in pass 1        */
+  int nu_post;                       /* post-smoothing MR steps (Sec. 3: 4)          */
+  int gcr_restart;                   /* outer flexible GCR restart length            */
+  int cycle_gamma;                   /* 1 = V-cycle, 2 = W-cycle at middle levels    */
+  double tol;                        /* target |b - D x| / |b| (FP64 true residual)  */
+  double coarse_tol;                 /* coarsest CGNR relative tolerance             */
+  int coarse_maxit;                  /* coarsest CGNR iteration cap                  */
+  int max_iter;                      /* outer iteration cap (cycle applications)     */
+  int prec_sloppy;                   /* precision of the cycle, the hierarchy and the
+                                        inner Krylov vectors (WMG_PREC_*)            */
+  int pad_;
+  double reliable_delta;             /* FP64 reliable update when the iterated
+                                        residual fell by this factor                */
+  uint64_t seed;                     /* seed of the setup's Gaussian starts when no
+                                        starts are passed                           */
+} wmg_params;
+
+/* Per-right-hand-side result of a solve. */
+typedef struct {
+  int iters;               /* outer iterations = applications of the cycle        */
+  int reliable_updates;    /* FP64 true-residual recomputations                   */
+  int converged;           /* 1 if true_resid <= tol                              */
+  int pad_;
+  double true_resid;       /* |b - D x| / |b| computed in FP64 on the device       */
+  double seconds;          /* wall time of the whole (batched) solve              */
+} wmg_info;
+
+/* Fill *p with the defaults (see the implementation for the values). */
+void wmg_default_params(wmg_params* p);
+
+const char* wmg_strerror(wmg_status s);
+/* Text of the last error seen by this context (or ""). */
+const char* wmg_last_error(const wmg_ctx* ctx);
+
+/* Create a context for an X*Y*Z*T lattice working on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  Every extent must be >= 2.
+ * The context owns all device memory it allocates. */
+wmg_status wmg_create(wmg_ctx** out, const int dims[4], void* cuda_stream);
+wmg_status wmg_destroy(wmg_ctx* ctx);
+
+/* Load U (canonical layout, V*4*9 complex double).  Keeps the 12-real compressed
+ * form (rows 0 and 1; row 2 = conj(row0 x row1) is rebuilt on use, Table 2's "12
+ * floats") in FP64 and FP32.  Drops any hierarchy.  Host variant synchronises. */
+wmg_status wmg_load_gauge(wmg_ctx* ctx, const double* U_host);
+wmg_status wmg_load_gauge_dev(wmg_ctx* ctx, const double* U_dev);
+
+/* Set the Wilson mass m (Sec. 2, the (4 + m) term).  An existing hierarchy's coarse
+ * operators are shifted by (m - m_setup) on their diagonal blocks, which is exact
+ * because P^dag P = 1. */
+wmg_status wmg_set_mass(wmg_ctx* ctx, double m);
+
+/* Adaptive setup (Sec. 2): near-null vectors, block orthonormalisation with the
+ * chirality split of Sec. 3, Galerkin coarse operators, level by level.
+ * starts_host: NULL (seeded Gaussian starts) or, for the fine level, nvec[0] fine
+ * spinors in the canonical layout.  Synchronises. */
+wmg_status wmg_setup(wmg_ctx* ctx, const wmg_params* p, const double* starts_host);
+
+/* Replace the near-null vectors of `level` (0: fine spinors, canonical layout;
+ * 1: coarse fields of the level-1 lattice) by the given host vectors, then
+ * block-orthonormalise them and rebuild the coarse operators from that level down.
+ * p gives the parameters (NULL: those of the last setup).  Synchronises. */
+wmg_status wmg_import_nullvecs(wmg_ctx* ctx, const wmg_params* p, int level, const double* host);
+/* Copy the block-orthonormalised vectors P of `level` to host (same layout).      */
+wmg_status wmg_export_nullvecs(wmg_ctx* ctx, int level, double* host);
+/* Copy the coarse operator of lattice level+1 (FP64) to host as
+ * [site][9][2N][2N] complex double, slot k = 0 self, 1 + 2 mu + (0: +mu, 1: -mu),
+ * row-major blocks: (D^ phi)(xhat) = sum_k D^[xhat][k] phi(xhat + k).  Synchronises. */
+wmg_status wmg_export_coarse(wmg_ctx* ctx, int level, double* host);
+/* Number of sites and of complex dof per site of lattice `level` (0 = fine). */
+wmg_status wmg_level_info(const wmg_ctx* ctx, int level, int* nsites, int* ndof);
+
+/* Solve D x = b for nrhs right-hand sides with MG-preconditioned flexible GCR
+ * (Sec. 3) to |b - D x| <= tol |b| in FP64.  b, x: canonical fine spinors.  Every
+ * right-hand side is iterated independently (its result does not depend on the
+ * others in the batch).  info: array of nrhs or NULL.  Returns WMG_ENOCONV if any
+ * right-hand side missed the tolerance.  Both variants synchronise. */
+wmg_status wmg_solve(wmg_ctx* ctx, const double* b_host, double* x_host, int nrhs, wmg_info* info);
+wmg_status wmg_solve_dev(wmg_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, wmg_info* info);
+/* The same outer solver without preconditioner (FP64), for comparison. */
+wmg_status wmg_solve_plain_dev(wmg_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, wmg_info* info);
+
+/* ---- operator-level entry points (native device layouts, stream-ordered) ---- */
+
+/* canonical [rhs][V][12] complex double  <->  native fine spinor of precision prec */
+wmg_status wmg_pack_spinor(wmg_ctx* ctx, int prec, const double* canon_dev, void* native_dev, int nrhs);
+wmg_status wmg_unpack_spinor(wmg_ctx* ctx, int prec, const void* native_dev, double* canon_dev, int nrhs);
+
+/* out = D(U) in for nrhs native fine spinors (Sec. 2, eq. for D) at the context's
+ * mass.  in and out must not overlap. */
+wmg_status wmg_apply_D(wmg_ctx* ctx, int prec, const void* in_dev, void* out_dev, int nrhs);
+
+/* coarse = P^dag fine (Sec. 2, R = P^dag): level 0 maps native fine spinors to
+ * level-1 coarse vectors, level 1 maps level-1 to level-2 coarse vectors.  prec is
+ * the precision of both buffers (the hierarchy must hold P in it). */
+wmg_status wmg_restrict(wmg_ctx* ctx, int level, int prec, const void* fine_dev, void* coarse_dev, int nrhs);
+/* fine = P coarse (Sec. 2). */
+wmg_status wmg_prolong(wmg_ctx* ctx, int level, int prec, const void* coarse_dev, void* fine_dev, int nrhs);
+/* out = D^ in on coarse lattice `level` >= 1 (Sec. 2 Galerkin operator), or
+ * sigma_3 D^ sigma_3 = D^dag (Sec. 3) if dagger != 0. */
+wmg_status wmg_apply_coarse(wmg_ctx* ctx, int level, int prec, int dagger, const void* in_dev, void* out_dev,
+                            int nrhs);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WMG_H */

@@ -22,10 +22,14 @@ the vectors, repeat).  The details the paper leaves open are read as follows:
   residual r = b - A x decides whether to restart.  "Iterations" counts K calls
   (Table 1's fine-grid iteration count).
 * Adaptive setup (fixed N): pass 1 relaxes each random start with `relax` MR steps
-  on A psi = 0 and normalises; every later pass replaces psi_k by
-  psi_k + K(-A psi_k) with the current hierarchy and normalises; P and D^ are
-  rebuilt after each pass.  Three levels: finish level 1, then the same procedure
-  on A_2 = D^ with its own starts and a 2-level cycle.
+  on A psi = 0 and normalises; every later pass uses the trial hierarchy built
+  from the current vectors to solve again: psi_k <- K(psi_k) (one cycle as an
+  approximate solve of A psi_new = psi_k, i.e. inverse iteration), normalised; P
+  and D^ are rebuilt after each pass.  (Applying the cycle to the homogeneous
+  equation instead, psi_k + K(-A psi_k), returns zero for a vector that already
+  lies in span(P) when the coarse solve is exact, so a fixed set cannot be
+  improved that way.)  Three levels: finish level 1, then the same procedure on
+  A_2 = D^ with its own starts and a 2-level cycle.
 
 Pins (tests/test_oracle_solvers.py): MR residual non-increasing and one-step exact
 for A = I; CGNR against a dense solve; FGCR with the exact inverse as
@@ -208,8 +212,7 @@ def setup_level(op, block, starts, passes=5, relax=20, params=None, history=None
         H = Hierarchy([op, Ac], [P], [block], params)
         new = []
         for v in psi:
-            e = cycle(H, 0, -op.apply(v))
-            new.append(_normalise(v + e))
+            new.append(_normalise(cycle(H, 0, v)))
         psi = np.array(new)
         record()
         P = mg.block_orthonormalise(psi, block)

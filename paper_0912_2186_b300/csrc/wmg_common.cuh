@@ -1,0 +1,242 @@
+// Common device/host helpers of libwmg: complex arithmetic, lattice geometry,
+// native field layouts and the deterministic reduction scheme.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "wmg.h"
+
+#define WMG_HD __host__ __device__ __forceinline__
+#define WMG_D __device__ __forceinline__
+
+// ---------------------------------------------------------------------------------
+// complex numbers
+// ---------------------------------------------------------------------------------
+template <typename R>
+struct cpx {
+  R re, im;
+};
+using cd = cpx<double>;
+using cf = cpx<float>;
+
+template <typename R> WMG_HD cpx<R> operator+(cpx<R> a, cpx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R> WMG_HD cpx<R> operator-(cpx<R> a, cpx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R> WMG_HD cpx<R> operator-(cpx<R> a) { return {-a.re, -a.im}; }
+template <typename R> WMG_HD cpx<R> operator*(cpx<R> a, cpx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R> WMG_HD cpx<R> operator*(R s, cpx<R> a) { return {s * a.re, s * a.im}; }
+template <typename R> WMG_HD cpx<R>& operator+=(cpx<R>& a, cpx<R> b) {
+  a.re += b.re;
+  a.im += b.im;
+  return a;
+}
+template <typename R> WMG_HD cpx<R>& operator-=(cpx<R>& a, cpx<R> b) {
+  a.re -= b.re;
+  a.im -= b.im;
+  return a;
+}
+template <typename R> WMG_HD cpx<R> conj(cpx<R> a) { return {a.re, -a.im}; }
+// conj(a) * b
+template <typename R> WMG_HD cpx<R> cmulc(cpx<R> a, cpx<R> b) {
+  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+// acc += a * b
+template <typename R> WMG_HD void cfma(cpx<R>& acc, cpx<R> a, cpx<R> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+}
+// acc += conj(a) * b
+template <typename R> WMG_HD void cfmac(cpx<R>& acc, cpx<R> a, cpx<R> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+}
+template <typename R> WMG_HD R norm2(cpx<R> a) { return a.re * a.re + a.im * a.im; }
+template <typename T, typename R> WMG_HD cpx<T> ccast(cpx<R> a) { return {T(a.re), T(a.im)}; }
+
+// multiply by a unit phase: ph = 0 -> 1, 1 -> i, 2 -> -1, 3 -> -i
+template <typename R> WMG_HD cpx<R> mul_phase(cpx<R> a, int ph) {
+  switch (ph & 3) {
+    case 0: return a;
+    case 1: return {-a.im, a.re};
+    case 2: return {-a.re, -a.im};
+    default: return {a.im, -a.re};
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// lattice geometry
+// ---------------------------------------------------------------------------------
+struct Geom {
+  int L[4];  // X, Y, Z, T
+  int V;
+};
+
+inline Geom make_geom(const int d[4]) {
+  Geom g;
+  for (int i = 0; i < 4; ++i) g.L[i] = d[i];
+  g.V = d[0] * d[1] * d[2] * d[3];
+  return g;
+}
+
+WMG_HD void site_coords(const Geom& g, int v, int c[4]) {
+  c[0] = v % g.L[0];
+  v /= g.L[0];
+  c[1] = v % g.L[1];
+  v /= g.L[1];
+  c[2] = v % g.L[2];
+  c[3] = v / g.L[2];
+}
+WMG_HD int site_index(const Geom& g, const int c[4]) {
+  return c[0] + g.L[0] * (c[1] + g.L[1] * (c[2] + g.L[2] * c[3]));
+}
+WMG_HD int dir_stride(const Geom& g, int mu) {
+  int s = 1;
+  for (int i = 0; i < mu; ++i) s *= g.L[i];
+  return s;
+}
+// neighbour of site v (coordinates c) in direction mu, sign +1/-1, periodic
+WMG_HD int neighbour(const Geom& g, int v, const int c[4], int mu, int sign) {
+  const int stride = dir_stride(g, mu);
+  const int x = c[mu];
+  if (sign > 0) return (x + 1 == g.L[mu]) ? v - (g.L[mu] - 1) * stride : v + stride;
+  return (x == 0) ? v + (g.L[mu] - 1) * stride : v - stride;
+}
+
+// ---------------------------------------------------------------------------------
+// native fine spinor layout: [rhs][6][V] chunks of two complex numbers.
+// chunk c of site v holds the components k = 2c, 2c+1 (k = 3*spin + colour).
+// ---------------------------------------------------------------------------------
+template <typename R> struct Chunk2;
+template <> struct Chunk2<float> {
+  WMG_D static void load(const void* base, size_t idx, cf& a, cf& b) {
+    float4 t = __ldg(reinterpret_cast<const float4*>(base) + idx);
+    a = {t.x, t.y};
+    b = {t.z, t.w};
+  }
+  WMG_D static void load_cg(const void* base, size_t idx, cf& a, cf& b) {  // no read-only path
+    float4 t = reinterpret_cast<const float4*>(base)[idx];
+    a = {t.x, t.y};
+    b = {t.z, t.w};
+  }
+  WMG_D static void store(void* base, size_t idx, cf a, cf b) {
+    reinterpret_cast<float4*>(base)[idx] = make_float4(a.re, a.im, b.re, b.im);
+  }
+};
+template <> struct Chunk2<double> {
+  WMG_D static void load(const void* base, size_t idx, cd& a, cd& b) {
+    const double2* p = reinterpret_cast<const double2*>(base) + 2 * idx;
+    double2 t0 = __ldg(p), t1 = __ldg(p + 1);
+    a = {t0.x, t0.y};
+    b = {t1.x, t1.y};
+  }
+  WMG_D static void load_cg(const void* base, size_t idx, cd& a, cd& b) {
+    const double2* p = reinterpret_cast<const double2*>(base) + 2 * idx;
+    double2 t0 = p[0], t1 = p[1];
+    a = {t0.x, t0.y};
+    b = {t1.x, t1.y};
+  }
+  WMG_D static void store(void* base, size_t idx, cd a, cd b) {
+    double2* p = reinterpret_cast<double2*>(base) + 2 * idx;
+    p[0] = make_double2(a.re, a.im);
+    p[1] = make_double2(b.re, b.im);
+  }
+};
+
+template <typename R>
+WMG_D void load_spinor(const void* base, int V, int v, cpx<R> s[12]) {
+#pragma unroll
+  for (int c = 0; c < 6; ++c) Chunk2<R>::load(base, (size_t)c * V + v, s[2 * c], s[2 * c + 1]);
+}
+template <typename R>
+WMG_D void store_spinor(void* base, int V, int v, const cpx<R> s[12]) {
+#pragma unroll
+  for (int c = 0; c < 6; ++c) Chunk2<R>::store(base, (size_t)c * V + v, s[2 * c], s[2 * c + 1]);
+}
+// byte offset of right-hand side r of a native fine field
+template <typename R> WMG_HD size_t spinor_field_bytes(int V) { return (size_t)V * 12 * 2 * sizeof(R); }
+
+// native gauge layout: [mu][3][V] chunks (rows 0 and 1 of U_mu(x), element e = 3*row + col,
+// chunk c holds e = 2c, 2c+1); row 2 = conj(row0 x row1) is rebuilt on load.
+template <typename R>
+WMG_D void load_link(const void* base, int V, int mu, int v, cpx<R> u[9]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) Chunk2<R>::load(base, (size_t)(mu * 3 + c) * V + v, u[2 * c], u[2 * c + 1]);
+  u[6] = conj(u[1] * u[5] - u[2] * u[4]);
+  u[7] = conj(u[2] * u[3] - u[0] * u[5]);
+  u[8] = conj(u[0] * u[4] - u[1] * u[3]);
+}
+
+// ---------------------------------------------------------------------------------
+// deterministic reductions: each CTA writes its partial sums (double) for its rhs;
+// the last CTA of that rhs (counter) sums the partials in index order.
+// ---------------------------------------------------------------------------------
+struct RedBuf {
+  double* partial;    // [nrhs][nblk][nval]
+  unsigned* counter;  // [nrhs], zero between uses
+  double* result;     // [nrhs][nval]
+};
+
+// Reduce NVAL doubles across the CTA (blockDim.x a multiple of 32, <= 1024); the result
+// is valid in thread 0.  Fixed summation order.
+template <int NVAL>
+WMG_D void cta_reduce(double v[NVAL], double* smem /* >= 32*NVAL */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NVAL; ++i)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NVAL; ++i) smem[warp * NVAL + i] = v[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NVAL; ++i) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += smem[w * NVAL + i];
+      v[i] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// After cta_reduce (thread 0 holds v): writes the CTA's partials; the last CTA for `rhs`
+// sums all partials in order into rb.result.  nblk = number of CTAs per rhs.
+template <int NVAL>
+WMG_D void grid_finish(const RedBuf& rb, int rhs, int blk, int nblk, const double v[NVAL]) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    double* p = rb.partial + ((size_t)rhs * nblk + blk) * NVAL;
+#pragma unroll
+    for (int i = 0; i < NVAL; ++i) p[i] = v[i];
+    __threadfence();
+    unsigned prev = atomicAdd(rb.counter + rhs, 1u);
+    last = (prev == (unsigned)nblk - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    if (threadIdx.x < NVAL) {
+      const volatile double* p = rb.partial + (size_t)rhs * nblk * NVAL;
+      double s = 0.0;
+      for (int b = 0; b < nblk; ++b) s += p[(size_t)b * NVAL + threadIdx.x];
+      rb.result[(size_t)rhs * NVAL + threadIdx.x] = s;
+    }
+    if (threadIdx.x == 0) rb.counter[rhs] = 0u;
+  }
+}
+
+#define WMG_CUDA_TRY(expr)                                      \
+  do {                                                          \
+    cudaError_t e_ = (expr);                                    \
+    if (e_ != cudaSuccess) return ::wmg_cuda_fail(e_, #expr);   \
+  } while (0)
+
+wmg_status wmg_cuda_fail(cudaError_t e, const char* what);

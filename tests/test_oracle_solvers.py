@@ -80,3 +80,30 @@ def test_three_level_cycle_converges():
     x, info = solvers.mg_solve(H, b, 1e-10)
     assert info.true_resid <= 1e-10
     assert solvers.norm(b - dirac.apply_D(U, x, 0.05)) <= 1e-10 * solvers.norm(b) * 1.01
+
+
+def test_setup_homogeneous_cycle_kills_vectors_in_span():
+    """Why the setup improves vectors by inverse iteration: a vector already in span(P),
+    passed through the cycle on the homogeneous equation with an exact coarse solve,
+    comes back as exactly zero (the coarse correction reproduces it)."""
+    dims, block, op, P, Ac = _tiny()
+    H = solvers.Hierarchy([op, Ac], [P], [block], solvers.CycleParams(coarse_tol=1e-14))
+    cd = mg.coarse_dims(dims, block)
+    v = mg.prolong(P, synth.coarse_starts(cd, Ac.n, 1, 60)[0], block)
+    e = solvers.cycle(H, 0, -op.apply(v))
+    assert solvers.norm(v + e) < 1e-10 * solvers.norm(v)
+
+
+def test_setup_passes_lower_the_rayleigh_quotient():
+    """Setup parity is unpinned at the vector level; its indirect pin: the mean
+    |A psi_k| / |psi_k| decreases from pass to pass, and the final vectors lie in span(P)."""
+    dims, block = (4, 4, 4, 8), (2, 2, 2, 2)
+    U = synth.gauge_field(dims, 0.5, 61)
+    op = mg.WilsonOp(U, 0.0)
+    starts = synth.setup_starts(dims, 4, 62)
+    hist = []
+    P, Ac, psi = solvers.setup_level(op, block, starts, passes=4, relax=10,
+                                     params=solvers.CycleParams(coarse_tol=1e-8), history=hist)
+    assert all(hist[i + 1] < hist[i] for i in range(len(hist) - 1)), hist
+    for v in psi:
+        assert solvers.norm(mg.prolong(P, mg.restrict(P, v, block), block) - v) < 1e-12
