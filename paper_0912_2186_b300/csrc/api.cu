@@ -1,0 +1,423 @@
+// The C ABI of libwmg (include/wmg.h): argument checking, memory ownership and sequencing
+// of the driver in solver.cu.
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "ctx.h"
+#include "solver.h"
+
+using namespace wmg;
+
+#define TRY(x)                     \
+  do {                             \
+    wmg_status st_ = (x);          \
+    if (st_ != WMG_OK) return st_; \
+  } while (0)
+#define CU(c, x)                                     \
+  do {                                               \
+    cudaError_t e_ = (x);                            \
+    if (e_ != cudaSuccess) return fail((c), e_, #x); \
+  } while (0)
+
+namespace {
+
+size_t csize(int prec) { return prec == WMG_PREC_DOUBLE ? sizeof(cd) : sizeof(cf); }
+bool prec_ok(int p) { return p == WMG_PREC_DOUBLE || p == WMG_PREC_SINGLE; }
+
+void free_hierarchy(wmg_ctx* c) {
+  for (int l = 0; l < WMG_MAX_LEVELS; ++l)
+    for (int p = 0; p < 2; ++p) {
+      if (c->L[l].A[p]) cudaFree(c->L[l].A[p]);
+      if (c->L[l].P[p]) cudaFree(c->L[l].P[p]);
+      c->L[l].A[p] = c->L[l].P[p] = nullptr;
+    }
+  c->have_hier = false;
+}
+
+wmg_status bad(wmg_ctx* c, const std::string& what) {
+  if (c) c->err = what;
+  return WMG_EINVAL;
+}
+
+// validate parameters and lay out (allocate) the hierarchy's transfer operators
+wmg_status alloc_hierarchy(wmg_ctx* c, const wmg_params* p) {
+  if (p->nlevels < 2 || p->nlevels > WMG_MAX_LEVELS) return bad(c, "nlevels must be 2 or 3");
+  if (!prec_ok(p->prec_sloppy)) return bad(c, "prec_sloppy");
+  if (p->gcr_restart < 1 || p->gcr_restart > kMaxKrylov) return bad(c, "gcr_restart must be in 1..32");
+  if (p->setup_passes < 1 || p->nu_post < 0 || p->setup_relax < 0 || p->max_iter < 1 || p->coarse_maxit < 1)
+    return bad(c, "iteration counts");
+  if (!(p->tol > 0) || !(p->coarse_tol > 0)) return bad(c, "tolerances must be positive");
+  free_hierarchy(c);
+  c->prm = *p;
+  c->nlev = p->nlevels;
+  c->L[0].g = c->fine;
+  c->L[0].ndof = 12;
+  for (int l = 0; l + 1 < c->nlev; ++l) {
+    LevelData& L = c->L[l];
+    Blocking& bk = L.bk;
+    bk.fine = L.g;
+    int cd4[4];
+    bk.bs = 1;
+    for (int i = 0; i < 4; ++i) {
+      const int b = p->block[l][i];
+      if (b < 1 || L.g.L[i] % b) return bad(c, "block extents must divide the lattice");
+      bk.b[i] = b;
+      bk.bs *= b;
+      cd4[i] = L.g.L[i] / b;
+    }
+    bk.coarse = make_geom(cd4);
+    bk.N = p->nvec[l];
+    bk.nf = L.ndof;
+    if (bk.N < 1 || 2 * bk.N > 256) return bad(c, "nvec must be in 1..128");
+    const int E = l == 0 ? bk.bs * 6 : bk.bs * (L.ndof / 2);
+    if (E > 256 * 8) return bad(c, "block too large for the Gram-Schmidt kernel (sites x dof per chirality > 2048)");
+    if (l == 0 && (size_t)4 * 12 * bk.bs * sizeof(cf) > 200 * 1024) return bad(c, "fine block too large");
+    if (l > 0 && (size_t)4 * bk.bs * bk.nf * sizeof(cd) > 200 * 1024) return bad(c, "coarse block too large");
+    if (E < bk.N) return bad(c, "more vectors than dof per block and chirality");
+    c->L[l + 1].g = bk.coarse;
+    c->L[l + 1].ndof = 2 * bk.N;
+    for (int pr = 0; pr < 2; ++pr) CU(c, cudaMalloc(&L.P[pr], L.nvec_elems() * bk.N * csize(pr)));
+  }
+  return WMG_OK;
+}
+
+void fill_gaussian(std::vector<double>& v, uint64_t seed) {
+  std::mt19937_64 gen(seed);
+  std::normal_distribution<double> nd(0.0, 1.0);
+  for (auto& x : v) x = nd(gen);
+}
+
+}  // namespace
+
+extern "C" {
+
+void wmg_default_params(wmg_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->nlevels = 2;
+  for (int l = 0; l < WMG_MAX_LEVELS - 1; ++l)
+    for (int i = 0; i < 4; ++i) p->block[l][i] = l == 0 ? 4 : 2;
+  p->nvec[0] = 24;
+  p->nvec[1] = 32;
+  p->setup_passes = 5;
+  p->setup_relax = 20;
+  p->nu_post = 4;
+  p->gcr_restart = 16;
+  p->cycle_gamma = 1;
+  p->tol = 1e-10;
+  p->coarse_tol = 1e-4;
+  p->coarse_maxit = 2000;
+  p->max_iter = 1000;
+  p->prec_sloppy = WMG_PREC_SINGLE;
+  p->reliable_delta = 0.1;
+  p->seed = 20091212ULL;
+}
+
+const char* wmg_strerror(wmg_status s) {
+  switch (s) {
+    case WMG_OK: return "ok";
+    case WMG_EINVAL: return "invalid argument";
+    case WMG_ENOMEM: return "out of memory";
+    case WMG_ECUDA: return "CUDA error";
+    case WMG_ENOCONV: return "solver did not converge";
+    case WMG_ERANK: return "rank-deficient block in Gram-Schmidt";
+    case WMG_ETIMEOUT: return "bounded device wait expired";
+    case WMG_ESTATE: return "call order";
+  }
+  return "unknown status";
+}
+
+const char* wmg_last_error(const wmg_ctx* c) { return c ? c->err.c_str() : ""; }
+
+wmg_status wmg_create(wmg_ctx** out, const int dims[4], void* stream) {
+  if (!out || !dims) return WMG_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < 4; ++i)
+    if (dims[i] < 2) return WMG_EINVAL;
+  if ((long long)dims[0] * dims[1] * dims[2] * dims[3] > (1LL << 30)) return WMG_EINVAL;
+  wmg_ctx* c = new wmg_ctx();
+  c->fine = make_geom(dims);
+  c->stream = (cudaStream_t)stream;
+  cudaGetDevice(&c->device);
+  c->L[0].g = c->fine;
+  c->L[0].ndof = 12;
+  cudaError_t e = cudaSuccess;
+  auto al = [&](void** p, size_t b) {
+    if (e == cudaSuccess) e = cudaMalloc(p, b);
+  };
+  al((void**)&c->d_mass, kMaxRhs * sizeof(double));
+  for (int l = 1; l < WMG_MAX_LEVELS; ++l) al((void**)&c->d_shift[l], kMaxRhs * sizeof(double));
+  al((void**)&c->d_active, kMaxRhs * sizeof(int));
+  al((void**)&c->d_mask, kMaxRhs * sizeof(int));
+  al((void**)&c->d_flag, sizeof(int));
+  al((void**)&c->d_cgint, 2 * kMaxRhs * sizeof(int));
+  al((void**)&c->red_counter, 4 * kMaxRhs * sizeof(unsigned));
+  al((void**)&c->res, (size_t)24 * kMaxRhs * 16 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(c->red_counter, 0, 4 * kMaxRhs * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(c->d_shift[1], 0, kMaxRhs * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(c->d_shift[2], 0, kMaxRhs * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pin, 4096 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pin_i, 4096 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->gauge[0], (size_t)c->fine.V * 4 * 6 * sizeof(cd));
+  if (e == cudaSuccess) e = cudaMalloc(&c->gauge[1], (size_t)c->fine.V * 4 * 6 * sizeof(cf));
+  if (e != cudaSuccess) {
+    wmg_destroy(c);
+    return e == cudaErrorMemoryAllocation ? WMG_ENOMEM : WMG_ECUDA;
+  }
+  wmg_default_params(&c->prm);
+  *out = c;
+  return WMG_OK;
+}
+
+wmg_status wmg_destroy(wmg_ctx* c) {
+  if (!c) return WMG_EINVAL;
+  cudaStreamSynchronize(c->stream);
+  free_hierarchy(c);
+  for (auto& kv : c->ws) cudaFree(kv.second.first);
+  c->ws.clear();
+  void* ptrs[] = {c->d_mass, c->d_shift[1], c->d_shift[2], c->d_active, c->d_mask, c->d_flag, c->d_cgint,
+                  c->red_counter, c->res, c->red_partial, c->gauge[0], c->gauge[1]};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->h_pin) cudaFreeHost(c->h_pin);
+  if (c->h_pin_i) cudaFreeHost(c->h_pin_i);
+  delete c;
+  return WMG_OK;
+}
+
+wmg_status wmg_load_gauge_dev(wmg_ctx* c, const double* U) {
+  if (!c || !U) return WMG_EINVAL;
+  free_hierarchy(c);
+  pack_gauge(WMG_PREC_DOUBLE, U, c->gauge[0], c->fine.V, c->stream);
+  pack_gauge(WMG_PREC_SINGLE, U, c->gauge[1], c->fine.V, c->stream);
+  TRY(check(c, "pack_gauge"));
+  c->have_gauge = true;
+  return WMG_OK;
+}
+
+wmg_status wmg_load_gauge(wmg_ctx* c, const double* U_host) {
+  if (!c || !U_host) return WMG_EINVAL;
+  void* st;
+  const size_t bytes = (size_t)c->fine.V * 4 * 9 * sizeof(cd);
+  TRY(ws_get(c, "stage", bytes, &st));
+  CU(c, cudaMemcpyAsync(st, U_host, bytes, cudaMemcpyHostToDevice, c->stream));
+  TRY(wmg_load_gauge_dev(c, (const double*)st));
+  CU(c, cudaStreamSynchronize(c->stream));
+  return WMG_OK;
+}
+
+wmg_status wmg_set_mass(wmg_ctx* c, double m) {
+  if (!c || !(m == m)) return WMG_EINVAL;
+  c->mass = m;
+  return WMG_OK;
+}
+
+wmg_status wmg_setup(wmg_ctx* c, const wmg_params* p, const double* starts_host) {
+  if (!c || !p) return WMG_EINVAL;
+  if (!c->have_gauge) return WMG_ESTATE;
+  TRY(alloc_hierarchy(c, p));
+  c->mass_setup = c->mass;
+  const int prec = p->prec_sloppy;
+  // level 0 starts
+  const int N0 = p->nvec[0];
+  const size_t V = c->fine.V;
+  void *canon, *vecs;
+  TRY(ws_get(c, "stage", V * 12 * N0 * sizeof(cd), &canon));
+  TRY(vec_ws(c, 0, "setup_vecs", prec, N0, &vecs));
+  if (starts_host) {
+    CU(c, cudaMemcpy(canon, starts_host, V * 12 * N0 * sizeof(cd), cudaMemcpyHostToDevice));
+  } else {
+    std::vector<double> h(V * 24 * N0);
+    fill_gaussian(h, p->seed);
+    CU(c, cudaMemcpy(canon, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  pack_spinor(prec, (const double*)canon, vecs, c->fine.V, N0, c->stream);
+  TRY(setup_level(c, 0, vecs));
+  if (c->nlev == 3) {
+    const int N1 = p->nvec[1];
+    const size_t n1 = c->L[1].nvec_elems();
+    void *stage1, *vecs1;
+    TRY(ws_get(c, "stage1", n1 * N1 * sizeof(cd), &stage1));
+    TRY(vec_ws(c, 1, "setup_vecs", prec, N1, &vecs1));
+    std::vector<double> h(n1 * 2 * N1);
+    fill_gaussian(h, p->seed + 1);
+    CU(c, cudaMemcpy(stage1, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+    blas_convert(prec, vecs1, WMG_PREC_DOUBLE, stage1, n1, N1, nullptr, c->stream);
+    TRY(setup_level(c, 1, vecs1));
+  }
+  CU(c, cudaStreamSynchronize(c->stream));
+  c->have_hier = true;
+  return WMG_OK;
+}
+
+wmg_status wmg_import_nullvecs(wmg_ctx* c, const wmg_params* p, int level, const double* host) {
+  if (!c || !host) return WMG_EINVAL;
+  if (!c->have_gauge) return WMG_ESTATE;
+  if (p) {
+    if (level == 0 || !c->L[0].P[0]) {
+      TRY(alloc_hierarchy(c, p));
+      c->mass_setup = c->mass;
+    }
+  } else if (!c->L[0].P[0]) {
+    return WMG_ESTATE;
+  }
+  if (level < 0 || level >= c->nlev - 1) return bad(c, "level");
+  if (level == 1 && !c->L[1].A[0]) return WMG_ESTATE;
+  LevelData& L = c->L[level];
+  const size_t n = L.nvec_elems();
+  const int N = L.bk.N;
+  TRY(ensure_reductions(c, N));
+  std::vector<double> m(N, c->mass_setup);
+  TRY(set_rhs_scalars(c, m.data(), N));
+  if (level == 0) {
+    void* canon;
+    TRY(ws_get(c, "stage", n * N * sizeof(cd), &canon));
+    CU(c, cudaMemcpy(canon, host, n * N * sizeof(cd), cudaMemcpyHostToDevice));
+    pack_spinor(WMG_PREC_DOUBLE, (const double*)canon, L.P[0], c->fine.V, N, c->stream);
+  } else {
+    CU(c, cudaMemcpy(L.P[0], host, n * N * sizeof(cd), cudaMemcpyHostToDevice));
+  }
+  TRY(orthonormalise(c, level));
+  TRY(galerkin(c, level, c->prm.prec_sloppy));
+  for (int l = level + 1; l + 1 < c->nlev; ++l)
+    if (c->L[l].P[0] && c->L[l].A[0] && level == 0 && c->have_hier) TRY(galerkin(c, l, c->prm.prec_sloppy));
+  CU(c, cudaStreamSynchronize(c->stream));
+  c->have_hier = (c->nlev == 2) || (level == 1) || c->have_hier;
+  return WMG_OK;
+}
+
+wmg_status wmg_export_nullvecs(wmg_ctx* c, int level, double* host) {
+  if (!c || !host) return WMG_EINVAL;
+  if (level < 0 || level >= c->nlev - 1 || !c->L[level].P[0]) return WMG_ESTATE;
+  LevelData& L = c->L[level];
+  const size_t n = L.nvec_elems();
+  const int N = L.bk.N;
+  if (level == 0) {
+    void* canon;
+    TRY(ws_get(c, "stage", n * N * sizeof(cd), &canon));
+    unpack_spinor(WMG_PREC_DOUBLE, L.P[0], (double*)canon, c->fine.V, N, c->stream);
+    CU(c, cudaMemcpyAsync(host, canon, n * N * sizeof(cd), cudaMemcpyDeviceToHost, c->stream));
+  } else {
+    CU(c, cudaMemcpyAsync(host, L.P[0], n * N * sizeof(cd), cudaMemcpyDeviceToHost, c->stream));
+  }
+  CU(c, cudaStreamSynchronize(c->stream));
+  return WMG_OK;
+}
+
+wmg_status wmg_export_coarse(wmg_ctx* c, int level, double* host) {
+  if (!c || !host) return WMG_EINVAL;
+  if (level < 0 || level + 1 >= c->nlev || !c->L[level + 1].A[0]) return WMG_ESTATE;
+  const LevelData& C = c->L[level + 1];
+  const int n = C.ndof;
+  const size_t count = (size_t)C.g.V * 9 * n * n;
+  std::vector<cd> tmp(count);
+  CU(c, cudaMemcpyAsync(tmp.data(), C.A[0], count * sizeof(cd), cudaMemcpyDeviceToHost, c->stream));
+  CU(c, cudaStreamSynchronize(c->stream));
+  cd* out = reinterpret_cast<cd*>(host);
+  for (size_t sk = 0; sk < (size_t)C.g.V * 9; ++sk)
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) out[(sk * n + i) * n + j] = tmp[(sk * n + j) * n + i];
+  return WMG_OK;
+}
+
+wmg_status wmg_level_info(const wmg_ctx* c, int level, int* nsites, int* ndof) {
+  if (!c || level < 0 || level >= WMG_MAX_LEVELS) return WMG_EINVAL;
+  if (level > 0 && level >= c->nlev) return WMG_ESTATE;
+  if (nsites) *nsites = c->L[level].g.V;
+  if (ndof) *ndof = c->L[level].ndof;
+  return WMG_OK;
+}
+
+static wmg_status solve_dev_impl(wmg_ctx* c, const double* b, double* x, int nrhs, wmg_info* info, bool mg) {
+  if (!c || !b || !x || nrhs < 1) return WMG_EINVAL;
+  if (!c->have_gauge || (mg && !c->have_hier)) return WMG_ESTATE;
+  const size_t V = c->fine.V;
+  wmg_status worst = WMG_OK;
+  for (int r0 = 0; r0 < nrhs; r0 += kMaxRhs) {
+    const int nr = std::min(kMaxRhs, nrhs - r0);
+    void *b64, *x64;
+    TRY(vec_ws(c, 0, "solve_b", WMG_PREC_DOUBLE, nr, &b64));
+    TRY(vec_ws(c, 0, "solve_x", WMG_PREC_DOUBLE, nr, &x64));
+    pack_spinor(WMG_PREC_DOUBLE, b + V * 24 * r0, b64, c->fine.V, nr, c->stream);
+    wmg_status st = fgcr(c, b64, x64, nr, nullptr, info ? info + r0 : nullptr, mg);
+    if (st != WMG_OK && st != WMG_ENOCONV) return st;
+    if (st != WMG_OK) worst = st;
+    unpack_spinor(WMG_PREC_DOUBLE, x64, x + V * 24 * r0, c->fine.V, nr, c->stream);
+  }
+  CU(c, cudaStreamSynchronize(c->stream));
+  TRY(check(c, "solve"));
+  return worst;
+}
+
+wmg_status wmg_solve_dev(wmg_ctx* c, const double* b, double* x, int nrhs, wmg_info* info) {
+  return solve_dev_impl(c, b, x, nrhs, info, true);
+}
+
+wmg_status wmg_solve_plain_dev(wmg_ctx* c, const double* b, double* x, int nrhs, wmg_info* info) {
+  return solve_dev_impl(c, b, x, nrhs, info, false);
+}
+
+wmg_status wmg_solve(wmg_ctx* c, const double* b_host, double* x_host, int nrhs, wmg_info* info) {
+  if (!c || !b_host || !x_host || nrhs < 1) return WMG_EINVAL;
+  const size_t bytes = (size_t)c->fine.V * 12 * sizeof(cd) * nrhs;
+  void *bd, *xd;
+  TRY(ws_get(c, "host_b", bytes, &bd));
+  TRY(ws_get(c, "host_x", bytes, &xd));
+  CU(c, cudaMemcpyAsync(bd, b_host, bytes, cudaMemcpyHostToDevice, c->stream));
+  wmg_status st = solve_dev_impl(c, (const double*)bd, (double*)xd, nrhs, info, true);
+  if (st != WMG_OK && st != WMG_ENOCONV) return st;
+  CU(c, cudaMemcpyAsync(x_host, xd, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CU(c, cudaStreamSynchronize(c->stream));
+  return st;
+}
+
+wmg_status wmg_pack_spinor(wmg_ctx* c, int prec, const double* canon, void* native, int nrhs) {
+  if (!c || !canon || !native || nrhs < 1 || !prec_ok(prec)) return WMG_EINVAL;
+  pack_spinor(prec, canon, native, c->fine.V, nrhs, c->stream);
+  return check(c, "pack_spinor");
+}
+
+wmg_status wmg_unpack_spinor(wmg_ctx* c, int prec, const void* native, double* canon, int nrhs) {
+  if (!c || !canon || !native || nrhs < 1 || !prec_ok(prec)) return WMG_EINVAL;
+  unpack_spinor(prec, native, canon, c->fine.V, nrhs, c->stream);
+  return check(c, "unpack_spinor");
+}
+
+wmg_status wmg_apply_D(wmg_ctx* c, int prec, const void* in, void* out, int nrhs) {
+  if (!c || !in || !out || nrhs < 1 || nrhs > kMaxRhs || !prec_ok(prec) || in == out) return WMG_EINVAL;
+  if (!c->have_gauge) return WMG_ESTATE;
+  TRY(set_rhs_scalars(c, nullptr, nrhs));
+  dslash(prec, out, in, nullptr, c->gauge[prec], c->fine, c->d_mass, nullptr, nrhs, 0, nullptr, c->stream);
+  return check(c, "apply_D");
+}
+
+wmg_status wmg_restrict(wmg_ctx* c, int level, int prec, const void* fine, void* coarse, int nrhs) {
+  if (!c || !fine || !coarse || nrhs < 1 || !prec_ok(prec)) return WMG_EINVAL;
+  if (level < 0 || level + 1 >= c->nlev || !c->L[level + 1].A[0]) return WMG_ESTATE;
+  const LevelData& L = c->L[level];
+  if (level == 0) restrict_fine(prec, L.P[prec], L.bk, fine, coarse, nrhs, nullptr, c->stream);
+  else restrict_coarse(prec, L.P[prec], L.bk, fine, coarse, nrhs, nullptr, c->stream);
+  return check(c, "restrict");
+}
+
+wmg_status wmg_prolong(wmg_ctx* c, int level, int prec, const void* coarse, void* fine, int nrhs) {
+  if (!c || !fine || !coarse || nrhs < 1 || !prec_ok(prec)) return WMG_EINVAL;
+  if (level < 0 || level + 1 >= c->nlev || !c->L[level + 1].A[0]) return WMG_ESTATE;
+  const LevelData& L = c->L[level];
+  if (level == 0) prolong_fine(prec, L.P[prec], L.bk, coarse, fine, nrhs, nullptr, c->stream);
+  else prolong_coarse(prec, L.P[prec], L.bk, coarse, fine, nrhs, nullptr, c->stream);
+  return check(c, "prolong");
+}
+
+wmg_status wmg_apply_coarse(wmg_ctx* c, int level, int prec, int dagger, const void* in, void* out, int nrhs) {
+  if (!c || !in || !out || nrhs < 1 || nrhs > kMaxRhs || !prec_ok(prec) || in == out) return WMG_EINVAL;
+  if (level < 1 || level >= c->nlev || !c->L[level].A[0]) return WMG_ESTATE;
+  TRY(set_rhs_scalars(c, nullptr, nrhs));
+  const LevelData& L = c->L[level];
+  coarse_apply(prec, L.A[prec], L.g, L.ndof, in, out, nrhs, c->d_shift[level], dagger != 0, nullptr, nullptr,
+               c->stream);
+  return check(c, "apply_coarse");
+}
+
+}  // extern "C"

@@ -1,0 +1,348 @@
+// Level-1 vector kernels of the smoother, the coarsest CGNR and the outer GCR.  Vectors are
+// flat arrays of n complex numbers per right-hand side (any field layout: operands of one
+// call share it).  Every scalar is per right-hand side and lives on the device; reductions
+// are deterministic (fixed-order two-stage sums in double precision).
+#include "kernels.h"
+
+namespace wmg {
+
+constexpr int kBlasMaxBlocks = 148 * 8;
+
+int blas_blocks(size_t n) {
+  size_t b = (n + kBlasThreads - 1) / kBlasThreads;
+  if (b > (size_t)kBlasMaxBlocks) b = kBlasMaxBlocks;
+  return b < 1 ? 1 : (int)b;
+}
+
+#define WMG_GRID_LOOP(i) \
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+
+template <typename R>
+WMG_D cpx<R>* vec(void* p, size_t n, int r) { return reinterpret_cast<cpx<R>*>(p) + n * r; }
+template <typename R>
+WMG_D const cpx<R>* vec(const void* p, size_t n, int r) { return reinterpret_cast<const cpx<R>*>(p) + n * r; }
+
+template <typename R>
+__global__ void k_zero(void* x, size_t n) {
+  cpx<R>* a = vec<R>(x, n, blockIdx.y);
+  WMG_GRID_LOOP(i) a[i] = cpx<R>{R(0), R(0)};
+}
+
+template <typename Rd, typename Rs>
+__global__ void k_convert(void* dst, const void* src, size_t n, const int* mask) {
+  const int r = blockIdx.y;
+  if (mask && !mask[r]) return;
+  cpx<Rd>* d = vec<Rd>(dst, n, r);
+  const cpx<Rs>* s = vec<Rs>(src, n, r);
+  WMG_GRID_LOOP(i) d[i] = ccast<Rd>(s[i]);
+}
+
+template <typename R>
+__global__ void k_xmy(const void* x, void* y, size_t n) {
+  const int r = blockIdx.y;
+  const cpx<R>* a = vec<R>(x, n, r);
+  cpx<R>* b = vec<R>(y, n, r);
+  WMG_GRID_LOOP(i) b[i] = a[i] - b[i];
+}
+
+template <typename R>
+__global__ void k_xpy(const void* x, void* y, size_t n) {
+  const int r = blockIdx.y;
+  const cpx<R>* a = vec<R>(x, n, r);
+  cpx<R>* b = vec<R>(y, n, r);
+  WMG_GRID_LOOP(i) b[i] = a[i] + b[i];
+}
+
+template <typename R>
+__global__ void k_dot_norm(const void* a_, const void* b_, size_t n, RedBuf rb) {
+  const int r = blockIdx.y;
+  const cpx<R>* a = vec<R>(a_, n, r);
+  const cpx<R>* b = vec<R>(b_, n, r);
+  double v[3] = {0, 0, 0};
+  WMG_GRID_LOOP(i) {
+    cpx<R> x = a[i], y = b[i];
+    v[0] += double(x.re) * y.re + double(x.im) * y.im;
+    v[1] += double(x.re) * y.im - double(x.im) * y.re;
+    v[2] += double(x.re) * x.re + double(x.im) * x.im;
+  }
+  __shared__ double sm[32 * 3];
+  cta_reduce<3>(v, sm);
+  grid_finish<3>(rb, r, blockIdx.x, gridDim.x, v);
+}
+
+template <typename R>
+__global__ void k_norm2(const void* a_, size_t n, RedBuf rb) {
+  const int r = blockIdx.y;
+  const cpx<R>* a = vec<R>(a_, n, r);
+  double v[1] = {0};
+  WMG_GRID_LOOP(i) {
+    cpx<R> x = a[i];
+    v[0] += double(x.re) * x.re + double(x.im) * x.im;
+  }
+  __shared__ double sm[32];
+  cta_reduce<1>(v, sm);
+  grid_finish<1>(rb, r, blockIdx.x, gridDim.x, v);
+}
+
+template <typename R>
+__global__ void k_scale_inv_sqrt(void* x, size_t n, const double* nrm2, int stride) {
+  const int r = blockIdx.y;
+  const double q = nrm2[(size_t)r * stride];
+  if (!(q > 0.0)) return;
+  const R s = R(1.0 / sqrt(q));
+  cpx<R>* a = vec<R>(x, n, r);
+  WMG_GRID_LOOP(i) a[i] = s * a[i];
+}
+
+template <typename R>
+__global__ void k_mr_update(void* x_, void* r_, const void* q_, size_t n, const double* red, const int* active) {
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  const double qq = red[r * 3 + 2];
+  if (!(qq > 0.0)) return;
+  const cpx<R> al{R(red[r * 3 + 0] / qq), R(red[r * 3 + 1] / qq)};
+  cpx<R>* x = vec<R>(x_, n, r);
+  cpx<R>* rr = vec<R>(r_, n, r);
+  const cpx<R>* q = vec<R>(q_, n, r);
+  WMG_GRID_LOOP(i) {
+    cpx<R> ri = rr[i];
+    cfma(x[i], al, ri);
+    cpx<R> t = al * q[i];
+    rr[i] = ri - t;
+  }
+}
+
+// x += alpha p, r -= alpha q with alpha = zz[parity]/qq; |r|^2 reduced; the last CTA marks
+// convergence (|r|^2 <= tol2 |b|^2) and counts the iteration.
+template <typename R>
+__global__ void k_cg_update(void* x_, void* r_, const void* p_, const void* q_, size_t n, CgScalars cg, int parity,
+                            int nrhs, RedBuf rb) {
+  const int r = blockIdx.y;
+  const bool on = !cg.done[r] && cg.qq[r] > 0.0;
+  const R al = on ? R(cg.zz[parity * nrhs + r] / cg.qq[r]) : R(0);
+  cpx<R>* x = vec<R>(x_, n, r);
+  cpx<R>* rr = vec<R>(r_, n, r);
+  const cpx<R>* p = vec<R>(p_, n, r);
+  const cpx<R>* q = vec<R>(q_, n, r);
+  double v[1] = {0};
+  WMG_GRID_LOOP(i) {
+    cpx<R> ri = rr[i];
+    if (on) {
+      x[i] += al * p[i];
+      ri = ri - al * q[i];
+      rr[i] = ri;
+    }
+    v[0] += double(ri.re) * ri.re + double(ri.im) * ri.im;
+  }
+  __shared__ double sm[32];
+  cta_reduce<1>(v, sm);
+  grid_finish<1>(rb, r, blockIdx.x, gridDim.x, v);
+}
+
+__global__ void k_cg_flags(CgScalars cg, int nrhs) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs || cg.done[r]) return;
+  cg.iters[r] += 1;
+  if (cg.rr[r] <= cg.tol2 * cg.bb[r]) cg.done[r] = 1;
+}
+
+// p = z + beta p, beta = zz[1-parity]/zz[parity]
+template <typename R>
+__global__ void k_cg_xpay(void* p_, const void* z_, size_t n, CgScalars cg, int parity, int nrhs) {
+  const int r = blockIdx.y;
+  if (cg.done[r]) return;
+  const double zo = cg.zz[parity * nrhs + r];
+  const R be = zo > 0.0 ? R(cg.zz[(1 - parity) * nrhs + r] / zo) : R(0);
+  cpx<R>* p = vec<R>(p_, n, r);
+  const cpx<R>* z = vec<R>(z_, n, r);
+  WMG_GRID_LOOP(i) p[i] = z[i] + be * p[i];
+}
+
+// coef_j = <W_j, w> for j = j0 .. j0+J-1 (j < kmax)
+template <typename R, int J>
+__global__ void k_multidot(const void* W, size_t slot_stride, int j0, int kmax, const void* w_, size_t n,
+                           const int* active, RedBuf rb) {
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  const cpx<R>* w = vec<R>(w_, n, r);
+  double v[2 * J];
+#pragma unroll
+  for (int j = 0; j < 2 * J; ++j) v[j] = 0.0;
+  WMG_GRID_LOOP(i) {
+    const cpx<R> b = w[i];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      if (j0 + j < kmax) {
+        const cpx<R> a = vec<R>((const char*)W + (j0 + j) * slot_stride, n, r)[i];
+        v[2 * j] += double(a.re) * b.re + double(a.im) * b.im;
+        v[2 * j + 1] += double(a.re) * b.im - double(a.im) * b.re;
+      }
+    }
+  }
+  __shared__ double sm[32 * 2 * J];
+  cta_reduce<2 * J>(v, sm);
+  grid_finish<2 * J>(rb, r, blockIdx.x, gridDim.x, v);
+}
+
+constexpr int kDotChunk = 8;
+
+// w -= sum_{j<k} c_j W_j ; z -= sum c_j Z_j ; red = {|w|^2, Re<w,r>, Im<w,r>}
+template <typename R>
+__global__ void k_gcr_orth(const void* W, const void* Z, size_t slot_stride, int k, void* w_, void* z_,
+                           const void* r_, const double* coef, int nrhs, size_t n, const int* active, RedBuf rb) {
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  __shared__ cpx<R> c[kMaxKrylov];
+  if (threadIdx.x < k) {
+    const int j = threadIdx.x;
+    const double* cc = coef + ((size_t)(j / kDotChunk) * nrhs + r) * (2 * kDotChunk) + 2 * (j % kDotChunk);
+    c[j] = cpx<R>{R(cc[0]), R(cc[1])};
+  }
+  __syncthreads();
+  cpx<R>* w = vec<R>(w_, n, r);
+  cpx<R>* z = vec<R>(z_, n, r);
+  const cpx<R>* rv = vec<R>(r_, n, r);
+  double v[3] = {0, 0, 0};
+  WMG_GRID_LOOP(i) {
+    cpx<R> wi = w[i], zi = z[i];
+    for (int j = 0; j < k; ++j) {
+      const cpx<R> cj = c[j];
+      wi = wi - cj * vec<R>((const char*)W + j * slot_stride, n, r)[i];
+      zi = zi - cj * vec<R>((const char*)Z + j * slot_stride, n, r)[i];
+    }
+    w[i] = wi;
+    z[i] = zi;
+    const cpx<R> ri = rv[i];
+    v[0] += double(wi.re) * wi.re + double(wi.im) * wi.im;
+    v[1] += double(wi.re) * ri.re + double(wi.im) * ri.im;
+    v[2] += double(wi.re) * ri.im - double(wi.im) * ri.re;
+  }
+  __shared__ double sm[32 * 3];
+  cta_reduce<3>(v, sm);
+  grid_finish<3>(rb, r, blockIdx.x, gridDim.x, v);
+}
+
+// alpha = <w,r>/|w|^2; x64 += alpha z; r -= alpha w; w, z scaled by 1/|w|; red = |r|^2
+template <typename R>
+__global__ void k_gcr_update(double* x64, void* r_, void* w_, void* z_, const double* wred, size_t n,
+                             const int* active, RedBuf rb) {
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  const double ww = wred[r * 3 + 0];
+  const bool ok = ww > 0.0;
+  const double inv = ok ? 1.0 / sqrt(ww) : 0.0;
+  const cd al{ok ? wred[r * 3 + 1] / ww : 0.0, ok ? wred[r * 3 + 2] / ww : 0.0};
+  const cpx<R> alr{R(al.re), R(al.im)};
+  cd* x = reinterpret_cast<cd*>(x64) + n * r;
+  cpx<R>* rv = vec<R>(r_, n, r);
+  cpx<R>* w = vec<R>(w_, n, r);
+  cpx<R>* z = vec<R>(z_, n, r);
+  double v[1] = {0};
+  WMG_GRID_LOOP(i) {
+    const cpx<R> zi = z[i], wi = w[i];
+    cd xi = x[i];
+    cfma(xi, al, cd{double(zi.re), double(zi.im)});
+    x[i] = xi;
+    const cpx<R> ri = rv[i] - alr * wi;
+    rv[i] = ri;
+    w[i] = R(inv) * wi;
+    z[i] = R(inv) * zi;
+    v[0] += double(ri.re) * ri.re + double(ri.im) * ri.im;
+  }
+  __shared__ double sm[32];
+  cta_reduce<1>(v, sm);
+  grid_finish<1>(rb, r, blockIdx.x, gridDim.x, v);
+}
+
+// ------------------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------------------
+#define WMG_BY_PREC(prec, KER, ...)          \
+  do {                                       \
+    if ((prec) == WMG_PREC_DOUBLE) KER<double>__VA_ARGS__; \
+    else KER<float>__VA_ARGS__;              \
+  } while (0)
+
+void blas_zero(int prec, void* x, size_t n, int nrhs, cudaStream_t s) {
+  dim3 g(blas_blocks(n), nrhs);
+  WMG_BY_PREC(prec, k_zero, <<<g, kBlasThreads, 0, s>>>(x, n));
+}
+
+void blas_convert(int pd, void* dst, int ps, const void* src, size_t n, int nrhs, const int* mask, cudaStream_t s) {
+  dim3 g(blas_blocks(n), nrhs);
+  if (pd == WMG_PREC_DOUBLE && ps == WMG_PREC_DOUBLE) k_convert<double, double><<<g, kBlasThreads, 0, s>>>(dst, src, n, mask);
+  else if (pd == WMG_PREC_DOUBLE) k_convert<double, float><<<g, kBlasThreads, 0, s>>>(dst, src, n, mask);
+  else if (ps == WMG_PREC_DOUBLE) k_convert<float, double><<<g, kBlasThreads, 0, s>>>(dst, src, n, mask);
+  else k_convert<float, float><<<g, kBlasThreads, 0, s>>>(dst, src, n, mask);
+}
+
+void blas_xmy(int prec, const void* x, void* y, size_t n, int nrhs, cudaStream_t s) {
+  dim3 g(blas_blocks(n), nrhs);
+  WMG_BY_PREC(prec, k_xmy, <<<g, kBlasThreads, 0, s>>>(x, y, n));
+}
+
+void blas_xpy(int prec, const void* x, void* y, size_t n, int nrhs, cudaStream_t s) {
+  dim3 g(blas_blocks(n), nrhs);
+  WMG_BY_PREC(prec, k_xpy, <<<g, kBlasThreads, 0, s>>>(x, y, n));
+}
+
+void blas_dot_norm(int prec, const void* a, const void* b, size_t n, int nrhs, const RedBuf& rb, cudaStream_t s) {
+  dim3 g(blas_blocks(n), nrhs);
+  WMG_BY_PREC(prec, k_dot_norm, <<<g, kBlasThreads, 0, s>>>(a, b, n, rb));
+}
+
+void blas_norm2(int prec, const void* a, size_t n, int nrhs, const RedBuf& rb, cudaStream_t s) {
+  dim3 g(blas_blocks(n), nrhs);
+  WMG_BY_PREC(prec, k_norm2, <<<g, kBlasThreads, 0, s>>>(a, n, rb));
+}
+
+void blas_scale_inv_sqrt(int prec, void* x, size_t n, int nrhs, const double* nrm2, int stride, cudaStream_t s) {
+  dim3 g(blas_blocks(n), nrhs);
+  WMG_BY_PREC(prec, k_scale_inv_sqrt, <<<g, kBlasThreads, 0, s>>>(x, n, nrm2, stride));
+}
+
+void blas_mr_update(int prec, void* x, void* r, const void* q, size_t n, int nrhs, const double* red,
+                    const int* active, cudaStream_t s) {
+  dim3 g(blas_blocks(n), nrhs);
+  WMG_BY_PREC(prec, k_mr_update, <<<g, kBlasThreads, 0, s>>>(x, r, q, n, red, active));
+}
+
+void cg_update(int prec, void* x, void* r, const void* p, const void* q, size_t n, int nrhs, const CgScalars& cg,
+               int parity, const RedBuf& rb_rr, cudaStream_t s) {
+  dim3 g(blas_blocks(n), nrhs);
+  WMG_BY_PREC(prec, k_cg_update, <<<g, kBlasThreads, 0, s>>>(x, r, p, q, n, cg, parity, nrhs, rb_rr));
+  k_cg_flags<<<(nrhs + 63) / 64, 64, 0, s>>>(cg, nrhs);
+}
+
+void cg_xpay(int prec, void* p, const void* z, size_t n, int nrhs, const CgScalars& cg, int parity, cudaStream_t s) {
+  dim3 g(blas_blocks(n), nrhs);
+  WMG_BY_PREC(prec, k_cg_xpay, <<<g, kBlasThreads, 0, s>>>(p, z, n, cg, parity, nrhs));
+}
+
+void gcr_multidot(int prec, const void* W, size_t slot_stride, int kmax, const void* w, size_t n, int nrhs,
+                  const int* active, const RedBuf& rb, cudaStream_t s) {
+  dim3 g(blas_blocks(n), nrhs);
+  for (int j0 = 0; j0 < kmax; j0 += kDotChunk) {
+    RedBuf r = rb;
+    r.result = rb.result + (size_t)(j0 / kDotChunk) * nrhs * 2 * kDotChunk;
+    if (prec == WMG_PREC_DOUBLE)
+      k_multidot<double, kDotChunk><<<g, kBlasThreads, 0, s>>>(W, slot_stride, j0, kmax, w, n, active, r);
+    else
+      k_multidot<float, kDotChunk><<<g, kBlasThreads, 0, s>>>(W, slot_stride, j0, kmax, w, n, active, r);
+  }
+}
+
+void gcr_orth(int prec, const void* W, const void* Z, size_t slot_stride, int k, void* w, void* z, const void* r,
+              const double* coef, int kmax, size_t n, int nrhs, const int* active, const RedBuf& rb, cudaStream_t s) {
+  (void)kmax;
+  dim3 g(blas_blocks(n), nrhs);
+  WMG_BY_PREC(prec, k_gcr_orth, <<<g, kBlasThreads, 0, s>>>(W, Z, slot_stride, k, w, z, r, coef, nrhs, n, active, rb));
+}
+
+void gcr_update(int prec, double* x64, void* r, void* w, void* z, const double* wred, size_t n, int nrhs,
+                const int* active, const RedBuf& rb, cudaStream_t s) {
+  dim3 g(blas_blocks(n), nrhs);
+  WMG_BY_PREC(prec, k_gcr_update, <<<g, kBlasThreads, 0, s>>>(x64, r, w, z, wred, n, active, rb));
+}
+
+}  // namespace wmg

@@ -1,0 +1,287 @@
+// Galerkin coarse operator D^ = P^dag D P (Sec. 2) as a 9-point stencil of n x n complex
+// blocks (n = 2N, chirality-split, Sec. 3) and its application.
+//
+// Storage: A[site][slot][col][row] complex (column-major blocks, so that the threads of a
+// site, one per row, read consecutive addresses).  Slot 0 is the self coupling, slot
+// 1 + 2 mu + (0: +mu, 1: -mu) multiplies phi(xhat +/- mu):
+//   (D^ phi)(xhat) = sum_k A[xhat][k] phi(xhat + k).
+// The adjoint is sigma_3 D^ sigma_3 (gamma_5-hermiticity carried to the coarse level, Sec. 3).
+#include "kernels.h"
+#include "wilson.cuh"
+
+namespace wmg {
+
+WMG_D int stencil_neighbour(const Geom& g, int v, const int c[4], int slot) {
+  if (slot == 0) return v;
+  const int mu = (slot - 1) >> 1, sign = ((slot - 1) & 1) ? -1 : +1;
+  return neighbour(g, v, c, mu, sign);
+}
+
+// the neighbour in direction (mu, sign) of a site with coordinate x lies in the same block
+WMG_HD bool same_block(int x, int L, int b, int sign) {
+  int y = x + sign;
+  if (y < 0) y += L;
+  if (y >= L) y -= L;
+  return (x / b) == (y / b);
+}
+
+// ------------------------------------------------------------------------------------
+// apply: thread per (site, row) and RC right-hand sides
+// ------------------------------------------------------------------------------------
+template <typename R, int RC>
+__global__ void k_coarse_apply(const void* __restrict__ A_, Geom g, int n, const void* __restrict__ in_,
+                               void* __restrict__ out_, int nrhs, const double* __restrict__ shift, int dagger,
+                               const int* __restrict__ active, RedBuf rb, int want_norm) {
+  const int spc = blockDim.x / n;  // sites per CTA
+  const int ls = threadIdx.x / n, row = threadIdx.x % n;
+  const int v = blockIdx.x * spc + ls;
+  const int r0 = blockIdx.y * RC;
+  const int N = n / 2;
+  const cpx<R>* A = reinterpret_cast<const cpx<R>*>(A_);
+  const cpx<R>* in = reinterpret_cast<const cpx<R>*>(in_);
+  cpx<R>* out = reinterpret_cast<cpx<R>*>(out_);
+  double nv[RC];
+#pragma unroll
+  for (int rr = 0; rr < RC; ++rr) nv[rr] = 0.0;
+  if (ls < spc && v < g.V) {
+    cpx<R> acc[RC];
+#pragma unroll
+    for (int rr = 0; rr < RC; ++rr) acc[rr] = cpx<R>{R(0), R(0)};
+    int c[4];
+    site_coords(g, v, c);
+    for (int k = 0; k < 9; ++k) {
+      const int nb = stencil_neighbour(g, v, c, k);
+      const cpx<R>* Ak = A + ((size_t)v * 9 + k) * n * n + row;
+      for (int j = 0; j < n; ++j) {
+        const cpx<R> a = Ak[(size_t)j * n];
+        const bool neg = dagger && j >= N;
+#pragma unroll
+        for (int rr = 0; rr < RC; ++rr) {
+          const int r = r0 + rr < nrhs ? r0 + rr : nrhs - 1;
+          cpx<R> x = in[((size_t)r * g.V + nb) * n + j];
+          if (neg) x = -x;
+          cfma(acc[rr], a, x);
+        }
+      }
+    }
+    const bool oneg = dagger && row >= N;
+#pragma unroll
+    for (int rr = 0; rr < RC; ++rr) {
+      const int r = r0 + rr;
+      if (r >= nrhs) continue;
+      cpx<R> o = oneg ? -acc[rr] : acc[rr];
+      if (shift) o += R(shift[r]) * in[((size_t)r * g.V + v) * n + row];
+      if (!active || active[r]) out[((size_t)r * g.V + v) * n + row] = o;
+      nv[rr] = double(o.re) * o.re + double(o.im) * o.im;
+    }
+  }
+  if (want_norm) {
+    __shared__ double sm[32 * RC];
+    cta_reduce<RC>(nv, sm);
+    // partial[r][blk]; counter per rhs chunk; the last CTA of the chunk sums every rhs of it
+    __shared__ bool last;
+    const int nblk = gridDim.x;
+    if (threadIdx.x == 0) {
+      for (int rr = 0; rr < RC; ++rr)
+        if (r0 + rr < nrhs) rb.partial[(size_t)(r0 + rr) * nblk + blockIdx.x] = nv[rr];
+      __threadfence();
+      const unsigned prev = atomicAdd(rb.counter + blockIdx.y, 1u);
+      last = prev == (unsigned)nblk - 1;
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      if (threadIdx.x < RC && r0 + threadIdx.x < nrhs) {
+        const volatile double* p = rb.partial + (size_t)(r0 + threadIdx.x) * nblk;
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += p[b];
+        rb.result[r0 + threadIdx.x] = s;
+      }
+      if (threadIdx.x == 0) rb.counter[blockIdx.y] = 0u;
+    }
+  }
+}
+
+template <typename R, int RC>
+static void launch_coarse_apply(const void* A, const Geom& g, int n, const void* in, void* out, int nrhs,
+                                const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s) {
+  int spc = 256 / n;
+  if (spc < 1) spc = 1;
+  const int T = ((spc * n + 31) / 32) * 32;
+  dim3 grid((g.V + spc - 1) / spc, (nrhs + RC - 1) / RC);
+  RedBuf r = rb ? *rb : RedBuf{nullptr, nullptr, nullptr};
+  k_coarse_apply<R, RC><<<grid, T, 0, s>>>(A, g, n, in, out, nrhs, shift, dagger ? 1 : 0, active, r, rb ? 1 : 0);
+}
+
+void coarse_apply(int prec, const void* A, const Geom& g, int n, const void* in, void* out, int nrhs,
+                  const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s) {
+  if (prec == WMG_PREC_DOUBLE) {
+    if (nrhs == 1) launch_coarse_apply<double, 1>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
+    else if (nrhs == 2) launch_coarse_apply<double, 2>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
+    else launch_coarse_apply<double, 4>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
+  } else {
+    if (nrhs == 1) launch_coarse_apply<float, 1>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
+    else if (nrhs == 2) launch_coarse_apply<float, 2>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
+    else if (nrhs <= 4) launch_coarse_apply<float, 4>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
+    else launch_coarse_apply<float, 8>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Galerkin build, fine level.  For column c = (s, alpha) the field g_c holds P_alpha
+// restricted to chirality s in every block.  Each hop term of D g_c at site x goes to the
+// self field if its neighbour lies in the block of x, else to the field of its slot; the
+// diagonal (4 + m) g_c goes to the self field.  Output: [cc][9] native fine fields.
+// ------------------------------------------------------------------------------------
+template <typename R>
+__global__ void k_hop_split_fine(const void* __restrict__ gauge, const void* __restrict__ P, Blocking bk, R diag,
+                                 int col0, void* __restrict__ out9) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cc = blockIdx.y;
+  const Geom& g = bk.fine;
+  if (v >= g.V) return;
+  const int col = col0 + cc, s = col / bk.N, a = col % bk.N;
+  const size_t fb = spinor_field_bytes<R>(g.V);
+  const char* Pa = (const char*)P + fb * a;
+  char* o = (char*)out9 + fb * (size_t)cc * 9;
+  int c[4];
+  site_coords(g, v, c);
+  cpx<R> self[12], t[12];
+  load_spinor<R>(Pa, g.V, v, self);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) self[k] = ((k < 6) == (s == 0)) ? diag * self[k] : cpx<R>{R(0), R(0)};
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll
+    for (int sg = 0; sg < 2; ++sg) {
+      const int sign = sg ? -1 : +1;
+      const int slot = 1 + 2 * mu + sg;
+      const int nb = neighbour(g, v, c, mu, sign);
+      cpx<R> u[9], x[12];
+      load_spinor<R>(Pa, g.V, nb, x);
+#pragma unroll
+      for (int k = 0; k < 12; ++k)
+        if ((k < 6) != (s == 0)) x[k] = cpx<R>{R(0), R(0)};
+#pragma unroll
+      for (int k = 0; k < 12; ++k) t[k] = cpx<R>{R(0), R(0)};
+      if (sg == 0) {
+        load_link<R>(gauge, g.V, mu, v, u);
+        hop_accumulate<+1>(mu, u, x, t);
+      } else {
+        load_link<R>(gauge, g.V, mu, nb, u);
+        hop_accumulate<-1>(mu, u, x, t);
+      }
+#pragma unroll
+      for (int k = 0; k < 12; ++k) t[k] = R(-0.5) * t[k];
+      const bool inb = same_block(c[mu], g.L[mu], bk.b[mu], sign);
+      if (inb) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) self[k] += t[k];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) t[k] = cpx<R>{R(0), R(0)};
+      }
+      store_spinor<R>(o + fb * slot, g.V, v, t);
+    }
+  }
+  store_spinor<R>(o, g.V, v, self);
+}
+
+void hop_split_fine(int prec, const void* gauge, const void* P, const Blocking& bk, double mass, int col0, int ncol,
+                    void* out9, cudaStream_t s) {
+  dim3 grid((bk.fine.V + 127) / 128, ncol);
+  if (prec == WMG_PREC_DOUBLE)
+    k_hop_split_fine<double><<<grid, 128, 0, s>>>(gauge, P, bk, 4.0 + mass, col0, out9);
+  else
+    k_hop_split_fine<float><<<grid, 128, 0, s>>>(gauge, P, bk, float(4.0 + mass), col0, out9);
+}
+
+// Galerkin build, coarse level: the same split for the stencil A of the finer coarse lattice.
+// Thread per (site of bk.fine, row).  Output: [cc][9] coarse fields [Vf][nf].
+template <typename R>
+__global__ void k_hop_split_coarse(const void* __restrict__ A_, const void* __restrict__ P_, Blocking bk, int col0,
+                                   void* __restrict__ out9) {
+  const int nf = bk.nf, h = nf / 2;
+  const int spc = blockDim.x / nf;
+  const int ls = threadIdx.x / nf, row = threadIdx.x % nf;
+  const int v = blockIdx.x * spc + ls;
+  const Geom& g = bk.fine;
+  if (ls >= spc || v >= g.V) return;
+  const int cc = blockIdx.y, col = col0 + cc, s = col / bk.N, a = col % bk.N;
+  const cpx<R>* A = reinterpret_cast<const cpx<R>*>(A_);
+  const cpx<R>* P = reinterpret_cast<const cpx<R>*>(P_) + (size_t)a * g.V * nf;
+  cpx<R>* o = reinterpret_cast<cpx<R>*>(out9) + (size_t)cc * 9 * g.V * nf;
+  int c[4];
+  site_coords(g, v, c);
+  cpx<R> self{R(0), R(0)};
+  for (int k = 0; k < 9; ++k) {
+    const int nb = stencil_neighbour(g, v, c, k);
+    const cpx<R>* Ak = A + ((size_t)v * 9 + k) * nf * nf + row;
+    cpx<R> t{R(0), R(0)};
+    for (int j = s * h; j < (s + 1) * h; ++j) cfma(t, Ak[(size_t)j * nf], P[(size_t)nb * nf + j]);
+    bool inb = true;
+    if (k > 0) {
+      const int mu = (k - 1) >> 1, sign = ((k - 1) & 1) ? -1 : +1;
+      inb = same_block(c[mu], g.L[mu], bk.b[mu], sign);
+    }
+    if (inb) {
+      self += t;
+      if (k > 0) o[((size_t)k * g.V + v) * nf + row] = cpx<R>{R(0), R(0)};
+    } else {
+      o[((size_t)k * g.V + v) * nf + row] = t;
+    }
+  }
+  o[(size_t)v * nf + row] = self;
+}
+
+void hop_split_coarse(int prec, const void* A, const void* P, const Blocking& bk, int col0, int ncol, void* out9,
+                      cudaStream_t s) {
+  int spc = 256 / bk.nf;
+  if (spc < 1) spc = 1;
+  const int T = ((spc * bk.nf + 31) / 32) * 32;
+  dim3 grid((bk.fine.V + spc - 1) / spc, ncol);
+  if (prec == WMG_PREC_DOUBLE) k_hop_split_coarse<double><<<grid, T, 0, s>>>(A, P, bk, col0, out9);
+  else k_hop_split_coarse<float><<<grid, T, 0, s>>>(A, P, bk, col0, out9);
+}
+
+// rs: [cc][9][Vc][n] restricted slot fields -> A[site][slot][col0 + cc][row]
+template <typename R>
+__global__ void k_stencil_scatter(const cpx<R>* __restrict__ rs, cpx<R>* __restrict__ A, int Vc, int n, int col0,
+                                  int ncol) {
+  const size_t tot = (size_t)ncol * 9 * Vc * n;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
+    const int row = (int)(i % n);
+    size_t t = i / n;
+    const int site = (int)(t % Vc);
+    t /= Vc;
+    const int slot = (int)(t % 9);
+    const int cc = (int)(t / 9);
+    A[(((size_t)site * 9 + slot) * n + (col0 + cc)) * n + row] = rs[i];
+  }
+}
+
+void stencil_scatter(int prec, const void* rs, void* A, int Vc, int n, int col0, int ncol, cudaStream_t s) {
+  const size_t tot = (size_t)ncol * 9 * Vc * n;
+  int B = (int)((tot + 255) / 256);
+  if (B > 148 * 16) B = 148 * 16;
+  if (prec == WMG_PREC_DOUBLE)
+    k_stencil_scatter<double><<<B, 256, 0, s>>>((const cd*)rs, (cd*)A, Vc, n, col0, ncol);
+  else
+    k_stencil_scatter<float><<<B, 256, 0, s>>>((const cf*)rs, (cf*)A, Vc, n, col0, ncol);
+}
+
+template <typename Rd, typename Rs>
+__global__ void k_stencil_convert(cpx<Rd>* d, const cpx<Rs>* s, size_t count) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    d[i] = ccast<Rd>(s[i]);
+}
+
+void stencil_convert(int pd, void* dst, int ps, const void* src, size_t count, cudaStream_t s) {
+  int B = (int)((count + 255) / 256);
+  if (B > 148 * 16) B = 148 * 16;
+  if (pd == WMG_PREC_DOUBLE && ps == WMG_PREC_DOUBLE) k_stencil_convert<double, double><<<B, 256, 0, s>>>((cd*)dst, (const cd*)src, count);
+  else if (pd == WMG_PREC_DOUBLE) k_stencil_convert<double, float><<<B, 256, 0, s>>>((cd*)dst, (const cf*)src, count);
+  else if (ps == WMG_PREC_DOUBLE) k_stencil_convert<float, double><<<B, 256, 0, s>>>((cf*)dst, (const cd*)src, count);
+  else k_stencil_convert<float, float><<<B, 256, 0, s>>>((cf*)dst, (const cf*)src, count);
+}
+
+}  // namespace wmg

@@ -1,0 +1,52 @@
+// Internal state of a libwmg context.
+#pragma once
+#include <string>
+#include <vector>
+#include <map>
+
+#include "kernels.h"
+
+namespace wmg {
+
+struct LevelData {
+  Geom g;            // lattice of this level
+  int ndof = 12;     // complex dof per site (12 fine, 2N coarse)
+  // coarse operator of this level (levels >= 1): [site][9][col][row], per precision
+  void* A[2] = {nullptr, nullptr};
+  // transfer to the next level (levels < nlev - 1)
+  Blocking bk{};
+  void* P[2] = {nullptr, nullptr};  // N fields of this level, per precision (P[0] = FP64)
+  size_t nvec_elems() const { return (size_t)g.V * ndof; }  // complex numbers per field
+};
+
+}  // namespace wmg
+
+struct wmg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  Geom fine{};
+  void* gauge[2] = {nullptr, nullptr};  // native 12-real links, FP64 and FP32
+  bool have_gauge = false;
+  double mass = 0.0, mass_setup = 0.0;
+  wmg_params prm{};
+  bool have_hier = false;
+  int nlev = 1;
+  wmg::LevelData L[WMG_MAX_LEVELS];
+  std::string err;
+  // allocations
+  std::vector<void*> owned;
+  std::map<std::string, std::pair<void*, size_t>> ws;  // named grow-only workspaces
+  // reductions (shared partials and counters, distinct result arrays)
+  double* red_partial = nullptr;
+  size_t red_partial_n = 0;
+  unsigned* red_counter = nullptr;
+  double* res = nullptr;  // result arena [kResSlots][kMaxRhs * 16]
+  double* d_mass = nullptr;                    // [kMaxRhs] Wilson mass per rhs
+  double* d_shift[WMG_MAX_LEVELS] = {nullptr, nullptr, nullptr};  // coarse shift per rhs
+  int* d_active = nullptr;                     // [kMaxRhs]
+  int* d_mask = nullptr;                       // [kMaxRhs]
+  int* d_flag = nullptr;                       // misc device flag
+  int* d_cgint = nullptr;                      // [2][kMaxRhs] cg done / iters
+  double* h_pin = nullptr;                     // pinned host scratch [4096]
+  int* h_pin_i = nullptr;                      // pinned host scratch [4096]
+};

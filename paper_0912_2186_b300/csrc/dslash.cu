@@ -1,0 +1,175 @@
+// Fine-lattice kernels: gauge 12-real packing (Table 2's "12 floats"), spinor layout
+// conversion and the spin-projected Wilson operator (Sec. 2, eq. for D_xy(U)).
+#include "kernels.h"
+#include "wilson.cuh"
+
+namespace wmg {
+
+// ------------------------------------------------------------------------------------
+// packing
+// ------------------------------------------------------------------------------------
+// canonical U [V][4][3][3] complex double -> native [mu][3][V] chunks (rows 0, 1)
+template <typename R>
+__global__ void k_pack_gauge(const double2* __restrict__ canon, void* __restrict__ out, int V) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  for (int mu = 0; mu < 4; ++mu) {
+    const double2* u = canon + ((size_t)v * 4 + mu) * 9;
+    for (int c = 0; c < 3; ++c) {
+      double2 a = u[2 * c], b = u[2 * c + 1];
+      Chunk2<R>::store(out, (size_t)(mu * 3 + c) * V + v, cpx<R>{R(a.x), R(a.y)}, cpx<R>{R(b.x), R(b.y)});
+    }
+  }
+}
+
+// canonical [rhs][V][12] <-> native [rhs][6][V][2]
+template <typename R>
+__global__ void k_pack_spinor(const double2* __restrict__ canon, void* __restrict__ out, int V, int nrhs) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)V * nrhs) return;
+  int r = (int)(i / V), v = (int)(i % V);
+  const double2* s = canon + i * 12;
+  char* o = reinterpret_cast<char*>(out) + spinor_field_bytes<R>(V) * r;
+  for (int c = 0; c < 6; ++c) {
+    double2 a = s[2 * c], b = s[2 * c + 1];
+    Chunk2<R>::store(o, (size_t)c * V + v, cpx<R>{R(a.x), R(a.y)}, cpx<R>{R(b.x), R(b.y)});
+  }
+}
+template <typename R>
+__global__ void k_unpack_spinor(const void* __restrict__ in, double2* __restrict__ canon, int V, int nrhs) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)V * nrhs) return;
+  int r = (int)(i / V), v = (int)(i % V);
+  const char* p = reinterpret_cast<const char*>(in) + spinor_field_bytes<R>(V) * r;
+  double2* s = canon + i * 12;
+  for (int c = 0; c < 6; ++c) {
+    cpx<R> a, b;
+    Chunk2<R>::load(p, (size_t)c * V + v, a, b);
+    s[2 * c] = make_double2(a.re, a.im);
+    s[2 * c + 1] = make_double2(b.re, b.im);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Wilson operator.  One thread per (site, rhs); the rhs index runs fastest over CTAs so
+// that CTAs working on the same sites for different right-hand sides share the links in
+// L2.  out = (4 + m_r) in - 1/2 sum_mu hops       (b == nullptr)
+//      out = b - D in                               (b != nullptr, residual form)
+// Optional fused reductions per rhs: red0 = {<out, in>, |out|^2} (MR smoother) or
+// {|out|^2} alone.
+// ------------------------------------------------------------------------------------
+template <typename R, int RED>
+__global__ void __launch_bounds__(128) k_dslash(void* __restrict__ out, const void* __restrict__ in,
+                                                const void* __restrict__ b, const void* __restrict__ gauge,
+                                                Geom g, const double* __restrict__ mass, const int* __restrict__ active,
+                                                int nrhs, int nblk_site, RedBuf rb) {
+  const int rhs = blockIdx.x % nrhs;
+  const int sb = blockIdx.x / nrhs;
+  if (active && !active[rhs]) return;  // whole CTA exits together (uniform per CTA)
+  const int v = sb * blockDim.x + threadIdx.x;
+  const size_t fb = spinor_field_bytes<R>(g.V);
+  const char* inr = reinterpret_cast<const char*>(in) + fb * rhs;
+  cpx<R> acc[12];
+  double red[RED > 0 ? RED : 1];
+  for (int i = 0; i < (RED > 0 ? RED : 1); ++i) red[i] = 0.0;
+  if (v < g.V) {
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[i] = cpx<R>{R(0), R(0)};
+    int c[4];
+    site_coords(g, v, c);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      cpx<R> u[9], nb[12];
+      const int vf = neighbour(g, v, c, mu, +1);
+      load_link<R>(gauge, g.V, mu, v, u);
+      load_spinor<R>(inr, g.V, vf, nb);
+      hop_accumulate<+1>(mu, u, nb, acc);
+      const int vb = neighbour(g, v, c, mu, -1);
+      load_link<R>(gauge, g.V, mu, vb, u);
+      load_spinor<R>(inr, g.V, vb, nb);
+      hop_accumulate<-1>(mu, u, nb, acc);
+    }
+    cpx<R> self[12];
+    load_spinor<R>(inr, g.V, v, self);
+    const R diag = R(4.0 + mass[rhs]);
+    const R half = R(-0.5);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      cpx<R> o{diag * self[i].re + half * acc[i].re, diag * self[i].im + half * acc[i].im};
+      acc[i] = o;
+    }
+    if (b) {
+      cpx<R> bb[12];
+      load_spinor<R>(reinterpret_cast<const char*>(b) + fb * rhs, g.V, v, bb);
+#pragma unroll
+      for (int i = 0; i < 12; ++i) acc[i] = bb[i] - acc[i];
+    }
+    store_spinor<R>(reinterpret_cast<char*>(out) + fb * rhs, g.V, v, acc);
+    if (RED == 2) {
+#pragma unroll
+      for (int i = 0; i < 12; ++i) {
+        red[0] += double(acc[i].re) * double(self[i].re) + double(acc[i].im) * double(self[i].im);
+        red[1] += double(acc[i].re) * double(self[i].im) - double(acc[i].im) * double(self[i].re);
+      }
+    }
+    if (RED >= 1) {
+      double n = 0.0;
+#pragma unroll
+      for (int i = 0; i < 12; ++i) n += double(acc[i].re) * double(acc[i].re) + double(acc[i].im) * double(acc[i].im);
+      red[RED == 2 ? 2 : 0] = n;
+    }
+  }
+  if (RED > 0) {
+    constexpr int NV = RED == 2 ? 3 : 1;
+    __shared__ double sm[32 * 3];
+    double vals[NV];
+    for (int i = 0; i < NV; ++i) vals[i] = red[i];
+    cta_reduce<NV>(vals, sm);
+    grid_finish<NV>(rb, rhs, sb, nblk_site, vals);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------------------
+void pack_gauge(int prec, const double* canon, void* out, int V, cudaStream_t s) {
+  const int T = 256, B = (V + T - 1) / T;
+  if (prec == WMG_PREC_DOUBLE) k_pack_gauge<double><<<B, T, 0, s>>>((const double2*)canon, out, V);
+  else k_pack_gauge<float><<<B, T, 0, s>>>((const double2*)canon, out, V);
+}
+
+void pack_spinor(int prec, const double* canon, void* out, int V, int nrhs, cudaStream_t s) {
+  const size_t n = (size_t)V * nrhs;
+  const int T = 256;
+  const unsigned B = (unsigned)((n + T - 1) / T);
+  if (prec == WMG_PREC_DOUBLE) k_pack_spinor<double><<<B, T, 0, s>>>((const double2*)canon, out, V, nrhs);
+  else k_pack_spinor<float><<<B, T, 0, s>>>((const double2*)canon, out, V, nrhs);
+}
+
+void unpack_spinor(int prec, const void* in, double* canon, int V, int nrhs, cudaStream_t s) {
+  const size_t n = (size_t)V * nrhs;
+  const int T = 256;
+  const unsigned B = (unsigned)((n + T - 1) / T);
+  if (prec == WMG_PREC_DOUBLE) k_unpack_spinor<double><<<B, T, 0, s>>>(in, (double2*)canon, V, nrhs);
+  else k_unpack_spinor<float><<<B, T, 0, s>>>(in, (double2*)canon, V, nrhs);
+}
+
+int dslash_blocks(int V) { return (V + kDslashThreads - 1) / kDslashThreads; }
+
+void dslash(int prec, void* out, const void* in, const void* b, const void* gauge, const Geom& g,
+            const double* mass_dev, const int* active, int nrhs, int red, const RedBuf* rb, cudaStream_t s) {
+  const int nb = dslash_blocks(g.V);
+  const unsigned grid = (unsigned)nb * nrhs;
+  RedBuf r = rb ? *rb : RedBuf{nullptr, nullptr, nullptr};
+#define WMG_DS(R)                                                                                             \
+  do {                                                                                                        \
+    if (red == 0) k_dslash<R, 0><<<grid, kDslashThreads, 0, s>>>(out, in, b, gauge, g, mass_dev, active, nrhs, nb, r); \
+    else if (red == 1) k_dslash<R, 1><<<grid, kDslashThreads, 0, s>>>(out, in, b, gauge, g, mass_dev, active, nrhs, nb, r); \
+    else k_dslash<R, 2><<<grid, kDslashThreads, 0, s>>>(out, in, b, gauge, g, mass_dev, active, nrhs, nb, r); \
+  } while (0)
+  if (prec == WMG_PREC_DOUBLE) WMG_DS(double);
+  else WMG_DS(float);
+#undef WMG_DS
+}
+
+}  // namespace wmg

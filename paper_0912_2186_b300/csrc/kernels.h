@@ -1,0 +1,105 @@
+// Internal launch interface of the libwmg kernels (host side, not part of the C ABI).
+#pragma once
+#include "wmg_common.cuh"
+
+namespace wmg {
+
+constexpr int kDslashThreads = 128;
+constexpr int kBlasThreads = 256;
+constexpr int kMaxRhs = 64;          // right-hand sides per batched launch
+constexpr int kMaxKrylov = 32;       // outer GCR restart length limit
+
+inline size_t prec_real_bytes(int prec) { return prec == WMG_PREC_DOUBLE ? 8 : 4; }
+
+// ---- fine lattice (dslash.cu) ----
+void pack_gauge(int prec, const double* canon, void* out, int V, cudaStream_t s);
+void pack_spinor(int prec, const double* canon, void* out, int V, int nrhs, cudaStream_t s);
+void unpack_spinor(int prec, const void* in, double* canon, int V, int nrhs, cudaStream_t s);
+int dslash_blocks(int V);
+// out = D in, or out = b - D in when b != nullptr.  mass_dev[nrhs]: per-rhs Wilson mass.
+// red = 0: none; 1: |out|^2 per rhs into rb->result[rhs]; 2: {Re, Im <out,in>, |out|^2}.
+void dslash(int prec, void* out, const void* in, const void* b, const void* gauge, const Geom& g,
+            const double* mass_dev, const int* active, int nrhs, int red, const RedBuf* rb, cudaStream_t s);
+
+// ---- BLAS on flat complex vectors: n complex numbers per rhs, rhs stride n (blas.cu) ----
+int blas_blocks(size_t n);
+void blas_zero(int prec, void* x, size_t n, int nrhs, cudaStream_t s);
+// dst (prec_d) = src (prec_s) for rhs with mask==nullptr or mask[r] != 0
+void blas_convert(int prec_d, void* dst, int prec_s, const void* src, size_t n, int nrhs, const int* mask,
+                  cudaStream_t s);
+// result[r] = {Re <a,b>, Im <a,b>, |a|^2}
+void blas_dot_norm(int prec, const void* a, const void* b, size_t n, int nrhs, const RedBuf& rb, cudaStream_t s);
+// result[r] = {|a|^2}
+void blas_norm2(int prec, const void* a, size_t n, int nrhs, const RedBuf& rb, cudaStream_t s);
+// x[r] *= scale[r] (scale double, per rhs; skip where scale pointer entry is not finite)
+void blas_scale_inv_sqrt(int prec, void* x, size_t n, int nrhs, const double* norm2, int stride, cudaStream_t s);
+// y = x - y  (y := x - y)
+void blas_xmy(int prec, const void* x, void* y, size_t n, int nrhs, cudaStream_t s);
+// y = x + y
+void blas_xpy(int prec, const void* x, void* y, size_t n, int nrhs, cudaStream_t s);
+// MR update: alpha = qr/qq from red[r*3 + {0,1,2}]; x += alpha r; r -= alpha q
+void blas_mr_update(int prec, void* x, void* r, const void* q, size_t n, int nrhs, const double* red,
+                    const int* active, cudaStream_t s);
+// CG (normal equations) helpers, scalars per rhs in `cg` (see blas.cu)
+struct CgScalars {
+  double* zz;       // [2][nrhs]  |z|^2, double-buffered by iteration parity
+  double* rr;       // [nrhs] (RedBuf result of the update kernel)
+  double* qq;       // [nrhs]
+  double* bb;       // [nrhs]
+  int* done;        // [nrhs]
+  int* iters;       // [nrhs]
+  double tol2;
+};
+void cg_update(int prec, void* x, void* r, const void* p, const void* q, size_t n, int nrhs, const CgScalars& cg,
+               int parity, const RedBuf& rb_rr, cudaStream_t s);
+void cg_xpay(int prec, void* p, const void* z, size_t n, int nrhs, const CgScalars& cg, int parity, cudaStream_t s);
+// GCR
+// coef[r*kmax + j] = <W_j, w> for j < kmax  (W_j at W + j*slot_stride)
+void gcr_multidot(int prec, const void* W, size_t slot_stride, int kmax, const void* w, size_t n, int nrhs,
+                  const int* active, const RedBuf& rb, cudaStream_t s);
+// w -= sum_j c_j W_j, z -= sum_j c_j Z_j, then red = {|w|^2, Re<w,r>, Im<w,r>}
+void gcr_orth(int prec, const void* W, const void* Z, size_t slot_stride, int k, void* w, void* z, const void* r,
+              const double* coef, int kmax, size_t n, int nrhs, const int* active, const RedBuf& rb, cudaStream_t s);
+// alpha = <w,r>/|w|^2, x64 += alpha z, r -= alpha w, w /= |w|, z /= |w|; red = |r|^2
+void gcr_update(int prec, double* x64, void* r, void* w, void* z, const double* wred, size_t n, int nrhs,
+                const int* active, const RedBuf& rb, cudaStream_t s);
+
+// ---- transfer (transfer.cu) ----
+struct Blocking {
+  Geom fine, coarse;
+  int b[4];      // block extents
+  int bs;        // sites per block
+  int N;         // vectors
+  int nf;        // complex dof per fine site (12 on the fine lattice, 2N' on a coarse one)
+};
+// fine level: fine spinors (native) <-> coarse vectors; P = N native fine fields
+void restrict_fine(int prec, const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
+                   const int* active, cudaStream_t s);
+void prolong_fine(int prec, const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
+                  const int* active, cudaStream_t s);
+// coarse level: coarse vectors [rhs][Vf][nf] <-> [rhs][Vc][2N]; P = N coarse fields
+void restrict_coarse(int prec, const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
+                     const int* active, cudaStream_t s);
+void prolong_coarse(int prec, const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
+                    const int* active, cudaStream_t s);
+// block Gram-Schmidt (FP64, in place) on N vectors; fine: native FP64 fields, coarse: coarse
+// FP64 fields.  rank_flag: device int set to 1 on rank deficiency.
+void block_gs(bool fine_level, void* vecs, const Blocking& bk, int* rank_flag, cudaStream_t s);
+
+// ---- coarse operator (coarse.cu) ----
+// stencil layout [site][9][col][row] complex (col-major blocks), n = 2N rows
+// out = A in (+ shift[r] in), or sigma_3 A sigma_3 in for dagger; optional |out|^2 per rhs
+void coarse_apply(int prec, const void* A, const Geom& g, int n, const void* in, void* out, int nrhs,
+                  const double* shift, bool dagger, const int* active, const RedBuf* rb_norm, cudaStream_t s);
+// Galerkin build helpers: split the operator applied to column vectors into 9 slot fields
+// fine level: g = column (s, alpha) of P, written for ncol columns starting at col0
+void hop_split_fine(int prec, const void* gauge, const void* P, const Blocking& bk, double mass, int col0,
+                    int ncol, void* out9, cudaStream_t s);
+void hop_split_coarse(int prec, const void* A, const void* P, const Blocking& bk, int col0, int ncol, void* out9,
+                      cudaStream_t s);
+// scatter restricted slot fields [ncol][9][Vc][n] into the stencil at columns col0..
+void stencil_scatter(int prec, const void* rs, void* A, int Vc, int n, int col0, int ncol, cudaStream_t s);
+// convert a stencil between precisions
+void stencil_convert(int prec_d, void* dst, int prec_s, const void* src, size_t count, cudaStream_t s);
+
+}  // namespace wmg

@@ -1,0 +1,446 @@
+// Host-side driver of libwmg: the multigrid cycle with post-smoothing (Sec. 3), the MR
+// smoother, CG on the normal equations on the coarsest level, flexible GCR on the fine level
+// with FP64 reliable updates, the adaptive setup (Sec. 2) and the Galerkin construction
+// D^ = P^dag D P (Sec. 2).  Every arithmetic step runs in the kernels of this library; the
+// host only sequences launches and reads per-rhs residual norms.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <random>
+
+#include "ctx.h"
+#include "solver.h"
+
+using namespace wmg;
+
+wmg_status wmg_cuda_fail(cudaError_t e, const char* what) {
+  (void)what;
+  return e == cudaErrorMemoryAllocation ? WMG_ENOMEM : WMG_ECUDA;
+}
+
+namespace wmg {
+
+static size_t csize(int prec) { return prec == WMG_PREC_DOUBLE ? sizeof(cd) : sizeof(cf); }
+
+wmg_status fail(wmg_ctx* c, cudaError_t e, const char* what) {
+  c->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? WMG_ENOMEM : WMG_ECUDA;
+}
+
+wmg_status check(wmg_ctx* c, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, e, what);
+  return WMG_OK;
+}
+
+#define TRY(x)                              \
+  do {                                      \
+    wmg_status st_ = (x);                   \
+    if (st_ != WMG_OK) return st_;          \
+  } while (0)
+#define CU(c, x)                                      \
+  do {                                                \
+    cudaError_t e_ = (x);                             \
+    if (e_ != cudaSuccess) return fail((c), e_, #x);  \
+  } while (0)
+
+wmg_status ws_get(wmg_ctx* c, const std::string& name, size_t bytes, void** out) {
+  auto it = c->ws.find(name);
+  if (it != c->ws.end() && it->second.second >= bytes) {
+    *out = it->second.first;
+    return WMG_OK;
+  }
+  if (it != c->ws.end()) {
+    CU(c, cudaStreamSynchronize(c->stream));
+    cudaFree(it->second.first);
+    c->ws.erase(it);
+  }
+  void* p = nullptr;
+  CU(c, cudaMalloc(&p, bytes > 0 ? bytes : 16));
+  c->ws[name] = {p, bytes};
+  *out = p;
+  return WMG_OK;
+}
+
+// vector workspace of level l: nrhs fields of V_l * ndof_l complex numbers
+wmg_status vec_ws(wmg_ctx* c, int l, const char* tag, int prec, int nrhs, void** out) {
+  const size_t n = c->L[l].nvec_elems();
+  return ws_get(c, "v" + std::to_string(l) + tag + (prec == WMG_PREC_DOUBLE ? "d" : "s"), n * nrhs * csize(prec),
+                out);
+}
+
+static double* res_slot(wmg_ctx* c, int slot) { return c->res + (size_t)slot * kMaxRhs * 16; }
+enum { RES_MR = 0, RES_NORM, RES_WRED, RES_RN, RES_R64, RES_BB, RES_CGQQ, RES_CGRR, RES_CGBB, RES_CGZZ,
+       RES_SETUP, RES_COEF = 16, RES_SLOTS = 24 };
+
+RedBuf redbuf(wmg_ctx* c, int slot) { return RedBuf{c->red_partial, c->red_counter, res_slot(c, slot)}; }
+
+wmg_status ensure_partials(wmg_ctx* c, size_t need) {
+  if (need <= c->red_partial_n) return WMG_OK;
+  CU(c, cudaStreamSynchronize(c->stream));
+  if (c->red_partial) cudaFree(c->red_partial);
+  c->red_partial = nullptr;
+  CU(c, cudaMalloc(&c->red_partial, need * sizeof(double)));
+  c->red_partial_n = need;
+  return WMG_OK;
+}
+
+wmg_status ensure_reductions(wmg_ctx* c, int nrhs) {
+  // dslash: nrhs * blocks * 3; blas: nrhs * 1184 * 16; coarse apply: nrhs * blocks
+  size_t need = (size_t)nrhs * (size_t)dslash_blocks(c->fine.V) * 3;
+  need = std::max(need, (size_t)nrhs * 148 * 8 * 16);
+  for (int l = 1; l < c->nlev; ++l) need = std::max(need, (size_t)nrhs * (size_t)c->L[l].g.V);
+  return ensure_partials(c, need);
+}
+
+wmg_status set_rhs_scalars(wmg_ctx* c, const double* masses, int nrhs) {
+  for (int r = 0; r < nrhs; ++r) c->h_pin[r] = masses ? masses[r] : c->mass;
+  CU(c, cudaMemcpyAsync(c->d_mass, c->h_pin, nrhs * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  for (int l = 1; l < c->nlev; ++l) {
+    for (int r = 0; r < nrhs; ++r) c->h_pin[kMaxRhs + r] = (masses ? masses[r] : c->mass) - c->mass_setup;
+    CU(c, cudaMemcpyAsync(c->d_shift[l], c->h_pin + kMaxRhs, nrhs * sizeof(double), cudaMemcpyHostToDevice,
+                          c->stream));
+    CU(c, cudaStreamSynchronize(c->stream));
+  }
+  CU(c, cudaStreamSynchronize(c->stream));
+  return WMG_OK;
+}
+
+wmg_status upload_ints(wmg_ctx* c, int* dst, const std::vector<int>& v) {
+  for (size_t i = 0; i < v.size(); ++i) c->h_pin_i[i] = v[i];
+  CU(c, cudaMemcpyAsync(dst, c->h_pin_i, v.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CU(c, cudaStreamSynchronize(c->stream));
+  return WMG_OK;
+}
+
+wmg_status download(wmg_ctx* c, const double* src, size_t n, std::vector<double>& out) {
+  CU(c, cudaMemcpyAsync(c->h_pin, src, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(c, cudaStreamSynchronize(c->stream));
+  out.assign(c->h_pin, c->h_pin + n);
+  return WMG_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// operators of a level
+// ------------------------------------------------------------------------------------
+// out = A_l in   (l = 0: Wilson D; l >= 1: coarse stencil with the per-rhs shift)
+void level_apply(wmg_ctx* c, int l, int prec, const void* in, void* out, int nrhs, const int* active, int red,
+                 const RedBuf* rb) {
+  if (l == 0) {
+    dslash(prec, out, in, nullptr, c->gauge[prec], c->fine, c->d_mass, active, nrhs, red, rb, c->stream);
+  } else {
+    const LevelData& L = c->L[l];
+    coarse_apply(prec, L.A[prec], L.g, L.ndof, in, out, nrhs, c->d_shift[l], false, active,
+                 red == 1 ? rb : nullptr, c->stream);
+  }
+}
+
+// MR smoother (nu steps) on level l: x is the initial guess and the result, b the rhs
+wmg_status mr(wmg_ctx* c, int l, int prec, void* x, const void* b, int nrhs, int nu, const int* active) {
+  void *r, *q;
+  TRY(vec_ws(c, l, "mr_r", prec, nrhs, &r));
+  TRY(vec_ws(c, l, "mr_q", prec, nrhs, &q));
+  const size_t n = c->L[l].nvec_elems();
+  RedBuf rb = redbuf(c, RES_MR);
+  if (l == 0) {
+    dslash(prec, r, x, b, c->gauge[prec], c->fine, c->d_mass, active, nrhs, 0, nullptr, c->stream);
+  } else {
+    level_apply(c, l, prec, x, r, nrhs, active, 0, nullptr);
+    blas_xmy(prec, b, r, n, nrhs, c->stream);
+  }
+  for (int i = 0; i < nu; ++i) {
+    if (l == 0) {
+      dslash(prec, q, r, nullptr, c->gauge[prec], c->fine, c->d_mass, active, nrhs, 2, &rb, c->stream);
+    } else {
+      level_apply(c, l, prec, r, q, nrhs, active, 0, nullptr);
+      blas_dot_norm(prec, q, r, n, nrhs, rb, c->stream);
+    }
+    blas_mr_update(prec, x, r, q, n, nrhs, rb.result, active, c->stream);
+  }
+  return check(c, "mr");
+}
+
+__global__ void k_cg_init(int* done, int* iters, const double* bb, const int* active, int nrhs) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  iters[r] = 0;
+  done[r] = (active && !active[r]) || !(bb[r] > 0.0);
+}
+
+// CG on the normal equations on level l (coarse): x = A^-1 b approximately
+wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, const int* active) {
+  const LevelData& L = c->L[l];
+  const size_t n = L.nvec_elems();
+  void *r, *p, *q, *z;
+  TRY(vec_ws(c, l, "cg_r", prec, nrhs, &r));
+  TRY(vec_ws(c, l, "cg_p", prec, nrhs, &p));
+  TRY(vec_ws(c, l, "cg_q", prec, nrhs, &q));
+  TRY(vec_ws(c, l, "cg_z", prec, nrhs, &z));
+  CgScalars cg;
+  cg.zz = res_slot(c, RES_CGZZ);
+  cg.rr = res_slot(c, RES_CGRR);
+  cg.qq = res_slot(c, RES_CGQQ);
+  cg.bb = res_slot(c, RES_CGBB);
+  cg.done = c->d_cgint;
+  cg.iters = c->d_cgint + kMaxRhs;
+  cg.tol2 = c->prm.coarse_tol * c->prm.coarse_tol;
+  cudaStream_t s = c->stream;
+  blas_zero(prec, x, n, nrhs, s);
+  blas_convert(prec, r, prec, b, n, nrhs, nullptr, s);
+  blas_norm2(prec, b, n, nrhs, redbuf(c, RES_CGBB), s);
+  RedBuf rzz0{c->red_partial, c->red_counter, cg.zz};
+  coarse_apply(prec, L.A[prec], L.g, L.ndof, r, z, nrhs, c->d_shift[l], true, nullptr, &rzz0, s);
+  blas_convert(prec, p, prec, z, n, nrhs, nullptr, s);
+  k_cg_init<<<1, 64, 0, s>>>(cg.done, cg.iters, cg.bb, active, nrhs);
+  RedBuf rqq{c->red_partial, c->red_counter, cg.qq};
+  RedBuf rrr{c->red_partial, c->red_counter, cg.rr};
+  int parity = 0;
+  const int check_every = 8;
+  for (int it = 0; it < c->prm.coarse_maxit; ++it) {
+    coarse_apply(prec, L.A[prec], L.g, L.ndof, p, q, nrhs, c->d_shift[l], false, nullptr, &rqq, s);
+    cg_update(prec, x, r, p, q, n, nrhs, cg, parity, rrr, s);
+    RedBuf rzz{c->red_partial, c->red_counter, cg.zz + (1 - parity) * nrhs};
+    coarse_apply(prec, L.A[prec], L.g, L.ndof, r, z, nrhs, c->d_shift[l], true, nullptr, &rzz, s);
+    cg_xpay(prec, p, z, n, nrhs, cg, parity, s);
+    parity ^= 1;
+    if ((it + 1) % check_every == 0) {
+      CU(c, cudaMemcpyAsync(c->h_pin_i, cg.done, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CU(c, cudaStreamSynchronize(s));
+      bool all = true;
+      for (int i = 0; i < nrhs; ++i) all = all && c->h_pin_i[i];
+      if (all) break;
+    }
+  }
+  return check(c, "cgnr");
+}
+
+// One application of the multigrid preconditioner of level l: e = K_l(r); the coarsest
+// level used is `last` (CGNR there).
+wmg_status cycle(wmg_ctx* c, int l, int last, int prec, const void* r, void* e, int nrhs, const int* active) {
+  if (l == last) return cgnr(c, l, prec, r, e, nrhs, active);
+  const LevelData& L = c->L[l];
+  const size_t n = L.nvec_elems();
+  const int lc = l + 1;
+  void *rc, *ec, *t;
+  TRY(vec_ws(c, lc, "in", prec, nrhs, &rc));
+  TRY(vec_ws(c, lc, "out", prec, nrhs, &ec));
+  const int reps = (l == 0 || lc == last) ? 1 : std::max(1, c->prm.cycle_gamma);
+  for (int rep = 0; rep < reps; ++rep) {
+    const void* rin = r;
+    if (rep > 0) {
+      TRY(vec_ws(c, l, "cyc_t", prec, nrhs, &t));
+      level_apply(c, l, prec, e, t, nrhs, active, 0, nullptr);
+      blas_xmy(prec, r, t, n, nrhs, c->stream);
+      rin = t;
+    }
+    if (l == 0) restrict_fine(prec, L.P[prec], L.bk, rin, rc, nrhs, active, c->stream);
+    else restrict_coarse(prec, L.P[prec], L.bk, rin, rc, nrhs, active, c->stream);
+    TRY(cycle(c, lc, last, prec, rc, ec, nrhs, active));
+    void* dst = e;
+    if (rep > 0) TRY(vec_ws(c, l, "cyc_p", prec, nrhs, &dst));
+    if (l == 0) prolong_fine(prec, L.P[prec], L.bk, ec, dst, nrhs, active, c->stream);
+    else prolong_coarse(prec, L.P[prec], L.bk, ec, dst, nrhs, active, c->stream);
+    if (rep > 0) blas_xpy(prec, dst, e, n, nrhs, c->stream);
+    TRY(mr(c, l, prec, e, r, nrhs, c->prm.nu_post, active));
+  }
+  return check(c, "cycle");
+}
+
+// ------------------------------------------------------------------------------------
+// Galerkin construction of A_{l+1} = P_l^dag A_l P_l (Sec. 2), in precision prec, into
+// L[l+1].A[prec]; the other precision is converted from it.
+// ------------------------------------------------------------------------------------
+wmg_status galerkin(wmg_ctx* c, int l, int prec) {
+  LevelData& L = c->L[l];
+  LevelData& C = c->L[l + 1];
+  const Blocking& bk = L.bk;
+  const int n = 2 * bk.N;
+  const size_t fb = L.nvec_elems() * csize(prec);
+  const size_t budget = (size_t)3 << 30;
+  int ncol = (int)std::max<size_t>(1, budget / (9 * fb));
+  ncol = std::min(ncol, n);
+  void *out9, *rs;
+  TRY(ws_get(c, "gal_out9", (size_t)ncol * 9 * fb, &out9));
+  TRY(ws_get(c, "gal_rs", (size_t)ncol * 9 * C.g.V * n * csize(prec), &rs));
+  const size_t count = (size_t)C.g.V * 9 * n * n;
+  for (int p = 0; p < 2; ++p)
+    if (!C.A[p]) CU(c, cudaMalloc(&C.A[p], count * csize(p)));
+  for (int col0 = 0; col0 < n; col0 += ncol) {
+    const int nc = std::min(ncol, n - col0);
+    if (l == 0) {
+      hop_split_fine(prec, c->gauge[prec], L.P[prec], bk, c->mass_setup, col0, nc, out9, c->stream);
+      restrict_fine(prec, L.P[prec], bk, out9, rs, 9 * nc, nullptr, c->stream);
+    } else {
+      hop_split_coarse(prec, L.A[prec], L.P[prec], bk, col0, nc, out9, c->stream);
+      restrict_coarse(prec, L.P[prec], bk, out9, rs, 9 * nc, nullptr, c->stream);
+    }
+    stencil_scatter(prec, rs, C.A[prec], C.g.V, n, col0, nc, c->stream);
+  }
+  stencil_convert(1 - prec, C.A[1 - prec], prec, C.A[prec], count, c->stream);
+  return check(c, "galerkin");
+}
+
+// block-orthonormalise the FP64 vectors of level l in place (they become P_l) and derive the
+// other precision
+wmg_status orthonormalise(wmg_ctx* c, int l) {
+  LevelData& L = c->L[l];
+  CU(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
+  block_gs(l == 0, L.P[0], L.bk, c->d_flag, c->stream);
+  blas_convert(WMG_PREC_SINGLE, L.P[1], WMG_PREC_DOUBLE, L.P[0], L.nvec_elems(), L.bk.N, nullptr, c->stream);
+  CU(c, cudaMemcpyAsync(c->h_pin_i, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(c, cudaStreamSynchronize(c->stream));
+  if (c->h_pin_i[0]) {
+    c->err = "block Gram-Schmidt: rank-deficient block at level " + std::to_string(l);
+    return WMG_ERANK;
+  }
+  return check(c, "block_gs");
+}
+
+// vecs (precision prec, N fields of level l) -> P_l (both precisions) -> A_{l+1}
+wmg_status build_from_vectors(wmg_ctx* c, int l, int prec, const void* vecs) {
+  LevelData& L = c->L[l];
+  blas_convert(WMG_PREC_DOUBLE, L.P[0], prec, vecs, L.nvec_elems(), L.bk.N, nullptr, c->stream);
+  TRY(orthonormalise(c, l));
+  return galerkin(c, l, c->prm.prec_sloppy);
+}
+
+wmg_status normalise(wmg_ctx* c, int l, int prec, void* v, int nrhs) {
+  const size_t n = c->L[l].nvec_elems();
+  RedBuf rb = redbuf(c, RES_SETUP);
+  blas_norm2(prec, v, n, nrhs, rb, c->stream);
+  blas_scale_inv_sqrt(prec, v, n, nrhs, rb.result, 1, c->stream);
+  return check(c, "normalise");
+}
+
+// Adaptive setup of level l (Sec. 2): vecs (precision prec, N fields) hold the starts.
+wmg_status setup_level(wmg_ctx* c, int l, void* vecs) {
+  const int prec = c->prm.prec_sloppy;
+  const int N = c->L[l].bk.N;
+  void* zero;
+  TRY(vec_ws(c, l, "zero", prec, N, &zero));
+  blas_zero(prec, zero, c->L[l].nvec_elems(), N, c->stream);
+  TRY(ensure_reductions(c, N));
+  std::vector<double> m(N, c->mass_setup);
+  TRY(set_rhs_scalars(c, m.data(), N));
+  // pass 1: relax A psi = 0 from the starts
+  TRY(mr(c, l, prec, vecs, zero, N, c->prm.setup_relax, nullptr));
+  TRY(normalise(c, l, prec, vecs, N));
+  TRY(build_from_vectors(c, l, prec, vecs));
+  // later passes: one cycle of the trial hierarchy as an approximate solve of A psi' = psi
+  void* out;
+  TRY(vec_ws(c, l, "setup_out", prec, N, &out));
+  for (int pass = 1; pass < c->prm.setup_passes; ++pass) {
+    TRY(cycle(c, l, l + 1, prec, vecs, out, N, nullptr));
+    blas_convert(prec, vecs, prec, out, c->L[l].nvec_elems(), N, nullptr, c->stream);
+    TRY(normalise(c, l, prec, vecs, N));
+    TRY(build_from_vectors(c, l, prec, vecs));
+  }
+  return check(c, "setup_level");
+}
+
+// ------------------------------------------------------------------------------------
+// outer flexible GCR with FP64 reliable updates.  b64, x64: native FP64 fine spinors.
+// ------------------------------------------------------------------------------------
+wmg_status fgcr(wmg_ctx* c, const void* b64, void* x64, int nrhs, const double* masses, wmg_info* info,
+                bool use_mg) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (info) std::memset(info, 0, sizeof(wmg_info) * nrhs);
+  const int lo = use_mg ? c->prm.prec_sloppy : WMG_PREC_DOUBLE;
+  const size_t n = (size_t)c->fine.V * 12;
+  const int m = std::min(std::max(c->prm.gcr_restart, 1), kMaxKrylov);
+  cudaStream_t s = c->stream;
+  TRY(ensure_reductions(c, nrhs));
+  TRY(set_rhs_scalars(c, masses, nrhs));
+  void *r64, *rlo, *Z, *W;
+  TRY(vec_ws(c, 0, "gcr_r64", WMG_PREC_DOUBLE, nrhs, &r64));
+  TRY(vec_ws(c, 0, "gcr_rlo", lo, nrhs, &rlo));
+  const size_t slot = n * nrhs * csize(lo);
+  TRY(ws_get(c, std::string("gcr_Z") + (lo ? "s" : "d"), slot * m, &Z));
+  TRY(ws_get(c, std::string("gcr_W") + (lo ? "s" : "d"), slot * m, &W));
+  blas_zero(WMG_PREC_DOUBLE, x64, n, nrhs, s);
+  blas_convert(WMG_PREC_DOUBLE, r64, WMG_PREC_DOUBLE, b64, n, nrhs, nullptr, s);
+  blas_norm2(WMG_PREC_DOUBLE, b64, n, nrhs, redbuf(c, RES_BB), s);
+  std::vector<double> bb, rn2, t;
+  TRY(download(c, res_slot(c, RES_BB), nrhs, bb));
+  std::vector<int> active(nrhs), mask(nrhs), iters(nrhs, 0), rel(nrhs, 0), conv(nrhs, 0);
+  std::vector<double> bnorm(nrhs), ref(nrhs), tres(nrhs, 0.0);
+  for (int r = 0; r < nrhs; ++r) {
+    bnorm[r] = std::sqrt(bb[r]);
+    ref[r] = bnorm[r];
+    active[r] = bb[r] > 0.0;
+    conv[r] = !active[r];
+  }
+  TRY(upload_ints(c, c->d_active, active));
+  blas_convert(lo, rlo, WMG_PREC_DOUBLE, r64, n, nrhs, nullptr, s);
+  const double tol = c->prm.tol;
+  const double delta = (lo == WMG_PREC_DOUBLE) ? 0.0 : c->prm.reliable_delta;
+  int k = 0;
+  RedBuf rb_coef = redbuf(c, RES_COEF), rb_w = redbuf(c, RES_WRED), rb_rn = redbuf(c, RES_RN),
+         rb_r64 = redbuf(c, RES_R64);
+  while (true) {
+    bool any = false;
+    for (int r = 0; r < nrhs; ++r) any = any || active[r];
+    if (!any) break;
+    void* zk = (char*)Z + slot * k;
+    void* wk = (char*)W + slot * k;
+    if (use_mg) TRY(cycle(c, 0, c->nlev - 1, lo, rlo, zk, nrhs, c->d_active));
+    else blas_convert(lo, zk, lo, rlo, n, nrhs, c->d_active, s);
+    dslash(lo, wk, zk, nullptr, c->gauge[lo], c->fine, c->d_mass, c->d_active, nrhs, 0, nullptr, s);
+    if (k > 0) gcr_multidot(lo, W, slot, k, wk, n, nrhs, c->d_active, rb_coef, s);
+    gcr_orth(lo, W, Z, slot, k, wk, zk, rlo, rb_coef.result, k, n, nrhs, c->d_active, rb_w, s);
+    gcr_update(lo, (double*)x64, rlo, wk, zk, rb_w.result, n, nrhs, c->d_active, rb_rn, s);
+    TRY(check(c, "gcr iteration"));
+    TRY(download(c, rb_rn.result, nrhs, rn2));
+    ++k;
+    bool anyrel = false;
+    for (int r = 0; r < nrhs; ++r) {
+      rel[r] = 0;
+      if (!active[r]) continue;
+      ++iters[r];
+      const double rn = std::sqrt(std::max(rn2[r], 0.0));
+      if (rn <= tol * bnorm[r] || rn < delta * ref[r] || k == m || iters[r] >= c->prm.max_iter || !(rn == rn))
+        rel[r] = 1;
+      anyrel = anyrel || rel[r];
+    }
+    if (anyrel) {
+      // FP64 true residual r64 = b - D x64 for every rhs; applied where rel is set
+      dslash(WMG_PREC_DOUBLE, r64, x64, b64, c->gauge[0], c->fine, c->d_mass, nullptr, nrhs, 1, &rb_r64, s);
+      TRY(download(c, rb_r64.result, nrhs, t));
+      TRY(upload_ints(c, c->d_mask, rel));
+      blas_convert(lo, rlo, WMG_PREC_DOUBLE, r64, n, nrhs, c->d_mask, s);
+      bool changed = false;
+      for (int r = 0; r < nrhs; ++r) {
+        if (!rel[r]) continue;
+        const double tr = std::sqrt(std::max(t[r], 0.0));
+        tres[r] = tr / bnorm[r];
+        ref[r] = tr;
+        if (info) info[r].reliable_updates += 1;
+        if (tr <= tol * bnorm[r]) {
+          conv[r] = 1;
+          active[r] = 0;
+          changed = true;
+        } else if (iters[r] >= c->prm.max_iter) {
+          active[r] = 0;
+          changed = true;
+        }
+      }
+      if (changed) TRY(upload_ints(c, c->d_active, active));
+    }
+    if (k == m) k = 0;
+  }
+  CU(c, cudaStreamSynchronize(s));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  bool allconv = true;
+  for (int r = 0; r < nrhs; ++r) {
+    allconv = allconv && conv[r];
+    if (info) {
+      info[r].iters = iters[r];
+      info[r].converged = conv[r];
+      info[r].true_resid = bb[r] > 0.0 ? tres[r] : 0.0;
+      info[r].seconds = secs;
+    }
+  }
+  return allconv ? WMG_OK : WMG_ENOCONV;
+}
+
+}  // namespace wmg
