@@ -224,7 +224,7 @@ wmg_status cycle(wmg_ctx* c, int l, int last, int prec, const void* r, void* e, 
   void *rc, *ec, *t;
   TRY(vec_ws(c, lc, "in", prec, nrhs, &rc));
   TRY(vec_ws(c, lc, "out", prec, nrhs, &ec));
-  const int reps = (l == 0 || lc == last) ? 1 : std::max(1, c->prm.cycle_gamma);
+  const int reps = (l == 0) ? 1 : std::max(1, c->prm.cycle_gamma);  // W-cycle: gamma at middle levels
   for (int rep = 0; rep < reps; ++rep) {
     const void* rin = r;
     if (rep > 0) {

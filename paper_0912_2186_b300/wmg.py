@@ -1,0 +1,244 @@
+"""Thin ctypes binding of libwmg's C ABI (include/wmg.h): argument marshalling only.
+
+Every step of the solve runs in the CUDA kernels of libwmg.so.  Device buffers are passed as
+torch CUDA tensors (their data pointers); host buffers as numpy arrays.  The library must be
+built (``paper_0912_2186_b300.build.build()``); there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwmg.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "wmg.h")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ERANK, ETIMEOUT, ESTATE = range(8)
+PREC_DOUBLE, PREC_SINGLE = 0, 1
+MAX_LEVELS = 3
+
+
+class WmgError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__(what)
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("nlevels", ctypes.c_int),
+        ("block", (ctypes.c_int * 4) * (MAX_LEVELS - 1)),
+        ("nvec", ctypes.c_int * (MAX_LEVELS - 1)),
+        ("setup_passes", ctypes.c_int),
+        ("setup_relax", ctypes.c_int),
+        ("nu_post", ctypes.c_int),
+        ("gcr_restart", ctypes.c_int),
+        ("cycle_gamma", ctypes.c_int),
+        ("tol", ctypes.c_double),
+        ("coarse_tol", ctypes.c_double),
+        ("coarse_maxit", ctypes.c_int),
+        ("max_iter", ctypes.c_int),
+        ("prec_sloppy", ctypes.c_int),
+        ("pad_", ctypes.c_int),
+        ("reliable_delta", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int),
+        ("reliable_updates", ctypes.c_int),
+        ("converged", ctypes.c_int),
+        ("pad_", ctypes.c_int),
+        ("true_resid", ctypes.c_double),
+        ("seconds", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+_lib = None
+
+
+def load():
+    """Load libwmg.so (fails loudly if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libwmg.so not built ({LIB_PATH}); run paper_0912_2186_b300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "wmg_default_params": (None, [P(Params)]),
+        "wmg_strerror": (ctypes.c_char_p, [i]),
+        "wmg_last_error": (ctypes.c_char_p, [vp]),
+        "wmg_create": (i, [P(vp), P(ctypes.c_int * 4), vp]),
+        "wmg_destroy": (i, [vp]),
+        "wmg_load_gauge": (i, [vp, vp]),
+        "wmg_load_gauge_dev": (i, [vp, vp]),
+        "wmg_set_mass": (i, [vp, d]),
+        "wmg_setup": (i, [vp, P(Params), vp]),
+        "wmg_import_nullvecs": (i, [vp, P(Params), i, vp]),
+        "wmg_export_nullvecs": (i, [vp, i, vp]),
+        "wmg_export_coarse": (i, [vp, i, vp]),
+        "wmg_level_info": (i, [vp, i, P(i), P(i)]),
+        "wmg_solve": (i, [vp, vp, vp, i, P(Info)]),
+        "wmg_solve_dev": (i, [vp, vp, vp, i, P(Info)]),
+        "wmg_solve_plain_dev": (i, [vp, vp, vp, i, P(Info)]),
+        "wmg_pack_spinor": (i, [vp, i, vp, vp, i]),
+        "wmg_unpack_spinor": (i, [vp, i, vp, vp, i]),
+        "wmg_apply_D": (i, [vp, i, vp, vp, i]),
+        "wmg_restrict": (i, [vp, i, i, vp, vp, i]),
+        "wmg_prolong": (i, [vp, i, i, vp, vp, i]),
+        "wmg_apply_coarse": (i, [vp, i, i, i, vp, vp, i]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def declared_symbols(header=HEADER):
+    """Names of the functions include/wmg.h declares."""
+    txt = open(header).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(wmg_[a-z_0-9]+)\s*\(", txt)))
+
+
+def default_params(**kw):
+    p = Params()
+    load().wmg_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "block":
+            for l, blk in enumerate(v):
+                for j in range(4):
+                    p.block[l][j] = blk[j]
+        elif k == "nvec":
+            for l, n in enumerate(v):
+                p.nvec[l] = n
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor or host pointer of a numpy array (contiguous)."""
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return ctypes.c_void_p(x.ctypes.data)
+    assert x.is_contiguous()
+    return ctypes.c_void_p(x.data_ptr())
+
+
+class Context:
+    """One lattice (dims = (X, Y, Z, T)) with its gauge field and multigrid hierarchy."""
+
+    def __init__(self, dims, stream=None):
+        self.lib = load()
+        self.dims = tuple(int(a) for a in dims)
+        h = ctypes.c_void_p()
+        arr = (ctypes.c_int * 4)(*self.dims)
+        self._check(self.lib.wmg_create(ctypes.byref(h), ctypes.byref(arr), ctypes.c_void_p(stream or 0)), None)
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.wmg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, h=True, allow=()):
+        if st == OK or st in allow:
+            return st
+        msg = self.lib.wmg_strerror(st).decode()
+        if h and getattr(self, "h", None):
+            msg += ": " + (self.lib.wmg_last_error(self.h) or b"").decode()
+        raise WmgError(st, msg)
+
+    @property
+    def V(self):
+        X, Y, Z, T = self.dims
+        return X * Y * Z * T
+
+    # --- state ---
+    def load_gauge(self, U):
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=np.complex128)
+            return self._check(self.lib.wmg_load_gauge(self.h, _ptr(U)))
+        return self._check(self.lib.wmg_load_gauge_dev(self.h, _ptr(U)))
+
+    def set_mass(self, m):
+        return self._check(self.lib.wmg_set_mass(self.h, float(m)))
+
+    def setup(self, params, starts=None):
+        s = None if starts is None else np.ascontiguousarray(starts, dtype=np.complex128)
+        return self._check(self.lib.wmg_setup(self.h, ctypes.byref(params), _ptr(s) if s is not None else None))
+
+    def import_nullvecs(self, level, vecs, params=None):
+        v = np.ascontiguousarray(vecs, dtype=np.complex128)
+        p = ctypes.byref(params) if params is not None else None
+        return self._check(self.lib.wmg_import_nullvecs(self.h, p, int(level), _ptr(v)))
+
+    def level_info(self, level):
+        ns, nd = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.wmg_level_info(self.h, int(level), ctypes.byref(ns), ctypes.byref(nd)))
+        return ns.value, nd.value
+
+    def export_nullvecs(self, level, nvec):
+        ns, nd = self.level_info(level)
+        out = np.empty((nvec, ns, nd), dtype=np.complex128)
+        self._check(self.lib.wmg_export_nullvecs(self.h, int(level), _ptr(out)))
+        return out
+
+    def export_coarse(self, level):
+        ns, nd = self.level_info(level + 1)
+        out = np.empty((ns, 9, nd, nd), dtype=np.complex128)
+        self._check(self.lib.wmg_export_coarse(self.h, int(level), _ptr(out)))
+        return out
+
+    # --- solves ---
+    def solve(self, b, x, nrhs, plain=False):
+        """b, x: canonical complex128 fine spinors (torch CUDA tensors or numpy host arrays)."""
+        info = (Info * nrhs)()
+        if isinstance(b, np.ndarray):
+            assert not plain
+            st = self.lib.wmg_solve(self.h, _ptr(b), _ptr(x), int(nrhs), info)
+        else:
+            f = self.lib.wmg_solve_plain_dev if plain else self.lib.wmg_solve_dev
+            st = f(self.h, _ptr(b), _ptr(x), int(nrhs), info)
+        self._check(st, allow=(ENOCONV,))
+        return st, [i.as_dict() for i in info]
+
+    # --- operator-level entry points (device tensors) ---
+    def pack(self, prec, canon, native, nrhs):
+        return self._check(self.lib.wmg_pack_spinor(self.h, prec, _ptr(canon), _ptr(native), int(nrhs)))
+
+    def unpack(self, prec, native, canon, nrhs):
+        return self._check(self.lib.wmg_unpack_spinor(self.h, prec, _ptr(native), _ptr(canon), int(nrhs)))
+
+    def apply_D(self, prec, inp, out, nrhs):
+        return self._check(self.lib.wmg_apply_D(self.h, prec, _ptr(inp), _ptr(out), int(nrhs)))
+
+    def restrict(self, level, prec, fine, coarse, nrhs):
+        return self._check(self.lib.wmg_restrict(self.h, int(level), prec, _ptr(fine), _ptr(coarse), int(nrhs)))
+
+    def prolong(self, level, prec, coarse, fine, nrhs):
+        return self._check(self.lib.wmg_prolong(self.h, int(level), prec, _ptr(coarse), _ptr(fine), int(nrhs)))
+
+    def apply_coarse(self, level, prec, inp, out, nrhs, dagger=False):
+        return self._check(self.lib.wmg_apply_coarse(self.h, int(level), prec, int(bool(dagger)), _ptr(inp),
+                                                     _ptr(out), int(nrhs)))

@@ -1,0 +1,37 @@
+"""Host-side checks of the C ABI boundary (no GPU needed): the library loads and exports every
+function include/wmg.h declares; argument checks that fail before any device work."""
+import ctypes
+
+import pytest
+
+from paper_0912_2186_b300 import build, wmg
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return wmg.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = wmg.declared_symbols()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_default_params_and_strerror(lib):
+    p = wmg.default_params()
+    assert p.nlevels == 2 and p.nu_post == 4 and p.tol == 1e-10
+    assert tuple(p.block[0]) == (4, 4, 4, 4)
+    assert lib.wmg_strerror(wmg.ENOCONV) == b"solver did not converge"
+    assert ctypes.sizeof(wmg.Params) == 112 and ctypes.sizeof(wmg.Info) == 32
+
+
+def test_invalid_arguments_rejected_without_device_work(lib):
+    h = ctypes.c_void_p()
+    bad = (ctypes.c_int * 4)(8, 8, 1, 8)
+    assert lib.wmg_create(ctypes.byref(h), ctypes.byref(bad), None) == wmg.EINVAL
+    assert lib.wmg_destroy(None) == wmg.EINVAL
+    assert lib.wmg_set_mass(None, 0.1) == wmg.EINVAL
+    assert lib.wmg_apply_D(None, 0, None, None, 1) == wmg.EINVAL

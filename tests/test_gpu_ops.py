@@ -1,0 +1,158 @@
+"""GPU parity of the operator-level kernels against the FP64 oracle, through the C ABI:
+packing, the Wilson operator (Sec. 2 eq. for D), block orthonormalisation and P / P^dag
+(Sec. 2), the Galerkin coarse operator and its adjoint sigma_3 D^ sigma_3 (Sec. 3)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dirac, mg
+from tests.gpu_util import TOL, coarse_buf, dev, host, native_fine, rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def W():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0912_2186_b300 import build, wmg
+    build.build()
+    return wmg
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pack_roundtrip(W, prec):
+    dims = (6, 4, 4, 6)
+    ctx = W.Context(dims)
+    b = synth.gaussian_spinors(dims, 3, 1)
+    nat = native_fine(ctx.V, 3, prec)
+    out = dev(np.zeros_like(b))
+    ctx.pack(prec, dev(b), nat, 3)
+    ctx.unpack(prec, nat, out, 3)
+    got = host(out)
+    if prec == 0:
+        assert np.array_equal(got, b)
+    else:
+        assert rel_err(got, b) < 1e-7
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dims", [(6, 4, 4, 6), (4, 6, 2, 10), (8, 8, 8, 8)])
+def test_dslash_parity(W, prec, dims):
+    """V = 576 and 480 are not multiples of the 128-site CTA (ragged tail)."""
+    U = synth.gauge_field(dims, 0.6, 3)
+    m = -0.27
+    nrhs = 3
+    b = synth.gaussian_spinors(dims, nrhs, 4)
+    ctx = W.Context(dims)
+    ctx.load_gauge(U)
+    ctx.set_mass(m)
+    xin, xout = native_fine(ctx.V, nrhs, prec), native_fine(ctx.V, nrhs, prec)
+    ctx.pack(prec, dev(b), xin, nrhs)
+    ctx.apply_D(prec, xin, xout, nrhs)
+    canon = dev(np.zeros_like(b))
+    ctx.unpack(prec, xout, canon, nrhs)
+    got = host(canon)
+    want = np.stack([dirac.apply_D(U, b[r], m) for r in range(nrhs)])
+    assert rel_err(got, want) < TOL[prec]
+
+
+def _hier(W, dims, blocks, nvecs, prec, seed=10, m=-0.1, eps=0.6):
+    U = synth.gauge_field(dims, eps, seed)
+    ctx = W.Context(dims)
+    ctx.load_gauge(U)
+    ctx.set_mass(m)
+    p = W.default_params(nlevels=len(blocks) + 1, block=blocks, nvec=nvecs, prec_sloppy=prec)
+    v0 = synth.setup_starts(dims, nvecs[0], seed + 1)
+    ctx.import_nullvecs(0, v0, p)
+    op = mg.WilsonOp(U, m)
+    P0 = mg.block_orthonormalise(v0, blocks[0])
+    A1 = mg.galerkin(op, P0, blocks[0])
+    out = dict(ctx=ctx, U=U, op=op, P=[P0], A=[op, A1], v=[v0])
+    if len(blocks) == 2:
+        v1 = synth.coarse_starts(A1.dims, A1.n, nvecs[1], seed + 2)
+        ctx.import_nullvecs(1, v1.reshape(nvecs[1], -1, A1.n))
+        P1 = mg.block_orthonormalise(v1, blocks[1])
+        out["P"].append(P1)
+        out["A"].append(mg.galerkin(A1, P1, blocks[1]))
+        out["v"].append(v1)
+    return out
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_two_level_operator_parity(W, prec):
+    dims, blocks, nv = (8, 8, 8, 12), [(4, 4, 4, 4)], [4]
+    h = _hier(W, dims, blocks, nv, prec)
+    ctx, P0, A1 = h["ctx"], h["P"][0], h["A"][1]
+    # P after block Gram-Schmidt (always FP64 on the device)
+    Pg = ctx.export_nullvecs(0, nv[0])
+    assert rel_err(Pg, P0.reshape(nv[0], -1, 12)) < 1e-12
+    # Galerkin operator
+    Ag = ctx.export_coarse(0)
+    assert rel_err(Ag, A1.D.reshape(Ag.shape)) < TOL[prec]
+    # restrict / prolong / coarse apply on 5 right-hand sides
+    nrhs = 5
+    psi = synth.gaussian_spinors(dims, nrhs, 30)
+    V = ctx.V
+    nc, n = A1.D.reshape(-1, 9, A1.n, A1.n).shape[0], A1.n
+    fin = native_fine(V, nrhs, prec)
+    ctx.pack(prec, dev(psi), fin, nrhs)
+    co = coarse_buf(nc * n, nrhs, prec)
+    ctx.restrict(0, prec, fin, co, nrhs)
+    want = np.stack([mg.restrict(P0, psi[r], blocks[0]) for r in range(nrhs)])
+    assert rel_err(host(co), want.reshape(nrhs, -1)) < TOL[prec]
+    phi = synth.coarse_starts(A1.dims, n, nrhs, 31)
+    fout = native_fine(V, nrhs, prec)
+    ctx.prolong(0, prec, dev(phi.reshape(-1).astype(np.complex128 if prec == 0 else np.complex64)), fout, nrhs)
+    canon = dev(np.zeros_like(psi))
+    ctx.unpack(prec, fout, canon, nrhs)
+    want = np.stack([mg.prolong(P0, phi[r], blocks[0]) for r in range(nrhs)])
+    assert rel_err(host(canon), want) < TOL[prec]
+    cdt = np.complex128 if prec == 0 else np.complex64
+    for dag in (False, True):
+        out = coarse_buf(nc * n, nrhs, prec)
+        ctx.apply_coarse(1, prec, dev(phi.reshape(-1).astype(cdt)), out, nrhs, dagger=dag)
+        f = A1.apply_dagger if dag else A1.apply
+        want = np.stack([f(phi[r]) for r in range(nrhs)])
+        assert rel_err(host(out), want.reshape(nrhs, -1)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_three_level_operator_parity(W, prec):
+    dims, blocks, nv = (8, 8, 8, 8), [(2, 2, 2, 2), (2, 2, 2, 2)], [3, 5]
+    h = _hier(W, dims, blocks, nv, prec, seed=40)
+    ctx, A1, A2, P1 = h["ctx"], h["A"][1], h["A"][2], h["P"][1]
+    assert rel_err(ctx.export_nullvecs(1, nv[1]), P1.reshape(nv[1], -1, A1.n)) < 1e-12
+    Ag = ctx.export_coarse(1)
+    assert rel_err(Ag, A2.D.reshape(Ag.shape)) < TOL[prec]
+    nrhs = 3
+    cdt = np.complex128 if prec == 0 else np.complex64
+    phi1 = synth.coarse_starts(A1.dims, A1.n, nrhs, 41)
+    out2 = coarse_buf(A2.D.reshape(-1, 9, A2.n, A2.n).shape[0] * A2.n, nrhs, prec)
+    ctx.restrict(1, prec, dev(phi1.reshape(-1).astype(cdt)), out2, nrhs)
+    want = np.stack([mg.restrict(P1, phi1[r], blocks[1]) for r in range(nrhs)])
+    assert rel_err(host(out2), want.reshape(nrhs, -1)) < TOL[prec]
+    phi2 = synth.coarse_starts(A2.dims, A2.n, nrhs, 42)
+    out1 = coarse_buf(phi1.size // nrhs, nrhs, prec)
+    ctx.prolong(1, prec, dev(phi2.reshape(-1).astype(cdt)), out1, nrhs)
+    want = np.stack([mg.prolong(P1, phi2[r], blocks[1]) for r in range(nrhs)])
+    assert rel_err(host(out1), want.reshape(nrhs, -1)) < TOL[prec]
+    out = coarse_buf(phi2.size // nrhs, nrhs, prec)
+    ctx.apply_coarse(2, prec, dev(phi2.reshape(-1).astype(cdt)), out, nrhs)
+    want = np.stack([A2.apply(phi2[r]) for r in range(nrhs)])
+    assert rel_err(host(out), want.reshape(nrhs, -1)) < TOL[prec]
+
+
+def test_mass_shift_on_coarse_levels(W):
+    """set_mass after the setup shifts D^ by (m - m_setup) I (exact since P^dag P = 1)."""
+    dims, blocks, nv = (8, 8, 8, 12), [(4, 4, 4, 4)], [4]
+    h = _hier(W, dims, blocks, nv, 0, m=-0.1)
+    ctx, A1 = h["ctx"], h["A"][1]
+    ctx.set_mass(0.35)
+    phi = synth.coarse_starts(A1.dims, A1.n, 2, 50)
+    out = coarse_buf(phi.size // 2, 2, 0)
+    ctx.apply_coarse(1, 0, dev(phi.reshape(-1)), out, 2)
+    want = np.stack([A1.shifted(0.45).apply(phi[r]) for r in range(2)])
+    assert rel_err(host(out), want.reshape(2, -1)) < 1e-12

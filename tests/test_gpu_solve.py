@@ -1,0 +1,114 @@
+"""GPU MG-GCR solves (Sec. 3) through the C ABI, checked by the FP64 oracle: every solution
+has |b - D x| / |b| <= 1e-10 with D applied by the oracle; the solve is independent of the
+other right-hand sides of its batch; the hierarchy built from oracle vectors gives the
+oracle's iteration count."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dirac, mg, solvers
+from tests.gpu_util import dev, host
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def W():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0912_2186_b300 import build, wmg
+    build.build()
+    return wmg
+
+
+def oracle_resid(U, m, b, x):
+    return np.linalg.norm(b - dirac.apply_D(U, x, m)) / np.linalg.norm(b)
+
+
+CFG1 = dict(dims=(8, 8, 8, 8), eps=0.4, m=0.05, N=8)
+
+
+def _ctx(W, cfg, prec, seed=11, setup=True, **kw):
+    U = synth.gauge_field(cfg["dims"], cfg["eps"], seed)
+    ctx = W.Context(cfg["dims"])
+    ctx.load_gauge(U)
+    ctx.set_mass(cfg["m"])
+    p = W.default_params(nvec=[cfg["N"]], prec_sloppy=prec, **kw)
+    if setup:
+        ctx.setup(p, synth.setup_starts(cfg["dims"], cfg["N"], seed + 1))
+    return ctx, U, p
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_mg_solve_true_residual(W, prec):
+    ctx, U, p = _ctx(W, CFG1, prec)
+    b = synth.gaussian_spinors(CFG1["dims"], 2, 13)
+    x = dev(np.zeros_like(b))
+    st, info = ctx.solve(dev(b), x, 2)
+    xs = host(x)
+    for r in range(2):
+        assert info[r]["converged"] and info[r]["true_resid"] <= 1e-10
+        assert oracle_resid(U, CFG1["m"], b[r], xs[r]) <= 1.05e-10
+        assert info[r]["iters"] < 60
+
+
+def test_host_solve_and_plain_solver(W):
+    ctx, U, p = _ctx(W, CFG1, 1)
+    b = synth.gaussian_spinors(CFG1["dims"], 1, 14)
+    x = np.zeros_like(b)
+    st, info = ctx.solve(b, x, 1)
+    assert oracle_resid(U, CFG1["m"], b[0], x[0]) <= 1.05e-10
+    xp = dev(np.zeros_like(b))
+    st, pinfo = ctx.solve(dev(b), xp, 1, plain=True)
+    assert oracle_resid(U, CFG1["m"], b[0], host(xp)[0]) <= 1.05e-10
+    assert pinfo[0]["iters"] > 2 * info[0]["iters"]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_independence(W, prec):
+    """Each right-hand side gives bit-identical results alone and inside a batch."""
+    ctx, U, p = _ctx(W, CFG1, prec)
+    b = synth.gaussian_spinors(CFG1["dims"], 3, 15)
+    b[2] *= 1e-3                      # very different scales in one batch
+    xb = dev(np.zeros_like(b))
+    _, ib = ctx.solve(dev(b), xb, 3)
+    xb = host(xb)
+    for r in (0, 2):
+        x1 = dev(np.zeros_like(b[r:r + 1]))
+        _, i1 = ctx.solve(dev(b[r:r + 1]), x1, 1)
+        assert np.array_equal(host(x1)[0], xb[r])
+        assert i1[0]["iters"] == ib[r]["iters"]
+
+
+def test_iterations_match_oracle_with_shared_vectors(W):
+    """FP64 hierarchy from the oracle's own near-null vectors: same iteration count (+-1)."""
+    cfg = dict(dims=(8, 8, 8, 8), eps=0.5, m=-0.2, N=6)
+    ctx, U, p = _ctx(W, cfg, 0, seed=21, setup=False, coarse_tol=1e-8)
+    v = synth.setup_starts(cfg["dims"], cfg["N"], 22)
+    op = mg.WilsonOp(U, cfg["m"])
+    v = np.array([solvers._normalise(solvers.mr(op.apply, np.zeros_like(s), s, 20)) for s in v])
+    ctx.import_nullvecs(0, v.reshape(cfg["N"], -1, 12), p)
+    H = solvers.hierarchy_from_vectors(op, [(4, 4, 4, 4)], [v], solvers.CycleParams(coarse_tol=1e-8))
+    b = synth.gaussian_spinors(cfg["dims"], 1, 23)
+    xo, io = solvers.mg_solve(H, b[0], 1e-10, 16)
+    x = dev(np.zeros_like(b))
+    _, info = ctx.solve(dev(b), x, 1)
+    assert abs(info[0]["iters"] - io.iters) <= 1
+    assert oracle_resid(U, cfg["m"], b[0], host(x)[0]) <= 1.05e-10
+
+
+def test_three_level_solve(W):
+    cfg = dict(dims=(8, 8, 8, 16), eps=0.5, m=0.0)
+    U = synth.gauge_field(cfg["dims"], cfg["eps"], 31)
+    ctx = W.Context(cfg["dims"])
+    ctx.load_gauge(U)
+    ctx.set_mass(cfg["m"])
+    p = W.default_params(nlevels=3, block=[(2, 2, 2, 2), (2, 2, 2, 2)], nvec=[6, 8], prec_sloppy=1)
+    ctx.setup(p, synth.setup_starts(cfg["dims"], 6, 32))
+    b = synth.gaussian_spinors(cfg["dims"], 2, 33)
+    x = dev(np.zeros_like(b))
+    _, info = ctx.solve(dev(b), x, 2)
+    xs = host(x)
+    for r in range(2):
+        assert oracle_resid(U, cfg["m"], b[r], xs[r]) <= 1.05e-10
