@@ -70,8 +70,7 @@ __global__ void __launch_bounds__(128) k_dslash(void* __restrict__ out, const vo
   const size_t fb = spinor_field_bytes<R>(g.V);
   const char* inr = reinterpret_cast<const char*>(in) + fb * rhs;
   cpx<R> acc[12];
-  double red[RED > 0 ? RED : 1];
-  for (int i = 0; i < (RED > 0 ? RED : 1); ++i) red[i] = 0.0;
+  double red[3] = {0.0, 0.0, 0.0};
   if (v < g.V) {
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc[i] = cpx<R>{R(0), R(0)};
