@@ -192,6 +192,19 @@ wmg_status wmg_prolong(wmg_ctx* ctx, int level, int prec, const void* coarse_dev
 wmg_status wmg_apply_coarse(wmg_ctx* ctx, int level, int prec, int dagger, const void* in_dev, void* out_dev,
                             int nrhs);
 
+/* ---- instrumentation (no counterpart in the paper) ----
+ * When enabled, every launch of the solver's kernels is bracketed by two CUDA events on
+ * the context's stream (this adds host work per launch; leave it off for timing runs).
+ * Classes: 0 sloppy fine dslash, 1 FP64 fine dslash (true residuals), 2 coarse stencil,
+ * 3 restrict, 4 prolong, 5 vector updates and reductions, 6 setup (Gram-Schmidt and
+ * Galerkin construction).  wmg_profile_enable(ctx, 1) resets the counters. */
+wmg_status wmg_profile_enable(wmg_ctx* ctx, int on);
+/* Totals of class cls since the last enable: kernel milliseconds, launches (or launch
+ * groups), and the algorithmic bytes those launches must move (compulsory reads + writes:
+ * operator / link / P data once, each input and output vector once; 0 for class 5, 6).
+ * Synchronises. */
+wmg_status wmg_profile_get(wmg_ctx* ctx, int cls, double* ms, long long* launches, double* bytes);
+
 #ifdef __cplusplus
 }
 #endif

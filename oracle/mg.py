@@ -37,6 +37,7 @@ from __future__ import annotations
 
 import numpy as np
 
+from . import cref
 from .dirac import AXIS, apply_D, hop as wilson_hop
 
 NSLOT = 9
@@ -115,35 +116,60 @@ def block_orthonormalise(vectors, block, rank_tol=1e-10):
     return np.stack([from_blocks(out[a], dims, block) for a in range(N)])
 
 
+_BLOCKED = {}
+
+
+def _blocked(P, block):
+    """Per chirality s, the block-restricted columns of P as a (Vc, N, bs*n/2) array
+    (cached per array; the cache keeps P alive)."""
+    key = (id(P), tuple(block))
+    hit = _BLOCKED.get(key)
+    if hit is not None and hit[0] is P:
+        return hit[1]
+    if len(_BLOCKED) > 8:
+        _BLOCKED.clear()
+    N, n = P.shape[0], P.shape[-1]
+    h = n // 2
+    Pb = np.stack([to_blocks(p, block) for p in P])  # (N, Vc, bs, n)
+    halves = [np.ascontiguousarray(Pb[:, :, :, s * h:(s + 1) * h].reshape(N, Pb.shape[1], -1).transpose(1, 0, 2))
+              for s in range(2)]
+    _BLOCKED[key] = (P, halves)
+    return halves
+
+
 def restrict(P, psi, block):
-    """phi = P^dag psi: (T,Z,Y,X,n) fine -> (Tc,Zc,Yc,Xc,2N) coarse."""
+    """phi = P^dag psi: (T,Z,Y,X,n) fine -> (Tc,Zc,Yc,Xc,2N) coarse.
+    phi(xhat, s*N + alpha) = sum_{x in xhat, d in s} conj(P_alpha(x, d)) psi(x, d)."""
     N = P.shape[0]
     n = psi.shape[-1]
     h = n // 2
     dims = field_dims(psi)
     cd = coarse_dims(dims, block)
-    Pb = np.stack([to_blocks(p, block) for p in P])  # (N, Vc, bs, n)
-    fb = to_blocks(psi, block)  # (Vc, bs, n)
+    halves = _blocked(P, block)            # [s] -> (Vc, N, bs*h)
+    fb = to_blocks(psi, block)             # (Vc, bs, n)
     phi = np.zeros((fb.shape[0], 2 * N), dtype=np.complex128)
     for s in range(2):
-        sl = slice(s * h, (s + 1) * h)
-        phi[:, s * N:(s + 1) * N] = np.einsum("avbd,vbd->va", np.conj(Pb[:, :, :, sl]), fb[:, :, sl])
+        f = fb[:, :, s * h:(s + 1) * h].reshape(fb.shape[0], -1, 1)
+        phi[:, s * N:(s + 1) * N] = np.matmul(np.conj(halves[s]), f)[..., 0]
     X, Y, Z, T = cd
     return phi.reshape(T, Z, Y, X, 2 * N)
 
 
 def prolong(P, phi, block):
-    """psi = P phi: coarse (Tc,Zc,Yc,Xc,2N) -> fine (T,Z,Y,X,n)."""
+    """psi = P phi: coarse (Tc,Zc,Yc,Xc,2N) -> fine (T,Z,Y,X,n).
+    psi(x, d) = sum_alpha P_alpha(x, d) phi(xhat(x), s(d)*N + alpha)."""
     N = P.shape[0]
     n = P.shape[-1]
     h = n // 2
     dims = field_dims(P[0])
-    Pb = np.stack([to_blocks(p, block) for p in P])  # (N, Vc, bs, n)
+    halves = _blocked(P, block)            # [s] -> (Vc, N, bs*h)
     ph = phi.reshape(-1, 2 * N)
-    fb = np.zeros(Pb.shape[1:], dtype=np.complex128)
+    Vc = ph.shape[0]
+    bs = halves[0].shape[2] // h
+    fb = np.zeros((Vc, bs, n), dtype=np.complex128)
     for s in range(2):
-        sl = slice(s * h, (s + 1) * h)
-        fb[:, :, sl] = np.einsum("avbd,va->vbd", Pb[:, :, :, sl], ph[:, s * N:(s + 1) * N])
+        v = np.matmul(ph[:, None, s * N:(s + 1) * N], halves[s])[:, 0, :]   # (Vc, bs*h)
+        fb[:, :, s * h:(s + 1) * h] = v.reshape(Vc, bs, h)
     return from_blocks(fb, dims, block)
 
 
@@ -161,9 +187,13 @@ class WilsonOp:
         return (4.0 + self.m) * psi
 
     def hop(self, psi, mu, sign):
+        if psi.shape[0] * psi.shape[1] * psi.shape[2] * psi.shape[3] >= 4096:
+            return cref.hop(self.U, psi, mu, sign)      # plain C restatement, same arithmetic
         return wilson_hop(self.U, psi, mu, sign)
 
     def apply(self, psi):
+        if psi.shape[0] * psi.shape[1] * psi.shape[2] * psi.shape[3] >= 4096:
+            return cref.apply_D(self.U, psi, self.m)
         return apply_D(self.U, psi, self.m)
 
     def gamma5(self, psi):
@@ -185,11 +215,11 @@ class StencilOp:
         self.n = D.shape[-1]
 
     def diag(self, phi):
-        return np.einsum("...ij,...j->...i", self.D[..., 0, :, :], phi)
+        return np.matmul(self.D[..., 0, :, :], phi[..., None])[..., 0]
 
     def hop(self, phi, mu, sign):
         nb = np.roll(phi, -sign, axis=AXIS[mu])  # phi(xhat + sign*mu)
-        return np.einsum("...ij,...j->...i", self.D[..., slot(mu, sign), :, :], nb)
+        return np.matmul(self.D[..., slot(mu, sign), :, :], nb[..., None])[..., 0]
 
     def apply(self, phi):
         out = self.diag(phi)
@@ -201,14 +231,14 @@ class StencilOp:
     def apply_dagger(self, phi):
         """Explicit adjoint: (A^dag phi)(y) = sum_k D[y - k, k]^dag phi(y - k)."""
         Dh = np.conj(np.swapaxes(self.D, -1, -2))
-        out = np.einsum("...ij,...j->...i", Dh[..., 0, :, :], phi)
+        out = np.matmul(Dh[..., 0, :, :], phi[..., None])[..., 0]
         for mu in range(4):
             for sign in (+1, -1):
                 ax = AXIS[mu]
                 # term from site y - sign*mu whose slot (mu, sign) points at y
                 Dk = np.roll(Dh[..., slot(mu, sign), :, :], sign, axis=ax)
                 ph = np.roll(phi, sign, axis=ax)
-                out = out + np.einsum("...ij,...j->...i", Dk, ph)
+                out = out + np.matmul(Dk, ph[..., None])[..., 0]
         return out
 
     def sigma3(self, phi):

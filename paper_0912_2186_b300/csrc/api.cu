@@ -173,6 +173,8 @@ wmg_status wmg_create(wmg_ctx** out, const int dims[4], void* stream) {
 wmg_status wmg_destroy(wmg_ctx* c) {
   if (!c) return WMG_EINVAL;
   cudaStreamSynchronize(c->stream);
+  prof_flush(c);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   free_hierarchy(c);
   for (auto& kv : c->ws) cudaFree(kv.second.first);
   c->ws.clear();
@@ -418,6 +420,26 @@ wmg_status wmg_apply_coarse(wmg_ctx* c, int level, int prec, int dagger, const v
   coarse_apply(prec, L.A[prec], L.g, L.ndof, in, out, nrhs, c->d_shift[level], dagger != 0, nullptr, nullptr,
                c->stream);
   return check(c, "apply_coarse");
+}
+
+wmg_status wmg_profile_enable(wmg_ctx* c, int on) {
+  if (!c) return WMG_EINVAL;
+  prof_flush(c);
+  c->prof_on = on != 0;
+  for (int i = 0; i < PROF_NCLASS; ++i) {
+    c->prof_ms[i] = c->prof_bytes[i] = 0.0;
+    c->prof_n[i] = 0;
+  }
+  return WMG_OK;
+}
+
+wmg_status wmg_profile_get(wmg_ctx* c, int cls, double* ms, long long* launches, double* bytes) {
+  if (!c || cls < 0 || cls >= PROF_NCLASS) return WMG_EINVAL;
+  prof_flush(c);
+  if (ms) *ms = c->prof_ms[cls];
+  if (launches) *launches = c->prof_n[cls];
+  if (bytes) *bytes = c->prof_bytes[cls];
+  return WMG_OK;
 }
 
 }  // extern "C"

@@ -8,6 +8,16 @@
 
 namespace wmg {
 
+// kernel classes timed by the optional CUDA-event instrumentation (wmg_profile_*)
+enum { PROF_DSLASH_LO = 0, PROF_DSLASH_64, PROF_COARSE, PROF_RESTRICT, PROF_PROLONG, PROF_BLAS, PROF_SETUP,
+       PROF_NCLASS };
+
+struct ProfRec {
+  cudaEvent_t a, b;
+  int cls;
+  double bytes;
+};
+
 struct LevelData {
   Geom g;            // lattice of this level
   int ndof = 12;     // complex dof per site (12 fine, 2N coarse)
@@ -47,6 +57,14 @@ struct wmg_ctx {
   int* d_mask = nullptr;                       // [kMaxRhs]
   int* d_flag = nullptr;                       // misc device flag
   int* d_cgint = nullptr;                      // [2][kMaxRhs] cg done / iters
+  int n_active = 0;                            // active right-hand sides of the current solve
+  // instrumentation
+  bool prof_on = false;
+  std::vector<wmg::ProfRec> prof_pending;
+  std::vector<cudaEvent_t> ev_pool;
+  double prof_ms[wmg::PROF_NCLASS] = {};
+  double prof_bytes[wmg::PROF_NCLASS] = {};
+  long long prof_n[wmg::PROF_NCLASS] = {};
   double* h_pin = nullptr;                     // pinned host scratch [4096]
   int* h_pin_i = nullptr;                      // pinned host scratch [4096]
 };

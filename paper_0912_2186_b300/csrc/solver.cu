@@ -121,14 +121,83 @@ wmg_status download(wmg_ctx* c, const double* src, size_t n, std::vector<double>
 }
 
 // ------------------------------------------------------------------------------------
+// optional CUDA-event instrumentation: every timed launch (or launch group) is bracketed by
+// two events on the context's stream; elapsed times are collected at wmg_profile_get.
+// ------------------------------------------------------------------------------------
+static cudaEvent_t ev_get(wmg_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void prof_flush(wmg_ctx* c) {
+  for (auto& r : c->prof_pending) {
+    cudaEventSynchronize(r.b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    c->prof_ms[r.cls] += ms;
+    c->prof_bytes[r.cls] += r.bytes;
+    c->prof_n[r.cls] += 1;
+    c->ev_pool.push_back(r.a);
+    c->ev_pool.push_back(r.b);
+  }
+  c->prof_pending.clear();
+}
+
+struct ProfScope {
+  wmg_ctx* c;
+  int cls;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  ProfScope(wmg_ctx* c_, int cls_, double bytes_) : c(c_), cls(cls_), bytes(bytes_) {
+    if (c->prof_on) {
+      a = ev_get(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~ProfScope() {
+    if (!c->prof_on || !a) return;
+    cudaEvent_t b = ev_get(c);
+    cudaEventRecord(b, c->stream);
+    c->prof_pending.push_back({a, b, cls, bytes});
+    if (c->prof_pending.size() > 8192) prof_flush(c);
+  }
+};
+
+// algorithmic (compulsory) bytes of one launch
+static double rb_(int prec) { return prec == WMG_PREC_DOUBLE ? 8.0 : 4.0; }
+double dslash_bytes(const wmg_ctx* c, int prec, int nact, bool resid) {
+  const double s = rb_(prec), V = c->fine.V;
+  return V * (48.0 * s) + (double)nact * V * 24.0 * s * (resid ? 3.0 : 2.0);
+}
+double coarse_bytes(const wmg_ctx* c, int l, int prec, int nact) {
+  const double s = rb_(prec), V = c->L[l].g.V, n = c->L[l].ndof;
+  return V * 9.0 * n * n * 2.0 * s + (double)nact * V * n * 2.0 * s * 2.0;
+}
+double transfer_bytes(const wmg_ctx* c, int l, int prec, int nact) {
+  const LevelData& L = c->L[l];
+  const double s = rb_(prec), nf = (double)L.g.V * L.ndof, nc = (double)L.bk.coarse.V * 2.0 * L.bk.N;
+  return (double)L.bk.N * nf * 2.0 * s + (double)nact * (nf + nc) * 2.0 * s;
+}
+static int nact_of(const wmg_ctx* c, const int* active, int nrhs) { return active ? c->n_active : nrhs; }
+
+// ------------------------------------------------------------------------------------
 // operators of a level
 // ------------------------------------------------------------------------------------
 // out = A_l in   (l = 0: Wilson D; l >= 1: coarse stencil with the per-rhs shift)
 void level_apply(wmg_ctx* c, int l, int prec, const void* in, void* out, int nrhs, const int* active, int red,
                  const RedBuf* rb) {
+  const int na = nact_of(c, active, nrhs);
   if (l == 0) {
+    ProfScope ps(c, prec == WMG_PREC_DOUBLE ? PROF_DSLASH_64 : PROF_DSLASH_LO, dslash_bytes(c, prec, na, false));
     dslash(prec, out, in, nullptr, c->gauge[prec], c->fine, c->d_mass, active, nrhs, red, rb, c->stream);
   } else {
+    ProfScope ps(c, PROF_COARSE, coarse_bytes(c, l, prec, na));
     const LevelData& L = c->L[l];
     coarse_apply(prec, L.A[prec], L.g, L.ndof, in, out, nrhs, c->d_shift[l], false, active,
                  red == 1 ? rb : nullptr, c->stream);
@@ -142,7 +211,10 @@ wmg_status mr(wmg_ctx* c, int l, int prec, void* x, const void* b, int nrhs, int
   TRY(vec_ws(c, l, "mr_q", prec, nrhs, &q));
   const size_t n = c->L[l].nvec_elems();
   RedBuf rb = redbuf(c, RES_MR);
+  const int na = nact_of(c, active, nrhs);
+  const int dcls = prec == WMG_PREC_DOUBLE ? PROF_DSLASH_64 : PROF_DSLASH_LO;
   if (l == 0) {
+    ProfScope ps(c, dcls, dslash_bytes(c, prec, na, true));
     dslash(prec, r, x, b, c->gauge[prec], c->fine, c->d_mass, active, nrhs, 0, nullptr, c->stream);
   } else {
     level_apply(c, l, prec, x, r, nrhs, active, 0, nullptr);
@@ -150,11 +222,14 @@ wmg_status mr(wmg_ctx* c, int l, int prec, void* x, const void* b, int nrhs, int
   }
   for (int i = 0; i < nu; ++i) {
     if (l == 0) {
+      ProfScope ps(c, dcls, dslash_bytes(c, prec, na, false));
       dslash(prec, q, r, nullptr, c->gauge[prec], c->fine, c->d_mass, active, nrhs, 2, &rb, c->stream);
     } else {
       level_apply(c, l, prec, r, q, nrhs, active, 0, nullptr);
+      ProfScope ps(c, PROF_BLAS, 0);
       blas_dot_norm(prec, q, r, n, nrhs, rb, c->stream);
     }
+    ProfScope ps(c, PROF_BLAS, 0);
     blas_mr_update(prec, x, r, q, n, nrhs, rb.result, active, c->stream);
   }
   return check(c, "mr");
@@ -196,12 +271,25 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
   RedBuf rrr{c->red_partial, c->red_counter, cg.rr};
   int parity = 0;
   const int check_every = 8;
+  const double cb = coarse_bytes(c, l, prec, nrhs);
   for (int it = 0; it < c->prm.coarse_maxit; ++it) {
-    coarse_apply(prec, L.A[prec], L.g, L.ndof, p, q, nrhs, c->d_shift[l], false, nullptr, &rqq, s);
-    cg_update(prec, x, r, p, q, n, nrhs, cg, parity, rrr, s);
+    {
+      ProfScope ps(c, PROF_COARSE, cb);
+      coarse_apply(prec, L.A[prec], L.g, L.ndof, p, q, nrhs, c->d_shift[l], false, nullptr, &rqq, s);
+    }
+    {
+      ProfScope ps(c, PROF_BLAS, 0);
+      cg_update(prec, x, r, p, q, n, nrhs, cg, parity, rrr, s);
+    }
     RedBuf rzz{c->red_partial, c->red_counter, cg.zz + (1 - parity) * nrhs};
-    coarse_apply(prec, L.A[prec], L.g, L.ndof, r, z, nrhs, c->d_shift[l], true, nullptr, &rzz, s);
-    cg_xpay(prec, p, z, n, nrhs, cg, parity, s);
+    {
+      ProfScope ps(c, PROF_COARSE, cb);
+      coarse_apply(prec, L.A[prec], L.g, L.ndof, r, z, nrhs, c->d_shift[l], true, nullptr, &rzz, s);
+    }
+    {
+      ProfScope ps(c, PROF_BLAS, 0);
+      cg_xpay(prec, p, z, n, nrhs, cg, parity, s);
+    }
     parity ^= 1;
     if ((it + 1) % check_every == 0) {
       CU(c, cudaMemcpyAsync(c->h_pin_i, cg.done, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -233,13 +321,19 @@ wmg_status cycle(wmg_ctx* c, int l, int last, int prec, const void* r, void* e, 
       blas_xmy(prec, r, t, n, nrhs, c->stream);
       rin = t;
     }
-    if (l == 0) restrict_fine(prec, L.P[prec], L.bk, rin, rc, nrhs, active, c->stream);
-    else restrict_coarse(prec, L.P[prec], L.bk, rin, rc, nrhs, active, c->stream);
+    {
+      ProfScope ps(c, PROF_RESTRICT, transfer_bytes(c, l, prec, nact_of(c, active, nrhs)));
+      if (l == 0) restrict_fine(prec, L.P[prec], L.bk, rin, rc, nrhs, active, c->stream);
+      else restrict_coarse(prec, L.P[prec], L.bk, rin, rc, nrhs, active, c->stream);
+    }
     TRY(cycle(c, lc, last, prec, rc, ec, nrhs, active));
     void* dst = e;
     if (rep > 0) TRY(vec_ws(c, l, "cyc_p", prec, nrhs, &dst));
-    if (l == 0) prolong_fine(prec, L.P[prec], L.bk, ec, dst, nrhs, active, c->stream);
-    else prolong_coarse(prec, L.P[prec], L.bk, ec, dst, nrhs, active, c->stream);
+    {
+      ProfScope ps(c, PROF_PROLONG, transfer_bytes(c, l, prec, nact_of(c, active, nrhs)));
+      if (l == 0) prolong_fine(prec, L.P[prec], L.bk, ec, dst, nrhs, active, c->stream);
+      else prolong_coarse(prec, L.P[prec], L.bk, ec, dst, nrhs, active, c->stream);
+    }
     if (rep > 0) blas_xpy(prec, dst, e, n, nrhs, c->stream);
     TRY(mr(c, l, prec, e, r, nrhs, c->prm.nu_post, active));
   }
@@ -265,6 +359,7 @@ wmg_status galerkin(wmg_ctx* c, int l, int prec) {
   const size_t count = (size_t)C.g.V * 9 * n * n;
   for (int p = 0; p < 2; ++p)
     if (!C.A[p]) CU(c, cudaMalloc(&C.A[p], count * csize(p)));
+  ProfScope ps(c, PROF_SETUP, 0);
   for (int col0 = 0; col0 < n; col0 += ncol) {
     const int nc = std::min(ncol, n - col0);
     if (l == 0) {
@@ -285,7 +380,10 @@ wmg_status galerkin(wmg_ctx* c, int l, int prec) {
 wmg_status orthonormalise(wmg_ctx* c, int l) {
   LevelData& L = c->L[l];
   CU(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
-  block_gs(l == 0, L.P[0], L.bk, c->d_flag, c->stream);
+  {
+    ProfScope ps(c, PROF_SETUP, 0);
+    block_gs(l == 0, L.P[0], L.bk, c->d_flag, c->stream);
+  }
   blas_convert(WMG_PREC_SINGLE, L.P[1], WMG_PREC_DOUBLE, L.P[0], L.nvec_elems(), L.bk.N, nullptr, c->stream);
   CU(c, cudaMemcpyAsync(c->h_pin_i, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CU(c, cudaStreamSynchronize(c->stream));
@@ -371,6 +469,8 @@ wmg_status fgcr(wmg_ctx* c, const void* b64, void* x64, int nrhs, const double* 
     conv[r] = !active[r];
   }
   TRY(upload_ints(c, c->d_active, active));
+  c->n_active = 0;
+  for (int r = 0; r < nrhs; ++r) c->n_active += active[r];
   blas_convert(lo, rlo, WMG_PREC_DOUBLE, r64, n, nrhs, nullptr, s);
   const double tol = c->prm.tol;
   const double delta = (lo == WMG_PREC_DOUBLE) ? 0.0 : c->prm.reliable_delta;
@@ -385,10 +485,16 @@ wmg_status fgcr(wmg_ctx* c, const void* b64, void* x64, int nrhs, const double* 
     void* wk = (char*)W + slot * k;
     if (use_mg) TRY(cycle(c, 0, c->nlev - 1, lo, rlo, zk, nrhs, c->d_active));
     else blas_convert(lo, zk, lo, rlo, n, nrhs, c->d_active, s);
-    dslash(lo, wk, zk, nullptr, c->gauge[lo], c->fine, c->d_mass, c->d_active, nrhs, 0, nullptr, s);
-    if (k > 0) gcr_multidot(lo, W, slot, k, wk, n, nrhs, c->d_active, rb_coef, s);
-    gcr_orth(lo, W, Z, slot, k, wk, zk, rlo, rb_coef.result, k, n, nrhs, c->d_active, rb_w, s);
-    gcr_update(lo, (double*)x64, rlo, wk, zk, rb_w.result, n, nrhs, c->d_active, rb_rn, s);
+    {
+      ProfScope ps(c, lo == WMG_PREC_DOUBLE ? PROF_DSLASH_64 : PROF_DSLASH_LO, dslash_bytes(c, lo, c->n_active, false));
+      dslash(lo, wk, zk, nullptr, c->gauge[lo], c->fine, c->d_mass, c->d_active, nrhs, 0, nullptr, s);
+    }
+    {
+      ProfScope ps(c, PROF_BLAS, 0);
+      if (k > 0) gcr_multidot(lo, W, slot, k, wk, n, nrhs, c->d_active, rb_coef, s);
+      gcr_orth(lo, W, Z, slot, k, wk, zk, rlo, rb_coef.result, k, n, nrhs, c->d_active, rb_w, s);
+      gcr_update(lo, (double*)x64, rlo, wk, zk, rb_w.result, n, nrhs, c->d_active, rb_rn, s);
+    }
     TRY(check(c, "gcr iteration"));
     TRY(download(c, rb_rn.result, nrhs, rn2));
     ++k;
@@ -404,7 +510,10 @@ wmg_status fgcr(wmg_ctx* c, const void* b64, void* x64, int nrhs, const double* 
     }
     if (anyrel) {
       // FP64 true residual r64 = b - D x64 for every rhs; applied where rel is set
-      dslash(WMG_PREC_DOUBLE, r64, x64, b64, c->gauge[0], c->fine, c->d_mass, nullptr, nrhs, 1, &rb_r64, s);
+      {
+        ProfScope ps(c, PROF_DSLASH_64, dslash_bytes(c, WMG_PREC_DOUBLE, nrhs, true));
+        dslash(WMG_PREC_DOUBLE, r64, x64, b64, c->gauge[0], c->fine, c->d_mass, nullptr, nrhs, 1, &rb_r64, s);
+      }
       TRY(download(c, rb_r64.result, nrhs, t));
       TRY(upload_ints(c, c->d_mask, rel));
       blas_convert(lo, rlo, WMG_PREC_DOUBLE, r64, n, nrhs, c->d_mask, s);
@@ -424,7 +533,11 @@ wmg_status fgcr(wmg_ctx* c, const void* b64, void* x64, int nrhs, const double* 
           changed = true;
         }
       }
-      if (changed) TRY(upload_ints(c, c->d_active, active));
+      if (changed) {
+        TRY(upload_ints(c, c->d_active, active));
+        c->n_active = 0;
+        for (int r = 0; r < nrhs; ++r) c->n_active += active[r];
+      }
     }
     if (k == m) k = 0;
   }

@@ -98,6 +98,8 @@ def load():
         "wmg_restrict": (i, [vp, i, i, vp, vp, i]),
         "wmg_prolong": (i, [vp, i, i, vp, vp, i]),
         "wmg_apply_coarse": (i, [vp, i, i, i, vp, vp, i]),
+        "wmg_profile_enable": (i, [vp, i]),
+        "wmg_profile_get": (i, [vp, i, P(d), P(ctypes.c_longlong), P(d)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -238,6 +240,19 @@ class Context:
 
     def prolong(self, level, prec, coarse, fine, nrhs):
         return self._check(self.lib.wmg_prolong(self.h, int(level), prec, _ptr(coarse), _ptr(fine), int(nrhs)))
+
+    PROF_CLASSES = ("dslash_sloppy", "dslash_fp64", "coarse", "restrict", "prolong", "blas", "setup")
+
+    def profile(self, on=True):
+        return self._check(self.lib.wmg_profile_enable(self.h, int(bool(on))))
+
+    def profile_get(self):
+        out = {}
+        for k, name in enumerate(self.PROF_CLASSES):
+            ms, n, b = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+            self._check(self.lib.wmg_profile_get(self.h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)))
+            out[name] = {"ms": ms.value, "launches": n.value, "bytes": b.value}
+        return out
 
     def apply_coarse(self, level, prec, inp, out, nrhs, dagger=False):
         return self._check(self.lib.wmg_apply_coarse(self.h, int(level), prec, int(bool(dagger)), _ptr(inp),

@@ -125,3 +125,25 @@ def test_planted_mistakes_are_caught():
     lhs = literal_D(Up, dirac.transform_spinor(Om, psi))
     rhs = dirac.transform_spinor(Om, literal_D(U, psi))
     assert np.abs(lhs - rhs).max() > 1e-3
+
+
+def test_c_restatement_matches_numpy_definition():
+    """oracle/c/dirac_ref.c (used for large lattices) against the numpy definition above."""
+    from oracle import cref
+    dims = (4, 6, 2, 8)
+    U = synth.gauge_field(dims, 0.7, 41)
+    psi = synth.gaussian_spinors(dims, 1, 42)[0]
+    assert np.abs(cref.apply_D(U, psi, -0.31) - dirac.apply_D(U, psi, -0.31)).max() < 1e-13
+    for mu in range(4):
+        for s in (+1, -1):
+            assert np.abs(cref.hop(U, psi, mu, s) - dirac.hop(U, psi, mu, s)).max() < 1e-14
+    # and it satisfies the closed form on its own: free-field plane wave on a larger lattice
+    dims = (8, 8, 8, 8)
+    X, Y, Z, T = dims
+    t, z, y, x = np.meshgrid(*(np.arange(L) for L in (T, Z, Y, X)), indexing="ij")
+    p = 2 * np.pi * np.array([1 / X, 3 / Y, 2 / Z, 5 / T])
+    chi = np.arange(12).reshape(4, 3) + 1j
+    ph = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t))
+    psi = (ph[..., None, None] * chi).reshape(x.shape + (12,))
+    want = (ph[..., None, None] * (dirac.free_plane_wave_factor(p, 0.2) @ chi)).reshape(psi.shape)
+    assert np.abs(cref.apply_D(synth.unit_gauge(dims), psi, 0.2) - want).max() < 1e-12
