@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Benchmark of the adaptive-multigrid Wilson-Dirac solve on one B300.
+
+One step is one whole job on the 16^3x32 workload (epsilon = 0.6 random SU(3) field, three
+masses at which lambda_min(D^dag D) is 1e-3, 1e-4, 1e-5 of its free-field value, 12 point
+sources): load the gauge field, run the adaptive setup (2 levels, 4^4 blocks, N = 24,
+5 passes) at the lightest mass, then solve the 12 right-hand sides to a true FP64 residual
+of 1e-10 at each of the three masses (FP32 cycle and Krylov vectors, FP64 reliable updates,
+all right-hand sides of a mass batched).  `value` is the device time of one step (the
+time-to-solution of the job, setup included); the same job in all-FP64 with one
+right-hand side at a time is timed once for comparison ("plain_fp64").
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl wmg|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "MG-GCR time-to-solution @1e-10 vs plain; dslash GB/s; p50/p99 solve latency"
+WORKLOADS = {
+    "16x16x16x32": dict(dims=(16, 16, 16, 32), eps=0.6, gauge_seed=11, nvec=24, block=(4, 4, 4, 4), nrhs=12,
+                        masses_file=os.path.join(ROOT, "tests", "golden", "masses_16x16x16x32_eps0.6.json")),
+}
+PROF_CLASSES = ("dslash_sloppy", "dslash_fp64", "coarse", "restrict", "prolong", "blas", "setup")
+
+
+def load_masses(w, override):
+    if override:
+        return sorted((float(m) for m in override.split(",")), reverse=True)
+    with open(w["masses_file"]) as f:
+        rec = json.load(f)
+    return sorted(rec["masses"].values(), reverse=True)   # heaviest first; last = lightest
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ------------------------------------------------------------------------------------------
+OPCOUNTS = os.path.join(ROOT, "profiles", "op_counts_16x16x16x32.json")
+
+
+def oracle_unit_costs(w, reps=3):
+    """Host seconds of the oracle's unit operations on this workload's shapes."""
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    from oracle import cref, mg
+    dims, N, blk = w["dims"], w["nvec"], w["block"]
+    U = synth.gauge_field(dims, w["eps"], w["gauge_seed"])
+    v = synth.setup_starts(dims, N, 5)
+    P = mg.block_orthonormalise(v, blk)
+    cd = mg.coarse_dims(dims, blk)
+    psi = synth.gaussian_spinors(dims, 1, 6)[0]
+    rng = np.random.default_rng(0)
+    shape = tuple(reversed(cd)) + (9, 2 * N, 2 * N)
+    A = mg.StencilOp(rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
+    phi = synth.coarse_starts(cd, 2 * N, 1, 7)[0]
+    t = {}
+
+    def tm(name, f):
+        f()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            f()
+        t[name] = (time.perf_counter() - t0) / reps
+
+    tm("D", lambda: cref.apply_D(U, psi, -1.0))
+    tm("coarse", lambda: A.apply(phi))
+    tm("restrict", lambda: mg.restrict(P, psi, blk))
+    tm("prolong", lambda: mg.prolong(P, phi, blk))
+    t0 = time.perf_counter()
+    mg.block_orthonormalise(v, blk)
+    t["gs"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    op = mg.WilsonOp(U, -1.0)
+    g = np.zeros_like(psi)
+    g[..., :6] = P[0][..., :6]
+    for mu in range(4):
+        for s in (1, -1):
+            mg.restrict(P, op.hop(g, mu, s), blk)
+    t["galerkin_column"] = time.perf_counter() - t0
+    return t, os.cpu_count()
+
+
+def oracle_estimate(w, counts, unit):
+    """Oracle seconds for one step: unit costs x the step's operation counts."""
+    N = w["nvec"]
+    sec = (counts["dslash_sloppy"] + counts["dslash_fp64"]) * unit["D"] + counts["coarse"] * unit["coarse"] \
+        + counts["restrict"] * unit["restrict"] + counts["prolong"] * unit["prolong"] \
+        + counts["setup_builds"] * (unit["gs"] + 2 * N * unit["galerkin_column"])
+    return sec
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    try:
+        with open(OPCOUNTS) as f:
+            counts = json.load(f)["counts"]
+    except OSError:
+        print(json.dumps({"impl": "reference", "unavailable": "operation counts of the job not recorded yet"}))
+        return
+    vals = []
+    for i in range(args.warmup + args.steps):
+        unit, cores = oracle_unit_costs(w, reps=1)
+        if i >= args.warmup:
+            vals.append(oracle_estimate(w, counts, unit))
+    v = statistics.mean(vals)
+    sample = ("FP64 oracle on the host: C restatement of D, numpy coarse stencil, restrict, prolong, block "
+              "Gram-Schmidt and one Galerkin column timed on this workload's shapes, times the operation counts "
+              "of one step (vector updates not included)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "higher_is_better": False,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+def run_gpu(args, w):
+    import torch
+
+    from paper_0912_2186_b300 import build, wmg
+    build.build()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    masses = load_masses(w, args.masses)
+    m_light = masses[-1]
+    dims, nrhs = w["dims"], w["nrhs"]
+    V = int(np.prod(dims))
+    U = synth.gauge_field(dims, w["eps"], w["gauge_seed"])
+    b = synth.point_sources(dims, nrhs)
+    U_dev = torch.from_numpy(U).cuda()
+    b_dev = torch.from_numpy(b).cuda()
+    x_dev = torch.zeros_like(b_dev)
+    ctx = wmg.Context(dims)
+    params = wmg.default_params(nvec=[w["nvec"]], block=[w["block"]], prec_sloppy=wmg.PREC_SINGLE,
+                                seed=1000 + rank)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    record = {"iters": [], "true_resid": []}
+
+    def step(host=False):
+        if host:
+            ctx.load_gauge(U)
+        else:
+            ctx.load_gauge(U_dev)
+        ctx.set_mass(m_light)
+        ctx.setup(params)
+        for m in masses:
+            ctx.set_mass(m)
+            if host:
+                xh = np.zeros_like(b)
+                st, info = ctx.solve(b, xh, nrhs)
+            else:
+                st, info = ctx.solve(b_dev, x_dev, nrhs)
+            if st != wmg.OK:
+                raise RuntimeError(f"solve at m={m} did not converge: {info}")
+            record["iters"].append([i["iters"] for i in info])
+            record["true_resid"].append(max(i["true_resid"] for i in info))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # timed region: device time of each step (CUDA events on the legacy stream the library uses)
+    record["iters"].clear()
+    record["true_resid"].clear()
+    clocks = Clocks(local)
+    times = []
+    l0 = wmg.launch_count()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    launches = (wmg.launch_count() - l0) // max(args.steps, 1)
+    clk = clocks.stop()
+    t_step = statistics.mean(times)
+    if dist:
+        tt = torch.tensor([t_step], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    iters = record["iters"]
+    resid = max(record["true_resid"])
+
+    # end to end through the host-buffer entry points
+    e2e = []
+    for _ in range(max(1, min(args.steps, 2))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(host=True)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t0)
+    h2d = U.nbytes + len(masses) * b.nbytes
+    d2h = len(masses) * b.nbytes
+
+    # instrumented step: per-class kernel time, algorithmic bytes and operation counts
+    ctx.profile(True)
+    step()
+    prof = ctx.profile_get()
+    ctx.profile(False)
+    builds = params.setup_passes
+    counts = {k: prof[k]["units"] for k in PROF_CLASSES}
+    counts["setup_builds"] = builds
+    hot = max(("dslash_sloppy", "coarse", "restrict", "prolong"), key=lambda k: prof[k]["ms"])
+    peaks, src = measured_peaks()
+    achieved = prof[hot]["bytes"] / (prof[hot]["ms"] * 1e-3) / 1e9 if prof[hot]["ms"] > 0 else 0.0
+    roof = {"bound": "hbm", "kernel": hot, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+            "launches": prof[hot]["launches"], "ms_per_launch": prof[hot]["ms"] / max(prof[hot]["launches"], 1)}
+    total_ms = sum(prof[k]["ms"] for k in PROF_CLASSES)
+    breakdown = {k: {"ms": round(prof[k]["ms"], 3), "share": round(prof[k]["ms"] / total_ms, 4) if total_ms else 0,
+                     "GB_s": round(prof[k]["bytes"] / (prof[k]["ms"] * 1e6), 1) if prof[k]["ms"] > 0 else None}
+                 for k in PROF_CLASSES}
+
+    # isolated dslash throughput (FP32, 12 right-hand sides and 1)
+    dsl = {}
+    for nr in (1, nrhs):
+        xin = torch.zeros(nr * 12 * V, dtype=torch.complex64, device="cuda")
+        xout = torch.zeros_like(xin)
+        ctx.pack(wmg.PREC_SINGLE, b_dev[:nr].contiguous(), xin, nr)
+        for _ in range(3):
+            ctx.apply_D(wmg.PREC_SINGLE, xin, xout, nr)
+        reps = 50
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            ctx.apply_D(wmg.PREC_SINGLE, xin, xout, nr)
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3 / reps
+        by = V * 48 * 4 + nr * V * 48 * 4
+        dsl[f"nrhs{nr}"] = {"us": sec * 1e6, "GB_s": by / sec / 1e9, "GFLOP_s": 1368 * V * nr / sec / 1e9}
+
+    # plain comparison: the same job in all-FP64, one right-hand side at a time
+    plain = None
+    if not args.no_plain:
+        pp = wmg.default_params(nvec=[w["nvec"]], block=[w["block"]], prec_sloppy=wmg.PREC_DOUBLE, seed=1000 + rank)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.load_gauge(U_dev)
+        ctx.set_mass(m_light)
+        ctx.setup(pp)
+        pit = []
+        for m in masses:
+            ctx.set_mass(m)
+            for r in range(nrhs):
+                st, info = ctx.solve(b_dev[r:r + 1].contiguous(), x_dev[r:r + 1], 1)
+                pit.append(info[0]["iters"])
+        e1.record()
+        torch.cuda.synchronize()
+        plain = {"s": e0.elapsed_time(e1) / 1e3, "iters_mean": float(np.mean(pit)), "prec": "f64", "nrhs_per_solve": 1}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        unit, cores = oracle_unit_costs(w, reps=2)
+        cpu = {"value": oracle_estimate(w, counts, unit), "unit": "s", "cores": cores, "kind": "oracle",
+               "sample": "FP64 oracle unit operations (C restatement of D, numpy coarse stencil, restrict, prolong, "
+                         "block Gram-Schmidt, one Galerkin column) timed on this workload's shapes, times the "
+                         "operation counts of one step; vector updates not included"}
+        os.makedirs(os.path.dirname(OPCOUNTS), exist_ok=True)
+        if args.record_counts:
+            with open(OPCOUNTS, "w") as f:
+                json.dump({"workload": args.workload, "counts": counts,
+                           "note": "operator applications per step measured by bench.py --record-counts"}, f, indent=1)
+
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "lattice": "x".join(map(str, dims)), "epsilon": w["eps"],
+                   "masses": masses, "rhs": f"{nrhs} point sources", "levels": 2, "block": "4^4", "nvec": w["nvec"],
+                   "setup_passes": params.setup_passes, "smoother": "MR nu=4 FP32", "outer": "FGCR(16) FP64 reliable",
+                   "l2": "flushed (256 MB write) between timed steps", "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "solves_per_s": world * len(masses) * nrhs / t_step,
+        "iters_per_mass": [float(np.mean(i)) for i in iters[:len(masses)]],
+        "max_true_resid": resid,
+        "plain_fp64": plain,
+        "speedup_vs_plain": (plain["s"] / t_step) if plain else None,
+        "dslash_fp32_isolated": dsl,
+        "kernel_breakdown": breakdown,
+        "roofline": roof,
+        "gpu_launches": int(launches),
+        "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="wmg", choices=["wmg", "reference"])
+    ap.add_argument("--workload", default="16x16x16x32", choices=sorted(WORKLOADS))
+    ap.add_argument("--masses", default=None, help="comma-separated masses (default: the oracle's)")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--record-counts", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    main()

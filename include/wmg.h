@@ -143,8 +143,10 @@ wmg_status wmg_set_mass(wmg_ctx* ctx, double m);
 
 /* Adaptive setup (Sec. 2): near-null vectors, block orthonormalisation with the
  * chirality split of Sec. 3, Galerkin coarse operators, level by level.
- * starts_host: NULL (seeded Gaussian starts) or, for the fine level, nvec[0] fine
- * spinors in the canonical layout.  Synchronises. */
+ * starts_host: NULL or, for the fine level, nvec[0] fine spinors in the canonical
+ * layout.  NULL draws Gaussian starts on the device from the counter-based Philox-4x32-10
+ * generator keyed by p->seed (p->seed + 1 for the second level), real and imaginary
+ * parts in canonical order.  Synchronises. */
 wmg_status wmg_setup(wmg_ctx* ctx, const wmg_params* p, const double* starts_host);
 
 /* Replace the near-null vectors of `level` (0: fine spinors, canonical layout;
@@ -200,10 +202,12 @@ wmg_status wmg_apply_coarse(wmg_ctx* ctx, int level, int prec, int dagger, const
  * Galerkin construction).  wmg_profile_enable(ctx, 1) resets the counters. */
 wmg_status wmg_profile_enable(wmg_ctx* ctx, int on);
 /* Totals of class cls since the last enable: kernel milliseconds, launches (or launch
- * groups), and the algorithmic bytes those launches must move (compulsory reads + writes:
- * operator / link / P data once, each input and output vector once; 0 for class 5, 6).
- * Synchronises. */
-wmg_status wmg_profile_get(wmg_ctx* ctx, int cls, double* ms, long long* launches, double* bytes);
+ * groups), the algorithmic bytes those launches must move (compulsory reads + writes:
+ * operator / link / P data once, each input and output vector once; 0 for class 5, 6)
+ * and the right-hand sides they processed (operator applications).  Synchronises. */
+wmg_status wmg_profile_get(wmg_ctx* ctx, int cls, double* ms, long long* launches, double* bytes, double* units);
+/* Total number of CUDA kernels this library has launched in this process (all contexts). */
+wmg_status wmg_launch_count(long long* n);
 
 #ifdef __cplusplus
 }

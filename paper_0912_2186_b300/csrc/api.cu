@@ -82,12 +82,6 @@ wmg_status alloc_hierarchy(wmg_ctx* c, const wmg_params* p) {
   return WMG_OK;
 }
 
-void fill_gaussian(std::vector<double>& v, uint64_t seed) {
-  std::mt19937_64 gen(seed);
-  std::normal_distribution<double> nd(0.0, 1.0);
-  for (auto& x : v) x = nd(gen);
-}
-
 }  // namespace
 
 extern "C" {
@@ -230,9 +224,7 @@ wmg_status wmg_setup(wmg_ctx* c, const wmg_params* p, const double* starts_host)
   if (starts_host) {
     CU(c, cudaMemcpy(canon, starts_host, V * 12 * N0 * sizeof(cd), cudaMemcpyHostToDevice));
   } else {
-    std::vector<double> h(V * 24 * N0);
-    fill_gaussian(h, p->seed);
-    CU(c, cudaMemcpy(canon, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+    gaussian_fill((double*)canon, V * 24 * N0, p->seed, c->stream);
   }
   pack_spinor(prec, (const double*)canon, vecs, c->fine.V, N0, c->stream);
   TRY(setup_level(c, 0, vecs));
@@ -242,9 +234,7 @@ wmg_status wmg_setup(wmg_ctx* c, const wmg_params* p, const double* starts_host)
     void *stage1, *vecs1;
     TRY(ws_get(c, "stage1", n1 * N1 * sizeof(cd), &stage1));
     TRY(vec_ws(c, 1, "setup_vecs", prec, N1, &vecs1));
-    std::vector<double> h(n1 * 2 * N1);
-    fill_gaussian(h, p->seed + 1);
-    CU(c, cudaMemcpy(stage1, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+    gaussian_fill((double*)stage1, n1 * 2 * N1, p->seed + 1, c->stream);
     blas_convert(prec, vecs1, WMG_PREC_DOUBLE, stage1, n1, N1, nullptr, c->stream);
     TRY(setup_level(c, 1, vecs1));
   }
@@ -427,18 +417,25 @@ wmg_status wmg_profile_enable(wmg_ctx* c, int on) {
   prof_flush(c);
   c->prof_on = on != 0;
   for (int i = 0; i < PROF_NCLASS; ++i) {
-    c->prof_ms[i] = c->prof_bytes[i] = 0.0;
+    c->prof_ms[i] = c->prof_bytes[i] = c->prof_units[i] = 0.0;
     c->prof_n[i] = 0;
   }
   return WMG_OK;
 }
 
-wmg_status wmg_profile_get(wmg_ctx* c, int cls, double* ms, long long* launches, double* bytes) {
+wmg_status wmg_launch_count(long long* n) {
+  if (!n) return WMG_EINVAL;
+  *n = launch_count();
+  return WMG_OK;
+}
+
+wmg_status wmg_profile_get(wmg_ctx* c, int cls, double* ms, long long* launches, double* bytes, double* units) {
   if (!c || cls < 0 || cls >= PROF_NCLASS) return WMG_EINVAL;
   prof_flush(c);
   if (ms) *ms = c->prof_ms[cls];
   if (launches) *launches = c->prof_n[cls];
   if (bytes) *bytes = c->prof_bytes[cls];
+  if (units) *units = c->prof_units[cls];
   return WMG_OK;
 }
 

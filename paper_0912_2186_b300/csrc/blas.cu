@@ -264,11 +264,13 @@ __global__ void k_gcr_update(double* x64, void* r_, void* w_, void* z_, const do
   } while (0)
 
 void blas_zero(int prec, void* x, size_t n, int nrhs, cudaStream_t s) {
+  count_launch();
   dim3 g(blas_blocks(n), nrhs);
   WMG_BY_PREC(prec, k_zero, <<<g, kBlasThreads, 0, s>>>(x, n));
 }
 
 void blas_convert(int pd, void* dst, int ps, const void* src, size_t n, int nrhs, const int* mask, cudaStream_t s) {
+  count_launch();
   dim3 g(blas_blocks(n), nrhs);
   if (pd == WMG_PREC_DOUBLE && ps == WMG_PREC_DOUBLE) k_convert<double, double><<<g, kBlasThreads, 0, s>>>(dst, src, n, mask);
   else if (pd == WMG_PREC_DOUBLE) k_convert<double, float><<<g, kBlasThreads, 0, s>>>(dst, src, n, mask);
@@ -277,50 +279,59 @@ void blas_convert(int pd, void* dst, int ps, const void* src, size_t n, int nrhs
 }
 
 void blas_xmy(int prec, const void* x, void* y, size_t n, int nrhs, cudaStream_t s) {
+  count_launch();
   dim3 g(blas_blocks(n), nrhs);
   WMG_BY_PREC(prec, k_xmy, <<<g, kBlasThreads, 0, s>>>(x, y, n));
 }
 
 void blas_xpy(int prec, const void* x, void* y, size_t n, int nrhs, cudaStream_t s) {
+  count_launch();
   dim3 g(blas_blocks(n), nrhs);
   WMG_BY_PREC(prec, k_xpy, <<<g, kBlasThreads, 0, s>>>(x, y, n));
 }
 
 void blas_dot_norm(int prec, const void* a, const void* b, size_t n, int nrhs, const RedBuf& rb, cudaStream_t s) {
+  count_launch();
   dim3 g(blas_blocks(n), nrhs);
   WMG_BY_PREC(prec, k_dot_norm, <<<g, kBlasThreads, 0, s>>>(a, b, n, rb));
 }
 
 void blas_norm2(int prec, const void* a, size_t n, int nrhs, const RedBuf& rb, cudaStream_t s) {
+  count_launch();
   dim3 g(blas_blocks(n), nrhs);
   WMG_BY_PREC(prec, k_norm2, <<<g, kBlasThreads, 0, s>>>(a, n, rb));
 }
 
 void blas_scale_inv_sqrt(int prec, void* x, size_t n, int nrhs, const double* nrm2, int stride, cudaStream_t s) {
+  count_launch();
   dim3 g(blas_blocks(n), nrhs);
   WMG_BY_PREC(prec, k_scale_inv_sqrt, <<<g, kBlasThreads, 0, s>>>(x, n, nrm2, stride));
 }
 
 void blas_mr_update(int prec, void* x, void* r, const void* q, size_t n, int nrhs, const double* red,
                     const int* active, cudaStream_t s) {
+  count_launch();
   dim3 g(blas_blocks(n), nrhs);
   WMG_BY_PREC(prec, k_mr_update, <<<g, kBlasThreads, 0, s>>>(x, r, q, n, red, active));
 }
 
 void cg_update(int prec, void* x, void* r, const void* p, const void* q, size_t n, int nrhs, const CgScalars& cg,
                int parity, const RedBuf& rb_rr, cudaStream_t s) {
+  count_launch(2);
   dim3 g(blas_blocks(n), nrhs);
   WMG_BY_PREC(prec, k_cg_update, <<<g, kBlasThreads, 0, s>>>(x, r, p, q, n, cg, parity, nrhs, rb_rr));
   k_cg_flags<<<(nrhs + 63) / 64, 64, 0, s>>>(cg, nrhs);
 }
 
 void cg_xpay(int prec, void* p, const void* z, size_t n, int nrhs, const CgScalars& cg, int parity, cudaStream_t s) {
+  count_launch();
   dim3 g(blas_blocks(n), nrhs);
   WMG_BY_PREC(prec, k_cg_xpay, <<<g, kBlasThreads, 0, s>>>(p, z, n, cg, parity, nrhs));
 }
 
 void gcr_multidot(int prec, const void* W, size_t slot_stride, int kmax, const void* w, size_t n, int nrhs,
                   const int* active, const RedBuf& rb, cudaStream_t s) {
+  count_launch((kmax + kDotChunk - 1) / kDotChunk);
   dim3 g(blas_blocks(n), nrhs);
   for (int j0 = 0; j0 < kmax; j0 += kDotChunk) {
     RedBuf r = rb;
@@ -334,6 +345,7 @@ void gcr_multidot(int prec, const void* W, size_t slot_stride, int kmax, const v
 
 void gcr_orth(int prec, const void* W, const void* Z, size_t slot_stride, int k, void* w, void* z, const void* r,
               const double* coef, int kmax, size_t n, int nrhs, const int* active, const RedBuf& rb, cudaStream_t s) {
+  count_launch();
   (void)kmax;
   dim3 g(blas_blocks(n), nrhs);
   WMG_BY_PREC(prec, k_gcr_orth, <<<g, kBlasThreads, 0, s>>>(W, Z, slot_stride, k, w, z, r, coef, nrhs, n, active, rb));
@@ -341,6 +353,7 @@ void gcr_orth(int prec, const void* W, const void* Z, size_t slot_stride, int k,
 
 void gcr_update(int prec, double* x64, void* r, void* w, void* z, const double* wred, size_t n, int nrhs,
                 const int* active, const RedBuf& rb, cudaStream_t s) {
+  count_launch();
   dim3 g(blas_blocks(n), nrhs);
   WMG_BY_PREC(prec, k_gcr_update, <<<g, kBlasThreads, 0, s>>>(x64, r, w, z, wred, n, active, rb));
 }

@@ -115,6 +115,7 @@ static void launch_coarse_apply(const void* A, const Geom& g, int n, const void*
 
 void coarse_apply(int prec, const void* A, const Geom& g, int n, const void* in, void* out, int nrhs,
                   const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s) {
+  count_launch();
   if (prec == WMG_PREC_DOUBLE) {
     if (nrhs == 1) launch_coarse_apply<double, 1>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
     else if (nrhs == 2) launch_coarse_apply<double, 2>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
@@ -188,6 +189,7 @@ __global__ void k_hop_split_fine(const void* __restrict__ gauge, const void* __r
 
 void hop_split_fine(int prec, const void* gauge, const void* P, const Blocking& bk, double mass, int col0, int ncol,
                     void* out9, cudaStream_t s) {
+  count_launch();
   dim3 grid((bk.fine.V + 127) / 128, ncol);
   if (prec == WMG_PREC_DOUBLE)
     k_hop_split_fine<double><<<grid, 128, 0, s>>>(gauge, P, bk, 4.0 + mass, col0, out9);
@@ -235,6 +237,7 @@ __global__ void k_hop_split_coarse(const void* __restrict__ A_, const void* __re
 
 void hop_split_coarse(int prec, const void* A, const void* P, const Blocking& bk, int col0, int ncol, void* out9,
                       cudaStream_t s) {
+  count_launch();
   int spc = 256 / bk.nf;
   if (spc < 1) spc = 1;
   const int T = ((spc * bk.nf + 31) / 32) * 32;
@@ -260,6 +263,7 @@ __global__ void k_stencil_scatter(const cpx<R>* __restrict__ rs, cpx<R>* __restr
 }
 
 void stencil_scatter(int prec, const void* rs, void* A, int Vc, int n, int col0, int ncol, cudaStream_t s) {
+  count_launch();
   const size_t tot = (size_t)ncol * 9 * Vc * n;
   int B = (int)((tot + 255) / 256);
   if (B > 148 * 16) B = 148 * 16;
@@ -276,6 +280,7 @@ __global__ void k_stencil_convert(cpx<Rd>* d, const cpx<Rs>* s, size_t count) {
 }
 
 void stencil_convert(int pd, void* dst, int ps, const void* src, size_t count, cudaStream_t s) {
+  count_launch();
   int B = (int)((count + 255) / 256);
   if (B > 148 * 16) B = 148 * 16;
   if (pd == WMG_PREC_DOUBLE && ps == WMG_PREC_DOUBLE) k_stencil_convert<double, double><<<B, 256, 0, s>>>((cd*)dst, (const cd*)src, count);

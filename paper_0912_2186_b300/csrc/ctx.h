@@ -16,6 +16,7 @@ struct ProfRec {
   cudaEvent_t a, b;
   int cls;
   double bytes;
+  double units;  // right-hand sides (vector applications) processed
 };
 
 struct LevelData {
@@ -64,6 +65,7 @@ struct wmg_ctx {
   std::vector<cudaEvent_t> ev_pool;
   double prof_ms[wmg::PROF_NCLASS] = {};
   double prof_bytes[wmg::PROF_NCLASS] = {};
+  double prof_units[wmg::PROF_NCLASS] = {};
   long long prof_n[wmg::PROF_NCLASS] = {};
   double* h_pin = nullptr;                     // pinned host scratch [4096]
   int* h_pin_i = nullptr;                      // pinned host scratch [4096]

@@ -132,12 +132,14 @@ __global__ void __launch_bounds__(128) k_dslash(void* __restrict__ out, const vo
 // launchers
 // ------------------------------------------------------------------------------------
 void pack_gauge(int prec, const double* canon, void* out, int V, cudaStream_t s) {
+  count_launch();
   const int T = 256, B = (V + T - 1) / T;
   if (prec == WMG_PREC_DOUBLE) k_pack_gauge<double><<<B, T, 0, s>>>((const double2*)canon, out, V);
   else k_pack_gauge<float><<<B, T, 0, s>>>((const double2*)canon, out, V);
 }
 
 void pack_spinor(int prec, const double* canon, void* out, int V, int nrhs, cudaStream_t s) {
+  count_launch();
   const size_t n = (size_t)V * nrhs;
   const int T = 256;
   const unsigned B = (unsigned)((n + T - 1) / T);
@@ -146,6 +148,7 @@ void pack_spinor(int prec, const double* canon, void* out, int V, int nrhs, cuda
 }
 
 void unpack_spinor(int prec, const void* in, double* canon, int V, int nrhs, cudaStream_t s) {
+  count_launch();
   const size_t n = (size_t)V * nrhs;
   const int T = 256;
   const unsigned B = (unsigned)((n + T - 1) / T);
@@ -157,6 +160,7 @@ int dslash_blocks(int V) { return (V + kDslashThreads - 1) / kDslashThreads; }
 
 void dslash(int prec, void* out, const void* in, const void* b, const void* gauge, const Geom& g,
             const double* mass_dev, const int* active, int nrhs, int red, const RedBuf* rb, cudaStream_t s) {
+  count_launch();
   const int nb = dslash_blocks(g.V);
   const unsigned grid = (unsigned)nb * nrhs;
   RedBuf r = rb ? *rb : RedBuf{nullptr, nullptr, nullptr};

@@ -11,6 +11,13 @@ constexpr int kMaxKrylov = 32;       // outer GCR restart length limit
 
 inline size_t prec_real_bytes(int prec) { return prec == WMG_PREC_DOUBLE ? 8 : 4; }
 
+// number of kernel launches issued by this library (all contexts)
+long long launch_count();
+void count_launch(int n = 1);
+
+// N(0,1) reals from the counter-based generator (rng.cu): out[i] depends only on (seed, i)
+void gaussian_fill(double* out, size_t n, uint64_t seed, cudaStream_t s);
+
 // ---- fine lattice (dslash.cu) ----
 void pack_gauge(int prec, const double* canon, void* out, int V, cudaStream_t s);
 void pack_spinor(int prec, const double* canon, void* out, int V, int nrhs, cudaStream_t s);

@@ -1,0 +1,53 @@
+// Gaussian random starts for the adaptive setup, generated on the device with the
+// counter-based Philox-4x32-10 generator (Salmon, Moraes, Dror, Shaw, SC'11) and the
+// Box-Muller transform.  Element i of the stream (seed) is a pure function of (seed, i).
+#include "kernels.h"
+
+namespace wmg {
+
+WMG_D void mulhilo32(uint32_t a, uint32_t b, uint32_t& hi, uint32_t& lo) {
+  const uint64_t p = (uint64_t)a * b;
+  hi = (uint32_t)(p >> 32);
+  lo = (uint32_t)p;
+}
+
+// ten Philox rounds on the counter c with key k
+WMG_D uint4 philox4x32_10(uint4 c, uint2 k) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0, lo0, hi1, lo1;
+    mulhilo32(M0, c.x, hi0, lo0);
+    mulhilo32(M1, c.z, hi1, lo1);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += W0;
+    k.y += W1;
+  }
+  return c;
+}
+
+// out[4 i .. 4 i + 3] = four N(0, 1) numbers from counter i
+__global__ void k_gaussian(double* out, size_t n, uint64_t seed) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (4 * i >= n) return;
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(i >> 32), 0u, 0u),
+                                make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  const double inv = 1.0 / 4294967296.0;
+  // (0, 1] uniforms from 32-bit integers
+  const double u0 = ((double)r.x + 1.0) * inv, u1 = ((double)r.y + 1.0) * inv;
+  const double u2 = ((double)r.z + 1.0) * inv, u3 = ((double)r.w + 1.0) * inv;
+  const double a = sqrt(-2.0 * log(u0)), b = sqrt(-2.0 * log(u2));
+  double s0, c0, s1, c1;
+  sincospi(2.0 * u1, &s0, &c0);
+  sincospi(2.0 * u3, &s1, &c1);
+  const double z[4] = {a * c0, a * s0, b * c1, b * s1};
+  for (int j = 0; j < 4 && 4 * i + j < n; ++j) out[4 * i + j] = z[j];
+}
+
+void gaussian_fill(double* out, size_t n, uint64_t seed, cudaStream_t s) {
+  const size_t threads = (n + 3) / 4;
+  k_gaussian<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(out, n, seed);
+  count_launch();
+}
+
+}  // namespace wmg

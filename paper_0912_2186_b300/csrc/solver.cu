@@ -3,6 +3,7 @@
 // with FP64 reliable updates, the adaptive setup (Sec. 2) and the Galerkin construction
 // D^ = P^dag D P (Sec. 2).  Every arithmetic step runs in the kernels of this library; the
 // host only sequences launches and reads per-rhs residual norms.
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -12,6 +13,12 @@
 #include "solver.h"
 
 using namespace wmg;
+
+namespace wmg {
+static std::atomic<long long> g_launches{0};
+long long launch_count() { return g_launches.load(); }
+void count_launch(int n) { g_launches += n; }
+}  // namespace wmg
 
 wmg_status wmg_cuda_fail(cudaError_t e, const char* what) {
   (void)what;
@@ -142,6 +149,7 @@ void prof_flush(wmg_ctx* c) {
     cudaEventElapsedTime(&ms, r.a, r.b);
     c->prof_ms[r.cls] += ms;
     c->prof_bytes[r.cls] += r.bytes;
+    c->prof_units[r.cls] += r.units;
     c->prof_n[r.cls] += 1;
     c->ev_pool.push_back(r.a);
     c->ev_pool.push_back(r.b);
@@ -152,9 +160,10 @@ void prof_flush(wmg_ctx* c) {
 struct ProfScope {
   wmg_ctx* c;
   int cls;
-  double bytes;
+  double bytes, units;
   cudaEvent_t a = nullptr;
-  ProfScope(wmg_ctx* c_, int cls_, double bytes_) : c(c_), cls(cls_), bytes(bytes_) {
+  ProfScope(wmg_ctx* c_, int cls_, double bytes_, double units_ = 0)
+      : c(c_), cls(cls_), bytes(bytes_), units(units_) {
     if (c->prof_on) {
       a = ev_get(c);
       cudaEventRecord(a, c->stream);
@@ -164,7 +173,7 @@ struct ProfScope {
     if (!c->prof_on || !a) return;
     cudaEvent_t b = ev_get(c);
     cudaEventRecord(b, c->stream);
-    c->prof_pending.push_back({a, b, cls, bytes});
+    c->prof_pending.push_back({a, b, cls, bytes, units});
     if (c->prof_pending.size() > 8192) prof_flush(c);
   }
 };
@@ -194,10 +203,10 @@ void level_apply(wmg_ctx* c, int l, int prec, const void* in, void* out, int nrh
                  const RedBuf* rb) {
   const int na = nact_of(c, active, nrhs);
   if (l == 0) {
-    ProfScope ps(c, prec == WMG_PREC_DOUBLE ? PROF_DSLASH_64 : PROF_DSLASH_LO, dslash_bytes(c, prec, na, false));
+    ProfScope ps(c, prec == WMG_PREC_DOUBLE ? PROF_DSLASH_64 : PROF_DSLASH_LO, dslash_bytes(c, prec, na, false), na);
     dslash(prec, out, in, nullptr, c->gauge[prec], c->fine, c->d_mass, active, nrhs, red, rb, c->stream);
   } else {
-    ProfScope ps(c, PROF_COARSE, coarse_bytes(c, l, prec, na));
+    ProfScope ps(c, PROF_COARSE, coarse_bytes(c, l, prec, na), na);
     const LevelData& L = c->L[l];
     coarse_apply(prec, L.A[prec], L.g, L.ndof, in, out, nrhs, c->d_shift[l], false, active,
                  red == 1 ? rb : nullptr, c->stream);
@@ -214,7 +223,7 @@ wmg_status mr(wmg_ctx* c, int l, int prec, void* x, const void* b, int nrhs, int
   const int na = nact_of(c, active, nrhs);
   const int dcls = prec == WMG_PREC_DOUBLE ? PROF_DSLASH_64 : PROF_DSLASH_LO;
   if (l == 0) {
-    ProfScope ps(c, dcls, dslash_bytes(c, prec, na, true));
+    ProfScope ps(c, dcls, dslash_bytes(c, prec, na, true), na);
     dslash(prec, r, x, b, c->gauge[prec], c->fine, c->d_mass, active, nrhs, 0, nullptr, c->stream);
   } else {
     level_apply(c, l, prec, x, r, nrhs, active, 0, nullptr);
@@ -222,7 +231,7 @@ wmg_status mr(wmg_ctx* c, int l, int prec, void* x, const void* b, int nrhs, int
   }
   for (int i = 0; i < nu; ++i) {
     if (l == 0) {
-      ProfScope ps(c, dcls, dslash_bytes(c, prec, na, false));
+      ProfScope ps(c, dcls, dslash_bytes(c, prec, na, false), na);
       dslash(prec, q, r, nullptr, c->gauge[prec], c->fine, c->d_mass, active, nrhs, 2, &rb, c->stream);
     } else {
       level_apply(c, l, prec, r, q, nrhs, active, 0, nullptr);
@@ -267,6 +276,7 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
   coarse_apply(prec, L.A[prec], L.g, L.ndof, r, z, nrhs, c->d_shift[l], true, nullptr, &rzz0, s);
   blas_convert(prec, p, prec, z, n, nrhs, nullptr, s);
   k_cg_init<<<1, 64, 0, s>>>(cg.done, cg.iters, cg.bb, active, nrhs);
+  count_launch();
   RedBuf rqq{c->red_partial, c->red_counter, cg.qq};
   RedBuf rrr{c->red_partial, c->red_counter, cg.rr};
   int parity = 0;
@@ -274,7 +284,7 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
   const double cb = coarse_bytes(c, l, prec, nrhs);
   for (int it = 0; it < c->prm.coarse_maxit; ++it) {
     {
-      ProfScope ps(c, PROF_COARSE, cb);
+      ProfScope ps(c, PROF_COARSE, cb, nrhs);
       coarse_apply(prec, L.A[prec], L.g, L.ndof, p, q, nrhs, c->d_shift[l], false, nullptr, &rqq, s);
     }
     {
@@ -283,7 +293,7 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
     }
     RedBuf rzz{c->red_partial, c->red_counter, cg.zz + (1 - parity) * nrhs};
     {
-      ProfScope ps(c, PROF_COARSE, cb);
+      ProfScope ps(c, PROF_COARSE, cb, nrhs);
       coarse_apply(prec, L.A[prec], L.g, L.ndof, r, z, nrhs, c->d_shift[l], true, nullptr, &rzz, s);
     }
     {
@@ -322,7 +332,7 @@ wmg_status cycle(wmg_ctx* c, int l, int last, int prec, const void* r, void* e, 
       rin = t;
     }
     {
-      ProfScope ps(c, PROF_RESTRICT, transfer_bytes(c, l, prec, nact_of(c, active, nrhs)));
+      ProfScope ps(c, PROF_RESTRICT, transfer_bytes(c, l, prec, nact_of(c, active, nrhs)), nact_of(c, active, nrhs));
       if (l == 0) restrict_fine(prec, L.P[prec], L.bk, rin, rc, nrhs, active, c->stream);
       else restrict_coarse(prec, L.P[prec], L.bk, rin, rc, nrhs, active, c->stream);
     }
@@ -330,7 +340,7 @@ wmg_status cycle(wmg_ctx* c, int l, int last, int prec, const void* r, void* e, 
     void* dst = e;
     if (rep > 0) TRY(vec_ws(c, l, "cyc_p", prec, nrhs, &dst));
     {
-      ProfScope ps(c, PROF_PROLONG, transfer_bytes(c, l, prec, nact_of(c, active, nrhs)));
+      ProfScope ps(c, PROF_PROLONG, transfer_bytes(c, l, prec, nact_of(c, active, nrhs)), nact_of(c, active, nrhs));
       if (l == 0) prolong_fine(prec, L.P[prec], L.bk, ec, dst, nrhs, active, c->stream);
       else prolong_coarse(prec, L.P[prec], L.bk, ec, dst, nrhs, active, c->stream);
     }
@@ -486,7 +496,8 @@ wmg_status fgcr(wmg_ctx* c, const void* b64, void* x64, int nrhs, const double* 
     if (use_mg) TRY(cycle(c, 0, c->nlev - 1, lo, rlo, zk, nrhs, c->d_active));
     else blas_convert(lo, zk, lo, rlo, n, nrhs, c->d_active, s);
     {
-      ProfScope ps(c, lo == WMG_PREC_DOUBLE ? PROF_DSLASH_64 : PROF_DSLASH_LO, dslash_bytes(c, lo, c->n_active, false));
+      ProfScope ps(c, lo == WMG_PREC_DOUBLE ? PROF_DSLASH_64 : PROF_DSLASH_LO, dslash_bytes(c, lo, c->n_active, false),
+                   c->n_active);
       dslash(lo, wk, zk, nullptr, c->gauge[lo], c->fine, c->d_mass, c->d_active, nrhs, 0, nullptr, s);
     }
     {
@@ -511,7 +522,7 @@ wmg_status fgcr(wmg_ctx* c, const void* b64, void* x64, int nrhs, const double* 
     if (anyrel) {
       // FP64 true residual r64 = b - D x64 for every rhs; applied where rel is set
       {
-        ProfScope ps(c, PROF_DSLASH_64, dslash_bytes(c, WMG_PREC_DOUBLE, nrhs, true));
+        ProfScope ps(c, PROF_DSLASH_64, dslash_bytes(c, WMG_PREC_DOUBLE, nrhs, true), nrhs);
         dslash(WMG_PREC_DOUBLE, r64, x64, b64, c->gauge[0], c->fine, c->d_mass, nullptr, nrhs, 1, &rb_r64, s);
       }
       TRY(download(c, rb_r64.result, nrhs, t));

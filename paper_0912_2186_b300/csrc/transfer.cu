@@ -318,6 +318,7 @@ static void launch_restrict_fine(const void* P, const Blocking& bk, const void* 
 
 void restrict_fine(int prec, const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
                    const int* active, cudaStream_t s) {
+  count_launch();
   if (prec == WMG_PREC_DOUBLE) {
     if (nrhs == 1) launch_restrict_fine<double, 1>(P, bk, in, out, nrhs, active, s);
     else launch_restrict_fine<double, 2>(P, bk, in, out, nrhs, active, s);
@@ -339,6 +340,7 @@ static void launch_prolong_fine(const void* P, const Blocking& bk, const void* i
 
 void prolong_fine(int prec, const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
                   const int* active, cudaStream_t s) {
+  count_launch();
   if (prec == WMG_PREC_DOUBLE) {
     if (nrhs == 1) launch_prolong_fine<double, 1>(P, bk, in, out, nrhs, active, s);
     else launch_prolong_fine<double, 2>(P, bk, in, out, nrhs, active, s);
@@ -364,6 +366,7 @@ static void launch_restrict_coarse(const void* P, const Blocking& bk, const void
 
 void restrict_coarse(int prec, const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
                      const int* active, cudaStream_t s) {
+  count_launch();
   if (prec == WMG_PREC_DOUBLE) {
     if (nrhs == 1) launch_restrict_coarse<double, 1>(P, bk, in, out, nrhs, active, s);
     else launch_restrict_coarse<double, 4>(P, bk, in, out, nrhs, active, s);
@@ -383,6 +386,7 @@ static void launch_prolong_coarse(const void* P, const Blocking& bk, const void*
 
 void prolong_coarse(int prec, const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
                     const int* active, cudaStream_t s) {
+  count_launch();
   if (prec == WMG_PREC_DOUBLE) {
     if (nrhs == 1) launch_prolong_coarse<double, 1>(P, bk, in, out, nrhs, active, s);
     else launch_prolong_coarse<double, 4>(P, bk, in, out, nrhs, active, s);
@@ -393,6 +397,7 @@ void prolong_coarse(int prec, const void* P, const Blocking& bk, const void* in,
 }
 
 void block_gs(bool fine_level, void* vecs, const Blocking& bk, int* rank_flag, cudaStream_t s) {
+  count_launch();
   GsLayout L;
   L.fine = fine_level;
   L.bk = bk;

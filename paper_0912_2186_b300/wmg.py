@@ -99,7 +99,8 @@ def load():
         "wmg_prolong": (i, [vp, i, i, vp, vp, i]),
         "wmg_apply_coarse": (i, [vp, i, i, i, vp, vp, i]),
         "wmg_profile_enable": (i, [vp, i]),
-        "wmg_profile_get": (i, [vp, i, P(d), P(ctypes.c_longlong), P(d)]),
+        "wmg_launch_count": (i, [P(ctypes.c_longlong)]),
+        "wmg_profile_get": (i, [vp, i, P(d), P(ctypes.c_longlong), P(d), P(d)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -130,6 +131,12 @@ def default_params(**kw):
         else:
             setattr(p, k, v)
     return p
+
+
+def launch_count():
+    n = ctypes.c_longlong()
+    load().wmg_launch_count(ctypes.byref(n))
+    return n.value
 
 
 def _ptr(x):
@@ -249,9 +256,10 @@ class Context:
     def profile_get(self):
         out = {}
         for k, name in enumerate(self.PROF_CLASSES):
-            ms, n, b = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
-            self._check(self.lib.wmg_profile_get(self.h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)))
-            out[name] = {"ms": ms.value, "launches": n.value, "bytes": b.value}
+            ms, n, b, u = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+            self._check(self.lib.wmg_profile_get(self.h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b),
+                                                 ctypes.byref(u)))
+            out[name] = {"ms": ms.value, "launches": n.value, "bytes": b.value, "units": u.value}
         return out
 
     def apply_coarse(self, level, prec, inp, out, nrhs, dagger=False):
