@@ -194,6 +194,23 @@ wmg_status wmg_prolong(wmg_ctx* ctx, int level, int prec, const void* coarse_dev
 wmg_status wmg_apply_coarse(wmg_ctx* ctx, int level, int prec, int dagger, const void* in_dev, void* out_dev,
                             int nrhs);
 
+/* ---- allocation-free residual (no counterpart in the paper) ----
+ * r = b - D(U) x and norm2[k] = |r_k|^2 for nrhs native fine spinors of precision prec
+ * (norm2: device array of nrhs doubles, accumulated in FP64), at the context's mass.
+ * For callers that must not allocate device memory inside a call: code that has handed
+ * all device memory to its own arena, or code that cannot afford the device-wide
+ * synchronisation a cudaMalloc / cudaFree may cause.  This call never allocates; its
+ * scratch (1 MiB of partial sums, 64 counters, 64 masses) is a fixed static device array
+ * that every GPU loading the library holds until exit.  Limits: nrhs <= 64 and
+ * nrhs * ceil(V / 128) <= 131072 (e.g. V = 16^3 x 32 allows 64 right-hand sides,
+ * V = 48^3 x 96 one); larger requests return WMG_EINVAL with the reason in
+ * wmg_last_error.  The first call on a device looks up the scratch's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls
+ * share the scratch: calls that overlap on the GPU race; r must not alias x.
+ * Stream-ordered on the context's stream. */
+wmg_status wmg_residual_noalloc(wmg_ctx* ctx, int prec, const void* b_dev, const void* x_dev, void* r_dev,
+                                double* norm2_dev, int nrhs);
+
 /* ---- instrumentation (no counterpart in the paper) ----
  * When enabled, every launch of the solver's kernels is bracketed by two CUDA events on
  * the context's stream (this adds host work per launch; leave it off for timing runs).

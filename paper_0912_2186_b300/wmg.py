@@ -98,6 +98,7 @@ def load():
         "wmg_restrict": (i, [vp, i, i, vp, vp, i]),
         "wmg_prolong": (i, [vp, i, i, vp, vp, i]),
         "wmg_apply_coarse": (i, [vp, i, i, i, vp, vp, i]),
+        "wmg_residual_noalloc": (i, [vp, i, vp, vp, vp, vp, i]),
         "wmg_profile_enable": (i, [vp, i]),
         "wmg_launch_count": (i, [P(ctypes.c_longlong)]),
         "wmg_profile_get": (i, [vp, i, P(d), P(ctypes.c_longlong), P(d), P(d)]),
@@ -247,6 +248,11 @@ class Context:
 
     def prolong(self, level, prec, coarse, fine, nrhs):
         return self._check(self.lib.wmg_prolong(self.h, int(level), prec, _ptr(coarse), _ptr(fine), int(nrhs)))
+
+    def residual_noalloc(self, prec, b, x, r, norm2, nrhs):
+        """r = b - D x and norm2[k] = |r_k|^2 without any device allocation (static scratch)."""
+        return self._check(self.lib.wmg_residual_noalloc(self.h, prec, _ptr(b), _ptr(x), _ptr(r), _ptr(norm2),
+                                                         int(nrhs)))
 
     PROF_CLASSES = ("dslash_sloppy", "dslash_fp64", "coarse", "restrict", "prolong", "blas", "setup")
 
