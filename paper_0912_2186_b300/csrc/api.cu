@@ -1,5 +1,6 @@
 // The C ABI of libwmg (include/wmg.h): argument checking, memory ownership and sequencing
 // of the driver in solver.cu.
+#include <cstdlib>
 #include <cstring>
 #include <random>
 #include <vector>
@@ -26,6 +27,8 @@ size_t csize(int prec) { return prec == WMG_PREC_DOUBLE ? sizeof(cd) : sizeof(cf
 bool prec_ok(int p) { return p == WMG_PREC_DOUBLE || p == WMG_PREC_SINGLE; }
 
 void free_hierarchy(wmg_ctx* c) {
+  cudaStreamSynchronize(c->stream);
+  clear_graphs(c);
   for (int l = 0; l < WMG_MAX_LEVELS; ++l)
     for (int p = 0; p < 2; ++p) {
       if (c->L[l].A[p]) cudaFree(c->L[l].A[p]);
@@ -69,7 +72,7 @@ wmg_status alloc_hierarchy(wmg_ctx* c, const wmg_params* p) {
     bk.coarse = make_geom(cd4);
     bk.N = p->nvec[l];
     bk.nf = L.ndof;
-    if (bk.N < 1 || 2 * bk.N > 256) return bad(c, "nvec must be in 1..128");
+    if (bk.N < 1 || bk.N > 32) return bad(c, "nvec must be in 1..32");
     const int E = l == 0 ? bk.bs * 6 : bk.bs * (L.ndof / 2);
     if (E > 256 * 8) return bad(c, "block too large for the Gram-Schmidt kernel (sites x dof per chirality > 2048)");
     if (l == 0 && (size_t)4 * 12 * bk.bs * sizeof(cf) > 200 * 1024) return bad(c, "fine block too large");
@@ -104,7 +107,7 @@ void wmg_default_params(wmg_params* p) {
   p->coarse_maxit = 2000;
   p->max_iter = 1000;
   p->prec_sloppy = WMG_PREC_SINGLE;
-  p->reliable_delta = 0.1;
+  p->reliable_delta = 0.01;
   p->seed = 20091212ULL;
 }
 
@@ -134,6 +137,15 @@ wmg_status wmg_create(wmg_ctx** out, const int dims[4], void* stream) {
   c->fine = make_geom(dims);
   c->stream = (cudaStream_t)stream;
   cudaGetDevice(&c->device);
+  if (!stream) {
+    // a stream of our own (ordered with the legacy default stream) so that work can be captured
+    if (cudaStreamCreate(&c->own_stream) != cudaSuccess) {
+      delete c;
+      return WMG_ECUDA;
+    }
+    c->stream = c->own_stream;
+  }
+  if (const char* g = std::getenv("WMG_NO_GRAPHS")) c->use_graphs = !(g[0] == '1');
   c->L[0].g = c->fine;
   c->L[0].ndof = 12;
   cudaError_t e = cudaSuccess;
@@ -168,6 +180,7 @@ wmg_status wmg_destroy(wmg_ctx* c) {
   if (!c) return WMG_EINVAL;
   cudaStreamSynchronize(c->stream);
   prof_flush(c);
+  clear_graphs(c);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   free_hierarchy(c);
   for (auto& kv : c->ws) cudaFree(kv.second.first);
@@ -178,6 +191,7 @@ wmg_status wmg_destroy(wmg_ctx* c) {
     if (p) cudaFree(p);
   if (c->h_pin) cudaFreeHost(c->h_pin);
   if (c->h_pin_i) cudaFreeHost(c->h_pin_i);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;
   return WMG_OK;
 }

@@ -26,63 +26,83 @@ WMG_HD bool same_block(int x, int L, int b, int sign) {
 }
 
 // ------------------------------------------------------------------------------------
-// apply: thread per (site, row) and RC right-hand sides
+// apply: one CTA per coarse site and chunk of NR right-hand sides.  The nine neighbour
+// vectors of the chunk are staged in shared memory (sigma_3 applied on load for the
+// adjoint); thread (row, ks) accumulates the products of its row of the 9 n x n blocks over
+// the columns kk = ks, ks + KS, ... for all NR right-hand sides in registers; the KS partial
+// sums of a row are added in shared memory.  Optional per-rhs |out|^2 (deterministic order).
 // ------------------------------------------------------------------------------------
-template <typename R, int RC>
-__global__ void k_coarse_apply(const void* __restrict__ A_, Geom g, int n, const void* __restrict__ in_,
-                               void* __restrict__ out_, int nrhs, const double* __restrict__ shift, int dagger,
-                               const int* __restrict__ active, RedBuf rb, int want_norm) {
-  const int spc = blockDim.x / n;  // sites per CTA
-  const int ls = threadIdx.x / n, row = threadIdx.x % n;
-  const int v = blockIdx.x * spc + ls;
-  const int r0 = blockIdx.y * RC;
+constexpr int kCoarseKS = 4;
+
+template <typename R, int NR>
+__global__ void __launch_bounds__(256) k_coarse_apply(const void* __restrict__ A_, Geom g, int n,
+                                                      const void* __restrict__ in_, void* __restrict__ out_, int nrhs,
+                                                      const double* __restrict__ shift, int dagger,
+                                                      const int* __restrict__ active, RedBuf rb, int want_norm) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<R>* xs = reinterpret_cast<cpx<R>*>(smraw);          // [9 n][NR]
+  cpx<R>* red = xs + (size_t)9 * n * NR;                   // [KS][n][NR]
+  const int v = blockIdx.x;
+  const int r0 = blockIdx.y * NR;
   const int N = n / 2;
-  const cpx<R>* A = reinterpret_cast<const cpx<R>*>(A_);
+  const cpx<R>* A = reinterpret_cast<const cpx<R>*>(A_) + (size_t)v * 9 * n * n;
   const cpx<R>* in = reinterpret_cast<const cpx<R>*>(in_);
   cpx<R>* out = reinterpret_cast<cpx<R>*>(out_);
-  double nv[RC];
-#pragma unroll
-  for (int rr = 0; rr < RC; ++rr) nv[rr] = 0.0;
-  if (ls < spc && v < g.V) {
-    cpx<R> acc[RC];
-#pragma unroll
-    for (int rr = 0; rr < RC; ++rr) acc[rr] = cpx<R>{R(0), R(0)};
-    int c[4];
-    site_coords(g, v, c);
-    for (int k = 0; k < 9; ++k) {
+  int c[4];
+  site_coords(g, v, c);
+  for (int i = threadIdx.x; i < 9 * n * NR; i += blockDim.x) {
+    const int rr = i % NR, kj = i / NR, k = kj / n, j = kj % n;
+    const int r = r0 + rr;
+    cpx<R> x{R(0), R(0)};
+    if (r < nrhs) {
       const int nb = stencil_neighbour(g, v, c, k);
-      const cpx<R>* Ak = A + ((size_t)v * 9 + k) * n * n + row;
-      for (int j = 0; j < n; ++j) {
-        const cpx<R> a = Ak[(size_t)j * n];
-        const bool neg = dagger && j >= N;
-#pragma unroll
-        for (int rr = 0; rr < RC; ++rr) {
-          const int r = r0 + rr < nrhs ? r0 + rr : nrhs - 1;
-          cpx<R> x = in[((size_t)r * g.V + nb) * n + j];
-          if (neg) x = -x;
-          cfma(acc[rr], a, x);
-        }
-      }
+      x = in[((size_t)r * g.V + nb) * n + j];
+      if (dagger && j >= N) x = -x;
     }
+    xs[i] = x;
+  }
+  __syncthreads();
+  const int row = threadIdx.x % n, ks = threadIdx.x / n;
+  cpx<R> acc[NR];
+#pragma unroll
+  for (int rr = 0; rr < NR; ++rr) acc[rr] = cpx<R>{R(0), R(0)};
+  if (ks < kCoarseKS) {
+    const int K = 9 * n;
+#pragma unroll 4
+    for (int kk = ks; kk < K; kk += kCoarseKS) {
+      const cpx<R> a = A[(size_t)kk * n + row];
+      const cpx<R>* xr = xs + (size_t)kk * NR;
+#pragma unroll
+      for (int rr = 0; rr < NR; ++rr) cfma(acc[rr], a, xr[rr]);
+    }
+#pragma unroll
+    for (int rr = 0; rr < NR; ++rr) red[((size_t)ks * n + row) * NR + rr] = acc[rr];
+  }
+  __syncthreads();
+  double nv[NR];
+#pragma unroll
+  for (int rr = 0; rr < NR; ++rr) nv[rr] = 0.0;
+  if (ks == 0) {
     const bool oneg = dagger && row >= N;
 #pragma unroll
-    for (int rr = 0; rr < RC; ++rr) {
+    for (int rr = 0; rr < NR; ++rr) {
+      cpx<R> o = red[(size_t)row * NR + rr];
+      for (int q = 1; q < kCoarseKS; ++q) o += red[((size_t)q * n + row) * NR + rr];
       const int r = r0 + rr;
       if (r >= nrhs) continue;
-      cpx<R> o = oneg ? -acc[rr] : acc[rr];
+      if (oneg) o = -o;
       if (shift) o += R(shift[r]) * in[((size_t)r * g.V + v) * n + row];
       if (!active || active[r]) out[((size_t)r * g.V + v) * n + row] = o;
       nv[rr] = double(o.re) * o.re + double(o.im) * o.im;
     }
   }
   if (want_norm) {
-    __shared__ double sm[32 * RC];
-    cta_reduce<RC>(nv, sm);
-    // partial[r][blk]; counter per rhs chunk; the last CTA of the chunk sums every rhs of it
+    __shared__ double sm[32 * NR];
+    cta_reduce<NR>(nv, sm);
     __shared__ bool last;
     const int nblk = gridDim.x;
     if (threadIdx.x == 0) {
-      for (int rr = 0; rr < RC; ++rr)
+      for (int rr = 0; rr < NR; ++rr)
         if (r0 + rr < nrhs) rb.partial[(size_t)(r0 + rr) * nblk + blockIdx.x] = nv[rr];
       __threadfence();
       const unsigned prev = atomicAdd(rb.counter + blockIdx.y, 1u);
@@ -91,26 +111,29 @@ __global__ void k_coarse_apply(const void* __restrict__ A_, Geom g, int n, const
     __syncthreads();
     if (last) {
       __threadfence();
-      if (threadIdx.x < RC && r0 + threadIdx.x < nrhs) {
-        const volatile double* p = rb.partial + (size_t)(r0 + threadIdx.x) * nblk;
-        double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += p[b];
-        rb.result[r0 + threadIdx.x] = s;
+      __shared__ double sred[32];
+      for (int rr = 0; rr < NR && r0 + rr < nrhs; ++rr) {
+        const double s = cta_sum_strided(rb.partial + (size_t)(r0 + rr) * nblk, nblk, 1, sred);
+        if (threadIdx.x == 0) rb.result[r0 + rr] = s;
       }
       if (threadIdx.x == 0) rb.counter[blockIdx.y] = 0u;
     }
   }
 }
 
-template <typename R, int RC>
+template <typename R, int NR>
 static void launch_coarse_apply(const void* A, const Geom& g, int n, const void* in, void* out, int nrhs,
                                 const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s) {
-  int spc = 256 / n;
-  if (spc < 1) spc = 1;
-  const int T = ((spc * n + 31) / 32) * 32;
-  dim3 grid((g.V + spc - 1) / spc, (nrhs + RC - 1) / RC);
+  const int T = ((n * kCoarseKS + 31) / 32) * 32;
+  const size_t smem = ((size_t)9 * n * NR + (size_t)kCoarseKS * n * NR) * sizeof(cpx<R>);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_coarse_apply<R, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  dim3 grid(g.V, (nrhs + NR - 1) / NR);
   RedBuf r = rb ? *rb : RedBuf{nullptr, nullptr, nullptr};
-  k_coarse_apply<R, RC><<<grid, T, 0, s>>>(A, g, n, in, out, nrhs, shift, dagger ? 1 : 0, active, r, rb ? 1 : 0);
+  k_coarse_apply<R, NR><<<grid, T, smem, s>>>(A, g, n, in, out, nrhs, shift, dagger ? 1 : 0, active, r, rb ? 1 : 0);
 }
 
 void coarse_apply(int prec, const void* A, const Geom& g, int n, const void* in, void* out, int nrhs,
@@ -118,13 +141,13 @@ void coarse_apply(int prec, const void* A, const Geom& g, int n, const void* in,
   count_launch();
   if (prec == WMG_PREC_DOUBLE) {
     if (nrhs == 1) launch_coarse_apply<double, 1>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
-    else if (nrhs == 2) launch_coarse_apply<double, 2>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
-    else launch_coarse_apply<double, 4>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
+    else if (nrhs <= 4) launch_coarse_apply<double, 4>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
+    else launch_coarse_apply<double, 8>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
   } else {
     if (nrhs == 1) launch_coarse_apply<float, 1>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
-    else if (nrhs == 2) launch_coarse_apply<float, 2>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
     else if (nrhs <= 4) launch_coarse_apply<float, 4>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
-    else launch_coarse_apply<float, 8>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
+    else if (nrhs <= 8) launch_coarse_apply<float, 8>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
+    else launch_coarse_apply<float, 12>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
   }
 }
 

@@ -58,6 +58,9 @@ struct wmg_ctx {
   int* d_mask = nullptr;                       // [kMaxRhs]
   int* d_flag = nullptr;                       // misc device flag
   int* d_cgint = nullptr;                      // [2][kMaxRhs] cg done / iters
+  cudaStream_t own_stream = nullptr;          // created when the caller passes no stream
+  bool use_graphs = true;                      // capture the coarsest CGNR iterations
+  std::map<std::string, std::pair<cudaGraphExec_t, long long>> graphs;  // + launches per replay
   int n_active = 0;                            // active right-hand sides of the current solve
   // instrumentation
   bool prof_on = false;

@@ -6,6 +6,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <random>
 
@@ -51,6 +52,8 @@ wmg_status check(wmg_ctx* c, const char* what) {
     if (e_ != cudaSuccess) return fail((c), e_, #x);  \
   } while (0)
 
+wmg_status clear_graphs(wmg_ctx* c);
+
 wmg_status ws_get(wmg_ctx* c, const std::string& name, size_t bytes, void** out) {
   auto it = c->ws.find(name);
   if (it != c->ws.end() && it->second.second >= bytes) {
@@ -61,6 +64,7 @@ wmg_status ws_get(wmg_ctx* c, const std::string& name, size_t bytes, void** out)
     CU(c, cudaStreamSynchronize(c->stream));
     cudaFree(it->second.first);
     c->ws.erase(it);
+    clear_graphs(c);  // captured graphs may refer to the old buffer
   }
   void* p = nullptr;
   CU(c, cudaMalloc(&p, bytes > 0 ? bytes : 16));
@@ -87,6 +91,7 @@ wmg_status ensure_partials(wmg_ctx* c, size_t need) {
   CU(c, cudaStreamSynchronize(c->stream));
   if (c->red_partial) cudaFree(c->red_partial);
   c->red_partial = nullptr;
+  clear_graphs(c);
   CU(c, cudaMalloc(&c->red_partial, need * sizeof(double)));
   c->red_partial_n = need;
   return WMG_OK;
@@ -251,6 +256,12 @@ __global__ void k_cg_init(int* done, int* iters, const double* bb, const int* ac
   done[r] = (active && !active[r]) || !(bb[r] > 0.0);
 }
 
+wmg_status clear_graphs(wmg_ctx* c) {
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
+  c->graphs.clear();
+  return WMG_OK;
+}
+
 // CG on the normal equations on level l (coarse): x = A^-1 b approximately
 wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, const int* active) {
   const LevelData& L = c->L[l];
@@ -279,10 +290,10 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
   count_launch();
   RedBuf rqq{c->red_partial, c->red_counter, cg.qq};
   RedBuf rrr{c->red_partial, c->red_counter, cg.rr};
-  int parity = 0;
-  const int check_every = 8;
   const double cb = coarse_bytes(c, l, prec, nrhs);
-  for (int it = 0; it < c->prm.coarse_maxit; ++it) {
+  // one CGNR iteration: q = A p (|q|^2), x += alpha p, r -= alpha q (|r|^2, convergence flags),
+  // z = A^dag r (|z|^2), p = z + beta p
+  auto body = [&](int parity) {
     {
       ProfScope ps(c, PROF_COARSE, cb, nrhs);
       coarse_apply(prec, L.A[prec], L.g, L.ndof, p, q, nrhs, c->d_shift[l], false, nullptr, &rqq, s);
@@ -300,12 +311,51 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
       ProfScope ps(c, PROF_BLAS, 0);
       cg_xpay(prec, p, z, n, nrhs, cg, parity, s);
     }
-    parity ^= 1;
-    if ((it + 1) % check_every == 0) {
-      CU(c, cudaMemcpyAsync(c->h_pin_i, cg.done, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
-      CU(c, cudaStreamSynchronize(s));
-      bool all = true;
-      for (int i = 0; i < nrhs; ++i) all = all && c->h_pin_i[i];
+  };
+  auto all_done = [&](bool* all) -> wmg_status {
+    CU(c, cudaMemcpyAsync(c->h_pin_i, cg.done, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(c, cudaStreamSynchronize(s));
+    *all = true;
+    for (int i = 0; i < nrhs; ++i) *all = *all && c->h_pin_i[i];
+    return WMG_OK;
+  };
+  const int chunk = 8;  // even: every chunk starts at parity 0
+  if (!c->prof_on && c->use_graphs) {
+    // the chunk of iterations is captured once per argument set and replayed
+    char key[512];
+    std::snprintf(key, sizeof key, "cg%d/%d/%d/%p/%p/%p/%p/%p/%p/%p/%p/%p/%.17g", l, prec, nrhs, L.A[prec], x, r, p,
+                  q, z, (void*)c->d_shift[l], (void*)c->red_partial, (void*)c->res, cg.tol2);
+    cudaGraphExec_t ge = nullptr;
+    auto it = c->graphs.find(key);
+    if (it != c->graphs.end()) {
+      ge = it->second.first;
+    } else {
+      if (c->graphs.size() > 64) TRY(clear_graphs(c));
+      const long long l0 = launch_count();
+      cudaGraph_t gr;
+      CU(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      for (int i = 0; i < chunk; ++i) body(i & 1);
+      CU(c, cudaStreamEndCapture(s, &gr));
+      const long long per = launch_count() - l0;
+      count_launch((int)-per);  // captured, not launched
+      cudaError_t e = cudaGraphInstantiate(&ge, gr, 0);
+      cudaGraphDestroy(gr);
+      if (e != cudaSuccess) return fail(c, e, "cudaGraphInstantiate");
+      c->graphs[key] = {ge, per};
+    }
+    const long long per = c->graphs[key].second;
+    for (int itr = 0; itr < c->prm.coarse_maxit; itr += chunk) {
+      CU(c, cudaGraphLaunch(ge, s));
+      count_launch((int)per);
+      bool all;
+      TRY(all_done(&all));
+      if (all) break;
+    }
+  } else {
+    for (int itr = 0; itr < c->prm.coarse_maxit; itr += chunk) {
+      for (int i = 0; i < chunk; ++i) body(i & 1);
+      bool all;
+      TRY(all_done(&all));
       if (all) break;
     }
   }

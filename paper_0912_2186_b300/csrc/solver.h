@@ -22,6 +22,7 @@ wmg_status orthonormalise(wmg_ctx* c, int l);
 wmg_status build_from_vectors(wmg_ctx* c, int l, int prec, const void* vecs);
 wmg_status setup_level(wmg_ctx* c, int l, void* vecs);
 void prof_flush(wmg_ctx* c);
+wmg_status clear_graphs(wmg_ctx* c);
 wmg_status fgcr(wmg_ctx* c, const void* b64, void* x64, int nrhs, const double* masses, wmg_info* info, bool use_mg);
 
 }  // namespace wmg

@@ -207,11 +207,21 @@ WMG_D void cta_reduce(double v[NVAL], double* smem /* >= 32*NVAL */) {
   __syncthreads();
 }
 
+// Sum p[b * stride], b < count, over the whole CTA in a fixed order (thread t takes
+// b = t, t + blockDim, ...; then the fixed-shape tree of cta_reduce).  Valid in thread 0.
+WMG_D double cta_sum_strided(const volatile double* p, int count, int stride, double* smem /* >= 32 */) {
+  double s[1] = {0.0};
+  for (int b = threadIdx.x; b < count; b += blockDim.x) s[0] += p[(size_t)b * stride];
+  cta_reduce<1>(s, smem);
+  return s[0];
+}
+
 // After cta_reduce (thread 0 holds v): writes the CTA's partials; the last CTA for `rhs`
-// sums all partials in order into rb.result.  nblk = number of CTAs per rhs.
+// sums all partials (fixed order, whole CTA) into rb.result.  nblk = CTAs per rhs.
 template <int NVAL>
 WMG_D void grid_finish(const RedBuf& rb, int rhs, int blk, int nblk, const double v[NVAL]) {
   __shared__ bool last;
+  __shared__ double sred[32];
   if (threadIdx.x == 0) {
     double* p = rb.partial + ((size_t)rhs * nblk + blk) * NVAL;
 #pragma unroll
@@ -223,11 +233,10 @@ WMG_D void grid_finish(const RedBuf& rb, int rhs, int blk, int nblk, const doubl
   __syncthreads();
   if (last) {
     __threadfence();
-    if (threadIdx.x < NVAL) {
-      const volatile double* p = rb.partial + (size_t)rhs * nblk * NVAL;
-      double s = 0.0;
-      for (int b = 0; b < nblk; ++b) s += p[(size_t)b * NVAL + threadIdx.x];
-      rb.result[(size_t)rhs * NVAL + threadIdx.x] = s;
+    const volatile double* p = rb.partial + (size_t)rhs * nblk * NVAL;
+    for (int i = 0; i < NVAL; ++i) {
+      const double s = cta_sum_strided(p + i, nblk, NVAL, sred);
+      if (threadIdx.x == 0) rb.result[(size_t)rhs * NVAL + i] = s;
     }
     if (threadIdx.x == 0) rb.counter[rhs] = 0u;
   }
