@@ -194,6 +194,33 @@ wmg_status wmg_prolong(wmg_ctx* ctx, int level, int prec, const void* coarse_dev
 wmg_status wmg_apply_coarse(wmg_ctx* ctx, int level, int prec, int dagger, const void* in_dev, void* out_dev,
                             int nrhs);
 
+/* ---- serving: continuous-batching solve server ----
+ * Keeps several gauge fields and their hierarchies resident (one context per field, set up
+ * with wmg_setup) and serves solve requests (a mass and 1..n right-hand sides) for them.
+ * Each field has a worker thread and the context's own CUDA stream, so different fields'
+ * work overlaps on the device.  A field's requests are batched: their right-hand sides
+ * occupy the slots of one multi-right-hand-side outer solve (all slots share the field's
+ * hierarchy; masses may differ, entering as diagonal shifts), and requests arriving while a
+ * batch runs are admitted into slots freed by converged right-hand sides at the next restart
+ * boundary.  Every right-hand side is iterated independently, so its result does not depend
+ * on what else is in the batch.  Fields are admitted against an HBM budget by their
+ * footprint (gauge + hierarchy + slot workspaces). */
+typedef struct wmg_server wmg_server;
+wmg_status wmg_server_create(wmg_server** out, size_t hbm_budget_bytes);
+/* Hand a set-up context to the server (no other call may use it until wmg_server_destroy).
+ * nslots (1..64): right-hand sides solved together.  WMG_ENOMEM if the budget is exceeded. */
+wmg_status wmg_server_add_field(wmg_server* s, wmg_ctx* ctx, int nslots, int* field_id);
+/* Queue a solve of D(m) x = b (canonical host spinors, nrhs of them).  b and x must stay valid
+ * until wmg_server_wait returns for the ticket.  Thread-safe. */
+wmg_status wmg_server_submit(wmg_server* s, int field_id, double mass, const double* b_host, double* x_host,
+                             int nrhs, long long* ticket);
+wmg_status wmg_server_poll(wmg_server* s, long long ticket, int* done);
+/* Block until the request is complete; info: array of nrhs (or NULL); latency_s: seconds from
+ * submission to completion (or NULL).  Returns the request's status and releases the ticket. */
+wmg_status wmg_server_wait(wmg_server* s, long long ticket, wmg_info* info, double* latency_s);
+/* Finish the queued work, stop the workers, free the server (the contexts stay the caller's). */
+wmg_status wmg_server_destroy(wmg_server* s);
+
 /* ---- allocation-free residual (no counterpart in the paper) ----
  * r = b - D(U) x and norm2[k] = |r_k|^2 for nrhs native fine spinors of precision prec
  * (norm2: device array of nrhs doubles, accumulated in FP64), at the context's mass.

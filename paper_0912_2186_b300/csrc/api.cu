@@ -342,14 +342,9 @@ static wmg_status solve_dev_impl(wmg_ctx* c, const double* b, double* x, int nrh
   wmg_status worst = WMG_OK;
   for (int r0 = 0; r0 < nrhs; r0 += kMaxRhs) {
     const int nr = std::min(kMaxRhs, nrhs - r0);
-    void *b64, *x64;
-    TRY(vec_ws(c, 0, "solve_b", WMG_PREC_DOUBLE, nr, &b64));
-    TRY(vec_ws(c, 0, "solve_x", WMG_PREC_DOUBLE, nr, &x64));
-    pack_spinor(WMG_PREC_DOUBLE, b + V * 24 * r0, b64, c->fine.V, nr, c->stream);
-    wmg_status st = fgcr(c, b64, x64, nr, nullptr, info ? info + r0 : nullptr, mg);
+    wmg_status st = fgcr(c, b + V * 24 * r0, x + V * 24 * r0, nr, nullptr, info ? info + r0 : nullptr, mg);
     if (st != WMG_OK && st != WMG_ENOCONV) return st;
     if (st != WMG_OK) worst = st;
-    unpack_spinor(WMG_PREC_DOUBLE, x64, x + V * 24 * r0, c->fine.V, nr, c->stream);
   }
   CU(c, cudaStreamSynchronize(c->stream));
   TRY(check(c, "solve"));

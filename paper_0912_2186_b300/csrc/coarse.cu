@@ -126,11 +126,11 @@ static void launch_coarse_apply(const void* A, const Geom& g, int n, const void*
                                 const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s) {
   const int T = ((n * kCoarseKS + 31) / 32) * 32;
   const size_t smem = ((size_t)9 * n * NR + (size_t)kCoarseKS * n * NR) * sizeof(cpx<R>);
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {
     cudaFuncSetAttribute(k_coarse_apply<R, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   dim3 grid(g.V, (nrhs + NR - 1) / NR);
   RedBuf r = rb ? *rb : RedBuf{nullptr, nullptr, nullptr};
   k_coarse_apply<R, NR><<<grid, T, smem, s>>>(A, g, n, in, out, nrhs, shift, dagger ? 1 : 0, active, r, rb ? 1 : 0);

@@ -497,70 +497,113 @@ wmg_status setup_level(wmg_ctx* c, int l, void* vecs) {
 }
 
 // ------------------------------------------------------------------------------------
-// outer flexible GCR with FP64 reliable updates.  b64, x64: native FP64 fine spinors.
+// Outer flexible GCR (Sec. 3) with FP64 reliable updates, run as a slot engine: each
+// right-hand side occupies one slot with its own mass, Krylov scalars, reliable-update
+// reference and convergence state; kernels run over all slots and skip inactive ones.  New
+// right-hand sides are admitted into free slots at restart boundaries (k = 0), so a solve
+// can take in work while others are in flight (continuous batching).  The arithmetic of a
+// slot never depends on the other slots: its result is the same alone and in a batch.
 // ------------------------------------------------------------------------------------
-wmg_status fgcr(wmg_ctx* c, const void* b64, void* x64, int nrhs, const double* masses, wmg_info* info,
-                bool use_mg) {
-  auto t0 = std::chrono::steady_clock::now();
-  if (info) std::memset(info, 0, sizeof(wmg_info) * nrhs);
+wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
   const int lo = use_mg ? c->prm.prec_sloppy : WMG_PREC_DOUBLE;
   const size_t n = (size_t)c->fine.V * 12;
   const int m = std::min(std::max(c->prm.gcr_restart, 1), kMaxKrylov);
   cudaStream_t s = c->stream;
-  TRY(ensure_reductions(c, nrhs));
-  TRY(set_rhs_scalars(c, masses, nrhs));
-  void *r64, *rlo, *Z, *W;
-  TRY(vec_ws(c, 0, "gcr_r64", WMG_PREC_DOUBLE, nrhs, &r64));
-  TRY(vec_ws(c, 0, "gcr_rlo", lo, nrhs, &rlo));
-  const size_t slot = n * nrhs * csize(lo);
+  if (nslots < 1 || nslots > kMaxRhs) return WMG_EINVAL;
+  TRY(ensure_reductions(c, nslots));
+  void *b64, *x64, *r64, *rlo, *Z, *W;
+  TRY(vec_ws(c, 0, "gcr_b64", WMG_PREC_DOUBLE, nslots, &b64));
+  TRY(vec_ws(c, 0, "gcr_x64", WMG_PREC_DOUBLE, nslots, &x64));
+  TRY(vec_ws(c, 0, "gcr_r64", WMG_PREC_DOUBLE, nslots, &r64));
+  TRY(vec_ws(c, 0, "gcr_rlo", lo, nslots, &rlo));
+  const size_t slot = n * nslots * csize(lo);
   TRY(ws_get(c, std::string("gcr_Z") + (lo ? "s" : "d"), slot * m, &Z));
   TRY(ws_get(c, std::string("gcr_W") + (lo ? "s" : "d"), slot * m, &W));
-  blas_zero(WMG_PREC_DOUBLE, x64, n, nrhs, s);
-  blas_convert(WMG_PREC_DOUBLE, r64, WMG_PREC_DOUBLE, b64, n, nrhs, nullptr, s);
-  blas_norm2(WMG_PREC_DOUBLE, b64, n, nrhs, redbuf(c, RES_BB), s);
-  std::vector<double> bb, rn2, t;
-  TRY(download(c, res_slot(c, RES_BB), nrhs, bb));
-  std::vector<int> active(nrhs), mask(nrhs), iters(nrhs, 0), rel(nrhs, 0), conv(nrhs, 0);
-  std::vector<double> bnorm(nrhs), ref(nrhs), tres(nrhs, 0.0);
-  for (int r = 0; r < nrhs; ++r) {
-    bnorm[r] = std::sqrt(bb[r]);
-    ref[r] = bnorm[r];
-    active[r] = bb[r] > 0.0;
-    conv[r] = !active[r];
-  }
-  TRY(upload_ints(c, c->d_active, active));
-  c->n_active = 0;
-  for (int r = 0; r < nrhs; ++r) c->n_active += active[r];
-  blas_convert(lo, rlo, WMG_PREC_DOUBLE, r64, n, nrhs, nullptr, s);
+  const size_t f64 = n * sizeof(cd), flo = n * csize(lo);
+  auto at = [](void* base, size_t bytes, int r) { return (void*)((char*)base + bytes * r); };
   const double tol = c->prm.tol;
   const double delta = (lo == WMG_PREC_DOUBLE) ? 0.0 : c->prm.reliable_delta;
-  int k = 0;
+  std::vector<int> active(nslots, 0), rel(nslots, 0), iters(nslots, 0), relups(nslots, 0);
+  std::vector<double> bnorm(nslots, 0.0), ref(nslots, 0.0), tres(nslots, 0.0), mass(nslots, c->mass);
+  std::vector<std::chrono::steady_clock::time_point> t0(nslots);
+  std::vector<double> rn2, t;
   RedBuf rb_coef = redbuf(c, RES_COEF), rb_w = redbuf(c, RES_WRED), rb_rn = redbuf(c, RES_RN),
-         rb_r64 = redbuf(c, RES_R64);
+         rb_r64 = redbuf(c, RES_R64), rb_bb = redbuf(c, RES_BB);
+  auto count_active = [&]() {
+    c->n_active = 0;
+    for (int r = 0; r < nslots; ++r) c->n_active += active[r];
+  };
+  auto finish = [&](int r, bool conv) -> wmg_status {
+    wmg_info info{};
+    info.iters = iters[r];
+    info.reliable_updates = relups[r];
+    info.converged = conv;
+    info.true_resid = tres[r];
+    info.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0[r]).count();
+    active[r] = 0;
+    return src.finish(c, r, at(x64, f64, r), info);
+  };
+  TRY(set_rhs_scalars(c, mass.data(), nslots));
+  int k = 0;
   while (true) {
-    bool any = false;
-    for (int r = 0; r < nrhs; ++r) any = any || active[r];
-    if (!any) break;
+    if (k == 0) {
+      // admission into free slots
+      std::vector<int> free_slots;
+      for (int r = 0; r < nslots; ++r)
+        if (!active[r]) free_slots.push_back(r);
+      std::vector<Admission> adm;
+      if (!free_slots.empty()) src.admit(c, free_slots, adm);
+      if (!adm.empty()) {
+        std::vector<int> mask(nslots, 0);
+        for (const Admission& a : adm) {
+          pack_spinor(WMG_PREC_DOUBLE, a.b_canon_dev, at(b64, f64, a.slot), c->fine.V, 1, s);
+          blas_zero(WMG_PREC_DOUBLE, at(x64, f64, a.slot), n, 1, s);
+          blas_convert(WMG_PREC_DOUBLE, at(r64, f64, a.slot), WMG_PREC_DOUBLE, at(b64, f64, a.slot), n, 1, nullptr, s);
+          mass[a.slot] = a.mass;
+          mask[a.slot] = 1;
+          iters[a.slot] = relups[a.slot] = 0;
+          t0[a.slot] = std::chrono::steady_clock::now();
+        }
+        blas_norm2(WMG_PREC_DOUBLE, b64, n, nslots, rb_bb, s);
+        std::vector<double> bb;
+        TRY(download(c, rb_bb.result, nslots, bb));
+        TRY(set_rhs_scalars(c, mass.data(), nslots));
+        TRY(upload_ints(c, c->d_mask, mask));
+        blas_convert(lo, rlo, WMG_PREC_DOUBLE, r64, n, nslots, c->d_mask, s);
+        for (const Admission& a : adm) {
+          const int r = a.slot;
+          bnorm[r] = ref[r] = std::sqrt(bb[r]);
+          tres[r] = 0.0;
+          if (bb[r] > 0.0) active[r] = 1;
+          else TRY(finish(r, true));  // b = 0: x = 0 exactly
+        }
+        TRY(upload_ints(c, c->d_active, active));
+        count_active();
+      }
+      bool any = false;
+      for (int r = 0; r < nslots; ++r) any = any || active[r];
+      if (!any) break;
+    }
     void* zk = (char*)Z + slot * k;
     void* wk = (char*)W + slot * k;
-    if (use_mg) TRY(cycle(c, 0, c->nlev - 1, lo, rlo, zk, nrhs, c->d_active));
-    else blas_convert(lo, zk, lo, rlo, n, nrhs, c->d_active, s);
+    if (use_mg) TRY(cycle(c, 0, c->nlev - 1, lo, rlo, zk, nslots, c->d_active));
+    else blas_convert(lo, zk, lo, rlo, n, nslots, c->d_active, s);
     {
       ProfScope ps(c, lo == WMG_PREC_DOUBLE ? PROF_DSLASH_64 : PROF_DSLASH_LO, dslash_bytes(c, lo, c->n_active, false),
                    c->n_active);
-      dslash(lo, wk, zk, nullptr, c->gauge[lo], c->fine, c->d_mass, c->d_active, nrhs, 0, nullptr, s);
+      dslash(lo, wk, zk, nullptr, c->gauge[lo], c->fine, c->d_mass, c->d_active, nslots, 0, nullptr, s);
     }
     {
       ProfScope ps(c, PROF_BLAS, 0);
-      if (k > 0) gcr_multidot(lo, W, slot, k, wk, n, nrhs, c->d_active, rb_coef, s);
-      gcr_orth(lo, W, Z, slot, k, wk, zk, rlo, rb_coef.result, k, n, nrhs, c->d_active, rb_w, s);
-      gcr_update(lo, (double*)x64, rlo, wk, zk, rb_w.result, n, nrhs, c->d_active, rb_rn, s);
+      if (k > 0) gcr_multidot(lo, W, slot, k, wk, n, nslots, c->d_active, rb_coef, s);
+      gcr_orth(lo, W, Z, slot, k, wk, zk, rlo, rb_coef.result, k, n, nslots, c->d_active, rb_w, s);
+      gcr_update(lo, (double*)x64, rlo, wk, zk, rb_w.result, n, nslots, c->d_active, rb_rn, s);
     }
     TRY(check(c, "gcr iteration"));
-    TRY(download(c, rb_rn.result, nrhs, rn2));
+    TRY(download(c, rb_rn.result, nslots, rn2));
     ++k;
     bool anyrel = false;
-    for (int r = 0; r < nrhs; ++r) {
+    for (int r = 0; r < nslots; ++r) {
       rel[r] = 0;
       if (!active[r]) continue;
       ++iters[r];
@@ -570,51 +613,85 @@ wmg_status fgcr(wmg_ctx* c, const void* b64, void* x64, int nrhs, const double* 
       anyrel = anyrel || rel[r];
     }
     if (anyrel) {
-      // FP64 true residual r64 = b - D x64 for every rhs; applied where rel is set
+      // FP64 true residual r64 = b - D x64 for the active slots; applied where rel is set
       {
-        ProfScope ps(c, PROF_DSLASH_64, dslash_bytes(c, WMG_PREC_DOUBLE, nrhs, true), nrhs);
-        dslash(WMG_PREC_DOUBLE, r64, x64, b64, c->gauge[0], c->fine, c->d_mass, nullptr, nrhs, 1, &rb_r64, s);
+        ProfScope ps(c, PROF_DSLASH_64, dslash_bytes(c, WMG_PREC_DOUBLE, c->n_active, true), c->n_active);
+        dslash(WMG_PREC_DOUBLE, r64, x64, b64, c->gauge[0], c->fine, c->d_mass, c->d_active, nslots, 1, &rb_r64, s);
       }
-      TRY(download(c, rb_r64.result, nrhs, t));
+      TRY(download(c, rb_r64.result, nslots, t));
       TRY(upload_ints(c, c->d_mask, rel));
-      blas_convert(lo, rlo, WMG_PREC_DOUBLE, r64, n, nrhs, c->d_mask, s);
+      blas_convert(lo, rlo, WMG_PREC_DOUBLE, r64, n, nslots, c->d_mask, s);
       bool changed = false;
-      for (int r = 0; r < nrhs; ++r) {
+      for (int r = 0; r < nslots; ++r) {
         if (!rel[r]) continue;
         const double tr = std::sqrt(std::max(t[r], 0.0));
         tres[r] = tr / bnorm[r];
         ref[r] = tr;
-        if (info) info[r].reliable_updates += 1;
+        relups[r] += 1;
         if (tr <= tol * bnorm[r]) {
-          conv[r] = 1;
-          active[r] = 0;
+          TRY(finish(r, true));
           changed = true;
-        } else if (iters[r] >= c->prm.max_iter) {
-          active[r] = 0;
+        } else if (iters[r] >= c->prm.max_iter || !(tr == tr)) {
+          TRY(finish(r, false));
           changed = true;
         }
       }
       if (changed) {
         TRY(upload_ints(c, c->d_active, active));
-        c->n_active = 0;
-        for (int r = 0; r < nrhs; ++r) c->n_active += active[r];
+        count_active();
       }
     }
     if (k == m) k = 0;
-  }
-  CU(c, cudaStreamSynchronize(s));
-  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  bool allconv = true;
-  for (int r = 0; r < nrhs; ++r) {
-    allconv = allconv && conv[r];
-    if (info) {
-      info[r].iters = iters[r];
-      info[r].converged = conv[r];
-      info[r].true_resid = bb[r] > 0.0 ? tres[r] : 0.0;
-      info[r].seconds = secs;
+    if (k != 0) {
+      bool any = false;
+      for (int r = 0; r < nslots; ++r) any = any || active[r];
+      if (!any) k = 0;  // everything finished mid-cycle: go back to admission
     }
   }
-  return allconv ? WMG_OK : WMG_ENOCONV;
+  CU(c, cudaStreamSynchronize(s));
+  return WMG_OK;
+}
+
+// All right-hand sides of one call, admitted at once; results unpacked into x (canonical).
+namespace {
+struct BatchSource : SlotSource {
+  const double* b;  // canonical device
+  double* x;        // canonical device
+  const double* masses;
+  int nrhs;
+  bool given = false;
+  wmg_info* info;
+  bool allconv = true;
+  void admit(wmg_ctx* c, const std::vector<int>& free_slots, std::vector<Admission>& out) override {
+    if (given) return;
+    given = true;
+    for (int r = 0; r < nrhs; ++r)
+      out.push_back({free_slots[r], b + (size_t)c->fine.V * 24 * r, masses ? masses[r] : c->mass});
+  }
+  wmg_status finish(wmg_ctx* c, int slot, const void* x64, const wmg_info& inf) override {
+    unpack_spinor(WMG_PREC_DOUBLE, x64, x + (size_t)c->fine.V * 24 * slot, c->fine.V, 1, c->stream);
+    if (info) info[slot] = inf;
+    allconv = allconv && inf.converged;
+    return check(c, "unpack");
+  }
+};
+}  // namespace
+
+wmg_status fgcr(wmg_ctx* c, const double* b_canon, double* x_canon, int nrhs, const double* masses, wmg_info* info,
+                bool use_mg) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (info) std::memset(info, 0, sizeof(wmg_info) * nrhs);
+  BatchSource src;
+  src.b = b_canon;
+  src.x = x_canon;
+  src.masses = masses;
+  src.nrhs = nrhs;
+  src.info = info;
+  TRY(fgcr_engine(c, nrhs, src, use_mg));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info)
+    for (int r = 0; r < nrhs; ++r) info[r].seconds = secs;
+  return src.allconv ? WMG_OK : WMG_ENOCONV;
 }
 
 }  // namespace wmg

@@ -1,6 +1,7 @@
 // Internal host driver interface (solver.cu) used by the C ABI (api.cu).
 #pragma once
 #include <string>
+#include <vector>
 
 #include "ctx.h"
 
@@ -23,6 +24,22 @@ wmg_status build_from_vectors(wmg_ctx* c, int l, int prec, const void* vecs);
 wmg_status setup_level(wmg_ctx* c, int l, void* vecs);
 void prof_flush(wmg_ctx* c);
 wmg_status clear_graphs(wmg_ctx* c);
-wmg_status fgcr(wmg_ctx* c, const void* b64, void* x64, int nrhs, const double* masses, wmg_info* info, bool use_mg);
+// a source of right-hand sides for the outer-solver slot engine
+struct Admission {
+  int slot;
+  const double* b_canon_dev;  // one canonical fine spinor on the device
+  double mass;
+};
+struct SlotSource {
+  virtual ~SlotSource() {}
+  // fill some of the free slots (called at restart boundaries)
+  virtual void admit(wmg_ctx* c, const std::vector<int>& free_slots, std::vector<Admission>& out) = 0;
+  // slot finished: its FP64 native solution and its info
+  virtual wmg_status finish(wmg_ctx* c, int slot, const void* x64_native, const wmg_info& info) = 0;
+};
+wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg);
+// b_canon, x_canon: canonical device spinors, nrhs <= 64
+wmg_status fgcr(wmg_ctx* c, const double* b_canon, double* x_canon, int nrhs, const double* masses, wmg_info* info,
+                bool use_mg);
 
 }  // namespace wmg

@@ -307,11 +307,11 @@ template <typename R, int RC>
 static void launch_restrict_fine(const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
                                  const int* active, cudaStream_t s) {
   const size_t smem = (size_t)RC * 12 * bk.bs * sizeof(cpx<R>);
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {
     cudaFuncSetAttribute(k_restrict_fine<R, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   dim3 g(bk.coarse.V, (nrhs + RC - 1) / RC);
   k_restrict_fine<R, RC><<<g, 128, smem, s>>>(P, bk, in, out, nrhs, active);
 }
@@ -355,11 +355,11 @@ template <typename R, int RC>
 static void launch_restrict_coarse(const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
                                    const int* active, cudaStream_t s) {
   const size_t smem = (size_t)RC * bk.bs * bk.nf * sizeof(cpx<R>);
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {
     cudaFuncSetAttribute(k_restrict_coarse<R, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   dim3 g(bk.coarse.V, (nrhs + RC - 1) / RC);
   k_restrict_coarse<R, RC><<<g, 128, smem, s>>>(P, bk, in, out, nrhs, active);
 }

@@ -99,6 +99,12 @@ def load():
         "wmg_prolong": (i, [vp, i, i, vp, vp, i]),
         "wmg_apply_coarse": (i, [vp, i, i, i, vp, vp, i]),
         "wmg_residual_noalloc": (i, [vp, i, vp, vp, vp, vp, i]),
+        "wmg_server_create": (i, [P(vp), ctypes.c_size_t]),
+        "wmg_server_add_field": (i, [vp, vp, i, P(i)]),
+        "wmg_server_submit": (i, [vp, i, d, vp, vp, i, P(ctypes.c_longlong)]),
+        "wmg_server_poll": (i, [vp, ctypes.c_longlong, P(i)]),
+        "wmg_server_wait": (i, [vp, ctypes.c_longlong, P(Info), P(d)]),
+        "wmg_server_destroy": (i, [vp]),
         "wmg_profile_enable": (i, [vp, i]),
         "wmg_launch_count": (i, [P(ctypes.c_longlong)]),
         "wmg_profile_get": (i, [vp, i, P(d), P(ctypes.c_longlong), P(d), P(d)]),
@@ -271,3 +277,60 @@ class Context:
     def apply_coarse(self, level, prec, inp, out, nrhs, dagger=False):
         return self._check(self.lib.wmg_apply_coarse(self.h, int(level), prec, int(bool(dagger)), _ptr(inp),
                                                      _ptr(out), int(nrhs)))
+
+
+class Server:
+    """Continuous-batching solve server over resident fields (contexts handed over with add_field)."""
+
+    def __init__(self, hbm_budget_bytes=200 << 30):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        st = self.lib.wmg_server_create(ctypes.byref(h), ctypes.c_size_t(int(hbm_budget_bytes)))
+        if st != OK:
+            raise WmgError(st, "wmg_server_create")
+        self.h = h
+        self.fields = []
+        self.pending = {}
+
+    def add_field(self, ctx, nslots):
+        fid = ctypes.c_int()
+        st = self.lib.wmg_server_add_field(self.h, ctx.h, int(nslots), ctypes.byref(fid))
+        if st != OK:
+            raise WmgError(st, self.lib.wmg_strerror(st).decode() + ": " + (self.lib.wmg_last_error(ctx.h) or b"").decode())
+        self.fields.append(ctx)           # keep the context alive while served
+        return fid.value
+
+    def submit(self, field, mass, b, x):
+        """b, x: canonical host arrays (nrhs, T, Z, Y, X, 12) complex128, kept alive until wait()."""
+        assert b.flags["C_CONTIGUOUS"] and x.flags["C_CONTIGUOUS"] and b.dtype == np.complex128
+        t = ctypes.c_longlong()
+        st = self.lib.wmg_server_submit(self.h, int(field), float(mass), _ptr(b), _ptr(x), int(b.shape[0]),
+                                        ctypes.byref(t))
+        if st != OK:
+            raise WmgError(st, "wmg_server_submit")
+        self.pending[t.value] = (b, x)
+        return t.value
+
+    def poll(self, ticket):
+        d = ctypes.c_int()
+        self.lib.wmg_server_poll(self.h, ctypes.c_longlong(ticket), ctypes.byref(d))
+        return bool(d.value)
+
+    def wait(self, ticket):
+        b, x = self.pending.pop(ticket)
+        info = (Info * b.shape[0])()
+        lat = ctypes.c_double()
+        st = self.lib.wmg_server_wait(self.h, ctypes.c_longlong(ticket), info, ctypes.byref(lat))
+        return st, [i.as_dict() for i in info], lat.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.wmg_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

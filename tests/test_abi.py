@@ -35,3 +35,15 @@ def test_invalid_arguments_rejected_without_device_work(lib):
     assert lib.wmg_destroy(None) == wmg.EINVAL
     assert lib.wmg_set_mass(None, 0.1) == wmg.EINVAL
     assert lib.wmg_apply_D(None, 0, None, None, 1) == wmg.EINVAL
+
+
+def test_server_host_side_argument_checks(lib):
+    h = ctypes.c_void_p()
+    assert lib.wmg_server_create(ctypes.byref(h), 1 << 30) == wmg.OK
+    t = ctypes.c_longlong()
+    fid = ctypes.c_int()
+    assert lib.wmg_server_add_field(h, None, 4, ctypes.byref(fid)) == wmg.EINVAL
+    assert lib.wmg_server_submit(h, 0, 0.1, None, None, 1, ctypes.byref(t)) == wmg.EINVAL
+    d = ctypes.c_int()
+    assert lib.wmg_server_poll(h, 12345, ctypes.byref(d)) == wmg.EINVAL
+    assert lib.wmg_server_destroy(h) == wmg.OK
