@@ -5,17 +5,19 @@ TEST INFRASTRUCTURE ONLY (see the package header).
 
 The workloads are specified by the ratio r = lambda_min(D^dag D) / lambda_min^free, where
 the free periodic operator at mass m has lambda_min^free = m^2 (its p = 0 mode has
-eigenvalue m, from the closed form in oracle/dirac.py).  lambda_min(D^dag D) is found by
-inverse iteration, v <- (D^dag D)^-1 v = D^-1 gamma_5 D^-1 gamma_5 v (gamma_5-hermiticity,
-Sec. 3), with each D^-1 an oracle MG-GCR solve; the mass is then located from the heavy
-side (m above the critical mass) with the model sqrt(lambda_min) = s (m - m_c), refitted
-from the two most recent evaluations (a secant step on sqrt(lambda_min)), until the ratio
-is within `rtol` of r.  The hierarchy is built once near the target and moved to other
-masses by the exact coarse shift D^(m) = D^(m0) + (m - m0) I (P^dag P = 1).
+eigenvalue m, from the closed form in oracle/dirac.py).  lambda_min(D^dag D) is the
+largest eigenvalue of (D^dag D)^-1 = D^-1 gamma_5 D^-1 gamma_5 (gamma_5-hermiticity,
+Sec. 3), found by Lanczos (scipy's ARPACK eigsh) with each D^-1 an oracle MG-GCR solve
+whose coarsest level is solved by a sparse LU factorisation (an exact coarse solve; the
+mass search only needs accurate D^-1, not the paper's CGNR).  The mass is located from the
+heavy side (m above the critical mass) with the model sqrt(lambda_min) = s (m - m_c),
+refitted from the two evaluations closest to the target (a secant step on
+sqrt(lambda_min)), until the ratio is within `rtol` of r.  The hierarchy is built once near
+the first target and moved to other masses by the exact coarse shift
+D^(m) = D^(m0) + (m - m0) I (P^dag P = 1).
 
-Pinned by tests/test_oracle_masses.py: on the free field the finder reproduces
-lambda_min = m^2 (ratio 1), and on a tiny lattice inverse iteration agrees with the dense
-smallest eigenvalue of D^dag D.
+Pinned by tests/test_oracle_masses.py: on the free field lambda_min = m^2 (ratio 1), and on
+a tiny lattice the Lanczos value agrees with the dense smallest eigenvalue of D^dag D.
 """
 from __future__ import annotations
 
@@ -23,6 +25,8 @@ import json
 import time
 
 import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as sla
 
 from . import mg, solvers
 
@@ -33,43 +37,72 @@ def _g5(v):
     return out
 
 
+def stencil_sparse(A):
+    """The coarse stencil operator as a scipy CSC matrix (rows site*n + i, columns nb*n + j)."""
+    X, Y, Z, T = A.dims
+    V, n = X * Y * Z * T, A.n
+    Df = A.D.reshape(V, mg.NSLOT, n, n)
+    v = np.arange(V)
+    crd = [v % X, (v // X) % Y, (v // (X * Y)) % Z, v // (X * Y * Z)]
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    rows, cols, vals = [], [], []
+    for k in range(mg.NSLOT):
+        c = [a.copy() for a in crd]
+        if k > 0:
+            mu, sg = (k - 1) // 2, (1 if (k - 1) % 2 == 0 else -1)
+            c[mu] = (c[mu] + sg) % (X, Y, Z, T)[mu]
+        nb = c[0] + X * (c[1] + Y * (c[2] + Z * c[3]))
+        rows.append((v[:, None, None] * n + ii[None]).ravel())
+        cols.append((nb[:, None, None] * n + jj[None]).ravel())
+        vals.append(Df[:, k].ravel())
+    return sp.csc_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(V * n, V * n))
+
+
+def direct_coarse_solver(A):
+    """Exact coarsest solve by sparse LU (used by the mass search only)."""
+    lu = sla.splu(stencil_sparse(A))
+    return lambda _A, b: lu.solve(b.ravel()).reshape(b.shape)
+
+
 def shifted_hierarchy(H, m):
     """The hierarchy H (built at some mass m0) moved to mass m by the exact diagonal shift."""
     op0 = H.ops[0]
     dm = m - op0.m
     ops = [mg.WilsonOp(op0.U, m)] + [A.shifted(dm) for A in H.ops[1:]]
-    return solvers.Hierarchy(ops, H.P, H.blocks, H.params)
+    Hm = solvers.Hierarchy(ops, H.P, H.blocks, H.params)
+    Hm.coarse_solver = direct_coarse_solver(ops[-1])
+    return Hm
 
 
-def lambda_min(H, v0, tol=1e-8, rel=1e-4, max_steps=12, log=None):
-    """Smallest eigenvalue of D^dag D (D = H.ops[0]) by inverse iteration with MG-GCR solves.
-    Returns (lambda, eigenvector estimate)."""
-    D = H.ops[0]
-    v = v0 / solvers.norm(v0)
-    lam_old = np.inf
-    lam = np.inf
-    for step in range(max_steps):
+def lambda_min(H, v0, tol=1e-10, eig_tol=1e-4, log=None):
+    """Smallest eigenvalue of D^dag D (D = H.ops[0]) and its eigenvector, by Lanczos on
+    (D^dag D)^-1 applied with MG-GCR solves."""
+    shape = v0.shape
+    nsolve = [0]
+
+    def matvec(x):
+        v = x.reshape(shape)
         y, _ = solvers.mg_solve(H, _g5(v), tol)
         w, _ = solvers.mg_solve(H, _g5(y), tol)
-        v = w / solvers.norm(w)
-        Dv = D.apply(v)
-        lam = float(np.vdot(Dv, Dv).real)
-        if log:
-            log(f"    inverse iteration {step}: lambda = {lam:.6e}")
-        if abs(lam_old - lam) <= rel * lam:
-            break
-        lam_old = lam
-    return lam, v
+        nsolve[0] += 2
+        return w.ravel()
+
+    n = v0.size
+    Op = sla.LinearOperator((n, n), matvec=matvec, dtype=np.complex128)
+    vals, vecs = sla.eigsh(Op, k=1, which="LA", v0=v0.ravel(), tol=eig_tol, ncv=8)
+    lam = 1.0 / float(vals[0])
+    if log:
+        log(f"    Lanczos: lambda_min = {lam:.6e} ({nsolve[0]} MG solves)")
+    return lam, vecs[:, 0].reshape(shape)
 
 
 def find_masses(U, ratios, block=(4, 4, 4, 4), nvec=24, m_start=0.0, m_step=0.2, seed=7, rtol=0.05,
-                setup_passes=5, coarse_tol=1e-6, log=print, max_evals=12):
+                setup_passes=5, log=print, max_evals=12):
     """Masses m (heavier than critical) with lambda_min(D^dag D) = r m^2 for each r in ratios."""
     from synth import gaussian_spinors, setup_starts
 
     T, Z, Y, X = U.shape[:4]
     dims = (X, Y, Z, T)
-    params = solvers.CycleParams(coarse_tol=coarse_tol)
     v = gaussian_spinors(dims, 1, seed + 100)[0]
     evals = []  # (m, lambda)
     H = None
@@ -78,9 +111,10 @@ def find_masses(U, ratios, block=(4, 4, 4, 4), nvec=24, m_start=0.0, m_step=0.2,
         t = time.time()
         op = mg.WilsonOp(U, m)
         starts = setup_starts(dims, nvec, seed)
-        Hn = solvers.adaptive_setup(op, [block], [starts], passes=setup_passes, params=params)
+        P, Ac, _ = solvers.setup_level(op, block, starts, passes=setup_passes,
+                                       coarse_solver_factory=direct_coarse_solver)
         log(f"  setup at m = {m:.6f}: {time.time() - t:.1f} s")
-        return Hn
+        return solvers.Hierarchy([op, Ac], [P], [block])
 
     def evaluate(m):
         nonlocal v
@@ -93,27 +127,19 @@ def find_masses(U, ratios, block=(4, 4, 4, 4), nvec=24, m_start=0.0, m_step=0.2,
     H = build(m_start)
     evaluate(m_start)
     evaluate(m_start - m_step)
-    rebuilt = False
     out = {}
     for r in sorted(ratios, reverse=True):
         for _ in range(max_evals):
-            (m1, l1), (m2, l2) = sorted(evals, key=lambda e: abs(e[1] / e[0] ** 2 - r) / r)[:2]
-            s = (np.sqrt(l1) - np.sqrt(l2)) / (m1 - m2)
-            mc = m1 - np.sqrt(l1) / s
-            # sqrt(r) |m| = s (m - m_c), m on the heavy side of m_c
-            cands = [s * mc / (s - np.sqrt(r)), s * mc / (s + np.sqrt(r))]
-            cands = [c for c in cands if c > mc]
-            m = min(cands, key=lambda c: abs(c - m1))
             close = [e for e in evals if abs(e[1] / e[0] ** 2 - r) <= rtol * r]
             if close:
                 out[r] = close[0][0]
                 break
-            if not rebuilt and r == max(ratios):
-                pass
-            if not rebuilt and abs(m - mc) < 0.05:
-                H = build(m)
-                rebuilt = True
-            evaluate(m)
+            (m1, l1), (m2, l2) = sorted(evals, key=lambda e: abs(np.log(e[1] / e[0] ** 2 / r)))[:2]
+            s = (np.sqrt(l1) - np.sqrt(l2)) / (m1 - m2)
+            mc = m1 - np.sqrt(l1) / s
+            # sqrt(r) |m| = s (m - m_c) on the heavy side of m_c
+            cands = [c for c in (s * mc / (s - np.sqrt(r)), s * mc / (s + np.sqrt(r))) if c > mc]
+            evaluate(min(cands, key=lambda c: abs(c - m1)))
         else:
             raise RuntimeError(f"mass search for ratio {r} did not converge: {evals}")
     return out, evals

@@ -110,6 +110,7 @@ class Hierarchy:
     blocks: list                # block shape used to coarsen level l
     params: CycleParams = field(default_factory=CycleParams)
     coarse_iters: list = field(default_factory=list)
+    coarse_solver: object = None   # optional callable(A, b) replacing CGNR on the coarsest level
 
     @property
     def nlevels(self):
@@ -121,6 +122,8 @@ def cycle(H, level, r):
     p = H.params
     A = H.ops[level]
     if level == H.nlevels - 1:
+        if H.coarse_solver is not None:
+            return H.coarse_solver(A, r)
         x, it = cgnr(A, r, p.coarse_tol, p.coarse_maxit)
         H.coarse_iters.append(it)
         return x
@@ -192,7 +195,7 @@ def _normalise(v):
     return v / norm(v)
 
 
-def setup_level(op, block, starts, passes=5, relax=20, params=None, history=None):
+def setup_level(op, block, starts, passes=5, relax=20, params=None, history=None, coarse_solver_factory=None):
     """Adaptive near-null vectors for one level (2-level cycle on op).
 
     Returns (P, coarse StencilOp, final vectors).  `history`, if a list, receives per
@@ -210,6 +213,8 @@ def setup_level(op, block, starts, passes=5, relax=20, params=None, history=None
     Ac = mg.galerkin(op, P, block)
     for _ in range(passes - 1):
         H = Hierarchy([op, Ac], [P], [block], params)
+        if coarse_solver_factory is not None:
+            H.coarse_solver = coarse_solver_factory(Ac)
         new = []
         for v in psi:
             new.append(_normalise(cycle(H, 0, v)))
