@@ -209,16 +209,19 @@ def run_gpu(args, w):
     params = wmg.default_params(nvec=[w["nvec"]], block=[w["block"]], prec_sloppy=wmg.PREC_SINGLE,
                                 seed=1000 + rank)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    record = {"iters": [], "true_resid": []}
+    record = {"iters": [], "true_resid": [], "phases": []}
 
     def step(host=False):
+        t0 = time.perf_counter()
         if host:
             ctx.load_gauge(U)
         else:
             ctx.load_gauge(U_dev)
         ctx.set_mass(m_light)
         ctx.setup(params)
+        ph = {"setup_s": time.perf_counter() - t0, "solve_s": []}
         for m in masses:
+            t1 = time.perf_counter()
             ctx.set_mass(m)
             if host:
                 xh = np.zeros_like(b)
@@ -227,8 +230,10 @@ def run_gpu(args, w):
                 st, info = ctx.solve(b_dev, x_dev, nrhs)
             if st != wmg.OK:
                 raise RuntimeError(f"solve at m={m} did not converge: {info}")
+            ph["solve_s"].append(time.perf_counter() - t1)
             record["iters"].append([i["iters"] for i in info])
             record["true_resid"].append(max(i["true_resid"] for i in info))
+        record["phases"].append(ph)
 
     def barrier():
         if dist:
@@ -240,6 +245,7 @@ def run_gpu(args, w):
     # timed region: device time of each step (CUDA events on the legacy stream the library uses)
     record["iters"].clear()
     record["true_resid"].clear()
+    record["phases"].clear()
     clocks = Clocks(local)
     times = []
     l0 = wmg.launch_count()
@@ -262,6 +268,9 @@ def run_gpu(args, w):
         t_step = float(tt.item())
     iters = record["iters"]
     resid = max(record["true_resid"])
+    phases = {"setup_s": statistics.mean(p["setup_s"] for p in record["phases"]),
+              "solve_s_per_mass": [statistics.mean(p["solve_s"][i] for p in record["phases"])
+                                   for i in range(len(masses))]}
 
     # end to end through the host-buffer entry points
     e2e = []
@@ -359,6 +368,7 @@ def run_gpu(args, w):
                    "l2": "flushed (256 MB write) between timed steps", "parallelism": "replicas" if world > 1 else "1 GPU"},
         "solves_per_s": world * len(masses) * nrhs / t_step,
         "iters_per_mass": [float(np.mean(i)) for i in iters[:len(masses)]],
+        "phases": phases,
         "max_true_resid": resid,
         "plain_fp64": plain,
         "speedup_vs_plain": (plain["s"] / t_step) if plain else None,

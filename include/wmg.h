@@ -78,7 +78,8 @@ typedef enum {
 
 typedef enum {
   WMG_PREC_DOUBLE = 0, /* FP64 storage and arithmetic */
-  WMG_PREC_SINGLE = 1  /* FP32 storage and arithmetic */
+  WMG_PREC_SINGLE = 1, /* FP32 storage and arithmetic */
+  WMG_PREC_HALF = 2    /* wmg_apply_coarse only: FP16 operator on tensor cores, FP32 vectors */
 } wmg_prec;
 
 #define WMG_MAX_LEVELS 3
@@ -100,7 +101,9 @@ typedef struct {
   int max_iter;                      /* outer iteration cap (cycle applications)     */
   int prec_sloppy;                   /* precision of the cycle, the hierarchy and the
                                         inner Krylov vectors (WMG_PREC_*)            */
-  int pad_;
+  int coarse_tc;                     /* with prec_sloppy = SINGLE: apply the coarse
+                                        stencils with FP16 tensor-core MMA (FP32
+                                        accumulation) where 2N is 16, 32, 48 or 64     */
   double reliable_delta;             /* FP64 reliable update when the iterated
                                         residual fell by this factor                */
   uint64_t seed;                     /* seed of the setup's Gaussian starts when no
@@ -190,7 +193,8 @@ wmg_status wmg_restrict(wmg_ctx* ctx, int level, int prec, const void* fine_dev,
 /* fine = P coarse (Sec. 2). */
 wmg_status wmg_prolong(wmg_ctx* ctx, int level, int prec, const void* coarse_dev, void* fine_dev, int nrhs);
 /* out = D^ in on coarse lattice `level` >= 1 (Sec. 2 Galerkin operator), or
- * sigma_3 D^ sigma_3 = D^dag (Sec. 3) if dagger != 0. */
+ * sigma_3 D^ sigma_3 = D^dag (Sec. 3) if dagger != 0.  prec = WMG_PREC_HALF applies the FP16
+ * tensor-core copy of the operator to FP32 vectors (requires coarse_tc and 2N in {16..64}). */
 wmg_status wmg_apply_coarse(wmg_ctx* ctx, int level, int prec, int dagger, const void* in_dev, void* out_dev,
                             int nrhs);
 

@@ -32,6 +32,8 @@ void free_hierarchy(wmg_ctx* c) {
   for (int l = 0; l < WMG_MAX_LEVELS; ++l)
     for (int p = 0; p < 2; ++p) {
       if (c->L[l].A[p]) cudaFree(c->L[l].A[p]);
+      if (p == 0 && c->L[l].A16) cudaFree(c->L[l].A16), c->L[l].A16 = nullptr;
+      if (p == 0 && c->L[l].sA) cudaFree(c->L[l].sA), c->L[l].sA = nullptr;
       if (c->L[l].P[p]) cudaFree(c->L[l].P[p]);
       c->L[l].A[p] = c->L[l].P[p] = nullptr;
     }
@@ -107,6 +109,7 @@ void wmg_default_params(wmg_params* p) {
   p->coarse_maxit = 2000;
   p->max_iter = 1000;
   p->prec_sloppy = WMG_PREC_SINGLE;
+  p->coarse_tc = 1;
   p->reliable_delta = 0.01;
   p->seed = 20091212ULL;
 }
@@ -156,7 +159,7 @@ wmg_status wmg_create(wmg_ctx** out, const int dims[4], void* stream) {
   for (int l = 1; l < WMG_MAX_LEVELS; ++l) al((void**)&c->d_shift[l], kMaxRhs * sizeof(double));
   al((void**)&c->d_active, kMaxRhs * sizeof(int));
   al((void**)&c->d_mask, kMaxRhs * sizeof(int));
-  al((void**)&c->d_flag, sizeof(int));
+  al((void**)&c->d_flag, 4 * sizeof(int));
   al((void**)&c->d_cgint, 2 * kMaxRhs * sizeof(int));
   al((void**)&c->red_counter, 4 * kMaxRhs * sizeof(unsigned));
   al((void**)&c->res, (size_t)24 * kMaxRhs * 16 * sizeof(double));
@@ -412,12 +415,18 @@ wmg_status wmg_prolong(wmg_ctx* c, int level, int prec, const void* coarse, void
 }
 
 wmg_status wmg_apply_coarse(wmg_ctx* c, int level, int prec, int dagger, const void* in, void* out, int nrhs) {
-  if (!c || !in || !out || nrhs < 1 || nrhs > kMaxRhs || !prec_ok(prec) || in == out) return WMG_EINVAL;
+  if (!c || !in || !out || nrhs < 1 || nrhs > kMaxRhs || in == out) return WMG_EINVAL;
+  if (!prec_ok(prec) && prec != WMG_PREC_HALF) return WMG_EINVAL;
   if (level < 1 || level >= c->nlev || !c->L[level].A[0]) return WMG_ESTATE;
+  if (prec == WMG_PREC_HALF && !c->L[level].A16) return WMG_ESTATE;
   TRY(set_rhs_scalars(c, nullptr, nrhs));
   const LevelData& L = c->L[level];
-  coarse_apply(prec, L.A[prec], L.g, L.ndof, in, out, nrhs, c->d_shift[level], dagger != 0, nullptr, nullptr,
-               c->stream);
+  if (prec == WMG_PREC_HALF)
+    coarse_apply_mma(L.A16, L.sA, L.g, L.ndof, in, out, nrhs, c->d_shift[level], dagger != 0, nullptr, nullptr,
+                     c->stream);
+  else
+    coarse_apply(prec, L.A[prec], L.g, L.ndof, in, out, nrhs, c->d_shift[level], dagger != 0, nullptr, nullptr,
+                 c->stream);
   return check(c, "apply_coarse");
 }
 
@@ -434,7 +443,7 @@ wmg_status wmg_profile_enable(wmg_ctx* c, int on) {
 
 wmg_status wmg_launch_count(long long* n) {
   if (!n) return WMG_EINVAL;
-  *n = launch_count();
+  *n = launch_count() + graph_launch_count();
   return WMG_OK;
 }
 

@@ -48,19 +48,23 @@ __global__ void __launch_bounds__(256) k_coarse_apply(const void* __restrict__ A
   const cpx<R>* A = reinterpret_cast<const cpx<R>*>(A_) + (size_t)v * 9 * n * n;
   const cpx<R>* in = reinterpret_cast<const cpx<R>*>(in_);
   cpx<R>* out = reinterpret_cast<cpx<R>*>(out_);
-  int c[4];
-  site_coords(g, v, c);
-  for (int i = threadIdx.x; i < 9 * n * NR; i += blockDim.x) {
-    const int rr = i % NR, kj = i / NR, k = kj / n, j = kj % n;
-    const int r = r0 + rr;
-    cpx<R> x{R(0), R(0)};
-    if (r < nrhs) {
-      const int nb = stencil_neighbour(g, v, c, k);
-      x = in[((size_t)r * g.V + nb) * n + j];
-      if (dagger && j >= N) x = -x;
-    }
-    xs[i] = x;
+  __shared__ int nbs[9];
+  if (threadIdx.x < 9) {
+    int c[4];
+    site_coords(g, v, c);
+    nbs[threadIdx.x] = stencil_neighbour(g, v, c, threadIdx.x);
   }
+  __syncthreads();
+  for (int k = 0; k < 9; ++k)
+    for (int i = threadIdx.x; i < n * NR; i += blockDim.x) {
+      const int j = i / NR, rr = i % NR, r = r0 + rr;
+      cpx<R> x{R(0), R(0)};
+      if (r < nrhs) {
+        x = in[((size_t)r * g.V + nbs[k]) * n + j];
+        if (dagger && j >= N) x = -x;
+      }
+      xs[(size_t)(k * n + j) * NR + rr] = x;
+    }
   __syncthreads();
   const int row = threadIdx.x % n, ks = threadIdx.x / n;
   cpx<R> acc[NR];

@@ -1,0 +1,265 @@
+// Tensor-core application of the coarse stencil (Sec. 2 Galerkin operator) to many
+// right-hand sides: per coarse site the 9 n x n complex blocks form one n x 9n complex matrix
+// A that multiplies the 9n x R matrix X of gathered neighbour values.  In real arithmetic,
+//     [Ar; Ai] (2n x 9n)  x  [Xr | Xi] (9n x 2R)  =  [[Ar Xr, Ar Xi], [Ai Xr, Ai Xi]],
+// and Yr = Ar Xr - Ai Xi, Yi = Ar Xi + Ai Xr.  One warp owns the row tile of Ar and the
+// same row tile of Ai, and the right-hand sides are laid out as column tiles
+// [Xr 0..7 | Xi 0..7 | Xr 8..15 | Xi 8..15], so every thread holds all four products of its
+// output elements in its own accumulators.
+//
+// Operands are FP16 with FP32 accumulation (mma.sync m16n8k16): A is stored once per
+// setup in FP16 scaled by a per-site factor s_A (max |Re|, |Im| of the site's blocks) and
+// pre-arranged in fragment order, so each lane loads one 16-byte word per 16 x 16 tile; X
+// is converted in shared memory with a per-(site, rhs) factor s_X.  The result is
+// rescaled by s_A s_X.  Relative error is about 1e-3 (FP16 operands), enough for the coarse
+// solve of a preconditioner.
+#include <cuda_fp16.h>
+
+#include "kernels.h"
+
+namespace wmg {
+
+namespace {
+
+constexpr int kKPad = 8;  // halves of padding per staged column (bank-conflict free B loads)
+
+WMG_D uint32_t pack_half2(float lo, float hi) {
+  __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+WMG_D void mma16816(float d[4], const uint4& a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
+}
+
+}  // namespace
+
+// Per-site scale: max over the site's 9 n x n blocks of |Re| and |Im|.
+template <typename R>
+__global__ void k_stencil_site_scale(const cpx<R>* __restrict__ A, int n, float* __restrict__ scale) {
+  const int v = blockIdx.x;
+  const size_t cnt = (size_t)9 * n * n;
+  float m = 0.f;
+  for (size_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const cpx<R> a = A[(size_t)v * cnt + i];
+    m = fmaxf(m, fmaxf(fabsf((float)a.re), fabsf((float)a.im)));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ float sm[32];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, sm[w]);
+    scale[v] = t > 0.f ? t : 1.f;
+  }
+}
+
+// Fragment-order FP16 copy of the stencil: [site][plane][mtile][kstep][lane] uint4, where
+// plane 0 = Re, 1 = Im, and the 16 x 16 tile (rows 16 mtile.., k 16 kstep..) of the real
+// n x 9n matrix of that plane is held as the m16n8k16 A fragment of each lane.
+template <typename R>
+__global__ void k_stencil_to_mma(const cpx<R>* __restrict__ A, int n, const float* __restrict__ scale,
+                                 uint4* __restrict__ out, int Vc) {
+  const int mt = n / 16, ks = 9 * n / 16;
+  const size_t per_site = (size_t)2 * mt * ks * 32;
+  const size_t total = per_site * Vc;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int lane = (int)(idx % 32);
+    size_t t = idx / 32;
+    const int kk = (int)(t % ks);
+    t /= ks;
+    const int m = (int)(t % mt);
+    t /= mt;
+    const int plane = (int)(t % 2);
+    const int v = (int)(t / 2);
+    const float inv = 1.f / scale[v];
+    const int g = lane >> 2, q = lane & 3;
+    auto val = [&](int row, int k) -> float {  // row of the n x 9n block matrix, k = slot * n + col
+      const cpx<R> a = A[(((size_t)v * 9 + k / n) * n + (k % n)) * n + row];
+      return (float)(plane == 0 ? a.re : a.im) * inv;
+    };
+    const int r0 = 16 * m + g, r1 = r0 + 8, c0 = 16 * kk + 2 * q, c1 = c0 + 8;
+    uint4 w;
+    w.x = pack_half2(val(r0, c0), val(r0, c0 + 1));
+    w.y = pack_half2(val(r1, c0), val(r1, c0 + 1));
+    w.z = pack_half2(val(r0, c1), val(r0, c1 + 1));
+    w.w = pack_half2(val(r1, c1), val(r1, c1 + 1));
+    out[idx] = w;
+  }
+}
+
+// y = A x (+ shift x), optionally sigma_3 A sigma_3 x, for a chunk of up to 8 NT right-hand
+// sides per CTA (grid.y chunks).  One CTA per coarse site, one warp per 16-row tile.
+template <int NT>
+__global__ void __launch_bounds__(128) k_coarse_apply_mma(const uint4* __restrict__ A16, const float* __restrict__ sA,
+                                                          Geom g, int n, const cf* __restrict__ in, cf* __restrict__ out,
+                                                          int nrhs, const double* __restrict__ shift, int dagger,
+                                                          const int* __restrict__ active, RedBuf rb, int want_norm) {
+  constexpr int R = 8 * NT;          // right-hand sides per chunk
+  constexpr int COLS = 2 * R;        // Xr / Xi columns
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int K = 9 * n, KP = K + kKPad;
+  __half* xb = reinterpret_cast<__half*>(smraw);                                   // [COLS][KP]
+  float* xmax = reinterpret_cast<float*>(smraw + (size_t)COLS * KP * sizeof(__half));  // [R]
+  const int v = blockIdx.x, r0 = blockIdx.y * R;
+  const int N = n / 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  __shared__ int nbs[9];
+  if (threadIdx.x < 9) {
+    int c[4];
+    site_coords(g, v, c);
+    const int k = threadIdx.x;
+    nbs[k] = k == 0 ? v : neighbour(g, v, c, (k - 1) >> 1, ((k - 1) & 1) ? -1 : +1);
+  }
+  __syncthreads();
+  // one warp per right-hand side: max |Re|, |Im| of its 9 gathered neighbour vectors, then the
+  // scaled FP16 copy in column layout [Xr 0..7 | Xi 0..7 | Xr 8..15 | Xi 8..15]
+  for (int rr = warp; rr < R; rr += nwarp) {
+    const int r = r0 + rr;
+    const int blk = rr >> 3, cc = rr & 7;
+    __half* colr = xb + (size_t)(blk * 16 + cc) * KP;
+    __half* coli = xb + (size_t)(blk * 16 + 8 + cc) * KP;
+    if (r >= nrhs) {
+      for (int kk = lane; kk < K; kk += 32) colr[kk] = coli[kk] = __float2half_rn(0.f);
+      if (lane == 0) xmax[rr] = 0.f;
+      continue;
+    }
+    float m = 0.f;
+    for (int k = 0; k < 9; ++k) {
+      const cf* src = in + ((size_t)r * g.V + nbs[k]) * n;
+      for (int j = lane; j < n; j += 32) {
+        const cf x = src[j];
+        m = fmaxf(m, fmaxf(fabsf(x.re), fabsf(x.im)));
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) xmax[rr] = m;
+    const float inv = m > 0.f ? 1.f / m : 0.f;
+    for (int k = 0; k < 9; ++k) {
+      const cf* src = in + ((size_t)r * g.V + nbs[k]) * n;
+      for (int j = lane; j < n; j += 32) {
+        const cf x = src[j];
+        const float sg = (dagger && j >= N) ? -inv : inv;
+        colr[k * n + j] = __float2half_rn(x.re * sg);
+        coli[k * n + j] = __float2half_rn(x.im * sg);
+      }
+    }
+  }
+  __syncthreads();
+  const int mt = n / 16, ksteps = K / 16;
+  const int gq = lane >> 2, q = lane & 3;
+  float acc[2][2 * NT][4];
+#pragma unroll
+  for (int p = 0; p < 2; ++p)
+#pragma unroll
+    for (int t = 0; t < 2 * NT; ++t)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[p][t][e] = 0.f;
+  if (warp < mt) {
+    const uint4* Ar = A16 + (((size_t)v * 2 + 0) * mt + warp) * ksteps * 32 + lane;
+    const uint4* Ai = A16 + (((size_t)v * 2 + 1) * mt + warp) * ksteps * 32 + lane;
+#pragma unroll 2
+    for (int k = 0; k < ksteps; ++k) {
+      const uint4 ar = __ldg(Ar + (size_t)k * 32), ai = __ldg(Ai + (size_t)k * 32);
+#pragma unroll
+      for (int t = 0; t < 2 * NT; ++t) {
+        const __half* col = xb + (size_t)(t * 8 + gq) * KP + 16 * k + 2 * q;
+        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(col);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(col + 8);
+        mma16816(acc[0][t], ar, b0, b1);
+        mma16816(acc[1][t], ai, b0, b1);
+      }
+    }
+  }
+  // epilogue: thread holds rows 16 warp + gq (+8), columns 2q + e of every tile
+  double nv[R];
+#pragma unroll
+  for (int rr = 0; rr < R; ++rr) nv[rr] = 0.0;
+  if (warp < mt) {
+    const float s_a = sA[v];
+#pragma unroll
+    for (int blk = 0; blk < NT; ++blk)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int row = 16 * warp + gq + (e >= 2 ? 8 : 0);
+        const int rr = blk * 8 + 2 * q + (e & 1);
+        const int r = r0 + rr;
+        if (r >= nrhs) continue;
+        // tiles 2 blk (Xr) and 2 blk + 1 (Xi); plane 0 = Ar, 1 = Ai
+        const float yr = acc[0][2 * blk][e] - acc[1][2 * blk + 1][e];
+        const float yi = acc[0][2 * blk + 1][e] + acc[1][2 * blk][e];
+        const float sc = s_a * xmax[rr] * ((dagger && row >= N) ? -1.f : 1.f);
+        cf o{yr * sc, yi * sc};
+        if (shift) o += (float)shift[r] * in[((size_t)r * g.V + v) * n + row];
+        if (!active || active[r]) out[((size_t)r * g.V + v) * n + row] = o;
+        nv[rr] += double(o.re) * o.re + double(o.im) * o.im;
+      }
+  }
+  if (want_norm) {
+    __shared__ double sm[32 * R];
+    cta_reduce<R>(nv, sm);
+    __shared__ bool last;
+    const int nblk = gridDim.x;
+    if (threadIdx.x == 0) {
+      for (int rr = 0; rr < R; ++rr)
+        if (r0 + rr < nrhs) rb.partial[(size_t)(r0 + rr) * nblk + blockIdx.x] = nv[rr];
+      __threadfence();
+      last = atomicAdd(rb.counter + blockIdx.y, 1u) == (unsigned)nblk - 1;
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      __shared__ double sred[32];
+      for (int rr = 0; rr < R && r0 + rr < nrhs; ++rr) {
+        const double s = cta_sum_strided(rb.partial + (size_t)(r0 + rr) * nblk, nblk, 1, sred);
+        if (threadIdx.x == 0) rb.result[r0 + rr] = s;
+      }
+      if (threadIdx.x == 0) rb.counter[blockIdx.y] = 0u;
+    }
+  }
+}
+
+size_t stencil_mma_words(int Vc, int n) { return (size_t)Vc * 2 * (n / 16) * (9 * n / 16) * 32; }
+
+void stencil_to_mma(int prec, const void* A, int Vc, int n, float* scale, void* out, cudaStream_t s) {
+  count_launch(2);
+  if (prec == WMG_PREC_DOUBLE) k_stencil_site_scale<double><<<Vc, 256, 0, s>>>((const cd*)A, n, scale);
+  else k_stencil_site_scale<float><<<Vc, 256, 0, s>>>((const cf*)A, n, scale);
+  const size_t tot = stencil_mma_words(Vc, n);
+  int B = (int)((tot + 255) / 256);
+  if (B > 148 * 32) B = 148 * 32;
+  if (prec == WMG_PREC_DOUBLE) k_stencil_to_mma<double><<<B, 256, 0, s>>>((const cd*)A, n, scale, (uint4*)out, Vc);
+  else k_stencil_to_mma<float><<<B, 256, 0, s>>>((const cf*)A, n, scale, (uint4*)out, Vc);
+}
+
+template <int NT>
+static void launch_mma(const void* A16, const float* sA, const Geom& g, int n, const void* in, void* out, int nrhs,
+                       const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s) {
+  constexpr int R = 8 * NT;
+  const size_t smem = (size_t)2 * R * (9 * n + kKPad) * sizeof(__half) + R * sizeof(float);
+  static const bool attr = [] {
+    cudaFuncSetAttribute(k_coarse_apply_mma<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    return true;
+  }();
+  (void)attr;
+  const int T = ((n / 16) * 32 + 127) / 128 * 128 > 128 ? 128 : 128;  // up to 4 row tiles (n <= 64)
+  dim3 grid(g.V, (nrhs + R - 1) / R);
+  RedBuf r = rb ? *rb : RedBuf{nullptr, nullptr, nullptr};
+  k_coarse_apply_mma<NT><<<grid, T, smem, s>>>((const uint4*)A16, sA, g, n, (const cf*)in, (cf*)out, nrhs, shift,
+                                               dagger ? 1 : 0, active, r, rb ? 1 : 0);
+}
+
+void coarse_apply_mma(const void* A16, const float* sA, const Geom& g, int n, const void* in, void* out, int nrhs,
+                      const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s) {
+  count_launch();
+  if (nrhs <= 8) launch_mma<1>(A16, sA, g, n, in, out, nrhs, shift, dagger, active, rb, s);
+  else launch_mma<2>(A16, sA, g, n, in, out, nrhs, shift, dagger, active, rb, s);
+}
+
+}  // namespace wmg

@@ -24,6 +24,8 @@ struct LevelData {
   int ndof = 12;     // complex dof per site (12 fine, 2N coarse)
   // coarse operator of this level (levels >= 1): [site][9][col][row], per precision
   void* A[2] = {nullptr, nullptr};
+  void* A16 = nullptr;     // FP16 fragment-order copy for the tensor-core apply (or null)
+  float* sA = nullptr;     // its per-site scale
   // transfer to the next level (levels < nlev - 1)
   Blocking bk{};
   void* P[2] = {nullptr, nullptr};  // N fields of this level, per precision (P[0] = FP64)

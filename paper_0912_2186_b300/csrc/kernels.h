@@ -13,6 +13,7 @@ inline size_t prec_real_bytes(int prec) { return prec == WMG_PREC_DOUBLE ? 8 : 4
 
 // number of kernel launches issued by this library (all contexts)
 long long launch_count();
+long long graph_launch_count();  // kernels launched inside device-side graph loops (synchronises)
 void count_launch(int n = 1);
 
 // N(0,1) reals from the counter-based generator (rng.cu): out[i] depends only on (seed, i)
@@ -106,6 +107,11 @@ void hop_split_coarse(int prec, const void* A, const void* P, const Blocking& bk
                       cudaStream_t s);
 // scatter restricted slot fields [ncol][9][Vc][n] into the stencil at columns col0..
 void stencil_scatter(int prec, const void* rs, void* A, int Vc, int n, int col0, int ncol, cudaStream_t s);
+// tensor-core (FP16 mma.sync) copy of a stencil and its application (coarse_mma.cu)
+size_t stencil_mma_words(int Vc, int n);  // uint4 words of the fragment-order copy
+void stencil_to_mma(int prec, const void* A, int Vc, int n, float* scale, void* out, cudaStream_t s);
+void coarse_apply_mma(const void* A16, const float* sA, const Geom& g, int n, const void* in, void* out, int nrhs,
+                      const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s);
 // convert a stencil between precisions
 void stencil_convert(int prec_d, void* dst, int prec_s, const void* src, size_t count, cudaStream_t s);
 

@@ -191,7 +191,8 @@ double dslash_bytes(const wmg_ctx* c, int prec, int nact, bool resid) {
 }
 double coarse_bytes(const wmg_ctx* c, int l, int prec, int nact) {
   const double s = rb_(prec), V = c->L[l].g.V, n = c->L[l].ndof;
-  return V * 9.0 * n * n * 2.0 * s + (double)nact * V * n * 2.0 * s * 2.0;
+  const double sa = (prec == WMG_PREC_SINGLE && c->L[l].A16) ? 2.0 : s;  // FP16 tensor-core copy
+  return V * 9.0 * n * n * 2.0 * sa + V * 4.0 + (double)nact * V * n * 2.0 * s * 2.0;
 }
 double transfer_bytes(const wmg_ctx* c, int l, int prec, int nact) {
   const LevelData& L = c->L[l];
@@ -203,6 +204,16 @@ static int nact_of(const wmg_ctx* c, const int* active, int nrhs) { return activ
 // ------------------------------------------------------------------------------------
 // operators of a level
 // ------------------------------------------------------------------------------------
+// coarse stencil of level l in precision prec (FP16 tensor-core copy when it exists and prec is SINGLE)
+void coarse_op(wmg_ctx* c, int l, int prec, const void* in, void* out, int nrhs, bool dagger, const int* active,
+               const RedBuf* rb) {
+  const LevelData& L = c->L[l];
+  if (prec == WMG_PREC_SINGLE && L.A16)
+    coarse_apply_mma(L.A16, L.sA, L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, active, rb, c->stream);
+  else
+    coarse_apply(prec, L.A[prec], L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, active, rb, c->stream);
+}
+
 // out = A_l in   (l = 0: Wilson D; l >= 1: coarse stencil with the per-rhs shift)
 void level_apply(wmg_ctx* c, int l, int prec, const void* in, void* out, int nrhs, const int* active, int red,
                  const RedBuf* rb) {
@@ -212,9 +223,7 @@ void level_apply(wmg_ctx* c, int l, int prec, const void* in, void* out, int nrh
     dslash(prec, out, in, nullptr, c->gauge[prec], c->fine, c->d_mass, active, nrhs, red, rb, c->stream);
   } else {
     ProfScope ps(c, PROF_COARSE, coarse_bytes(c, l, prec, na), na);
-    const LevelData& L = c->L[l];
-    coarse_apply(prec, L.A[prec], L.g, L.ndof, in, out, nrhs, c->d_shift[l], false, active,
-                 red == 1 ? rb : nullptr, c->stream);
+    coarse_op(c, l, prec, in, out, nrhs, false, active, red == 1 ? rb : nullptr);
   }
 }
 
@@ -249,11 +258,34 @@ wmg_status mr(wmg_ctx* c, int l, int prec, void* x, const void* b, int nrhs, int
   return check(c, "mr");
 }
 
-__global__ void k_cg_init(int* done, int* iters, const double* bb, const int* active, int nrhs) {
+__global__ void k_cg_init(int* done, int* iters, const double* bb, const int* active, int nrhs, int* loop_it) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r == 0) *loop_it = 0;
   if (r >= nrhs) return;
   iters[r] = 0;
   done[r] = (active && !active[r]) || !(bb[r] > 0.0);
+}
+
+// kernels launched from inside device-side graph loops (added to the host launch count)
+__device__ unsigned long long g_graph_launches = 0;
+
+// end of one captured chunk of CGNR iterations: keep looping while some right-hand side is
+// not converged and the iteration cap is not reached (the loop always terminates)
+__global__ void k_cg_check(const int* done, int* loop_it, int nrhs, int chunk, int maxit, int kernels_per_body,
+                           cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0) return;
+  bool all = true;
+  for (int r = 0; r < nrhs; ++r) all = all && done[r];
+  const int it = *loop_it + chunk;
+  *loop_it = it;
+  g_graph_launches += (unsigned long long)kernels_per_body;
+  cudaGraphSetConditional(h, (!all && it < maxit) ? 1u : 0u);
+}
+
+long long graph_launch_count() {
+  unsigned long long v = 0;
+  cudaMemcpyFromSymbol(&v, g_graph_launches, sizeof(v));
+  return (long long)v;
 }
 
 wmg_status clear_graphs(wmg_ctx* c) {
@@ -284,9 +316,9 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
   blas_convert(prec, r, prec, b, n, nrhs, nullptr, s);
   blas_norm2(prec, b, n, nrhs, redbuf(c, RES_CGBB), s);
   RedBuf rzz0{c->red_partial, c->red_counter, cg.zz};
-  coarse_apply(prec, L.A[prec], L.g, L.ndof, r, z, nrhs, c->d_shift[l], true, nullptr, &rzz0, s);
+  coarse_op(c, l, prec, r, z, nrhs, true, nullptr, &rzz0);
   blas_convert(prec, p, prec, z, n, nrhs, nullptr, s);
-  k_cg_init<<<1, 64, 0, s>>>(cg.done, cg.iters, cg.bb, active, nrhs);
+  k_cg_init<<<1, 64, 0, s>>>(cg.done, cg.iters, cg.bb, active, nrhs, c->d_flag + 1);
   count_launch();
   RedBuf rqq{c->red_partial, c->red_counter, cg.qq};
   RedBuf rrr{c->red_partial, c->red_counter, cg.rr};
@@ -296,7 +328,7 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
   auto body = [&](int parity) {
     {
       ProfScope ps(c, PROF_COARSE, cb, nrhs);
-      coarse_apply(prec, L.A[prec], L.g, L.ndof, p, q, nrhs, c->d_shift[l], false, nullptr, &rqq, s);
+      coarse_op(c, l, prec, p, q, nrhs, false, nullptr, &rqq);
     }
     {
       ProfScope ps(c, PROF_BLAS, 0);
@@ -305,7 +337,7 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
     RedBuf rzz{c->red_partial, c->red_counter, cg.zz + (1 - parity) * nrhs};
     {
       ProfScope ps(c, PROF_COARSE, cb, nrhs);
-      coarse_apply(prec, L.A[prec], L.g, L.ndof, r, z, nrhs, c->d_shift[l], true, nullptr, &rzz, s);
+      coarse_op(c, l, prec, r, z, nrhs, true, nullptr, &rzz);
     }
     {
       ProfScope ps(c, PROF_BLAS, 0);
@@ -321,36 +353,48 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
   };
   const int chunk = 8;  // even: every chunk starts at parity 0
   if (!c->prof_on && c->use_graphs) {
-    // the chunk of iterations is captured once per argument set and replayed
+    // The CGNR loop runs on the device: a graph whose WHILE node repeats a captured chunk of
+    // iterations followed by a check kernel that clears the loop condition once every
+    // right-hand side has converged or coarse_maxit is reached.  Built once per argument set.
     char key[512];
-    std::snprintf(key, sizeof key, "cg%d/%d/%d/%p/%p/%p/%p/%p/%p/%p/%p/%p/%.17g", l, prec, nrhs, L.A[prec], x, r, p,
-                  q, z, (void*)c->d_shift[l], (void*)c->red_partial, (void*)c->res, cg.tol2);
-    cudaGraphExec_t ge = nullptr;
+    std::snprintf(key, sizeof key, "cg%d/%d/%d/%p/%p/%p/%p/%p/%p/%p/%p/%p/%p/%.17g/%d", l, prec, nrhs, L.A[prec],
+                  (void*)L.A16, x, r, p, q, z, (void*)c->d_shift[l], (void*)c->red_partial, (void*)c->res, cg.tol2,
+                  c->prm.coarse_maxit);
     auto it = c->graphs.find(key);
-    if (it != c->graphs.end()) {
-      ge = it->second.first;
-    } else {
+    if (it == c->graphs.end()) {
       if (c->graphs.size() > 64) TRY(clear_graphs(c));
+      cudaGraph_t parent;
+      CU(c, cudaGraphCreate(&parent, 0));
+      cudaGraphConditionalHandle h;
+      cudaError_t e = cudaGraphConditionalHandleCreate(&h, parent, 1u, cudaGraphCondAssignDefault);
+      cudaGraphNodeParams np = {};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      cudaGraphNode_t node;
+      if (e == cudaSuccess) e = cudaGraphAddNode(&node, parent, nullptr, nullptr, 0, &np);
+      if (e != cudaSuccess) {
+        cudaGraphDestroy(parent);
+        return fail(c, e, "cgnr graph");
+      }
+      cudaGraph_t bodyg = np.conditional.phGraph_out[0];
       const long long l0 = launch_count();
-      cudaGraph_t gr;
-      CU(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      for (int i = 0; i < chunk; ++i) body(i & 1);
-      CU(c, cudaStreamEndCapture(s, &gr));
-      const long long per = launch_count() - l0;
-      count_launch((int)-per);  // captured, not launched
-      cudaError_t e = cudaGraphInstantiate(&ge, gr, 0);
-      cudaGraphDestroy(gr);
-      if (e != cudaSuccess) return fail(c, e, "cudaGraphInstantiate");
-      c->graphs[key] = {ge, per};
+      e = cudaStreamBeginCaptureToGraph(s, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        for (int i = 0; i < chunk; ++i) body(i & 1);
+        const int per = (int)(launch_count() - l0) + 1;
+        k_cg_check<<<1, 32, 0, s>>>(cg.done, c->d_flag + 1, nrhs, chunk, c->prm.coarse_maxit, per, h);
+        e = cudaStreamEndCapture(s, &bodyg);
+      }
+      count_launch((int)-(launch_count() - l0));  // captured, not launched
+      cudaGraphExec_t ge = nullptr;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, parent, 0);
+      cudaGraphDestroy(parent);
+      if (e != cudaSuccess) return fail(c, e, "cgnr graph capture");
+      it = c->graphs.emplace(key, std::make_pair(ge, 0LL)).first;
     }
-    const long long per = c->graphs[key].second;
-    for (int itr = 0; itr < c->prm.coarse_maxit; itr += chunk) {
-      CU(c, cudaGraphLaunch(ge, s));
-      count_launch((int)per);
-      bool all;
-      TRY(all_done(&all));
-      if (all) break;
-    }
+    CU(c, cudaGraphLaunch(it->second.first, s));
   } else {
     for (int itr = 0; itr < c->prm.coarse_maxit; itr += chunk) {
       for (int i = 0; i < chunk; ++i) body(i & 1);
@@ -432,6 +476,11 @@ wmg_status galerkin(wmg_ctx* c, int l, int prec) {
     stencil_scatter(prec, rs, C.A[prec], C.g.V, n, col0, nc, c->stream);
   }
   stencil_convert(1 - prec, C.A[1 - prec], prec, C.A[prec], count, c->stream);
+  if (c->prm.coarse_tc && c->prm.prec_sloppy == WMG_PREC_SINGLE && n % 16 == 0 && n <= 64) {
+    if (!C.A16) CU(c, cudaMalloc(&C.A16, stencil_mma_words(C.g.V, n) * 16));
+    if (!C.sA) CU(c, cudaMalloc((void**)&C.sA, C.g.V * sizeof(float)));
+    stencil_to_mma(WMG_PREC_SINGLE, C.A[1], C.g.V, n, C.sA, C.A16, c->stream);
+  }
   return check(c, "galerkin");
 }
 

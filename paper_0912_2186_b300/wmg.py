@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libwmg.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "wmg.h")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ERANK, ETIMEOUT, ESTATE = range(8)
-PREC_DOUBLE, PREC_SINGLE = 0, 1
+PREC_DOUBLE, PREC_SINGLE, PREC_HALF = 0, 1, 2
 MAX_LEVELS = 3
 
 
@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
         ("coarse_maxit", ctypes.c_int),
         ("max_iter", ctypes.c_int),
         ("prec_sloppy", ctypes.c_int),
-        ("pad_", ctypes.c_int),
+        ("coarse_tc", ctypes.c_int),
         ("reliable_delta", ctypes.c_double),
         ("seed", ctypes.c_uint64),
     ]

@@ -156,3 +156,20 @@ def test_mass_shift_on_coarse_levels(W):
     ctx.apply_coarse(1, 0, dev(phi.reshape(-1)), out, 2)
     want = np.stack([A1.shifted(0.45).apply(phi[r]) for r in range(2)])
     assert rel_err(host(out), want.reshape(2, -1)) < 1e-12
+
+
+@pytest.mark.parametrize("dims,block,N", [((8, 8, 8, 8), (2, 2, 2, 2), 8), ((8, 8, 8, 12), (4, 4, 4, 4), 24)])
+def test_tensor_core_coarse_apply(W, dims, block, N):
+    """FP16 tensor-core coarse stencil (2N = 16, 48) against the oracle, FP16 tolerance 2e-3."""
+    h = _hier(W, dims, [block], [N], 1)
+    ctx, A1 = h["ctx"], h["A"][1]
+    nrhs = 13                                    # two chunks of the 16-rhs kernel, ragged
+    phi = synth.coarse_starts(A1.dims, A1.n, nrhs, 60)
+    for dag in (False, True):
+        out = coarse_buf(phi.size // nrhs, nrhs, 1)
+        ctx.apply_coarse(1, 2, dev(phi.reshape(-1).astype(np.complex64)), out, nrhs, dagger=dag)
+        f = A1.apply_dagger if dag else A1.apply
+        want = np.stack([f(phi[r]) for r in range(nrhs)])
+        got = host(out).reshape(want.shape)
+        for r in range(nrhs):                    # per right-hand side (each has its own FP16 scale)
+            assert rel_err(got[r], want[r]) < 2e-3
