@@ -58,13 +58,14 @@ __global__ void k_dot_norm(const void* a_, const void* b_, size_t n, RedBuf rb) 
   const int r = blockIdx.y;
   const cpx<R>* a = vec<R>(a_, n, r);
   const cpx<R>* b = vec<R>(b_, n, r);
-  double v[3] = {0, 0, 0};
+  R t[3] = {0, 0, 0};  // per-thread sums in the vectors' precision, FP64 across threads
   WMG_GRID_LOOP(i) {
     cpx<R> x = a[i], y = b[i];
-    v[0] += double(x.re) * y.re + double(x.im) * y.im;
-    v[1] += double(x.re) * y.im - double(x.im) * y.re;
-    v[2] += double(x.re) * x.re + double(x.im) * x.im;
+    t[0] += x.re * y.re + x.im * y.im;
+    t[1] += x.re * y.im - x.im * y.re;
+    t[2] += x.re * x.re + x.im * x.im;
   }
+  double v[3] = {double(t[0]), double(t[1]), double(t[2])};
   __shared__ double sm[32 * 3];
   cta_reduce<3>(v, sm);
   grid_finish<3>(rb, r, blockIdx.x, gridDim.x, v);
@@ -74,11 +75,12 @@ template <typename R>
 __global__ void k_norm2(const void* a_, size_t n, RedBuf rb) {
   const int r = blockIdx.y;
   const cpx<R>* a = vec<R>(a_, n, r);
-  double v[1] = {0};
+  R t = 0;
   WMG_GRID_LOOP(i) {
     cpx<R> x = a[i];
-    v[0] += double(x.re) * x.re + double(x.im) * x.im;
+    t += x.re * x.re + x.im * x.im;
   }
+  double v[1] = {double(t)};
   __shared__ double sm[32];
   cta_reduce<1>(v, sm);
   grid_finish<1>(rb, r, blockIdx.x, gridDim.x, v);
@@ -124,7 +126,7 @@ __global__ void k_cg_update(void* x_, void* r_, const void* p_, const void* q_, 
   cpx<R>* rr = vec<R>(r_, n, r);
   const cpx<R>* p = vec<R>(p_, n, r);
   const cpx<R>* q = vec<R>(q_, n, r);
-  double v[1] = {0};
+  R t = 0;
   WMG_GRID_LOOP(i) {
     cpx<R> ri = rr[i];
     if (on) {
@@ -132,8 +134,9 @@ __global__ void k_cg_update(void* x_, void* r_, const void* p_, const void* q_, 
       ri = ri - al * q[i];
       rr[i] = ri;
     }
-    v[0] += double(ri.re) * ri.re + double(ri.im) * ri.im;
+    t += ri.re * ri.re + ri.im * ri.im;
   }
+  double v[1] = {double(t)};
   __shared__ double sm[32];
   cta_reduce<1>(v, sm);
   grid_finish<1>(rb, r, blockIdx.x, gridDim.x, v);
@@ -165,20 +168,23 @@ __global__ void k_multidot(const void* W, size_t slot_stride, int j0, int kmax, 
   const int r = blockIdx.y;
   if (active && !active[r]) return;
   const cpx<R>* w = vec<R>(w_, n, r);
-  double v[2 * J];
+  R t[2 * J];
 #pragma unroll
-  for (int j = 0; j < 2 * J; ++j) v[j] = 0.0;
+  for (int j = 0; j < 2 * J; ++j) t[j] = 0;
   WMG_GRID_LOOP(i) {
     const cpx<R> b = w[i];
 #pragma unroll
     for (int j = 0; j < J; ++j) {
       if (j0 + j < kmax) {
         const cpx<R> a = vec<R>((const char*)W + (j0 + j) * slot_stride, n, r)[i];
-        v[2 * j] += double(a.re) * b.re + double(a.im) * b.im;
-        v[2 * j + 1] += double(a.re) * b.im - double(a.im) * b.re;
+        t[2 * j] += a.re * b.re + a.im * b.im;
+        t[2 * j + 1] += a.re * b.im - a.im * b.re;
       }
     }
   }
+  double v[2 * J];
+#pragma unroll
+  for (int j = 0; j < 2 * J; ++j) v[j] = double(t[j]);
   __shared__ double sm[32 * 2 * J];
   cta_reduce<2 * J>(v, sm);
   grid_finish<2 * J>(rb, r, blockIdx.x, gridDim.x, v);
@@ -202,7 +208,7 @@ __global__ void k_gcr_orth(const void* W, const void* Z, size_t slot_stride, int
   cpx<R>* w = vec<R>(w_, n, r);
   cpx<R>* z = vec<R>(z_, n, r);
   const cpx<R>* rv = vec<R>(r_, n, r);
-  double v[3] = {0, 0, 0};
+  R t[3] = {0, 0, 0};
   WMG_GRID_LOOP(i) {
     cpx<R> wi = w[i], zi = z[i];
     for (int j = 0; j < k; ++j) {
@@ -213,45 +219,61 @@ __global__ void k_gcr_orth(const void* W, const void* Z, size_t slot_stride, int
     w[i] = wi;
     z[i] = zi;
     const cpx<R> ri = rv[i];
-    v[0] += double(wi.re) * wi.re + double(wi.im) * wi.im;
-    v[1] += double(wi.re) * ri.re + double(wi.im) * ri.im;
-    v[2] += double(wi.re) * ri.im - double(wi.im) * ri.re;
+    t[0] += wi.re * wi.re + wi.im * wi.im;
+    t[1] += wi.re * ri.re + wi.im * ri.im;
+    t[2] += wi.re * ri.im - wi.im * ri.re;
   }
+  double v[3] = {double(t[0]), double(t[1]), double(t[2])};
   __shared__ double sm[32 * 3];
   cta_reduce<3>(v, sm);
   grid_finish<3>(rb, r, blockIdx.x, gridDim.x, v);
 }
 
-// alpha = <w,r>/|w|^2; x64 += alpha z; r -= alpha w; w, z scaled by 1/|w|; red = |r|^2
+// alpha = <w,r>/|w|^2; x += alpha z; r -= alpha w; w, z scaled by 1/|w|; red = |r|^2.  x is the
+// iterate in the sloppy precision since the last reliable update.
 template <typename R>
-__global__ void k_gcr_update(double* x64, void* r_, void* w_, void* z_, const double* wred, size_t n,
+__global__ void k_gcr_update(void* x_, void* r_, void* w_, void* z_, const double* wred, size_t n,
                              const int* active, RedBuf rb) {
   const int r = blockIdx.y;
   if (active && !active[r]) return;
   const double ww = wred[r * 3 + 0];
   const bool ok = ww > 0.0;
-  const double inv = ok ? 1.0 / sqrt(ww) : 0.0;
-  const cd al{ok ? wred[r * 3 + 1] / ww : 0.0, ok ? wred[r * 3 + 2] / ww : 0.0};
-  const cpx<R> alr{R(al.re), R(al.im)};
-  cd* x = reinterpret_cast<cd*>(x64) + n * r;
+  const R inv = R(ok ? 1.0 / sqrt(ww) : 0.0);
+  const cpx<R> al{R(ok ? wred[r * 3 + 1] / ww : 0.0), R(ok ? wred[r * 3 + 2] / ww : 0.0)};
+  cpx<R>* x = vec<R>(x_, n, r);
   cpx<R>* rv = vec<R>(r_, n, r);
   cpx<R>* w = vec<R>(w_, n, r);
   cpx<R>* z = vec<R>(z_, n, r);
-  double v[1] = {0};
+  R t = 0;
   WMG_GRID_LOOP(i) {
     const cpx<R> zi = z[i], wi = w[i];
-    cd xi = x[i];
-    cfma(xi, al, cd{double(zi.re), double(zi.im)});
+    cpx<R> xi = x[i];
+    cfma(xi, al, zi);
     x[i] = xi;
-    const cpx<R> ri = rv[i] - alr * wi;
+    const cpx<R> ri = rv[i] - al * wi;
     rv[i] = ri;
-    w[i] = R(inv) * wi;
-    z[i] = R(inv) * zi;
-    v[0] += double(ri.re) * ri.re + double(ri.im) * ri.im;
+    w[i] = inv * wi;
+    z[i] = inv * zi;
+    t += ri.re * ri.re + ri.im * ri.im;
   }
+  double v[1] = {double(t)};
   __shared__ double sm[32];
   cta_reduce<1>(v, sm);
   grid_finish<1>(rb, r, blockIdx.x, gridDim.x, v);
+}
+
+// x64 += x (sloppy), x = 0, for the masked right-hand sides (reliable update)
+template <typename R>
+__global__ void k_fold(double* x64, void* x_, size_t n, const int* mask) {
+  const int r = blockIdx.y;
+  if (mask && !mask[r]) return;
+  cd* X = reinterpret_cast<cd*>(x64) + n * r;
+  cpx<R>* x = vec<R>(x_, n, r);
+  WMG_GRID_LOOP(i) {
+    const cpx<R> a = x[i];
+    X[i] += cd{double(a.re), double(a.im)};
+    x[i] = cpx<R>{R(0), R(0)};
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -351,11 +373,17 @@ void gcr_orth(int prec, const void* W, const void* Z, size_t slot_stride, int k,
   WMG_BY_PREC(prec, k_gcr_orth, <<<g, kBlasThreads, 0, s>>>(W, Z, slot_stride, k, w, z, r, coef, nrhs, n, active, rb));
 }
 
-void gcr_update(int prec, double* x64, void* r, void* w, void* z, const double* wred, size_t n, int nrhs,
+void gcr_update(int prec, void* x, void* r, void* w, void* z, const double* wred, size_t n, int nrhs,
                 const int* active, const RedBuf& rb, cudaStream_t s) {
   count_launch();
   dim3 g(blas_blocks(n), nrhs);
-  WMG_BY_PREC(prec, k_gcr_update, <<<g, kBlasThreads, 0, s>>>(x64, r, w, z, wred, n, active, rb));
+  WMG_BY_PREC(prec, k_gcr_update, <<<g, kBlasThreads, 0, s>>>(x, r, w, z, wred, n, active, rb));
+}
+
+void blas_fold(int prec, double* x64, void* x, size_t n, int nrhs, const int* mask, cudaStream_t s) {
+  count_launch();
+  dim3 g(blas_blocks(n), nrhs);
+  WMG_BY_PREC(prec, k_fold, <<<g, kBlasThreads, 0, s>>>(x64, x, n, mask));
 }
 
 }  // namespace wmg

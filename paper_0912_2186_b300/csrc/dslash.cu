@@ -104,18 +104,22 @@ __global__ void __launch_bounds__(128) k_dslash(void* __restrict__ out, const vo
       for (int i = 0; i < 12; ++i) acc[i] = bb[i] - acc[i];
     }
     store_spinor<R>(reinterpret_cast<char*>(out) + fb * rhs, g.V, v, acc);
+    // per-site sums in the field's precision; FP64 across threads and CTAs
     if (RED == 2) {
+      R a0 = 0, a1 = 0;
 #pragma unroll
       for (int i = 0; i < 12; ++i) {
-        red[0] += double(acc[i].re) * double(self[i].re) + double(acc[i].im) * double(self[i].im);
-        red[1] += double(acc[i].re) * double(self[i].im) - double(acc[i].im) * double(self[i].re);
+        a0 += acc[i].re * self[i].re + acc[i].im * self[i].im;
+        a1 += acc[i].re * self[i].im - acc[i].im * self[i].re;
       }
+      red[0] = double(a0);
+      red[1] = double(a1);
     }
     if (RED >= 1) {
-      double n = 0.0;
+      R nn = 0;
 #pragma unroll
-      for (int i = 0; i < 12; ++i) n += double(acc[i].re) * double(acc[i].re) + double(acc[i].im) * double(acc[i].im);
-      red[RED == 2 ? 2 : 0] = n;
+      for (int i = 0; i < 12; ++i) nn += acc[i].re * acc[i].re + acc[i].im * acc[i].im;
+      red[RED == 2 ? 2 : 0] = double(nn);
     }
   }
   if (RED > 0) {

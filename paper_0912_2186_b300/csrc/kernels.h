@@ -68,9 +68,11 @@ void gcr_multidot(int prec, const void* W, size_t slot_stride, int kmax, const v
 // w -= sum_j c_j W_j, z -= sum_j c_j Z_j, then red = {|w|^2, Re<w,r>, Im<w,r>}
 void gcr_orth(int prec, const void* W, const void* Z, size_t slot_stride, int k, void* w, void* z, const void* r,
               const double* coef, int kmax, size_t n, int nrhs, const int* active, const RedBuf& rb, cudaStream_t s);
-// alpha = <w,r>/|w|^2, x64 += alpha z, r -= alpha w, w /= |w|, z /= |w|; red = |r|^2
-void gcr_update(int prec, double* x64, void* r, void* w, void* z, const double* wred, size_t n, int nrhs,
+// alpha = <w,r>/|w|^2, x += alpha z, r -= alpha w, w /= |w|, z /= |w|; red = |r|^2 (x sloppy)
+void gcr_update(int prec, void* x, void* r, void* w, void* z, const double* wred, size_t n, int nrhs,
                 const int* active, const RedBuf& rb, cudaStream_t s);
+// reliable update of the solution: x64 += x, x = 0 for masked right-hand sides
+void blas_fold(int prec, double* x64, void* x, size_t n, int nrhs, const int* mask, cudaStream_t s);
 
 // ---- transfer (transfer.cu) ----
 struct Blocking {

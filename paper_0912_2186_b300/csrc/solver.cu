@@ -565,6 +565,8 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
   TRY(vec_ws(c, 0, "gcr_x64", WMG_PREC_DOUBLE, nslots, &x64));
   TRY(vec_ws(c, 0, "gcr_r64", WMG_PREC_DOUBLE, nslots, &r64));
   TRY(vec_ws(c, 0, "gcr_rlo", lo, nslots, &rlo));
+  void* xlo;
+  TRY(vec_ws(c, 0, "gcr_xlo", lo, nslots, &xlo));
   const size_t slot = n * nslots * csize(lo);
   TRY(ws_get(c, std::string("gcr_Z") + (lo ? "s" : "d"), slot * m, &Z));
   TRY(ws_get(c, std::string("gcr_W") + (lo ? "s" : "d"), slot * m, &W));
@@ -607,6 +609,7 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
         for (const Admission& a : adm) {
           pack_spinor(WMG_PREC_DOUBLE, a.b_canon_dev, at(b64, f64, a.slot), c->fine.V, 1, s);
           blas_zero(WMG_PREC_DOUBLE, at(x64, f64, a.slot), n, 1, s);
+          blas_zero(lo, at(xlo, flo, a.slot), n, 1, s);
           blas_convert(WMG_PREC_DOUBLE, at(r64, f64, a.slot), WMG_PREC_DOUBLE, at(b64, f64, a.slot), n, 1, nullptr, s);
           mass[a.slot] = a.mass;
           mask[a.slot] = 1;
@@ -646,7 +649,7 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
       ProfScope ps(c, PROF_BLAS, 0);
       if (k > 0) gcr_multidot(lo, W, slot, k, wk, n, nslots, c->d_active, rb_coef, s);
       gcr_orth(lo, W, Z, slot, k, wk, zk, rlo, rb_coef.result, k, n, nslots, c->d_active, rb_w, s);
-      gcr_update(lo, (double*)x64, rlo, wk, zk, rb_w.result, n, nslots, c->d_active, rb_rn, s);
+      gcr_update(lo, xlo, rlo, wk, zk, rb_w.result, n, nslots, c->d_active, rb_rn, s);
     }
     TRY(check(c, "gcr iteration"));
     TRY(download(c, rb_rn.result, nslots, rn2));
@@ -662,13 +665,15 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
       anyrel = anyrel || rel[r];
     }
     if (anyrel) {
-      // FP64 true residual r64 = b - D x64 for the active slots; applied where rel is set
+      // fold the sloppy iterate into the FP64 solution, then the FP64 true residual
+      // r64 = b - D x64 for the active slots; applied where rel is set
+      TRY(upload_ints(c, c->d_mask, rel));
+      blas_fold(lo, (double*)x64, xlo, n, nslots, c->d_mask, s);
       {
         ProfScope ps(c, PROF_DSLASH_64, dslash_bytes(c, WMG_PREC_DOUBLE, c->n_active, true), c->n_active);
         dslash(WMG_PREC_DOUBLE, r64, x64, b64, c->gauge[0], c->fine, c->d_mass, c->d_active, nslots, 1, &rb_r64, s);
       }
       TRY(download(c, rb_r64.result, nslots, t));
-      TRY(upload_ints(c, c->d_mask, rel));
       blas_convert(lo, rlo, WMG_PREC_DOUBLE, r64, n, nslots, c->d_mask, s);
       bool changed = false;
       for (int r = 0; r < nslots; ++r) {
