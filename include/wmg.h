@@ -148,8 +148,8 @@ wmg_status wmg_set_mass(wmg_ctx* ctx, double m);
  * chirality split of Sec. 3, Galerkin coarse operators, level by level.
  * starts_host: NULL or, for the fine level, nvec[0] fine spinors in the canonical
  * layout.  NULL draws Gaussian starts on the device from the counter-based Philox-4x32-10
- * generator keyed by p->seed (p->seed + 1 for the second level), real and imaginary
- * parts in canonical order.  Synchronises. */
+ * generator keyed by p->seed (p->seed + 1 for the second level; Box-Muller in FP32), real
+ * and imaginary parts in canonical order.  Synchronises. */
 wmg_status wmg_setup(wmg_ctx* ctx, const wmg_params* p, const double* starts_host);
 
 /* Replace the near-null vectors of `level` (0: fine spinors, canonical layout;

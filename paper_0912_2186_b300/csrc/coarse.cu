@@ -224,6 +224,180 @@ void hop_split_fine(int prec, const void* gauge, const void* P, const Blocking& 
     k_hop_split_fine<float><<<grid, 128, 0, s>>>(gauge, P, bk, float(4.0 + mass), col0, out9);
 }
 
+// Fused Galerkin construction on the fine level: CTA per (column c, coarse block) with the
+// columns of one block adjacent in the grid, so that the block's vectors P are shared in L2;
+// one thread per block site (bs <= 256, every block extent >= 2).  Thread x computes the terms
+// of D g_c at x (g_c = P_alpha restricted to chirality s in every block): the diagonal and the
+// hops whose neighbour lies in the block go to the self slot, each hop leaving the block to the
+// slot of its direction (at most one per direction).  For every row (s', alpha') the products
+// <P_alpha'(x)|_s', term> are summed over the block by warp shuffles, per-warp partials in
+// shared memory, and a final fixed-order sum; the CTA writes column c of all 9 blocks.
+template <typename R>
+__global__ void __launch_bounds__(256) k_galerkin_fine(const void* __restrict__ gauge, const void* __restrict__ P,
+                                                       Blocking bk, R diag, void* __restrict__ Aout) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int N = bk.N, n = 2 * N;
+  const int c = blockIdx.x % n, xc = blockIdx.x / n;
+  const int s = c / N, a = c % N;
+  const int e = threadIdx.x;
+  const int nw = blockDim.x >> 5, warp = e >> 5, lane = e & 31;
+  R* red = reinterpret_cast<R*>(smraw);  // [nw][N][9][2 chir][2 re/im]
+  const Geom& g = bk.fine;
+  const size_t fb = spinor_field_bytes<R>(g.V);
+  const char* Pa = (const char*)P + fb * a;
+  cpx<R> self[12], face[4][12];
+  int fslot[4];
+  const bool live = e < bk.bs;
+  int v = 0;
+  if (live) {
+    // block site e -> fine site
+    int cc[4];
+    site_coords(bk.coarse, xc, cc);
+    int o[4];
+    o[0] = e % bk.b[0];
+    int t = e / bk.b[0];
+    o[1] = t % bk.b[1];
+    t /= bk.b[1];
+    o[2] = t % bk.b[2];
+    o[3] = t / bk.b[2];
+    int f[4];
+    for (int i = 0; i < 4; ++i) f[i] = cc[i] * bk.b[i] + o[i];
+    v = site_index(g, f);
+    int crd[4];
+    site_coords(g, v, crd);
+    load_spinor<R>(Pa, g.V, v, self);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) self[k] = ((k < 6) == (s == 0)) ? diag * self[k] : cpx<R>{R(0), R(0)};
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      fslot[mu] = -1;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) face[mu][k] = cpx<R>{R(0), R(0)};
+#pragma unroll
+      for (int sg = 0; sg < 2; ++sg) {
+        const int sign = sg ? -1 : +1;
+        const int nb = neighbour(g, v, crd, mu, sign);
+        cpx<R> u[9], xg[12], tt[12];
+        load_spinor<R>(Pa, g.V, nb, xg);
+#pragma unroll
+        for (int k = 0; k < 12; ++k)
+          if ((k < 6) != (s == 0)) xg[k] = cpx<R>{R(0), R(0)};
+#pragma unroll
+        for (int k = 0; k < 12; ++k) tt[k] = cpx<R>{R(0), R(0)};
+        if (sg == 0) {
+          load_link<R>(gauge, g.V, mu, v, u);
+          hop_accumulate<+1>(mu, u, xg, tt);
+        } else {
+          load_link<R>(gauge, g.V, mu, nb, u);
+          hop_accumulate<-1>(mu, u, xg, tt);
+        }
+        const bool inb = same_block(crd[mu], g.L[mu], bk.b[mu], sign);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          const cpx<R> h = R(-0.5) * tt[k];
+          if (inb) self[k] += h;
+          else face[mu][k] = h;
+        }
+        if (!inb) fslot[mu] = 1 + 2 * mu + sg;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) self[k] = cpx<R>{R(0), R(0)};
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      fslot[mu] = -1;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) face[mu][k] = cpx<R>{R(0), R(0)};
+    }
+  }
+  for (int ap = 0; ap < N; ++ap) {
+    cpx<R> p[12];
+    if (live) load_spinor<R>((const char*)P + fb * ap, g.V, v, p);
+    else
+#pragma unroll
+      for (int k = 0; k < 12; ++k) p[k] = cpx<R>{R(0), R(0)};
+    R acc[9][4];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = R(0);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const int ch = k < 6 ? 0 : 2;
+      cpx<R> d = cmulc(p[k], self[k]);
+      acc[0][ch] += d.re;
+      acc[0][ch + 1] += d.im;
+    }
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      cpx<R> d0{R(0), R(0)}, d1{R(0), R(0)};
+#pragma unroll
+      for (int k = 0; k < 6; ++k) cfmac(d0, p[k], face[mu][k]);
+#pragma unroll
+      for (int k = 6; k < 12; ++k) cfmac(d1, p[k], face[mu][k]);
+      // the thread's face term of direction mu belongs to slot 1 + 2 mu (+) or 2 + 2 mu (-)
+      const bool minus = fslot[mu] == 2 + 2 * mu;
+#pragma unroll
+      for (int sg = 0; sg < 2; ++sg) {
+        const bool mine = (sg == 1) == minus;
+        acc[1 + 2 * mu + sg][0] += mine ? d0.re : R(0);
+        acc[1 + 2 * mu + sg][1] += mine ? d0.im : R(0);
+        acc[1 + 2 * mu + sg][2] += mine ? d1.re : R(0);
+        acc[1 + 2 * mu + sg][3] += mine ? d1.im : R(0);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+#pragma unroll
+      for (int w = 0; w < 4; ++w)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[q][w] += __shfl_xor_sync(0xffffffffu, acc[q][w], o);
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < 9; ++q)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) red[(((size_t)warp * N + ap) * 9 + q) * 4 + w] = acc[q][w];
+  }
+  __syncthreads();
+  // column c of the 9 blocks: rows s'*N + alpha', summed over warps in order
+  cpx<R>* A = reinterpret_cast<cpx<R>*>(Aout);
+  for (int i = threadIdx.x; i < 9 * n; i += blockDim.x) {
+    const int q = i / n, row = i % n, sp = row / N, ap = row % N;
+    R re = 0, im = 0;
+    for (int w = 0; w < nw; ++w) {
+      re += red[(((size_t)w * N + ap) * 9 + q) * 4 + 2 * sp];
+      im += red[(((size_t)w * N + ap) * 9 + q) * 4 + 2 * sp + 1];
+    }
+    A[(((size_t)xc * 9 + q) * n + c) * n + row] = cpx<R>{re, im};
+  }
+}
+
+bool galerkin_fine_fused(int prec, const void* gauge, const void* P, const Blocking& bk, double mass, void* A,
+                         cudaStream_t s) {
+  if (bk.bs > 256) return false;
+  for (int i = 0; i < 4; ++i)
+    if (bk.b[i] < 2) return false;
+  count_launch();
+  const int T = ((bk.bs + 31) / 32) * 32;
+  const size_t smem = (size_t)(T / 32) * bk.N * 9 * 4 * (prec == WMG_PREC_DOUBLE ? 8 : 4);
+  dim3 grid((unsigned)(2 * bk.N) * bk.coarse.V);
+  if (prec == WMG_PREC_DOUBLE) {
+    static const bool attr = [] {
+      cudaFuncSetAttribute(k_galerkin_fine<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      return true;
+    }();
+    (void)attr;
+    k_galerkin_fine<double><<<grid, T, smem, s>>>(gauge, P, bk, 4.0 + mass, A);
+  } else {
+    static const bool attr = [] {
+      cudaFuncSetAttribute(k_galerkin_fine<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      return true;
+    }();
+    (void)attr;
+    k_galerkin_fine<float><<<grid, T, smem, s>>>(gauge, P, bk, float(4.0 + mass), A);
+  }
+  return true;
+}
+
 // Galerkin build, coarse level: the same split for the stencil A of the finer coarse lattice.
 // Thread per (site of bk.fine, row).  Output: [cc][9] coarse fields [Vf][nf].
 template <typename R>

@@ -22,6 +22,7 @@ namespace wmg {
 namespace {
 
 constexpr int kKPad = 8;  // halves of padding per staged column (bank-conflict free B loads)
+constexpr int kEPL = 18;  // gathered values per lane: 9n <= 576 (n <= 64)
 
 WMG_D uint32_t pack_half2(float lo, float hi) {
   __half2 h = __floats2half2_rn(lo, hi);
@@ -117,37 +118,46 @@ __global__ void __launch_bounds__(128) k_coarse_apply_mma(const uint4* __restric
     nbs[k] = k == 0 ? v : neighbour(g, v, c, (k - 1) >> 1, ((k - 1) & 1) ? -1 : +1);
   }
   __syncthreads();
-  // one warp per right-hand side: max |Re|, |Im| of its 9 gathered neighbour vectors, then the
+  // lane-owned elements e = lane + 32 i of the 9n gathered values (same for every rhs)
+  int offs[kEPL];
+  unsigned neg = 0;  // bit i: sigma_3 sign flip of element i (adjoint, lower half of the dof)
+#pragma unroll
+  for (int i = 0; i < kEPL; ++i) {
+    const int e = lane + 32 * i;
+    offs[i] = -1;
+    if (e < K) {
+      const int k = e / n, j = e - k * n;
+      offs[i] = nbs[k] * n + j;
+      if (dagger && j >= N) neg |= 1u << i;
+    }
+  }
+  // one warp per right-hand side: values into registers, max |Re|, |Im| by shuffles, then the
   // scaled FP16 copy in column layout [Xr 0..7 | Xi 0..7 | Xr 8..15 | Xi 8..15]
   for (int rr = warp; rr < R; rr += nwarp) {
     const int r = r0 + rr;
     const int blk = rr >> 3, cc = rr & 7;
     __half* colr = xb + (size_t)(blk * 16 + cc) * KP;
     __half* coli = xb + (size_t)(blk * 16 + 8 + cc) * KP;
-    if (r >= nrhs) {
-      for (int kk = lane; kk < K; kk += 32) colr[kk] = coli[kk] = __float2half_rn(0.f);
-      if (lane == 0) xmax[rr] = 0.f;
-      continue;
-    }
+    cf xv[kEPL];
     float m = 0.f;
-    for (int k = 0; k < 9; ++k) {
-      const cf* src = in + ((size_t)r * g.V + nbs[k]) * n;
-      for (int j = lane; j < n; j += 32) {
-        const cf x = src[j];
-        m = fmaxf(m, fmaxf(fabsf(x.re), fabsf(x.im)));
-      }
+    const cf* src = in + (size_t)(r < nrhs ? r : 0) * g.V * n;
+#pragma unroll
+    for (int i = 0; i < kEPL; ++i) {
+      xv[i] = cf{0.f, 0.f};
+      if (offs[i] >= 0 && r < nrhs) xv[i] = src[offs[i]];
+      m = fmaxf(m, fmaxf(fabsf(xv[i].re), fabsf(xv[i].im)));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) xmax[rr] = m;
     const float inv = m > 0.f ? 1.f / m : 0.f;
-    for (int k = 0; k < 9; ++k) {
-      const cf* src = in + ((size_t)r * g.V + nbs[k]) * n;
-      for (int j = lane; j < n; j += 32) {
-        const cf x = src[j];
-        const float sg = (dagger && j >= N) ? -inv : inv;
-        colr[k * n + j] = __float2half_rn(x.re * sg);
-        coli[k * n + j] = __float2half_rn(x.im * sg);
+#pragma unroll
+    for (int i = 0; i < kEPL; ++i) {
+      const int e = lane + 32 * i;
+      if (e < K) {
+        const float sg = ((neg >> i) & 1u) ? -inv : inv;
+        colr[e] = __float2half_rn(xv[i].re * sg);
+        coli[e] = __float2half_rn(xv[i].im * sg);
       }
     }
   }
@@ -164,7 +174,7 @@ __global__ void __launch_bounds__(128) k_coarse_apply_mma(const uint4* __restric
   if (warp < mt) {
     const uint4* Ar = A16 + (((size_t)v * 2 + 0) * mt + warp) * ksteps * 32 + lane;
     const uint4* Ai = A16 + (((size_t)v * 2 + 1) * mt + warp) * ksteps * 32 + lane;
-#pragma unroll 2
+#pragma unroll 3
     for (int k = 0; k < ksteps; ++k) {
       const uint4 ar = __ldg(Ar + (size_t)k * 32), ai = __ldg(Ai + (size_t)k * 32);
 #pragma unroll

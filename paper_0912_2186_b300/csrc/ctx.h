@@ -62,6 +62,7 @@ struct wmg_ctx {
   int* d_cgint = nullptr;                      // [2][kMaxRhs] cg done / iters
   cudaStream_t own_stream = nullptr;          // created when the caller passes no stream
   bool use_graphs = true;                      // capture the coarsest CGNR iterations
+  bool use_fused_galerkin = true;              // fused fine-level Galerkin kernel
   std::map<std::string, std::pair<cudaGraphExec_t, long long>> graphs;  // + launches per replay
   int n_active = 0;                            // active right-hand sides of the current solve
   // instrumentation

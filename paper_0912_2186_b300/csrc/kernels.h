@@ -105,6 +105,10 @@ void coarse_apply(int prec, const void* A, const Geom& g, int n, const void* in,
 // fine level: g = column (s, alpha) of P, written for ncol columns starting at col0
 void hop_split_fine(int prec, const void* gauge, const void* P, const Blocking& bk, double mass, int col0,
                     int ncol, void* out9, cudaStream_t s);
+// fused fine-level Galerkin construction straight into the stencil (false if the blocking is
+// not supported: more than 256 sites per block or an extent of 1)
+bool galerkin_fine_fused(int prec, const void* gauge, const void* P, const Blocking& bk, double mass, void* A,
+                         cudaStream_t s);
 void hop_split_coarse(int prec, const void* A, const void* P, const Blocking& bk, int col0, int ncol, void* out9,
                       cudaStream_t s);
 // scatter restricted slot fields [ncol][9][Vc][n] into the stencil at columns col0..

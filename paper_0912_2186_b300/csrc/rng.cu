@@ -32,14 +32,14 @@ __global__ void k_gaussian(double* out, size_t n, uint64_t seed) {
   if (4 * i >= n) return;
   const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(i >> 32), 0u, 0u),
                                 make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-  const double inv = 1.0 / 4294967296.0;
-  // (0, 1] uniforms from 32-bit integers
-  const double u0 = ((double)r.x + 1.0) * inv, u1 = ((double)r.y + 1.0) * inv;
-  const double u2 = ((double)r.z + 1.0) * inv, u3 = ((double)r.w + 1.0) * inv;
-  const double a = sqrt(-2.0 * log(u0)), b = sqrt(-2.0 * log(u2));
-  double s0, c0, s1, c1;
-  sincospi(2.0 * u1, &s0, &c0);
-  sincospi(2.0 * u3, &s1, &c1);
+  // (0, 1] uniforms from the top 24 bits (exact in FP32); Box-Muller in FP32 arithmetic
+  const float inv = 1.0f / 16777216.0f;
+  const float u0 = (float)((r.x >> 8) + 1u) * inv, u1 = (float)((r.y >> 8) + 1u) * inv;
+  const float u2 = (float)((r.z >> 8) + 1u) * inv, u3 = (float)((r.w >> 8) + 1u) * inv;
+  const float a = sqrtf(-2.0f * logf(u0)), b = sqrtf(-2.0f * logf(u2));
+  float s0, c0, s1, c1;
+  sincospif(2.0f * u1, &s0, &c0);
+  sincospif(2.0f * u3, &s1, &c1);
   const double z[4] = {a * c0, a * s0, b * c1, b * s1};
   for (int j = 0; j < 4 && 4 * i + j < n; ++j) out[4 * i + j] = z[j];
 }

@@ -457,14 +457,21 @@ wmg_status galerkin(wmg_ctx* c, int l, int prec) {
   const size_t budget = (size_t)3 << 30;
   int ncol = (int)std::max<size_t>(1, budget / (9 * fb));
   ncol = std::min(ncol, n);
-  void *out9, *rs;
-  TRY(ws_get(c, "gal_out9", (size_t)ncol * 9 * fb, &out9));
-  TRY(ws_get(c, "gal_rs", (size_t)ncol * 9 * C.g.V * n * csize(prec), &rs));
+  void *out9 = nullptr, *rs = nullptr;
+  const bool fused = l == 0 && c->use_fused_galerkin && L.bk.bs <= 256 && L.bk.b[0] > 1 && L.bk.b[1] > 1 &&
+                     L.bk.b[2] > 1 && L.bk.b[3] > 1;
+  if (!fused) {
+    TRY(ws_get(c, "gal_out9", (size_t)ncol * 9 * fb, &out9));
+    TRY(ws_get(c, "gal_rs", (size_t)ncol * 9 * C.g.V * n * csize(prec), &rs));
+  }
   const size_t count = (size_t)C.g.V * 9 * n * n;
   for (int p = 0; p < 2; ++p)
     if (!C.A[p]) CU(c, cudaMalloc(&C.A[p], count * csize(p)));
   ProfScope ps(c, PROF_SETUP, 0);
-  for (int col0 = 0; col0 < n; col0 += ncol) {
+  if (l == 0 && c->use_fused_galerkin &&
+      galerkin_fine_fused(prec, c->gauge[prec], L.P[prec], bk, c->mass_setup, C.A[prec], c->stream))
+    ncol = 0;  // done by the fused kernel
+  for (int col0 = 0; ncol > 0 && col0 < n; col0 += ncol) {
     const int nc = std::min(ncol, n - col0);
     if (l == 0) {
       hop_split_fine(prec, c->gauge[prec], L.P[prec], bk, c->mass_setup, col0, nc, out9, c->stream);

@@ -218,12 +218,16 @@ __global__ void k_prolong_coarse(const void* __restrict__ P, Blocking bk, const 
 
 // ------------------------------------------------------------------------------------
 // block Gram-Schmidt, FP64.  CTA per (coarse site, chirality s): the N vectors restricted to
-// the block and to the s half of the dof are orthonormalised in order alpha = 0..N-1 by
-// modified Gram-Schmidt, applied twice.  A vector whose norm after projection is below
-// 1e-10 of its norm before sets *rank_flag.
+// the block and to the s half of the dof are orthonormalised in order alpha = 0..N-1.  Each
+// vector is projected against the previous ones by classical Gram-Schmidt, the k projections
+// of a pass being reduced together, and projected a second time when the first pass lost more
+// than half of its norm ("twice is enough"; the result is the basis of modified Gram-Schmidt
+// to rounding); then it is normalised.  A vector whose norm after projection is
+// below 1e-10 of its norm before sets *rank_flag.
 // ------------------------------------------------------------------------------------
 constexpr int kGsThreads = 256;
 constexpr int kGsMaxPerThread = 8;
+constexpr int kGsChunk = 8;  // projections reduced per CTA reduction
 
 struct GsLayout {
   bool fine;
@@ -231,71 +235,98 @@ struct GsLayout {
   size_t field_stride;  // complex numbers per vector
 };
 
-WMG_D cd* gs_elem(const GsLayout& L, void* base, int a, int xc, int s, int e) {
-  cd* f = reinterpret_cast<cd*>(base) + L.field_stride * a;
+// offset (in complex numbers) of element e of block xc, chirality s, inside vector 0
+WMG_D size_t gs_offset(const GsLayout& L, int xc, int s, int e) {
   if (L.fine) {
     const int v = block_site(L.bk, xc, e / 6);
-    return fine_elem<double>(f, L.bk.fine.V, v, s * 6 + e % 6);
+    const int k = s * 6 + e % 6;
+    return ((size_t)(k >> 1) * L.bk.fine.V + v) * 2 + (k & 1);
   }
   const int h = L.bk.nf / 2;
   const int v = block_site(L.bk, xc, e / h);
-  return f + (size_t)v * L.bk.nf + s * h + e % h;
-}
-
-__device__ void gs_bcast_reduce2(double& a, double& b, double* sm) {
-  double v[2] = {a, b};
-  cta_reduce<2>(v, sm);
-  if (threadIdx.x == 0) {
-    sm[64] = v[0];
-    sm[65] = v[1];
-  }
-  __syncthreads();
-  a = sm[64];
-  b = sm[65];
-  __syncthreads();
+  return (size_t)v * L.bk.nf + s * h + e % h;
 }
 
 __global__ void __launch_bounds__(kGsThreads) k_block_gs(void* vecs, GsLayout L, int* rank_flag) {
-  __shared__ double sm[72];
+  __shared__ double sm[32 * 2 * kGsChunk];
+  __shared__ double coef[2 * 128];
   const int xc = blockIdx.x, s = blockIdx.y;
   const int E = L.fine ? L.bk.bs * 6 : L.bk.bs * (L.bk.nf / 2);
   const int N = L.bk.N;
-  cd* ptr[kGsMaxPerThread];
-  cd vk[kGsMaxPerThread];
+  cd* base = reinterpret_cast<cd*>(vecs);
+  const size_t fs = L.field_stride;
+  size_t off[kGsMaxPerThread];
   int ne = 0;
-  for (int e = threadIdx.x; e < E && ne < kGsMaxPerThread; e += blockDim.x) ++ne;
+  for (int e = threadIdx.x; e < E && ne < kGsMaxPerThread; e += blockDim.x) off[ne++] = gs_offset(L, xc, s, e);
   for (int k = 0; k < N; ++k) {
-    int i = 0;
-    for (int e = threadIdx.x; i < ne; e += blockDim.x, ++i) {
-      ptr[i] = gs_elem(L, vecs, k, xc, s, e);
-      vk[i] = *ptr[i];
+    cd vk[kGsMaxPerThread];
+    for (int i = 0; i < ne; ++i) vk[i] = base[fs * k + off[i]];
+    double n0 = 0;
+    {
+      double t[1] = {0};
+      for (int i = 0; i < ne; ++i) t[0] += norm2(vk[i]);
+      cta_reduce<1>(t, sm);
+      if (threadIdx.x == 0) coef[0] = t[0];
+      __syncthreads();
+      n0 = coef[0];
+      __syncthreads();
     }
-    double n0 = 0, dummy = 0;
-    for (i = 0; i < ne; ++i) n0 += norm2(vk[i]);
-    gs_bcast_reduce2(n0, dummy, sm);
-    for (int pass = 0; pass < 2; ++pass)
-      for (int j = 0; j < k; ++j) {
-        double br = 0, bi = 0;
-        int ii = 0;
-        for (int e = threadIdx.x; ii < ne; e += blockDim.x, ++ii) {
-          const cd q = *gs_elem(L, vecs, j, xc, s, e);
-          br += q.re * vk[ii].re + q.im * vk[ii].im;
-          bi += q.re * vk[ii].im - q.im * vk[ii].re;
-        }
-        gs_bcast_reduce2(br, bi, sm);
-        const cd beta{br, bi};
-        ii = 0;
-        for (int e = threadIdx.x; ii < ne; e += blockDim.x, ++ii) vk[ii] = vk[ii] - beta * *gs_elem(L, vecs, j, xc, s, e);
+    for (int pass = 0; pass < 2 && k > 0; ++pass) {
+      if (pass == 1) {
+        // second projection only if the first one cancelled more than half of the norm
+        // (Kahan-Parlett criterion: otherwise one classical pass is already orthogonal to
+        // working precision)
+        double t[1] = {0};
+        for (int i = 0; i < ne; ++i) t[0] += norm2(vk[i]);
+        cta_reduce<1>(t, sm);
+        if (threadIdx.x == 0) coef[0] = t[0];
+        __syncthreads();
+        const double n_mid = coef[0];
+        __syncthreads();
+        if (n_mid > 0.5 * n0) break;
       }
-    double n1 = 0;
-    for (i = 0; i < ne; ++i) n1 += norm2(vk[i]);
-    gs_bcast_reduce2(n1, dummy, sm);
+      // c_j = <v_j, v_k> for all j < k, kGsChunk at a time
+      for (int j0 = 0; j0 < k; j0 += kGsChunk) {
+        double t[2 * kGsChunk];
+#pragma unroll
+        for (int q = 0; q < 2 * kGsChunk; ++q) t[q] = 0.0;
+#pragma unroll
+        for (int q = 0; q < kGsChunk; ++q) {
+          const int j = j0 + q;
+          if (j < k)
+            for (int i = 0; i < ne; ++i) {
+              const cd a = base[fs * j + off[i]];
+              t[2 * q] += a.re * vk[i].re + a.im * vk[i].im;
+              t[2 * q + 1] += a.re * vk[i].im - a.im * vk[i].re;
+            }
+        }
+        cta_reduce<2 * kGsChunk>(t, sm);
+        if (threadIdx.x == 0)
+          for (int q = 0; q < 2 * kGsChunk && 2 * j0 + q < 2 * 128; ++q) coef[2 * j0 + q] = t[q];
+        __syncthreads();
+      }
+      for (int j = 0; j < k; ++j) {
+        const cd cj{coef[2 * j], coef[2 * j + 1]};
+        for (int i = 0; i < ne; ++i) vk[i] = vk[i] - cj * base[fs * j + off[i]];
+      }
+      __syncthreads();
+    }
+    double n1;
+    {
+      double t[1] = {0};
+      for (int i = 0; i < ne; ++i) t[0] += norm2(vk[i]);
+      cta_reduce<1>(t, sm);
+      if (threadIdx.x == 0) coef[0] = t[0];
+      __syncthreads();
+      n1 = coef[0];
+      __syncthreads();
+    }
     if (!(n1 > 1e-20 * n0) || !(n0 > 0.0)) {
       if (threadIdx.x == 0) atomicExch(rank_flag, 1);
       n1 = 1.0;
     }
     const double inv = 1.0 / sqrt(n1);
-    for (i = 0; i < ne; ++i) *ptr[i] = inv * vk[i];
+    for (int i = 0; i < ne; ++i) base[fs * k + off[i]] = inv * vk[i];
     __syncthreads();
   }
 }
