@@ -105,12 +105,12 @@ void wmg_default_params(wmg_params* p) {
   p->gcr_restart = 16;
   p->cycle_gamma = 1;
   p->tol = 1e-10;
-  p->coarse_tol = 1e-4;
+  p->coarse_tol = 5e-3;
   p->coarse_maxit = 2000;
   p->max_iter = 1000;
   p->prec_sloppy = WMG_PREC_SINGLE;
   p->coarse_tc = 1;
-  p->reliable_delta = 0.01;
+  p->reliable_delta = 1e-3;
   p->seed = 20091212ULL;
 }
 

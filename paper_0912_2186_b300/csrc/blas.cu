@@ -6,10 +6,13 @@
 
 namespace wmg {
 
-constexpr int kBlasMaxBlocks = 148 * 8;
+constexpr int kBlasMaxBlocks = 148 * 2;
+constexpr int kBlasPerThread = 16;
 
+// CTAs per right-hand side: a function of the vector length only (so that every right-hand
+// side is reduced in the same order whatever the batch), each thread streaming >= 16 elements
 int blas_blocks(size_t n) {
-  size_t b = (n + kBlasThreads - 1) / kBlasThreads;
+  size_t b = (n + (size_t)kBlasThreads * kBlasPerThread - 1) / ((size_t)kBlasThreads * kBlasPerThread);
   if (b > (size_t)kBlasMaxBlocks) b = kBlasMaxBlocks;
   return b < 1 ? 1 : (int)b;
 }

@@ -667,7 +667,10 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
       if (!active[r]) continue;
       ++iters[r];
       const double rn = std::sqrt(std::max(rn2[r], 0.0));
-      if (rn <= tol * bnorm[r] || rn < delta * ref[r] || k == m || iters[r] >= c->prm.max_iter || !(rn == rn))
+      // reliable update: residual dropped by delta, apparent convergence, iteration cap, or (FP64
+      // outer solver only, as in the plain restarted method) the end of a restart cycle
+      const bool restart_check = (k == m) && lo == WMG_PREC_DOUBLE;
+      if (rn <= tol * bnorm[r] || rn < delta * ref[r] || restart_check || iters[r] >= c->prm.max_iter || !(rn == rn))
         rel[r] = 1;
       anyrel = anyrel || rel[r];
     }

@@ -183,8 +183,9 @@ struct RedBuf {
   double* result;     // [nrhs][nval]
 };
 
-// Reduce NVAL doubles across the CTA (blockDim.x a multiple of 32, <= 1024); the result
-// is valid in thread 0.  Fixed summation order.
+// Reduce NVAL doubles across the CTA (blockDim.x a multiple of 32, <= 1024); the result is
+// valid in thread 0.  Fixed summation order: shuffle tree within each warp, then the warps in
+// index order (thread i combines value i).
 template <int NVAL>
 WMG_D void cta_reduce(double v[NVAL], double* smem /* >= 32*NVAL */) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -196,14 +197,16 @@ WMG_D void cta_reduce(double v[NVAL], double* smem /* >= 32*NVAL */) {
 #pragma unroll
     for (int i = 0; i < NVAL; ++i) smem[warp * NVAL + i] = v[i];
   __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int i = 0; i < NVAL; ++i) {
-      double s = 0.0;
-      for (int w = 0; w < nw; ++w) s += smem[w * NVAL + i];
-      v[i] = s;
-    }
+  double tot = 0.0;
+  if (threadIdx.x < NVAL) {
+    for (int w = 0; w < nw; ++w) tot += smem[w * NVAL + threadIdx.x];
   }
+  __syncthreads();
+  if (threadIdx.x < NVAL) smem[threadIdx.x] = tot;
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int i = 0; i < NVAL; ++i) v[i] = smem[i];
   __syncthreads();
 }
 
