@@ -356,6 +356,11 @@ def run_gpu(args, w):
                 json.dump({"workload": args.workload, "counts": counts,
                            "note": "operator applications per step measured by bench.py --record-counts"}, f, indent=1)
 
+    serving = None
+    if rank == 0 and not args.no_serving:
+        ctx.close()
+        torch.cuda.empty_cache()
+        serving = run_serving(wmg, masses)
     if rank != 0:
         return
     out = {
@@ -379,11 +384,86 @@ def run_gpu(args, w):
         "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "cpu_baseline": cpu,
+        "serving": serving,
         "clocks": clk,
     }
     print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------
+# serving: 200 seeded Poisson arrivals over three resident fields (continuous batching)
+# ------------------------------------------------------------------------------------------
+SERVING_FIELDS = [
+    dict(dims=(8, 8, 8, 8), eps=0.4, gauge_seed=21, nvec=[8], block=[(4, 4, 4, 4)], masses=[0.05]),
+    dict(dims=(16, 16, 16, 32), eps=0.6, gauge_seed=11, nvec=[24], block=[(4, 4, 4, 4)], masses=None),
+    dict(dims=(24, 24, 24, 48), eps=0.7, gauge_seed=31, nvec=[24, 32], block=[(4, 4, 4, 4), (2, 2, 2, 2)],
+         masses=[-1.15, -1.2, -1.25]),
+]
+
+
+def run_serving(wmg, masses16, nreq=200, seed=2009, slots=12):
+    import threading
+    fields = []
+    srv = wmg.Server(hbm_budget_bytes=240 << 30)
+    for f in SERVING_FIELDS:
+        ms = f["masses"] or masses16
+        U = synth.gauge_field(f["dims"], f["eps"], f["gauge_seed"])
+        ctx = wmg.Context(f["dims"])
+        ctx.load_gauge(U)
+        ctx.set_mass(ms[-1])  # the hierarchy is built at the field's lightest mass
+        p = wmg.default_params(nlevels=len(f["nvec"]) + 1, nvec=f["nvec"], block=f["block"],
+                               prec_sloppy=wmg.PREC_SINGLE)
+        ctx.setup(p)
+        fid = srv.add_field(ctx, slots)
+        fields.append((fid, f["dims"], ms))
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(nreq):
+        fi = int(rng.integers(0, len(fields)))
+        fid, dims, ms = fields[fi]
+        reqs.append((fid, float(ms[int(rng.integers(0, len(ms)))]), synth.gaussian_spinors(dims, int(rng.integers(1, 13)),
+                                                                                        10_000 + i)))
+    # capacity: the first 12 requests back to back
+    t0 = time.perf_counter()
+    warm = []
+    for fid, m, b in reqs[:12]:
+        x = np.zeros_like(b)
+        warm.append(srv.submit(fid, m, b, x))
+    for t in warm:
+        srv.wait(t)
+    cap_rhs = sum(b.shape[0] for _, _, b in reqs[:12]) / (time.perf_counter() - t0)
+    mean_rhs = np.mean([b.shape[0] for _, _, b in reqs])
+    rate = 0.75 * cap_rhs / mean_rhs                     # requests per second
+    gaps = rng.exponential(1.0 / rate, size=nreq)
+    xs = [np.zeros_like(b) for _, _, b in reqs]
+    tickets = [None] * nreq
+
+    def producer():
+        for i, (fid, m, b) in enumerate(reqs):
+            time.sleep(float(gaps[i]))
+            tickets[i] = srv.submit(fid, m, b, xs[i])
+
+    t0 = time.perf_counter()
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    lat, worst, ok = [], 0.0, True
+    for i, t in enumerate(tickets):
+        st, info, l = srv.wait(t)
+        ok = ok and st == wmg.OK
+        lat.append(l)
+        worst = max(worst, max(x["true_resid"] for x in info))
+    wall = time.perf_counter() - t0
+    srv.close()
+    nrhs_total = sum(b.shape[0] for _, _, b in reqs)
+    return {"requests": nreq, "rhs": int(nrhs_total), "arrival_rate_per_s": rate, "wall_s": wall,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "solves_per_s": nrhs_total / wall, "all_converged": ok, "max_true_resid": worst,
+            "slots_per_field": slots,
+            "fields": ["8^4 eps0.4 N8", "16^3x32 eps0.6 N24 (oracle masses)",
+                       "24^3x48 eps0.7 3-level N24/32 (hand-chosen masses)"]}
 
 
 def main():
@@ -397,6 +477,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--record-counts", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
