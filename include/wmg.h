@@ -102,8 +102,9 @@ typedef struct {
   int prec_sloppy;                   /* precision of the cycle, the hierarchy and the
                                         inner Krylov vectors (WMG_PREC_*)            */
   int coarse_tc;                     /* with prec_sloppy = SINGLE: apply the coarse
-                                        stencils with FP16 tensor-core MMA (FP32
-                                        accumulation) where 2N is 16, 32, 48 or 64     */
+                                        stencils on FP16 tensor cores (FP32
+                                        accumulation) where 2N is 16, 32, 48 or 64:
+                                        1 = mma.sync, 2 = tcgen05 (TMEM accumulator)   */
   double reliable_delta;             /* FP64 reliable update when the iterated
                                         residual fell by this factor                */
   uint64_t seed;                     /* seed of the setup's Gaussian starts when no

@@ -34,6 +34,7 @@ void free_hierarchy(wmg_ctx* c) {
       if (c->L[l].A[p]) cudaFree(c->L[l].A[p]);
       if (p == 0 && c->L[l].A16) cudaFree(c->L[l].A16), c->L[l].A16 = nullptr;
       if (p == 0 && c->L[l].sA) cudaFree(c->L[l].sA), c->L[l].sA = nullptr;
+      if (p == 0 && c->L[l].A05) cudaFree(c->L[l].A05), c->L[l].A05 = nullptr;
       if (c->L[l].P[p]) cudaFree(c->L[l].P[p]);
       c->L[l].A[p] = c->L[l].P[p] = nullptr;
     }
@@ -422,7 +423,10 @@ wmg_status wmg_apply_coarse(wmg_ctx* c, int level, int prec, int dagger, const v
   if (prec == WMG_PREC_HALF && !c->L[level].A16) return WMG_ESTATE;
   TRY(set_rhs_scalars(c, nullptr, nrhs));
   const LevelData& L = c->L[level];
-  if (prec == WMG_PREC_HALF)
+  if (prec == WMG_PREC_HALF && L.A05)
+    coarse_apply_tc05(L.A05, L.sA, L.g, L.ndof, in, out, nrhs, c->d_shift[level], dagger != 0, nullptr, nullptr,
+                      c->stream);
+  else if (prec == WMG_PREC_HALF)
     coarse_apply_mma(L.A16, L.sA, L.g, L.ndof, in, out, nrhs, c->d_shift[level], dagger != 0, nullptr, nullptr,
                      c->stream);
   else

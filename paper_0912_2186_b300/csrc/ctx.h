@@ -26,6 +26,7 @@ struct LevelData {
   void* A[2] = {nullptr, nullptr};
   void* A16 = nullptr;     // FP16 fragment-order copy for the tensor-core apply (or null)
   float* sA = nullptr;     // its per-site scale
+  void* A05 = nullptr;     // FP16 canonical-layout copy for the tcgen05 apply (or null)
   // transfer to the next level (levels < nlev - 1)
   Blocking bk{};
   void* P[2] = {nullptr, nullptr};  // N fields of this level, per precision (P[0] = FP64)

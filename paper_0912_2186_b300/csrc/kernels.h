@@ -118,6 +118,13 @@ size_t stencil_mma_words(int Vc, int n);  // uint4 words of the fragment-order c
 void stencil_to_mma(int prec, const void* A, int Vc, int n, float* scale, void* out, cudaStream_t s);
 void coarse_apply_mma(const void* A16, const float* sA, const Geom& g, int n, const void* in, void* out, int nrhs,
                       const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s);
+// tcgen05 tensor-core copy of a stencil and its application (coarse_tc05.cu)
+size_t stencil_tc05_halves(int Vc, int n);
+bool coarse_tc05_supported(int n);
+void stencil_to_tc05(int prec, const void* A, int Vc, int n, const float* scale, void* out, cudaStream_t s);
+void coarse_apply_tc05(const void* A16, const float* sA, const Geom& g, int n, const void* in, void* out, int nrhs,
+                       const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s);
+int coarse_tc05_error();  // 1 if a bounded tcgen05 wait ever expired (synchronises)
 // convert a stencil between precisions
 void stencil_convert(int prec_d, void* dst, int prec_s, const void* src, size_t count, cudaStream_t s);
 

@@ -208,7 +208,9 @@ static int nact_of(const wmg_ctx* c, const int* active, int nrhs) { return activ
 void coarse_op(wmg_ctx* c, int l, int prec, const void* in, void* out, int nrhs, bool dagger, const int* active,
                const RedBuf* rb) {
   const LevelData& L = c->L[l];
-  if (prec == WMG_PREC_SINGLE && L.A16)
+  if (prec == WMG_PREC_SINGLE && L.A05)
+    coarse_apply_tc05(L.A05, L.sA, L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, active, rb, c->stream);
+  else if (prec == WMG_PREC_SINGLE && L.A16)
     coarse_apply_mma(L.A16, L.sA, L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, active, rb, c->stream);
   else
     coarse_apply(prec, L.A[prec], L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, active, rb, c->stream);
@@ -487,6 +489,10 @@ wmg_status galerkin(wmg_ctx* c, int l, int prec) {
     if (!C.A16) CU(c, cudaMalloc(&C.A16, stencil_mma_words(C.g.V, n) * 16));
     if (!C.sA) CU(c, cudaMalloc((void**)&C.sA, C.g.V * sizeof(float)));
     stencil_to_mma(WMG_PREC_SINGLE, C.A[1], C.g.V, n, C.sA, C.A16, c->stream);
+    if (c->prm.coarse_tc == 2 && coarse_tc05_supported(n)) {
+      if (!C.A05) CU(c, cudaMalloc(&C.A05, stencil_tc05_halves(C.g.V, n) * 2));
+      stencil_to_tc05(WMG_PREC_SINGLE, C.A[1], C.g.V, n, C.sA, C.A05, c->stream);
+    }
   }
   return check(c, "galerkin");
 }

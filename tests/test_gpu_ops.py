@@ -59,12 +59,12 @@ def test_dslash_parity(W, prec, dims):
     assert rel_err(got, want) < TOL[prec]
 
 
-def _hier(W, dims, blocks, nvecs, prec, seed=10, m=-0.1, eps=0.6):
+def _hier(W, dims, blocks, nvecs, prec, seed=10, m=-0.1, eps=0.6, tc=1):
     U = synth.gauge_field(dims, eps, seed)
     ctx = W.Context(dims)
     ctx.load_gauge(U)
     ctx.set_mass(m)
-    p = W.default_params(nlevels=len(blocks) + 1, block=blocks, nvec=nvecs, prec_sloppy=prec)
+    p = W.default_params(nlevels=len(blocks) + 1, block=blocks, nvec=nvecs, prec_sloppy=prec, coarse_tc=tc)
     v0 = synth.setup_starts(dims, nvecs[0], seed + 1)
     ctx.import_nullvecs(0, v0, p)
     op = mg.WilsonOp(U, m)
@@ -158,10 +158,13 @@ def test_mass_shift_on_coarse_levels(W):
     assert rel_err(host(out), want.reshape(2, -1)) < 1e-12
 
 
-@pytest.mark.parametrize("dims,block,N", [((8, 8, 8, 8), (2, 2, 2, 2), 8), ((8, 8, 8, 12), (4, 4, 4, 4), 24)])
-def test_tensor_core_coarse_apply(W, dims, block, N):
-    """FP16 tensor-core coarse stencil (2N = 16, 48) against the oracle, FP16 tolerance 2e-3."""
-    h = _hier(W, dims, [block], [N], 1)
+@pytest.mark.parametrize("tc", [1, 2])
+@pytest.mark.parametrize("dims,block,N", [((8, 8, 8, 8), (2, 2, 2, 2), 8), ((8, 8, 8, 12), (4, 4, 4, 4), 24),
+                                          ((8, 8, 8, 8), (2, 2, 2, 2), 32)])
+def test_tensor_core_coarse_apply(W, dims, block, N, tc):
+    """FP16 tensor-core coarse stencil (2N = 16, 48, 64; tc 1 = mma.sync, 2 = tcgen05 with a TMEM
+    accumulator) against the oracle, FP16 tolerance 2e-3."""
+    h = _hier(W, dims, [block], [N], 1, tc=tc)
     ctx, A1 = h["ctx"], h["A"][1]
     nrhs = 13                                    # two chunks of the 16-rhs kernel, ragged
     phi = synth.coarse_starts(A1.dims, A1.n, nrhs, 60)

@@ -112,3 +112,15 @@ def test_three_level_solve(W):
     xs = host(x)
     for r in range(2):
         assert oracle_resid(U, cfg["m"], b[r], xs[r]) <= 1.05e-10
+
+
+def test_tcgen05_coarse_solve(W):
+    """The mixed-precision solve with the coarse stencil on tcgen05 tensor cores."""
+    ctx, U, p = _ctx(W, CFG1, 1, coarse_tc=2)
+    b = synth.gaussian_spinors(CFG1["dims"], 3, 16)
+    x = dev(np.zeros_like(b))
+    st, info = ctx.solve(dev(b), x, 3)
+    xs = host(x)
+    for r in range(3):
+        assert info[r]["converged"]
+        assert oracle_resid(U, CFG1["m"], b[r], xs[r]) <= 1.05e-10
