@@ -74,7 +74,7 @@ def shifted_hierarchy(H, m):
     return Hm
 
 
-def lambda_min(H, v0, tol=1e-10, eig_tol=1e-4, log=None):
+def lambda_min(H, v0, tol=1e-10, eig_tol=1e-3, log=None):
     """Smallest eigenvalue of D^dag D (D = H.ops[0]) and its eigenvector, by Lanczos on
     (D^dag D)^-1 applied with MG-GCR solves."""
     shape = v0.shape
@@ -89,7 +89,7 @@ def lambda_min(H, v0, tol=1e-10, eig_tol=1e-4, log=None):
 
     n = v0.size
     Op = sla.LinearOperator((n, n), matvec=matvec, dtype=np.complex128)
-    vals, vecs = sla.eigsh(Op, k=1, which="LA", v0=v0.ravel(), tol=eig_tol, ncv=8)
+    vals, vecs = sla.eigsh(Op, k=1, which="LA", v0=v0.ravel(), tol=eig_tol, ncv=12)
     lam = 1.0 / float(vals[0])
     if log:
         log(f"    Lanczos: lambda_min = {lam:.6e} ({nsolve[0]} MG solves)")
