@@ -10,6 +10,25 @@
 
 namespace wmg {
 
+// 16-byte asynchronous global -> shared copies (Ampere-style cp.async; completion per group)
+WMG_D void cp_async16(void* dst_smem, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
+               "l"(src)
+               : "memory");
+}
+WMG_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> WMG_D void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+// two consecutive complex numbers from shared memory (16-byte aligned for float)
+WMG_D void lds2(const cpx<float>* p, cpx<float>& a, cpx<float>& b) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  a = {t.x, t.y};
+  b = {t.z, t.w};
+}
+WMG_D void lds2(const cpx<double>* p, cpx<double>& a, cpx<double>& b) {
+  a = p[0];
+  b = p[1];
+}
+
 WMG_D int block_site(const Blocking& bk, int xc, int e) {
   int c[4];
   site_coords(bk.coarse, xc, c);
@@ -134,6 +153,238 @@ __global__ void k_prolong_fine(const void* __restrict__ P, Blocking bk, const vo
     }
   }
 }
+
+// ------------------------------------------------------------------------------------
+// Fine-level transfer, one thread per (block site, component pair c): all RC right-hand sides
+// of the launch chunk are held in registers, so P is read once per launch with one
+// coalesced 2-complex load per vector alpha.
+//   prolong: CTA per (coarse site, pair c); psi_r(x)[2c..2c+1] = sum_alpha P_alpha(x)[..] phi_r
+//   restrict: CTA per (coarse site, chirality s) covering the 3 pairs of s; per (pair, alpha)
+//            the products are summed by warp shuffles and accumulated per warp in shared
+//            memory, then over warps in order (fixed summation order).
+// ------------------------------------------------------------------------------------
+// Prolong: CTA per (coarse site, component pair c), thread per block site holding all RC
+// right-hand sides; the thread's P entries stream through a kPSt-deep cp.async ring in shared
+// memory (each thread reads back only its own copies, so no block barrier is needed).
+constexpr int kPSt = 6;
+template <typename R, int RC>
+__global__ void __launch_bounds__(256) k_prolong_fine3(const void* __restrict__ P, Blocking bk,
+                                                       const void* __restrict__ in, void* __restrict__ out, int nrhs,
+                                                       const int* __restrict__ active) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int CB = 2 * sizeof(cpx<R>);  // bytes of one component pair
+  const int xc = blockIdx.x, c = blockIdx.y, r0 = blockIdx.z * RC;
+  const int N = bk.N, V = bk.fine.V, s = c / 3, T = blockDim.x;
+  cpx<R>* phi = reinterpret_cast<cpx<R>*>(smraw);  // [N][RC]
+  unsigned char* ring = smraw + (((size_t)N * RC * sizeof(cpx<R>) + 15) / 16) * 16;  // [kPSt][T][CB]
+  const size_t fb = spinor_field_bytes<R>(V);
+  const int e = threadIdx.x;
+  const bool live = e < bk.bs;
+  const int v = live ? block_site(bk, xc, e) : 0;
+  const char* src = (const char*)P + ((size_t)c * V + v) * CB;
+  auto issue = [&](int a) {
+    if (live && a < N)
+#pragma unroll
+      for (int q = 0; q < CB / 16; ++q) cp_async16(ring + ((size_t)(a % kPSt) * T + e) * CB + 16 * q, src + fb * a + 16 * q);
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int a = 0; a < kPSt - 1; ++a) issue(a);
+  for (int i = threadIdx.x; i < RC * N; i += T) {
+    const int a = i / RC, rr = i - a * RC, r = r0 + rr;
+    phi[i] = (r < nrhs) ? reinterpret_cast<const cpx<R>*>(in)[((size_t)r * bk.coarse.V + xc) * 2 * N + s * N + a]
+                        : cpx<R>{R(0), R(0)};
+  }
+  __syncthreads();
+  cpx<R> acc[RC][2];
+#pragma unroll
+  for (int rr = 0; rr < RC; ++rr) acc[rr][0] = acc[rr][1] = cpx<R>{R(0), R(0)};
+  for (int a = 0; a < N; ++a) {
+    cp_async_wait<kPSt - 2>();
+    cpx<R> p0, p1;
+    lds2(reinterpret_cast<const cpx<R>*>(ring + ((size_t)(a % kPSt) * T + e) * CB), p0, p1);
+    issue(a + kPSt - 1);
+#pragma unroll
+    for (int rr = 0; rr < RC; rr += 2) {
+      cpx<R> f0, f1;
+      lds2(phi + (size_t)a * RC + rr, f0, f1);
+      cfma(acc[rr][0], p0, f0);
+      cfma(acc[rr][1], p1, f0);
+      cfma(acc[rr + 1][0], p0, f1);
+      cfma(acc[rr + 1][1], p1, f1);
+    }
+  }
+  cp_async_wait<0>();
+  if (!live) return;
+#pragma unroll
+  for (int rr = 0; rr < RC; ++rr) {
+    const int r = r0 + rr;
+    if (r < nrhs && (!active || active[r])) Chunk2<R>::store((char*)out + fb * r, (size_t)c * V + v, acc[rr][0], acc[rr][1]);
+  }
+}
+
+// Restrict as a per-block complex GEMM  out[alpha][r] = sum_k conj(P[k][alpha]) x[k][r], k running
+// over the block's sites x the 6 components of chirality s.  The block is streamed in chunks
+// of S sites through a double-buffered cp.async stage in shared memory (P rows and x rows with
+// k contiguous); warp w owns a fixed slice of every chunk's k range, lane (ag, rg) =
+// (lane / 4, lane % 4) owns the TA x TR output tile alpha = ag*TA + i, r = rg*TR + j.  Warp
+// partials are summed in warp order at the end, so the result for one right-hand side does not
+// depend on the others or on TR.
+constexpr int kRWarps = 8;  // warps of the restrict CTA
+template <typename R, int TA, int TR, int S>
+__global__ void __launch_bounds__(kRWarps * 32) k_restrict_fine3(const void* __restrict__ P, Blocking bk,
+                                                                 const void* __restrict__ in, void* __restrict__ out,
+                                                                 int nrhs, const int* __restrict__ active) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int NA = 8 * TA, RC = 4 * TR;
+  constexpr int CB = 2 * sizeof(cpx<R>);
+  constexpr int K = 6 * S, Kp = K + 2;            // complex k per chunk, padded row length
+  constexpr int KW = ((K / 2 + kRWarps - 1) / kRWarps) * 2;  // even k slice per warp
+  constexpr int NT = kRWarps * 32, CE = 3 * S;    // threads; (component pair, site) items per row
+  constexpr int RSTEP = NT / CE;                  // rows staged per pass of the CTA
+  constexpr size_t stage = (size_t)(NA + RC) * Kp;  // complex per stage buffer
+  const int xc = blockIdx.x, s = blockIdx.y, r0 = blockIdx.z * RC;
+  const int N = bk.N, V = bk.fine.V, bs = bk.bs;
+  cpx<R>* buf = reinterpret_cast<cpx<R>*>(smraw);  // [2][NA + RC][Kp]: P rows, then x rows
+  int* vsite = reinterpret_cast<int*>(buf + 2 * stage);  // [bs] fine site of each block site
+  const size_t fb = spinor_field_bytes<R>(V);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, ag = lane >> 2, rg = lane & 3;
+  const int kb = warp * KW, ke = min(K, kb + KW);
+  unsigned rmask = 0;  // right-hand sides of this chunk that are present and active
+  for (int j = 0; j < RC; ++j)
+    if (r0 + j < nrhs && (!active || active[r0 + j])) rmask |= 1u << j;
+  for (int e = threadIdx.x; e < bs; e += NT) vsite[e] = block_site(bk, xc, e);
+  // P rows alpha >= N stay zero in both buffers
+  for (int i = threadIdx.x; i < (NA - N) * Kp; i += NT) {
+    buf[(size_t)N * Kp + i] = cpx<R>{R(0), R(0)};
+    buf[stage + (size_t)N * Kp + i] = cpx<R>{R(0), R(0)};
+  }
+  __syncthreads();
+  // this thread stages item (cc, e) of rows row0, row0 + RSTEP, ...
+  const int item = threadIdx.x % CE, row0 = threadIdx.x / CE, cc = item / S, e = item % S;
+  const size_t coff = (size_t)(3 * s + cc) * V;
+  const int nchunks = (bs + S - 1) / S;
+  auto issue = [&](int q) {
+    if (q < nchunks && row0 < RSTEP) {
+      cpx<R>* st = buf + (size_t)(q & 1) * stage + (cc * S + e) * 2;
+      const bool in_blk = q * S + e < bs;
+      const size_t off = (coff + (in_blk ? vsite[q * S + e] : 0)) * CB;
+      for (int row = row0; row < N + RC; row += RSTEP) {
+        const bool isP = row < N;
+        cpx<R>* dst = st + (size_t)(isP ? row : NA + row - N) * Kp;
+        if (in_blk && (isP || ((rmask >> (row - N)) & 1u))) {
+          const char* src = (const char*)(isP ? P : in) + fb * (isP ? row : r0 + row - N) + off;
+#pragma unroll
+          for (int h = 0; h < CB / 16; ++h) cp_async16((char*)dst + 16 * h, src + 16 * h);
+        } else {
+          dst[0] = dst[1] = cpx<R>{R(0), R(0)};
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  cpx<R> acc[TA][TR];
+#pragma unroll
+  for (int i = 0; i < TA; ++i)
+#pragma unroll
+    for (int j = 0; j < TR; ++j) acc[i][j] = cpx<R>{R(0), R(0)};
+  issue(0);
+  for (int q = 0; q < nchunks; ++q) {
+    issue(q + 1);
+    cp_async_wait<1>();
+    __syncthreads();
+    const cpx<R>* Ps = buf + (size_t)(q & 1) * stage;
+    const cpx<R>* Xs = Ps + (size_t)NA * Kp;
+#pragma unroll 2
+    for (int k = kb; k < ke; k += 2) {
+      cpx<R> p[TA][2], x[TR][2];
+#pragma unroll
+      for (int i = 0; i < TA; ++i) lds2(Ps + (size_t)(ag * TA + i) * Kp + k, p[i][0], p[i][1]);
+#pragma unroll
+      for (int j = 0; j < TR; ++j) lds2(Xs + (size_t)(rg * TR + j) * Kp + k, x[j][0], x[j][1]);
+#pragma unroll
+      for (int i = 0; i < TA; ++i)
+#pragma unroll
+        for (int j = 0; j < TR; ++j) {
+          cfmac(acc[i][j], p[i][0], x[j][0]);
+          cfmac(acc[i][j], p[i][1], x[j][1]);
+        }
+    }
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+  cpx<R>* red = buf;  // [warp][NA][RC]
+#pragma unroll
+  for (int i = 0; i < TA; ++i)
+#pragma unroll
+    for (int j = 0; j < TR; ++j) red[((size_t)warp * NA + ag * TA + i) * RC + rg * TR + j] = acc[i][j];
+  __syncthreads();
+  for (int i = threadIdx.x; i < N * RC; i += NT) {
+    const int a = i / RC, j = i - a * RC;
+    if (!((rmask >> j) & 1u)) continue;
+    cpx<R> t = red[(size_t)a * RC + j];
+    for (int w = 1; w < kRWarps; ++w) t += red[((size_t)w * NA + a) * RC + j];
+    reinterpret_cast<cpx<R>*>(out)[((size_t)(r0 + j) * bk.coarse.V + xc) * 2 * N + s * N + a] = t;
+  }
+}
+
+template <typename R, int TA, int TR, int S>
+static void launch_restrict_fine3s(const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
+                                   const int* active, cudaStream_t s) {
+  constexpr int NA = 8 * TA, RC = 4 * TR;
+  const size_t redb = (size_t)kRWarps * NA * RC * sizeof(cpx<R>);
+  const size_t stage = 2 * (size_t)(NA + RC) * (6 * S + 2) * sizeof(cpx<R>) + (size_t)bk.bs * sizeof(int);
+  const size_t smem = stage > redb ? stage : redb;
+  static const cudaError_t attr = cudaFuncSetAttribute(k_restrict_fine3<R, TA, TR, S>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  (void)attr;
+  dim3 g(bk.coarse.V, 2, (nrhs + RC - 1) / RC);
+  k_restrict_fine3<R, TA, TR, S><<<g, kRWarps * 32, smem, s>>>(P, bk, in, out, nrhs, active);
+}
+
+// sites per staged chunk: 16, or 8 when two 16-site stages would not fit in shared memory
+template <typename R, int TA, int TR>
+static void launch_restrict_fine3(const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
+                                  const int* active, cudaStream_t s) {
+  constexpr size_t big = 2 * (size_t)(8 * TA + 4 * TR) * (6 * 16 + 2) * sizeof(cpx<R>);
+  if (big + (size_t)bk.bs * sizeof(int) <= 200 * 1024)
+    launch_restrict_fine3s<R, TA, TR, 16>(P, bk, in, out, nrhs, active, s);
+  else
+    launch_restrict_fine3s<R, TA, TR, 8>(P, bk, in, out, nrhs, active, s);
+}
+
+template <typename R, int TA>
+static void restrict_fine3_tr(const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
+                              const int* active, cudaStream_t s) {
+  if (nrhs <= 4) launch_restrict_fine3<R, TA, 1>(P, bk, in, out, nrhs, active, s);
+  else if (nrhs <= 8) launch_restrict_fine3<R, TA, 2>(P, bk, in, out, nrhs, active, s);
+  else launch_restrict_fine3<R, TA, 3>(P, bk, in, out, nrhs, active, s);
+}
+
+template <typename R>
+static void restrict_fine3(const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
+                           const int* active, cudaStream_t s) {
+  const int ta = (bk.N + 7) / 8;
+  if (ta <= 1) restrict_fine3_tr<R, 1>(P, bk, in, out, nrhs, active, s);
+  else if (ta <= 2) restrict_fine3_tr<R, 2>(P, bk, in, out, nrhs, active, s);
+  else if (ta <= 3) restrict_fine3_tr<R, 3>(P, bk, in, out, nrhs, active, s);
+  else if (ta <= 4) restrict_fine3_tr<R, 4>(P, bk, in, out, nrhs, active, s);
+  else if (ta <= 6) restrict_fine3_tr<R, 6>(P, bk, in, out, nrhs, active, s);
+  else restrict_fine3_tr<R, 8>(P, bk, in, out, nrhs, active, s);
+}
+
+template <typename R, int RC>
+static void launch_prolong_fine3(const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
+                                 const int* active, cudaStream_t s) {
+  dim3 g(bk.coarse.V, 6, (nrhs + RC - 1) / RC);
+  const int T = ((bk.bs + 31) / 32) * 32;
+  const size_t smem = (((size_t)bk.N * RC * sizeof(cpx<R>) + 15) / 16) * 16 + (size_t)kPSt * T * 2 * sizeof(cpx<R>);
+  static const cudaError_t attr = cudaFuncSetAttribute(k_prolong_fine3<R, RC>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  (void)attr;
+  k_prolong_fine3<R, RC><<<g, T, smem, s>>>(P, bk, in, out, nrhs, active);
+}
+
 
 // ------------------------------------------------------------------------------------
 // restrict / prolong between coarse levels: fields [rhs][Vf][nf] -> [rhs][Vc][2N]
@@ -350,6 +601,11 @@ static void launch_restrict_fine(const void* P, const Blocking& bk, const void* 
 void restrict_fine(int prec, const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
                    const int* active, cudaStream_t s) {
   count_launch();
+  if (bk.N <= 64) {
+    if (prec == WMG_PREC_DOUBLE) restrict_fine3<double>(P, bk, in, out, nrhs, active, s);
+    else restrict_fine3<float>(P, bk, in, out, nrhs, active, s);
+    return;
+  }
   if (prec == WMG_PREC_DOUBLE) {
     if (nrhs == 1) launch_restrict_fine<double, 1>(P, bk, in, out, nrhs, active, s);
     else launch_restrict_fine<double, 2>(P, bk, in, out, nrhs, active, s);
@@ -372,6 +628,18 @@ static void launch_prolong_fine(const void* P, const Blocking& bk, const void* i
 void prolong_fine(int prec, const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
                   const int* active, cudaStream_t s) {
   count_launch();
+  if (bk.bs <= 256 && bk.N <= 64) {
+    if (prec == WMG_PREC_DOUBLE) {
+      if (nrhs <= 2) launch_prolong_fine3<double, 2>(P, bk, in, out, nrhs, active, s);
+      else launch_prolong_fine3<double, 4>(P, bk, in, out, nrhs, active, s);
+    } else {
+      if (nrhs <= 2) launch_prolong_fine3<float, 2>(P, bk, in, out, nrhs, active, s);
+      else if (nrhs <= 4) launch_prolong_fine3<float, 4>(P, bk, in, out, nrhs, active, s);
+      else if (nrhs <= 8) launch_prolong_fine3<float, 8>(P, bk, in, out, nrhs, active, s);
+      else launch_prolong_fine3<float, 12>(P, bk, in, out, nrhs, active, s);
+    }
+    return;
+  }
   if (prec == WMG_PREC_DOUBLE) {
     if (nrhs == 1) launch_prolong_fine<double, 1>(P, bk, in, out, nrhs, active, s);
     else launch_prolong_fine<double, 2>(P, bk, in, out, nrhs, active, s);
