@@ -9,13 +9,17 @@
 //
 // Operands are FP16 with FP32 accumulation (mma.sync m16n8k16): A is stored once per
 // setup in FP16 scaled by a per-site factor s_A (max |Re|, |Im| of the site's blocks) and
-// pre-arranged in fragment order, so each lane loads one 16-byte word per 16 x 16 tile; X
-// is converted in shared memory with a per-(site, rhs) factor s_X.  The result is
+// pre-arranged in fragment order, so each lane reads one 16-byte word per 16 x 16 tile.  The
+// site's fragments (both planes of one row tile are contiguous) arrive in shared memory by
+// bulk asynchronous copies, one per (plane, row tile), completing on one mbarrier per row
+// tile; meanwhile the CTA gathers X and converts it in shared memory with a per-(site, rhs)
+// factor s_X.  The result is
 // rescaled by s_A s_X.  Relative error is about 1e-3 (FP16 operands), enough for the coarse
 // solve of a preconditioner.
 #include <cuda_fp16.h>
 
 #include "kernels.h"
+#include "ptx.cuh"
 
 namespace wmg {
 
@@ -23,6 +27,9 @@ namespace {
 
 constexpr int kKPad = 8;  // halves of padding per staged column (bank-conflict free B loads)
 constexpr int kEPL = 18;  // gathered values per lane: 9n <= 576 (n <= 64)
+constexpr long long kMmaSpinLimit = 1LL << 22;
+
+__device__ int g_mma_error = 0;
 
 WMG_D uint32_t pack_half2(float lo, float hi) {
   __half2 h = __floats2half2_rn(lo, hi);
@@ -95,22 +102,37 @@ __global__ void k_stencil_to_mma(const cpx<R>* __restrict__ A, int n, const floa
 }
 
 // y = A x (+ shift x), optionally sigma_3 A sigma_3 x, for a chunk of up to 8 NT right-hand
-// sides per CTA (grid.y chunks).  One CTA per coarse site, one warp per 16-row tile.
+// sides per CTA (grid.y chunks).  One CTA of 8 warps per coarse site: every warp gathers and
+// converts X for R / 8 right-hand sides; warp w < mt NT then owns row tile m = w / NT and the
+// column block of right-hand sides 8 (w % NT) .. + 7 (its Xr and Xi tiles).
+constexpr int kMmaThreads = 256;
 template <int NT>
-__global__ void __launch_bounds__(128) k_coarse_apply_mma(const uint4* __restrict__ A16, const float* __restrict__ sA,
-                                                          Geom g, int n, const cf* __restrict__ in, cf* __restrict__ out,
-                                                          int nrhs, const double* __restrict__ shift, int dagger,
-                                                          const int* __restrict__ active, RedBuf rb, int want_norm) {
+__global__ void __launch_bounds__(kMmaThreads) k_coarse_apply_mma(const uint4* __restrict__ A16,
+                                                                  const float* __restrict__ sA, Geom g, int n,
+                                                                  const cf* __restrict__ in, cf* __restrict__ out,
+                                                                  int nrhs, const double* __restrict__ shift, int dagger,
+                                                                  const int* __restrict__ active, RedBuf rb,
+                                                                  int want_norm) {
   constexpr int R = 8 * NT;          // right-hand sides per chunk
   constexpr int COLS = 2 * R;        // Xr / Xi columns
-  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int NW = kMmaThreads / 32;
+  extern __shared__ __align__(128) unsigned char smraw[];
   const int K = 9 * n, KP = K + kKPad;
-  __half* xb = reinterpret_cast<__half*>(smraw);                                   // [COLS][KP]
-  float* xmax = reinterpret_cast<float*>(smraw + (size_t)COLS * KP * sizeof(__half));  // [R]
+  const int mt = n / 16, ksteps = K / 16;
+  const uint32_t tile_bytes = (uint32_t)ksteps * 32 * 16;  // one plane of one row tile
+  uint4* As = reinterpret_cast<uint4*>(smraw);                                     // [2][mt][ksteps][32]
+  __half* xb = reinterpret_cast<__half*>(smraw + (size_t)2 * mt * tile_bytes);      // [COLS][KP]
+  float* xmax = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(xb) + (size_t)COLS * KP * sizeof(__half));
+  __shared__ __align__(8) unsigned long long mbar[4];
+  __shared__ int nbs[9];
+  __shared__ double npart[NW][32][2];  // per-lane norm partials of the MMA warps
   const int v = blockIdx.x, r0 = blockIdx.y * R;
   const int N = n / 2;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-  __shared__ int nbs[9];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int m = 0; m < mt; ++m) mbar_init(smem_addr(&mbar[m]), 1);
+    mbar_fence_init();
+  }
   if (threadIdx.x < 9) {
     int c[4];
     site_coords(g, v, c);
@@ -118,6 +140,15 @@ __global__ void __launch_bounds__(128) k_coarse_apply_mma(const uint4* __restric
     nbs[k] = k == 0 ? v : neighbour(g, v, c, (k - 1) >> 1, ((k - 1) & 1) ? -1 : +1);
   }
   __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int m = 0; m < mt; ++m) {
+      const uint32_t bar = smem_addr(&mbar[m]);
+      mbar_arrive_expect_tx(bar, 2 * tile_bytes);
+      for (int p = 0; p < 2; ++p)
+        bulk_g2s(smem_addr(As + (size_t)(p * mt + m) * ksteps * 32),
+                 A16 + (((size_t)v * 2 + p) * mt + m) * ksteps * 32, tile_bytes, bar);
+    }
+  }
   // lane-owned elements e = lane + 32 i of the 9n gathered values (same for every rhs)
   int offs[kEPL];
   unsigned neg = 0;  // bit i: sigma_3 sign flip of element i (adjoint, lower half of the dof)
@@ -133,7 +164,7 @@ __global__ void __launch_bounds__(128) k_coarse_apply_mma(const uint4* __restric
   }
   // one warp per right-hand side: values into registers, max |Re|, |Im| by shuffles, then the
   // scaled FP16 copy in column layout [Xr 0..7 | Xi 0..7 | Xr 8..15 | Xi 8..15]
-  for (int rr = warp; rr < R; rr += nwarp) {
+  for (int rr = warp; rr < R; rr += NW) {
     const int r = r0 + rr;
     const int blk = rr >> 3, cc = rr & 7;
     __half* colr = xb + (size_t)(blk * 16 + cc) * KP;
@@ -162,24 +193,31 @@ __global__ void __launch_bounds__(128) k_coarse_apply_mma(const uint4* __restric
     }
   }
   __syncthreads();
-  const int mt = n / 16, ksteps = K / 16;
   const int gq = lane >> 2, q = lane & 3;
-  float acc[2][2 * NT][4];
+  const bool mma_warp = warp < mt * NT;
+  const int m = warp / NT, blk = warp % NT;
+  float acc[2][2][4];  // [plane Ar / Ai][tile Xr / Xi][fragment]
 #pragma unroll
   for (int p = 0; p < 2; ++p)
 #pragma unroll
-    for (int t = 0; t < 2 * NT; ++t)
+    for (int t = 0; t < 2; ++t)
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[p][t][e] = 0.f;
-  if (warp < mt) {
-    const uint4* Ar = A16 + (((size_t)v * 2 + 0) * mt + warp) * ksteps * 32 + lane;
-    const uint4* Ai = A16 + (((size_t)v * 2 + 1) * mt + warp) * ksteps * 32 + lane;
+  bool ready = true;
+  if (mma_warp) {
+    ready = mbar_wait_bounded(smem_addr(&mbar[m]), 0, kMmaSpinLimit);
+    if (!ready && lane == 0) atomicExch(&g_mma_error, 1);
+  }
+  if (mma_warp && ready) {
+    const uint4* Ar = As + (size_t)(0 * mt + m) * ksteps * 32 + lane;
+    const uint4* Ai = As + (size_t)(1 * mt + m) * ksteps * 32 + lane;
+    const __half* colbase = xb + (size_t)(blk * 16 + gq) * KP + 2 * q;
 #pragma unroll 3
     for (int k = 0; k < ksteps; ++k) {
-      const uint4 ar = __ldg(Ar + (size_t)k * 32), ai = __ldg(Ai + (size_t)k * 32);
+      const uint4 ar = Ar[(size_t)k * 32], ai = Ai[(size_t)k * 32];
 #pragma unroll
-      for (int t = 0; t < 2 * NT; ++t) {
-        const __half* col = xb + (size_t)(t * 8 + gq) * KP + 16 * k + 2 * q;
+      for (int t = 0; t < 2; ++t) {
+        const __half* col = colbase + (size_t)t * 8 * KP + 16 * k;
         const uint32_t b0 = *reinterpret_cast<const uint32_t*>(col);
         const uint32_t b1 = *reinterpret_cast<const uint32_t*>(col + 8);
         mma16816(acc[0][t], ar, b0, b1);
@@ -187,52 +225,61 @@ __global__ void __launch_bounds__(128) k_coarse_apply_mma(const uint4* __restric
       }
     }
   }
-  // epilogue: thread holds rows 16 warp + gq (+8), columns 2q + e of every tile
-  double nv[R];
-#pragma unroll
-  for (int rr = 0; rr < R; ++rr) nv[rr] = 0.0;
-  if (warp < mt) {
+  // epilogue: thread holds rows 16 m + gq (+8) and right-hand sides 8 blk + 2q + (e & 1)
+  double nv2[2] = {0.0, 0.0};
+  if (mma_warp) {
     const float s_a = sA[v];
 #pragma unroll
-    for (int blk = 0; blk < NT; ++blk)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int row = 16 * warp + gq + (e >= 2 ? 8 : 0);
-        const int rr = blk * 8 + 2 * q + (e & 1);
-        const int r = r0 + rr;
-        if (r >= nrhs) continue;
-        // tiles 2 blk (Xr) and 2 blk + 1 (Xi); plane 0 = Ar, 1 = Ai
-        const float yr = acc[0][2 * blk][e] - acc[1][2 * blk + 1][e];
-        const float yi = acc[0][2 * blk + 1][e] + acc[1][2 * blk][e];
-        const float sc = s_a * xmax[rr] * ((dagger && row >= N) ? -1.f : 1.f);
-        cf o{yr * sc, yi * sc};
-        if (shift) o += (float)shift[r] * in[((size_t)r * g.V + v) * n + row];
-        if (!active || active[r]) out[((size_t)r * g.V + v) * n + row] = o;
-        nv[rr] += double(o.re) * o.re + double(o.im) * o.im;
-      }
+    for (int e = 0; e < 4; ++e) {
+      const int row = 16 * m + gq + (e >= 2 ? 8 : 0);
+      const int rr = blk * 8 + 2 * q + (e & 1);
+      const int r = r0 + rr;
+      if (r >= nrhs) continue;
+      // tile 0 = Xr, 1 = Xi; plane 0 = Ar, 1 = Ai
+      const float yr = acc[0][0][e] - acc[1][1][e];
+      const float yi = acc[0][1][e] + acc[1][0][e];
+      const float sc = s_a * xmax[rr] * ((dagger && row >= N) ? -1.f : 1.f);
+      cf o{yr * sc, yi * sc};
+      if (shift) o += (float)shift[r] * in[((size_t)r * g.V + v) * n + row];
+      if (!active || active[r]) out[((size_t)r * g.V + v) * n + row] = o;
+      nv2[e & 1] += double(o.re) * o.re + double(o.im) * o.im;
+    }
   }
+  if (!ready) mbar_wait_bounded(smem_addr(&mbar[m]), 0, kMmaSpinLimit);  // let the copies drain (bounded)
   if (want_norm) {
-    __shared__ double sm[32 * R];
-    cta_reduce<R>(nv, sm);
+    if (mma_warp) {
+      npart[warp][lane][0] = nv2[0];
+      npart[warp][lane][1] = nv2[1];
+    }
+    __syncthreads();
     __shared__ bool last;
     const int nblk = gridDim.x;
-    if (threadIdx.x == 0) {
-      for (int rr = 0; rr < R; ++rr)
-        if (r0 + rr < nrhs) rb.partial[(size_t)(r0 + rr) * nblk + blockIdx.x] = nv[rr];
-      __threadfence();
-      last = atomicAdd(rb.counter + blockIdx.y, 1u) == (unsigned)nblk - 1;
+    if (threadIdx.x < R && r0 + threadIdx.x < nrhs) {
+      // fixed order: row tiles, then the 8 row groups of the fragment
+      const int rr = threadIdx.x, b = rr >> 3, qq = (rr & 7) >> 1, ee = rr & 1;
+      double t = 0.0;
+      for (int mm = 0; mm < mt; ++mm)
+        for (int gg = 0; gg < 8; ++gg) t += npart[mm * NT + b][gg * 4 + qq][ee];
+      rb.partial[(size_t)(r0 + rr) * nblk + blockIdx.x] = t;
     }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(rb.counter + blockIdx.y, 1u) == (unsigned)nblk - 1;
     __syncthreads();
     if (last) {
       __threadfence();
-      __shared__ double sred[32];
-      for (int rr = 0; rr < R && r0 + rr < nrhs; ++rr) {
-        const double s = cta_sum_strided(rb.partial + (size_t)(r0 + rr) * nblk, nblk, 1, sred);
-        if (threadIdx.x == 0) rb.result[r0 + rr] = s;
-      }
+      const int nvals = min(R, nrhs - r0);
+      cta_multi_sum(rb.partial + (size_t)r0 * nblk, nvals, (size_t)nblk, nblk, 1,
+                    [&](int i, double s) { rb.result[r0 + i] = s; });
       if (threadIdx.x == 0) rb.counter[blockIdx.y] = 0u;
     }
   }
+}
+
+int coarse_mma_error() {
+  int e = 0;
+  cudaMemcpyFromSymbol(&e, g_mma_error, sizeof(int));
+  return e;
 }
 
 size_t stencil_mma_words(int Vc, int n) { return (size_t)Vc * 2 * (n / 16) * (9 * n / 16) * 32; }
@@ -252,16 +299,16 @@ template <int NT>
 static void launch_mma(const void* A16, const float* sA, const Geom& g, int n, const void* in, void* out, int nrhs,
                        const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s) {
   constexpr int R = 8 * NT;
-  const size_t smem = (size_t)2 * R * (9 * n + kKPad) * sizeof(__half) + R * sizeof(float);
+  const size_t smem = (size_t)2 * (n / 16) * (9 * n / 16) * 512 + (size_t)2 * R * (9 * n + kKPad) * sizeof(__half) +
+                      R * sizeof(float);
   static const bool attr = [] {
-    cudaFuncSetAttribute(k_coarse_apply_mma<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_coarse_apply_mma<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     return true;
   }();
   (void)attr;
-  const int T = ((n / 16) * 32 + 127) / 128 * 128 > 128 ? 128 : 128;  // up to 4 row tiles (n <= 64)
   dim3 grid(g.V, (nrhs + R - 1) / R);
   RedBuf r = rb ? *rb : RedBuf{nullptr, nullptr, nullptr};
-  k_coarse_apply_mma<NT><<<grid, T, smem, s>>>((const uint4*)A16, sA, g, n, (const cf*)in, (cf*)out, nrhs, shift,
+  k_coarse_apply_mma<NT><<<grid, kMmaThreads, smem, s>>>((const uint4*)A16, sA, g, n, (const cf*)in, (cf*)out, nrhs, shift,
                                                dagger ? 1 : 0, active, r, rb ? 1 : 0);
 }
 

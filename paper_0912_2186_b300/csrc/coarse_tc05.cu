@@ -245,11 +245,9 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc05(const uint4* __restri
     __syncthreads();
     if (last) {
       __threadfence();
-      __shared__ double sred[32];
-      for (int rr = 0; rr < kTcRhs && r0 + rr < nrhs; ++rr) {
-        const double s = cta_sum_strided(rb.partial + (size_t)(r0 + rr) * nblk, nblk, 1, sred);
-        if (threadIdx.x == 0) rb.result[r0 + rr] = s;
-      }
+      const int nvals = min(kTcRhs, nrhs - r0);
+      cta_multi_sum(rb.partial + (size_t)r0 * nblk, nvals, (size_t)nblk, nblk, 1,
+                    [&](int i, double s) { rb.result[r0 + i] = s; });
       if (threadIdx.x == 0) rb.counter[blockIdx.y] = 0u;
     }
   }

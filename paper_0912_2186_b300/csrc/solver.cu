@@ -719,6 +719,10 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
     }
   }
   CU(c, cudaStreamSynchronize(s));
+  if (use_mg && (coarse_mma_error() || coarse_tc05_error())) {
+    c->err = "a bounded wait of the tensor-core coarse stencil expired";
+    return WMG_ETIMEOUT;
+  }
   return WMG_OK;
 }
 

@@ -78,6 +78,22 @@ struct Geom {
   int V;
 };
 
+// n / d for 0 <= n < 2^31 by multiply-high and shift (Granlund & Montgomery 1994, the
+// round-up multiplier with the extra add): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// q = (mulhi(n, m) + n) >> l.
+struct FastDiv {
+  uint32_t d, m, l;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  f.l = 0;
+  while ((1ull << f.l) < d) ++f.l;
+  f.m = (uint32_t)((((1ull << 32) * ((1ull << f.l) - d)) / d) + 1);
+  return f;
+}
+WMG_D uint32_t fdiv(uint32_t n, const FastDiv& f) { return (__umulhi(n, f.m) + n) >> f.l; }
+
 inline Geom make_geom(const int d[4]) {
   Geom g;
   for (int i = 0; i < 4; ++i) g.L[i] = d[i];
@@ -219,12 +235,28 @@ WMG_D double cta_sum_strided(const volatile double* p, int count, int stride, do
   return s[0];
 }
 
+// Sums of nval rows of partials at once: value i is sum_b p[i * istride + b * bstride], b < count.
+// Warp w takes values w, w + nwarps, ...; lane l adds b = l, l + 32, ... in order, then a fixed
+// xor-shuffle tree; lane 0 hands (i, sum) to `store`.  The order depends on count only.
+template <typename F>
+WMG_D void cta_multi_sum(const volatile double* p, int nval, size_t istride, int count, size_t bstride, F store) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < nval; i += nw) {
+    double s = 0.0;
+    for (int b = lane; b < count; b += 32) s += p[i * istride + (size_t)b * bstride];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) store(i, s);
+  }
+}
+
 // After cta_reduce (thread 0 holds v): writes the CTA's partials; the last CTA for `rhs`
-// sums all partials (fixed order, whole CTA) into rb.result.  nblk = CTAs per rhs.
+// sums all partials (fixed order, whole CTA, all values in parallel) into rb.result.
+// nblk = CTAs per rhs.  May be called several times in a row by one CTA.
 template <int NVAL>
 WMG_D void grid_finish(const RedBuf& rb, int rhs, int blk, int nblk, const double v[NVAL]) {
   __shared__ bool last;
-  __shared__ double sred[32];
+  __syncthreads();  // `last` of a previous call has been read by every thread
   if (threadIdx.x == 0) {
     double* p = rb.partial + ((size_t)rhs * nblk + blk) * NVAL;
 #pragma unroll
@@ -237,10 +269,8 @@ WMG_D void grid_finish(const RedBuf& rb, int rhs, int blk, int nblk, const doubl
   if (last) {
     __threadfence();
     const volatile double* p = rb.partial + (size_t)rhs * nblk * NVAL;
-    for (int i = 0; i < NVAL; ++i) {
-      const double s = cta_sum_strided(p + i, nblk, NVAL, sred);
-      if (threadIdx.x == 0) rb.result[(size_t)rhs * NVAL + i] = s;
-    }
+    double* res = rb.result + (size_t)rhs * NVAL;
+    cta_multi_sum(p, NVAL, 1, nblk, NVAL, [&](int i, double s) { res[i] = s; });
     if (threadIdx.x == 0) rb.counter[rhs] = 0u;
   }
 }
