@@ -7,10 +7,11 @@
 namespace wmg {
 
 constexpr int kBlasMaxBlocks = 148 * 2;
-constexpr int kBlasPerThread = 16;
+constexpr int kBlasPerThread = 4;
 
 // CTAs per right-hand side: a function of the vector length only (so that every right-hand
-// side is reduced in the same order whatever the batch), each thread streaming >= 16 elements
+// side is reduced in the same order whatever the batch): 4 elements per thread for short
+// (coarse-level) vectors, at most 2 CTAs per SM per right-hand side for long ones
 int blas_blocks(size_t n) {
   size_t b = (n + (size_t)kBlasThreads * kBlasPerThread - 1) / ((size_t)kBlasThreads * kBlasPerThread);
   if (b > (size_t)kBlasMaxBlocks) b = kBlasMaxBlocks;
@@ -117,8 +118,9 @@ __global__ void k_mr_update(void* x_, void* r_, const void* q_, size_t n, const 
   }
 }
 
-// x += alpha p, r -= alpha q with alpha = zz[parity]/qq; |r|^2 reduced; the last CTA marks
-// convergence (|r|^2 <= tol2 |b|^2) and counts the iteration.
+// x += alpha p, r -= alpha q with alpha = zz[parity]/qq; |r|^2 reduced; the CTA that completes
+// the sum marks convergence (|r|^2 <= tol2 |b|^2) and counts the iteration (every other CTA of
+// the right-hand side has read done[r] by then).
 template <typename R>
 __global__ void k_cg_update(void* x_, void* r_, const void* p_, const void* q_, size_t n, CgScalars cg, int parity,
                             int nrhs, RedBuf rb) {
@@ -142,14 +144,14 @@ __global__ void k_cg_update(void* x_, void* r_, const void* p_, const void* q_, 
   double v[1] = {double(t)};
   __shared__ double sm[32];
   cta_reduce<1>(v, sm);
-  grid_finish<1>(rb, r, blockIdx.x, gridDim.x, v);
-}
-
-__global__ void k_cg_flags(CgScalars cg, int nrhs) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrhs || cg.done[r]) return;
-  cg.iters[r] += 1;
-  if (cg.rr[r] <= cg.tol2 * cg.bb[r]) cg.done[r] = 1;
+  const bool last = grid_finish<1>(rb, r, blockIdx.x, gridDim.x, v);
+  if (last) {
+    __syncthreads();
+    if (threadIdx.x == 0 && !cg.done[r]) {
+      cg.iters[r] += 1;
+      if (cg.rr[r] <= cg.tol2 * cg.bb[r]) cg.done[r] = 1;
+    }
+  }
 }
 
 // p = z + beta p, beta = zz[1-parity]/zz[parity]
@@ -342,10 +344,9 @@ void blas_mr_update(int prec, void* x, void* r, const void* q, size_t n, int nrh
 
 void cg_update(int prec, void* x, void* r, const void* p, const void* q, size_t n, int nrhs, const CgScalars& cg,
                int parity, const RedBuf& rb_rr, cudaStream_t s) {
-  count_launch(2);
+  count_launch();
   dim3 g(blas_blocks(n), nrhs);
   WMG_BY_PREC(prec, k_cg_update, <<<g, kBlasThreads, 0, s>>>(x, r, p, q, n, cg, parity, nrhs, rb_rr));
-  k_cg_flags<<<(nrhs + 63) / 64, 64, 0, s>>>(cg, nrhs);
 }
 
 void cg_xpay(int prec, void* p, const void* z, size_t n, int nrhs, const CgScalars& cg, int parity, cudaStream_t s) {

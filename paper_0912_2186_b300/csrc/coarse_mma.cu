@@ -9,17 +9,13 @@
 //
 // Operands are FP16 with FP32 accumulation (mma.sync m16n8k16): A is stored once per
 // setup in FP16 scaled by a per-site factor s_A (max |Re|, |Im| of the site's blocks) and
-// pre-arranged in fragment order, so each lane reads one 16-byte word per 16 x 16 tile.  The
-// site's fragments (both planes of one row tile are contiguous) arrive in shared memory by
-// bulk asynchronous copies, one per (plane, row tile), completing on one mbarrier per row
-// tile; meanwhile the CTA gathers X and converts it in shared memory with a per-(site, rhs)
-// factor s_X.  The result is
+// pre-arranged in fragment order, so each lane loads one 16-byte word per 16 x 16 tile; X
+// is converted in shared memory with a per-(site, rhs) factor s_X.  The result is
 // rescaled by s_A s_X.  Relative error is about 1e-3 (FP16 operands), enough for the coarse
 // solve of a preconditioner.
 #include <cuda_fp16.h>
 
 #include "kernels.h"
-#include "ptx.cuh"
 
 namespace wmg {
 
@@ -27,9 +23,6 @@ namespace {
 
 constexpr int kKPad = 8;  // halves of padding per staged column (bank-conflict free B loads)
 constexpr int kEPL = 18;  // gathered values per lane: 9n <= 576 (n <= 64)
-constexpr long long kMmaSpinLimit = 1LL << 22;
-
-__device__ int g_mma_error = 0;
 
 WMG_D uint32_t pack_half2(float lo, float hi) {
   __half2 h = __floats2half2_rn(lo, hi);
@@ -102,36 +95,45 @@ __global__ void k_stencil_to_mma(const cpx<R>* __restrict__ A, int n, const floa
 }
 
 // y = A x (+ shift x), optionally sigma_3 A sigma_3 x, for a chunk of up to 8 NT right-hand
-// sides per CTA (grid.y chunks).  One CTA of 8 warps per coarse site: every warp gathers and
-// converts X for R / 8 right-hand sides; warp w < mt NT then owns row tile m = w / NT and the
-// column block of right-hand sides 8 (w % NT) .. + 7 (its Xr and Xi tiles).
+// sides per CTA (grid.y chunks), n = NDOF coarse dof.  One CTA of 8 warps per coarse site.
+// Every warp gathers X for R / 8 right-hand sides (all loads of the warp in flight together)
+// and converts it to FP16 in shared memory; warp w < MT NT owns row tile m = w % MT and the
+// column block of right-hand sides 8 (w / MT) .. + 7 (its Xr and Xi tiles), and loads its A
+// fragments straight from global memory, the first kPf k-steps before the staging barrier and
+// then kPf k-steps ahead of the MMAs.
 constexpr int kMmaThreads = 256;
-template <int NT>
-__global__ void __launch_bounds__(kMmaThreads) k_coarse_apply_mma(const uint4* __restrict__ A16,
-                                                                  const float* __restrict__ sA, Geom g, int n,
-                                                                  const cf* __restrict__ in, cf* __restrict__ out,
-                                                                  int nrhs, const double* __restrict__ shift, int dagger,
-                                                                  const int* __restrict__ active, RedBuf rb,
-                                                                  int want_norm) {
-  constexpr int R = 8 * NT;          // right-hand sides per chunk
-  constexpr int COLS = 2 * R;        // Xr / Xi columns
-  constexpr int NW = kMmaThreads / 32;
-  extern __shared__ __align__(128) unsigned char smraw[];
-  const int K = 9 * n, KP = K + kKPad;
-  const int mt = n / 16, ksteps = K / 16;
-  const uint32_t tile_bytes = (uint32_t)ksteps * 32 * 16;  // one plane of one row tile
-  uint4* As = reinterpret_cast<uint4*>(smraw);                                     // [2][mt][ksteps][32]
-  __half* xb = reinterpret_cast<__half*>(smraw + (size_t)2 * mt * tile_bytes);      // [COLS][KP]
-  float* xmax = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(xb) + (size_t)COLS * KP * sizeof(__half));
-  __shared__ __align__(8) unsigned long long mbar[4];
+constexpr int kPf = 3;
+template <int NDOF, int NT>
+__global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4* __restrict__ A16,
+                                                                     const float* __restrict__ sA, Geom g,
+                                                                     const cf* __restrict__ in, cf* __restrict__ out,
+                                                                     int nrhs, const double* __restrict__ shift,
+                                                                     int dagger, const int* __restrict__ active,
+                                                                     RedBuf rb, int want_norm) {
+  constexpr int n = NDOF, N = n / 2, K = 9 * n, KP = K + kKPad;
+  constexpr int MT = n / 16, KS = K / 16;
+  constexpr int R = 8 * NT, COLS = 2 * R;
+  constexpr int NW = kMmaThreads / 32, RPW = (R + NW - 1) / NW;  // right-hand sides per warp
+  constexpr int EPL = (K + 31) / 32;                              // gathered values per lane
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __half* xb = reinterpret_cast<__half*>(smraw);                                       // [COLS][KP]
+  float* xmax = reinterpret_cast<float*>(smraw + (size_t)COLS * KP * sizeof(__half));  // [R]
   __shared__ int nbs[9];
   __shared__ double npart[NW][32][2];  // per-lane norm partials of the MMA warps
   const int v = blockIdx.x, r0 = blockIdx.y * R;
-  const int N = n / 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
-    for (int m = 0; m < mt; ++m) mbar_init(smem_addr(&mbar[m]), 1);
-    mbar_fence_init();
+  const bool mma_warp = warp < MT * NT;
+  const int m = warp % MT, blk = warp / MT;
+  // A fragments of this warp's row tile: first kPf k-steps now (they do not depend on X)
+  const uint4* Ar = A16 + (((size_t)v * 2 + 0) * MT + m) * KS * 32 + lane;
+  const uint4* Ai = A16 + (((size_t)v * 2 + 1) * MT + m) * KS * 32 + lane;
+  uint4 ar[kPf], ai[kPf];
+  if (mma_warp) {
+#pragma unroll
+    for (int k = 0; k < kPf; ++k) {
+      ar[k] = __ldg(Ar + (size_t)k * 32);
+      ai[k] = __ldg(Ai + (size_t)k * 32);
+    }
   }
   if (threadIdx.x < 9) {
     int c[4];
@@ -140,20 +142,11 @@ __global__ void __launch_bounds__(kMmaThreads) k_coarse_apply_mma(const uint4* _
     nbs[k] = k == 0 ? v : neighbour(g, v, c, (k - 1) >> 1, ((k - 1) & 1) ? -1 : +1);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int m = 0; m < mt; ++m) {
-      const uint32_t bar = smem_addr(&mbar[m]);
-      mbar_arrive_expect_tx(bar, 2 * tile_bytes);
-      for (int p = 0; p < 2; ++p)
-        bulk_g2s(smem_addr(As + (size_t)(p * mt + m) * ksteps * 32),
-                 A16 + (((size_t)v * 2 + p) * mt + m) * ksteps * 32, tile_bytes, bar);
-    }
-  }
   // lane-owned elements e = lane + 32 i of the 9n gathered values (same for every rhs)
-  int offs[kEPL];
+  int offs[EPL];
   unsigned neg = 0;  // bit i: sigma_3 sign flip of element i (adjoint, lower half of the dof)
 #pragma unroll
-  for (int i = 0; i < kEPL; ++i) {
+  for (int i = 0; i < EPL; ++i) {
     const int e = lane + 32 * i;
     offs[i] = -1;
     if (e < K) {
@@ -162,40 +155,42 @@ __global__ void __launch_bounds__(kMmaThreads) k_coarse_apply_mma(const uint4* _
       if (dagger && j >= N) neg |= 1u << i;
     }
   }
-  // one warp per right-hand side: values into registers, max |Re|, |Im| by shuffles, then the
-  // scaled FP16 copy in column layout [Xr 0..7 | Xi 0..7 | Xr 8..15 | Xi 8..15]
-  for (int rr = warp; rr < R; rr += NW) {
-    const int r = r0 + rr;
-    const int blk = rr >> 3, cc = rr & 7;
-    __half* colr = xb + (size_t)(blk * 16 + cc) * KP;
-    __half* coli = xb + (size_t)(blk * 16 + 8 + cc) * KP;
-    cf xv[kEPL];
-    float m = 0.f;
-    const cf* src = in + (size_t)(r < nrhs ? r : 0) * g.V * n;
+  // gather this warp's right-hand sides (all loads first), then per rhs the max |Re|, |Im| by
+  // shuffles and the scaled FP16 copy in column layout [Xr 0..7 | Xi 0..7 | Xr 8..15 | Xi 8..15]
+  cf xv[RPW][EPL];
 #pragma unroll
-    for (int i = 0; i < kEPL; ++i) {
-      xv[i] = cf{0.f, 0.f};
-      if (offs[i] >= 0 && r < nrhs) xv[i] = src[offs[i]];
-      m = fmaxf(m, fmaxf(fabsf(xv[i].re), fabsf(xv[i].im)));
-    }
+  for (int h = 0; h < RPW; ++h) {
+    const int rr = warp + NW * h, r = r0 + rr;
+    const bool ok = rr < R && r < nrhs;
+    const cf* src = in + (size_t)(ok ? r : 0) * g.V * n;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) xmax[rr] = m;
-    const float inv = m > 0.f ? 1.f / m : 0.f;
+    for (int i = 0; i < EPL; ++i) xv[h][i] = (ok && offs[i] >= 0) ? src[offs[i]] : cf{0.f, 0.f};
+  }
 #pragma unroll
-    for (int i = 0; i < kEPL; ++i) {
+  for (int h = 0; h < RPW; ++h) {
+    const int rr = warp + NW * h;
+    if (rr >= R) continue;
+    float mx = 0.f;
+#pragma unroll
+    for (int i = 0; i < EPL; ++i) mx = fmaxf(mx, fmaxf(fabsf(xv[h][i].re), fabsf(xv[h][i].im)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) xmax[rr] = mx;
+    const float inv = mx > 0.f ? 1.f / mx : 0.f;
+    __half* colr = xb + (size_t)((rr >> 3) * 16 + (rr & 7)) * KP;
+    __half* coli = colr + (size_t)8 * KP;
+#pragma unroll
+    for (int i = 0; i < EPL; ++i) {
       const int e = lane + 32 * i;
       if (e < K) {
         const float sg = ((neg >> i) & 1u) ? -inv : inv;
-        colr[e] = __float2half_rn(xv[i].re * sg);
-        coli[e] = __float2half_rn(xv[i].im * sg);
+        colr[e] = __float2half_rn(xv[h][i].re * sg);
+        coli[e] = __float2half_rn(xv[h][i].im * sg);
       }
     }
   }
   __syncthreads();
   const int gq = lane >> 2, q = lane & 3;
-  const bool mma_warp = warp < mt * NT;
-  const int m = warp / NT, blk = warp % NT;
   float acc[2][2][4];  // [plane Ar / Ai][tile Xr / Xi][fragment]
 #pragma unroll
   for (int p = 0; p < 2; ++p)
@@ -203,25 +198,22 @@ __global__ void __launch_bounds__(kMmaThreads) k_coarse_apply_mma(const uint4* _
     for (int t = 0; t < 2; ++t)
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[p][t][e] = 0.f;
-  bool ready = true;
   if (mma_warp) {
-    ready = mbar_wait_bounded(smem_addr(&mbar[m]), 0, kMmaSpinLimit);
-    if (!ready && lane == 0) atomicExch(&g_mma_error, 1);
-  }
-  if (mma_warp && ready) {
-    const uint4* Ar = As + (size_t)(0 * mt + m) * ksteps * 32 + lane;
-    const uint4* Ai = As + (size_t)(1 * mt + m) * ksteps * 32 + lane;
     const __half* colbase = xb + (size_t)(blk * 16 + gq) * KP + 2 * q;
-#pragma unroll 3
-    for (int k = 0; k < ksteps; ++k) {
-      const uint4 ar = Ar[(size_t)k * 32], ai = Ai[(size_t)k * 32];
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+      const uint4 a0 = ar[k % kPf], a1 = ai[k % kPf];
+      if (k + kPf < KS) {
+        ar[k % kPf] = __ldg(Ar + (size_t)(k + kPf) * 32);
+        ai[k % kPf] = __ldg(Ai + (size_t)(k + kPf) * 32);
+      }
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         const __half* col = colbase + (size_t)t * 8 * KP + 16 * k;
         const uint32_t b0 = *reinterpret_cast<const uint32_t*>(col);
         const uint32_t b1 = *reinterpret_cast<const uint32_t*>(col + 8);
-        mma16816(acc[0][t], ar, b0, b1);
-        mma16816(acc[1][t], ai, b0, b1);
+        mma16816(acc[0][t], a0, b0, b1);
+        mma16816(acc[1][t], a1, b0, b1);
       }
     }
   }
@@ -245,7 +237,6 @@ __global__ void __launch_bounds__(kMmaThreads) k_coarse_apply_mma(const uint4* _
       nv2[e & 1] += double(o.re) * o.re + double(o.im) * o.im;
     }
   }
-  if (!ready) mbar_wait_bounded(smem_addr(&mbar[m]), 0, kMmaSpinLimit);  // let the copies drain (bounded)
   if (want_norm) {
     if (mma_warp) {
       npart[warp][lane][0] = nv2[0];
@@ -254,12 +245,12 @@ __global__ void __launch_bounds__(kMmaThreads) k_coarse_apply_mma(const uint4* _
     __syncthreads();
     __shared__ bool last;
     const int nblk = gridDim.x;
-    if (threadIdx.x < R && r0 + threadIdx.x < nrhs) {
+    if (threadIdx.x < R && r0 + (int)threadIdx.x < nrhs) {
       // fixed order: row tiles, then the 8 row groups of the fragment
       const int rr = threadIdx.x, b = rr >> 3, qq = (rr & 7) >> 1, ee = rr & 1;
       double t = 0.0;
-      for (int mm = 0; mm < mt; ++mm)
-        for (int gg = 0; gg < 8; ++gg) t += npart[mm * NT + b][gg * 4 + qq][ee];
+      for (int mm = 0; mm < MT; ++mm)
+        for (int gg = 0; gg < 8; ++gg) t += npart[b * MT + mm][gg * 4 + qq][ee];
       rb.partial[(size_t)(r0 + rr) * nblk + blockIdx.x] = t;
     }
     __threadfence();
@@ -276,12 +267,6 @@ __global__ void __launch_bounds__(kMmaThreads) k_coarse_apply_mma(const uint4* _
   }
 }
 
-int coarse_mma_error() {
-  int e = 0;
-  cudaMemcpyFromSymbol(&e, g_mma_error, sizeof(int));
-  return e;
-}
-
 size_t stencil_mma_words(int Vc, int n) { return (size_t)Vc * 2 * (n / 16) * (9 * n / 16) * 32; }
 
 void stencil_to_mma(int prec, const void* A, int Vc, int n, float* scale, void* out, cudaStream_t s) {
@@ -295,28 +280,39 @@ void stencil_to_mma(int prec, const void* A, int Vc, int n, float* scale, void* 
   else k_stencil_to_mma<float><<<B, 256, 0, s>>>((const cf*)A, n, scale, (uint4*)out, Vc);
 }
 
-template <int NT>
-static void launch_mma(const void* A16, const float* sA, const Geom& g, int n, const void* in, void* out, int nrhs,
+template <int NDOF, int NT>
+static void launch_mma(const void* A16, const float* sA, const Geom& g, const void* in, void* out, int nrhs,
                        const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s) {
   constexpr int R = 8 * NT;
-  const size_t smem = (size_t)2 * (n / 16) * (9 * n / 16) * 512 + (size_t)2 * R * (9 * n + kKPad) * sizeof(__half) +
-                      R * sizeof(float);
+  const size_t smem = (size_t)2 * R * (9 * NDOF + kKPad) * sizeof(__half) + R * sizeof(float);
   static const bool attr = [] {
-    cudaFuncSetAttribute(k_coarse_apply_mma<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(k_coarse_apply_mma<NDOF, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
     return true;
   }();
   (void)attr;
   dim3 grid(g.V, (nrhs + R - 1) / R);
   RedBuf r = rb ? *rb : RedBuf{nullptr, nullptr, nullptr};
-  k_coarse_apply_mma<NT><<<grid, kMmaThreads, smem, s>>>((const uint4*)A16, sA, g, n, (const cf*)in, (cf*)out, nrhs, shift,
-                                               dagger ? 1 : 0, active, r, rb ? 1 : 0);
+  k_coarse_apply_mma<NDOF, NT><<<grid, kMmaThreads, smem, s>>>((const uint4*)A16, sA, g, (const cf*)in, (cf*)out,
+                                                               nrhs, shift, dagger ? 1 : 0, active, r, rb ? 1 : 0);
 }
 
+template <int NDOF>
+static void launch_mma_n(const void* A16, const float* sA, const Geom& g, const void* in, void* out, int nrhs,
+                         const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s) {
+  if (nrhs <= 8) launch_mma<NDOF, 1>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s);
+  else launch_mma<NDOF, 2>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s);
+}
+
+// n = 2N in {16, 32, 48, 64} (the tensor-core copy exists only for those)
 void coarse_apply_mma(const void* A16, const float* sA, const Geom& g, int n, const void* in, void* out, int nrhs,
                       const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s) {
   count_launch();
-  if (nrhs <= 8) launch_mma<1>(A16, sA, g, n, in, out, nrhs, shift, dagger, active, rb, s);
-  else launch_mma<2>(A16, sA, g, n, in, out, nrhs, shift, dagger, active, rb, s);
+  switch (n) {
+    case 16: launch_mma_n<16>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s); break;
+    case 32: launch_mma_n<32>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s); break;
+    case 48: launch_mma_n<48>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s); break;
+    default: launch_mma_n<64>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s); break;
+  }
 }
 
 }  // namespace wmg

@@ -125,7 +125,6 @@ void stencil_to_tc05(int prec, const void* A, int Vc, int n, const float* scale,
 void coarse_apply_tc05(const void* A16, const float* sA, const Geom& g, int n, const void* in, void* out, int nrhs,
                        const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s);
 int coarse_tc05_error();  // 1 if a bounded tcgen05 wait ever expired (synchronises)
-int coarse_mma_error();   // 1 if a bounded wait of the mma.sync coarse kernel ever expired (synchronises)
 // convert a stencil between precisions
 void stencil_convert(int prec_d, void* dst, int prec_s, const void* src, size_t count, cudaStream_t s);
 

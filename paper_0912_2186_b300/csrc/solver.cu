@@ -683,11 +683,14 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
     if (anyrel) {
       // fold the sloppy iterate into the FP64 solution, then the FP64 true residual
       // r64 = b - D x64 for the active slots; applied where rel is set
+      // (the FP64 operator runs only on the slots that take the update)
       TRY(upload_ints(c, c->d_mask, rel));
       blas_fold(lo, (double*)x64, xlo, n, nslots, c->d_mask, s);
+      int nrel = 0;
+      for (int r = 0; r < nslots; ++r) nrel += rel[r];
       {
-        ProfScope ps(c, PROF_DSLASH_64, dslash_bytes(c, WMG_PREC_DOUBLE, c->n_active, true), c->n_active);
-        dslash(WMG_PREC_DOUBLE, r64, x64, b64, c->gauge[0], c->fine, c->d_mass, c->d_active, nslots, 1, &rb_r64, s);
+        ProfScope ps(c, PROF_DSLASH_64, dslash_bytes(c, WMG_PREC_DOUBLE, nrel, true), nrel);
+        dslash(WMG_PREC_DOUBLE, r64, x64, b64, c->gauge[0], c->fine, c->d_mass, c->d_mask, nslots, 1, &rb_r64, s);
       }
       TRY(download(c, rb_r64.result, nslots, t));
       blas_convert(lo, rlo, WMG_PREC_DOUBLE, r64, n, nslots, c->d_mask, s);
@@ -719,7 +722,7 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
     }
   }
   CU(c, cudaStreamSynchronize(s));
-  if (use_mg && (coarse_mma_error() || coarse_tc05_error())) {
+  if (use_mg && c->L[c->nlev - 1].A05 && coarse_tc05_error()) {
     c->err = "a bounded wait of the tensor-core coarse stencil expired";
     return WMG_ETIMEOUT;
   }

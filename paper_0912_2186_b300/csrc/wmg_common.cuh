@@ -253,8 +253,10 @@ WMG_D void cta_multi_sum(const volatile double* p, int nval, size_t istride, int
 // After cta_reduce (thread 0 holds v): writes the CTA's partials; the last CTA for `rhs`
 // sums all partials (fixed order, whole CTA, all values in parallel) into rb.result.
 // nblk = CTAs per rhs.  May be called several times in a row by one CTA.
+// Returns true in the CTA that completed the sums (whose threads then see rb.result after a
+// barrier).
 template <int NVAL>
-WMG_D void grid_finish(const RedBuf& rb, int rhs, int blk, int nblk, const double v[NVAL]) {
+WMG_D bool grid_finish(const RedBuf& rb, int rhs, int blk, int nblk, const double v[NVAL]) {
   __shared__ bool last;
   __syncthreads();  // `last` of a previous call has been read by every thread
   if (threadIdx.x == 0) {
@@ -273,6 +275,7 @@ WMG_D void grid_finish(const RedBuf& rb, int rhs, int blk, int nblk, const doubl
     cta_multi_sum(p, NVAL, 1, nblk, NVAL, [&](int i, double s) { res[i] = s; });
     if (threadIdx.x == 0) rb.counter[rhs] = 0u;
   }
+  return last;
 }
 
 #define WMG_CUDA_TRY(expr)                                      \
