@@ -79,7 +79,9 @@ typedef enum {
 typedef enum {
   WMG_PREC_DOUBLE = 0, /* FP64 storage and arithmetic */
   WMG_PREC_SINGLE = 1, /* FP32 storage and arithmetic */
-  WMG_PREC_HALF = 2    /* wmg_apply_coarse only: FP16 operator on tensor cores, FP32 vectors */
+  WMG_PREC_HALF = 2    /* FP16 storage, FP32 arithmetic: wmg_apply_coarse (FP16 operator on tensor
+                          cores), wmg_restrict / wmg_prolong (FP16 null vectors), prec_nullvec,
+                          prec_smoother */
 } wmg_prec;
 
 #define WMG_MAX_LEVELS 3
@@ -109,6 +111,13 @@ typedef struct {
                                         residual fell by this factor                */
   uint64_t seed;                     /* seed of the setup's Gaussian starts when no
                                         starts are passed                           */
+  int prec_nullvec;                  /* storage of the fine-level null vectors in the
+                                        cycle's restrict / prolong with prec_sloppy =
+                                        SINGLE: SINGLE, or HALF (FP16 P, FP32
+                                        arithmetic; the setup keeps FP64 / FP32 P)   */
+  int prec_smoother;                 /* storage of the fine-level MR smoother vectors
+                                        with prec_sloppy = SINGLE: SINGLE, or HALF
+                                        (FP16 with a per-site norm, FP32 arithmetic)  */
 } wmg_params;
 
 /* Per-right-hand-side result of a solve. */
@@ -184,7 +193,9 @@ wmg_status wmg_pack_spinor(wmg_ctx* ctx, int prec, const double* canon_dev, void
 wmg_status wmg_unpack_spinor(wmg_ctx* ctx, int prec, const void* native_dev, double* canon_dev, int nrhs);
 
 /* out = D(U) in for nrhs native fine spinors (Sec. 2, eq. for D) at the context's
- * mass.  in and out must not overlap. */
+ * mass.  in and out must not overlap.  prec = WMG_PREC_HALF takes FP32 buffers and runs
+ * the smoother's FP16 storage path: in rounded to FP16 with a per-site norm, D applied
+ * in FP32 arithmetic, the result rounded to FP16 the same way and widened into out. */
 wmg_status wmg_apply_D(wmg_ctx* ctx, int prec, const void* in_dev, void* out_dev, int nrhs);
 
 /* coarse = P^dag fine (Sec. 2, R = P^dag): level 0 maps native fine spinors to

@@ -36,6 +36,7 @@ void free_hierarchy(wmg_ctx* c) {
       if (p == 0 && c->L[l].sA) cudaFree(c->L[l].sA), c->L[l].sA = nullptr;
       if (p == 0 && c->L[l].A05) cudaFree(c->L[l].A05), c->L[l].A05 = nullptr;
       if (c->L[l].P[p]) cudaFree(c->L[l].P[p]);
+      if (p == 0 && c->L[l].P16) cudaFree(c->L[l].P16), c->L[l].P16 = nullptr;
       c->L[l].A[p] = c->L[l].P[p] = nullptr;
     }
   c->have_hier = false;
@@ -54,6 +55,11 @@ wmg_status alloc_hierarchy(wmg_ctx* c, const wmg_params* p) {
   if (p->setup_passes < 1 || p->nu_post < 0 || p->setup_relax < 0 || p->max_iter < 1 || p->coarse_maxit < 1)
     return bad(c, "iteration counts");
   if (!(p->tol > 0) || !(p->coarse_tol > 0)) return bad(c, "tolerances must be positive");
+  const bool half_ok = p->prec_sloppy == WMG_PREC_SINGLE;
+  if (p->prec_nullvec != WMG_PREC_SINGLE && !(p->prec_nullvec == WMG_PREC_HALF && half_ok))
+    return bad(c, "prec_nullvec must be SINGLE, or HALF with prec_sloppy SINGLE");
+  if (p->prec_smoother != WMG_PREC_SINGLE && !(p->prec_smoother == WMG_PREC_HALF && half_ok))
+    return bad(c, "prec_smoother must be SINGLE, or HALF with prec_sloppy SINGLE");
   free_hierarchy(c);
   c->prm = *p;
   c->nlev = p->nlevels;
@@ -84,6 +90,8 @@ wmg_status alloc_hierarchy(wmg_ctx* c, const wmg_params* p) {
     c->L[l + 1].g = bk.coarse;
     c->L[l + 1].ndof = 2 * bk.N;
     for (int pr = 0; pr < 2; ++pr) CU(c, cudaMalloc(&L.P[pr], L.nvec_elems() * bk.N * csize(pr)));
+    if (l == 0 && p->prec_nullvec == WMG_PREC_HALF)
+      CU(c, cudaMalloc(&L.P16, L.nvec_elems() * bk.N * 4 /* __half2 */));
   }
   return WMG_OK;
 }
@@ -113,6 +121,8 @@ void wmg_default_params(wmg_params* p) {
   p->coarse_tc = 1;
   p->reliable_delta = 1e-3;
   p->seed = 20091212ULL;
+  p->prec_nullvec = WMG_PREC_SINGLE;
+  p->prec_smoother = WMG_PREC_SINGLE;
 }
 
 const char* wmg_strerror(wmg_status s) {
@@ -391,26 +401,51 @@ wmg_status wmg_unpack_spinor(wmg_ctx* c, int prec, const void* native, double* c
 }
 
 wmg_status wmg_apply_D(wmg_ctx* c, int prec, const void* in, void* out, int nrhs) {
-  if (!c || !in || !out || nrhs < 1 || nrhs > kMaxRhs || !prec_ok(prec) || in == out) return WMG_EINVAL;
+  if (!c || !in || !out || nrhs < 1 || nrhs > kMaxRhs || in == out) return WMG_EINVAL;
+  if (!(prec_ok(prec) || prec == WMG_PREC_HALF)) return WMG_EINVAL;
   if (!c->have_gauge) return WMG_ESTATE;
   TRY(set_rhs_scalars(c, nullptr, nrhs));
+  if (prec == WMG_PREC_HALF) {
+    // the smoother's FP16 storage: FP32 in -> FP16 (per-site norms) -> D -> FP16 -> FP32 out
+    const int V = c->fine.V;
+    void *h_in, *h_out, *n_in, *n_out;
+    TRY(ws_get(c, "aD_h_in", spinor_h_bytes(V) * nrhs, &h_in));
+    TRY(ws_get(c, "aD_h_out", spinor_h_bytes(V) * nrhs, &h_out));
+    TRY(ws_get(c, "aD_n_in", (size_t)V * nrhs * sizeof(float), &n_in));
+    TRY(ws_get(c, "aD_n_out", (size_t)V * nrhs * sizeof(float), &n_out));
+    spinor_to_h(in, h_in, (float*)n_in, V, nrhs, c->stream);
+    dslash_h(1, h_out, (float*)n_out, h_in, (const float*)n_in, nullptr, c->gauge[1], c->fine, c->d_mass, nullptr,
+             nrhs, 0, nullptr, c->stream);
+    spinor_from_h(h_out, (const float*)n_out, out, V, nrhs, c->stream);
+    return check(c, "apply_D (FP16 storage)");
+  }
   dslash(prec, out, in, nullptr, c->gauge[prec], c->fine, c->d_mass, nullptr, nrhs, 0, nullptr, c->stream);
   return check(c, "apply_D");
 }
 
 wmg_status wmg_restrict(wmg_ctx* c, int level, int prec, const void* fine, void* coarse, int nrhs) {
-  if (!c || !fine || !coarse || nrhs < 1 || !prec_ok(prec)) return WMG_EINVAL;
+  if (!c || !fine || !coarse || nrhs < 1 || !(prec_ok(prec) || prec == WMG_PREC_HALF)) return WMG_EINVAL;
   if (level < 0 || level + 1 >= c->nlev || !c->L[level + 1].A[0]) return WMG_ESTATE;
   const LevelData& L = c->L[level];
+  if (prec == WMG_PREC_HALF) {  // FP16 null vectors, FP32 buffers
+    if (level != 0 || !L.P16) return WMG_ESTATE;
+    if (!restrict_fine_h(L.P16, L.bk, fine, coarse, nrhs, nullptr, c->stream)) return WMG_EINVAL;
+    return check(c, "restrict");
+  }
   if (level == 0) restrict_fine(prec, L.P[prec], L.bk, fine, coarse, nrhs, nullptr, c->stream);
   else restrict_coarse(prec, L.P[prec], L.bk, fine, coarse, nrhs, nullptr, c->stream);
   return check(c, "restrict");
 }
 
 wmg_status wmg_prolong(wmg_ctx* c, int level, int prec, const void* coarse, void* fine, int nrhs) {
-  if (!c || !fine || !coarse || nrhs < 1 || !prec_ok(prec)) return WMG_EINVAL;
+  if (!c || !fine || !coarse || nrhs < 1 || !(prec_ok(prec) || prec == WMG_PREC_HALF)) return WMG_EINVAL;
   if (level < 0 || level + 1 >= c->nlev || !c->L[level + 1].A[0]) return WMG_ESTATE;
   const LevelData& L = c->L[level];
+  if (prec == WMG_PREC_HALF) {  // FP16 null vectors, FP32 buffers
+    if (level != 0 || !L.P16) return WMG_ESTATE;
+    if (!prolong_fine_h(L.P16, L.bk, coarse, fine, nrhs, nullptr, c->stream)) return WMG_EINVAL;
+    return check(c, "prolong");
+  }
   if (level == 0) prolong_fine(prec, L.P[prec], L.bk, coarse, fine, nrhs, nullptr, c->stream);
   else prolong_coarse(prec, L.P[prec], L.bk, coarse, fine, nrhs, nullptr, c->stream);
   return check(c, "prolong");

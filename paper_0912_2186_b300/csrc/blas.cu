@@ -100,8 +100,10 @@ __global__ void k_scale_inv_sqrt(void* x, size_t n, const double* nrm2, int stri
   WMG_GRID_LOOP(i) a[i] = s * a[i];
 }
 
+// x += alpha r and (update_r) r -= alpha q, alpha = red[0..1] / red[2] per rhs
 template <typename R>
-__global__ void k_mr_update(void* x_, void* r_, const void* q_, size_t n, const double* red, const int* active) {
+__global__ void k_mr_update(void* x_, void* r_, const void* q_, size_t n, const double* red, const int* active,
+                            int update_r) {
   const int r = blockIdx.y;
   if (active && !active[r]) return;
   const double qq = red[r * 3 + 2];
@@ -110,6 +112,10 @@ __global__ void k_mr_update(void* x_, void* r_, const void* q_, size_t n, const 
   cpx<R>* x = vec<R>(x_, n, r);
   cpx<R>* rr = vec<R>(r_, n, r);
   const cpx<R>* q = vec<R>(q_, n, r);
+  if (!update_r) {
+    WMG_GRID_LOOP(i) cfma(x[i], al, rr[i]);
+    return;
+  }
   WMG_GRID_LOOP(i) {
     cpx<R> ri = rr[i];
     cfma(x[i], al, ri);
@@ -335,11 +341,11 @@ void blas_scale_inv_sqrt(int prec, void* x, size_t n, int nrhs, const double* nr
   WMG_BY_PREC(prec, k_scale_inv_sqrt, <<<g, kBlasThreads, 0, s>>>(x, n, nrm2, stride));
 }
 
-void blas_mr_update(int prec, void* x, void* r, const void* q, size_t n, int nrhs, const double* red,
+void blas_mr_update(int prec, void* x, void* r, const void* q, size_t n, int nrhs, const double* red, bool update_r,
                     const int* active, cudaStream_t s) {
   count_launch();
   dim3 g(blas_blocks(n), nrhs);
-  WMG_BY_PREC(prec, k_mr_update, <<<g, kBlasThreads, 0, s>>>(x, r, q, n, red, active));
+  WMG_BY_PREC(prec, k_mr_update, <<<g, kBlasThreads, 0, s>>>(x, r, q, n, red, active, update_r ? 1 : 0));
 }
 
 void cg_update(int prec, void* x, void* r, const void* p, const void* q, size_t n, int nrhs, const CgScalars& cg,

@@ -9,20 +9,26 @@
 //
 // Operands are FP16 with FP32 accumulation (mma.sync m16n8k16): A is stored once per
 // setup in FP16 scaled by a per-site factor s_A (max |Re|, |Im| of the site's blocks) and
-// pre-arranged in fragment order, so each lane loads one 16-byte word per 16 x 16 tile; X
-// is converted in shared memory with a per-(site, rhs) factor s_X.  The result is
+// pre-arranged in fragment order, so each lane reads one 16-byte word per 16 x 16 tile.  The
+// site's fragments (both planes of one row tile are contiguous) arrive in shared memory by
+// bulk asynchronous copies issued at kernel start, one per (plane, row tile), completing on
+// one mbarrier per row tile (bounded wait); meanwhile the CTA gathers X and converts it in
+// shared memory with a per-(site, rhs) factor s_X.  The result is
 // rescaled by s_A s_X.  Relative error is about 1e-3 (FP16 operands), enough for the coarse
 // solve of a preconditioner.
 #include <cuda_fp16.h>
 
 #include "kernels.h"
+#include "ptx.cuh"
 
 namespace wmg {
 
 namespace {
 
 constexpr int kKPad = 8;  // halves of padding per staged column (bank-conflict free B loads)
-constexpr int kEPL = 18;  // gathered values per lane: 9n <= 576 (n <= 64)
+constexpr long long kMmaSpinLimit = 1LL << 22;
+
+__device__ int g_mma_error = 0;
 
 WMG_D uint32_t pack_half2(float lo, float hi) {
   __half2 h = __floats2half2_rn(lo, hi);
@@ -98,11 +104,8 @@ __global__ void k_stencil_to_mma(const cpx<R>* __restrict__ A, int n, const floa
 // sides per CTA (grid.y chunks), n = NDOF coarse dof.  One CTA of 8 warps per coarse site.
 // Every warp gathers X for R / 8 right-hand sides (all loads of the warp in flight together)
 // and converts it to FP16 in shared memory; warp w < MT NT owns row tile m = w % MT and the
-// column block of right-hand sides 8 (w / MT) .. + 7 (its Xr and Xi tiles), and loads its A
-// fragments straight from global memory, the first kPf k-steps before the staging barrier and
-// then kPf k-steps ahead of the MMAs.
+// column block of right-hand sides 8 (w / MT) .. + 7 (its Xr and Xi tiles).
 constexpr int kMmaThreads = 256;
-constexpr int kPf = 3;
 template <int NDOF, int NT>
 __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4* __restrict__ A16,
                                                                      const float* __restrict__ sA, Geom g,
@@ -115,24 +118,27 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
   constexpr int R = 8 * NT, COLS = 2 * R;
   constexpr int NW = kMmaThreads / 32, RPW = (R + NW - 1) / NW;  // right-hand sides per warp
   constexpr int EPL = (K + 31) / 32;                              // gathered values per lane
-  extern __shared__ __align__(16) unsigned char smraw[];
-  __half* xb = reinterpret_cast<__half*>(smraw);                                       // [COLS][KP]
-  float* xmax = reinterpret_cast<float*>(smraw + (size_t)COLS * KP * sizeof(__half));  // [R]
+  constexpr uint32_t kTileBytes = (uint32_t)KS * 32 * 16;         // one plane of one row tile
+  extern __shared__ __align__(128) unsigned char smraw[];
+  uint4* As = reinterpret_cast<uint4*>(smraw);                                        // [2][MT][KS][32]
+  __half* xb = reinterpret_cast<__half*>(smraw + (size_t)2 * MT * kTileBytes);        // [COLS][KP]
+  float* xmax = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(xb) + (size_t)COLS * KP * sizeof(__half));
+  __shared__ __align__(8) unsigned long long mbar[MT];
   __shared__ int nbs[9];
   __shared__ double npart[NW][32][2];  // per-lane norm partials of the MMA warps
   const int v = blockIdx.x, r0 = blockIdx.y * R;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool mma_warp = warp < MT * NT;
   const int m = warp % MT, blk = warp / MT;
-  // A fragments of this warp's row tile: first kPf k-steps now (they do not depend on X)
-  const uint4* Ar = A16 + (((size_t)v * 2 + 0) * MT + m) * KS * 32 + lane;
-  const uint4* Ai = A16 + (((size_t)v * 2 + 1) * MT + m) * KS * 32 + lane;
-  uint4 ar[kPf], ai[kPf];
-  if (mma_warp) {
-#pragma unroll
-    for (int k = 0; k < kPf; ++k) {
-      ar[k] = __ldg(Ar + (size_t)k * 32);
-      ai[k] = __ldg(Ai + (size_t)k * 32);
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < MT; ++t) mbar_init(smem_addr(&mbar[t]), 1);
+    mbar_fence_init();
+    for (int t = 0; t < MT; ++t) {
+      const uint32_t bar = smem_addr(&mbar[t]);
+      mbar_arrive_expect_tx(bar, 2 * kTileBytes);
+      for (int p = 0; p < 2; ++p)
+        bulk_g2s(smem_addr(As + (size_t)(p * MT + t) * KS * 32), A16 + (((size_t)v * 2 + p) * MT + t) * KS * 32,
+                 kTileBytes, bar);
     }
   }
   if (threadIdx.x < 9) {
@@ -198,15 +204,18 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
     for (int t = 0; t < 2; ++t)
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[p][t][e] = 0.f;
+  bool ready = true;
   if (mma_warp) {
+    ready = mbar_wait_bounded(smem_addr(&mbar[m]), 0, kMmaSpinLimit);
+    if (!ready && lane == 0) atomicExch(&g_mma_error, 1);
+  }
+  if (mma_warp && ready) {
+    const uint4* Ar = As + (size_t)(0 * MT + m) * KS * 32 + lane;
+    const uint4* Ai = As + (size_t)(1 * MT + m) * KS * 32 + lane;
     const __half* colbase = xb + (size_t)(blk * 16 + gq) * KP + 2 * q;
-#pragma unroll
+#pragma unroll 9
     for (int k = 0; k < KS; ++k) {
-      const uint4 a0 = ar[k % kPf], a1 = ai[k % kPf];
-      if (k + kPf < KS) {
-        ar[k % kPf] = __ldg(Ar + (size_t)(k + kPf) * 32);
-        ai[k % kPf] = __ldg(Ai + (size_t)(k + kPf) * 32);
-      }
+      const uint4 a0 = Ar[(size_t)k * 32], a1 = Ai[(size_t)k * 32];
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         const __half* col = colbase + (size_t)t * 8 * KP + 16 * k;
@@ -217,6 +226,8 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
       }
     }
   }
+  // a tile whose wait expired: give its copies a second bounded chance to land before exit
+  if (mma_warp && !ready) mbar_wait_bounded(smem_addr(&mbar[m]), 0, kMmaSpinLimit);
   // epilogue: thread holds rows 16 m + gq (+8) and right-hand sides 8 blk + 2q + (e & 1)
   double nv2[2] = {0.0, 0.0};
   if (mma_warp) {
@@ -267,6 +278,12 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
   }
 }
 
+int coarse_mma_error() {
+  int e = 0;
+  cudaMemcpyFromSymbol(&e, g_mma_error, sizeof(int));
+  return e;
+}
+
 size_t stencil_mma_words(int Vc, int n) { return (size_t)Vc * 2 * (n / 16) * (9 * n / 16) * 32; }
 
 void stencil_to_mma(int prec, const void* A, int Vc, int n, float* scale, void* out, cudaStream_t s) {
@@ -284,9 +301,10 @@ template <int NDOF, int NT>
 static void launch_mma(const void* A16, const float* sA, const Geom& g, const void* in, void* out, int nrhs,
                        const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s) {
   constexpr int R = 8 * NT;
-  const size_t smem = (size_t)2 * R * (9 * NDOF + kKPad) * sizeof(__half) + R * sizeof(float);
+  const size_t smem = (size_t)2 * (NDOF / 16) * (9 * NDOF / 16) * 512 +
+                      (size_t)2 * R * (9 * NDOF + kKPad) * sizeof(__half) + R * sizeof(float);
   static const bool attr = [] {
-    cudaFuncSetAttribute(k_coarse_apply_mma<NDOF, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    cudaFuncSetAttribute(k_coarse_apply_mma<NDOF, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     return true;
   }();
   (void)attr;

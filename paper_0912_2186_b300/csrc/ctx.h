@@ -30,6 +30,7 @@ struct LevelData {
   // transfer to the next level (levels < nlev - 1)
   Blocking bk{};
   void* P[2] = {nullptr, nullptr};  // N fields of this level, per precision (P[0] = FP64)
+  void* P16 = nullptr;     // FP16 (__half2) copy of the fine-level P for the cycle (prec_nullvec HALF)
   size_t nvec_elems() const { return (size_t)g.V * ndof; }  // complex numbers per field
 };
 

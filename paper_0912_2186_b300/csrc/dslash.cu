@@ -133,6 +133,149 @@ __global__ void __launch_bounds__(128) k_dslash(void* __restrict__ out, const vo
 }
 
 // ------------------------------------------------------------------------------------
+// The smoother's FP16 storage (FP32 arithmetic).  out16 (+ per-site norms) = [b -] D in, with
+// in FP32 native (IN16 = 0) or FP16 with norms (IN16 = 1) and b FP32 native; the scale of an
+// FP16 neighbour enters the accumulation of its hop.  RED = 2: per rhs {<out, in>, |out|^2}
+// from the FP32 values before rounding.
+// ------------------------------------------------------------------------------------
+template <int IN16, int RED>
+__global__ void __launch_bounds__(128) k_dslash_h(void* __restrict__ out16, float* __restrict__ out_norm,
+                                                  const void* __restrict__ in, const float* __restrict__ in_norm,
+                                                  const void* __restrict__ b, const void* __restrict__ gauge, Geom g,
+                                                  const double* __restrict__ mass, const int* __restrict__ active,
+                                                  int nrhs, int nblk_site, RedBuf rb) {
+  const int rhs = blockIdx.x % nrhs;
+  const int sb = blockIdx.x / nrhs;
+  if (active && !active[rhs]) return;  // whole CTA exits together (uniform per CTA)
+  const int v = sb * blockDim.x + threadIdx.x;
+  const size_t fbi = IN16 ? spinor_h_bytes(g.V) : spinor_field_bytes<float>(g.V);
+  const char* inr = reinterpret_cast<const char*>(in) + fbi * rhs;
+  const float* inn = IN16 ? in_norm + (size_t)g.V * rhs : nullptr;
+  cpx<float> acc[12];
+  double red[3] = {0.0, 0.0, 0.0};
+  if (v < g.V) {
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[i] = cpx<float>{0.f, 0.f};
+    int c[4];
+    site_coords(g, v, c);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      cpx<float> u[9], nb[12];
+      const int vf = neighbour(g, v, c, mu, +1);
+      load_link<float>(gauge, g.V, mu, v, u);
+      if (IN16) {
+        load_spinor_h(inr, g.V, vf, nb);
+        hop_accumulate_scaled<+1>(mu, u, nb, __ldg(inn + vf), acc);
+      } else {
+        load_spinor<float>(inr, g.V, vf, nb);
+        hop_accumulate<+1>(mu, u, nb, acc);
+      }
+      const int vb = neighbour(g, v, c, mu, -1);
+      load_link<float>(gauge, g.V, mu, vb, u);
+      if (IN16) {
+        load_spinor_h(inr, g.V, vb, nb);
+        hop_accumulate_scaled<-1>(mu, u, nb, __ldg(inn + vb), acc);
+      } else {
+        load_spinor<float>(inr, g.V, vb, nb);
+        hop_accumulate<-1>(mu, u, nb, acc);
+      }
+    }
+    cpx<float> self[12];
+    if (IN16) {
+      load_spinor_h(inr, g.V, v, self);
+      const float sc = __ldg(inn + v);
+#pragma unroll
+      for (int i = 0; i < 12; ++i) self[i] = sc * self[i];
+    } else {
+      load_spinor<float>(inr, g.V, v, self);
+    }
+    const float diag = float(4.0 + mass[rhs]);
+#pragma unroll
+    for (int i = 0; i < 12; ++i)
+      acc[i] = cpx<float>{fmaf(diag, self[i].re, -0.5f * acc[i].re), fmaf(diag, self[i].im, -0.5f * acc[i].im)};
+    if (b) {
+      cpx<float> bb[12];
+      load_spinor<float>(reinterpret_cast<const char*>(b) + spinor_field_bytes<float>(g.V) * rhs, g.V, v, bb);
+#pragma unroll
+      for (int i = 0; i < 12; ++i) acc[i] = bb[i] - acc[i];
+    }
+    store_spinor_h(reinterpret_cast<char*>(out16) + spinor_h_bytes(g.V) * rhs, out_norm + (size_t)g.V * rhs, g.V, v,
+                   acc);
+    if (RED == 2) {
+      float a0 = 0.f, a1 = 0.f, nn = 0.f;
+#pragma unroll
+      for (int i = 0; i < 12; ++i) {
+        a0 += acc[i].re * self[i].re + acc[i].im * self[i].im;
+        a1 += acc[i].re * self[i].im - acc[i].im * self[i].re;
+        nn += acc[i].re * acc[i].re + acc[i].im * acc[i].im;
+      }
+      red[0] = double(a0);
+      red[1] = double(a1);
+      red[2] = double(nn);
+    }
+  }
+  if constexpr (RED == 2) {
+    __shared__ double sm[32 * 3];
+    cta_reduce<3>(red, sm);
+    grid_finish<3>(rb, rhs, sb, nblk_site, red);
+  }
+}
+
+// x += alpha r and (update_r) r -= alpha q, alpha = red[0..1] / red[2] per rhs; x FP32 native,
+// r and q FP16 with per-site norms.  Thread per (site, rhs).
+__global__ void k_mr_update_h(void* __restrict__ x, void* __restrict__ r16, float* __restrict__ rn,
+                              const void* __restrict__ q16, const float* __restrict__ qn, int V,
+                              const double* __restrict__ red, const int* __restrict__ active, int update_r) {
+  const int rhs = blockIdx.y;
+  if (active && !active[rhs]) return;
+  const double qq = red[rhs * 3 + 2];
+  if (!(qq > 0.0)) return;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const cpx<float> al{float(red[rhs * 3 + 0] / qq), float(red[rhs * 3 + 1] / qq)};
+  const size_t fh = spinor_h_bytes(V), ff = spinor_field_bytes<float>(V);
+  char* rr = reinterpret_cast<char*>(r16) + fh * rhs;
+  char* xr = reinterpret_cast<char*>(x) + ff * rhs;
+  cpx<float> rv[12], xv[12];
+  load_spinor_h(rr, V, v, rv);
+  const float rs = rn[(size_t)V * rhs + v];
+  load_spinor<float>(xr, V, v, xv);
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    rv[i] = rs * rv[i];
+    cfma(xv[i], al, rv[i]);
+  }
+  store_spinor<float>(xr, V, v, xv);
+  if (!update_r) return;
+  cpx<float> qv[12];
+  load_spinor_h(reinterpret_cast<const char*>(q16) + fh * rhs, V, v, qv);
+  const float qs = qn[(size_t)V * rhs + v];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) rv[i] = rv[i] - (qs * al) * qv[i];
+  store_spinor_h(rr, rn + (size_t)V * rhs, V, v, rv);
+}
+
+// native FP32 <-> FP16 with per-site norms (test entry point)
+__global__ void k_spinor_to_h(const void* __restrict__ in, void* __restrict__ out16, float* __restrict__ norm, int V) {
+  const int rhs = blockIdx.y, v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  cpx<float> t[12];
+  load_spinor<float>(reinterpret_cast<const char*>(in) + spinor_field_bytes<float>(V) * rhs, V, v, t);
+  store_spinor_h(reinterpret_cast<char*>(out16) + spinor_h_bytes(V) * rhs, norm + (size_t)V * rhs, V, v, t);
+}
+__global__ void k_spinor_from_h(const void* __restrict__ in16, const float* __restrict__ norm, void* __restrict__ out,
+                                int V) {
+  const int rhs = blockIdx.y, v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  cpx<float> t[12];
+  load_spinor_h(reinterpret_cast<const char*>(in16) + spinor_h_bytes(V) * rhs, V, v, t);
+  const float sc = norm[(size_t)V * rhs + v];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) t[i] = sc * t[i];
+  store_spinor<float>(reinterpret_cast<char*>(out) + spinor_field_bytes<float>(V) * rhs, V, v, t);
+}
+
+// ------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------
 void pack_gauge(int prec, const double* canon, void* out, int V, cudaStream_t s) {
@@ -177,6 +320,41 @@ void dslash(int prec, void* out, const void* in, const void* b, const void* gaug
   if (prec == WMG_PREC_DOUBLE) WMG_DS(double);
   else WMG_DS(float);
 #undef WMG_DS
+}
+
+void dslash_h(int in16, void* out16, float* out_norm, const void* in, const float* in_norm, const void* b,
+              const void* gauge, const Geom& g, const double* mass_dev, const int* active, int nrhs, int red,
+              const RedBuf* rb, cudaStream_t s) {
+  count_launch();
+  const int nb = dslash_blocks(g.V);
+  const unsigned grid = (unsigned)nb * nrhs;
+  RedBuf r = rb ? *rb : RedBuf{nullptr, nullptr, nullptr};
+  if (in16) {
+    if (red == 2) k_dslash_h<1, 2><<<grid, kDslashThreads, 0, s>>>(out16, out_norm, in, in_norm, b, gauge, g, mass_dev, active, nrhs, nb, r);
+    else k_dslash_h<1, 0><<<grid, kDslashThreads, 0, s>>>(out16, out_norm, in, in_norm, b, gauge, g, mass_dev, active, nrhs, nb, r);
+  } else {
+    if (red == 2) k_dslash_h<0, 2><<<grid, kDslashThreads, 0, s>>>(out16, out_norm, in, in_norm, b, gauge, g, mass_dev, active, nrhs, nb, r);
+    else k_dslash_h<0, 0><<<grid, kDslashThreads, 0, s>>>(out16, out_norm, in, in_norm, b, gauge, g, mass_dev, active, nrhs, nb, r);
+  }
+}
+
+void mr_update_h(void* x, void* r16, float* rn, const void* q16, const float* qn, int V, int nrhs, const double* red,
+                 const int* active, bool update_r, cudaStream_t s) {
+  count_launch();
+  dim3 grid((V + 127) / 128, nrhs);
+  k_mr_update_h<<<grid, 128, 0, s>>>(x, r16, rn, q16, qn, V, red, active, update_r ? 1 : 0);
+}
+
+void spinor_to_h(const void* in, void* out16, float* norm, int V, int nrhs, cudaStream_t s) {
+  count_launch();
+  dim3 grid((V + 127) / 128, nrhs);
+  k_spinor_to_h<<<grid, 128, 0, s>>>(in, out16, norm, V);
+}
+
+void spinor_from_h(const void* in16, const float* norm, void* out, int V, int nrhs, cudaStream_t s) {
+  count_launch();
+  dim3 grid((V + 127) / 128, nrhs);
+  k_spinor_from_h<<<grid, 128, 0, s>>>(in16, norm, out, V);
 }
 
 }  // namespace wmg

@@ -28,6 +28,16 @@ int dslash_blocks(int V);
 // red = 0: none; 1: |out|^2 per rhs into rb->result[rhs]; 2: {Re, Im <out,in>, |out|^2}.
 void dslash(int prec, void* out, const void* in, const void* b, const void* gauge, const Geom& g,
             const double* mass_dev, const int* active, int nrhs, int red, const RedBuf* rb, cudaStream_t s);
+// the smoother's FP16 storage (per-site norms, FP32 arithmetic): out16 = [b -] D in with in
+// FP32 native (in16 = 0) or FP16 (in16 = 1); red = 2 adds per-rhs {<out, in>, |out|^2}
+void dslash_h(int in16, void* out16, float* out_norm, const void* in, const float* in_norm, const void* b,
+              const void* gauge, const Geom& g, const double* mass_dev, const int* active, int nrhs, int red,
+              const RedBuf* rb, cudaStream_t s);
+// x += alpha r, r -= alpha q (update_r) with x FP32 native and r, q FP16
+void mr_update_h(void* x, void* r16, float* rn, const void* q16, const float* qn, int V, int nrhs, const double* red,
+                 const int* active, bool update_r, cudaStream_t s);
+void spinor_to_h(const void* in, void* out16, float* norm, int V, int nrhs, cudaStream_t s);
+void spinor_from_h(const void* in16, const float* norm, void* out, int V, int nrhs, cudaStream_t s);
 
 // ---- BLAS on flat complex vectors: n complex numbers per rhs, rhs stride n (blas.cu) ----
 int blas_blocks(size_t n);
@@ -46,7 +56,7 @@ void blas_xmy(int prec, const void* x, void* y, size_t n, int nrhs, cudaStream_t
 // y = x + y
 void blas_xpy(int prec, const void* x, void* y, size_t n, int nrhs, cudaStream_t s);
 // MR update: alpha = qr/qq from red[r*3 + {0,1,2}]; x += alpha r; r -= alpha q
-void blas_mr_update(int prec, void* x, void* r, const void* q, size_t n, int nrhs, const double* red,
+void blas_mr_update(int prec, void* x, void* r, const void* q, size_t n, int nrhs, const double* red, bool update_r,
                     const int* active, cudaStream_t s);
 // CG (normal equations) helpers, scalars per rhs in `cg` (see blas.cu)
 struct CgScalars {
@@ -87,6 +97,12 @@ void restrict_fine(int prec, const void* P, const Blocking& bk, const void* in, 
                    const int* active, cudaStream_t s);
 void prolong_fine(int prec, const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
                   const int* active, cudaStream_t s);
+// FP32 vectors, FP16 null vectors (false: blocking not handled, use the FP32 copy)
+bool restrict_fine_h(const void* P16, const Blocking& bk, const void* in, void* out, int nrhs, const int* active,
+                     cudaStream_t s);
+bool prolong_fine_h(const void* P16, const Blocking& bk, const void* in, void* out, int nrhs, const int* active,
+                    cudaStream_t s);
+void convert_to_half2(const void* src64, void* dst16, size_t n, cudaStream_t s);  // complex FP64 -> (re, im) FP16
 // coarse level: coarse vectors [rhs][Vf][nf] <-> [rhs][Vc][2N]; P = N coarse fields
 void restrict_coarse(int prec, const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
                      const int* active, cudaStream_t s);
@@ -124,6 +140,7 @@ bool coarse_tc05_supported(int n);
 void stencil_to_tc05(int prec, const void* A, int Vc, int n, const float* scale, void* out, cudaStream_t s);
 void coarse_apply_tc05(const void* A16, const float* sA, const Geom& g, int n, const void* in, void* out, int nrhs,
                        const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s);
+int coarse_mma_error();   // 1 if a bounded wait of the mma.sync coarse kernel ever expired (synchronises)
 int coarse_tc05_error();  // 1 if a bounded tcgen05 wait ever expired (synchronises)
 // convert a stencil between precisions
 void stencil_convert(int prec_d, void* dst, int prec_s, const void* src, size_t count, cudaStream_t s);

@@ -229,8 +229,37 @@ void level_apply(wmg_ctx* c, int l, int prec, const void* in, void* out, int nrh
   }
 }
 
+// MR smoother on the fine level with FP16 storage of r and q (per-site norms); x, b FP32
+static wmg_status mr_half(wmg_ctx* c, void* x, const void* b, int nrhs, int nu, const int* active) {
+  const int V = c->fine.V;
+  void *r, *q, *rn, *qn;
+  TRY(ws_get(c, "mr_r16", spinor_h_bytes(V) * nrhs, &r));
+  TRY(ws_get(c, "mr_q16", spinor_h_bytes(V) * nrhs, &q));
+  TRY(ws_get(c, "mr_rn", (size_t)V * nrhs * sizeof(float), &rn));
+  TRY(ws_get(c, "mr_qn", (size_t)V * nrhs * sizeof(float), &qn));
+  RedBuf rb = redbuf(c, RES_MR);
+  const int na = nact_of(c, active, nrhs);
+  const double hb = (double)V * (48.0 * 4.0) + (double)na * V * (96.0 + 52.0);  // gauge, x + b in, r out
+  {
+    ProfScope ps(c, PROF_DSLASH_LO, hb + (double)na * V * 96.0, na);
+    dslash_h(0, r, (float*)rn, x, nullptr, b, c->gauge[1], c->fine, c->d_mass, active, nrhs, 0, nullptr, c->stream);
+  }
+  for (int i = 0; i < nu; ++i) {
+    {
+      ProfScope ps(c, PROF_DSLASH_LO, (double)V * 192.0 + (double)na * V * 104.0, na);
+      dslash_h(1, q, (float*)qn, r, (const float*)rn, nullptr, c->gauge[1], c->fine, c->d_mass, active, nrhs, 2, &rb,
+               c->stream);
+    }
+    ProfScope ps(c, PROF_BLAS, 0);
+    mr_update_h(x, r, (float*)rn, q, (const float*)qn, V, nrhs, rb.result, active, i + 1 < nu, c->stream);
+  }
+  return check(c, "mr (FP16 storage)");
+}
+
 // MR smoother (nu steps) on level l: x is the initial guess and the result, b the rhs
 wmg_status mr(wmg_ctx* c, int l, int prec, void* x, const void* b, int nrhs, int nu, const int* active) {
+  if (l == 0 && prec == WMG_PREC_SINGLE && c->prm.prec_smoother == WMG_PREC_HALF && nu > 0)
+    return mr_half(c, x, b, nrhs, nu, active);
   void *r, *q;
   TRY(vec_ws(c, l, "mr_r", prec, nrhs, &r));
   TRY(vec_ws(c, l, "mr_q", prec, nrhs, &q));
@@ -255,7 +284,7 @@ wmg_status mr(wmg_ctx* c, int l, int prec, void* x, const void* b, int nrhs, int
       blas_dot_norm(prec, q, r, n, nrhs, rb, c->stream);
     }
     ProfScope ps(c, PROF_BLAS, 0);
-    blas_mr_update(prec, x, r, q, n, nrhs, rb.result, active, c->stream);
+    blas_mr_update(prec, x, r, q, n, nrhs, rb.result, i + 1 < nu, active, c->stream);  // last r unused
   }
   return check(c, "mr");
 }
@@ -429,7 +458,10 @@ wmg_status cycle(wmg_ctx* c, int l, int last, int prec, const void* r, void* e, 
     }
     {
       ProfScope ps(c, PROF_RESTRICT, transfer_bytes(c, l, prec, nact_of(c, active, nrhs)), nact_of(c, active, nrhs));
-      if (l == 0) restrict_fine(prec, L.P[prec], L.bk, rin, rc, nrhs, active, c->stream);
+      if (l == 0) {
+        if (!(prec == WMG_PREC_SINGLE && L.P16 && restrict_fine_h(L.P16, L.bk, rin, rc, nrhs, active, c->stream)))
+          restrict_fine(prec, L.P[prec], L.bk, rin, rc, nrhs, active, c->stream);
+      }
       else restrict_coarse(prec, L.P[prec], L.bk, rin, rc, nrhs, active, c->stream);
     }
     TRY(cycle(c, lc, last, prec, rc, ec, nrhs, active));
@@ -437,7 +469,10 @@ wmg_status cycle(wmg_ctx* c, int l, int last, int prec, const void* r, void* e, 
     if (rep > 0) TRY(vec_ws(c, l, "cyc_p", prec, nrhs, &dst));
     {
       ProfScope ps(c, PROF_PROLONG, transfer_bytes(c, l, prec, nact_of(c, active, nrhs)), nact_of(c, active, nrhs));
-      if (l == 0) prolong_fine(prec, L.P[prec], L.bk, ec, dst, nrhs, active, c->stream);
+      if (l == 0) {
+        if (!(prec == WMG_PREC_SINGLE && L.P16 && prolong_fine_h(L.P16, L.bk, ec, dst, nrhs, active, c->stream)))
+          prolong_fine(prec, L.P[prec], L.bk, ec, dst, nrhs, active, c->stream);
+      }
       else prolong_coarse(prec, L.P[prec], L.bk, ec, dst, nrhs, active, c->stream);
     }
     if (rep > 0) blas_xpy(prec, dst, e, n, nrhs, c->stream);
@@ -507,6 +542,7 @@ wmg_status orthonormalise(wmg_ctx* c, int l) {
     block_gs(l == 0, L.P[0], L.bk, c->d_flag, c->stream);
   }
   blas_convert(WMG_PREC_SINGLE, L.P[1], WMG_PREC_DOUBLE, L.P[0], L.nvec_elems(), L.bk.N, nullptr, c->stream);
+  if (L.P16) convert_to_half2(L.P[0], L.P16, L.nvec_elems() * L.bk.N, c->stream);
   CU(c, cudaMemcpyAsync(c->h_pin_i, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CU(c, cudaStreamSynchronize(c->stream));
   if (c->h_pin_i[0]) {
@@ -722,7 +758,7 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
     }
   }
   CU(c, cudaStreamSynchronize(s));
-  if (use_mg && c->L[c->nlev - 1].A05 && coarse_tc05_error()) {
+  if (use_mg && c->prm.coarse_tc && (coarse_mma_error() || coarse_tc05_error())) {
     c->err = "a bounded wait of the tensor-core coarse stencil expired";
     return WMG_ETIMEOUT;
   }

@@ -6,6 +6,8 @@
 // components 0..5; coarse: dof 0..N-1) and the second half chirality -1.  P is stored as N
 // fields of the finer lattice (P_alpha, both chiralities in one field); the coarse dof of
 // column (s, alpha) is s*N + alpha.
+#include <cuda_fp16.h>
+
 #include "kernels.h"
 
 namespace wmg {
@@ -28,6 +30,43 @@ WMG_D void lds2(const cpx<double>* p, cpx<double>& a, cpx<double>& b) {
   a = p[0];
   b = p[1];
 }
+WMG_D void cp_async8(void* dst_smem, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
+               "l"(src)
+               : "memory");
+}
+
+// Storage of the null vectors P for the transfers: complex in the vectors' precision, or FP16
+// (__half2 = re, im) read into FP32.  One component pair (the unit of the native layout) is
+// kPair bytes; copy() moves it global -> shared asynchronously, ld2() reads it back widened.
+template <typename PT> struct PSt;
+template <> struct PSt<cpx<float>> {
+  static constexpr int kPair = 16;
+  WMG_D static void copy(void* dst, const void* src) { cp_async16(dst, src); }
+  WMG_D static void ld2(const cpx<float>* p, cf& a, cf& b) { lds2(p, a, b); }
+  WMG_D static cpx<float> zero() { return cf{0.f, 0.f}; }
+};
+template <> struct PSt<cpx<double>> {
+  static constexpr int kPair = 32;
+  WMG_D static void copy(void* dst, const void* src) {
+    cp_async16(dst, src);
+    cp_async16((char*)dst + 16, (const char*)src + 16);
+  }
+  WMG_D static void ld2(const cpx<double>* p, cd& a, cd& b) { lds2(p, a, b); }
+  WMG_D static cpx<double> zero() { return cd{0.0, 0.0}; }
+};
+template <> struct PSt<__half2> {
+  static constexpr int kPair = 8;
+  WMG_D static void copy(void* dst, const void* src) { cp_async8(dst, src); }
+  WMG_D static void ld2(const __half2* p, cf& a, cf& b) {
+    const uint2 t = *reinterpret_cast<const uint2*>(p);
+    const float2 x = __half22float2(*reinterpret_cast<const __half2*>(&t.x));
+    const float2 y = __half22float2(*reinterpret_cast<const __half2*>(&t.y));
+    a = {x.x, x.y};
+    b = {y.x, y.y};
+  }
+  WMG_D static __half2 zero() { return __floats2half2_rn(0.f, 0.f); }
+};
 
 WMG_D int block_site(const Blocking& bk, int xc, int e) {
   int c[4];
@@ -167,25 +206,24 @@ __global__ void k_prolong_fine(const void* __restrict__ P, Blocking bk, const vo
 // right-hand sides; the thread's P entries stream through a kPSt-deep cp.async ring in shared
 // memory (each thread reads back only its own copies, so no block barrier is needed).
 constexpr int kPSt = 6;
-template <typename R, int RC>
+template <typename R, typename PT, int RC>
 __global__ void __launch_bounds__(256) k_prolong_fine3(const void* __restrict__ P, Blocking bk,
                                                        const void* __restrict__ in, void* __restrict__ out, int nrhs,
                                                        const int* __restrict__ active) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  constexpr int CB = 2 * sizeof(cpx<R>);  // bytes of one component pair
+  constexpr int CB = PSt<PT>::kPair;  // bytes of one component pair of P
   const int xc = blockIdx.x, c = blockIdx.y, r0 = blockIdx.z * RC;
   const int N = bk.N, V = bk.fine.V, s = c / 3, T = blockDim.x;
   cpx<R>* phi = reinterpret_cast<cpx<R>*>(smraw);  // [N][RC]
   unsigned char* ring = smraw + (((size_t)N * RC * sizeof(cpx<R>) + 15) / 16) * 16;  // [kPSt][T][CB]
-  const size_t fb = spinor_field_bytes<R>(V);
+  const size_t fb = spinor_field_bytes<R>(V), fbp = (size_t)V * 6 * CB;  // vector / P field bytes
   const int e = threadIdx.x;
   const bool live = e < bk.bs;
   const int v = live ? block_site(bk, xc, e) : 0;
   const char* src = (const char*)P + ((size_t)c * V + v) * CB;
   auto issue = [&](int a) {
     if (live && a < N)
-#pragma unroll
-      for (int q = 0; q < CB / 16; ++q) cp_async16(ring + ((size_t)(a % kPSt) * T + e) * CB + 16 * q, src + fb * a + 16 * q);
+      PSt<PT>::copy(ring + ((size_t)(a % kPSt) * T + e) * CB, src + fbp * a);
     cp_async_commit();
   };
 #pragma unroll
@@ -202,7 +240,7 @@ __global__ void __launch_bounds__(256) k_prolong_fine3(const void* __restrict__ 
   for (int a = 0; a < N; ++a) {
     cp_async_wait<kPSt - 2>();
     cpx<R> p0, p1;
-    lds2(reinterpret_cast<const cpx<R>*>(ring + ((size_t)(a % kPSt) * T + e) * CB), p0, p1);
+    PSt<PT>::ld2(reinterpret_cast<const PT*>(ring + ((size_t)(a % kPSt) * T + e) * CB), p0, p1);
     issue(a + kPSt - 1);
 #pragma unroll
     for (int rr = 0; rr < RC; rr += 2) {
@@ -231,23 +269,26 @@ __global__ void __launch_bounds__(256) k_prolong_fine3(const void* __restrict__ 
 // partials are summed in warp order at the end, so the result for one right-hand side does not
 // depend on the others or on TR.
 constexpr int kRWarps = 8;  // warps of the restrict CTA
-template <typename R, int TA, int TR, int S>
+template <typename R, typename PT, int TA, int TR, int S>
 __global__ void __launch_bounds__(kRWarps * 32) k_restrict_fine3(const void* __restrict__ P, Blocking bk,
                                                                  const void* __restrict__ in, void* __restrict__ out,
                                                                  int nrhs, const int* __restrict__ active) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int NA = 8 * TA, RC = 4 * TR;
-  constexpr int CB = 2 * sizeof(cpx<R>);
+  constexpr int CB = 2 * sizeof(cpx<R>), CBP = PSt<PT>::kPair;  // bytes of a component pair: x, P
   constexpr int K = 6 * S, Kp = K + 2;            // complex k per chunk, padded row length
   constexpr int KW = ((K / 2 + kRWarps - 1) / kRWarps) * 2;  // even k slice per warp
   constexpr int NT = kRWarps * 32, CE = 3 * S;    // threads; (component pair, site) items per row
   constexpr int RSTEP = NT / CE;                  // rows staged per pass of the CTA
-  constexpr size_t stage = (size_t)(NA + RC) * Kp;  // complex per stage buffer
+  // stage buffer q: P rows [NA][Kp] (PT), then x rows [RC][Kp] (complex R), 16-byte aligned
+  constexpr size_t pbytes = (((size_t)NA * Kp * sizeof(PT) + 15) / 16) * 16;
+  constexpr size_t stage = pbytes + (size_t)RC * Kp * sizeof(cpx<R>);
   const int xc = blockIdx.x, s = blockIdx.y, r0 = blockIdx.z * RC;
   const int N = bk.N, V = bk.fine.V, bs = bk.bs;
-  cpx<R>* buf = reinterpret_cast<cpx<R>*>(smraw);  // [2][NA + RC][Kp]: P rows, then x rows
-  int* vsite = reinterpret_cast<int*>(buf + 2 * stage);  // [bs] fine site of each block site
-  const size_t fb = spinor_field_bytes<R>(V);
+  auto Pbuf = [&](int q) { return reinterpret_cast<PT*>(smraw + (size_t)q * stage); };
+  auto Xbuf = [&](int q) { return reinterpret_cast<cpx<R>*>(smraw + (size_t)q * stage + pbytes); };
+  int* vsite = reinterpret_cast<int*>(smraw + 2 * stage);  // [bs] fine site of each block site
+  const size_t fb = spinor_field_bytes<R>(V), fbp = (size_t)V * 6 * CBP;  // vector / P field bytes
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, ag = lane >> 2, rg = lane & 3;
   const int kb = warp * KW, ke = min(K, kb + KW);
   unsigned rmask = 0;  // right-hand sides of this chunk that are present and active
@@ -256,8 +297,8 @@ __global__ void __launch_bounds__(kRWarps * 32) k_restrict_fine3(const void* __r
   for (int e = threadIdx.x; e < bs; e += NT) vsite[e] = block_site(bk, xc, e);
   // P rows alpha >= N stay zero in both buffers
   for (int i = threadIdx.x; i < (NA - N) * Kp; i += NT) {
-    buf[(size_t)N * Kp + i] = cpx<R>{R(0), R(0)};
-    buf[stage + (size_t)N * Kp + i] = cpx<R>{R(0), R(0)};
+    Pbuf(0)[(size_t)N * Kp + i] = PSt<PT>::zero();
+    Pbuf(1)[(size_t)N * Kp + i] = PSt<PT>::zero();
   }
   __syncthreads();
   // this thread stages item (cc, e) of rows row0, row0 + RSTEP, ...
@@ -266,18 +307,22 @@ __global__ void __launch_bounds__(kRWarps * 32) k_restrict_fine3(const void* __r
   const int nchunks = (bs + S - 1) / S;
   auto issue = [&](int q) {
     if (q < nchunks && row0 < RSTEP) {
-      cpx<R>* st = buf + (size_t)(q & 1) * stage + (cc * S + e) * 2;
       const bool in_blk = q * S + e < bs;
-      const size_t off = (coff + (in_blk ? vsite[q * S + e] : 0)) * CB;
+      const size_t site = coff + (in_blk ? vsite[q * S + e] : 0);
       for (int row = row0; row < N + RC; row += RSTEP) {
-        const bool isP = row < N;
-        cpx<R>* dst = st + (size_t)(isP ? row : NA + row - N) * Kp;
-        if (in_blk && (isP || ((rmask >> (row - N)) & 1u))) {
-          const char* src = (const char*)(isP ? P : in) + fb * (isP ? row : r0 + row - N) + off;
-#pragma unroll
-          for (int h = 0; h < CB / 16; ++h) cp_async16((char*)dst + 16 * h, src + 16 * h);
+        if (row < N) {
+          PT* dst = Pbuf(q & 1) + (size_t)row * Kp + (cc * S + e) * 2;
+          if (in_blk) PSt<PT>::copy(dst, (const char*)P + fbp * row + site * CBP);
+          else dst[0] = dst[1] = PSt<PT>::zero();
         } else {
-          dst[0] = dst[1] = cpx<R>{R(0), R(0)};
+          cpx<R>* dst = Xbuf(q & 1) + (size_t)(row - N) * Kp + (cc * S + e) * 2;
+          if (in_blk && ((rmask >> (row - N)) & 1u)) {
+            const char* src = (const char*)in + fb * (r0 + row - N) + site * CB;
+#pragma unroll
+            for (int h = 0; h < CB / 16; ++h) cp_async16((char*)dst + 16 * h, src + 16 * h);
+          } else {
+            dst[0] = dst[1] = cpx<R>{R(0), R(0)};
+          }
         }
       }
     }
@@ -293,13 +338,13 @@ __global__ void __launch_bounds__(kRWarps * 32) k_restrict_fine3(const void* __r
     issue(q + 1);
     cp_async_wait<1>();
     __syncthreads();
-    const cpx<R>* Ps = buf + (size_t)(q & 1) * stage;
-    const cpx<R>* Xs = Ps + (size_t)NA * Kp;
+    const PT* Ps = Pbuf(q & 1);
+    const cpx<R>* Xs = Xbuf(q & 1);
 #pragma unroll 2
     for (int k = kb; k < ke; k += 2) {
       cpx<R> p[TA][2], x[TR][2];
 #pragma unroll
-      for (int i = 0; i < TA; ++i) lds2(Ps + (size_t)(ag * TA + i) * Kp + k, p[i][0], p[i][1]);
+      for (int i = 0; i < TA; ++i) PSt<PT>::ld2(Ps + (size_t)(ag * TA + i) * Kp + k, p[i][0], p[i][1]);
 #pragma unroll
       for (int j = 0; j < TR; ++j) lds2(Xs + (size_t)(rg * TR + j) * Kp + k, x[j][0], x[j][1]);
 #pragma unroll
@@ -313,7 +358,7 @@ __global__ void __launch_bounds__(kRWarps * 32) k_restrict_fine3(const void* __r
     __syncthreads();
   }
   cp_async_wait<0>();
-  cpx<R>* red = buf;  // [warp][NA][RC]
+  cpx<R>* red = reinterpret_cast<cpx<R>*>(smraw);  // [warp][NA][RC]
 #pragma unroll
   for (int i = 0; i < TA; ++i)
 #pragma unroll
@@ -328,63 +373,79 @@ __global__ void __launch_bounds__(kRWarps * 32) k_restrict_fine3(const void* __r
   }
 }
 
-template <typename R, int TA, int TR, int S>
+template <typename R, typename PT, int TA, int TR, int S>
+static size_t restrict3_smem(int bs) {
+  constexpr int NA = 8 * TA, RC = 4 * TR, Kp = 6 * S + 2;
+  const size_t pbytes = (((size_t)NA * Kp * sizeof(PT) + 15) / 16) * 16;
+  const size_t stage = 2 * (pbytes + (size_t)RC * Kp * sizeof(cpx<R>)) + (size_t)bs * sizeof(int);
+  const size_t redb = (size_t)kRWarps * NA * RC * sizeof(cpx<R>);
+  return stage > redb ? stage : redb;
+}
+
+template <typename R, typename PT, int TA, int TR, int S>
 static void launch_restrict_fine3s(const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
                                    const int* active, cudaStream_t s) {
-  constexpr int NA = 8 * TA, RC = 4 * TR;
-  const size_t redb = (size_t)kRWarps * NA * RC * sizeof(cpx<R>);
-  const size_t stage = 2 * (size_t)(NA + RC) * (6 * S + 2) * sizeof(cpx<R>) + (size_t)bk.bs * sizeof(int);
-  const size_t smem = stage > redb ? stage : redb;
-  static const cudaError_t attr = cudaFuncSetAttribute(k_restrict_fine3<R, TA, TR, S>,
+  constexpr int RC = 4 * TR;
+  static const cudaError_t attr = cudaFuncSetAttribute(k_restrict_fine3<R, PT, TA, TR, S>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   (void)attr;
   dim3 g(bk.coarse.V, 2, (nrhs + RC - 1) / RC);
-  k_restrict_fine3<R, TA, TR, S><<<g, kRWarps * 32, smem, s>>>(P, bk, in, out, nrhs, active);
+  k_restrict_fine3<R, PT, TA, TR, S><<<g, kRWarps * 32, restrict3_smem<R, PT, TA, TR, S>(bk.bs), s>>>(P, bk, in, out,
+                                                                                                      nrhs, active);
 }
 
 // sites per staged chunk: 16, or 8 when two 16-site stages would not fit in shared memory
-template <typename R, int TA, int TR>
+template <typename R, typename PT, int TA, int TR>
 static void launch_restrict_fine3(const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
                                   const int* active, cudaStream_t s) {
-  constexpr size_t big = 2 * (size_t)(8 * TA + 4 * TR) * (6 * 16 + 2) * sizeof(cpx<R>);
-  if (big + (size_t)bk.bs * sizeof(int) <= 200 * 1024)
-    launch_restrict_fine3s<R, TA, TR, 16>(P, bk, in, out, nrhs, active, s);
+  if (restrict3_smem<R, PT, TA, TR, 16>(bk.bs) <= 200 * 1024)
+    launch_restrict_fine3s<R, PT, TA, TR, 16>(P, bk, in, out, nrhs, active, s);
   else
-    launch_restrict_fine3s<R, TA, TR, 8>(P, bk, in, out, nrhs, active, s);
+    launch_restrict_fine3s<R, PT, TA, TR, 8>(P, bk, in, out, nrhs, active, s);
 }
 
-template <typename R, int TA>
+template <typename R, typename PT, int TA>
 static void restrict_fine3_tr(const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
                               const int* active, cudaStream_t s) {
-  if (nrhs <= 4) launch_restrict_fine3<R, TA, 1>(P, bk, in, out, nrhs, active, s);
-  else if (nrhs <= 8) launch_restrict_fine3<R, TA, 2>(P, bk, in, out, nrhs, active, s);
-  else launch_restrict_fine3<R, TA, 3>(P, bk, in, out, nrhs, active, s);
+  if (nrhs <= 4) launch_restrict_fine3<R, PT, TA, 1>(P, bk, in, out, nrhs, active, s);
+  else if (nrhs <= 8) launch_restrict_fine3<R, PT, TA, 2>(P, bk, in, out, nrhs, active, s);
+  else launch_restrict_fine3<R, PT, TA, 3>(P, bk, in, out, nrhs, active, s);
 }
 
-template <typename R>
+template <typename R, typename PT>
 static void restrict_fine3(const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
                            const int* active, cudaStream_t s) {
   const int ta = (bk.N + 7) / 8;
-  if (ta <= 1) restrict_fine3_tr<R, 1>(P, bk, in, out, nrhs, active, s);
-  else if (ta <= 2) restrict_fine3_tr<R, 2>(P, bk, in, out, nrhs, active, s);
-  else if (ta <= 3) restrict_fine3_tr<R, 3>(P, bk, in, out, nrhs, active, s);
-  else if (ta <= 4) restrict_fine3_tr<R, 4>(P, bk, in, out, nrhs, active, s);
-  else if (ta <= 6) restrict_fine3_tr<R, 6>(P, bk, in, out, nrhs, active, s);
-  else restrict_fine3_tr<R, 8>(P, bk, in, out, nrhs, active, s);
+  if (ta <= 1) restrict_fine3_tr<R, PT, 1>(P, bk, in, out, nrhs, active, s);
+  else if (ta <= 2) restrict_fine3_tr<R, PT, 2>(P, bk, in, out, nrhs, active, s);
+  else if (ta <= 3) restrict_fine3_tr<R, PT, 3>(P, bk, in, out, nrhs, active, s);
+  else if (ta <= 4) restrict_fine3_tr<R, PT, 4>(P, bk, in, out, nrhs, active, s);
+  else if (ta <= 6) restrict_fine3_tr<R, PT, 6>(P, bk, in, out, nrhs, active, s);
+  else restrict_fine3_tr<R, PT, 8>(P, bk, in, out, nrhs, active, s);
 }
 
-template <typename R, int RC>
+template <typename R, typename PT, int RC>
 static void launch_prolong_fine3(const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
                                  const int* active, cudaStream_t s) {
   dim3 g(bk.coarse.V, 6, (nrhs + RC - 1) / RC);
   const int T = ((bk.bs + 31) / 32) * 32;
-  const size_t smem = (((size_t)bk.N * RC * sizeof(cpx<R>) + 15) / 16) * 16 + (size_t)kPSt * T * 2 * sizeof(cpx<R>);
-  static const cudaError_t attr = cudaFuncSetAttribute(k_prolong_fine3<R, RC>,
+  const size_t smem =
+      (((size_t)bk.N * RC * sizeof(cpx<R>) + 15) / 16) * 16 + (size_t)kPSt * T * PSt<PT>::kPair;
+  static const cudaError_t attr = cudaFuncSetAttribute(k_prolong_fine3<R, PT, RC>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   (void)attr;
-  k_prolong_fine3<R, RC><<<g, T, smem, s>>>(P, bk, in, out, nrhs, active);
+  k_prolong_fine3<R, PT, RC><<<g, T, smem, s>>>(P, bk, in, out, nrhs, active);
 }
 
+template <typename R, typename PT>
+static void prolong_fine3(const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
+                          const int* active, cudaStream_t s) {
+  if (nrhs <= 2) launch_prolong_fine3<R, PT, 2>(P, bk, in, out, nrhs, active, s);
+  else if (nrhs <= 4) launch_prolong_fine3<R, PT, 4>(P, bk, in, out, nrhs, active, s);
+  else if (sizeof(R) == 8) launch_prolong_fine3<R, PT, 4>(P, bk, in, out, nrhs, active, s);
+  else if (nrhs <= 8) launch_prolong_fine3<R, PT, 8>(P, bk, in, out, nrhs, active, s);
+  else launch_prolong_fine3<R, PT, 12>(P, bk, in, out, nrhs, active, s);
+}
 
 // ------------------------------------------------------------------------------------
 // restrict / prolong between coarse levels: fields [rhs][Vf][nf] -> [rhs][Vc][2N]
@@ -598,12 +659,40 @@ static void launch_restrict_fine(const void* P, const Blocking& bk, const void* 
   k_restrict_fine<R, RC><<<g, 128, smem, s>>>(P, bk, in, out, nrhs, active);
 }
 
+// FP32 vectors with FP16 null vectors (the native layout with __half2 elements); false when the
+// blocking is outside what the staged kernels handle (the caller then uses the FP32 copy).
+bool restrict_fine_h(const void* P16, const Blocking& bk, const void* in, void* out, int nrhs, const int* active,
+                     cudaStream_t s) {
+  if (bk.N > 64) return false;
+  count_launch();
+  restrict_fine3<float, __half2>(P16, bk, in, out, nrhs, active, s);
+  return true;
+}
+bool prolong_fine_h(const void* P16, const Blocking& bk, const void* in, void* out, int nrhs, const int* active,
+                    cudaStream_t s) {
+  if (bk.bs > 256 || bk.N > 64) return false;
+  count_launch();
+  prolong_fine3<float, __half2>(P16, bk, in, out, nrhs, active, s);
+  return true;
+}
+
+__global__ void k_to_half2(const cd* __restrict__ src, __half2* __restrict__ dst, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = __floats2half2_rn((float)src[i].re, (float)src[i].im);
+}
+void convert_to_half2(const void* src64, void* dst16, size_t n, cudaStream_t s) {
+  count_launch();
+  size_t b = (n + 255) / 256;
+  if (b > 148 * 16) b = 148 * 16;
+  k_to_half2<<<(unsigned)b, 256, 0, s>>>((const cd*)src64, (__half2*)dst16, n);
+}
+
 void restrict_fine(int prec, const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
                    const int* active, cudaStream_t s) {
   count_launch();
   if (bk.N <= 64) {
-    if (prec == WMG_PREC_DOUBLE) restrict_fine3<double>(P, bk, in, out, nrhs, active, s);
-    else restrict_fine3<float>(P, bk, in, out, nrhs, active, s);
+    if (prec == WMG_PREC_DOUBLE) restrict_fine3<double, cpx<double>>(P, bk, in, out, nrhs, active, s);
+    else restrict_fine3<float, cpx<float>>(P, bk, in, out, nrhs, active, s);
     return;
   }
   if (prec == WMG_PREC_DOUBLE) {
@@ -629,15 +718,8 @@ void prolong_fine(int prec, const void* P, const Blocking& bk, const void* in, v
                   const int* active, cudaStream_t s) {
   count_launch();
   if (bk.bs <= 256 && bk.N <= 64) {
-    if (prec == WMG_PREC_DOUBLE) {
-      if (nrhs <= 2) launch_prolong_fine3<double, 2>(P, bk, in, out, nrhs, active, s);
-      else launch_prolong_fine3<double, 4>(P, bk, in, out, nrhs, active, s);
-    } else {
-      if (nrhs <= 2) launch_prolong_fine3<float, 2>(P, bk, in, out, nrhs, active, s);
-      else if (nrhs <= 4) launch_prolong_fine3<float, 4>(P, bk, in, out, nrhs, active, s);
-      else if (nrhs <= 8) launch_prolong_fine3<float, 8>(P, bk, in, out, nrhs, active, s);
-      else launch_prolong_fine3<float, 12>(P, bk, in, out, nrhs, active, s);
-    }
+    if (prec == WMG_PREC_DOUBLE) prolong_fine3<double, cpx<double>>(P, bk, in, out, nrhs, active, s);
+    else prolong_fine3<float, cpx<float>>(P, bk, in, out, nrhs, active, s);
     return;
   }
   if (prec == WMG_PREC_DOUBLE) {

@@ -89,3 +89,27 @@ WMG_D void hop_accumulate(int mu, const cpx<R> u[9], const cpx<R> nb[12], cpx<R>
   else link_mul_dag(u, h, uh);
   spin_reconstruct_add<SIGN>(mu, uh, acc);
 }
+
+// The same hop with the neighbour spinor held as s * nb (FP16 storage with the per-site scale
+// s): the scale is applied in the accumulation, acc += s * [h', -/+ C h'].
+template <int SIGN>
+WMG_D void hop_accumulate_scaled(int mu, const cpx<float> u[9], const cpx<float> nb[12], float sc, cpx<float> acc[12]) {
+  cpx<float> h[6], uh[6];
+  spin_project<SIGN>(mu, nb, h);
+  if (SIGN > 0) link_mul(u, h, uh);
+  else link_mul_dag(u, h, uh);
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int col = spin_B_col(mu, j), ph = spin_C_ph(mu, j);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const cpx<float> t = uh[3 * j + a];
+      acc[3 * j + a].re = fmaf(sc, t.re, acc[3 * j + a].re);
+      acc[3 * j + a].im = fmaf(sc, t.im, acc[3 * j + a].im);
+      const cpx<float> c = mul_phase(uh[3 * col + a], ph);
+      const float g = SIGN > 0 ? -sc : sc;
+      acc[3 * (2 + j) + a].re = fmaf(g, c.re, acc[3 * (2 + j) + a].re);
+      acc[3 * (2 + j) + a].im = fmaf(g, c.im, acc[3 * (2 + j) + a].im);
+    }
+  }
+}

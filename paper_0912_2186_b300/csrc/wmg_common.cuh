@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 #include <cstddef>
 
@@ -177,6 +178,39 @@ WMG_D void store_spinor(void* base, int V, int v, const cpx<R> s[12]) {
 }
 // byte offset of right-hand side r of a native fine field
 template <typename R> WMG_HD size_t spinor_field_bytes(int V) { return (size_t)V * 12 * 2 * sizeof(R); }
+
+// FP16 fine spinor with a per-site scale (the smoother's storage): [rhs][6][V] chunks of two
+// complex numbers as __half2 (re, im) pairs (8 bytes) plus norm[rhs][V] = max |Re|, |Im| of the
+// site's 24 reals; stored values are the components divided by the norm.
+WMG_HD size_t spinor_h_bytes(int V) { return (size_t)V * 6 * 8; }
+WMG_D void load_spinor_h(const void* base, int V, int v, cpx<float> s[12]) {
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const uint2 t = __ldg(reinterpret_cast<const uint2*>(base) + (size_t)c * V + v);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&t.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&t.y));
+    s[2 * c] = {a.x, a.y};
+    s[2 * c + 1] = {b.x, b.y};
+  }
+}
+// s / norm rounded to FP16; returns the norm written
+WMG_D float store_spinor_h(void* base, float* norm, int V, int v, const cpx<float> s[12]) {
+  float m = 0.f;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(s[k].re), fabsf(s[k].im)));
+  const float inv = m > 0.f ? 1.f / m : 0.f;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const __half2 a = __floats2half2_rn(s[2 * c].re * inv, s[2 * c].im * inv);
+    const __half2 b = __floats2half2_rn(s[2 * c + 1].re * inv, s[2 * c + 1].im * inv);
+    uint2 t;
+    t.x = *reinterpret_cast<const unsigned*>(&a);
+    t.y = *reinterpret_cast<const unsigned*>(&b);
+    reinterpret_cast<uint2*>(base)[(size_t)c * V + v] = t;
+  }
+  norm[v] = m;
+  return m;
+}
 
 // native gauge layout: [mu][3][V] chunks (rows 0 and 1 of U_mu(x), element e = 3*row + col,
 // chunk c holds e = 2c, 2c+1); row 2 = conj(row0 x row1) is rebuilt on load.

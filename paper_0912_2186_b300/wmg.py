@@ -45,6 +45,8 @@ class Params(ctypes.Structure):
         ("coarse_tc", ctypes.c_int),
         ("reliable_delta", ctypes.c_double),
         ("seed", ctypes.c_uint64),
+        ("prec_nullvec", ctypes.c_int),
+        ("prec_smoother", ctypes.c_int),
     ]
 
 

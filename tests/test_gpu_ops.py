@@ -59,12 +59,12 @@ def test_dslash_parity(W, prec, dims):
     assert rel_err(got, want) < TOL[prec]
 
 
-def _hier(W, dims, blocks, nvecs, prec, seed=10, m=-0.1, eps=0.6, tc=1):
+def _hier(W, dims, blocks, nvecs, prec, seed=10, m=-0.1, eps=0.6, tc=1, **kw):
     U = synth.gauge_field(dims, eps, seed)
     ctx = W.Context(dims)
     ctx.load_gauge(U)
     ctx.set_mass(m)
-    p = W.default_params(nlevels=len(blocks) + 1, block=blocks, nvec=nvecs, prec_sloppy=prec, coarse_tc=tc)
+    p = W.default_params(nlevels=len(blocks) + 1, block=blocks, nvec=nvecs, prec_sloppy=prec, coarse_tc=tc, **kw)
     v0 = synth.setup_starts(dims, nvecs[0], seed + 1)
     ctx.import_nullvecs(0, v0, p)
     op = mg.WilsonOp(U, m)
@@ -176,3 +176,52 @@ def test_tensor_core_coarse_apply(W, dims, block, N, tc):
         got = host(out).reshape(want.shape)
         for r in range(nrhs):                    # per right-hand side (each has its own FP16 scale)
             assert rel_err(got[r], want[r]) < 2e-3
+
+
+@pytest.mark.parametrize("dims,block,N", [((8, 8, 8, 12), (4, 4, 4, 4), 24), ((6, 4, 4, 6), (2, 2, 2, 2), 8)])
+def test_half_nullvec_transfers(W, dims, block, N):
+    """FP16 null vectors (prec_nullvec = HALF) in restrict / prolong with FP32 vectors, against the
+    FP64 oracle at the FP16 storage tolerance 2e-3, per right-hand side; 7 rhs = a ragged chunk."""
+    h = _hier(W, dims, [block], [N], 1, prec_nullvec=2)
+    ctx, P0, A1 = h["ctx"], h["P"][0], h["A"][1]
+    nrhs = 7
+    psi = synth.gaussian_spinors(dims, nrhs, 40)
+    nc, n = A1.D.reshape(-1, 9, A1.n, A1.n).shape[0], A1.n
+    fin = native_fine(ctx.V, nrhs, 1)
+    ctx.pack(1, dev(psi), fin, nrhs)
+    co = coarse_buf(nc * n, nrhs, 1)
+    ctx.restrict(0, 2, fin, co, nrhs)
+    got = host(co).reshape(nrhs, -1)
+    for r in range(nrhs):
+        assert rel_err(got[r], mg.restrict(P0, psi[r], block)) < 2e-3
+    phi = synth.coarse_starts(A1.dims, n, nrhs, 41)
+    fout = native_fine(ctx.V, nrhs, 1)
+    ctx.prolong(0, 2, dev(phi.reshape(-1).astype(np.complex64)), fout, nrhs)
+    canon = dev(np.zeros_like(psi))
+    ctx.unpack(1, fout, canon, nrhs)
+    got = host(canon)
+    for r in range(nrhs):
+        assert rel_err(got[r], mg.prolong(P0, phi[r], block)) < 2e-3
+
+
+@pytest.mark.parametrize("dims", [(6, 4, 4, 6), (8, 8, 8, 8)])
+def test_dslash_half_storage_parity(W, dims):
+    """The smoother's FP16 storage (per-site norm, FP32 arithmetic): D applied to an FP16-rounded
+    input and rounded to FP16 again, against the FP64 oracle at 2e-3 per right-hand side; a
+    per-rhs amplitude spread of 1e6 checks that the per-site scaling keeps small fields exact."""
+    U = synth.gauge_field(dims, 0.6, 5)
+    m = -0.27
+    nrhs = 3
+    b = synth.gaussian_spinors(dims, nrhs, 6)
+    b[1] *= 1e-6
+    ctx = W.Context(dims)
+    ctx.load_gauge(U)
+    ctx.set_mass(m)
+    xin, xout = native_fine(ctx.V, nrhs, 1), native_fine(ctx.V, nrhs, 1)
+    ctx.pack(1, dev(b), xin, nrhs)
+    ctx.apply_D(2, xin, xout, nrhs)
+    canon = dev(np.zeros_like(b))
+    ctx.unpack(1, xout, canon, nrhs)
+    got = host(canon)
+    for r in range(nrhs):
+        assert rel_err(got[r], dirac.apply_D(U, b[r], m)) < 2e-3

@@ -124,3 +124,39 @@ def test_tcgen05_coarse_solve(W):
     for r in range(3):
         assert info[r]["converged"]
         assert oracle_resid(U, CFG1["m"], b[r], xs[r]) <= 1.05e-10
+
+
+def test_half_nullvec_solve(W):
+    """FP16 null vectors in the cycle: every solution still meets the FP64 true residual 1e-10."""
+    ctx, U, p = _ctx(W, CFG1, 1, prec_nullvec=2)
+    b = synth.gaussian_spinors(CFG1["dims"], 3, 17)
+    x = dev(np.zeros_like(b))
+    st, info = ctx.solve(dev(b), x, 3)
+    xs = host(x)
+    for r in range(3):
+        assert info[r]["converged"]
+        assert oracle_resid(U, CFG1["m"], b[r], xs[r]) <= 1.05e-10
+
+
+def test_half_storage_three_level_solve(W):
+    """The reduced-precision configuration on a small lattice: 3 levels, FP16 smoother storage,
+    FP16 null vectors, tensor-core coarse stencils, 12 Gaussian right-hand sides; every solution
+    meets the FP64 true residual 1e-10 (oracle D) and the batch result equals the single solve."""
+    dims = (8, 8, 8, 16)
+    U = synth.gauge_field(dims, 0.7, 35)
+    ctx = W.Context(dims)
+    ctx.load_gauge(U)
+    ctx.set_mass(-0.05)
+    p = W.default_params(nlevels=3, block=[(2, 2, 2, 2), (2, 2, 2, 2)], nvec=[8, 8], prec_sloppy=1,
+                         prec_smoother=2, prec_nullvec=2, coarse_tc=1)
+    ctx.setup(p, synth.setup_starts(dims, 8, 36))
+    b = synth.gaussian_spinors(dims, 12, 37)
+    x = dev(np.zeros_like(b))
+    _, info = ctx.solve(dev(b), x, 12)
+    xs = host(x)
+    for r in range(12):
+        assert info[r]["converged"]
+        assert oracle_resid(U, -0.05, b[r], xs[r]) <= 1.05e-10
+    x1 = dev(np.zeros_like(b[5:6]))
+    _, i1 = ctx.solve(dev(b[5:6]), x1, 1)
+    assert np.array_equal(host(x1)[0], xs[5]) and i1[0]["iters"] == info[5]["iters"]
