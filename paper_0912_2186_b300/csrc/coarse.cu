@@ -222,177 +222,187 @@ void hop_split_fine(int prec, const void* gauge, const void* P, const Blocking& 
     k_hop_split_fine<float><<<grid, 128, 0, s>>>(gauge, P, bk, float(4.0 + mass), col0, out9);
 }
 
-// Fused Galerkin construction on the fine level: CTA per (column c, coarse block) with the
-// columns of one block adjacent in the grid, so that the block's vectors P are shared in L2;
-// one thread per block site (bs <= 256, every block extent >= 2).  Thread x computes the terms
-// of D g_c at x (g_c = P_alpha restricted to chirality s in every block): the diagonal and the
-// hops whose neighbour lies in the block go to the self slot, each hop leaving the block to the
-// slot of its direction (at most one per direction).  For every row (s', alpha') the products
-// <P_alpha'(x)|_s', term> are summed over the block by warp shuffles, per-warp partials in
-// shared memory, and a final fixed-order sum; the CTA writes column c of all 9 blocks.
-template <typename R>
-__global__ void __launch_bounds__(256) k_galerkin_fine(const void* __restrict__ gauge, const void* __restrict__ P,
-                                                       Blocking bk, R diag, void* __restrict__ Aout) {
+// Fused Galerkin construction on the fine level, as per-block complex GEMMs.  For coarse site
+// xc and stencil slot q (0 = self, 1 + 2 mu + sg = the block across the face of direction mu,
+// sg = 0 forward / 1 backward):
+//     A_q[(s', alpha')][(s, a)] = sum_{x, k in s'} conj(P_alpha'(x)[k]) T_q,(s,a)(x)[k]
+// where T_0 = (4 + m) g + the hops of D g that stay in the block and T_q (q > 0) is the hop of
+// D g from across face q, g = P_a restricted to chirality s (every block).  One CTA of 256
+// threads per coarse site takes the slots in turn and the contributing sites (all block sites
+// for the self slot, the face sites for a face slot) in chunks of kGc sites: thread (j, a)
+// stages P_a(x_j) (both chiralities) in shared memory as the GEMM's row operand and computes the
+// 2N term columns (s, a) of its site; then thread (s', ta, tj) accumulates rows (s', ta + 8 i)
+// x columns tj + 16 i over the chunk's components of chirality s'.  Fixed summation order; the
+// CTA writes the 9 blocks [site][9][col][row].
+constexpr int kGc = 8;           // sites per chunk
+constexpr int kGThreads = 256;
+template <typename R, int RT>    // RT = ceil(N / 8): rows (and columns) per thread
+__global__ void __launch_bounds__(kGThreads, sizeof(R) == 4 ? 2 : 1) k_galerkin_fine(const void* __restrict__ gauge, const void* __restrict__ P,
+                                                             Blocking bk, R diag, void* __restrict__ Aout) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = bk.N, n = 2 * N;
-  const int c = blockIdx.x % n, xc = blockIdx.x / n;
-  const int s = c / N, a = c % N;
-  const int e = threadIdx.x;
-  const int nw = blockDim.x >> 5, warp = e >> 5, lane = e & 31;
-  R* red = reinterpret_cast<R*>(smraw);  // [nw][N][9][2 chir][2 re/im]
+  const int N = bk.N, n = 2 * N, xc = blockIdx.x;
+  const int PW = N + 1, MW = n + 1;  // padded row widths (complex)
+  cpx<R>* Ps = reinterpret_cast<cpx<R>*>(smraw);    // [kGc * 12][PW]: P_alpha(x_j)[k]
+  cpx<R>* Ms = Ps + (size_t)kGc * 12 * PW;          // [kGc * 12][MW]: T column (s, a) at (x_j, k)
   const Geom& g = bk.fine;
   const size_t fb = spinor_field_bytes<R>(g.V);
-  const char* Pa = (const char*)P + fb * a;
-  cpx<R> self[12], face[4][12];
-  int fslot[4];
-  const bool live = e < bk.bs;
-  int v = 0;
-  if (live) {
-    // block site e -> fine site
-    int cc[4];
-    site_coords(bk.coarse, xc, cc);
-    int o[4];
-    o[0] = e % bk.b[0];
-    int t = e / bk.b[0];
-    o[1] = t % bk.b[1];
-    t /= bk.b[1];
-    o[2] = t % bk.b[2];
-    o[3] = t / bk.b[2];
-    int f[4];
-    for (int i = 0; i < 4; ++i) f[i] = cc[i] * bk.b[i] + o[i];
-    v = site_index(g, f);
-    int crd[4];
-    site_coords(g, v, crd);
-    load_spinor<R>(Pa, g.V, v, self);
+  const int t = threadIdx.x;
+  // producer role: site j of the chunk, vector a
+  const int pj = t / N, pa = t % N;
+  const bool producer = t < kGc * N;
+  // GEMM role: row chirality ts, rows ta + 8 i, columns tj + 16 i
+  const int tj = t & 15, ta = (t >> 4) & 7, ts = t >> 7;
+  int cc[4];
+  site_coords(bk.coarse, xc, cc);
+  for (int q = 0; q < 9; ++q) {
+    const int mu = (q - 1) >> 1, sg = (q - 1) & 1;
+    // sites of this slot: all bs block sites (self) or the bs / b_mu on face q
+    const int nsite = q == 0 ? bk.bs : bk.bs / bk.b[mu];
+    cpx<R> acc[RT][RT];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) self[k] = ((k < 6) == (s == 0)) ? diag * self[k] : cpx<R>{R(0), R(0)};
+    for (int i = 0; i < RT; ++i)
 #pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      fslot[mu] = -1;
+      for (int k = 0; k < RT; ++k) acc[i][k] = cpx<R>{R(0), R(0)};
+    for (int j0 = 0; j0 < nsite; j0 += kGc) {
+      if (producer) {
+        const int j = j0 + pj;
+        cpx<R>* prow = Ps + (size_t)(pj * 12) * PW + pa;       // column a of the chunk's P rows
+        cpx<R>* m0 = Ms + (size_t)(pj * 12) * MW + pa;         // term column (s = 0, a)
+        cpx<R>* m1 = m0 + N;                                   // term column (s = 1, a)
+        if (j < nsite) {
+          // block offsets of site j of this slot's list
+          int o[4];
+          if (q == 0) {
+            int e = j;
+            o[0] = e % bk.b[0];
+            e /= bk.b[0];
+            o[1] = e % bk.b[1];
+            e /= bk.b[1];
+            o[2] = e % bk.b[2];
+            o[3] = e / bk.b[2];
+          } else {
+            int e = j;
 #pragma unroll
-      for (int k = 0; k < 12; ++k) face[mu][k] = cpx<R>{R(0), R(0)};
+            for (int d = 0; d < 4; ++d) {
+              if (d == mu) {
+                o[d] = sg == 0 ? bk.b[d] - 1 : 0;
+              } else {
+                o[d] = e % bk.b[d];
+                e /= bk.b[d];
+              }
+            }
+          }
+          int f[4];
 #pragma unroll
-      for (int sg = 0; sg < 2; ++sg) {
-        const int sign = sg ? -1 : +1;
-        const int nb = neighbour(g, v, crd, mu, sign);
-        cpx<R> u[9], xg[12], tt[12];
-        load_spinor<R>(Pa, g.V, nb, xg);
+          for (int d = 0; d < 4; ++d) f[d] = cc[d] * bk.b[d] + o[d];
+          const int v = site_index(g, f);
+          const char* Pa = (const char*)P + fb * pa;
+          {
+            cpx<R> self[12];
+            load_spinor<R>(Pa, g.V, v, self);
 #pragma unroll
-        for (int k = 0; k < 12; ++k)
-          if ((k < 6) != (s == 0)) xg[k] = cpx<R>{R(0), R(0)};
+            for (int k = 0; k < 12; ++k) {
+              prow[(size_t)k * PW] = self[k];
+              const bool up = k < 6;
+              m0[(size_t)k * MW] = (q == 0 && up) ? diag * self[k] : cpx<R>{R(0), R(0)};
+              m1[(size_t)k * MW] = (q == 0 && !up) ? diag * self[k] : cpx<R>{R(0), R(0)};
+            }
+          }
 #pragma unroll
-        for (int k = 0; k < 12; ++k) tt[k] = cpx<R>{R(0), R(0)};
-        if (sg == 0) {
-          load_link<R>(gauge, g.V, mu, v, u);
-          hop_accumulate<+1>(mu, u, xg, tt);
+          for (int m2 = 0; m2 < 4; ++m2)
+#pragma unroll
+            for (int s2 = 0; s2 < 2; ++s2) {
+              const int sign = s2 ? -1 : +1;
+              const bool inb = same_block(f[m2], g.L[m2], bk.b[m2], sign);
+              // self slot: the in-block hops; face slot q: its own hop when it leaves the block
+              const bool take = q == 0 ? inb : (m2 == mu && s2 == sg && !inb);
+              if (!take) continue;
+              const int nb = neighbour(g, v, f, m2, sign);
+              cpx<R> u[9], x[12];
+              load_spinor<R>(Pa, g.V, nb, x);
+#pragma unroll
+              for (int k = 0; k < 12; ++k) x[k] = R(-0.5) * x[k];
+              if (s2 == 0) load_link<R>(gauge, g.V, m2, v, u);
+              else load_link<R>(gauge, g.V, m2, nb, u);
+#pragma unroll
+              for (int sc = 0; sc < 2; ++sc) {  // the hop of the chirality-sc part of P_a
+                cpx<R> h[12], t[12];
+#pragma unroll
+                for (int k = 0; k < 12; ++k) {
+                  h[k] = ((k < 6) == (sc == 0)) ? x[k] : cpx<R>{R(0), R(0)};
+                  t[k] = cpx<R>{R(0), R(0)};
+                }
+                if (s2 == 0) hop_accumulate<+1>(m2, u, h, t);
+                else hop_accumulate<-1>(m2, u, h, t);
+                cpx<R>* mc = sc == 0 ? m0 : m1;
+#pragma unroll
+                for (int k = 0; k < 12; ++k) mc[(size_t)k * MW] += t[k];
+              }
+            }
         } else {
-          load_link<R>(gauge, g.V, mu, nb, u);
-          hop_accumulate<-1>(mu, u, xg, tt);
+#pragma unroll
+          for (int k = 0; k < 12; ++k) {
+            prow[(size_t)k * PW] = cpx<R>{R(0), R(0)};
+            m0[(size_t)k * MW] = m1[(size_t)k * MW] = cpx<R>{R(0), R(0)};
+          }
         }
-        const bool inb = same_block(crd[mu], g.L[mu], bk.b[mu], sign);
+      }
+      __syncthreads();
+      // GEMM: rows (ts, ta + 8 i), columns tj + 16 i, over the chunk's components of chirality ts
+      const int jn = min(kGc, nsite - j0);
+      for (int j = 0; j < jn; ++j)
+#pragma unroll 2
+        for (int kk = 0; kk < 6; ++kk) {
+          const int k = j * 12 + 6 * ts + kk;
+          cpx<R> pv[RT], mv[RT];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) {
-          const cpx<R> h = R(-0.5) * tt[k];
-          if (inb) self[k] += h;
-          else face[mu][k] = h;
+          for (int i = 0; i < RT; ++i) {
+            const int al = ta + 8 * i, col = tj + 16 * i;
+            pv[i] = al < N ? Ps[(size_t)k * PW + al] : cpx<R>{R(0), R(0)};
+            mv[i] = col < n ? Ms[(size_t)k * MW + col] : cpx<R>{R(0), R(0)};
+          }
+#pragma unroll
+          for (int i = 0; i < RT; ++i)
+#pragma unroll
+            for (int i2 = 0; i2 < RT; ++i2) cfmac(acc[i][i2], pv[i], mv[i2]);
         }
-        if (!inb) fslot[mu] = 1 + 2 * mu + sg;
+      __syncthreads();
+    }
+    cpx<R>* A = reinterpret_cast<cpx<R>*>(Aout);
+#pragma unroll
+    for (int i = 0; i < RT; ++i)
+#pragma unroll
+      for (int i2 = 0; i2 < RT; ++i2) {
+        const int al = ta + 8 * i, col = tj + 16 * i2;
+        if (al < N && col < n) A[(((size_t)xc * 9 + q) * n + col) * n + ts * N + al] = acc[i][i2];
       }
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < 12; ++k) self[k] = cpx<R>{R(0), R(0)};
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      fslot[mu] = -1;
-#pragma unroll
-      for (int k = 0; k < 12; ++k) face[mu][k] = cpx<R>{R(0), R(0)};
-    }
   }
-  for (int ap = 0; ap < N; ++ap) {
-    cpx<R> p[12];
-    if (live) load_spinor<R>((const char*)P + fb * ap, g.V, v, p);
-    else
-#pragma unroll
-      for (int k = 0; k < 12; ++k) p[k] = cpx<R>{R(0), R(0)};
-    R acc[9][4];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = R(0);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      const int ch = k < 6 ? 0 : 2;
-      cpx<R> d = cmulc(p[k], self[k]);
-      acc[0][ch] += d.re;
-      acc[0][ch + 1] += d.im;
-    }
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      cpx<R> d0{R(0), R(0)}, d1{R(0), R(0)};
-#pragma unroll
-      for (int k = 0; k < 6; ++k) cfmac(d0, p[k], face[mu][k]);
-#pragma unroll
-      for (int k = 6; k < 12; ++k) cfmac(d1, p[k], face[mu][k]);
-      // the thread's face term of direction mu belongs to slot 1 + 2 mu (+) or 2 + 2 mu (-)
-      const bool minus = fslot[mu] == 2 + 2 * mu;
-#pragma unroll
-      for (int sg = 0; sg < 2; ++sg) {
-        const bool mine = (sg == 1) == minus;
-        acc[1 + 2 * mu + sg][0] += mine ? d0.re : R(0);
-        acc[1 + 2 * mu + sg][1] += mine ? d0.im : R(0);
-        acc[1 + 2 * mu + sg][2] += mine ? d1.re : R(0);
-        acc[1 + 2 * mu + sg][3] += mine ? d1.im : R(0);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 9; ++q)
-#pragma unroll
-      for (int w = 0; w < 4; ++w)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[q][w] += __shfl_xor_sync(0xffffffffu, acc[q][w], o);
-    if (lane == 0)
-#pragma unroll
-      for (int q = 0; q < 9; ++q)
-#pragma unroll
-        for (int w = 0; w < 4; ++w) red[(((size_t)warp * N + ap) * 9 + q) * 4 + w] = acc[q][w];
-  }
-  __syncthreads();
-  // column c of the 9 blocks: rows s'*N + alpha', summed over warps in order
-  cpx<R>* A = reinterpret_cast<cpx<R>*>(Aout);
-  for (int i = threadIdx.x; i < 9 * n; i += blockDim.x) {
-    const int q = i / n, row = i % n, sp = row / N, ap = row % N;
-    R re = 0, im = 0;
-    for (int w = 0; w < nw; ++w) {
-      re += red[(((size_t)w * N + ap) * 9 + q) * 4 + 2 * sp];
-      im += red[(((size_t)w * N + ap) * 9 + q) * 4 + 2 * sp + 1];
-    }
-    A[(((size_t)xc * 9 + q) * n + c) * n + row] = cpx<R>{re, im};
-  }
+}
+
+template <typename R, int RT>
+static void launch_galerkin_fine(const void* gauge, const void* P, const Blocking& bk, R diag, void* A, cudaStream_t s) {
+  const size_t smem = (size_t)kGc * 12 * ((bk.N + 1) + (2 * bk.N + 1)) * sizeof(cpx<R>);
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(k_galerkin_fine<R, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  (void)attr;
+  k_galerkin_fine<R, RT><<<bk.coarse.V, kGThreads, smem, s>>>(gauge, P, bk, diag, A);
+}
+
+template <typename R>
+static void galerkin_fine_rt(const void* gauge, const void* P, const Blocking& bk, R diag, void* A, cudaStream_t s) {
+  const int rt = (bk.N + 7) / 8;
+  if (rt <= 1) launch_galerkin_fine<R, 1>(gauge, P, bk, diag, A, s);
+  else if (rt == 2) launch_galerkin_fine<R, 2>(gauge, P, bk, diag, A, s);
+  else if (rt == 3) launch_galerkin_fine<R, 3>(gauge, P, bk, diag, A, s);
+  else launch_galerkin_fine<R, 4>(gauge, P, bk, diag, A, s);
 }
 
 bool galerkin_fine_fused(int prec, const void* gauge, const void* P, const Blocking& bk, double mass, void* A,
                          cudaStream_t s) {
-  if (bk.bs > 256) return false;
-  for (int i = 0; i < 4; ++i)
-    if (bk.b[i] < 2) return false;
+  if (bk.N > 32 || kGc * bk.N > kGThreads) return false;
   count_launch();
-  const int T = ((bk.bs + 31) / 32) * 32;
-  const size_t smem = (size_t)(T / 32) * bk.N * 9 * 4 * (prec == WMG_PREC_DOUBLE ? 8 : 4);
-  dim3 grid((unsigned)(2 * bk.N) * bk.coarse.V);
-  if (prec == WMG_PREC_DOUBLE) {
-    static const bool attr = [] {
-      cudaFuncSetAttribute(k_galerkin_fine<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      return true;
-    }();
-    (void)attr;
-    k_galerkin_fine<double><<<grid, T, smem, s>>>(gauge, P, bk, 4.0 + mass, A);
-  } else {
-    static const bool attr = [] {
-      cudaFuncSetAttribute(k_galerkin_fine<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      return true;
-    }();
-    (void)attr;
-    k_galerkin_fine<float><<<grid, T, smem, s>>>(gauge, P, bk, float(4.0 + mass), A);
-  }
+  if (prec == WMG_PREC_DOUBLE) galerkin_fine_rt<double>(gauge, P, bk, 4.0 + mass, A, s);
+  else galerkin_fine_rt<float>(gauge, P, bk, float(4.0 + mass), A, s);
   return true;
 }
 

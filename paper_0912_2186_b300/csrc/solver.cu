@@ -495,8 +495,7 @@ wmg_status galerkin(wmg_ctx* c, int l, int prec) {
   int ncol = (int)std::max<size_t>(1, budget / (9 * fb));
   ncol = std::min(ncol, n);
   void *out9 = nullptr, *rs = nullptr;
-  const bool fused = l == 0 && c->use_fused_galerkin && L.bk.bs <= 256 && L.bk.b[0] > 1 && L.bk.b[1] > 1 &&
-                     L.bk.b[2] > 1 && L.bk.b[3] > 1;
+  const bool fused = l == 0 && c->use_fused_galerkin && L.bk.N <= 32;
   if (!fused) {
     TRY(ws_get(c, "gal_out9", (size_t)ncol * 9 * fb, &out9));
     TRY(ws_get(c, "gal_rs", (size_t)ncol * 9 * C.g.V * n * csize(prec), &rs));
