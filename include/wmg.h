@@ -269,6 +269,11 @@ wmg_status wmg_profile_get(wmg_ctx* ctx, int cls, double* ms, long long* launche
 /* Total number of CUDA kernels this library has launched in this process (all contexts). */
 wmg_status wmg_launch_count(long long* n);
 
+/* Measured FMA throughput of the current device in TFLOP/s (2 flops per FMA), FP32 and FP64
+ * (the ALU roofline denominators): dependent FMA chains over 8 CTAs of 256 threads per SM,
+ * best of 3 timed launches.  Synchronises the device; takes well under a second. */
+wmg_status wmg_probe_alu_peaks(double* fp32_tflops, double* fp64_tflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -109,6 +109,7 @@ def load():
         "wmg_server_destroy": (i, [vp]),
         "wmg_profile_enable": (i, [vp, i]),
         "wmg_launch_count": (i, [P(ctypes.c_longlong)]),
+        "wmg_probe_alu_peaks": (i, [P(d), P(d)]),
         "wmg_profile_get": (i, [vp, i, P(d), P(ctypes.c_longlong), P(d), P(d)]),
     }
     for name, (res, args) in sig.items():
@@ -140,6 +141,15 @@ def default_params(**kw):
         else:
             setattr(p, k, v)
     return p
+
+
+def probe_alu_peaks():
+    """Measured FP32 and FP64 FMA throughput of the current device, TFLOP/s."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    st = load().wmg_probe_alu_peaks(ctypes.byref(a), ctypes.byref(b))
+    if st != 0:
+        raise RuntimeError(f"wmg_probe_alu_peaks: status {st}")
+    return {"fp32_tflops": a.value, "fp64_tflops": b.value}
 
 
 def launch_count():
