@@ -173,6 +173,9 @@ wmg_status wmg_export_nullvecs(wmg_ctx* ctx, int level, double* host);
  * [site][9][2N][2N] complex double, slot k = 0 self, 1 + 2 mu + (0: +mu, 1: -mu),
  * row-major blocks: (D^ phi)(xhat) = sum_k D^[xhat][k] phi(xhat + k).  Synchronises. */
 wmg_status wmg_export_coarse(wmg_ctx* ctx, int level, double* host);
+/* Device bytes the context holds now (links in FP64 and FP32, every copy of the transfer and
+ * coarse operators, solver workspaces grown so far, reduction buffers). */
+wmg_status wmg_device_bytes(const wmg_ctx* ctx, size_t* bytes);
 /* Number of sites and of complex dof per site of lattice `level` (0 = fine). */
 wmg_status wmg_level_info(const wmg_ctx* ctx, int level, int* nsites, int* ndof);
 

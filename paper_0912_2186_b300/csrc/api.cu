@@ -42,6 +42,37 @@ void free_hierarchy(wmg_ctx* c) {
   c->have_hier = false;
 }
 
+}  // namespace
+
+namespace wmg {
+// device bytes the context holds now: links, transfer operators, coarse operators (all copies),
+// workspaces and reduction buffers
+size_t context_device_bytes(const wmg_ctx* c) {
+  size_t b = 0;
+  const size_t V = c->fine.V;
+  if (c->gauge[0]) b += V * 4 * 6 * sizeof(cd);
+  if (c->gauge[1]) b += V * 4 * 6 * sizeof(cf);
+  for (int l = 0; l < WMG_MAX_LEVELS; ++l) {
+    const LevelData& L = c->L[l];
+    const size_t pe = L.P[0] ? L.nvec_elems() * L.bk.N : 0;
+    if (L.P[0]) b += pe * sizeof(cd);
+    if (L.P[1]) b += pe * sizeof(cf);
+    if (L.P16) b += pe * 4;
+    const size_t ae = (size_t)L.g.V * 9 * L.ndof * L.ndof;
+    if (L.A[0]) b += ae * sizeof(cd);
+    if (L.A[1]) b += ae * sizeof(cf);
+    if (L.A16) b += stencil_mma_words(L.g.V, L.ndof) * 16;
+    if (L.sA) b += (size_t)L.g.V * sizeof(float);
+    if (L.A05) b += stencil_tc05_halves(L.g.V, L.ndof) * 2;
+  }
+  for (const auto& kv : c->ws) b += kv.second.second;
+  b += c->red_partial_n * sizeof(double);
+  return b;
+}
+}  // namespace wmg
+
+namespace {
+
 wmg_status bad(wmg_ctx* c, const std::string& what) {
   if (c) c->err = what;
   return WMG_EINVAL;
@@ -92,6 +123,28 @@ wmg_status alloc_hierarchy(wmg_ctx* c, const wmg_params* p) {
     for (int pr = 0; pr < 2; ++pr) CU(c, cudaMalloc(&L.P[pr], L.nvec_elems() * bk.N * csize(pr)));
     if (l == 0 && p->prec_nullvec == WMG_PREC_HALF)
       CU(c, cudaMalloc(&L.P16, L.nvec_elems() * bk.N * 4 /* __half2 */));
+  }
+  return WMG_OK;
+}
+
+// After a setup: with FP16 null vectors in the cycle (and a blocking their kernels take), the
+// fine level keeps only the FP16 copy of P; when the setup's workspaces (sized for N vectors at
+// once) hold more than a tenth of the device, or free memory is short, they are released and
+// regrow for the solve.
+wmg_status trim_after_setup(wmg_ctx* c) {
+  LevelData& L = c->L[0];
+  if (c->prm.prec_nullvec == WMG_PREC_HALF && L.P16 && L.bk.bs <= 256) {
+    for (int p = 0; p < 2; ++p)
+      if (L.P[p]) cudaFree(L.P[p]), L.P[p] = nullptr;
+  }
+  size_t free_b = 0, total_b = 0;
+  CU(c, cudaMemGetInfo(&free_b, &total_b));
+  size_t ws_total = 0;
+  for (const auto& kv : c->ws) ws_total += kv.second.second;
+  if (ws_total > total_b / 10 || free_b < total_b * 2 / 5) {
+    clear_graphs(c);
+    for (auto& kv : c->ws) cudaFree(kv.second.first);
+    c->ws.clear();
   }
   return WMG_OK;
 }
@@ -248,14 +301,20 @@ wmg_status wmg_setup(wmg_ctx* c, const wmg_params* p, const double* starts_host)
   const int N0 = p->nvec[0];
   const size_t V = c->fine.V;
   void *canon, *vecs;
-  TRY(ws_get(c, "stage", V * 12 * N0 * sizeof(cd), &canon));
+  // the starts go through a canonical FP64 stage one vector at a time (the stage of all N would be
+  // 49 GB on a 48^3x96 lattice); the device stream of a vector is its slice of the seed's stream
+  TRY(ws_get(c, "stage", V * 12 * sizeof(cd), &canon));
   TRY(vec_ws(c, 0, "setup_vecs", prec, N0, &vecs));
-  if (starts_host) {
-    CU(c, cudaMemcpy(canon, starts_host, V * 12 * N0 * sizeof(cd), cudaMemcpyHostToDevice));
-  } else {
-    gaussian_fill((double*)canon, V * 24 * N0, p->seed, c->stream);
+  const size_t fbp = V * 12 * (prec == WMG_PREC_DOUBLE ? sizeof(cd) : sizeof(cf));
+  for (int a = 0; a < N0; ++a) {
+    if (starts_host) {
+      CU(c, cudaMemcpyAsync(canon, starts_host + V * 24 * a, V * 12 * sizeof(cd), cudaMemcpyHostToDevice, c->stream));
+    } else {
+      gaussian_fill((double*)canon, V * 24, p->seed, V * 24 * a, c->stream);
+    }
+    pack_spinor(prec, (const double*)canon, (char*)vecs + fbp * a, c->fine.V, 1, c->stream);
   }
-  pack_spinor(prec, (const double*)canon, vecs, c->fine.V, N0, c->stream);
+  CU(c, cudaStreamSynchronize(c->stream));
   TRY(setup_level(c, 0, vecs));
   if (c->nlev == 3) {
     const int N1 = p->nvec[1];
@@ -263,12 +322,13 @@ wmg_status wmg_setup(wmg_ctx* c, const wmg_params* p, const double* starts_host)
     void *stage1, *vecs1;
     TRY(ws_get(c, "stage1", n1 * N1 * sizeof(cd), &stage1));
     TRY(vec_ws(c, 1, "setup_vecs", prec, N1, &vecs1));
-    gaussian_fill((double*)stage1, n1 * 2 * N1, p->seed + 1, c->stream);
+    gaussian_fill((double*)stage1, n1 * 2 * N1, p->seed + 1, 0, c->stream);
     blas_convert(prec, vecs1, WMG_PREC_DOUBLE, stage1, n1, N1, nullptr, c->stream);
     TRY(setup_level(c, 1, vecs1));
   }
   CU(c, cudaStreamSynchronize(c->stream));
   c->have_hier = true;
+  TRY(trim_after_setup(c));
   return WMG_OK;
 }
 
@@ -339,6 +399,12 @@ wmg_status wmg_export_coarse(wmg_ctx* c, int level, double* host) {
   for (size_t sk = 0; sk < (size_t)C.g.V * 9; ++sk)
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < n; ++j) out[(sk * n + i) * n + j] = tmp[(sk * n + j) * n + i];
+  return WMG_OK;
+}
+
+wmg_status wmg_device_bytes(const wmg_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return WMG_EINVAL;
+  *bytes = context_device_bytes(c);
   return WMG_OK;
 }
 
@@ -432,6 +498,10 @@ wmg_status wmg_restrict(wmg_ctx* c, int level, int prec, const void* fine, void*
     if (!restrict_fine_h(L.P16, L.bk, fine, coarse, nrhs, nullptr, c->stream)) return WMG_EINVAL;
     return check(c, "restrict");
   }
+  if (!L.P[prec]) {
+    c->err = "restrict: the hierarchy keeps only FP16 null vectors (use WMG_PREC_HALF)";
+    return WMG_ESTATE;
+  }
   if (level == 0) restrict_fine(prec, L.P[prec], L.bk, fine, coarse, nrhs, nullptr, c->stream);
   else restrict_coarse(prec, L.P[prec], L.bk, fine, coarse, nrhs, nullptr, c->stream);
   return check(c, "restrict");
@@ -445,6 +515,10 @@ wmg_status wmg_prolong(wmg_ctx* c, int level, int prec, const void* coarse, void
     if (level != 0 || !L.P16) return WMG_ESTATE;
     if (!prolong_fine_h(L.P16, L.bk, coarse, fine, nrhs, nullptr, c->stream)) return WMG_EINVAL;
     return check(c, "prolong");
+  }
+  if (!L.P[prec]) {
+    c->err = "prolong: the hierarchy keeps only FP16 null vectors (use WMG_PREC_HALF)";
+    return WMG_ESTATE;
   }
   if (level == 0) prolong_fine(prec, L.P[prec], L.bk, coarse, fine, nrhs, nullptr, c->stream);
   else prolong_coarse(prec, L.P[prec], L.bk, coarse, fine, nrhs, nullptr, c->stream);

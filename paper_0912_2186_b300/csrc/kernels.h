@@ -17,7 +17,7 @@ long long graph_launch_count();  // kernels launched inside device-side graph lo
 void count_launch(int n = 1);
 
 // N(0,1) reals from the counter-based generator (rng.cu): out[i] depends only on (seed, i)
-void gaussian_fill(double* out, size_t n, uint64_t seed, cudaStream_t s);
+void gaussian_fill(double* out, size_t n, uint64_t seed, size_t first, cudaStream_t s);  // first % 4 == 0
 
 // ---- fine lattice (dslash.cu) ----
 void pack_gauge(int prec, const double* canon, void* out, int V, cudaStream_t s);

@@ -26,11 +26,12 @@ WMG_D uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
-// out[4 i .. 4 i + 3] = four N(0, 1) numbers from counter i
-__global__ void k_gaussian(double* out, size_t n, uint64_t seed) {
+// out[4 i .. 4 i + 3] = four N(0, 1) numbers from counter cbase + i (stream elements 4 (cbase + i) ..)
+__global__ void k_gaussian(double* out, size_t n, uint64_t seed, size_t cbase) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (4 * i >= n) return;
-  const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(i >> 32), 0u, 0u),
+  const size_t ci = cbase + i;
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)ci, (uint32_t)(ci >> 32), 0u, 0u),
                                 make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
   // (0, 1] uniforms from the top 24 bits (exact in FP32); Box-Muller in FP32 arithmetic
   const float inv = 1.0f / 16777216.0f;
@@ -44,9 +45,10 @@ __global__ void k_gaussian(double* out, size_t n, uint64_t seed) {
   for (int j = 0; j < 4 && 4 * i + j < n; ++j) out[4 * i + j] = z[j];
 }
 
-void gaussian_fill(double* out, size_t n, uint64_t seed, cudaStream_t s) {
+// out[j] = element first + j of the stream of `seed` (first a multiple of 4)
+void gaussian_fill(double* out, size_t n, uint64_t seed, size_t first, cudaStream_t s) {
   const size_t threads = (n + 3) / 4;
-  k_gaussian<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(out, n, seed);
+  k_gaussian<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(out, n, seed, first / 4);
   count_launch();
 }
 

@@ -152,12 +152,12 @@ void worker(Field* f) {
 // device bytes held by a context for its field and hierarchy plus the slot workspaces
 size_t field_footprint(const wmg_ctx* c, int nslots) {
   const double V = c->fine.V;
-  double b = V * 4 * 6 * (16 + 8);  // gauge FP64 + FP32
-  for (int l = 0; l + 1 < c->nlev; ++l) {
-    const LevelData& L = c->L[l];
-    const LevelData& C = c->L[l + 1];
-    b += (double)L.nvec_elems() * L.bk.N * (16 + 8);
-    b += (double)C.g.V * 9 * C.ndof * C.ndof * (16 + 8);
+  // links and every operator copy as allocated, plus the slot workspaces of nslots
+  double b = 0.0;
+  {
+    size_t ops = context_device_bytes(c);
+    for (const auto& kv : c->ws) ops -= kv.second.second;
+    b = (double)ops;
   }
   const int m = c->prm.gcr_restart;
   const double lo = c->prm.prec_sloppy == WMG_PREC_DOUBLE ? 16 : 8;

@@ -91,6 +91,7 @@ def load():
         "wmg_export_nullvecs": (i, [vp, i, vp]),
         "wmg_export_coarse": (i, [vp, i, vp]),
         "wmg_level_info": (i, [vp, i, P(i), P(i)]),
+        "wmg_device_bytes": (i, [vp, P(ctypes.c_size_t)]),
         "wmg_solve": (i, [vp, vp, vp, i, P(Info)]),
         "wmg_solve_dev": (i, [vp, vp, vp, i, P(Info)]),
         "wmg_solve_plain_dev": (i, [vp, vp, vp, i, P(Info)]),
@@ -220,6 +221,12 @@ class Context:
         v = np.ascontiguousarray(vecs, dtype=np.complex128)
         p = ctypes.byref(params) if params is not None else None
         return self._check(self.lib.wmg_import_nullvecs(self.h, p, int(level), _ptr(v)))
+
+    def device_bytes(self):
+        """Device bytes this context holds now (fields, operators, workspaces)."""
+        n = ctypes.c_size_t()
+        self._check(self.lib.wmg_device_bytes(self.h, ctypes.byref(n)))
+        return n.value
 
     def level_info(self, level):
         ns, nd = ctypes.c_int(), ctypes.c_int()

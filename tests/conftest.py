@@ -10,4 +10,4 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (B300, sm_103a)")
-    config.addinivalue_line("markers", "slow: longer CPU-only test")
+    config.addinivalue_line("markers", "slow: long test (minutes)")

@@ -160,3 +160,52 @@ def test_half_storage_three_level_solve(W):
     x1 = dev(np.zeros_like(b[5:6]))
     _, i1 = ctx.solve(dev(b[5:6]), x1, 1)
     assert np.array_equal(host(x1)[0], xs[5]) and i1[0]["iters"] == info[5]["iters"]
+
+
+def _big_solve(W, dims, eps, mass, params, nrhs, seed):
+    from oracle import cref
+    U = synth.gauge_field(dims, eps, seed)
+    ctx = W.Context(dims)
+    ctx.load_gauge(U)
+    ctx.set_mass(mass)
+    ctx.setup(params)
+    ctx.bytes_after_setup = ctx.device_bytes()
+    b = synth.gaussian_spinors(dims, nrhs, seed + 1)
+    x = dev(np.zeros_like(b))
+    st, info = ctx.solve(dev(b), x, nrhs)
+    xs = host(x)
+    res = []
+    for r in range(nrhs):
+        assert info[r]["converged"]
+        res.append(np.linalg.norm(b[r] - cref.apply_D(U, xs[r], mass)) / np.linalg.norm(b[r]))
+    return ctx, info, res
+
+
+@pytest.mark.slow
+def test_24x24x24x48_three_level_half_storage(W):
+    """The 24^3x48 workload at full size: epsilon = 0.7, 3 levels (4^4 then 2^4 blocks, N = 24 and
+    32), FP16 per-site-norm smoother storage, tensor-core coarse stencils, 12 Gaussian right-hand
+    sides in one batch; every true residual (oracle C operator) <= 1e-10."""
+    p = W.default_params(nlevels=3, block=[(4, 4, 4, 4), (2, 2, 2, 2)], nvec=[24, 32], prec_sloppy=1,
+                         prec_smoother=2, coarse_tc=1)
+    ctx, info, res = _big_solve(W, (24, 24, 24, 48), 0.7, -1.2, p, 12, 31)
+    assert max(res) <= 1.05e-10
+    ctx.close()
+
+
+@pytest.mark.slow
+def test_48x48x48x96_memory_and_residual(W):
+    """The 48^3x96 workload at full size: 3 levels (N = 24 / 32), FP16 null vectors in the cycle,
+    FP32 12-real links, 4 right-hand sides; every true residual (oracle C operator) <= 1e-10, and
+    the context's device footprint is reported: after the setup (links, FP16 fine null vectors,
+    coarse operators, level-2 transfer) and after the solve (plus FP64 solution and residual and
+    the FP32 flexible-GCR basis of 2 x 16 vectors per right-hand side); it fits one B300."""
+    p = W.default_params(nlevels=3, block=[(4, 4, 4, 4), (2, 2, 2, 2)], nvec=[24, 32], prec_sloppy=1,
+                         prec_nullvec=2, prec_smoother=2, coarse_tc=1)
+    ctx, info, res = _big_solve(W, (48, 48, 48, 96), 0.7, -1.2, p, 4, 51)
+    assert max(res) <= 1.05e-10
+    gb_setup, gb = ctx.bytes_after_setup / 1e9, ctx.device_bytes() / 1e9
+    print(f"48^3x96 context device footprint: {gb_setup:.1f} GB after the setup, {gb:.1f} GB after the "
+          f"4-rhs solve; iterations {[i['iters'] for i in info]}; max true residual {max(res):.2e}")
+    assert gb < 250
+    ctx.close()
