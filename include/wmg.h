@@ -106,7 +106,10 @@ typedef struct {
   int coarse_tc;                     /* with prec_sloppy = SINGLE: apply the coarse
                                         stencils on FP16 tensor cores (FP32
                                         accumulation) where 2N is 16, 32, 48 or 64:
-                                        1 = mma.sync, 2 = tcgen05 (TMEM accumulator)   */
+                                        1 = mma.sync, 2 = tcgen05 (TMEM accumulator),
+                                        3 = autotune: after each Galerkin build, time the
+                                        FP32 CUDA-core, mma.sync and tcgen05 stencils on
+                                        12 rhs and keep the fastest per level            */
   double reliable_delta;             /* FP64 reliable update when the iterated
                                         residual fell by this factor                */
   uint64_t seed;                     /* seed of the setup's Gaussian starts when no
@@ -173,6 +176,10 @@ wmg_status wmg_export_nullvecs(wmg_ctx* ctx, int level, double* host);
  * [site][9][2N][2N] complex double, slot k = 0 self, 1 + 2 mu + (0: +mu, 1: -mu),
  * row-major blocks: (D^ phi)(xhat) = sum_k D^[xhat][k] phi(xhat + k).  Synchronises. */
 wmg_status wmg_export_coarse(wmg_ctx* ctx, int level, double* host);
+/* Stencil implementation the FP32 cycle uses on coarse `level` (0 CUDA cores FP32,
+ * 1 mma.sync FP16, 2 tcgen05 FP16) and, with coarse_tc = 3, the autotuner's times in ms per
+ * 12-rhs launch of each (0 where not available); ms may be NULL. */
+wmg_status wmg_coarse_impl(const wmg_ctx* ctx, int level, int* impl, float ms[3]);
 /* Device bytes the context holds now (links in FP64 and FP32, every copy of the transfer and
  * coarse operators, solver workspaces grown so far, reduction buffers). */
 wmg_status wmg_device_bytes(const wmg_ctx* ctx, size_t* bytes);

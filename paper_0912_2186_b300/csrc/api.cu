@@ -86,6 +86,7 @@ wmg_status alloc_hierarchy(wmg_ctx* c, const wmg_params* p) {
   if (p->setup_passes < 1 || p->nu_post < 0 || p->setup_relax < 0 || p->max_iter < 1 || p->coarse_maxit < 1)
     return bad(c, "iteration counts");
   if (!(p->tol > 0) || !(p->coarse_tol > 0)) return bad(c, "tolerances must be positive");
+  if (p->coarse_tc < 0 || p->coarse_tc > 3) return bad(c, "coarse_tc must be 0..3");
   const bool half_ok = p->prec_sloppy == WMG_PREC_SINGLE;
   if (p->prec_nullvec != WMG_PREC_SINGLE && !(p->prec_nullvec == WMG_PREC_HALF && half_ok))
     return bad(c, "prec_nullvec must be SINGLE, or HALF with prec_sloppy SINGLE");
@@ -399,6 +400,16 @@ wmg_status wmg_export_coarse(wmg_ctx* c, int level, double* host) {
   for (size_t sk = 0; sk < (size_t)C.g.V * 9; ++sk)
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < n; ++j) out[(sk * n + i) * n + j] = tmp[(sk * n + j) * n + i];
+  return WMG_OK;
+}
+
+wmg_status wmg_coarse_impl(const wmg_ctx* c, int level, int* impl, float ms[3]) {
+  if (!c || !impl || level < 1 || level >= WMG_MAX_LEVELS) return WMG_EINVAL;
+  if (!c->have_hier || level >= c->nlev) return WMG_ESTATE;
+  const LevelData& L = c->L[level];
+  *impl = L.impl >= 0 ? L.impl : (L.A05 ? 2 : (L.A16 ? 1 : 0));
+  if (ms)
+    for (int i = 0; i < 3; ++i) ms[i] = c->tune_ms[level][i];
   return WMG_OK;
 }
 

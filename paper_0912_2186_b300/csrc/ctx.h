@@ -27,6 +27,8 @@ struct LevelData {
   void* A16 = nullptr;     // FP16 fragment-order copy for the tensor-core apply (or null)
   float* sA = nullptr;     // its per-site scale
   void* A05 = nullptr;     // FP16 canonical-layout copy for the tcgen05 apply (or null)
+  int impl = -1;           // FP32-cycle stencil implementation picked by the autotuner (coarse_tc 3):
+                           // 0 CUDA cores FP32, 1 mma.sync FP16, 2 tcgen05 FP16; -1 by availability
   // transfer to the next level (levels < nlev - 1)
   Blocking bk{};
   void* P[2] = {nullptr, nullptr};  // N fields of this level, per precision (P[0] = FP64)
@@ -67,6 +69,7 @@ struct wmg_ctx {
   bool use_fused_galerkin = true;              // fused fine-level Galerkin kernel
   std::map<std::string, std::pair<cudaGraphExec_t, long long>> graphs;  // + launches per replay
   int n_active = 0;                            // active right-hand sides of the current solve
+  float tune_ms[WMG_MAX_LEVELS][3] = {};       // autotuner: ms per 12-rhs launch of each stencil impl
   // instrumentation
   bool prof_on = false;
   std::vector<wmg::ProfRec> prof_pending;

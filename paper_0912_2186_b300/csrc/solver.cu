@@ -208,12 +208,49 @@ static int nact_of(const wmg_ctx* c, const int* active, int nrhs) { return activ
 void coarse_op(wmg_ctx* c, int l, int prec, const void* in, void* out, int nrhs, bool dagger, const int* active,
                const RedBuf* rb) {
   const LevelData& L = c->L[l];
-  if (prec == WMG_PREC_SINGLE && L.A05)
+  int impl = 0;
+  if (prec == WMG_PREC_SINGLE) impl = L.impl >= 0 ? L.impl : (L.A05 ? 2 : (L.A16 ? 1 : 0));
+  if (impl == 2)
     coarse_apply_tc05(L.A05, L.sA, L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, active, rb, c->stream);
-  else if (prec == WMG_PREC_SINGLE && L.A16)
+  else if (impl == 1)
     coarse_apply_mma(L.A16, L.sA, L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, active, rb, c->stream);
   else
     coarse_apply(prec, L.A[prec], L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, active, rb, c->stream);
+}
+
+// The autotuner of the FP32 cycle's coarse stencil (coarse_tc = 3): each implementation that
+// exists for this level is timed on 12 right-hand sides (3 warm-up and 10 timed launches, CUDA
+// events on the context's stream) and the fastest is kept until the next setup, so that a
+// right-hand side's arithmetic never depends on the batch it is solved in.
+static wmg_status tune_coarse(wmg_ctx* c, int l) {
+  LevelData& L = c->L[l];
+  const int nr = 12;
+  void *in, *out;
+  TRY(vec_ws(c, l, "tune_in", WMG_PREC_SINGLE, nr, &in));
+  TRY(vec_ws(c, l, "tune_out", WMG_PREC_SINGLE, nr, &out));
+  CU(c, cudaMemsetAsync(in, 0, L.nvec_elems() * nr * sizeof(cf), c->stream));
+  cudaEvent_t e0, e1;
+  CU(c, cudaEventCreate(&e0));
+  CU(c, cudaEventCreate(&e1));
+  float best = 0.f;
+  int pick = 0;
+  for (int impl = 0; impl <= 2; ++impl) {
+    if ((impl == 1 && !L.A16) || (impl == 2 && !L.A05)) continue;
+    L.impl = impl;
+    for (int i = 0; i < 3; ++i) coarse_op(c, l, WMG_PREC_SINGLE, in, out, nr, false, nullptr, nullptr);
+    CU(c, cudaEventRecord(e0, c->stream));
+    for (int i = 0; i < 10; ++i) coarse_op(c, l, WMG_PREC_SINGLE, in, out, nr, false, nullptr, nullptr);
+    CU(c, cudaEventRecord(e1, c->stream));
+    CU(c, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CU(c, cudaEventElapsedTime(&ms, e0, e1));
+    c->tune_ms[l][impl] = ms / 10.f;
+    if (impl == 0 || ms < best) best = ms, pick = impl;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  L.impl = pick;
+  return check(c, "coarse autotune");
 }
 
 // out = A_l in   (l = 0: Wilson D; l >= 1: coarse stencil with the per-rhs shift)
@@ -519,15 +556,17 @@ wmg_status galerkin(wmg_ctx* c, int l, int prec) {
     stencil_scatter(prec, rs, C.A[prec], C.g.V, n, col0, nc, c->stream);
   }
   stencil_convert(1 - prec, C.A[1 - prec], prec, C.A[prec], count, c->stream);
+  C.impl = -1;
   if (c->prm.coarse_tc && c->prm.prec_sloppy == WMG_PREC_SINGLE && n % 16 == 0 && n <= 64) {
     if (!C.A16) CU(c, cudaMalloc(&C.A16, stencil_mma_words(C.g.V, n) * 16));
     if (!C.sA) CU(c, cudaMalloc((void**)&C.sA, C.g.V * sizeof(float)));
     stencil_to_mma(WMG_PREC_SINGLE, C.A[1], C.g.V, n, C.sA, C.A16, c->stream);
-    if (c->prm.coarse_tc == 2 && coarse_tc05_supported(n)) {
+    if ((c->prm.coarse_tc == 2 || c->prm.coarse_tc == 3) && coarse_tc05_supported(n)) {
       if (!C.A05) CU(c, cudaMalloc(&C.A05, stencil_tc05_halves(C.g.V, n) * 2));
       stencil_to_tc05(WMG_PREC_SINGLE, C.A[1], C.g.V, n, C.sA, C.A05, c->stream);
     }
   }
+  if (c->prm.coarse_tc == 3 && c->prm.prec_sloppy == WMG_PREC_SINGLE) TRY(tune_coarse(c, l + 1));
   return check(c, "galerkin");
 }
 

@@ -92,6 +92,7 @@ def load():
         "wmg_export_coarse": (i, [vp, i, vp]),
         "wmg_level_info": (i, [vp, i, P(i), P(i)]),
         "wmg_device_bytes": (i, [vp, P(ctypes.c_size_t)]),
+        "wmg_coarse_impl": (i, [vp, i, P(i), P(ctypes.c_float)]),
         "wmg_solve": (i, [vp, vp, vp, i, P(Info)]),
         "wmg_solve_dev": (i, [vp, vp, vp, i, P(Info)]),
         "wmg_solve_plain_dev": (i, [vp, vp, vp, i, P(Info)]),
@@ -221,6 +222,12 @@ class Context:
         v = np.ascontiguousarray(vecs, dtype=np.complex128)
         p = ctypes.byref(params) if params is not None else None
         return self._check(self.lib.wmg_import_nullvecs(self.h, p, int(level), _ptr(v)))
+
+    def coarse_impl(self, level):
+        """(implementation of the FP32 cycle's stencil on `level`, autotuner ms per impl)."""
+        impl, ms = ctypes.c_int(), (ctypes.c_float * 3)()
+        self._check(self.lib.wmg_coarse_impl(self.h, int(level), ctypes.byref(impl), ms))
+        return impl.value, list(ms)
 
     def device_bytes(self):
         """Device bytes this context holds now (fields, operators, workspaces)."""

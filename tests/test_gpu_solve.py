@@ -209,3 +209,18 @@ def test_48x48x48x96_memory_and_residual(W):
           f"4-rhs solve; iterations {[i['iters'] for i in info]}; max true residual {max(res):.2e}")
     assert gb < 250
     ctx.close()
+
+
+def test_autotuned_coarse_stencil(W):
+    """coarse_tc = 3: the setup times the CUDA-core, mma.sync and tcgen05 stencils of the coarse
+    level and keeps the fastest; the solve with that choice meets the 1e-10 true residual."""
+    ctx, U, p = _ctx(W, CFG1, 1, coarse_tc=3)
+    impl, ms = ctx.coarse_impl(1)
+    assert impl in (0, 1, 2) and all(t > 0 for t in ms)
+    assert ms[impl] == min(ms)
+    b = synth.gaussian_spinors(CFG1["dims"], 2, 18)
+    x = dev(np.zeros_like(b))
+    st, info = ctx.solve(dev(b), x, 2)
+    xs = host(x)
+    for r in range(2):
+        assert oracle_resid(U, CFG1["m"], b[r], xs[r]) <= 1.05e-10
