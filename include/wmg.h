@@ -269,7 +269,9 @@ wmg_status wmg_residual_noalloc(wmg_ctx* ctx, int prec, const void* b_dev, const
  * the context's stream (this adds host work per launch; leave it off for timing runs).
  * Classes: 0 sloppy fine dslash, 1 FP64 fine dslash (true residuals), 2 coarse stencil,
  * 3 restrict, 4 prolong, 5 vector updates and reductions, 6 setup (Gram-Schmidt and
- * Galerkin construction).  wmg_profile_enable(ctx, 1) resets the counters. */
+ * Galerkin construction), 7 coarsest solves run as one persistent kernel (stencil applications
+ * and their vector updates together; units = right-hand sides solved).
+ * wmg_profile_enable(ctx, 1) resets the counters. */
 wmg_status wmg_profile_enable(wmg_ctx* ctx, int on);
 /* Totals of class cls since the last enable: kernel milliseconds, launches (or launch
  * groups), the algorithmic bytes those launches must move (compulsory reads + writes:

@@ -173,7 +173,7 @@ void wmg_default_params(wmg_params* p) {
   p->max_iter = 1000;
   p->prec_sloppy = WMG_PREC_SINGLE;
   p->coarse_tc = 1;
-  p->reliable_delta = 1e-3;
+  p->reliable_delta = 1e-4;
   p->seed = 20091212ULL;
   p->prec_nullvec = WMG_PREC_SINGLE;
   p->prec_smoother = WMG_PREC_SINGLE;
@@ -215,6 +215,7 @@ wmg_status wmg_create(wmg_ctx** out, const int dims[4], void* stream) {
   }
   if (const char* g = std::getenv("WMG_NO_GRAPHS")) c->use_graphs = !(g[0] == '1');
   if (const char* g = std::getenv("WMG_UNFUSED_GALERKIN")) c->use_fused_galerkin = !(g[0] == '1');
+  if (const char* g = std::getenv("WMG_NO_PERSISTENT_CG")) c->use_persistent_cg = !(g[0] == '1');
   c->L[0].g = c->fine;
   c->L[0].ndof = 12;
   cudaError_t e = cudaSuccess;

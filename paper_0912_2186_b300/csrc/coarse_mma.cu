@@ -20,28 +20,15 @@
 
 #include "kernels.h"
 #include "ptx.cuh"
+#include "mma_sync.cuh"
 
 namespace wmg {
 
 namespace {
 
-constexpr int kKPad = 8;  // halves of padding per staged column (bank-conflict free B loads)
 constexpr long long kMmaSpinLimit = 1LL << 22;
 
 __device__ int g_mma_error = 0;
-
-WMG_D uint32_t pack_half2(float lo, float hi) {
-  __half2 h = __floats2half2_rn(lo, hi);
-  return *reinterpret_cast<uint32_t*>(&h);
-}
-
-WMG_D void mma16816(float d[4], const uint4& a, uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
-}
 
 }  // namespace
 

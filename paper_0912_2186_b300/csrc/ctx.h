@@ -10,7 +10,7 @@ namespace wmg {
 
 // kernel classes timed by the optional CUDA-event instrumentation (wmg_profile_*)
 enum { PROF_DSLASH_LO = 0, PROF_DSLASH_64, PROF_COARSE, PROF_RESTRICT, PROF_PROLONG, PROF_BLAS, PROF_SETUP,
-       PROF_NCLASS };
+       PROF_CGNR, PROF_NCLASS };
 
 struct ProfRec {
   cudaEvent_t a, b;
@@ -67,6 +67,8 @@ struct wmg_ctx {
   cudaStream_t own_stream = nullptr;          // created when the caller passes no stream
   bool use_graphs = true;                      // capture the coarsest CGNR iterations
   bool use_fused_galerkin = true;              // fused fine-level Galerkin kernel
+  bool use_persistent_cg = true;               // coarsest CGNR as one persistent kernel when it applies
+  int* d_pcg_err = nullptr;                    // sticky error flag of the persistent CGNR (per solve)
   std::map<std::string, std::pair<cudaGraphExec_t, long long>> graphs;  // + launches per replay
   int n_active = 0;                            // active right-hand sides of the current solve
   float tune_ms[WMG_MAX_LEVELS][3] = {};       // autotuner: ms per 12-rhs launch of each stencil impl

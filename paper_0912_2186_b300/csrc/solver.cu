@@ -371,6 +371,43 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
   TRY(vec_ws(c, l, "cg_p", prec, nrhs, &p));
   TRY(vec_ws(c, l, "cg_q", prec, nrhs, &q));
   TRY(vec_ws(c, l, "cg_z", prec, nrhs, &z));
+  const int impl = prec == WMG_PREC_SINGLE ? (L.impl >= 0 ? L.impl : (L.A05 ? 2 : (L.A16 ? 1 : 0))) : 0;
+  if (c->use_persistent_cg && impl == 1 && nrhs <= 16) {
+    // the whole solve in one cooperative kernel (FP16 tensor-core stencil, fused updates)
+    void *part, *bar;
+    TRY(ws_get(c, "pcg_part", (size_t)4 * 16 * kPersistentMaxGrid * sizeof(double), &part));
+    TRY(ws_get(c, "pcg_bar", 4 * sizeof(unsigned), &bar));
+    if (!c->d_pcg_err) {
+      TRY(ws_get(c, "pcg_err", sizeof(int), (void**)&c->d_pcg_err));
+      CU(c, cudaMemsetAsync(c->d_pcg_err, 0, sizeof(int), c->stream));
+    }
+    bool ran;
+    {
+      ProfScope ps(c, PROF_CGNR, 0, nact_of(c, active, nrhs));
+      ran = cgnr_persistent(L.A16, L.sA, L.g, L.ndof, c->d_shift[l], b, x, r, p, q, z, nrhs,
+                            c->prm.coarse_tol * c->prm.coarse_tol, c->prm.coarse_maxit, active, (double*)part,
+                            (unsigned*)bar, c->d_pcg_err, c->d_cgint, c->d_cgint + kMaxRhs, c->stream);
+    }
+    if (ran) {
+      if (c->prof_on) {
+        // instrumentation: the stencil applications the kernel made (2 per iteration + 1 per rhs)
+        // and the operator bytes they read, from its iteration counts
+        CU(c, cudaMemcpyAsync(c->h_pin_i, c->d_cgint, 2 * kMaxRhs * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CU(c, cudaStreamSynchronize(c->stream));
+        int maxit = 0;
+        double applies = 0;
+        for (int i = 0; i < nrhs; ++i) {
+          const int it = c->h_pin_i[kMaxRhs + i];
+          if (it > 0) applies += 2.0 * it + 1.0;
+          maxit = std::max(maxit, it);
+        }
+        c->prof_units[PROF_COARSE] += applies;
+        c->prof_bytes[PROF_CGNR] += (2.0 * maxit + 1.0) * coarse_bytes(c, l, prec, nact_of(c, active, nrhs));
+      }
+      return check(c, "cgnr (persistent kernel)");
+    }
+    (void)cudaGetLastError();  // not launchable here: the multi-kernel path below
+  }
   CgScalars cg;
   cg.zz = res_slot(c, RES_CGZZ);
   cg.rr = res_slot(c, RES_CGRR);
@@ -799,6 +836,15 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
   if (use_mg && c->prm.coarse_tc && (coarse_mma_error() || coarse_tc05_error())) {
     c->err = "a bounded wait of the tensor-core coarse stencil expired";
     return WMG_ETIMEOUT;
+  }
+  if (use_mg && c->d_pcg_err) {
+    int e = 0;
+    CU(c, cudaMemcpy(&e, c->d_pcg_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+      CU(c, cudaMemset(c->d_pcg_err, 0, sizeof(int)));
+      c->err = "a bounded wait of the persistent coarsest solve expired";
+      return WMG_ETIMEOUT;
+    }
   }
   return WMG_OK;
 }

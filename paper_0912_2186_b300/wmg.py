@@ -286,7 +286,7 @@ class Context:
         return self._check(self.lib.wmg_residual_noalloc(self.h, prec, _ptr(b), _ptr(x), _ptr(r), _ptr(norm2),
                                                          int(nrhs)))
 
-    PROF_CLASSES = ("dslash_sloppy", "dslash_fp64", "coarse", "restrict", "prolong", "blas", "setup")
+    PROF_CLASSES = ("dslash_sloppy", "dslash_fp64", "coarse", "restrict", "prolong", "blas", "setup", "cgnr")
 
     def profile(self, on=True):
         return self._check(self.lib.wmg_profile_enable(self.h, int(bool(on))))
