@@ -58,11 +58,26 @@ __global__ void k_unpack_spinor(const void* __restrict__ in, double2* __restrict
 // Optional fused reductions per rhs: red0 = {<out, in>, |out|^2} (MR smoother) or
 // {|out|^2} alone.
 // ------------------------------------------------------------------------------------
+// Site coordinates by multiply-shift division (the lattice extents are runtime values).
+struct DslashDiv {
+  FastDiv dx, dy, dz;
+};
+WMG_D void site_coords_fast(const Geom& g, const DslashDiv& d, int v, int c[4]) {
+  const uint32_t q0 = fdiv((uint32_t)v, d.dx), q1 = fdiv(q0, d.dy), q2 = fdiv(q1, d.dz);
+  c[0] = v - (int)q0 * g.L[0];
+  c[1] = (int)q0 - (int)q1 * g.L[1];
+  c[2] = (int)q1 - (int)q2 * g.L[2];
+  c[3] = (int)q2;
+}
+
 template <typename R, int RED>
-__global__ void __launch_bounds__(128) k_dslash(void* __restrict__ out, const void* __restrict__ in,
-                                                const void* __restrict__ b, const void* __restrict__ gauge,
-                                                Geom g, const double* __restrict__ mass, const int* __restrict__ active,
-                                                int nrhs, int nblk_site, RedBuf rb) {
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(void* __restrict__ out,
+                                                                        const void* __restrict__ in,
+                                                                        const void* __restrict__ b,
+                                                                        const void* __restrict__ gauge, Geom g,
+                                                                        DslashDiv dv, const double* __restrict__ mass,
+                                                                        const int* __restrict__ active, int nrhs,
+                                                                        int nblk_site, RedBuf rb) {
   const int rhs = blockIdx.x % nrhs;
   const int sb = blockIdx.x / nrhs;
   if (active && !active[rhs]) return;  // whole CTA exits together (uniform per CTA)
@@ -75,7 +90,7 @@ __global__ void __launch_bounds__(128) k_dslash(void* __restrict__ out, const vo
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc[i] = cpx<R>{R(0), R(0)};
     int c[4];
-    site_coords(g, v, c);
+    site_coords_fast(g, dv, v, c);
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
       cpx<R> u[9], nb[12];
@@ -311,11 +326,12 @@ void dslash(int prec, void* out, const void* in, const void* b, const void* gaug
   const int nb = dslash_blocks(g.V);
   const unsigned grid = (unsigned)nb * nrhs;
   RedBuf r = rb ? *rb : RedBuf{nullptr, nullptr, nullptr};
+  const DslashDiv dv{make_fastdiv(g.L[0]), make_fastdiv(g.L[1]), make_fastdiv(g.L[2])};
 #define WMG_DS(R)                                                                                             \
   do {                                                                                                        \
-    if (red == 0) k_dslash<R, 0><<<grid, kDslashThreads, 0, s>>>(out, in, b, gauge, g, mass_dev, active, nrhs, nb, r); \
-    else if (red == 1) k_dslash<R, 1><<<grid, kDslashThreads, 0, s>>>(out, in, b, gauge, g, mass_dev, active, nrhs, nb, r); \
-    else k_dslash<R, 2><<<grid, kDslashThreads, 0, s>>>(out, in, b, gauge, g, mass_dev, active, nrhs, nb, r); \
+    if (red == 0) k_dslash<R, 0><<<grid, kDslashThreads, 0, s>>>(out, in, b, gauge, g, dv, mass_dev, active, nrhs, nb, r); \
+    else if (red == 1) k_dslash<R, 1><<<grid, kDslashThreads, 0, s>>>(out, in, b, gauge, g, dv, mass_dev, active, nrhs, nb, r); \
+    else k_dslash<R, 2><<<grid, kDslashThreads, 0, s>>>(out, in, b, gauge, g, dv, mass_dev, active, nrhs, nb, r); \
   } while (0)
   if (prec == WMG_PREC_DOUBLE) WMG_DS(double);
   else WMG_DS(float);
