@@ -145,6 +145,68 @@ def find_masses(U, ratios, block=(4, 4, 4, 4), nvec=24, m_start=0.0, m_step=0.2,
     return out, evals
 
 
+# ---- staged search (one process builds the hierarchy, evaluations and the per-ratio secant
+# searches run in parallel processes sharing it through files) ----
+
+def build_hierarchy(U, m, block=(4, 4, 4, 4), nvec=24, seed=7, setup_passes=3, log=print):
+    """Adaptive 2-level hierarchy at mass m for the search's MG solves (its quality only affects
+    the solves' speed, not the eigenvalues); setup passes use the oracle's CGNR coarse solve."""
+    from synth import setup_starts
+
+    T, Z, Y, X = U.shape[:4]
+    dims = (X, Y, Z, T)
+    t = time.time()
+    op = mg.WilsonOp(U, m)
+    P, Ac, _ = solvers.setup_level(op, block, setup_starts(dims, nvec, seed), passes=setup_passes,
+                                   params=solvers.CycleParams(coarse_tol=1e-4))
+    log(f"  setup at m = {m:.6f}: {time.time() - t:.1f} s")
+    return solvers.Hierarchy([op, Ac], [P], [block])
+
+
+def save_hierarchy(path, H):
+    np.savez(path, P=H.P[0], D=H.ops[1].D, m=H.ops[0].m, block=np.array(H.blocks[0]))
+
+
+def load_hierarchy(path, U):
+    z = np.load(path)
+    op = mg.WilsonOp(U, float(z["m"]))
+    return solvers.Hierarchy([op, mg.StencilOp(z["D"])], [z["P"]], [tuple(int(b) for b in z["block"])])
+
+
+def evaluate(H, m, v0, solve_tol=1e-7, eig_tol=1e-2, log=print):
+    """(lambda_min(D(m)^dag D(m)), its eigenvector) with H moved to mass m."""
+    t = time.time()
+    lam, v = lambda_min(shifted_hierarchy(H, m), v0, tol=solve_tol, eig_tol=eig_tol, log=log)
+    log(f"  m = {m:.6f}: lambda_min = {lam:.6e}, ratio = {lam / m ** 2:.4e} ({time.time() - t:.1f} s)")
+    return lam, v
+
+
+def next_mass(evals, r):
+    """Secant step on sqrt(lambda_min) = s (m - m_c) through the two evaluations nearest ratio r,
+    heavy side of m_c."""
+    (m1, l1), (m2, l2) = sorted(evals, key=lambda e: abs(np.log(e[1] / e[0] ** 2 / r)))[:2]
+    s = (np.sqrt(l1) - np.sqrt(l2)) / (m1 - m2)
+    mc = m1 - np.sqrt(l1) / s
+    cands = [c for c in (s * mc / (s - np.sqrt(r)), s * mc / (s + np.sqrt(r))) if c > mc]
+    return min(cands, key=lambda c: abs(c - m1))
+
+
+def search_ratio(H, r, evals, v0, rtol=0.05, max_evals=8, log=print, on_eval=None):
+    """Mass with lambda_min = r m^2 within rtol, starting from evals [(m, lambda)]."""
+    evals = list(evals)
+    v = v0
+    for _ in range(max_evals):
+        close = [e for e in evals if abs(e[1] / e[0] ** 2 - r) <= rtol * r]
+        if close:
+            return close[0][0], evals
+        m = next_mass(evals, r)
+        lam, v = evaluate(H, m, v, log=log)
+        evals.append((m, lam))
+        if on_eval:
+            on_eval(m, lam)
+    raise RuntimeError(f"mass search for ratio {r} did not converge: {evals}")
+
+
 def main(dims, eps, gauge_seed, ratios, out_path, **kw):
     from synth import gauge_field
 

@@ -201,7 +201,6 @@ __global__ void k_multidot(const void* W, size_t slot_stride, int j0, int kmax, 
   grid_finish<2 * J>(rb, r, blockIdx.x, gridDim.x, v);
 }
 
-constexpr int kDotChunk = 8;
 
 // w -= sum_{j<k} c_j W_j ; z -= sum c_j Z_j ; red = {|w|^2, Re<w,r>, Im<w,r>}
 template <typename R>
@@ -217,18 +216,18 @@ __global__ void k_gcr_orth(const void* W, const void* Z, size_t slot_stride, int
   }
   __syncthreads();
   cpx<R>* w = vec<R>(w_, n, r);
-  cpx<R>* z = vec<R>(z_, n, r);
+  cpx<R>* z = Z ? vec<R>(z_, n, r) : nullptr;  // Z = nullptr: w only
   const cpx<R>* rv = vec<R>(r_, n, r);
   R t[3] = {0, 0, 0};
   WMG_GRID_LOOP(i) {
-    cpx<R> wi = w[i], zi = z[i];
-    for (int j = 0; j < k; ++j) {
-      const cpx<R> cj = c[j];
-      wi = wi - cj * vec<R>((const char*)W + j * slot_stride, n, r)[i];
-      zi = zi - cj * vec<R>((const char*)Z + j * slot_stride, n, r)[i];
-    }
+    cpx<R> wi = w[i];
+    for (int j = 0; j < k; ++j) wi = wi - c[j] * vec<R>((const char*)W + j * slot_stride, n, r)[i];
     w[i] = wi;
-    z[i] = zi;
+    if (z) {
+      cpx<R> zi = z[i];
+      for (int j = 0; j < k; ++j) zi = zi - c[j] * vec<R>((const char*)Z + j * slot_stride, n, r)[i];
+      z[i] = zi;
+    }
     const cpx<R> ri = rv[i];
     t[0] += wi.re * wi.re + wi.im * wi.im;
     t[1] += wi.re * ri.re + wi.im * ri.im;
@@ -271,6 +270,50 @@ __global__ void k_gcr_update(void* x_, void* r_, void* w_, void* z_, const doubl
   __shared__ double sm[32];
   cta_reduce<1>(v, sm);
   grid_finish<1>(rb, r, blockIdx.x, gridDim.x, v);
+}
+
+// alpha = <w,r>/|w|^2, r -= alpha w, w /= |w|; red = |r|^2 (the solution update is deferred)
+template <typename R>
+__global__ void k_gcr_update_r(void* r_, void* w_, const double* wred, size_t n, const int* active, RedBuf rb) {
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  const double ww = wred[r * 3 + 0];
+  const bool ok = ww > 0.0;
+  const R inv = R(ok ? 1.0 / sqrt(ww) : 0.0);
+  const cpx<R> al{R(ok ? wred[r * 3 + 1] / ww : 0.0), R(ok ? wred[r * 3 + 2] / ww : 0.0)};
+  cpx<R>* rv = vec<R>(r_, n, r);
+  cpx<R>* w = vec<R>(w_, n, r);
+  R t = 0;
+  WMG_GRID_LOOP(i) {
+    const cpx<R> wi = w[i];
+    const cpx<R> ri = rv[i] - al * wi;
+    rv[i] = ri;
+    w[i] = inv * wi;
+    t += ri.re * ri.re + ri.im * ri.im;
+  }
+  double v[1] = {double(t)};
+  __shared__ double sm[32];
+  cta_reduce<1>(v, sm);
+  grid_finish<1>(rb, r, blockIdx.x, gridDim.x, v);
+}
+
+// x += sum_{j < K} xi[r][j] Z_j for the masked right-hand sides (xi: complex FP64, kMaxKrylov
+// per rhs); the deferred solution update of the flexible GCR
+template <typename R>
+__global__ void k_gcr_xupdate(const void* Z, size_t slot_stride, int K, void* x_, const double* xi, size_t n,
+                              const int* mask) {
+  const int r = blockIdx.y;
+  if (mask && !mask[r]) return;
+  __shared__ cpx<R> c[kMaxKrylov];
+  if (threadIdx.x < K) c[threadIdx.x] = cpx<R>{R(xi[((size_t)r * kMaxKrylov + threadIdx.x) * 2]),
+                                                R(xi[((size_t)r * kMaxKrylov + threadIdx.x) * 2 + 1])};
+  __syncthreads();
+  cpx<R>* x = vec<R>(x_, n, r);
+  WMG_GRID_LOOP(i) {
+    cpx<R> xv = x[i];
+    for (int j = 0; j < K; ++j) cfma(xv, c[j], vec<R>((const char*)Z + j * slot_stride, n, r)[i]);
+    x[i] = xv;
+  }
 }
 
 // x64 += x (sloppy), x = 0, for the masked right-hand sides (reliable update)
@@ -388,6 +431,20 @@ void gcr_update(int prec, void* x, void* r, void* w, void* z, const double* wred
   count_launch();
   dim3 g(blas_blocks(n), nrhs);
   WMG_BY_PREC(prec, k_gcr_update, <<<g, kBlasThreads, 0, s>>>(x, r, w, z, wred, n, active, rb));
+}
+
+void gcr_update_r(int prec, void* r, void* w, const double* wred, size_t n, int nrhs, const int* active,
+                  const RedBuf& rb, cudaStream_t s) {
+  count_launch();
+  dim3 g(blas_blocks(n), nrhs);
+  WMG_BY_PREC(prec, k_gcr_update_r, <<<g, kBlasThreads, 0, s>>>(r, w, wred, n, active, rb));
+}
+
+void gcr_xupdate(int prec, const void* Z, size_t slot_stride, int K, void* x, const double* xi, size_t n, int nrhs,
+                 const int* mask, cudaStream_t s) {
+  count_launch();
+  dim3 g(blas_blocks(n), nrhs);
+  WMG_BY_PREC(prec, k_gcr_xupdate, <<<g, kBlasThreads, 0, s>>>(Z, slot_stride, K, x, xi, n, mask));
 }
 
 void blas_fold(int prec, double* x64, void* x, size_t n, int nrhs, const int* mask, cudaStream_t s) {

@@ -72,15 +72,23 @@ void cg_update(int prec, void* x, void* r, const void* p, const void* q, size_t 
                int parity, const RedBuf& rb_rr, cudaStream_t s);
 void cg_xpay(int prec, void* p, const void* z, size_t n, int nrhs, const CgScalars& cg, int parity, cudaStream_t s);
 // GCR
-// coef[r*kmax + j] = <W_j, w> for j < kmax  (W_j at W + j*slot_stride)
+// <W_j, w> for j < kmax (W_j at W + j*slot_stride), in chunks of kDotChunk: the value for (j, r)
+// is at coef + ((j / kDotChunk) * nrhs + r) * 2 kDotChunk + 2 (j % kDotChunk) (re, im)
+constexpr int kDotChunk = 8;
 void gcr_multidot(int prec, const void* W, size_t slot_stride, int kmax, const void* w, size_t n, int nrhs,
                   const int* active, const RedBuf& rb, cudaStream_t s);
-// w -= sum_j c_j W_j, z -= sum_j c_j Z_j, then red = {|w|^2, Re<w,r>, Im<w,r>}
+// w -= sum_j c_j W_j (and z -= sum_j c_j Z_j unless Z is null), then red = {|w|^2, Re<w,r>, Im<w,r>}
 void gcr_orth(int prec, const void* W, const void* Z, size_t slot_stride, int k, void* w, void* z, const void* r,
               const double* coef, int kmax, size_t n, int nrhs, const int* active, const RedBuf& rb, cudaStream_t s);
 // alpha = <w,r>/|w|^2, x += alpha z, r -= alpha w, w /= |w|, z /= |w|; red = |r|^2 (x sloppy)
 void gcr_update(int prec, void* x, void* r, void* w, void* z, const double* wred, size_t n, int nrhs,
                 const int* active, const RedBuf& rb, cudaStream_t s);
+// alpha = <w,r>/|w|^2, r -= alpha w, w /= |w|; red = |r|^2 (solution update deferred)
+void gcr_update_r(int prec, void* r, void* w, const double* wred, size_t n, int nrhs, const int* active,
+                  const RedBuf& rb, cudaStream_t s);
+// x += sum_{j<K} xi[r][j] Z_j (xi complex FP64, kMaxKrylov per rhs) for masked right-hand sides
+void gcr_xupdate(int prec, const void* Z, size_t slot_stride, int K, void* x, const double* xi, size_t n, int nrhs,
+                 const int* mask, cudaStream_t s);
 // reliable update of the solution: x64 += x, x = 0 for masked right-hand sides
 void blas_fold(int prec, double* x64, void* x, size_t n, int nrhs, const int* mask, cudaStream_t s);
 

@@ -6,6 +6,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <random>
@@ -704,6 +705,59 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
   std::vector<double> rn2, t;
   RedBuf rb_coef = redbuf(c, RES_COEF), rb_w = redbuf(c, RES_WRED), rb_rn = redbuf(c, RES_RN),
          rb_r64 = redbuf(c, RES_R64), rb_bb = redbuf(c, RES_BB);
+  // The solution update is deferred: the preconditioned directions Z_j are kept as they are, and
+  // with A Z_k = sum_{j<k} beta_jk W_j + gamma_k W_k (W orthonormal) and alpha_k = <W_k, r>, the
+  // increment x += sum_k xi_k Z_k solves Gamma xi = alpha (Gamma upper triangular, diagonal
+  // gamma_k, above it beta_jk).  The coefficients of every iteration of the cycle are copied on
+  // the device into a history; at a reliable update, a restart or the end, the host solves for
+  // xi over the iterations not yet folded in (alpha of earlier ones set to 0).
+  const size_t kcoef = (size_t)((kMaxKrylov + kDotChunk - 1) / kDotChunk) * nslots * 2 * kDotChunk;
+  const size_t hstride = kcoef + 3 * (size_t)nslots;
+  void *hist, *xi_dev, *xmask_dev;
+  TRY(ws_get(c, "gcr_hist", hstride * m * sizeof(double), &hist));
+  TRY(ws_get(c, "gcr_xi", (size_t)nslots * kMaxKrylov * 2 * sizeof(double), &xi_dev));
+  TRY(ws_get(c, "gcr_xmask", (size_t)nslots * sizeof(int), &xmask_dev));
+  std::vector<int> fold_from(nslots, 0);
+  std::vector<double> hh, xi_h;
+  auto xupdate = [&](const std::vector<int>& sel, int K) -> wmg_status {
+    std::vector<int> mask(nslots, 0);
+    bool any = false;
+    for (int r = 0; r < nslots; ++r)
+      if (sel[r] && fold_from[r] < K) mask[r] = 1, any = true;
+    if (!any || K == 0) return WMG_OK;
+    hh.resize(hstride * K);
+    CU(c, cudaMemcpyAsync(hh.data(), hist, hstride * K * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(c, cudaStreamSynchronize(s));
+    xi_h.assign((size_t)nslots * kMaxKrylov * 2, 0.0);
+    using C = std::complex<double>;
+    for (int r = 0; r < nslots; ++r) {
+      if (!mask[r]) continue;
+      std::vector<C> xi(K), al(K);
+      std::vector<double> gam(K);
+      for (int q = 0; q < K; ++q) {
+        const double* hw = hh.data() + (size_t)q * hstride + kcoef + 3 * r;
+        gam[q] = hw[0] > 0.0 ? std::sqrt(hw[0]) : 0.0;
+        al[q] = (q >= fold_from[r] && gam[q] > 0.0) ? C(hw[1], hw[2]) / gam[q] : C(0.0, 0.0);
+      }
+      for (int q = K - 1; q >= 0; --q) {
+        C acc = al[q];
+        for (int p = q + 1; p < K; ++p) {
+          const double* b = hh.data() + (size_t)p * hstride + ((size_t)(q / kDotChunk) * nslots + r) * 2 * kDotChunk +
+                            2 * (q % kDotChunk);
+          acc -= C(b[0], b[1]) * xi[p];
+        }
+        xi[q] = gam[q] > 0.0 ? acc / gam[q] : C(0.0, 0.0);
+        xi_h[((size_t)r * kMaxKrylov + q) * 2] = xi[q].real();
+        xi_h[((size_t)r * kMaxKrylov + q) * 2 + 1] = xi[q].imag();
+      }
+      fold_from[r] = K;
+    }
+    CU(c, cudaMemcpyAsync(xi_dev, xi_h.data(), xi_h.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    CU(c, cudaMemcpyAsync(xmask_dev, mask.data(), nslots * sizeof(int), cudaMemcpyHostToDevice, s));
+    gcr_xupdate(lo, Z, slot, K, xlo, (const double*)xi_dev, n, nslots, (const int*)xmask_dev, s);
+    CU(c, cudaStreamSynchronize(s));  // the host vectors above must outlive the copies
+    return check(c, "gcr solution update");
+  };
   auto count_active = [&]() {
     c->n_active = 0;
     for (int r = 0; r < nslots; ++r) c->n_active += active[r];
@@ -772,8 +826,11 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
     {
       ProfScope ps(c, PROF_BLAS, 0);
       if (k > 0) gcr_multidot(lo, W, slot, k, wk, n, nslots, c->d_active, rb_coef, s);
-      gcr_orth(lo, W, Z, slot, k, wk, zk, rlo, rb_coef.result, k, n, nslots, c->d_active, rb_w, s);
-      gcr_update(lo, xlo, rlo, wk, zk, rb_w.result, n, nslots, c->d_active, rb_rn, s);
+      gcr_orth(lo, W, nullptr, slot, k, wk, nullptr, rlo, rb_coef.result, k, n, nslots, c->d_active, rb_w, s);
+      gcr_update_r(lo, rlo, wk, rb_w.result, n, nslots, c->d_active, rb_rn, s);
+      double* hk = (double*)hist + (size_t)k * hstride;
+      if (k > 0) CU(c, cudaMemcpyAsync(hk, rb_coef.result, kcoef * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CU(c, cudaMemcpyAsync(hk + kcoef, rb_w.result, 3 * (size_t)nslots * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
     TRY(check(c, "gcr iteration"));
     TRY(download(c, rb_rn.result, nslots, rn2));
@@ -795,6 +852,7 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
       // fold the sloppy iterate into the FP64 solution, then the FP64 true residual
       // r64 = b - D x64 for the active slots; applied where rel is set
       // (the FP64 operator runs only on the slots that take the update)
+      TRY(xupdate(rel, k));
       TRY(upload_ints(c, c->d_mask, rel));
       blas_fold(lo, (double*)x64, xlo, n, nslots, c->d_mask, s);
       int nrel = 0;
@@ -825,12 +883,16 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
         count_active();
       }
     }
-    if (k == m) k = 0;
+    if (k == m) {
+      TRY(xupdate(active, k));  // restart: fold the cycle's remaining increments into x
+      k = 0;
+    }
     if (k != 0) {
       bool any = false;
       for (int r = 0; r < nslots; ++r) any = any || active[r];
       if (!any) k = 0;  // everything finished mid-cycle: go back to admission
     }
+    if (k == 0) std::fill(fold_from.begin(), fold_from.end(), 0);
   }
   CU(c, cudaStreamSynchronize(s));
   if (use_mg && c->prm.coarse_tc && (coarse_mma_error() || coarse_tc05_error())) {
