@@ -121,6 +121,12 @@ typedef struct {
   int prec_smoother;                 /* storage of the fine-level MR smoother vectors
                                         with prec_sloppy = SINGLE: SINGLE, or HALF
                                         (FP16 with a per-site norm, FP32 arithmetic)  */
+  int coarse_persistent;             /* 1: the coarsest CGNR as one cooperative
+                                        persistent kernel (mma.sync stencil, 2N in
+                                        {16..64}, <= 16 rhs; grid barriers bounded,
+                                        WMG_ETIMEOUT when one expires); 0 (default):
+                                        a device-side loop of separate launches
+                                        (CUDA graph with a conditional WHILE node)   */
 } wmg_params;
 
 /* Per-right-hand-side result of a solve. */

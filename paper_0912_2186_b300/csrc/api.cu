@@ -92,6 +92,7 @@ wmg_status alloc_hierarchy(wmg_ctx* c, const wmg_params* p) {
     return bad(c, "prec_nullvec must be SINGLE, or HALF with prec_sloppy SINGLE");
   if (p->prec_smoother != WMG_PREC_SINGLE && !(p->prec_smoother == WMG_PREC_HALF && half_ok))
     return bad(c, "prec_smoother must be SINGLE, or HALF with prec_sloppy SINGLE");
+  if (p->coarse_persistent != 0 && p->coarse_persistent != 1) return bad(c, "coarse_persistent must be 0 or 1");
   free_hierarchy(c);
   c->prm = *p;
   c->nlev = p->nlevels;
@@ -168,7 +169,7 @@ void wmg_default_params(wmg_params* p) {
   p->gcr_restart = 16;
   p->cycle_gamma = 1;
   p->tol = 1e-10;
-  p->coarse_tol = 5e-3;
+  p->coarse_tol = 2e-2;
   p->coarse_maxit = 2000;
   p->max_iter = 1000;
   p->prec_sloppy = WMG_PREC_SINGLE;
@@ -177,6 +178,7 @@ void wmg_default_params(wmg_params* p) {
   p->seed = 20091212ULL;
   p->prec_nullvec = WMG_PREC_SINGLE;
   p->prec_smoother = WMG_PREC_SINGLE;
+  p->coarse_persistent = 0;
 }
 
 const char* wmg_strerror(wmg_status s) {
@@ -215,7 +217,6 @@ wmg_status wmg_create(wmg_ctx** out, const int dims[4], void* stream) {
   }
   if (const char* g = std::getenv("WMG_NO_GRAPHS")) c->use_graphs = !(g[0] == '1');
   if (const char* g = std::getenv("WMG_UNFUSED_GALERKIN")) c->use_fused_galerkin = !(g[0] == '1');
-  if (const char* g = std::getenv("WMG_NO_PERSISTENT_CG")) c->use_persistent_cg = !(g[0] == '1');
   c->L[0].g = c->fine;
   c->L[0].ndof = 12;
   cudaError_t e = cudaSuccess;

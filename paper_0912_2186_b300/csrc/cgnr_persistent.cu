@@ -1,15 +1,20 @@
 // The coarsest-level solve (CG on the normal equations, Sec. 3) as one persistent cooperative
-// kernel for up to 16 right-hand sides: one CTA per SM keeps its coarse sites for the whole
-// solve, applies the FP16 tensor-core stencil to them (the site's operator fragments staged by
-// bulk asynchronous copies, mma.sync m16n8k16 with FP32 accumulation, D^dag = sigma_3 D sigma_3),
-// and performs the vector updates of its own sites; grid barriers separate the phases that read
-// neighbour values or global sums.  Per iteration:
+// kernel for up to 16 right-hand sides.  Each CTA owns fixed coarse sites v = blockIdx.x + k G and
+// performs, for them, the tensor-core stencil applications and the vector updates; grid barriers
+// separate the phases that read neighbour values or global sums.  Per iteration:
 //     q = A p, |q|^2 | alpha = zz / qq; x += alpha p; r -= alpha q; |r|^2 | convergence;
 //     z = A^dag r, |z|^2 | beta = zz' / zz; p = z + beta p |
-// Every per-rhs sum is formed per CTA in a fixed order, stored as [phase][rhs][CTA] partials,
-// and summed over the CTAs in a fixed order by every CTA, so all CTAs take the same decisions
-// and a right-hand side's arithmetic does not depend on the others.  Every wait (grid barrier,
-// mbarrier) is bounded; on expiry the kernel records an error, which the solve reports.
+// The vector passes also write FP16 copies of p and sigma_3 r in the B-fragment order of
+// mma.sync m16n8k16, scaled per (site, rhs) by the largest |Re|, |Im| of the site's values.  A
+// stencil application is a set of independent warp units (site, 16-row tile, 8-rhs block): per
+// neighbour slot the unit multiplies the site's FP16 operator fragments by the neighbour's vector
+// fragments (both read from L2, no staging), then rescales that slot's partial sums by the
+// neighbour's scales (D^dag = sigma_3 D sigma_3: sigma_3 of the input is in r's copy, that of the
+// output in the epilogue).  Per-rhs sums are formed per CTA in a fixed order, stored as
+// [phase][rhs][CTA] partials and summed over the CTAs in a fixed order by every CTA, so all CTAs
+// take the same decisions and a right-hand side's arithmetic does not depend on the others.
+// Every grid-barrier wait is bounded; on expiry the kernel records an error, which the solve
+// reports.
 #include <cuda_fp16.h>
 
 #include <cstdio>
@@ -17,15 +22,15 @@
 
 #include "kernels.h"
 #include "mma_sync.cuh"
-#include "ptx.cuh"
 
 namespace wmg {
 namespace {
 
 constexpr int kPThreads = 256;
-constexpr int kPR = 16;                  // right-hand sides of the kernel (one 16-column chunk)
+constexpr int kPR = 16;                  // right-hand sides of the kernel
+constexpr int kPNT = 2;                  // 8-rhs column blocks
 constexpr int kPWarps = kPThreads / 32;
-constexpr long long kPSpin = 1LL << 22;  // polls of a wait before it gives up
+constexpr long long kPSpin = 1LL << 22;  // polls of a barrier wait before it gives up
 
 struct PcgArgs {
   const uint4* A16;
@@ -34,6 +39,8 @@ struct PcgArgs {
   const double* shift;  // per-rhs diagonal shift of this level's stencil
   const cf* b;
   cf *x, *r, *p, *q, *z;
+  __half *r16, *p16;    // fragment-order FP16 copies of sigma_3 r and of p: [site][blk][kstep][lane][8]
+  float *rsc, *psc;     // their scales [site][kPR]
   int nrhs;
   double tol2;
   int maxit;
@@ -77,156 +84,121 @@ WMG_D bool grid_barrier(const PcgArgs& a) {
   return ok != 0;
 }
 
-template <int NDOF>
-struct Smem {
-  static constexpr int n = NDOF, K = 9 * n, KP = K + kKPad, MT = n / 16, KS = K / 16, COLS = 2 * kPR;
-  static constexpr uint32_t kTileBytes = (uint32_t)KS * 32 * 16;
-  static constexpr size_t kA = (size_t)2 * MT * kTileBytes;  // one site's fragments
-  static constexpr size_t kX = (size_t)COLS * KP * sizeof(__half);
-  // fragment buffers: two (the next visit's copy overlaps the current one) when they fit
-  static constexpr int NBUF = 2 * kA + kX <= 200 * 1024 ? 2 : 1;
-  static constexpr size_t bytes() { return NBUF * kA + kX; }
-};
-
 // Per-CTA state, identical in every CTA (derived from the same global sums).
 struct PcgState {
   double bb[kPR], zz[kPR], red[kPR];
   int done[kPR], iters[kPR];
-  float xmax[kPR];
-  double npart[kPWarps][32][2];
-  int nbs[9];
-  unsigned long long mbar[2];  // one per fragment buffer
+  double wsum[kPWarps][kPR];  // per-warp norm sums of the current application
 };
 
-// The CTA's own sites v = blockIdx.x + k gridDim.x are visited in the same cyclic order by every
-// stencil application; the fragments of visit c + 1 are requested while visit c is computed
-// (buffer c & 1, mbarrier phase (c >> 1) & 1), across applications too.
-template <int NDOF>
-WMG_D void request_fragments(const PcgArgs& a, PcgState& st, unsigned char* smraw, unsigned c) {
-  using S = Smem<NDOF>;
-  constexpr int MT = S::MT, KS = S::KS;
-  const int nown = (a.g.V - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-  if (threadIdx.x != 0 || nown <= 0) return;
-  const int v = blockIdx.x + (int)(c % (unsigned)nown) * gridDim.x;
-  const unsigned buf = S::NBUF == 2 ? (c & 1u) : 0u;
-  uint4* As = reinterpret_cast<uint4*>(smraw + buf * S::kA);
-  const uint32_t bar = smem_addr(&st.mbar[buf]);
-  // order earlier generic-proxy reads of this buffer before the async-proxy writes
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-  mbar_arrive_expect_tx(bar, (uint32_t)S::kA);
-  for (int t = 0; t < MT; ++t)
-    for (int pl = 0; pl < 2; ++pl)
-      bulk_g2s(smem_addr(As + (size_t)(pl * MT + t) * KS * 32), a.A16 + (((size_t)v * 2 + pl) * MT + t) * KS * 32,
-               S::kTileBytes, bar);
+WMG_D cf ldcg(const cf* p) {
+  const float2 u = __ldcg(reinterpret_cast<const float2*>(p));
+  return cf{u.x, u.y};
 }
 
-// out(v) = A in (v) [+ shift in(v)], sigma_3-conjugated if dagger; the thread's two norm sums
-// (its right-hand sides blk * 8 + 2 q + {0, 1}) grow by |out|^2.
+WMG_D int own_sites(const PcgArgs& a) { return (a.g.V - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x; }
+
+// Index (in halves) of component j, part t (0 Re, 1 Im), of right-hand side rr of site v in a
+// fragment-order copy: B fragment of lane gq*4 + q holds k = 2q, 2q+1 (word 0) and 2q+8, 2q+9
+// (word 1) of column gq; a lane's 16 bytes are {Re word 0, Re word 1, Im word 0, Im word 1}.
+WMG_D size_t frag_half(int v, int rr, int j, int t, int n) {
+  const int blk = rr >> 3, gq = rr & 7, kk = j >> 4, jj = j & 15;
+  const int q = (jj & 7) >> 1, hi = jj >> 3, lane = gq * 4 + q;
+  return ((((size_t)v * kPNT + blk) * (n / 16) + kk) * 32 + lane) * 8 + (t * 2 + hi) * 2 + (jj & 1);
+}
+
+// The warp's values val[u] (components j = lane + 32 u) of rhs rr at site v into a copy: scale
+// = max |Re|, |Im| over the site (warp shuffles); sigma_3 flips the lower half if sg3.
+template <int NE>
+WMG_D void write_frag(__half* dst, float* sc, int v, int rr, int n, const cf val[NE], bool sg3) {
+  const int lane = threadIdx.x & 31, N = n / 2;
+  float mx = 0.f;
+#pragma unroll
+  for (int u = 0; u < NE; ++u)
+    if (lane + 32 * u < n) mx = fmaxf(mx, fmaxf(fabsf(val[u].re), fabsf(val[u].im)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const float inv = mx > 0.f ? 1.f / mx : 0.f;
+#pragma unroll
+  for (int u = 0; u < NE; ++u) {
+    const int j = lane + 32 * u;
+    if (j >= n) continue;
+    const float s = (sg3 && j >= N) ? -inv : inv;
+    dst[frag_half(v, rr, j, 0, n)] = __float2half_rn(val[u].re * s);
+    dst[frag_half(v, rr, j, 1, n)] = __float2half_rn(val[u].im * s);
+  }
+  if (lane == 0) sc[(size_t)v * kPR + rr] = mx;
+}
+
+// One stencil application to the CTA's sites: out = A in (dagger: sigma_3 A sigma_3) + shift in,
+// from the FP16 copy (in16, insc) of the input; |out|^2 per rhs into st.wsum.
 template <int NDOF>
-WMG_D void site_apply(const PcgArgs& a, PcgState& st, unsigned char* smraw, int v, const cf* in, cf* out,
-                      bool dagger, unsigned& visit, double nacc[2]) {
-  using S = Smem<NDOF>;
-  constexpr int n = S::n, N = n / 2, K = S::K, KP = S::KP, MT = S::MT, KS = S::KS;
-  constexpr int EPL = (K + 31) / 32, RPW = kPR / kPWarps;
-  const unsigned buf = S::NBUF == 2 ? (visit & 1u) : 0u;
-  uint4* As = reinterpret_cast<uint4*>(smraw + buf * S::kA);
-  __half* xb = reinterpret_cast<__half*>(smraw + S::NBUF * S::kA);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+WMG_D void apply_units(const PcgArgs& a, PcgState& st, const __half* in16, const float* insc, const cf* in32, cf* out,
+                       bool dagger) {
+  constexpr int n = NDOF, N = n / 2, MT = n / 16, KPS = n / 16, KS = 9 * KPS;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, q = lane & 3;
+  const int nt = a.nrhs > 8 ? 2 : 1;
+  const int units = own_sites(a) * MT * nt;
   const Geom& g = a.g;
-  const uint32_t bar = smem_addr(&st.mbar[buf]);
-  const unsigned mphase = S::NBUF == 2 ? ((visit >> 1) & 1u) : (visit & 1u);
-  // two buffers: request the next visit (its buffer was freed by the last sync); one: this visit
-  request_fragments<NDOF>(a, st, smraw, S::NBUF == 2 ? visit + 1 : visit);
-  if (threadIdx.x < 9) {
+  const uint4* X = reinterpret_cast<const uint4*>(in16);
+  for (int u = warp; u < units; u += kPWarps) {
+    const int k = u / (MT * nt), rem = u - k * (MT * nt), m = rem % MT, blk = rem / MT;
+    const int v = blockIdx.x + k * gridDim.x;
     int c[4];
     site_coords(g, v, c);
-    const int k = threadIdx.x;
-    st.nbs[k] = k == 0 ? v : neighbour(g, v, c, (k - 1) >> 1, ((k - 1) & 1) ? -1 : +1);
-  }
-  __syncthreads();
-  int offs[EPL];
-  unsigned neg = 0;
+    const uint4* Ar = a.A16 + ((size_t)v * 2 * MT + m) * KS * 32 + lane;
+    const uint4* Ai = a.A16 + ((size_t)(v * 2 + 1) * MT + m) * KS * 32 + lane;
+    float acc[2][2][4];
 #pragma unroll
-  for (int i = 0; i < EPL; ++i) {
-    const int e = lane + 32 * i;
-    offs[i] = -1;
-    if (e < K) {
-      const int k = e / n, j = e - k * n;
-      offs[i] = st.nbs[k] * n + j;
-      if (dagger && j >= N) neg |= 1u << i;
-    }
-  }
-  // gather (bypassing L1: other CTAs wrote these values since the last barrier)
-  cf xv[RPW][EPL];
+    for (int pl = 0; pl < 2; ++pl)
 #pragma unroll
-  for (int h = 0; h < RPW; ++h) {
-    const int rr = warp + kPWarps * h;
-    const bool ok = rr < a.nrhs;
-    const cf* src = in + (size_t)(ok ? rr : 0) * g.V * n;
+      for (int t = 0; t < 2; ++t)
 #pragma unroll
-    for (int i = 0; i < EPL; ++i) {
-      cf t{0.f, 0.f};
-      if (ok && offs[i] >= 0) {
-        const float2 u = __ldcg(reinterpret_cast<const float2*>(src + offs[i]));
-        t = {u.x, u.y};
+        for (int e = 0; e < 4; ++e) acc[pl][t][e] = 0.f;
+    // the fragments of slot s + 1 are requested before slot s is multiplied
+    uint4 fa[2][KPS], fi[2][KPS], fb[2][KPS];
+    float sc0[2], sc1[2];
+    auto fetch = [&](int s, int bsel) {
+      const int nb = s == 0 ? v : neighbour(g, v, c, (s - 1) >> 1, ((s - 1) & 1) ? -1 : +1);
+#pragma unroll
+      for (int kk = 0; kk < KPS; ++kk) {
+        fa[bsel][kk] = __ldg(Ar + (size_t)(s * KPS + kk) * 32);
+        fi[bsel][kk] = __ldg(Ai + (size_t)(s * KPS + kk) * 32);
+        fb[bsel][kk] = __ldcg(X + (((size_t)nb * kPNT + blk) * KPS + kk) * 32 + lane);
       }
-      xv[h][i] = t;
-    }
-  }
+      sc0[bsel] = __ldcg(insc + (size_t)nb * kPR + blk * 8 + 2 * q);
+      sc1[bsel] = __ldcg(insc + (size_t)nb * kPR + blk * 8 + 2 * q + 1);
+    };
+    fetch(0, 0);
 #pragma unroll
-  for (int h = 0; h < RPW; ++h) {
-    const int rr = warp + kPWarps * h;
-    float mx = 0.f;
+    for (int s = 0; s < 9; ++s) {
+      const int cur = s & 1;
+      if (s + 1 < 9) fetch(s + 1, cur ^ 1);
+      float t[2][2][4];
 #pragma unroll
-    for (int i = 0; i < EPL; ++i) mx = fmaxf(mx, fmaxf(fabsf(xv[h][i].re), fabsf(xv[h][i].im)));
+      for (int pl = 0; pl < 2; ++pl)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) st.xmax[rr] = mx;
-    const float inv = mx > 0.f ? 1.f / mx : 0.f;
-    __half* colr = xb + (size_t)((rr >> 3) * 16 + (rr & 7)) * KP;
-    __half* coli = colr + (size_t)8 * KP;
+        for (int tt = 0; tt < 2; ++tt)
 #pragma unroll
-    for (int i = 0; i < EPL; ++i) {
-      const int e = lane + 32 * i;
-      if (e < K) {
-        const float sg = ((neg >> i) & 1u) ? -inv : inv;
-        colr[e] = __float2half_rn(xv[h][i].re * sg);
-        coli[e] = __float2half_rn(xv[h][i].im * sg);
+          for (int e = 0; e < 4; ++e) t[pl][tt][e] = 0.f;
+#pragma unroll
+      for (int kk = 0; kk < KPS; ++kk) {
+        mma16816(t[0][0], fa[cur][kk], fb[cur][kk].x, fb[cur][kk].y);
+        mma16816(t[1][0], fi[cur][kk], fb[cur][kk].x, fb[cur][kk].y);
+        mma16816(t[0][1], fa[cur][kk], fb[cur][kk].z, fb[cur][kk].w);
+        mma16816(t[1][1], fi[cur][kk], fb[cur][kk].z, fb[cur][kk].w);
       }
+#pragma unroll
+      for (int pl = 0; pl < 2; ++pl)
+#pragma unroll
+        for (int tt = 0; tt < 2; ++tt)
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            acc[pl][tt][e] = fmaf(t[pl][tt][e], (e & 1) ? sc1[cur] : sc0[cur], acc[pl][tt][e]);
     }
-  }
-  __syncthreads();
-  const bool mma_warp = warp < MT * 2;
-  const int m = warp % MT, blk = warp / MT, gq = lane >> 2, q = lane & 3;
-  float acc[2][2][4];
-#pragma unroll
-  for (int pl = 0; pl < 2; ++pl)
-#pragma unroll
-    for (int t = 0; t < 2; ++t)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[pl][t][e] = 0.f;
-  bool ready = true;
-  if (mma_warp) {
-    ready = mbar_wait_bounded(bar, mphase, kPSpin);
-    if (!ready && lane == 0) atomicExch(a.err, 1);
-  }
-  if (mma_warp && ready) {
-    const uint4* Ar = As + (size_t)(0 * MT + m) * KS * 32 + lane;
-    const uint4* Ai = As + (size_t)(1 * MT + m) * KS * 32 + lane;
-    const __half* colbase = xb + (size_t)(blk * 16 + gq) * KP + 2 * q;
-#pragma unroll 9
-    for (int k = 0; k < KS; ++k) {
-      const uint4 a0 = Ar[(size_t)k * 32], a1 = Ai[(size_t)k * 32];
-#pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        const __half* col = colbase + (size_t)t * 8 * KP + 16 * k;
-        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(col);
-        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(col + 8);
-        mma16816(acc[0][t], a0, b0, b1);
-        mma16816(acc[1][t], a1, b0, b1);
-      }
-    }
+    // epilogue: rows 16 m + gq (+8), right-hand sides blk*8 + 2q + (e & 1)
     const float s_a = a.sA[v];
+    double nv[2] = {0.0, 0.0};
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int row = 16 * m + gq + (e >= 2 ? 8 : 0);
@@ -234,37 +206,34 @@ WMG_D void site_apply(const PcgArgs& a, PcgState& st, unsigned char* smraw, int 
       if (rr >= a.nrhs) continue;
       const float yr = acc[0][0][e] - acc[1][1][e];
       const float yi = acc[0][1][e] + acc[1][0][e];
-      const float sc = s_a * st.xmax[rr] * ((dagger && row >= N) ? -1.f : 1.f);
+      const float sc = s_a * ((dagger && row >= N) ? -1.f : 1.f);
       cf o{yr * sc, yi * sc};
       const size_t idx = ((size_t)rr * g.V + v) * n + row;
-      if (a.shift) {
-        const float2 u = __ldcg(reinterpret_cast<const float2*>(in + idx));
-        o += (float)a.shift[rr] * cf{u.x, u.y};
-      }
+      if (a.shift) o += (float)a.shift[rr] * ldcg(in32 + idx);
       out[idx] = o;
-      nacc[e & 1] += double(o.re) * o.re + double(o.im) * o.im;
+      nv[e & 1] += double(o.re) * o.re + double(o.im) * o.im;
     }
+    // sum over the 8 row groups (lanes with the same q), then one lane per column adds in
+#pragma unroll
+    for (int cc = 0; cc < 2; ++cc)
+#pragma unroll
+      for (int o = 4; o < 32; o <<= 1) nv[cc] += __shfl_xor_sync(0xffffffffu, nv[cc], o);
+    if (gq == 0)
+#pragma unroll
+      for (int cc = 0; cc < 2; ++cc) st.wsum[warp][blk * 8 + 2 * q + cc] += nv[cc];
   }
-  if (mma_warp && !ready) mbar_wait_bounded(bar, mphase, kPSpin);  // let the copies land (bounded)
-  ++visit;
-  __syncthreads();  // this visit's buffers are free again
 }
 
-// The CTA's norm sums of one phase (per rhs, fixed order) -> part[ph][rhs][cta]
-template <int NDOF>
-WMG_D void store_norm_part(const PcgArgs& a, PcgState& st, int ph, double nacc[2]) {
-  constexpr int MT = NDOF / 16;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  st.npart[warp][lane][0] = nacc[0];
-  st.npart[warp][lane][1] = nacc[1];
-  nacc[0] = nacc[1] = 0.0;
+// the CTA's application sums (warps in order) -> part[ph][rhs][cta]; clears the warp sums
+WMG_D void store_apply_part(const PcgArgs& a, PcgState& st, int ph) {
   __syncthreads();
   if (threadIdx.x < kPR) {
-    const int rr = threadIdx.x, b = rr >> 3, qq = (rr & 7) >> 1, ee = rr & 1;
     double t = 0.0;
-    for (int mm = 0; mm < MT; ++mm)
-      for (int gg = 0; gg < 8; ++gg) t += st.npart[b * MT + mm][gg * 4 + qq][ee];
-    a.part[((size_t)ph * kPR + rr) * gridDim.x + blockIdx.x] = t;
+    for (int w = 0; w < kPWarps; ++w) {
+      t += st.wsum[w][threadIdx.x];
+      st.wsum[w][threadIdx.x] = 0.0;
+    }
+    a.part[((size_t)ph * kPR + threadIdx.x) * gridDim.x + blockIdx.x] = t;
   }
 }
 
@@ -282,158 +251,66 @@ WMG_D void reduce_part(const PcgArgs& a, PcgState& st, int ph) {
   __syncthreads();
 }
 
-// A per-site vector pass over the CTA's sites: warp w takes right-hand sides w, w + 8 and its
-// lanes the site's components; f(rhs, index) returns the value whose |.|^2 enters the CTA's
-// sum of phase ph for that rhs (ph < 0: none).
-template <typename F>
-WMG_D void site_pass(const PcgArgs& a, PcgState& st, int n, int ph, F f) {
+// Per-site vector pass over the CTA's sites: warp w takes right-hand sides w and w + 8 (also the
+// padding ones up to 16, whose copies stay zero), lanes the components j = lane + 32 u.  f(rr, idx,
+// val) fills the NE values of the site (idx[u] = index of component lane + 32 u, valid if < n);
+// with dst they also go into a copy (scales sc, sigma_3 if sg3); |val|^2 enters part[ph] unless
+// ph < 0.
+template <int NE, typename F>
+WMG_D void site_pass(const PcgArgs& a, int n, int ph, __half* dst, float* sc, bool sg3, F f) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double s[kPR / kPWarps] = {};
-  for (int v = blockIdx.x; v < a.g.V; v += gridDim.x)
-#pragma unroll
-    for (int h = 0; h < kPR / kPWarps; ++h) {
-      const int rr = warp + kPWarps * h;
-      if (rr >= a.nrhs) continue;
-      for (int j = lane; j < n; j += 32) {
-        const cf o = f(rr, ((size_t)rr * a.g.V + v) * n + j);
-        s[h] += double(o.re) * o.re + double(o.im) * o.im;
-      }
-    }
-  if (ph < 0) return;
-#pragma unroll
-  for (int h = 0; h < kPR / kPWarps; ++h) {
-    double t = s[h];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    const int rr = warp + kPWarps * h;
-    if (lane == 0 && rr < kPR) a.part[((size_t)ph * kPR + rr) * gridDim.x + blockIdx.x] = t;
-  }
-}
-
-WMG_D cf ldcg(const cf* p) {
-  const float2 u = __ldcg(reinterpret_cast<const float2*>(p));
-  return cf{u.x, u.y};
-}
-
-// Element e of right-hand side rr in the CTA's sites (e = site visit * n + component).
-WMG_D size_t own_index(const PcgArgs& a, int rr, int e, int n) {
-  const int k = e / n, j = e - k * n;
-  return ((size_t)rr * a.g.V + blockIdx.x + (size_t)k * gridDim.x) * n + j;
-}
-
-constexpr int kPCh = 4;  // elements per lane whose loads are issued together
-
-// x += alpha p, r -= alpha q for the CTA's sites (rhs not done and qq > 0; alpha = zz / qq with
-// qq in st.red); |r|^2 -> part[ph].  Warp w takes rhs w, w + 8; lanes stride the elements.
-WMG_D void pass_xr(const PcgArgs& a, PcgState& st, int n, int ph) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nown = (a.g.V - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-  const int ne = nown * n;
+  const int nown = own_sites(a);
 #pragma unroll
   for (int h = 0; h < kPR / kPWarps; ++h) {
     const int rr = warp + kPWarps * h;
     double s = 0.0;
-    if (rr < a.nrhs) {
-      const double qq = st.red[rr];
-      const bool upd = !st.done[rr] && qq > 0.0;
-      const float al = upd ? float(st.zz[rr] / qq) : 0.f;
-      for (int e0 = lane; e0 < ne; e0 += 32 * kPCh) {
-        cf rv[kPCh], pv[kPCh], qv[kPCh], xv[kPCh];
-        size_t id[kPCh];
+    for (int k = 0; k < nown; ++k) {
+      const int v = blockIdx.x + k * gridDim.x;
+      cf val[NE];
+      size_t idx[NE];
 #pragma unroll
-        for (int u = 0; u < kPCh; ++u) {
-          const int e = e0 + 32 * u;
-          id[u] = e < ne ? own_index(a, rr, e, n) : 0;
-          if (e < ne) {
-            rv[u] = ldcg(a.r + id[u]);
-            if (upd) {
-              pv[u] = ldcg(a.p + id[u]);
-              qv[u] = ldcg(a.q + id[u]);
-              xv[u] = ldcg(a.x + id[u]);
-            }
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kPCh; ++u) {
-          if (e0 + 32 * u >= ne) continue;
-          if (upd) {
-            xv[u] += al * pv[u];
-            rv[u] = rv[u] - al * qv[u];
-            a.x[id[u]] = xv[u];
-            a.r[id[u]] = rv[u];
-          }
-          s += double(rv[u].re) * rv[u].re + double(rv[u].im) * rv[u].im;
-        }
+      for (int u = 0; u < NE; ++u) {
+        idx[u] = ((size_t)rr * a.g.V + v) * n + lane + 32 * u;
+        val[u] = cf{0.f, 0.f};
       }
+      if (rr < a.nrhs) f(rr, idx, val);
+#pragma unroll
+      for (int u = 0; u < NE; ++u)
+        if (lane + 32 * u < n) s += double(val[u].re) * val[u].re + double(val[u].im) * val[u].im;
+      if (dst) write_frag<NE>(dst, sc, v, rr, n, val, sg3);
     }
+    if (ph >= 0) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0 && rr < kPR) a.part[((size_t)ph * kPR + rr) * gridDim.x + blockIdx.x] = s;
-  }
-}
-
-// p = z + beta p for the CTA's sites (rhs not done and zz > 0; beta = zz' / zz, zz' in st.red)
-WMG_D void pass_p(const PcgArgs& a, PcgState& st, int n) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nown = (a.g.V - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-  const int ne = nown * n;
-#pragma unroll
-  for (int h = 0; h < kPR / kPWarps; ++h) {
-    const int rr = warp + kPWarps * h;
-    if (rr >= a.nrhs || st.done[rr] || !(st.zz[rr] > 0.0)) continue;
-    const float be = float(st.red[rr] / st.zz[rr]);
-    for (int e0 = lane; e0 < ne; e0 += 32 * kPCh) {
-      cf zv[kPCh], pv[kPCh];
-      size_t id[kPCh];
-#pragma unroll
-      for (int u = 0; u < kPCh; ++u) {
-        const int e = e0 + 32 * u;
-        id[u] = e < ne ? own_index(a, rr, e, n) : 0;
-        if (e < ne) {
-          zv[u] = ldcg(a.z + id[u]);
-          pv[u] = ldcg(a.p + id[u]);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kPCh; ++u)
-        if (e0 + 32 * u < ne) a.p[id[u]] = zv[u] + be * pv[u];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) a.part[((size_t)ph * kPR + rr) * gridDim.x + blockIdx.x] = s;
     }
   }
 }
 
 template <int NDOF>
-__global__ void __launch_bounds__(kPThreads, 1) k_cgnr_persistent(PcgArgs a) {
-  extern __shared__ __align__(128) unsigned char smraw[];
+__global__ void __launch_bounds__(kPThreads) k_cgnr_persistent(PcgArgs a) {
   __shared__ PcgState st;
-  constexpr int n = NDOF;
-  const int V = a.g.V;
-  unsigned visit = 0;
-  double nacc[2] = {0.0, 0.0};
-  // before the CTA ends: the fragment request of the next visit must have landed (bounded)
-  auto drain = [&]() {
-    if (Smem<NDOF>::NBUF == 2 && threadIdx.x == 0 && V > (int)blockIdx.x)
-      mbar_wait_bounded(smem_addr(&st.mbar[visit & 1u]), (visit >> 1) & 1u, kPSpin);
-  };
-  if (threadIdx.x == 0) {
-    mbar_init(smem_addr(&st.mbar[0]), 1);
-    mbar_init(smem_addr(&st.mbar[1]), 1);
-    mbar_fence_init();
-  }
+  constexpr int n = NDOF, NE = (n + 31) / 32;
+  const int lane = threadIdx.x & 31;
   if (threadIdx.x < kPR) {
     const int r = threadIdx.x;
     st.done[r] = r >= a.nrhs || (a.active && !a.active[r]);
     st.iters[r] = 0;
+    for (int w = 0; w < kPWarps; ++w) st.wsum[w][r] = 0.0;
   }
   __syncthreads();
-  if (Smem<NDOF>::NBUF == 2) request_fragments<NDOF>(a, st, smraw, 0);  // during the first passes
-  // x = 0, r = b (zero for inactive slots), z = p = 0; |b|^2 -> phase 0
-  site_pass(a, st, n, 0, [&](int rr, size_t i) {
-    const cf bv = st.done[rr] ? cf{0.f, 0.f} : ldcg(a.b + i);
-    a.r[i] = bv;
-    a.x[i] = a.p[i] = a.z[i] = cf{0.f, 0.f};
-    return bv;
+  // x = 0, r = b (zero for inactive slots), z = p = 0; sigma_3 r -> copy; |b|^2 -> phase 0
+  site_pass<NE>(a, n, 0, a.r16, a.rsc, true, [&](int rr, const size_t* idx, cf* val) {
+#pragma unroll
+    for (int u = 0; u < NE; ++u) {
+      if (lane + 32 * u >= n) continue;
+      const cf bv = st.done[rr] ? cf{0.f, 0.f} : ldcg(a.b + idx[u]);
+      a.r[idx[u]] = bv;
+      a.x[idx[u]] = a.p[idx[u]] = a.z[idx[u]] = cf{0.f, 0.f};
+      val[u] = bv;
+    }
   });
-  if (!grid_barrier(a)) return drain();
+  if (!grid_barrier(a)) return;
   reduce_part(a, st, 0);
   if (threadIdx.x < kPR) {
     st.bb[threadIdx.x] = st.red[threadIdx.x];
@@ -441,29 +318,58 @@ __global__ void __launch_bounds__(kPThreads, 1) k_cgnr_persistent(PcgArgs a) {
   }
   __syncthreads();
   // z = A^dag r, |z|^2 -> phase 1
-  for (int v = blockIdx.x; v < V; v += gridDim.x) site_apply<NDOF>(a, st, smraw, v, a.r, a.z, true, visit, nacc);
-  store_norm_part<NDOF>(a, st, 1, nacc);
-  if (!grid_barrier(a)) return drain();
+  apply_units<NDOF>(a, st, a.r16, a.rsc, a.r, a.z, true);
+  store_apply_part(a, st, 1);
+  if (!grid_barrier(a)) return;
   reduce_part(a, st, 1);
   if (threadIdx.x < kPR) st.zz[threadIdx.x] = st.red[threadIdx.x];
   __syncthreads();
-  site_pass(a, st, n, -1, [&](int rr, size_t i) {
-    a.p[i] = ldcg(a.z + i);
-    return cf{0.f, 0.f};
+  // p = z -> copy
+  site_pass<NE>(a, n, -1, a.p16, a.psc, false, [&](int rr, const size_t* idx, cf* val) {
+#pragma unroll
+    for (int u = 0; u < NE; ++u) {
+      if (lane + 32 * u >= n) continue;
+      val[u] = ldcg(a.z + idx[u]);
+      a.p[idx[u]] = val[u];
+    }
   });
-  if (!grid_barrier(a)) return drain();
+  if (!grid_barrier(a)) return;
   for (int it = 0; it < a.maxit; ++it) {
     bool all = true;
     for (int r = 0; r < kPR; ++r) all = all && st.done[r];
     if (all) break;
     // q = A p, |q|^2 -> phase 2
-    for (int v = blockIdx.x; v < V; v += gridDim.x) site_apply<NDOF>(a, st, smraw, v, a.p, a.q, false, visit, nacc);
-    store_norm_part<NDOF>(a, st, 2, nacc);
-    if (!grid_barrier(a)) return drain();
+    apply_units<NDOF>(a, st, a.p16, a.psc, a.p, a.q, false);
+    store_apply_part(a, st, 2);
+    if (!grid_barrier(a)) return;
     reduce_part(a, st, 2);
-    // x += alpha p, r -= alpha q; |r|^2 -> phase 3
-    pass_xr(a, st, n, 3);
-    if (!grid_barrier(a)) return drain();
+    // x += alpha p, r -= alpha q (rhs not done); sigma_3 r -> copy; |r|^2 -> phase 3
+    site_pass<NE>(a, n, 3, a.r16, a.rsc, true, [&](int rr, const size_t* idx, cf* val) {
+      const double qq = st.red[rr];
+      const bool upd = !st.done[rr] && qq > 0.0;
+      const float al = upd ? float(st.zz[rr] / qq) : 0.f;
+      cf pv[NE], qv[NE], xv[NE];
+#pragma unroll
+      for (int u = 0; u < NE; ++u) {
+        if (lane + 32 * u >= n) continue;
+        val[u] = ldcg(a.r + idx[u]);
+        if (upd) {
+          pv[u] = ldcg(a.p + idx[u]);
+          qv[u] = ldcg(a.q + idx[u]);
+          xv[u] = ldcg(a.x + idx[u]);
+        }
+      }
+      if (!upd) return;
+#pragma unroll
+      for (int u = 0; u < NE; ++u) {
+        if (lane + 32 * u >= n) continue;
+        xv[u] += al * pv[u];
+        val[u] = val[u] - al * qv[u];
+        a.x[idx[u]] = xv[u];
+        a.r[idx[u]] = val[u];
+      }
+    });
+    if (!grid_barrier(a)) return;
     reduce_part(a, st, 3);
     if (threadIdx.x < kPR) {
       const int r = threadIdx.x;
@@ -477,40 +383,54 @@ __global__ void __launch_bounds__(kPThreads, 1) k_cgnr_persistent(PcgArgs a) {
     for (int r = 0; r < kPR; ++r) all = all && st.done[r];
     if (all || it + 1 == a.maxit) break;
     // z = A^dag r, |z|^2 -> phase 1
-    for (int v = blockIdx.x; v < V; v += gridDim.x) site_apply<NDOF>(a, st, smraw, v, a.r, a.z, true, visit, nacc);
-    store_norm_part<NDOF>(a, st, 1, nacc);
-    if (!grid_barrier(a)) return drain();
+    apply_units<NDOF>(a, st, a.r16, a.rsc, a.r, a.z, true);
+    store_apply_part(a, st, 1);
+    if (!grid_barrier(a)) return;
     reduce_part(a, st, 1);
-    // p = z + beta p
-    pass_p(a, st, n);
+    // p = z + beta p (rhs not done) -> copy
+    site_pass<NE>(a, n, -1, a.p16, a.psc, false, [&](int rr, const size_t* idx, cf* val) {
+      const bool upd = !st.done[rr] && st.zz[rr] > 0.0;
+      const float be = upd ? float(st.red[rr] / st.zz[rr]) : 0.f;
+      cf zv[NE];
+#pragma unroll
+      for (int u = 0; u < NE; ++u) {
+        if (lane + 32 * u >= n) continue;
+        val[u] = ldcg(a.p + idx[u]);
+        if (upd) zv[u] = ldcg(a.z + idx[u]);
+      }
+      if (!upd) return;
+#pragma unroll
+      for (int u = 0; u < NE; ++u) {
+        if (lane + 32 * u >= n) continue;
+        val[u] = zv[u] + be * val[u];
+        a.p[idx[u]] = val[u];
+      }
+    });
     __syncthreads();
     if (threadIdx.x < kPR && !st.done[threadIdx.x]) st.zz[threadIdx.x] = st.red[threadIdx.x];
-    if (!grid_barrier(a)) return drain();
+    if (!grid_barrier(a)) return;
   }
   if (blockIdx.x == 0 && threadIdx.x < kPR) {
     a.done_out[threadIdx.x] = st.done[threadIdx.x];
     a.iters_out[threadIdx.x] = st.iters[threadIdx.x];
   }
-  drain();
 }
 
 template <int NDOF>
 bool launch_persistent(PcgArgs& a, cudaStream_t s) {
   static int grid = -1;
-  const size_t smem = Smem<NDOF>::bytes();
   if (grid < 0) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_cgnr_persistent<NDOF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cgnr_persistent<NDOF>, kPThreads, smem);
-    grid = per >= 1 ? sms : 0;
-    if (std::getenv("WMG_DEBUG")) std::fprintf(stderr, "persistent CGNR (2N = %d): %d per SM, grid %d, smem %zu\n", NDOF, per, grid, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cgnr_persistent<NDOF>, kPThreads, 0);
+    grid = sms * (per >= 2 ? 2 : per);
+    if (std::getenv("WMG_DEBUG")) std::fprintf(stderr, "persistent CGNR (2N = %d): %d per SM, grid %d\n", NDOF, per, grid);
   }
-  if (grid == 0 || grid > kPersistentMaxGrid) return false;
+  if (grid <= 0 || grid > kPersistentMaxGrid) return false;
   void* args[] = {&a};
-  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_cgnr_persistent<NDOF>, dim3(grid), dim3(kPThreads),
-                                                    args, smem, s);
+  const cudaError_t e =
+      cudaLaunchCooperativeKernel((const void*)k_cgnr_persistent<NDOF>, dim3(grid), dim3(kPThreads), args, 0, s);
   if (e != cudaSuccess && std::getenv("WMG_DEBUG"))
     std::fprintf(stderr, "persistent CGNR (2N = %d): %s\n", NDOF, cudaGetErrorString(e));
   return e == cudaSuccess;
@@ -518,12 +438,15 @@ bool launch_persistent(PcgArgs& a, cudaStream_t s) {
 
 }  // namespace
 
+size_t cgnr_persistent_copy_bytes(int Vc, int n) { return (size_t)Vc * kPNT * (n / 16) * 32 * 16; }
+
 bool cgnr_persistent(const void* A16, const float* sA, const Geom& g, int n, const double* shift, const void* b,
-                     void* x, void* r, void* p, void* q, void* z, int nrhs, double tol2, int maxit, const int* active,
-                     double* part, unsigned* bar, int* err, int* done_out, int* iters_out, cudaStream_t s) {
+                     void* x, void* r, void* p, void* q, void* z, void* r16, void* p16, float* rsc, float* psc,
+                     int nrhs, double tol2, int maxit, const int* active, double* part, unsigned* bar, int* err,
+                     int* done_out, int* iters_out, cudaStream_t s) {
   if (nrhs < 1 || nrhs > kPR) return false;
   PcgArgs a{(const uint4*)A16, sA, g, shift, (const cf*)b, (cf*)x, (cf*)r, (cf*)p, (cf*)q, (cf*)z,
-            nrhs, tol2, maxit, active, part, bar, err, done_out, iters_out};
+            (__half*)r16, (__half*)p16, rsc, psc, nrhs, tol2, maxit, active, part, bar, err, done_out, iters_out};
   if (cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return false;
   bool ok = false;
   switch (n) {

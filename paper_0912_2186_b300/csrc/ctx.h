@@ -67,7 +67,6 @@ struct wmg_ctx {
   cudaStream_t own_stream = nullptr;          // created when the caller passes no stream
   bool use_graphs = true;                      // capture the coarsest CGNR iterations
   bool use_fused_galerkin = true;              // fused fine-level Galerkin kernel
-  bool use_persistent_cg = true;               // coarsest CGNR as one persistent kernel when it applies
   int* d_pcg_err = nullptr;                    // sticky error flag of the persistent CGNR (per solve)
   std::map<std::string, std::pair<cudaGraphExec_t, long long>> graphs;  // + launches per replay
   int n_active = 0;                            // active right-hand sides of the current solve

@@ -150,12 +150,15 @@ void coarse_apply_tc05(const void* A16, const float* sA, const Geom& g, int n, c
                        const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s);
 // Coarsest CGNR for nrhs <= 16 as one persistent cooperative kernel (FP16 tensor-core stencil
 // with 2N in {16, 32, 48, 64}, FP32 vectors [rhs][site][2N]); false if it cannot run (the caller
-// then uses the multi-kernel CGNR).  part: 4 * 16 * kPersistentMaxGrid doubles; bar: 2 unsigned;
+// then uses the multi-kernel CGNR).  r16, p16: cgnr_persistent_copy_bytes each (FP16 copies);
+// rsc, psc: 16 floats per site; part: 4 * 16 * kPersistentMaxGrid doubles; bar: 2 unsigned;
 // err: sticky error flag (bounded waits expired); done_out, iters_out: 16 ints.
 constexpr int kPersistentMaxGrid = 1024;
+size_t cgnr_persistent_copy_bytes(int Vc, int n);
 bool cgnr_persistent(const void* A16, const float* sA, const Geom& g, int n, const double* shift, const void* b,
-                     void* x, void* r, void* p, void* q, void* z, int nrhs, double tol2, int maxit, const int* active,
-                     double* part, unsigned* bar, int* err, int* done_out, int* iters_out, cudaStream_t s);
+                     void* x, void* r, void* p, void* q, void* z, void* r16, void* p16, float* rsc, float* psc,
+                     int nrhs, double tol2, int maxit, const int* active, double* part, unsigned* bar, int* err,
+                     int* done_out, int* iters_out, cudaStream_t s);
 int coarse_mma_error();   // 1 if a bounded wait of the mma.sync coarse kernel ever expired (synchronises)
 int coarse_tc05_error();  // 1 if a bounded tcgen05 wait ever expired (synchronises)
 // convert a stencil between precisions

@@ -373,11 +373,15 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
   TRY(vec_ws(c, l, "cg_q", prec, nrhs, &q));
   TRY(vec_ws(c, l, "cg_z", prec, nrhs, &z));
   const int impl = prec == WMG_PREC_SINGLE ? (L.impl >= 0 ? L.impl : (L.A05 ? 2 : (L.A16 ? 1 : 0))) : 0;
-  if (c->use_persistent_cg && impl == 1 && nrhs <= 16) {
+  if (c->prm.coarse_persistent && impl == 1 && nrhs <= 16) {
     // the whole solve in one cooperative kernel (FP16 tensor-core stencil, fused updates)
-    void *part, *bar;
+    void *part, *bar, *r16, *p16, *rsc, *psc;
     TRY(ws_get(c, "pcg_part", (size_t)4 * 16 * kPersistentMaxGrid * sizeof(double), &part));
     TRY(ws_get(c, "pcg_bar", 4 * sizeof(unsigned), &bar));
+    TRY(ws_get(c, "pcg_r16_" + std::to_string(l), cgnr_persistent_copy_bytes(L.g.V, L.ndof), &r16));
+    TRY(ws_get(c, "pcg_p16_" + std::to_string(l), cgnr_persistent_copy_bytes(L.g.V, L.ndof), &p16));
+    TRY(ws_get(c, "pcg_rsc_" + std::to_string(l), (size_t)L.g.V * 16 * sizeof(float), &rsc));
+    TRY(ws_get(c, "pcg_psc_" + std::to_string(l), (size_t)L.g.V * 16 * sizeof(float), &psc));
     if (!c->d_pcg_err) {
       TRY(ws_get(c, "pcg_err", sizeof(int), (void**)&c->d_pcg_err));
       CU(c, cudaMemsetAsync(c->d_pcg_err, 0, sizeof(int), c->stream));
@@ -385,7 +389,8 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
     bool ran;
     {
       ProfScope ps(c, PROF_CGNR, 0, nact_of(c, active, nrhs));
-      ran = cgnr_persistent(L.A16, L.sA, L.g, L.ndof, c->d_shift[l], b, x, r, p, q, z, nrhs,
+      ran = cgnr_persistent(L.A16, L.sA, L.g, L.ndof, c->d_shift[l], b, x, r, p, q, z, r16, p16, (float*)rsc,
+                            (float*)psc, nrhs,
                             c->prm.coarse_tol * c->prm.coarse_tol, c->prm.coarse_maxit, active, (double*)part,
                             (unsigned*)bar, c->d_pcg_err, c->d_cgint, c->d_cgint + kMaxRhs, c->stream);
     }

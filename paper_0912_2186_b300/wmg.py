@@ -47,6 +47,7 @@ class Params(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("prec_nullvec", ctypes.c_int),
         ("prec_smoother", ctypes.c_int),
+        ("coarse_persistent", ctypes.c_int),
     ]
 
 

@@ -224,3 +224,19 @@ def test_autotuned_coarse_stencil(W):
     xs = host(x)
     for r in range(2):
         assert oracle_resid(U, CFG1["m"], b[r], xs[r]) <= 1.05e-10
+
+
+def test_persistent_coarse_cgnr(W):
+    """coarse_persistent = 1: the coarsest CGNR as one cooperative kernel; every solution meets the
+    1e-10 true residual, and a right-hand side's result is the same alone and in its batch."""
+    ctx, U, p = _ctx(W, CFG1, 1, coarse_persistent=1)
+    b = synth.gaussian_spinors(CFG1["dims"], 3, 19)
+    x = dev(np.zeros_like(b))
+    st, info = ctx.solve(dev(b), x, 3)
+    xs = host(x)
+    for r in range(3):
+        assert info[r]["converged"]
+        assert oracle_resid(U, CFG1["m"], b[r], xs[r]) <= 1.05e-10
+    x1 = dev(np.zeros_like(b[1:2]))
+    _, i1 = ctx.solve(dev(b[1:2]), x1, 1)
+    assert np.array_equal(host(x1)[0], xs[1]) and i1[0]["iters"] == info[1]["iters"]
