@@ -16,10 +16,13 @@ paper computes:
 * ``solvers`` -- MR smoother, CGNR coarsest solve, the multigrid cycle with post
                  smoothing only, flexible GCR outer solver (Sec. 3) and the adaptive
                  near-null-vector setup (Sec. 2).
+* ``eo``      -- the even-odd (Schur complement) form of the coarsest-level CG solve:
+                 S = A_ee - A_eo A_oo^-1 A_oe, its adjoint, the prepared right-hand side
+                 and the reconstruction of the odd sites.
 
 Parity status per function is stated in each module header.  The adaptive setup
 (``solvers.adaptive_setup``) is "parity unpinned" at the level of individual vectors:
 near-null vectors have no closed form; it is pinned only indirectly (residual
 decrease, span and orthonormality invariants).
 """
-from . import dirac, mg, solvers  # noqa: F401
+from . import dirac, eo, mg, solvers  # noqa: F401

@@ -13,6 +13,8 @@ the vectors, repeat).  The details the paper leaves open are read as follows:
 * CGNR(A, b, tol, maxit) on A^dag A x = A^dag b (CGLS form): x = 0, r = b, z = A^dag r,
   p = z; loop: q = A p; alpha = |z|^2/|q|^2; x += alpha p; r -= alpha q;
   z' = A^dag r; beta = |z'|^2/|z|^2; p = z' + beta p; stop when |r| <= tol |b|.
+  Optionally (CycleParams.coarse_eo) the same CG on the even-odd Schur complement of the
+  coarsest operator (oracle/eo.py), with the same stopping test on the whole system.
 * Cycle K_l(r): at the coarsest level CGNR(A_l, r); otherwise e = 0 and gamma times
   { r_c = P^dag (r - A e); e += P K_{l+1}(r_c); e = MR(A, r, e, nu) }.
   gamma = 1 is the V-cycle, gamma = 2 at intermediate levels the W-cycle.
@@ -44,7 +46,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import mg
+from . import eo, mg
 
 
 def dot(a, b):
@@ -101,6 +103,7 @@ class CycleParams:
     gamma: int = 1              # 1 = V-cycle, 2 = W-cycle at intermediate levels
     coarse_tol: float = 1e-8    # CGNR relative tolerance on the coarsest level
     coarse_maxit: int = 5000
+    coarse_eo: bool = False     # CGNR on the even-odd Schur complement (oracle/eo.py) instead
 
 
 @dataclass
@@ -124,7 +127,8 @@ def cycle(H, level, r):
     if level == H.nlevels - 1:
         if H.coarse_solver is not None:
             return H.coarse_solver(A, r)
-        x, it = cgnr(A, r, p.coarse_tol, p.coarse_maxit)
+        solve = eo.cgnr_eo if p.coarse_eo else cgnr
+        x, it = solve(A, r, p.coarse_tol, p.coarse_maxit)
         H.coarse_iters.append(it)
         return x
     P, blk = H.P[level], H.blocks[level]
