@@ -127,6 +127,13 @@ typedef struct {
                                         WMG_ETIMEOUT when one expires); 0 (default):
                                         a device-side loop of separate launches
                                         (CUDA graph with a conditional WHILE node)   */
+  int coarse_eo;                     /* 1 (default): the coarsest CG runs on the normal
+                                        equations of the even-odd Schur complement
+                                        S = A_ee - A_eo A_oo^-1 A_oe and recovers
+                                        x_o = A_oo^-1 (b_o - A_oe x_e), same stopping
+                                        test |b - A x| <= coarse_tol |b|; used where
+                                        every extent of the coarsest lattice is even
+                                        and 2N <= 64, else the plain CGNR; 0: plain  */
 } wmg_params;
 
 /* Per-right-hand-side result of a solve. */
@@ -225,6 +232,16 @@ wmg_status wmg_prolong(wmg_ctx* ctx, int level, int prec, const void* coarse_dev
  * tensor-core copy of the operator to FP32 vectors (requires coarse_tc and 2N in {16..64}). */
 wmg_status wmg_apply_coarse(wmg_ctx* ctx, int level, int prec, int dagger, const void* in_dev, void* out_dev,
                             int nrhs);
+/* out = S in with S = D^_ee - D^_eo D^_oo^-1 D^_oe the even-odd Schur complement of the coarse
+ * operator of `level` at the context's mass (the operator of the coarsest CG with coarse_eo),
+ * or S^dag = sigma_3 S sigma_3 if dagger != 0.  Parity of a site: (x + y + z + t) mod 2, even
+ * = 0.  Vectors [rhs][site][2N] over the whole coarse lattice: the odd-site entries of in are
+ * not read, those of out are set to 0.  prec: DOUBLE or SINGLE (CUDA-core stencil, D^_oo^-1 in
+ * that precision from an FP64 inversion) or HALF (FP16 tensor-core stencil copy, FP32 vectors
+ * and inverse).  WMG_EINVAL if an extent of the level is odd or 2N > 64; WMG_ERANK if a site
+ * block of D^_oo is singular. */
+wmg_status wmg_apply_coarse_schur(wmg_ctx* ctx, int level, int prec, int dagger, const void* in_dev, void* out_dev,
+                                  int nrhs);
 
 /* ---- serving: continuous-batching solve server ----
  * Keeps several gauge fields and their hierarchies resident (one context per field, set up

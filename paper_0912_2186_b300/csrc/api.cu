@@ -93,6 +93,7 @@ wmg_status alloc_hierarchy(wmg_ctx* c, const wmg_params* p) {
   if (p->prec_smoother != WMG_PREC_SINGLE && !(p->prec_smoother == WMG_PREC_HALF && half_ok))
     return bad(c, "prec_smoother must be SINGLE, or HALF with prec_sloppy SINGLE");
   if (p->coarse_persistent != 0 && p->coarse_persistent != 1) return bad(c, "coarse_persistent must be 0 or 1");
+  if (p->coarse_eo != 0 && p->coarse_eo != 1) return bad(c, "coarse_eo must be 0 or 1");
   free_hierarchy(c);
   c->prm = *p;
   c->nlev = p->nlevels;
@@ -179,6 +180,7 @@ void wmg_default_params(wmg_params* p) {
   p->prec_nullvec = WMG_PREC_SINGLE;
   p->prec_smoother = WMG_PREC_SINGLE;
   p->coarse_persistent = 0;
+  p->coarse_eo = 1;
 }
 
 const char* wmg_strerror(wmg_status s) {
@@ -555,6 +557,21 @@ wmg_status wmg_apply_coarse(wmg_ctx* c, int level, int prec, int dagger, const v
     coarse_apply(prec, L.A[prec], L.g, L.ndof, in, out, nrhs, c->d_shift[level], dagger != 0, nullptr, nullptr,
                  c->stream);
   return check(c, "apply_coarse");
+}
+
+wmg_status wmg_apply_coarse_schur(wmg_ctx* c, int level, int prec, int dagger, const void* in, void* out, int nrhs) {
+  if (!c || !in || !out || nrhs < 1 || nrhs > kMaxRhs || in == out) return WMG_EINVAL;
+  if (!prec_ok(prec) && prec != WMG_PREC_HALF) return WMG_EINVAL;
+  if (level < 1 || level >= c->nlev || !c->L[level].A[0]) return WMG_ESTATE;
+  if (prec == WMG_PREC_HALF && !c->L[level].A16) return WMG_ESTATE;
+  TRY(set_rhs_scalars(c, nullptr, nrhs));
+  LevelData& L = c->L[level];
+  const int keep = L.impl;
+  L.impl = prec == WMG_PREC_HALF ? 1 : 0;  // the stencil copy the caller asked for
+  const wmg_status st = schur_apply(c, level, prec == WMG_PREC_HALF ? WMG_PREC_SINGLE : prec, in, out, nrhs,
+                                    dagger != 0);
+  L.impl = keep;
+  return st;
 }
 
 wmg_status wmg_profile_enable(wmg_ctx* c, int on) {

@@ -38,15 +38,18 @@ template <typename R, int NR>
 __global__ void __launch_bounds__(256) k_coarse_apply(const void* __restrict__ A_, Geom g, int n,
                                                       const void* __restrict__ in_, void* __restrict__ out_, int nrhs,
                                                       const double* __restrict__ shift, int dagger,
-                                                      const int* __restrict__ active, RedBuf rb, int want_norm) {
+                                                      const int* __restrict__ active, RedBuf rb, int want_norm,
+                                                      StencilEo eo) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<R>* xs = reinterpret_cast<cpx<R>*>(smraw);          // [9 n][NR]
   cpx<R>* red = xs + (size_t)9 * n * NR;                   // [KS][n][NR]
-  const int v = blockIdx.x;
+  const int v = eo.parity < 0 ? (int)blockIdx.x : parity_site(g, blockIdx.x, eo.parity);
   const int r0 = blockIdx.y * NR;
   const int N = n / 2;
   const cpx<R>* A = reinterpret_cast<const cpx<R>*>(A_) + (size_t)v * 9 * n * n;
   const cpx<R>* in = reinterpret_cast<const cpx<R>*>(in_);
+  const cpx<R>* hin = eo.hop_in ? reinterpret_cast<const cpx<R>*>(eo.hop_in) : in;
+  const cpx<R>* add = reinterpret_cast<const cpx<R>*>(eo.add);
   cpx<R>* out = reinterpret_cast<cpx<R>*>(out_);
   __shared__ int nbs[9];
   if (threadIdx.x < 9) {
@@ -55,16 +58,19 @@ __global__ void __launch_bounds__(256) k_coarse_apply(const void* __restrict__ A
     nbs[threadIdx.x] = stencil_neighbour(g, v, c, threadIdx.x);
   }
   __syncthreads();
-  for (int k = 0; k < 9; ++k)
+  for (int k = 0; k < 9; ++k) {
+    const cpx<R>* src = k == 0 ? in : hin;
+    const bool skip = k == 0 && eo.hop_only;
     for (int i = threadIdx.x; i < n * NR; i += blockDim.x) {
       const int j = i / NR, rr = i % NR, r = r0 + rr;
       cpx<R> x{R(0), R(0)};
-      if (r < nrhs) {
-        x = in[((size_t)r * g.V + nbs[k]) * n + j];
+      if (r < nrhs && !skip) {
+        x = src[((size_t)r * g.V + nbs[k]) * n + j];
         if (dagger && j >= N) x = -x;
       }
       xs[(size_t)(k * n + j) * NR + rr] = x;
     }
+  }
   __syncthreads();
   const int row = threadIdx.x % n, ks = threadIdx.x / n;
   cpx<R> acc[NR];
@@ -95,7 +101,8 @@ __global__ void __launch_bounds__(256) k_coarse_apply(const void* __restrict__ A
       const int r = r0 + rr;
       if (r >= nrhs) continue;
       if (oneg) o = -o;
-      if (shift) o += R(shift[r]) * in[((size_t)r * g.V + v) * n + row];
+      if (shift && !eo.hop_only) o += R(shift[r]) * in[((size_t)r * g.V + v) * n + row];
+      if (add) o += add[((size_t)r * g.V + v) * n + row];
       if (!active || active[r]) out[((size_t)r * g.V + v) * n + row] = o;
       nv[rr] = double(o.re) * o.re + double(o.im) * o.im;
     }
@@ -125,7 +132,8 @@ __global__ void __launch_bounds__(256) k_coarse_apply(const void* __restrict__ A
 
 template <typename R, int NR>
 static void launch_coarse_apply(const void* A, const Geom& g, int n, const void* in, void* out, int nrhs,
-                                const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s) {
+                                const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s,
+                                const StencilEo& eo) {
   const int T = ((n * kCoarseKS + 31) / 32) * 32;
   const size_t smem = ((size_t)9 * n * NR + (size_t)kCoarseKS * n * NR) * sizeof(cpx<R>);
   static const bool attr = [] {
@@ -133,23 +141,26 @@ static void launch_coarse_apply(const void* A, const Geom& g, int n, const void*
     return true;
   }();
   (void)attr;
-  dim3 grid(g.V, (nrhs + NR - 1) / NR);
+  dim3 grid(eo.parity < 0 ? g.V : g.V / 2, (nrhs + NR - 1) / NR);
   RedBuf r = rb ? *rb : RedBuf{nullptr, nullptr, nullptr};
-  k_coarse_apply<R, NR><<<grid, T, smem, s>>>(A, g, n, in, out, nrhs, shift, dagger ? 1 : 0, active, r, rb ? 1 : 0);
+  k_coarse_apply<R, NR><<<grid, T, smem, s>>>(A, g, n, in, out, nrhs, shift, dagger ? 1 : 0, active, r, rb ? 1 : 0,
+                                              eo);
 }
 
 void coarse_apply(int prec, const void* A, const Geom& g, int n, const void* in, void* out, int nrhs,
-                  const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s) {
+                  const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s,
+                  const StencilEo* eo_opt) {
   count_launch();
+  const StencilEo eo = eo_opt ? *eo_opt : StencilEo{};
   if (prec == WMG_PREC_DOUBLE) {
-    if (nrhs == 1) launch_coarse_apply<double, 1>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
-    else if (nrhs <= 4) launch_coarse_apply<double, 4>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
-    else launch_coarse_apply<double, 8>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
+    if (nrhs == 1) launch_coarse_apply<double, 1>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s, eo);
+    else if (nrhs <= 4) launch_coarse_apply<double, 4>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s, eo);
+    else launch_coarse_apply<double, 8>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s, eo);
   } else {
-    if (nrhs == 1) launch_coarse_apply<float, 1>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
-    else if (nrhs <= 4) launch_coarse_apply<float, 4>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
-    else if (nrhs <= 8) launch_coarse_apply<float, 8>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
-    else launch_coarse_apply<float, 12>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s);
+    if (nrhs == 1) launch_coarse_apply<float, 1>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s, eo);
+    else if (nrhs <= 4) launch_coarse_apply<float, 4>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s, eo);
+    else if (nrhs <= 8) launch_coarse_apply<float, 8>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s, eo);
+    else launch_coarse_apply<float, 12>(A, g, n, in, out, nrhs, shift, dagger, active, rb, s, eo);
   }
 }
 

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
                                                                      const cf* __restrict__ in, cf* __restrict__ out,
                                                                      int nrhs, const double* __restrict__ shift,
                                                                      int dagger, const int* __restrict__ active,
-                                                                     RedBuf rb, int want_norm) {
+                                                                     RedBuf rb, int want_norm, StencilEo eo) {
   constexpr int n = NDOF, N = n / 2, K = 9 * n, KP = K + kKPad;
   constexpr int MT = n / 16, KS = K / 16;
   constexpr int R = 8 * NT, COLS = 2 * R;
@@ -113,7 +113,8 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
   __shared__ __align__(8) unsigned long long mbar[MT];
   __shared__ int nbs[9];
   __shared__ double npart[NW][32][2];  // per-lane norm partials of the MMA warps
-  const int v = blockIdx.x, r0 = blockIdx.y * R;
+  const int v = eo.parity < 0 ? (int)blockIdx.x : parity_site(g, blockIdx.x, eo.parity);
+  const int r0 = blockIdx.y * R;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool mma_warp = warp < MT * NT;
   const int m = warp % MT, blk = warp / MT;
@@ -137,17 +138,20 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
   __syncthreads();
   // lane-owned elements e = lane + 32 i of the 9n gathered values (same for every rhs)
   int offs[EPL];
-  unsigned neg = 0;  // bit i: sigma_3 sign flip of element i (adjoint, lower half of the dof)
+  unsigned neg = 0;   // bit i: sigma_3 sign flip of element i (adjoint, lower half of the dof)
+  unsigned hopm = 0;  // bit i: element i is a neighbour value read from eo.hop_in
 #pragma unroll
   for (int i = 0; i < EPL; ++i) {
     const int e = lane + 32 * i;
     offs[i] = -1;
     if (e < K) {
       const int k = e / n, j = e - k * n;
-      offs[i] = nbs[k] * n + j;
+      if (!(k == 0 && eo.hop_only)) offs[i] = nbs[k] * n + j;
       if (dagger && j >= N) neg |= 1u << i;
+      if (k > 0 && eo.hop_in) hopm |= 1u << i;
     }
   }
+  const cf* hin = eo.hop_in ? reinterpret_cast<const cf*>(eo.hop_in) : in;
   // gather this warp's right-hand sides (all loads first), then per rhs the max |Re|, |Im| by
   // shuffles and the scaled FP16 copy in column layout [Xr 0..7 | Xi 0..7 | Xr 8..15 | Xi 8..15]
   cf xv[RPW][EPL];
@@ -155,9 +159,12 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
   for (int h = 0; h < RPW; ++h) {
     const int rr = warp + NW * h, r = r0 + rr;
     const bool ok = rr < R && r < nrhs;
-    const cf* src = in + (size_t)(ok ? r : 0) * g.V * n;
+    const size_t rb0 = (size_t)(ok ? r : 0) * g.V * n;
+    const cf* src = in + rb0;
+    const cf* hsrc = hin + rb0;
 #pragma unroll
-    for (int i = 0; i < EPL; ++i) xv[h][i] = (ok && offs[i] >= 0) ? src[offs[i]] : cf{0.f, 0.f};
+    for (int i = 0; i < EPL; ++i)
+      xv[h][i] = (ok && offs[i] >= 0) ? (((hopm >> i) & 1u) ? hsrc : src)[offs[i]] : cf{0.f, 0.f};
   }
 #pragma unroll
   for (int h = 0; h < RPW; ++h) {
@@ -200,8 +207,9 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
     const uint4* Ar = As + (size_t)(0 * MT + m) * KS * 32 + lane;
     const uint4* Ai = As + (size_t)(1 * MT + m) * KS * 32 + lane;
     const __half* colbase = xb + (size_t)(blk * 16 + gq) * KP + 2 * q;
+    const int k0 = eo.hop_only ? n / 16 : 0;  // the site's own block fills the first n / 16 k-steps
 #pragma unroll 9
-    for (int k = 0; k < KS; ++k) {
+    for (int k = k0; k < KS; ++k) {
       const uint4 a0 = Ar[(size_t)k * 32], a1 = Ai[(size_t)k * 32];
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
@@ -230,7 +238,8 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
       const float yi = acc[0][1][e] + acc[1][0][e];
       const float sc = s_a * xmax[rr] * ((dagger && row >= N) ? -1.f : 1.f);
       cf o{yr * sc, yi * sc};
-      if (shift) o += (float)shift[r] * in[((size_t)r * g.V + v) * n + row];
+      if (shift && !eo.hop_only) o += (float)shift[r] * in[((size_t)r * g.V + v) * n + row];
+      if (eo.add) o += reinterpret_cast<const cf*>(eo.add)[((size_t)r * g.V + v) * n + row];
       if (!active || active[r]) out[((size_t)r * g.V + v) * n + row] = o;
       nv2[e & 1] += double(o.re) * o.re + double(o.im) * o.im;
     }
@@ -286,7 +295,8 @@ void stencil_to_mma(int prec, const void* A, int Vc, int n, float* scale, void* 
 
 template <int NDOF, int NT>
 static void launch_mma(const void* A16, const float* sA, const Geom& g, const void* in, void* out, int nrhs,
-                       const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s) {
+                       const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s,
+                       const StencilEo& eo) {
   constexpr int R = 8 * NT;
   const size_t smem = (size_t)2 * (NDOF / 16) * (9 * NDOF / 16) * 512 +
                       (size_t)2 * R * (9 * NDOF + kKPad) * sizeof(__half) + R * sizeof(float);
@@ -295,28 +305,32 @@ static void launch_mma(const void* A16, const float* sA, const Geom& g, const vo
     return true;
   }();
   (void)attr;
-  dim3 grid(g.V, (nrhs + R - 1) / R);
+  dim3 grid(eo.parity < 0 ? g.V : g.V / 2, (nrhs + R - 1) / R);
   RedBuf r = rb ? *rb : RedBuf{nullptr, nullptr, nullptr};
   k_coarse_apply_mma<NDOF, NT><<<grid, kMmaThreads, smem, s>>>((const uint4*)A16, sA, g, (const cf*)in, (cf*)out,
-                                                               nrhs, shift, dagger ? 1 : 0, active, r, rb ? 1 : 0);
+                                                               nrhs, shift, dagger ? 1 : 0, active, r, rb ? 1 : 0,
+                                                               eo);
 }
 
 template <int NDOF>
 static void launch_mma_n(const void* A16, const float* sA, const Geom& g, const void* in, void* out, int nrhs,
-                         const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s) {
-  if (nrhs <= 8) launch_mma<NDOF, 1>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s);
-  else launch_mma<NDOF, 2>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s);
+                         const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s,
+                         const StencilEo& eo) {
+  if (nrhs <= 8) launch_mma<NDOF, 1>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s, eo);
+  else launch_mma<NDOF, 2>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s, eo);
 }
 
 // n = 2N in {16, 32, 48, 64} (the tensor-core copy exists only for those)
 void coarse_apply_mma(const void* A16, const float* sA, const Geom& g, int n, const void* in, void* out, int nrhs,
-                      const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s) {
+                      const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s,
+                      const StencilEo* eo_opt) {
   count_launch();
+  const StencilEo eo = eo_opt ? *eo_opt : StencilEo{};
   switch (n) {
-    case 16: launch_mma_n<16>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s); break;
-    case 32: launch_mma_n<32>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s); break;
-    case 48: launch_mma_n<48>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s); break;
-    default: launch_mma_n<64>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s); break;
+    case 16: launch_mma_n<16>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s, eo); break;
+    case 32: launch_mma_n<32>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s, eo); break;
+    case 48: launch_mma_n<48>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s, eo); break;
+    default: launch_mma_n<64>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s, eo); break;
   }
 }
 

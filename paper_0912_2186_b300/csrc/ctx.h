@@ -33,6 +33,14 @@ struct LevelData {
   Blocking bk{};
   void* P[2] = {nullptr, nullptr};  // N fields of this level, per precision (P[0] = FP64)
   void* P16 = nullptr;     // FP16 (__half2) copy of the fine-level P for the cycle (prec_nullvec HALF)
+  long long op_version = 0;  // bumped whenever the coarse operator of this level is rebuilt
+  // even-odd coarsest solve, per precision: table of (A_oo + shift I)^-1 entries, one per
+  // distinct shift (in a workspace buffer), and the per-rhs entry index last uploaded
+  std::vector<double> eo_shift[2];
+  const void* eo_inv_ptr[2] = {nullptr, nullptr};
+  long long eo_version[2] = {-1, -1};
+  std::vector<int> eo_idx_up[2];
+  const void* eo_idx_ptr[2] = {nullptr, nullptr};
   size_t nvec_elems() const { return (size_t)g.V * ndof; }  // complex numbers per field
 };
 
@@ -60,6 +68,7 @@ struct wmg_ctx {
   double* res = nullptr;  // result arena [kResSlots][kMaxRhs * 16]
   double* d_mass = nullptr;                    // [kMaxRhs] Wilson mass per rhs
   double* d_shift[WMG_MAX_LEVELS] = {nullptr, nullptr, nullptr};  // coarse shift per rhs
+  double h_shift[wmg::kMaxRhs] = {};                                // its host copy
   int* d_active = nullptr;                     // [kMaxRhs]
   int* d_mask = nullptr;                       // [kMaxRhs]
   int* d_flag = nullptr;                       // misc device flag

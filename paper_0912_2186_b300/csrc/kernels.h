@@ -122,9 +122,30 @@ void block_gs(bool fine_level, void* vecs, const Blocking& bk, int* rank_flag, c
 
 // ---- coarse operator (coarse.cu) ----
 // stencil layout [site][9][col][row] complex (col-major blocks), n = 2N rows
+// Options of a stencil application for the even-odd form of the coarsest solve: with
+// parity >= 0 only the sites of that parity are computed and written (grid over V / 2 sites,
+// every extent even); hop_only leaves out the site's own block and the shift; hop_in supplies
+// the neighbour values (slots 1..8) instead of `in`; add is added to the result.
+struct StencilEo {
+  int parity = -1;
+  int hop_only = 0;
+  const void* hop_in = nullptr;
+  const void* add = nullptr;
+};
 // out = A in (+ shift[r] in), or sigma_3 A sigma_3 in for dagger; optional |out|^2 per rhs
 void coarse_apply(int prec, const void* A, const Geom& g, int n, const void* in, void* out, int nrhs,
-                  const double* shift, bool dagger, const int* active, const RedBuf* rb_norm, cudaStream_t s);
+                  const double* shift, bool dagger, const int* active, const RedBuf* rb_norm, cudaStream_t s,
+                  const StencilEo* eo = nullptr);
+// A_oo^-1 for the even-odd coarsest solve (coarse_eo.cu): for table entries e0 + j, j < ne,
+// inv[e0 + j][k] = (A[odd site k][0] + shifts[j] I)^-1, FP64 Gauss-Jordan with partial
+// pivoting, stored [e][k][col][row] in precision prec; *singular set to 1 on a zero pivot.
+void eo_invert(int prec, const void* A, const Geom& g, int n, const double* shifts, int e0, int ne, void* inv,
+               int* singular, cudaStream_t s);
+size_t eo_inverse_bytes(int prec, const Geom& g, int n);  // one table entry
+// out_o[r] = M_r (bc b_o[r] + hc h_o[r]) at the odd sites, M_r = inv[idx[r]] or, for dagger,
+// sigma_3 inv[idx[r]] sigma_3; b or h may be null; out may alias h (not b)
+void eo_inv_apply(int prec, const void* inv, const int* idx, const Geom& g, int n, const void* b, double bc,
+                  const void* h, double hc, void* out, int nrhs, bool dagger, const int* active, cudaStream_t s);
 // Galerkin build helpers: split the operator applied to column vectors into 9 slot fields
 // fine level: g = column (s, alpha) of P, written for ncol columns starting at col0
 void hop_split_fine(int prec, const void* gauge, const void* P, const Blocking& bk, double mass, int col0,
@@ -141,7 +162,8 @@ void stencil_scatter(int prec, const void* rs, void* A, int Vc, int n, int col0,
 size_t stencil_mma_words(int Vc, int n);  // uint4 words of the fragment-order copy
 void stencil_to_mma(int prec, const void* A, int Vc, int n, float* scale, void* out, cudaStream_t s);
 void coarse_apply_mma(const void* A16, const float* sA, const Geom& g, int n, const void* in, void* out, int nrhs,
-                      const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s);
+                      const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s,
+                      const StencilEo* eo = nullptr);
 // tcgen05 tensor-core copy of a stencil and its application (coarse_tc05.cu)
 size_t stencil_tc05_halves(int Vc, int n);
 bool coarse_tc05_supported(int n);

@@ -3,6 +3,7 @@
 // with FP64 reliable updates, the adaptive setup (Sec. 2) and the Galerkin construction
 // D^ = P^dag D P (Sec. 2).  Every arithmetic step runs in the kernels of this library; the
 // host only sequences launches and reads per-rhs residual norms.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -110,7 +111,7 @@ wmg_status set_rhs_scalars(wmg_ctx* c, const double* masses, int nrhs) {
   for (int r = 0; r < nrhs; ++r) c->h_pin[r] = masses ? masses[r] : c->mass;
   CU(c, cudaMemcpyAsync(c->d_mass, c->h_pin, nrhs * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   for (int l = 1; l < c->nlev; ++l) {
-    for (int r = 0; r < nrhs; ++r) c->h_pin[kMaxRhs + r] = (masses ? masses[r] : c->mass) - c->mass_setup;
+    for (int r = 0; r < nrhs; ++r) c->h_pin[kMaxRhs + r] = c->h_shift[r] = (masses ? masses[r] : c->mass) - c->mass_setup;
     CU(c, cudaMemcpyAsync(c->d_shift[l], c->h_pin + kMaxRhs, nrhs * sizeof(double), cudaMemcpyHostToDevice,
                           c->stream));
     CU(c, cudaStreamSynchronize(c->stream));
@@ -363,6 +364,127 @@ wmg_status clear_graphs(wmg_ctx* c) {
   return WMG_OK;
 }
 
+// ---- even-odd form of the coarsest solve ----
+// CG on the normal equations of S = A_ee - A_eo A_oo^-1 A_oe (every hop of the coarse stencil
+// changes the parity, so A_oo is block diagonal), then x_o = A_oo^-1 (b_o - A_oe x_e).  The
+// vectors keep the whole-lattice layout with zero odd sites, so the CG vector kernels and
+// their per-rhs sums are those of the plain CGNR; the stopping test |r_e| <= tol |b| is the
+// whole system's (its residual vanishes at the odd sites).
+static bool eo_possible(const LevelData& L) {
+  if (L.ndof > 64 || !L.A[0]) return false;
+  for (int i = 0; i < 4; ++i)
+    if (L.g.L[i] % 2) return false;
+  return true;
+}
+static bool eo_usable(const wmg_ctx* c, int l) { return c->prm.coarse_eo && eo_possible(c->L[l]); }
+
+struct EoTable {
+  const void* inv;
+  const int* idx;
+};
+
+// the table entries for the shifts of right-hand sides 0 .. nrhs-1 (computed for shifts not
+// yet in the table; each entry depends only on the operator and its shift) and the per-rhs
+// entry index on the device
+static wmg_status ensure_eo(wmg_ctx* c, int l, int prec, int nrhs, EoTable* tb) {
+  LevelData& L = c->L[l];
+  const std::string tag = std::to_string(l) + (prec == WMG_PREC_DOUBLE ? "d" : "s");
+  std::vector<double>& tab = L.eo_shift[prec];
+  if (L.eo_version[prec] != L.op_version) tab.clear();
+  std::vector<double> need;
+  for (int r = 0; r < nrhs; ++r)
+    if (std::find(need.begin(), need.end(), c->h_shift[r]) == need.end()) need.push_back(c->h_shift[r]);
+  std::vector<double> missing;
+  for (double v : need)
+    if (std::find(tab.begin(), tab.end(), v) == tab.end()) missing.push_back(v);
+  const size_t eb = eo_inverse_bytes(prec, L.g, L.ndof);
+  void* inv = nullptr;
+  auto it = c->ws.find("eo_inv" + tag);
+  const size_t cap = it == c->ws.end() ? 0 : it->second.second / eb;
+  if (tab.size() + missing.size() > cap) {
+    tab.clear();
+    missing = need;
+  }
+  TRY(ws_get(c, "eo_inv" + tag, std::max(cap, tab.size() + missing.size()) * eb, &inv));
+  if (inv != L.eo_inv_ptr[prec] && !tab.empty()) {
+    tab.clear();  // the buffer moved (workspaces released): recompute what this call needs
+    missing = need;
+  }
+  L.eo_inv_ptr[prec] = inv;
+  L.eo_version[prec] = L.op_version;
+  if (!missing.empty()) {
+    double* sh;
+    TRY(ws_get(c, "eo_sh" + tag, kMaxRhs * sizeof(double), (void**)&sh));
+    for (size_t i = 0; i < missing.size(); ++i) c->h_pin[i] = missing[i];
+    CU(c, cudaMemcpyAsync(sh, c->h_pin, missing.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CU(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
+    {
+      ProfScope ps(c, PROF_CGNR, 0);
+      eo_invert(prec, L.A[prec], L.g, L.ndof, sh, (int)tab.size(), (int)missing.size(), inv, c->d_flag, c->stream);
+    }
+    CU(c, cudaMemcpyAsync(c->h_pin_i, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CU(c, cudaStreamSynchronize(c->stream));
+    if (c->h_pin_i[0]) {
+      tab.clear();
+      c->err = "even-odd coarsest solve: singular site block at level " + std::to_string(l);
+      return WMG_ERANK;
+    }
+    tab.insert(tab.end(), missing.begin(), missing.end());
+  }
+  std::vector<int> idx(nrhs);
+  for (int r = 0; r < nrhs; ++r)
+    idx[r] = (int)(std::find(tab.begin(), tab.end(), c->h_shift[r]) - tab.begin());
+  int* didx;
+  TRY(ws_get(c, "eo_idx" + tag, kMaxRhs * sizeof(int), (void**)&didx));
+  if (didx != L.eo_idx_ptr[prec] || L.eo_idx_up[prec] != idx) {
+    TRY(upload_ints(c, didx, idx));
+    L.eo_idx_up[prec] = idx;
+    L.eo_idx_ptr[prec] = didx;
+  }
+  tb->inv = inv;
+  tb->idx = didx;
+  return WMG_OK;
+}
+
+// a parity-restricted stencil pass: the mma.sync FP16 stencil where its copy exists and the
+// level's choice is a tensor-core one, else the CUDA-core stencil of precision prec
+static void eo_stencil(wmg_ctx* c, int l, int prec, const void* in, void* out, int nrhs, bool dagger,
+                       const StencilEo& eo, const RedBuf* rb) {
+  const LevelData& L = c->L[l];
+  const int impl = prec == WMG_PREC_SINGLE ? (L.impl >= 0 ? L.impl : (L.A16 ? 1 : 0)) : 0;
+  if (impl >= 1 && L.A16)
+    coarse_apply_mma(L.A16, L.sA, L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, nullptr, rb, c->stream, &eo);
+  else
+    coarse_apply(prec, L.A[prec], L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, nullptr, rb, c->stream, &eo);
+}
+
+// out_e = S in_e (or S^dag = sigma_3 S sigma_3 in_e), odd sites of out untouched; t: scratch
+static void schur_op(wmg_ctx* c, int l, int prec, const EoTable& tb, const void* in, void* out, void* t, int nrhs,
+                     bool dagger, const RedBuf* rb) {
+  const LevelData& L = c->L[l];
+  StencilEo hop;  // t_o = A_oe in_e
+  hop.parity = 1;
+  hop.hop_only = 1;
+  eo_stencil(c, l, prec, in, t, nrhs, dagger, hop, nullptr);
+  // t_o = -A_oo^-1 t_o
+  eo_inv_apply(prec, tb.inv, tb.idx, L.g, L.ndof, nullptr, 0.0, t, -1.0, t, nrhs, dagger, nullptr, c->stream);
+  StencilEo ev;  // out_e = (A_ee + shift) in_e + A_eo t_o
+  ev.parity = 0;
+  ev.hop_in = t;
+  eo_stencil(c, l, prec, in, out, nrhs, dagger, ev, rb);
+}
+
+wmg_status schur_apply(wmg_ctx* c, int l, int prec, const void* in, void* out, int nrhs, bool dagger) {
+  if (!eo_possible(c->L[l])) return WMG_EINVAL;
+  EoTable tb;
+  TRY(ensure_eo(c, l, prec, nrhs, &tb));
+  void* t;
+  TRY(vec_ws(c, l, "eo_t", prec, nrhs, &t));
+  blas_zero(prec, out, c->L[l].nvec_elems(), nrhs, c->stream);
+  schur_op(c, l, prec, tb, in, out, t, nrhs, dagger, nullptr);
+  return check(c, "schur_apply");
+}
+
 // CG on the normal equations on level l (coarse): x = A^-1 b approximately
 wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, const int* active) {
   const LevelData& L = c->L[l];
@@ -373,47 +495,61 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
   TRY(vec_ws(c, l, "cg_q", prec, nrhs, &q));
   TRY(vec_ws(c, l, "cg_z", prec, nrhs, &z));
   const int impl = prec == WMG_PREC_SINGLE ? (L.impl >= 0 ? L.impl : (L.A05 ? 2 : (L.A16 ? 1 : 0))) : 0;
-  if (c->prm.coarse_persistent && impl == 1 && nrhs <= 16) {
-    // the whole solve in one cooperative kernel (FP16 tensor-core stencil, fused updates)
-    void *part, *bar, *r16, *p16, *rsc, *psc;
-    TRY(ws_get(c, "pcg_part", (size_t)4 * 16 * kPersistentMaxGrid * sizeof(double), &part));
-    TRY(ws_get(c, "pcg_bar", 4 * sizeof(unsigned), &bar));
-    TRY(ws_get(c, "pcg_r16_" + std::to_string(l), cgnr_persistent_copy_bytes(L.g.V, L.ndof), &r16));
-    TRY(ws_get(c, "pcg_p16_" + std::to_string(l), cgnr_persistent_copy_bytes(L.g.V, L.ndof), &p16));
-    TRY(ws_get(c, "pcg_rsc_" + std::to_string(l), (size_t)L.g.V * 16 * sizeof(float), &rsc));
-    TRY(ws_get(c, "pcg_psc_" + std::to_string(l), (size_t)L.g.V * 16 * sizeof(float), &psc));
-    if (!c->d_pcg_err) {
-      TRY(ws_get(c, "pcg_err", sizeof(int), (void**)&c->d_pcg_err));
-      CU(c, cudaMemsetAsync(c->d_pcg_err, 0, sizeof(int), c->stream));
-    }
-    bool ran;
-    {
-      ProfScope ps(c, PROF_CGNR, 0, nact_of(c, active, nrhs));
-      ran = cgnr_persistent(L.A16, L.sA, L.g, L.ndof, c->d_shift[l], b, x, r, p, q, z, r16, p16, (float*)rsc,
-                            (float*)psc, nrhs,
-                            c->prm.coarse_tol * c->prm.coarse_tol, c->prm.coarse_maxit, active, (double*)part,
-                            (unsigned*)bar, c->d_pcg_err, c->d_cgint, c->d_cgint + kMaxRhs, c->stream);
-    }
-    if (ran) {
-      if (c->prof_on) {
-        // instrumentation: the stencil applications the kernel made (2 per iteration + 1 per rhs)
-        // and the operator bytes they read, from its iteration counts
-        CU(c, cudaMemcpyAsync(c->h_pin_i, c->d_cgint, 2 * kMaxRhs * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-        CU(c, cudaStreamSynchronize(c->stream));
-        int maxit = 0;
-        double applies = 0;
-        for (int i = 0; i < nrhs; ++i) {
-          const int it = c->h_pin_i[kMaxRhs + i];
-          if (it > 0) applies += 2.0 * it + 1.0;
-          maxit = std::max(maxit, it);
-        }
-        c->prof_units[PROF_COARSE] += applies;
-        c->prof_bytes[PROF_CGNR] += (2.0 * maxit + 1.0) * coarse_bytes(c, l, prec, nact_of(c, active, nrhs));
+  const bool eo = eo_usable(c, l);
+  if (!eo) {
+    if (c->prm.coarse_persistent && impl == 1 && nrhs <= 16) {
+      // the whole solve in one cooperative kernel (FP16 tensor-core stencil, fused updates)
+      void *part, *bar, *r16, *p16, *rsc, *psc;
+      TRY(ws_get(c, "pcg_part", (size_t)4 * 16 * kPersistentMaxGrid * sizeof(double), &part));
+      TRY(ws_get(c, "pcg_bar", 4 * sizeof(unsigned), &bar));
+      TRY(ws_get(c, "pcg_r16_" + std::to_string(l), cgnr_persistent_copy_bytes(L.g.V, L.ndof), &r16));
+      TRY(ws_get(c, "pcg_p16_" + std::to_string(l), cgnr_persistent_copy_bytes(L.g.V, L.ndof), &p16));
+      TRY(ws_get(c, "pcg_rsc_" + std::to_string(l), (size_t)L.g.V * 16 * sizeof(float), &rsc));
+      TRY(ws_get(c, "pcg_psc_" + std::to_string(l), (size_t)L.g.V * 16 * sizeof(float), &psc));
+      if (!c->d_pcg_err) {
+        TRY(ws_get(c, "pcg_err", sizeof(int), (void**)&c->d_pcg_err));
+        CU(c, cudaMemsetAsync(c->d_pcg_err, 0, sizeof(int), c->stream));
       }
-      return check(c, "cgnr (persistent kernel)");
+      bool ran;
+      {
+        ProfScope ps(c, PROF_CGNR, 0, nact_of(c, active, nrhs));
+        ran = cgnr_persistent(L.A16, L.sA, L.g, L.ndof, c->d_shift[l], b, x, r, p, q, z, r16, p16, (float*)rsc,
+                              (float*)psc, nrhs,
+                              c->prm.coarse_tol * c->prm.coarse_tol, c->prm.coarse_maxit, active, (double*)part,
+                              (unsigned*)bar, c->d_pcg_err, c->d_cgint, c->d_cgint + kMaxRhs, c->stream);
+      }
+      if (ran) {
+        if (c->prof_on) {
+          // instrumentation: the stencil applications the kernel made (2 per iteration + 1 per rhs)
+          // and the operator bytes they read, from its iteration counts
+          CU(c, cudaMemcpyAsync(c->h_pin_i, c->d_cgint, 2 * kMaxRhs * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+          CU(c, cudaStreamSynchronize(c->stream));
+          int maxit = 0;
+          double applies = 0;
+          for (int i = 0; i < nrhs; ++i) {
+            const int it = c->h_pin_i[kMaxRhs + i];
+            if (it > 0) applies += 2.0 * it + 1.0;
+            maxit = std::max(maxit, it);
+          }
+          c->prof_units[PROF_COARSE] += applies;
+          c->prof_bytes[PROF_CGNR] += (2.0 * maxit + 1.0) * coarse_bytes(c, l, prec, nact_of(c, active, nrhs));
+        }
+        return check(c, "cgnr (persistent kernel)");
+      }
+      (void)cudaGetLastError();  // not launchable here: the multi-kernel path below
     }
-    (void)cudaGetLastError();  // not launchable here: the multi-kernel path below
   }
+  EoTable tb{nullptr, nullptr};
+  void* t = nullptr;
+  if (eo) {
+    TRY(ensure_eo(c, l, prec, nrhs, &tb));
+    TRY(vec_ws(c, l, "eo_t", prec, nrhs, &t));
+  }
+  // the operator of the CG: A, or the Schur complement S on the even sites
+  auto op = [&](const void* in, void* out, bool dagger, const RedBuf* rb) {
+    if (eo) schur_op(c, l, prec, tb, in, out, t, nrhs, dagger, rb);
+    else coarse_op(c, l, prec, in, out, nrhs, dagger, nullptr, rb);
+  };
   CgScalars cg;
   cg.zz = res_slot(c, RES_CGZZ);
   cg.rr = res_slot(c, RES_CGRR);
@@ -424,10 +560,23 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
   cg.tol2 = c->prm.coarse_tol * c->prm.coarse_tol;
   cudaStream_t s = c->stream;
   blas_zero(prec, x, n, nrhs, s);
-  blas_convert(prec, r, prec, b, n, nrhs, nullptr, s);
   blas_norm2(prec, b, n, nrhs, redbuf(c, RES_CGBB), s);
+  if (eo) {
+    // r_e = b_e - A_eo A_oo^-1 b_o; q, z keep zero odd sites (their passes write even sites only)
+    blas_zero(prec, r, n, nrhs, s);
+    blas_zero(prec, q, n, nrhs, s);
+    blas_zero(prec, z, n, nrhs, s);
+    eo_inv_apply(prec, tb.inv, tb.idx, L.g, L.ndof, b, -1.0, nullptr, 0.0, t, nrhs, false, nullptr, s);
+    StencilEo pre;
+    pre.parity = 0;
+    pre.hop_only = 1;
+    pre.add = b;
+    eo_stencil(c, l, prec, t, r, nrhs, false, pre, nullptr);
+  } else {
+    blas_convert(prec, r, prec, b, n, nrhs, nullptr, s);
+  }
   RedBuf rzz0{c->red_partial, c->red_counter, cg.zz};
-  coarse_op(c, l, prec, r, z, nrhs, true, nullptr, &rzz0);
+  op(r, z, true, &rzz0);
   blas_convert(prec, p, prec, z, n, nrhs, nullptr, s);
   k_cg_init<<<1, 64, 0, s>>>(cg.done, cg.iters, cg.bb, active, nrhs, c->d_flag + 1);
   count_launch();
@@ -439,7 +588,7 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
   auto body = [&](int parity) {
     {
       ProfScope ps(c, PROF_COARSE, cb, nrhs);
-      coarse_op(c, l, prec, p, q, nrhs, false, nullptr, &rqq);
+      op(p, q, false, &rqq);
     }
     {
       ProfScope ps(c, PROF_BLAS, 0);
@@ -448,7 +597,7 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
     RedBuf rzz{c->red_partial, c->red_counter, cg.zz + (1 - parity) * nrhs};
     {
       ProfScope ps(c, PROF_COARSE, cb, nrhs);
-      coarse_op(c, l, prec, r, z, nrhs, true, nullptr, &rzz);
+      op(r, z, true, &rzz);
     }
     {
       ProfScope ps(c, PROF_BLAS, 0);
@@ -468,9 +617,9 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
     // iterations followed by a check kernel that clears the loop condition once every
     // right-hand side has converged or coarse_maxit is reached.  Built once per argument set.
     char key[512];
-    std::snprintf(key, sizeof key, "cg%d/%d/%d/%p/%p/%p/%p/%p/%p/%p/%p/%p/%p/%.17g/%d", l, prec, nrhs, L.A[prec],
-                  (void*)L.A16, x, r, p, q, z, (void*)c->d_shift[l], (void*)c->red_partial, (void*)c->res, cg.tol2,
-                  c->prm.coarse_maxit);
+    std::snprintf(key, sizeof key, "cg%d/%d/%d/%p/%p/%p/%p/%p/%p/%p/%p/%p/%p/%.17g/%d/%d/%p/%p/%p", l, prec, nrhs,
+                  L.A[prec], (void*)L.A16, x, r, p, q, z, (void*)c->d_shift[l], (void*)c->red_partial, (void*)c->res,
+                  cg.tol2, c->prm.coarse_maxit, eo ? 1 : 0, tb.inv, (const void*)tb.idx, t);
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
       if (c->graphs.size() > 64) TRY(clear_graphs(c));
@@ -513,6 +662,14 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
       TRY(all_done(&all));
       if (all) break;
     }
+  }
+  if (eo) {
+    // x_o = A_oo^-1 (b_o - A_oe x_e)
+    StencilEo hop;
+    hop.parity = 1;
+    hop.hop_only = 1;
+    eo_stencil(c, l, prec, x, t, nrhs, false, hop, nullptr);
+    eo_inv_apply(prec, tb.inv, tb.idx, L.g, L.ndof, b, 1.0, t, -1.0, x, nrhs, false, active, s);
   }
   return check(c, "cgnr");
 }
@@ -609,6 +766,7 @@ wmg_status galerkin(wmg_ctx* c, int l, int prec) {
       stencil_to_tc05(WMG_PREC_SINGLE, C.A[1], C.g.V, n, C.sA, C.A05, c->stream);
     }
   }
+  ++C.op_version;
   if (c->prm.coarse_tc == 3 && c->prm.prec_sloppy == WMG_PREC_SINGLE) TRY(tune_coarse(c, l + 1));
   return check(c, "galerkin");
 }

@@ -17,6 +17,8 @@ void level_apply(wmg_ctx* c, int l, int prec, const void* in, void* out, int nrh
                  const RedBuf* rb);
 wmg_status mr(wmg_ctx* c, int l, int prec, void* x, const void* b, int nrhs, int nu, const int* active);
 wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, const int* active);
+// out_e = S in_e (S^dag for dagger) with S the even-odd Schur complement of level l's operator
+wmg_status schur_apply(wmg_ctx* c, int l, int prec, const void* in, void* out, int nrhs, bool dagger);
 wmg_status cycle(wmg_ctx* c, int l, int last, int prec, const void* r, void* e, int nrhs, const int* active);
 wmg_status galerkin(wmg_ctx* c, int l, int prec);
 wmg_status orthonormalise(wmg_ctx* c, int l);

@@ -110,6 +110,13 @@ WMG_HD void site_coords(const Geom& g, int v, int c[4]) {
   c[2] = v % g.L[2];
   c[3] = v / g.L[2];
 }
+// the k-th site (lexicographic order) of parity p = (x + y + z + t) mod 2; L[0] even, so the
+// sites 2k and 2k + 1 share y, z, t and exactly one of them has parity p
+WMG_HD int parity_site(const Geom& g, int k, int p) {
+  int c[4];
+  site_coords(g, 2 * k, c);
+  return 2 * k + ((p + c[0] + c[1] + c[2] + c[3]) & 1);
+}
 WMG_HD int site_index(const Geom& g, const int c[4]) {
   return c[0] + g.L[0] * (c[1] + g.L[1] * (c[2] + g.L[2] * c[3]));
 }

@@ -48,6 +48,7 @@ class Params(ctypes.Structure):
         ("prec_nullvec", ctypes.c_int),
         ("prec_smoother", ctypes.c_int),
         ("coarse_persistent", ctypes.c_int),
+        ("coarse_eo", ctypes.c_int),
     ]
 
 
@@ -103,6 +104,7 @@ def load():
         "wmg_restrict": (i, [vp, i, i, vp, vp, i]),
         "wmg_prolong": (i, [vp, i, i, vp, vp, i]),
         "wmg_apply_coarse": (i, [vp, i, i, i, vp, vp, i]),
+        "wmg_apply_coarse_schur": (i, [vp, i, i, i, vp, vp, i]),
         "wmg_residual_noalloc": (i, [vp, i, vp, vp, vp, vp, i]),
         "wmg_server_create": (i, [P(vp), ctypes.c_size_t]),
         "wmg_server_add_field": (i, [vp, vp, i, P(i)]),
@@ -304,6 +306,10 @@ class Context:
     def apply_coarse(self, level, prec, inp, out, nrhs, dagger=False):
         return self._check(self.lib.wmg_apply_coarse(self.h, int(level), prec, int(bool(dagger)), _ptr(inp),
                                                      _ptr(out), int(nrhs)))
+
+    def apply_coarse_schur(self, level, prec, inp, out, nrhs, dagger=False):
+        return self._check(self.lib.wmg_apply_coarse_schur(self.h, int(level), prec, int(bool(dagger)), _ptr(inp),
+                                                           _ptr(out), int(nrhs)))
 
 
 class Server:

@@ -24,7 +24,7 @@ def test_default_params_and_strerror(lib):
     p = wmg.default_params()
     assert p.nlevels == 2 and p.nu_post == 4 and p.tol == 1e-10
     assert tuple(p.block[0]) == (4, 4, 4, 4)
-    assert p.prec_nullvec == 1 and p.prec_smoother == 1 and p.coarse_persistent == 0  # the tail is written
+    assert p.prec_nullvec == 1 and p.prec_smoother == 1 and p.coarse_persistent == 0 and p.coarse_eo == 1
     assert lib.wmg_strerror(wmg.ENOCONV) == b"solver did not converge"
     assert ctypes.sizeof(wmg.Params) == 128 and ctypes.sizeof(wmg.Info) == 32
 

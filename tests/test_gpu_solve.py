@@ -240,3 +240,26 @@ def test_persistent_coarse_cgnr(W):
     x1 = dev(np.zeros_like(b[1:2]))
     _, i1 = ctx.solve(dev(b[1:2]), x1, 1)
     assert np.array_equal(host(x1)[0], xs[1]) and i1[0]["iters"] == info[1]["iters"]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_even_odd_coarsest_solve(W, prec):
+    """coarse_eo = 1 (default) and 0 on the same hierarchy: both meet the 1e-10 true residual
+    (oracle D) with iteration counts within 2 of each other; the even-odd batch result equals the
+    single solve."""
+    its = {}
+    for flag in (1, 0):
+        ctx, U, p = _ctx(W, CFG1, prec, coarse_eo=flag)
+        b = synth.gaussian_spinors(CFG1["dims"], 3, 24)
+        x = dev(np.zeros_like(b))
+        st, info = ctx.solve(dev(b), x, 3)
+        xs = host(x)
+        for r in range(3):
+            assert info[r]["converged"]
+            assert oracle_resid(U, CFG1["m"], b[r], xs[r]) <= 1.05e-10
+        its[flag] = [i["iters"] for i in info]
+        if flag:
+            x1 = dev(np.zeros_like(b[2:3]))
+            _, i1 = ctx.solve(dev(b[2:3]), x1, 1)
+            assert np.array_equal(host(x1)[0], xs[2]) and i1[0]["iters"] == info[2]["iters"]
+    assert all(abs(a - b) <= 2 for a, b in zip(its[0], its[1]))
