@@ -218,6 +218,10 @@ wmg_status wmg_create(wmg_ctx** out, const int dims[4], void* stream) {
     c->stream = c->own_stream;
   }
   if (const char* g = std::getenv("WMG_NO_GRAPHS")) c->use_graphs = !(g[0] == '1');
+  if (const char* g = std::getenv("WMG_CG_CHUNK")) {
+    const int v = std::atoi(g);
+    if (v >= 2 && v <= 32 && v % 2 == 0) c->cg_chunk = v;
+  }
   if (const char* g = std::getenv("WMG_UNFUSED_GALERKIN")) c->use_fused_galerkin = !(g[0] == '1');
   c->L[0].g = c->fine;
   c->L[0].ndof = 12;

@@ -223,6 +223,43 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
   }
   // a tile whose wait expired: give its copies a second bounded chance to land before exit
   if (mma_warp && !ready) mbar_wait_bounded(smem_addr(&mbar[m]), 0, kMmaSpinLimit);
+  if (eo.inv) {
+    // odd-site pass of the Schur complement: u = -M_r h with h = A_oe x (this CTA's result,
+    // before the adjoint's output sigma_3) and M_r = A_oo^-1 of the rhs's table entry; for the
+    // adjoint -sigma_3 M_r h (= -sigma_3 M_r sigma_3 of the sigma_3-flipped result).  h goes
+    // through shared memory (the FP16 staging area, free once every warp is past its MMAs);
+    // thread (row, rhs) forms the row's dot product, the inverse read by columns.
+    __syncthreads();
+    cf* hs = reinterpret_cast<cf*>(xb);  // [R][n]
+    if (mma_warp) {
+      const float s_a = sA[v];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int row = 16 * m + gq + (e >= 2 ? 8 : 0);
+        const int rr = blk * 8 + 2 * q + (e & 1);
+        const float sc = s_a * xmax[rr];
+        hs[rr * n + row] = cf{(acc[0][0][e] - acc[1][1][e]) * sc, (acc[0][1][e] + acc[1][0][e]) * sc};
+      }
+    }
+    __syncthreads();
+    const cf* inv = reinterpret_cast<const cf*>(eo.inv);
+    for (int t = threadIdx.x; t < n * R; t += kMmaThreads) {
+      const int rr = t / n, row = t - rr * n, r = r0 + rr;
+      if (r >= nrhs) continue;
+      const float2* mcol =
+          reinterpret_cast<const float2*>(inv + ((size_t)eo.inv_idx[r] * (g.V / 2) + blockIdx.x) * n * n + row);
+      const cf* h = hs + rr * n;
+      cf u{0.f, 0.f};
+#pragma unroll 8
+      for (int col = 0; col < n; ++col) {
+        const float2 a = __ldg(mcol + (size_t)col * n);
+        cfma(u, cf{a.x, a.y}, h[col]);
+      }
+      const float sg = (dagger && row >= N) ? 1.f : -1.f;
+      if (!active || active[r]) out[((size_t)r * g.V + v) * n + row] = cf{sg * u.re, sg * u.im};
+    }
+    return;
+  }
   // epilogue: thread holds rows 16 m + gq (+8) and right-hand sides 8 blk + 2q + (e & 1)
   double nv2[2] = {0.0, 0.0};
   if (mma_warp) {

@@ -75,6 +75,7 @@ struct wmg_ctx {
   int* d_cgint = nullptr;                      // [2][kMaxRhs] cg done / iters
   cudaStream_t own_stream = nullptr;          // created when the caller passes no stream
   bool use_graphs = true;                      // capture the coarsest CGNR iterations
+  int cg_chunk = 2;                            // CGNR iterations between convergence checks (even)
   bool use_fused_galerkin = true;              // fused fine-level Galerkin kernel
   int* d_pcg_err = nullptr;                    // sticky error flag of the persistent CGNR (per solve)
   std::map<std::string, std::pair<cudaGraphExec_t, long long>> graphs;  // + launches per replay

@@ -126,11 +126,15 @@ void block_gs(bool fine_level, void* vecs, const Blocking& bk, int* rank_flag, c
 // parity >= 0 only the sites of that parity are computed and written (grid over V / 2 sites,
 // every extent even); hop_only leaves out the site's own block and the shift; hop_in supplies
 // the neighbour values (slots 1..8) instead of `in`; add is added to the result.
+// The tensor-core stencil also takes the odd-site block inverses (inv, inv_idx as for
+// eo_inv_apply; parity 1 and hop_only): it then writes -M_r (its result) instead of the result.
 struct StencilEo {
   int parity = -1;
   int hop_only = 0;
   const void* hop_in = nullptr;
   const void* add = nullptr;
+  const void* inv = nullptr;
+  const int* inv_idx = nullptr;
 };
 // out = A in (+ shift[r] in), or sigma_3 A sigma_3 in for dagger; optional |out|^2 per rhs
 void coarse_apply(int prec, const void* A, const Geom& g, int n, const void* in, void* out, int nrhs,

@@ -446,13 +446,17 @@ static wmg_status ensure_eo(wmg_ctx* c, int l, int prec, int nrhs, EoTable* tb) 
   return WMG_OK;
 }
 
-// a parity-restricted stencil pass: the mma.sync FP16 stencil where its copy exists and the
-// level's choice is a tensor-core one, else the CUDA-core stencil of precision prec
+// the parity-restricted stencil passes use the mma.sync FP16 stencil where its copy exists and
+// the level's choice is a tensor-core one, else the CUDA-core stencil of precision prec
+static bool eo_mma(const wmg_ctx* c, int l, int prec) {
+  const LevelData& L = c->L[l];
+  const int impl = prec == WMG_PREC_SINGLE ? (L.impl >= 0 ? L.impl : (L.A16 ? 1 : 0)) : 0;
+  return impl >= 1 && L.A16;
+}
 static void eo_stencil(wmg_ctx* c, int l, int prec, const void* in, void* out, int nrhs, bool dagger,
                        const StencilEo& eo, const RedBuf* rb) {
   const LevelData& L = c->L[l];
-  const int impl = prec == WMG_PREC_SINGLE ? (L.impl >= 0 ? L.impl : (L.A16 ? 1 : 0)) : 0;
-  if (impl >= 1 && L.A16)
+  if (eo_mma(c, l, prec))
     coarse_apply_mma(L.A16, L.sA, L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, nullptr, rb, c->stream, &eo);
   else
     coarse_apply(prec, L.A[prec], L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, nullptr, rb, c->stream, &eo);
@@ -462,12 +466,17 @@ static void eo_stencil(wmg_ctx* c, int l, int prec, const void* in, void* out, i
 static void schur_op(wmg_ctx* c, int l, int prec, const EoTable& tb, const void* in, void* out, void* t, int nrhs,
                      bool dagger, const RedBuf* rb) {
   const LevelData& L = c->L[l];
-  StencilEo hop;  // t_o = A_oe in_e
+  StencilEo hop;  // t_o = -A_oo^-1 A_oe in_e
   hop.parity = 1;
   hop.hop_only = 1;
-  eo_stencil(c, l, prec, in, t, nrhs, dagger, hop, nullptr);
-  // t_o = -A_oo^-1 t_o
-  eo_inv_apply(prec, tb.inv, tb.idx, L.g, L.ndof, nullptr, 0.0, t, -1.0, t, nrhs, dagger, nullptr, c->stream);
+  if (eo_mma(c, l, prec)) {
+    hop.inv = tb.inv;  // the tensor-core pass applies the block inverses in its epilogue
+    hop.inv_idx = tb.idx;
+    eo_stencil(c, l, prec, in, t, nrhs, dagger, hop, nullptr);
+  } else {
+    eo_stencil(c, l, prec, in, t, nrhs, dagger, hop, nullptr);
+    eo_inv_apply(prec, tb.inv, tb.idx, L.g, L.ndof, nullptr, 0.0, t, -1.0, t, nrhs, dagger, nullptr, c->stream);
+  }
   StencilEo ev;  // out_e = (A_ee + shift) in_e + A_eo t_o
   ev.parity = 0;
   ev.hop_in = t;
@@ -611,7 +620,7 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
     for (int i = 0; i < nrhs; ++i) *all = *all && c->h_pin_i[i];
     return WMG_OK;
   };
-  const int chunk = 8;  // even: every chunk starts at parity 0
+  const int chunk = c->cg_chunk;  // even: every chunk starts at parity 0
   if (!c->prof_on && c->use_graphs) {
     // The CGNR loop runs on the device: a graph whose WHILE node repeats a captured chunk of
     // iterations followed by a check kernel that clears the loop condition once every
@@ -619,7 +628,7 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
     char key[512];
     std::snprintf(key, sizeof key, "cg%d/%d/%d/%p/%p/%p/%p/%p/%p/%p/%p/%p/%p/%.17g/%d/%d/%p/%p/%p", l, prec, nrhs,
                   L.A[prec], (void*)L.A16, x, r, p, q, z, (void*)c->d_shift[l], (void*)c->red_partial, (void*)c->res,
-                  cg.tol2, c->prm.coarse_maxit, eo ? 1 : 0, tb.inv, (const void*)tb.idx, t);
+                  cg.tol2, c->prm.coarse_maxit * 64 + chunk, eo ? 1 : 0, tb.inv, (const void*)tb.idx, t);
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
       if (c->graphs.size() > 64) TRY(clear_graphs(c));

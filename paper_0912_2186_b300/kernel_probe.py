@@ -4,8 +4,10 @@ profiling (ncu --nvtx --nvtx-include "probe/") and quick timing.
     python -m paper_0912_2186_b300.kernel_probe [--nrhs 12] [--reps 2] [--time]
 
 The hierarchy is built once (adaptive setup, 4^4 blocks, N = 24, FP32 cycle) before the range;
-inside it each of the fine dslash (FP32, fused MR reductions off), restrict, prolong and the
-tensor-core coarse stencil runs `reps` times on nrhs right-hand sides.  --time prints CUDA-event
+inside it each of the fine dslash (FP32, fused MR reductions off), restrict, prolong, the
+tensor-core coarse stencil and the even-odd Schur complement of the coarse operator (two
+parity-restricted tensor-core stencil passes and the odd-site block inverses) runs `reps` times
+on nrhs right-hand sides.  --time prints CUDA-event
 times per call of 50 back-to-back calls; for kernels shorter than the host's per-call cost
 (Python and ctypes, some 10 us) that time is the host's, not the kernel's.
 """
@@ -51,6 +53,7 @@ def main(argv=None):
         "restrict": lambda: ctx.restrict(0, wmg.PREC_SINGLE, fi, co, nr),
         "prolong": lambda: ctx.prolong(0, wmg.PREC_SINGLE, ci, fo, nr),
         "coarse": lambda: ctx.apply_coarse(1, wmg.PREC_HALF, ci, co, nr),
+        "schur": lambda: ctx.apply_coarse_schur(1, wmg.PREC_HALF, ci, co, nr),
     }
     for f in ops.values():
         f()
