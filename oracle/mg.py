@@ -150,7 +150,9 @@ def restrict(P, psi, block):
     phi = np.zeros((fb.shape[0], 2 * N), dtype=np.complex128)
     for s in range(2):
         f = fb[:, :, s * h:(s + 1) * h].reshape(fb.shape[0], -1, 1)
-        phi[:, s * N:(s + 1) * N] = np.matmul(np.conj(halves[s]), f)[..., 0]
+        # conj(P)^T f written as conj(P^T conj(f)): the same products and sums, without a
+        # conjugated copy of P
+        phi[:, s * N:(s + 1) * N] = np.conj(np.matmul(halves[s], np.conj(f)))[..., 0]
     X, Y, Z, T = cd
     return phi.reshape(T, Z, Y, X, 2 * N)
 

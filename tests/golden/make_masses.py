@@ -68,7 +68,7 @@ def main():
                "definition": "lambda_min(D^dag D) = ratio * m^2 (free-field lambda_min at mass m)",
                "masses": {k: found[k] for k in sorted(found, key=float, reverse=True)},
                "evaluations": sorted([[e["m"], e["lambda"], e["lambda"] / e["m"] ** 2] for e in evals]),
-               "method": "oracle MG-GCR solves (tol 1e-7) inside Lanczos on (D^dag D)^-1 (eig tol 1e-2); "
+               "method": "oracle MG-GCR solves (tol 1e-5) inside Lanczos on (D^dag D)^-1 (eig tol 1e-2); "
                          "secant on sqrt(lambda_min); ratio within 5 %"}
         with open(out, "w") as fh:
             json.dump(rec, fh, indent=1)
