@@ -70,6 +70,12 @@ WMG_D void site_coords_fast(const Geom& g, const DslashDiv& d, int v, int c[4]) 
   c[3] = (int)q2;
 }
 
+// With RED > 0 an FP32 CTA takes SPB consecutive site blocks of one rhs (its per-site sums
+// added in that order), so that the CTAs publishing partial sums (a fence and an atomic each)
+// are SPB times fewer; the partition depends on the volume only.  (The FP64 kernel runs one
+// CTA per SM and keeps one block per CTA.)
+template <typename R, int RED> constexpr int dslash_spb() { return RED > 0 && sizeof(R) == 4 ? 8 : 1; }
+
 template <typename R, int RED>
 __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(void* __restrict__ out,
                                                                         const void* __restrict__ in,
@@ -78,14 +84,17 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(void* __
                                                                         DslashDiv dv, const double* __restrict__ mass,
                                                                         const int* __restrict__ active, int nrhs,
                                                                         int nblk_site, RedBuf rb) {
+  constexpr int SPB = dslash_spb<R, RED>();
   const int rhs = blockIdx.x % nrhs;
-  const int sb = blockIdx.x / nrhs;
+  const int sbe = blockIdx.x / nrhs;
   if (active && !active[rhs]) return;  // whole CTA exits together (uniform per CTA)
-  const int v = sb * blockDim.x + threadIdx.x;
   const size_t fb = spinor_field_bytes<R>(g.V);
   const char* inr = reinterpret_cast<const char*>(in) + fb * rhs;
-  cpx<R> acc[12];
   double red[3] = {0.0, 0.0, 0.0};
+#pragma unroll 1
+  for (int j = 0; j < SPB; ++j) {
+  const int v = (sbe * SPB + j) * blockDim.x + threadIdx.x;
+  cpx<R> acc[12];
   if (v < g.V) {
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc[i] = cpx<R>{R(0), R(0)};
@@ -127,15 +136,16 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(void* __
         a0 += acc[i].re * self[i].re + acc[i].im * self[i].im;
         a1 += acc[i].re * self[i].im - acc[i].im * self[i].re;
       }
-      red[0] = double(a0);
-      red[1] = double(a1);
+      red[0] += double(a0);
+      red[1] += double(a1);
     }
     if (RED >= 1) {
       R nn = 0;
 #pragma unroll
       for (int i = 0; i < 12; ++i) nn += acc[i].re * acc[i].re + acc[i].im * acc[i].im;
-      red[RED == 2 ? 2 : 0] = double(nn);
+      red[RED == 2 ? 2 : 0] += double(nn);
     }
+  }
   }
   if (RED > 0) {
     constexpr int NV = RED == 2 ? 3 : 1;
@@ -143,7 +153,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(void* __
     double vals[NV];
     for (int i = 0; i < NV; ++i) vals[i] = red[i];
     cta_reduce<NV>(vals, sm);
-    grid_finish<NV>(rb, rhs, sb, nblk_site, vals);
+    grid_finish<NV>(rb, rhs, sbe, nblk_site, vals);
   }
 }
 
@@ -324,14 +334,16 @@ void dslash(int prec, void* out, const void* in, const void* b, const void* gaug
             const double* mass_dev, const int* active, int nrhs, int red, const RedBuf* rb, cudaStream_t s) {
   count_launch();
   const int nb = dslash_blocks(g.V);
-  const unsigned grid = (unsigned)nb * nrhs;
+  const int spb = prec == WMG_PREC_DOUBLE ? dslash_spb<double, 1>() : dslash_spb<float, 1>();
+  const int nbr = (nb + spb - 1) / spb;  // CTAs per rhs with RED > 0
+  const unsigned grid = (unsigned)nb * nrhs, gridr = (unsigned)nbr * nrhs;
   RedBuf r = rb ? *rb : RedBuf{nullptr, nullptr, nullptr};
   const DslashDiv dv{make_fastdiv(g.L[0]), make_fastdiv(g.L[1]), make_fastdiv(g.L[2])};
 #define WMG_DS(R)                                                                                             \
   do {                                                                                                        \
     if (red == 0) k_dslash<R, 0><<<grid, kDslashThreads, 0, s>>>(out, in, b, gauge, g, dv, mass_dev, active, nrhs, nb, r); \
-    else if (red == 1) k_dslash<R, 1><<<grid, kDslashThreads, 0, s>>>(out, in, b, gauge, g, dv, mass_dev, active, nrhs, nb, r); \
-    else k_dslash<R, 2><<<grid, kDslashThreads, 0, s>>>(out, in, b, gauge, g, dv, mass_dev, active, nrhs, nb, r); \
+    else if (red == 1) k_dslash<R, 1><<<gridr, kDslashThreads, 0, s>>>(out, in, b, gauge, g, dv, mass_dev, active, nrhs, nbr, r); \
+    else k_dslash<R, 2><<<gridr, kDslashThreads, 0, s>>>(out, in, b, gauge, g, dv, mass_dev, active, nrhs, nbr, r); \
   } while (0)
   if (prec == WMG_PREC_DOUBLE) WMG_DS(double);
   else WMG_DS(float);

@@ -278,13 +278,28 @@ WMG_D double cta_sum_strided(const volatile double* p, int count, int stride, do
 
 // Sums of nval rows of partials at once: value i is sum_b p[i * istride + b * bstride], b < count.
 // Warp w takes values w, w + nwarps, ...; lane l adds b = l, l + 32, ... in order, then a fixed
-// xor-shuffle tree; lane 0 hands (i, sum) to `store`.  The order depends on count only.
+// xor-shuffle tree; lane 0 hands (i, sum) to `store`.  The order depends on count only.  The
+// partials come from other CTAs (written before their counter increment): they are read from
+// L2 (ld.global.cg), eight per lane in flight before the additions, in the same order.
+constexpr int kSumBatch = 8;
 template <typename F>
-WMG_D void cta_multi_sum(const volatile double* p, int nval, size_t istride, int count, size_t bstride, F store) {
+WMG_D void cta_multi_sum(const volatile double* pv, int nval, size_t istride, int count, size_t bstride, F store) {
+  const double* p = const_cast<const double*>(pv);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = warp; i < nval; i += nw) {
     double s = 0.0;
-    for (int b = lane; b < count; b += 32) s += p[i * istride + (size_t)b * bstride];
+    const double* row = p + i * istride;
+    for (int b0 = lane; b0 < count; b0 += 32 * kSumBatch) {
+      double t[kSumBatch];
+#pragma unroll
+      for (int u = 0; u < kSumBatch; ++u) {
+        const int b = b0 + 32 * u;
+        t[u] = b < count ? __ldcg(row + (size_t)b * bstride) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kSumBatch; ++u)
+        if (b0 + 32 * u < count) s += t[u];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) store(i, s);
