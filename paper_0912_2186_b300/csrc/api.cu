@@ -170,7 +170,7 @@ void wmg_default_params(wmg_params* p) {
   p->gcr_restart = 16;
   p->cycle_gamma = 1;
   p->tol = 1e-10;
-  p->coarse_tol = 2e-2;
+  p->coarse_tol = 5e-2;
   p->coarse_maxit = 2000;
   p->max_iter = 1000;
   p->prec_sloppy = WMG_PREC_SINGLE;
