@@ -227,9 +227,10 @@ def test_autotuned_coarse_stencil(W):
 
 
 def test_persistent_coarse_cgnr(W):
-    """coarse_persistent = 1: the coarsest CGNR as one cooperative kernel; every solution meets the
-    1e-10 true residual, and a right-hand side's result is the same alone and in its batch."""
-    ctx, U, p = _ctx(W, CFG1, 1, coarse_persistent=1)
+    """coarse_persistent = 1 (with the plain CGNR, coarse_eo = 0): the coarsest CGNR as one
+    cooperative kernel; every solution meets the 1e-10 true residual, and a right-hand side's
+    result is the same alone and in its batch."""
+    ctx, U, p = _ctx(W, CFG1, 1, coarse_persistent=1, coarse_eo=0)
     b = synth.gaussian_spinors(CFG1["dims"], 3, 19)
     x = dev(np.zeros_like(b))
     st, info = ctx.solve(dev(b), x, 3)
