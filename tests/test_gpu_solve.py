@@ -115,8 +115,9 @@ def test_three_level_solve(W):
 
 
 def test_tcgen05_coarse_solve(W):
-    """The mixed-precision solve with the coarse stencil on tcgen05 tensor cores."""
-    ctx, U, p = _ctx(W, CFG1, 1, coarse_tc=2)
+    """The mixed-precision solve with the coarse stencil on tcgen05 tensor cores (plain coarsest
+    CGNR: the even-odd passes use the mma.sync stencil)."""
+    ctx, U, p = _ctx(W, CFG1, 1, coarse_tc=2, coarse_eo=0)
     b = synth.gaussian_spinors(CFG1["dims"], 3, 16)
     x = dev(np.zeros_like(b))
     st, info = ctx.solve(dev(b), x, 3)
