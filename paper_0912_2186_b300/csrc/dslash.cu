@@ -74,7 +74,7 @@ WMG_D void site_coords_fast(const Geom& g, const DslashDiv& d, int v, int c[4]) 
 // added in that order), so that the CTAs publishing partial sums (a fence and an atomic each)
 // are SPB times fewer; the partition depends on the volume only.  (The FP64 kernel runs one
 // CTA per SM and keeps one block per CTA.)
-template <typename R, int RED> constexpr int dslash_spb() { return RED > 0 && sizeof(R) == 4 ? 8 : 1; }
+template <typename R, int RED> constexpr int dslash_spb() { return RED > 0 && sizeof(R) == 4 ? 4 : 1; }
 
 template <typename R, int RED>
 __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(void* __restrict__ out,
