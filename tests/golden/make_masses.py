@@ -40,6 +40,7 @@ def main():
     ap.add_argument("--dir", default=os.path.join(HERE, ".masses_stage"), help="stage directory")
     ap.add_argument("--m", type=float, help="mass of the setup / of an evaluation")
     ap.add_argument("--ratio", type=float, help="target ratio of a search")
+    ap.add_argument("--rtol", type=float, default=0.05, help="accepted relative error of the ratio (search)")
     a = ap.parse_args()
     dims = tuple(int(v) for v in a.dims.split(","))
     out = a.out or default_out(dims, a.eps)
@@ -64,12 +65,17 @@ def main():
         for f in sorted(glob.glob(os.path.join(a.dir, "eval_*.json"))):
             with open(f) as fh:
                 evals.append(json.load(fh))
+        ratios_found = {}
+        for k, m in found.items():
+            lam = [e["lambda"] for e in evals if e["m"] == m]
+            ratios_found[k] = lam[0] / m ** 2 if lam else None
         rec = {"dims": list(dims), "eps": a.eps, "gauge_seed": a.seed,
                "definition": "lambda_min(D^dag D) = ratio * m^2 (free-field lambda_min at mass m)",
                "masses": {k: found[k] for k in sorted(found, key=float, reverse=True)},
+               "ratio_at_mass": {k: ratios_found[k] for k in sorted(found, key=float, reverse=True)},
                "evaluations": sorted([[e["m"], e["lambda"], e["lambda"] / e["m"] ** 2] for e in evals]),
                "method": "oracle MG-GCR solves (tol 1e-5) inside Lanczos on (D^dag D)^-1 (eig tol 1e-2); "
-                         "secant on sqrt(lambda_min); ratio within 5 %"}
+                         "secant on sqrt(lambda_min); the ratio reached at each mass is in ratio_at_mass"}
         with open(out, "w") as fh:
             json.dump(rec, fh, indent=1)
         print(rec["masses"])
@@ -92,7 +98,7 @@ def main():
             e = json.load(fh)
         evals.append((e["m"], e["lambda"]))
     t = time.time()
-    m, _ = masses.search_ratio(H, a.ratio, evals, v0, log=log, on_eval=save_eval)
+    m, _ = masses.search_ratio(H, a.ratio, evals, v0, rtol=a.rtol, log=log, on_eval=save_eval)
     with open(os.path.join(a.dir, f"found_{a.ratio:.0e}.json"), "w") as fh:
         json.dump({f"{a.ratio:.0e}": m}, fh)
     log(f"ratio {a.ratio:.0e}: m = {m:.6f} ({time.time() - t:.0f} s)")
