@@ -166,7 +166,9 @@ def run_reference(args, w):
         return
     try:
         with open(OPCOUNTS) as f:
-            counts = json.load(f)["counts"]
+            rec = json.load(f)
+        counts = rec["counts"]
+        counts_at = f"{rec.get('masses')} ({rec.get('masses_source', 'unknown source')})"
     except OSError:
         print(json.dumps({"impl": "reference", "unavailable": "operation counts of the job not recorded yet"}))
         return
@@ -178,7 +180,7 @@ def run_reference(args, w):
     v = statistics.mean(vals)
     sample = ("FP64 oracle on the host: C restatement of D, numpy coarse stencil, restrict, prolong, block "
               "Gram-Schmidt and one Galerkin column timed on this workload's shapes, times the operation counts "
-              "of one step (vector updates not included)")
+              f"of one step recorded by the GPU arm at masses {counts_at} (vector updates not included)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "higher_is_better": False,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
