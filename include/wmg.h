@@ -221,6 +221,25 @@ wmg_status wmg_unpack_spinor(wmg_ctx* ctx, int prec, const void* native_dev, dou
  * in FP32 arithmetic, the result rounded to FP16 the same way and widened into out. */
 wmg_status wmg_apply_D(wmg_ctx* ctx, int prec, const void* in_dev, void* out_dev, int nrhs);
 
+/* out = K(in): one application of the multigrid preconditioner of the fine level (Sec. 3: the
+ * cycle the outer GCR applies each iteration) to nrhs native fine spinors of precision prec
+ * (DOUBLE or SINGLE) at the context's mass: restrict with P^dag, the coarse solve (CG on the
+ * normal equations on the coarsest level, to coarse_tol) or, with 3 levels, the next cycle
+ * (cycle_gamma times at the middle level: the W-cycle for 2), prolong with P, then nu_post MR
+ * steps on D out = in from the prolonged correction (post-smoothing only).  SINGLE uses the
+ * hierarchy's FP32 operators (and its tensor-core coarse stencil, FP16 null vectors or FP16
+ * smoother storage where configured); DOUBLE its FP64 operators.  in and out must not overlap.
+ * WMG_ESTATE without a hierarchy, or for DOUBLE / SINGLE when only FP16 fine null vectors are
+ * kept. */
+wmg_status wmg_apply_cycle(wmg_ctx* ctx, int prec, const void* in_dev, void* out_dev, int nrhs);
+/* The smoother of the cycle on its own (Sec. 3, "post smoothing iterations"): nu steps of
+ * minimal-residual relaxation of D x = b on the fine level for nrhs native fine spinors of
+ * precision prec, in place on x (its contents are the initial guess): r = b - D x, then nu
+ * times q = D r, alpha = <q, r> / <q, q>, x += alpha r, r -= alpha q.  With prec SINGLE and a
+ * hierarchy set up with prec_smoother HALF, r and q are stored in FP16 as in the cycle.  b and
+ * x must not overlap. */
+wmg_status wmg_smooth(wmg_ctx* ctx, int prec, const void* b_dev, void* x_dev, int nrhs, int nu);
+
 /* coarse = P^dag fine (Sec. 2, R = P^dag): level 0 maps native fine spinors to
  * level-1 coarse vectors, level 1 maps level-1 to level-2 coarse vectors.  prec is
  * the precision of both buffers (the hierarchy must hold P in it). */
@@ -291,15 +310,17 @@ wmg_status wmg_residual_noalloc(wmg_ctx* ctx, int prec, const void* b_dev, const
  * When enabled, every launch of the solver's kernels is bracketed by two CUDA events on
  * the context's stream (this adds host work per launch; leave it off for timing runs).
  * Classes: 0 sloppy fine dslash, 1 FP64 fine dslash (true residuals), 2 coarse stencil,
- * 3 restrict, 4 prolong, 5 vector updates and reductions, 6 setup (Gram-Schmidt and
- * Galerkin construction), 7 coarsest solves run as one persistent kernel (stencil applications
- * and their vector updates together; units = right-hand sides solved).
+ * 3 restrict, 4 prolong, 5 vector updates and reductions on the fine level, 6 setup
+ * (Gram-Schmidt and Galerkin construction), 7 coarsest solves run as one persistent kernel
+ * (stencil applications and their vector updates together; units = right-hand sides solved),
+ * 8 vector updates and reductions on the coarse levels (CG iterations, coarse smoothers).
  * wmg_profile_enable(ctx, 1) resets the counters. */
 wmg_status wmg_profile_enable(wmg_ctx* ctx, int on);
 /* Totals of class cls since the last enable: kernel milliseconds, launches (or launch
  * groups), the algorithmic bytes those launches must move (compulsory reads + writes:
- * operator / link / P data once, each input and output vector once; 0 for class 5, 6)
- * and the right-hand sides they processed (operator applications).  Synchronises. */
+ * operator / link / P data once, each input and output vector once per pass a kernel makes over
+ * it; 0 for class 6) and the right-hand sides they processed (operator applications).
+ * Synchronises. */
 wmg_status wmg_profile_get(wmg_ctx* ctx, int cls, double* ms, long long* launches, double* bytes, double* units);
 /* Total number of CUDA kernels this library has launched in this process (all contexts). */
 wmg_status wmg_launch_count(long long* n);

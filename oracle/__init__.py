@@ -20,9 +20,9 @@ paper computes:
                  S = A_ee - A_eo A_oo^-1 A_oe, its adjoint, the prepared right-hand side
                  and the reconstruction of the odd sites.
 
-Parity status per function is stated in each module header.  The adaptive setup
-(``solvers.adaptive_setup``) is "parity unpinned" at the level of individual vectors:
-near-null vectors have no closed form; it is pinned only indirectly (residual
-decrease, span and orthonormality invariants).
+Parity status per function is stated in each module header.  Near-null vectors have
+no closed form, so the adaptive setup (``solvers.setup_level``) is pinned as an
+algorithm: against a dense restatement of its steps made of library routines on a tiny
+lattice, plus the indirect invariants (residual decrease, span, orthonormality).
 """
 from . import dirac, eo, mg, solvers  # noqa: F401

@@ -36,9 +36,15 @@ the vectors, repeat).  The details the paper leaves open are read as follows:
 Pins (tests/test_oracle_solvers.py): MR residual non-increasing and one-step exact
 for A = I; CGNR against a dense solve; FGCR with the exact inverse as
 preconditioner converges in one iteration, residual norms non-increasing, solution
-against dense LU; the full MG-GCR solution against dense LU on a tiny lattice.
-The adaptive setup is "parity unpinned" at the vector level (no closed form);
-pinned indirectly by the decrease of |A psi_k| / |psi_k| over passes.
+against dense LU; the full MG-GCR solution against dense LU on a tiny lattice; the
+cycle (2 levels with nu = 0, 1, 2, 4; 3 levels, V and W) against its dense closed form
+with an exact coarsest solve (the Petrov-Galerkin correction P (P^dag D P)^-1 P^dag r,
+then nu minimal-residual steps each solved as a one-column least-squares problem); the
+adaptive setup against a dense restatement built from library routines (least-squares
+relaxation steps, Gram-Schmidt as the QR factorisation with a positive diagonal, the
+dense cycle), which a different relax count, smoothing count or per-vector rebuild of
+the basis fails.  Near-null vectors have no closed form: the setup is pinned as an
+algorithm, not by its result.
 """
 from __future__ import annotations
 

@@ -1,5 +1,6 @@
 // The C ABI of libwmg (include/wmg.h): argument checking, memory ownership and sequencing
 // of the driver in solver.cu.
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <random>
@@ -235,6 +236,7 @@ wmg_status wmg_create(wmg_ctx** out, const int dims[4], void* stream) {
   al((void**)&c->d_mask, kMaxRhs * sizeof(int));
   al((void**)&c->d_flag, 4 * sizeof(int));
   al((void**)&c->d_cgint, 2 * kMaxRhs * sizeof(int));
+  al((void**)&c->d_err, sizeof(int));
   al((void**)&c->red_counter, 4 * kMaxRhs * sizeof(unsigned));
   al((void**)&c->res, (size_t)24 * kMaxRhs * 16 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(c->red_counter, 0, 4 * kMaxRhs * sizeof(unsigned));
@@ -242,6 +244,14 @@ wmg_status wmg_create(wmg_ctx** out, const int dims[4], void* stream) {
   if (e == cudaSuccess) e = cudaMemset(c->d_shift[2], 0, kMaxRhs * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pin, 4096 * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pin_i, 4096 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_ring, (size_t)kRingSlots * kRingInts * sizeof(int));
+  for (int k = 0; k < kRingSlots && e == cudaSuccess; ++k)
+    e = cudaEventCreateWithFlags(&c->ring_ev[k], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
+  for (int r = 0; r < kMaxRhs; ++r) {
+    c->mass_up[r] = std::nan("");
+    for (int l = 0; l < WMG_MAX_LEVELS; ++l) c->shift_up[l][r] = std::nan("");
+  }
   if (e == cudaSuccess) e = cudaMalloc(&c->gauge[0], (size_t)c->fine.V * 4 * 6 * sizeof(cd));
   if (e == cudaSuccess) e = cudaMalloc(&c->gauge[1], (size_t)c->fine.V * 4 * 6 * sizeof(cf));
   if (e != cudaSuccess) {
@@ -263,11 +273,14 @@ wmg_status wmg_destroy(wmg_ctx* c) {
   for (auto& kv : c->ws) cudaFree(kv.second.first);
   c->ws.clear();
   void* ptrs[] = {c->d_mass, c->d_shift[1], c->d_shift[2], c->d_active, c->d_mask, c->d_flag, c->d_cgint,
-                  c->red_counter, c->res, c->red_partial, c->gauge[0], c->gauge[1]};
+                  c->red_counter, c->res, c->red_partial, c->gauge[0], c->gauge[1], c->d_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pin) cudaFreeHost(c->h_pin);
   if (c->h_pin_i) cudaFreeHost(c->h_pin_i);
+  if (c->h_ring) cudaFreeHost(c->h_ring);
+  for (int k = 0; k < kRingSlots; ++k)
+    if (c->ring_ev[k]) cudaEventDestroy(c->ring_ev[k]);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;
   return WMG_OK;
@@ -508,6 +521,31 @@ wmg_status wmg_apply_D(wmg_ctx* c, int prec, const void* in, void* out, int nrhs
   return check(c, "apply_D");
 }
 
+wmg_status wmg_apply_cycle(wmg_ctx* c, int prec, const void* in, void* out, int nrhs) {
+  if (!c || !in || !out || nrhs < 1 || nrhs > kMaxRhs || in == out || !prec_ok(prec)) return WMG_EINVAL;
+  if (!c->have_hier) return WMG_ESTATE;
+  if (!c->L[0].P[prec]) {
+    c->err = "apply_cycle: the hierarchy keeps only FP16 null vectors on the fine level";
+    return WMG_ESTATE;
+  }
+  TRY(ensure_reductions(c, nrhs));
+  TRY(set_rhs_scalars(c, nullptr, nrhs));
+  c->n_active = nrhs;
+  CU(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  TRY(cycle(c, 0, c->nlev - 1, prec, in, out, nrhs, nullptr));
+  return check(c, "apply_cycle");
+}
+
+wmg_status wmg_smooth(wmg_ctx* c, int prec, const void* b, void* x, int nrhs, int nu) {
+  if (!c || !b || !x || nrhs < 1 || nrhs > kMaxRhs || b == x || nu < 0 || !prec_ok(prec)) return WMG_EINVAL;
+  if (!c->have_gauge) return WMG_ESTATE;
+  TRY(ensure_reductions(c, nrhs));
+  TRY(set_rhs_scalars(c, nullptr, nrhs));
+  c->n_active = nrhs;
+  TRY(mr(c, 0, prec, x, b, nrhs, nu, nullptr));
+  return check(c, "smooth");
+}
+
 wmg_status wmg_restrict(wmg_ctx* c, int level, int prec, const void* fine, void* coarse, int nrhs) {
   if (!c || !fine || !coarse || nrhs < 1 || !(prec_ok(prec) || prec == WMG_PREC_HALF)) return WMG_EINVAL;
   if (level < 0 || level + 1 >= c->nlev || !c->L[level + 1].A[0]) return WMG_ESTATE;
@@ -553,10 +591,10 @@ wmg_status wmg_apply_coarse(wmg_ctx* c, int level, int prec, int dagger, const v
   const LevelData& L = c->L[level];
   if (prec == WMG_PREC_HALF && L.A05)
     coarse_apply_tc05(L.A05, L.sA, L.g, L.ndof, in, out, nrhs, c->d_shift[level], dagger != 0, nullptr, nullptr,
-                      c->stream);
+                      c->stream, c->d_err);
   else if (prec == WMG_PREC_HALF)
     coarse_apply_mma(L.A16, L.sA, L.g, L.ndof, in, out, nrhs, c->d_shift[level], dagger != 0, nullptr, nullptr,
-                     c->stream);
+                     c->stream, nullptr, c->d_err);
   else
     coarse_apply(prec, L.A[prec], L.g, L.ndof, in, out, nrhs, c->d_shift[level], dagger != 0, nullptr, nullptr,
                  c->stream);

@@ -316,6 +316,52 @@ __global__ void k_gcr_xupdate(const void* Z, size_t slot_stride, int K, void* x_
   }
 }
 
+// Back-substitution of the deferred GCR update (see kernels.h): CTA r stages beta_jq (j < q < K),
+// gamma_q and alpha_q in shared memory; lane j of warp 0 holds the running right-hand side of
+// row j, and for q = K-1 .. 0 lane q divides by gamma_q and broadcasts xi_q, which rows j < q
+// subtract (column-oriented back-substitution).
+__global__ void __launch_bounds__(128) k_gcr_backsolve(const double* __restrict__ hist, size_t hstride, size_t kcoef,
+                                                       int K, int nslots, const int* __restrict__ ints,
+                                                       double* __restrict__ xi) {
+  const int r = blockIdx.x;
+  if (!ints[r]) return;
+  const int from = ints[nslots + r];
+  __shared__ cd beta[kMaxKrylov][kMaxKrylov];  // beta[q][j] = <W_j, w_q>, j < q
+  __shared__ double gam[kMaxKrylov];
+  __shared__ cd alpha[kMaxKrylov];
+  for (int t = threadIdx.x; t < K * K; t += blockDim.x) {
+    const int q = t / K, j = t % K;
+    if (j < q) {
+      const double* b = hist + (size_t)q * hstride + ((size_t)(j / kDotChunk) * nslots + r) * 2 * kDotChunk +
+                        2 * (j % kDotChunk);
+      beta[q][j] = cd{b[0], b[1]};
+    }
+  }
+  if (threadIdx.x < K) {
+    const int q = threadIdx.x;
+    const double* hw = hist + (size_t)q * hstride + kcoef + 3 * (size_t)r;
+    const double g = hw[0] > 0.0 ? sqrt(hw[0]) : 0.0;
+    gam[q] = g;
+    alpha[q] = (q >= from && g > 0.0) ? cd{hw[1] / g, hw[2] / g} : cd{0.0, 0.0};
+  }
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const int j = threadIdx.x;
+  cd acc = j < K ? alpha[j] : cd{0.0, 0.0}, mine{0.0, 0.0};
+  for (int q = K - 1; q >= 0; --q) {
+    cd x{0.0, 0.0};
+    if (j == q && gam[q] > 0.0) x = cd{acc.re / gam[q], acc.im / gam[q]};
+    x.re = __shfl_sync(0xffffffffu, x.re, q);
+    x.im = __shfl_sync(0xffffffffu, x.im, q);
+    if (j == q) mine = x;
+    if (j < q) acc -= beta[q][j] * x;
+  }
+  if (j < K) {
+    xi[((size_t)r * kMaxKrylov + j) * 2] = mine.re;
+    xi[((size_t)r * kMaxKrylov + j) * 2 + 1] = mine.im;
+  }
+}
+
 // x64 += x (sloppy), x = 0, for the masked right-hand sides (reliable update)
 template <typename R>
 __global__ void k_fold(double* x64, void* x_, size_t n, const int* mask) {
@@ -445,6 +491,12 @@ void gcr_xupdate(int prec, const void* Z, size_t slot_stride, int K, void* x, co
   count_launch();
   dim3 g(blas_blocks(n), nrhs);
   WMG_BY_PREC(prec, k_gcr_xupdate, <<<g, kBlasThreads, 0, s>>>(Z, slot_stride, K, x, xi, n, mask));
+}
+
+void gcr_backsolve(const double* hist, size_t hstride, size_t kcoef, int K, int nslots, const int* ints, double* xi,
+                   cudaStream_t s) {
+  count_launch();
+  k_gcr_backsolve<<<nslots, 128, 0, s>>>(hist, hstride, kcoef, K, nslots, ints, xi);
 }
 
 void blas_fold(int prec, double* x64, void* x, size_t n, int nrhs, const int* mask, cudaStream_t s) {

@@ -99,7 +99,8 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
                                                                      const cf* __restrict__ in, cf* __restrict__ out,
                                                                      int nrhs, const double* __restrict__ shift,
                                                                      int dagger, const int* __restrict__ active,
-                                                                     RedBuf rb, int want_norm, StencilEo eo) {
+                                                                     RedBuf rb, int want_norm, StencilEo eo,
+                                                                     int* __restrict__ err) {
   constexpr int n = NDOF, N = n / 2, K = 9 * n, KP = K + kKPad;
   constexpr int MT = n / 16, KS = K / 16;
   constexpr int R = 8 * NT, COLS = 2 * R;
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
   bool ready = true;
   if (mma_warp) {
     ready = mbar_wait_bounded(smem_addr(&mbar[m]), 0, kMmaSpinLimit);
-    if (!ready && lane == 0) atomicExch(&g_mma_error, 1);
+    if (!ready && lane == 0) atomicExch(err ? err : &g_mma_error, 1);
   }
   if (mma_warp && ready) {
     const uint4* Ar = As + (size_t)(0 * MT + m) * KS * 32 + lane;
@@ -333,7 +334,7 @@ void stencil_to_mma(int prec, const void* A, int Vc, int n, float* scale, void* 
 template <int NDOF, int NT>
 static void launch_mma(const void* A16, const float* sA, const Geom& g, const void* in, void* out, int nrhs,
                        const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s,
-                       const StencilEo& eo) {
+                       const StencilEo& eo, int* err) {
   constexpr int R = 8 * NT;
   const size_t smem = (size_t)2 * (NDOF / 16) * (9 * NDOF / 16) * 512 +
                       (size_t)2 * R * (9 * NDOF + kKPad) * sizeof(__half) + R * sizeof(float);
@@ -346,28 +347,28 @@ static void launch_mma(const void* A16, const float* sA, const Geom& g, const vo
   RedBuf r = rb ? *rb : RedBuf{nullptr, nullptr, nullptr};
   k_coarse_apply_mma<NDOF, NT><<<grid, kMmaThreads, smem, s>>>((const uint4*)A16, sA, g, (const cf*)in, (cf*)out,
                                                                nrhs, shift, dagger ? 1 : 0, active, r, rb ? 1 : 0,
-                                                               eo);
+                                                               eo, err);
 }
 
 template <int NDOF>
 static void launch_mma_n(const void* A16, const float* sA, const Geom& g, const void* in, void* out, int nrhs,
                          const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s,
-                         const StencilEo& eo) {
-  if (nrhs <= 8) launch_mma<NDOF, 1>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s, eo);
-  else launch_mma<NDOF, 2>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s, eo);
+                         const StencilEo& eo, int* err) {
+  if (nrhs <= 8) launch_mma<NDOF, 1>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s, eo, err);
+  else launch_mma<NDOF, 2>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s, eo, err);
 }
 
 // n = 2N in {16, 32, 48, 64} (the tensor-core copy exists only for those)
 void coarse_apply_mma(const void* A16, const float* sA, const Geom& g, int n, const void* in, void* out, int nrhs,
                       const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s,
-                      const StencilEo* eo_opt) {
+                      const StencilEo* eo_opt, int* err) {
   count_launch();
   const StencilEo eo = eo_opt ? *eo_opt : StencilEo{};
   switch (n) {
-    case 16: launch_mma_n<16>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s, eo); break;
-    case 32: launch_mma_n<32>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s, eo); break;
-    case 48: launch_mma_n<48>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s, eo); break;
-    default: launch_mma_n<64>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s, eo); break;
+    case 16: launch_mma_n<16>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s, eo, err); break;
+    case 32: launch_mma_n<32>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s, eo, err); break;
+    case 48: launch_mma_n<48>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s, eo, err); break;
+    default: launch_mma_n<64>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s, eo, err); break;
   }
 }
 

@@ -91,7 +91,8 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc05(const uint4* __restri
                                                            Geom g, int n, const cf* __restrict__ in,
                                                            cf* __restrict__ out, int nrhs,
                                                            const double* __restrict__ shift, int dagger,
-                                                           const int* __restrict__ active, RedBuf rb, int want_norm) {
+                                                           const int* __restrict__ active, RedBuf rb, int want_norm,
+                                                           int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   const int K = 9 * n, KG = K / 8;
   const uint32_t SBO = (uint32_t)KG * 128;  // bytes between row groups
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(128) k_coarse_apply_tc05(const uint4* __restri
   }
   bool ok = mbar_wait(smem_u32(&mbar), 0);
   if (!ok) {
-    if (threadIdx.x == 0) atomicExch(&g_tc05_error, 1);
+    if (threadIdx.x == 0) atomicExch(err ? err : &g_tc05_error, 1);
     mbar_wait(smem_u32(&mbar), 0);  // give the issued MMAs a second bounded chance to drain
   }
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -267,7 +268,8 @@ void stencil_to_tc05(int prec, const void* A, int Vc, int n, const float* scale,
 bool coarse_tc05_supported(int n) { return n == 48 || n == 64 || n == 32 || n == 16; }
 
 void coarse_apply_tc05(const void* A16, const float* sA, const Geom& g, int n, const void* in, void* out, int nrhs,
-                       const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s) {
+                       const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s,
+                       int* err) {
   count_launch();
   const size_t SBO = (size_t)(9 * n / 8) * 128;
   const size_t smem = (size_t)(kTcM / 8) * SBO + (size_t)(kTcN / 8) * SBO + (size_t)kTcM * 33 * sizeof(float) + 1024;
@@ -279,7 +281,7 @@ void coarse_apply_tc05(const void* A16, const float* sA, const Geom& g, int n, c
   dim3 grid(g.V, (nrhs + kTcRhs - 1) / kTcRhs);
   RedBuf r = rb ? *rb : RedBuf{nullptr, nullptr, nullptr};
   k_coarse_apply_tc05<<<grid, 128, smem, s>>>((const uint4*)A16, sA, g, n, (const cf*)in, (cf*)out, nrhs, shift,
-                                              dagger ? 1 : 0, active, r, rb ? 1 : 0);
+                                              dagger ? 1 : 0, active, r, rb ? 1 : 0, err);
 }
 
 int coarse_tc05_error() {

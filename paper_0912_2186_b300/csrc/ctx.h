@@ -10,7 +10,12 @@ namespace wmg {
 
 // kernel classes timed by the optional CUDA-event instrumentation (wmg_profile_*)
 enum { PROF_DSLASH_LO = 0, PROF_DSLASH_64, PROF_COARSE, PROF_RESTRICT, PROF_PROLONG, PROF_BLAS, PROF_SETUP,
-       PROF_CGNR, PROF_NCLASS };
+       PROF_CGNR, PROF_BLAS_COARSE, PROF_NCLASS };
+
+// pinned staging ring for small asynchronous host-to-device uploads (flags, masks): a slot is
+// reused only after the copy that last read it has completed (one event per slot)
+constexpr int kRingSlots = 8;
+constexpr int kRingInts = 256;
 
 struct ProfRec {
   cudaEvent_t a, b;
@@ -78,6 +83,15 @@ struct wmg_ctx {
   int cg_chunk = 2;                            // CGNR iterations between convergence checks (even)
   bool use_fused_galerkin = true;              // fused fine-level Galerkin kernel
   int* d_pcg_err = nullptr;                    // sticky error flag of the persistent CGNR (per solve)
+  int* d_err = nullptr;                        // error word of the tensor-core stencils' bounded waits
+                                               // (cleared at the start of each solve)
+  // values last uploaded to d_mass / d_shift (NaN = unknown), so that an unchanged set is not
+  // uploaded again
+  double mass_up[wmg::kMaxRhs];
+  double shift_up[WMG_MAX_LEVELS][wmg::kMaxRhs];
+  int* h_ring = nullptr;                       // pinned [kRingSlots][kRingInts]
+  cudaEvent_t ring_ev[wmg::kRingSlots] = {};
+  int ring_pos = 0;
   std::map<std::string, std::pair<cudaGraphExec_t, long long>> graphs;  // + launches per replay
   int n_active = 0;                            // active right-hand sides of the current solve
   float tune_ms[WMG_MAX_LEVELS][3] = {};       // autotuner: ms per 12-rhs launch of each stencil impl

@@ -86,6 +86,14 @@ void gcr_update(int prec, void* x, void* r, void* w, void* z, const double* wred
 // alpha = <w,r>/|w|^2, r -= alpha w, w /= |w|; red = |r|^2 (solution update deferred)
 void gcr_update_r(int prec, void* r, void* w, const double* wred, size_t n, int nrhs, const int* active,
                   const RedBuf& rb, cudaStream_t s);
+// Deferred solution update of the flexible GCR: for each right-hand side r with ints[r] != 0,
+// solve Gamma xi = alpha by back-substitution (Gamma upper triangular: gamma_q = |w_q| before
+// normalisation on the diagonal, beta_jq = <W_j, w_q> above it; alpha_q = <W_q, r_q> for q >=
+// ints[nslots + r], 0 below) from the per-iteration history hist + q hstride = {multidot
+// coefficients as gcr_multidot writes them (kcoef doubles), then |w|^2, Re, Im <w, r> per rhs};
+// xi: complex FP64, kMaxKrylov per rhs.  One warp per right-hand side.
+void gcr_backsolve(const double* hist, size_t hstride, size_t kcoef, int K, int nslots, const int* ints, double* xi,
+                   cudaStream_t s);
 // x += sum_{j<K} xi[r][j] Z_j (xi complex FP64, kMaxKrylov per rhs) for masked right-hand sides
 void gcr_xupdate(int prec, const void* Z, size_t slot_stride, int K, void* x, const double* xi, size_t n, int nrhs,
                  const int* mask, cudaStream_t s);
@@ -167,13 +175,14 @@ size_t stencil_mma_words(int Vc, int n);  // uint4 words of the fragment-order c
 void stencil_to_mma(int prec, const void* A, int Vc, int n, float* scale, void* out, cudaStream_t s);
 void coarse_apply_mma(const void* A16, const float* sA, const Geom& g, int n, const void* in, void* out, int nrhs,
                       const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s,
-                      const StencilEo* eo = nullptr);
+                      const StencilEo* eo = nullptr, int* err = nullptr);
 // tcgen05 tensor-core copy of a stencil and its application (coarse_tc05.cu)
 size_t stencil_tc05_halves(int Vc, int n);
 bool coarse_tc05_supported(int n);
 void stencil_to_tc05(int prec, const void* A, int Vc, int n, const float* scale, void* out, cudaStream_t s);
 void coarse_apply_tc05(const void* A16, const float* sA, const Geom& g, int n, const void* in, void* out, int nrhs,
-                       const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s);
+                       const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s,
+                       int* err = nullptr);
 // Coarsest CGNR for nrhs <= 16 as one persistent cooperative kernel (FP16 tensor-core stencil
 // with 2N in {16, 32, 48, 64}, FP32 vectors [rhs][site][2N]); false if it cannot run (the caller
 // then uses the multi-kernel CGNR).  r16, p16: cgnr_persistent_copy_bytes each (FP16 copies);
@@ -185,8 +194,10 @@ bool cgnr_persistent(const void* A16, const float* sA, const Geom& g, int n, con
                      void* x, void* r, void* p, void* q, void* z, void* r16, void* p16, float* rsc, float* psc,
                      int nrhs, double tol2, int maxit, const int* active, double* part, unsigned* bar, int* err,
                      int* done_out, int* iters_out, cudaStream_t s);
-int coarse_mma_error();   // 1 if a bounded wait of the mma.sync coarse kernel ever expired (synchronises)
-int coarse_tc05_error();  // 1 if a bounded tcgen05 wait ever expired (synchronises)
+// err (per context) is set to 1 when a bounded wait of a tensor-core stencil expires; without one
+// (err = nullptr) the kernels set a process-wide flag read by these (synchronises)
+int coarse_mma_error();
+int coarse_tc05_error();
 // convert a stencil between precisions
 void stencil_convert(int prec_d, void* dst, int prec_s, const void* src, size_t count, cudaStream_t s);
 

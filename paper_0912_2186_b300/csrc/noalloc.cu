@@ -38,12 +38,18 @@ struct NoallocPtrs {
 NoallocPtrs g_ptrs[kNoallocMaxDevices];
 std::mutex g_ptrs_mutex;
 
-// Device addresses of the static arrays on the current device.  In host code the array
-// names are host-side stand-ins, so the addresses are looked up once per device.
+// Device addresses of the static arrays on the context's device.  In host code the array
+// names are host-side stand-ins, so the addresses are looked up once per device, with that
+// device current; a call from a thread whose current device is not the context's is refused
+// (the lookup and the launch would otherwise use different devices).
 wmg_status noalloc_ptrs(wmg_ctx* c, NoallocPtrs* out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(c, e, "cudaGetDevice");
+  if (dev != c->device) {
+    c->err = "wmg_residual_noalloc: the calling thread's current device is not the context's device";
+    return WMG_EINVAL;
+  }
   if (dev < 0 || dev >= kNoallocMaxDevices) {
     c->err = "wmg_residual_noalloc: device index out of range";
     return WMG_EINVAL;

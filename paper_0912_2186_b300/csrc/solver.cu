@@ -107,24 +107,52 @@ wmg_status ensure_reductions(wmg_ctx* c, int nrhs) {
   return ensure_partials(c, need);
 }
 
-wmg_status set_rhs_scalars(wmg_ctx* c, const double* masses, int nrhs) {
-  for (int r = 0; r < nrhs; ++r) c->h_pin[r] = masses ? masses[r] : c->mass;
-  CU(c, cudaMemcpyAsync(c->d_mass, c->h_pin, nrhs * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  for (int l = 1; l < c->nlev; ++l) {
-    for (int r = 0; r < nrhs; ++r) c->h_pin[kMaxRhs + r] = c->h_shift[r] = (masses ? masses[r] : c->mass) - c->mass_setup;
-    CU(c, cudaMemcpyAsync(c->d_shift[l], c->h_pin + kMaxRhs, nrhs * sizeof(double), cudaMemcpyHostToDevice,
-                          c->stream));
-    CU(c, cudaStreamSynchronize(c->stream));
+// Small asynchronous host-to-device copy through the context's pinned ring (no host
+// synchronisation; the slot is reused only once the copy that last read it has completed).
+wmg_status ring_upload(wmg_ctx* c, void* dst, const void* src, size_t bytes) {
+  if (bytes > kRingInts * sizeof(int)) {
+    c->err = "internal: upload larger than a ring slot";
+    return WMG_EINVAL;
   }
-  CU(c, cudaStreamSynchronize(c->stream));
+  const int k = c->ring_pos;
+  c->ring_pos = (k + 1) % kRingSlots;
+  CU(c, cudaEventSynchronize(c->ring_ev[k]));
+  int* slot = c->h_ring + (size_t)k * kRingInts;
+  std::memcpy(slot, src, bytes);
+  CU(c, cudaMemcpyAsync(dst, slot, bytes, cudaMemcpyHostToDevice, c->stream));
+  CU(c, cudaEventRecord(c->ring_ev[k], c->stream));
+  return WMG_OK;
+}
+
+// Per-rhs Wilson masses (d_mass) and coarse diagonal shifts m_r - m_setup (d_shift[l]); a set
+// equal to the one last uploaded is not uploaded again.
+wmg_status set_rhs_scalars(wmg_ctx* c, const double* masses, int nrhs) {
+  double m[kMaxRhs], sh[kMaxRhs];
+  bool same = true;
+  for (int r = 0; r < nrhs; ++r) {
+    m[r] = masses ? masses[r] : c->mass;
+    same = same && m[r] == c->mass_up[r];
+  }
+  if (!same) {
+    TRY(ring_upload(c, c->d_mass, m, nrhs * sizeof(double)));
+    for (int r = 0; r < nrhs; ++r) c->mass_up[r] = m[r];
+  }
+  for (int l = 1; l < c->nlev; ++l) {
+    same = true;
+    for (int r = 0; r < nrhs; ++r) {
+      sh[r] = c->h_shift[r] = m[r] - c->mass_setup;
+      same = same && sh[r] == c->shift_up[l][r];
+    }
+    if (!same) {
+      TRY(ring_upload(c, c->d_shift[l], sh, nrhs * sizeof(double)));
+      for (int r = 0; r < nrhs; ++r) c->shift_up[l][r] = sh[r];
+    }
+  }
   return WMG_OK;
 }
 
 wmg_status upload_ints(wmg_ctx* c, int* dst, const std::vector<int>& v) {
-  for (size_t i = 0; i < v.size(); ++i) c->h_pin_i[i] = v[i];
-  CU(c, cudaMemcpyAsync(dst, c->h_pin_i, v.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-  CU(c, cudaStreamSynchronize(c->stream));
-  return WMG_OK;
+  return ring_upload(c, dst, v.data(), v.size() * sizeof(int));
 }
 
 wmg_status download(wmg_ctx* c, const double* src, size_t n, std::vector<double>& out) {
@@ -209,6 +237,11 @@ double transfer_bytes(const wmg_ctx* c, int l, int prec, int nact) {
   return (double)L.bk.N * nf * 2.0 * s + (double)nact * (nf + nc) * 2.0 * s;
 }
 static int nact_of(const wmg_ctx* c, const int* active, int nrhs) { return active ? c->n_active : nrhs; }
+// `passes` full reads or writes of nact vectors of level l (vector kernels)
+static double vec_bytes(const wmg_ctx* c, int l, int prec, int nact, double passes) {
+  return passes * (double)nact * (double)c->L[l].nvec_elems() * (prec == WMG_PREC_DOUBLE ? 16.0 : 8.0);
+}
+static int blas_cls(int l) { return l == 0 ? PROF_BLAS : PROF_BLAS_COARSE; }
 
 // ------------------------------------------------------------------------------------
 // operators of a level
@@ -220,9 +253,11 @@ void coarse_op(wmg_ctx* c, int l, int prec, const void* in, void* out, int nrhs,
   int impl = 0;
   if (prec == WMG_PREC_SINGLE) impl = L.impl >= 0 ? L.impl : (L.A05 ? 2 : (L.A16 ? 1 : 0));
   if (impl == 2)
-    coarse_apply_tc05(L.A05, L.sA, L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, active, rb, c->stream);
+    coarse_apply_tc05(L.A05, L.sA, L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, active, rb, c->stream,
+                      c->d_err);
   else if (impl == 1)
-    coarse_apply_mma(L.A16, L.sA, L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, active, rb, c->stream);
+    coarse_apply_mma(L.A16, L.sA, L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, active, rb, c->stream,
+                     nullptr, c->d_err);
   else
     coarse_apply(prec, L.A[prec], L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, active, rb, c->stream);
 }
@@ -296,7 +331,9 @@ static wmg_status mr_half(wmg_ctx* c, void* x, const void* b, int nrhs, int nu, 
       dslash_h(1, q, (float*)qn, r, (const float*)rn, nullptr, c->gauge[1], c->fine, c->d_mass, active, nrhs, 2, &rb,
                c->stream);
     }
-    ProfScope ps(c, PROF_BLAS, 0);
+    // x read + written (FP32), r16 read (+ written), q16 read when r is updated
+    const double ub = (double)na * V * (192.0 + (i + 1 < nu ? 3.0 * 52.0 : 52.0));
+    ProfScope ps(c, PROF_BLAS, ub, na);
     mr_update_h(x, r, (float*)rn, q, (const float*)qn, V, nrhs, rb.result, active, i + 1 < nu, c->stream);
   }
   return check(c, "mr (FP16 storage)");
@@ -318,6 +355,7 @@ wmg_status mr(wmg_ctx* c, int l, int prec, void* x, const void* b, int nrhs, int
     dslash(prec, r, x, b, c->gauge[prec], c->fine, c->d_mass, active, nrhs, 0, nullptr, c->stream);
   } else {
     level_apply(c, l, prec, x, r, nrhs, active, 0, nullptr);
+    ProfScope ps(c, blas_cls(l), vec_bytes(c, l, prec, na, 3), na);
     blas_xmy(prec, b, r, n, nrhs, c->stream);
   }
   for (int i = 0; i < nu; ++i) {
@@ -326,10 +364,11 @@ wmg_status mr(wmg_ctx* c, int l, int prec, void* x, const void* b, int nrhs, int
       dslash(prec, q, r, nullptr, c->gauge[prec], c->fine, c->d_mass, active, nrhs, 2, &rb, c->stream);
     } else {
       level_apply(c, l, prec, r, q, nrhs, active, 0, nullptr);
-      ProfScope ps(c, PROF_BLAS, 0);
+      ProfScope ps(c, blas_cls(l), vec_bytes(c, l, prec, na, 2), na);
       blas_dot_norm(prec, q, r, n, nrhs, rb, c->stream);
     }
-    ProfScope ps(c, PROF_BLAS, 0);
+    // x read + written, r read (+ written), q read when r is updated
+    ProfScope ps(c, blas_cls(l), vec_bytes(c, l, prec, na, i + 1 < nu ? 5 : 3), na);
     blas_mr_update(prec, x, r, q, n, nrhs, rb.result, i + 1 < nu, active, c->stream);  // last r unused
   }
   return check(c, "mr");
@@ -464,7 +503,8 @@ static void eo_stencil(wmg_ctx* c, int l, int prec, const void* in, void* out, i
                        const StencilEo& eo, const RedBuf* rb) {
   const LevelData& L = c->L[l];
   if (eo_mma(c, l, prec))
-    coarse_apply_mma(L.A16, L.sA, L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, nullptr, rb, c->stream, &eo);
+    coarse_apply_mma(L.A16, L.sA, L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, nullptr, rb, c->stream, &eo,
+                     c->d_err);
   else
     coarse_apply(prec, L.A[prec], L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, nullptr, rb, c->stream, &eo);
 }
@@ -607,7 +647,7 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
       op(p, q, false, &rqq);
     }
     {
-      ProfScope ps(c, PROF_BLAS, 0);
+      ProfScope ps(c, PROF_BLAS_COARSE, vec_bytes(c, l, prec, nrhs, 6), nrhs);  // x, r read + written; p, q read
       cg_update(prec, x, r, p, q, n, nrhs, cg, parity, rrr, s);
     }
     RedBuf rzz{c->red_partial, c->red_counter, cg.zz + (1 - parity) * nrhs};
@@ -616,7 +656,7 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
       op(r, z, true, &rzz);
     }
     {
-      ProfScope ps(c, PROF_BLAS, 0);
+      ProfScope ps(c, PROF_BLAS_COARSE, vec_bytes(c, l, prec, nrhs, 3), nrhs);  // p read + written, z read
       cg_xpay(prec, p, z, n, nrhs, cg, parity, s);
     }
   };
@@ -888,53 +928,37 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
   // with A Z_k = sum_{j<k} beta_jk W_j + gamma_k W_k (W orthonormal) and alpha_k = <W_k, r>, the
   // increment x += sum_k xi_k Z_k solves Gamma xi = alpha (Gamma upper triangular, diagonal
   // gamma_k, above it beta_jk).  The coefficients of every iteration of the cycle are copied on
-  // the device into a history; at a reliable update, a restart or the end, the host solves for
-  // xi over the iterations not yet folded in (alpha of earlier ones set to 0).
+  // the device into a history; at a reliable update, a restart or the end, a kernel solves for
+  // xi over the iterations not yet folded in (alpha of earlier ones set to 0) and the directions
+  // are combined into the iterate, all on the device.
   const size_t kcoef = (size_t)((kMaxKrylov + kDotChunk - 1) / kDotChunk) * nslots * 2 * kDotChunk;
   const size_t hstride = kcoef + 3 * (size_t)nslots;
   void *hist, *xi_dev, *xmask_dev;
   TRY(ws_get(c, "gcr_hist", hstride * m * sizeof(double), &hist));
   TRY(ws_get(c, "gcr_xi", (size_t)nslots * kMaxKrylov * 2 * sizeof(double), &xi_dev));
-  TRY(ws_get(c, "gcr_xmask", (size_t)nslots * sizeof(int), &xmask_dev));
+  TRY(ws_get(c, "gcr_xmask", (size_t)2 * nslots * sizeof(int), &xmask_dev));
   std::vector<int> fold_from(nslots, 0);
-  std::vector<double> hh, xi_h;
   auto xupdate = [&](const std::vector<int>& sel, int K) -> wmg_status {
-    std::vector<int> mask(nslots, 0);
+    std::vector<int> up(2 * (size_t)nslots, 0);  // mask, then the first iteration to fold per rhs
     bool any = false;
-    for (int r = 0; r < nslots; ++r)
-      if (sel[r] && fold_from[r] < K) mask[r] = 1, any = true;
-    if (!any || K == 0) return WMG_OK;
-    hh.resize(hstride * K);
-    CU(c, cudaMemcpyAsync(hh.data(), hist, hstride * K * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CU(c, cudaStreamSynchronize(s));
-    xi_h.assign((size_t)nslots * kMaxKrylov * 2, 0.0);
-    using C = std::complex<double>;
     for (int r = 0; r < nslots; ++r) {
-      if (!mask[r]) continue;
-      std::vector<C> xi(K), al(K);
-      std::vector<double> gam(K);
-      for (int q = 0; q < K; ++q) {
-        const double* hw = hh.data() + (size_t)q * hstride + kcoef + 3 * r;
-        gam[q] = hw[0] > 0.0 ? std::sqrt(hw[0]) : 0.0;
-        al[q] = (q >= fold_from[r] && gam[q] > 0.0) ? C(hw[1], hw[2]) / gam[q] : C(0.0, 0.0);
-      }
-      for (int q = K - 1; q >= 0; --q) {
-        C acc = al[q];
-        for (int p = q + 1; p < K; ++p) {
-          const double* b = hh.data() + (size_t)p * hstride + ((size_t)(q / kDotChunk) * nslots + r) * 2 * kDotChunk +
-                            2 * (q % kDotChunk);
-          acc -= C(b[0], b[1]) * xi[p];
-        }
-        xi[q] = gam[q] > 0.0 ? acc / gam[q] : C(0.0, 0.0);
-        xi_h[((size_t)r * kMaxKrylov + q) * 2] = xi[q].real();
-        xi_h[((size_t)r * kMaxKrylov + q) * 2 + 1] = xi[q].imag();
-      }
-      fold_from[r] = K;
+      if (sel[r] && fold_from[r] < K) up[r] = 1, any = true;
+      up[nslots + r] = fold_from[r];
     }
-    CU(c, cudaMemcpyAsync(xi_dev, xi_h.data(), xi_h.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-    CU(c, cudaMemcpyAsync(xmask_dev, mask.data(), nslots * sizeof(int), cudaMemcpyHostToDevice, s));
-    gcr_xupdate(lo, Z, slot, K, xlo, (const double*)xi_dev, n, nslots, (const int*)xmask_dev, s);
-    CU(c, cudaStreamSynchronize(s));  // the host vectors above must outlive the copies
+    if (!any || K == 0) return WMG_OK;
+    TRY(upload_ints(c, (int*)xmask_dev, up));
+    {
+      ProfScope ps(c, PROF_BLAS, 0);
+      gcr_backsolve((const double*)hist, hstride, kcoef, K, nslots, (const int*)xmask_dev, (double*)xi_dev, s);
+    }
+    int nup = 0;
+    for (int r = 0; r < nslots; ++r) nup += up[r];
+    {
+      ProfScope ps(c, PROF_BLAS, vec_bytes(c, 0, lo, nup, K + 2), nup);  // Z_0..Z_{K-1} read, x read + written
+      gcr_xupdate(lo, Z, slot, K, xlo, (const double*)xi_dev, n, nslots, (const int*)xmask_dev, s);
+    }
+    for (int r = 0; r < nslots; ++r)
+      if (up[r]) fold_from[r] = K;
     return check(c, "gcr solution update");
   };
   auto count_active = [&]() {
@@ -952,6 +976,7 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
     return src.finish(c, r, at(x64, f64, r), info);
   };
   TRY(set_rhs_scalars(c, mass.data(), nslots));
+  CU(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
   int k = 0;
   while (true) {
     if (k == 0) {
@@ -1003,7 +1028,9 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
       dslash(lo, wk, zk, nullptr, c->gauge[lo], c->fine, c->d_mass, c->d_active, nslots, 0, nullptr, s);
     }
     {
-      ProfScope ps(c, PROF_BLAS, 0);
+      // multidot: W_0..W_{k-1} and w read; orth: W_0..W_{k-1}, r read, w read + written;
+      // update: r, w read + written
+      ProfScope ps(c, PROF_BLAS, vec_bytes(c, 0, lo, c->n_active, (k > 0 ? k + 1 : 0) + (k + 3) + 4), c->n_active);
       if (k > 0) gcr_multidot(lo, W, slot, k, wk, n, nslots, c->d_active, rb_coef, s);
       gcr_orth(lo, W, nullptr, slot, k, wk, nullptr, rlo, rb_coef.result, k, n, nslots, c->d_active, rb_w, s);
       gcr_update_r(lo, rlo, wk, rb_w.result, n, nslots, c->d_active, rb_rn, s);
@@ -1074,9 +1101,13 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
     if (k == 0) std::fill(fold_from.begin(), fold_from.end(), 0);
   }
   CU(c, cudaStreamSynchronize(s));
-  if (use_mg && c->prm.coarse_tc && (coarse_mma_error() || coarse_tc05_error())) {
-    c->err = "a bounded wait of the tensor-core coarse stencil expired";
-    return WMG_ETIMEOUT;
+  if (use_mg && c->prm.coarse_tc) {
+    int e = 0;
+    CU(c, cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+      c->err = "a bounded wait of the tensor-core coarse stencil expired";
+      return WMG_ETIMEOUT;
+    }
   }
   if (use_mg && c->d_pcg_err) {
     int e = 0;

@@ -101,6 +101,8 @@ def load():
         "wmg_pack_spinor": (i, [vp, i, vp, vp, i]),
         "wmg_unpack_spinor": (i, [vp, i, vp, vp, i]),
         "wmg_apply_D": (i, [vp, i, vp, vp, i]),
+        "wmg_apply_cycle": (i, [vp, i, vp, vp, i]),
+        "wmg_smooth": (i, [vp, i, vp, vp, i, i]),
         "wmg_restrict": (i, [vp, i, i, vp, vp, i]),
         "wmg_prolong": (i, [vp, i, i, vp, vp, i]),
         "wmg_apply_coarse": (i, [vp, i, i, i, vp, vp, i]),
@@ -278,6 +280,14 @@ class Context:
     def apply_D(self, prec, inp, out, nrhs):
         return self._check(self.lib.wmg_apply_D(self.h, prec, _ptr(inp), _ptr(out), int(nrhs)))
 
+    def apply_cycle(self, prec, inp, out, nrhs):
+        """out = K(in): one multigrid cycle of the fine level (native fine spinors)."""
+        return self._check(self.lib.wmg_apply_cycle(self.h, prec, _ptr(inp), _ptr(out), int(nrhs)))
+
+    def smooth(self, prec, b, x, nrhs, nu):
+        """x <- nu MR steps on D x = b from the initial guess x (native fine spinors, in place)."""
+        return self._check(self.lib.wmg_smooth(self.h, prec, _ptr(b), _ptr(x), int(nrhs), int(nu)))
+
     def restrict(self, level, prec, fine, coarse, nrhs):
         return self._check(self.lib.wmg_restrict(self.h, int(level), prec, _ptr(fine), _ptr(coarse), int(nrhs)))
 
@@ -289,7 +299,8 @@ class Context:
         return self._check(self.lib.wmg_residual_noalloc(self.h, prec, _ptr(b), _ptr(x), _ptr(r), _ptr(norm2),
                                                          int(nrhs)))
 
-    PROF_CLASSES = ("dslash_sloppy", "dslash_fp64", "coarse", "restrict", "prolong", "blas", "setup", "cgnr")
+    PROF_CLASSES = ("dslash_sloppy", "dslash_fp64", "coarse", "restrict", "prolong", "blas", "setup", "cgnr",
+                    "blas_coarse")
 
     def profile(self, on=True):
         return self._check(self.lib.wmg_profile_enable(self.h, int(bool(on))))

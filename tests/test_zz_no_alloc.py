@@ -1,5 +1,5 @@
 """The allocation-free residual entry point (wmg_residual_noalloc) against the ordinary
-operator entry point wmg_apply_D.
+operator entry point wmg_apply_D and against the FP64 oracle's operator.
 
 wmg_residual_noalloc serves callers that cannot allocate device memory during a call (an
 application that owns all device memory through its own arena, or one that cannot accept
@@ -10,7 +10,8 @@ import numpy as np
 import pytest
 
 import synth
-from tests.gpu_util import TOL, dev, native_fine, rel_err
+from oracle import dirac
+from tests.gpu_util import TOL, dev, host, native_fine, rel_err
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -50,6 +51,16 @@ def test_residual_noalloc_matches_apply_D(W, prec):
         assert rel_err(r.view(nrhs, -1).cpu().numpy(), want.cpu().numpy()) < TOL[prec], call
         want_n2 = (want.abs() ** 2).sum(dim=1).double().cpu().numpy()
         assert np.abs(n2.cpu().numpy() - want_n2).max() < TOL[prec] * want_n2.max() * 10, call
+        # the oracle: r = b - D x with the FP64 definition of D (inputs as rounded on the device)
+        xc, bc, rc = (dev(np.zeros_like(xs)) for _ in range(3))
+        ctx.unpack(prec, x, xc, nrhs)
+        ctx.unpack(prec, b, bc, nrhs)
+        ctx.unpack(prec, r, rc, nrhs)
+        xh, bh = host(xc), host(bc)
+        ro = np.stack([bh[k] - dirac.apply_D(U, xh[k], -0.3) for k in range(nrhs)])
+        assert rel_err(host(rc), ro) < TOL[prec], call
+        n2o = np.array([np.vdot(ro[k], ro[k]).real for k in range(nrhs)])
+        assert np.abs(n2.cpu().numpy() - n2o).max() < TOL[prec] * n2o.max() * 10, call
 
 
 def test_residual_noalloc_rejects_oversize(W):
