@@ -166,12 +166,12 @@ void wmg_default_params(wmg_params* p) {
   p->nvec[0] = 24;
   p->nvec[1] = 32;
   p->setup_passes = 5;
-  p->setup_relax = 20;
+  p->setup_relax = 100;
   p->nu_post = 4;
   p->gcr_restart = 16;
   p->cycle_gamma = 1;
   p->tol = 1e-10;
-  p->coarse_tol = 5e-2;
+  p->coarse_tol = 0.1;
   p->coarse_maxit = 2000;
   p->max_iter = 1000;
   p->prec_sloppy = WMG_PREC_SINGLE;
@@ -224,6 +224,7 @@ wmg_status wmg_create(wmg_ctx** out, const int dims[4], void* stream) {
     if (v >= 2 && v <= 32 && v % 2 == 0) c->cg_chunk = v;
   }
   if (const char* g = std::getenv("WMG_UNFUSED_GALERKIN")) c->use_fused_galerkin = !(g[0] == '1');
+  if (const char* g = std::getenv("WMG_NO_EOB")) c->use_eoB = !(g[0] == '1');
   c->L[0].g = c->fine;
   c->L[0].ndof = 12;
   cudaError_t e = cudaSuccess;

@@ -146,6 +146,45 @@ __global__ void k_eo_inv_apply(const cpx<R>* __restrict__ inv, const int* __rest
   if (!active || active[r]) out[at] = acc;
 }
 
+// The odd-site pass of S as a plain hop stencil: for odd site k (grid.x) and hop slot
+// 1 + blockIdx.y, B_slot = -M A_slot with M = (A_kk + shift I)^-1 (FP32 table entry, [col][row])
+// and A_slot the site's hop block; written in the stencil layout [k][9][col][row] (slot 0 left
+// as it is: the hop-only pass never reads it).  Both factors are staged in shared memory;
+// thread (row, col) forms the n-term row-by-column product.
+__global__ void __launch_bounds__(256) k_eo_hop_inverse(const cf* __restrict__ A, const cf* __restrict__ inv,
+                                                        Geom g, int n, cf* __restrict__ B) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cf* Ms = reinterpret_cast<cf*>(smraw);  // [col][row]
+  cf* As = Ms + (size_t)n * n;            // [col][row]
+  const int k = blockIdx.x, slot = 1 + blockIdx.y, nn = n * n;
+  const int v = parity_site(g, k, 1);
+  const cf* a = A + ((size_t)v * 9 + slot) * nn;
+  const cf* m = inv + (size_t)k * nn;
+  for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+    Ms[i] = m[i];
+    As[i] = a[i];
+  }
+  __syncthreads();
+  cf* o = B + ((size_t)k * 9 + slot) * nn;
+  for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+    const int col = i / n, row = i - col * n;
+    cf acc{0.f, 0.f};
+    for (int j = 0; j < n; ++j) cfma(acc, Ms[(size_t)j * n + row], As[(size_t)col * n + j]);
+    o[i] = cf{-acc.re, -acc.im};
+  }
+}
+
+void eo_hop_inverse(const void* A, const void* inv_entry, const Geom& g, int n, void* B, cudaStream_t s) {
+  count_launch();
+  const size_t smem = (size_t)2 * n * n * sizeof(cf);
+  static const bool attr = [] {
+    cudaFuncSetAttribute(k_eo_hop_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    return true;
+  }();
+  (void)attr;
+  k_eo_hop_inverse<<<dim3(g.V / 2, 8), 256, smem, s>>>((const cf*)A, (const cf*)inv_entry, g, n, (cf*)B);
+}
+
 size_t eo_inverse_bytes(int prec, const Geom& g, int n) {
   return (size_t)(g.V / 2) * n * n * 2 * prec_real_bytes(prec);
 }

@@ -115,6 +115,10 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
   __shared__ int nbs[9];
   __shared__ double npart[NW][32][2];  // per-lane norm partials of the MMA warps
   const int v = eo.parity < 0 ? (int)blockIdx.x : parity_site(g, blockIdx.x, eo.parity);
+  // the operator (and its scale) of this site: the level's, or the precomputed odd-site pass
+  const uint4* Aop = eo.opB ? reinterpret_cast<const uint4*>(eo.opB) : A16;
+  const int vop = eo.opB ? (int)blockIdx.x : v;
+  const float s_site = eo.opB ? eo.sB[blockIdx.x] : sA[v];
   const int r0 = blockIdx.y * R;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool mma_warp = warp < MT * NT;
@@ -126,7 +130,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
       const uint32_t bar = smem_addr(&mbar[t]);
       mbar_arrive_expect_tx(bar, 2 * kTileBytes);
       for (int p = 0; p < 2; ++p)
-        bulk_g2s(smem_addr(As + (size_t)(p * MT + t) * KS * 32), A16 + (((size_t)v * 2 + p) * MT + t) * KS * 32,
+        bulk_g2s(smem_addr(As + (size_t)(p * MT + t) * KS * 32), Aop + (((size_t)vop * 2 + p) * MT + t) * KS * 32,
                  kTileBytes, bar);
     }
   }
@@ -233,7 +237,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
     __syncthreads();
     cf* hs = reinterpret_cast<cf*>(xb);  // [R][n]
     if (mma_warp) {
-      const float s_a = sA[v];
+      const float s_a = s_site;
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int row = 16 * m + gq + (e >= 2 ? 8 : 0);
@@ -264,7 +268,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
   // epilogue: thread holds rows 16 m + gq (+8) and right-hand sides 8 blk + 2q + (e & 1)
   double nv2[2] = {0.0, 0.0};
   if (mma_warp) {
-    const float s_a = sA[v];
+    const float s_a = s_site;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int row = 16 * m + gq + (e >= 2 ? 8 : 0);

@@ -46,6 +46,10 @@ struct LevelData {
   long long eo_version[2] = {-1, -1};
   std::vector<int> eo_idx_up[2];
   const void* eo_idx_ptr[2] = {nullptr, nullptr};
+  // precomputed odd-site pass -A_oo^-1 A_oe (FP16 tensor-core copy) for one mass shift
+  double eoB_shift = 0.0;
+  long long eoB_version = -1;
+  const void* eoB_ptr = nullptr;
   size_t nvec_elems() const { return (size_t)g.V * ndof; }  // complex numbers per field
 };
 
@@ -82,6 +86,7 @@ struct wmg_ctx {
   bool use_graphs = true;                      // capture the coarsest CGNR iterations
   int cg_chunk = 2;                            // CGNR iterations between convergence checks (even)
   bool use_fused_galerkin = true;              // fused fine-level Galerkin kernel
+  bool use_eoB = true;                         // precomputed odd-site pass for single-shift batches
   int* d_pcg_err = nullptr;                    // sticky error flag of the persistent CGNR (per solve)
   int* d_err = nullptr;                        // error word of the tensor-core stencils' bounded waits
                                                // (cleared at the start of each solve)

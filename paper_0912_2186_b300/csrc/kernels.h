@@ -136,6 +136,9 @@ void block_gs(bool fine_level, void* vecs, const Blocking& bk, int* rank_flag, c
 // the neighbour values (slots 1..8) instead of `in`; add is added to the result.
 // The tensor-core stencil also takes the odd-site block inverses (inv, inv_idx as for
 // eo_inv_apply; parity 1 and hop_only): it then writes -M_r (its result) instead of the result.
+// With opB (tensor-core stencil, parity 1, hop_only) the operator is not the level's but opB
+// with scales sB, both indexed by the parity-site number: the precomputed odd-site pass
+// B_k = -A_oo^-1 A_oe,k of one mass shift (eo_hop_inverse).
 struct StencilEo {
   int parity = -1;
   int hop_only = 0;
@@ -143,6 +146,8 @@ struct StencilEo {
   const void* add = nullptr;
   const void* inv = nullptr;
   const int* inv_idx = nullptr;
+  const void* opB = nullptr;
+  const float* sB = nullptr;
 };
 // out = A in (+ shift[r] in), or sigma_3 A sigma_3 in for dagger; optional |out|^2 per rhs
 void coarse_apply(int prec, const void* A, const Geom& g, int n, const void* in, void* out, int nrhs,
@@ -154,6 +159,9 @@ void coarse_apply(int prec, const void* A, const Geom& g, int n, const void* in,
 void eo_invert(int prec, const void* A, const Geom& g, int n, const double* shifts, int e0, int ne, void* inv,
                int* singular, cudaStream_t s);
 size_t eo_inverse_bytes(int prec, const Geom& g, int n);  // one table entry
+// B[k][slot][col][row] = -(inv_entry[k]) A[odd site k][slot] for the hop slots 1..8 (FP32; A in
+// the stencil layout, inv_entry one FP32 table entry of eo_invert)
+void eo_hop_inverse(const void* A, const void* inv_entry, const Geom& g, int n, void* B, cudaStream_t s);
 // out_o[r] = M_r (bc b_o[r] + hc h_o[r]) at the odd sites, M_r = inv[idx[r]] or, for dagger,
 // sigma_3 inv[idx[r]] sigma_3; b or h may be null; out may alias h (not b)
 void eo_inv_apply(int prec, const void* inv, const int* idx, const Geom& g, int n, const void* b, double bc,

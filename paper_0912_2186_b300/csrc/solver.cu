@@ -427,6 +427,8 @@ static bool eo_usable(const wmg_ctx* c, int l) { return c->prm.coarse_eo && eo_p
 struct EoTable {
   const void* inv;
   const int* idx;
+  const void* B16 = nullptr;  // precomputed odd-site pass (single-shift batches) or null
+  const float* sB = nullptr;
 };
 
 // the table entries for the shifts of right-hand sides 0 .. nrhs-1 (computed for shifts not
@@ -509,6 +511,45 @@ static void eo_stencil(wmg_ctx* c, int l, int prec, const void* in, void* out, i
     coarse_apply(prec, L.A[prec], L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, nullptr, rb, c->stream, &eo);
 }
 
+// When every right-hand side of the call has the same mass shift and the parity passes run on
+// the tensor-core stencil, the odd-site pass t_o = -A_oo^-1 A_oe x_e is a plain hop stencil with
+// the blocks B_k = -A_oo^-1 A_oe,k, built once per operator and shift (FP32 product of the
+// table's inverse and the hop blocks, then the FP16 fragment copy); otherwise tb->B16 stays null
+// and the pass applies the inverses in its epilogue.
+static wmg_status ensure_eoB(wmg_ctx* c, int l, int prec, int nrhs, EoTable* tb) {
+  tb->B16 = nullptr;
+  tb->sB = nullptr;
+  if (!c->use_eoB || !eo_mma(c, l, prec)) return WMG_OK;
+  const double sh = c->h_shift[0];
+  for (int r = 1; r < nrhs; ++r)
+    if (c->h_shift[r] != sh) return WMG_OK;
+  LevelData& L = c->L[l];
+  const int n = L.ndof, Vh = L.g.V / 2;
+  const std::string tag = std::to_string(l);
+  void *B16, *sB;
+  TRY(ws_get(c, "eoB16_" + tag, stencil_mma_words(Vh, n) * 16, &B16));
+  TRY(ws_get(c, "eoBs_" + tag, (size_t)Vh * sizeof(float), &sB));
+  if (L.eoB_version != L.op_version || L.eoB_shift != sh || L.eoB_ptr != B16) {
+    void* Bt;
+    TRY(ws_get(c, "eoBt_" + tag, (size_t)Vh * 9 * n * n * sizeof(cf), &Bt));
+    const std::vector<double>& tab = L.eo_shift[prec];
+    const size_t e = (size_t)(std::find(tab.begin(), tab.end(), sh) - tab.begin());
+    const void* inv_e = (const char*)tb->inv + e * eo_inverse_bytes(prec, L.g, n);
+    {
+      ProfScope ps(c, PROF_CGNR, 0);
+      eo_hop_inverse(L.A[WMG_PREC_SINGLE], inv_e, L.g, n, Bt, c->stream);
+      stencil_to_mma(WMG_PREC_SINGLE, Bt, Vh, n, (float*)sB, B16, c->stream);
+    }
+    TRY(check(c, "even-odd odd-site operator"));
+    L.eoB_version = L.op_version;
+    L.eoB_shift = sh;
+    L.eoB_ptr = B16;
+  }
+  tb->B16 = B16;
+  tb->sB = (const float*)sB;
+  return WMG_OK;
+}
+
 // out_e = S in_e (or S^dag = sigma_3 S sigma_3 in_e), odd sites of out untouched; t: scratch
 static void schur_op(wmg_ctx* c, int l, int prec, const EoTable& tb, const void* in, void* out, void* t, int nrhs,
                      bool dagger, const RedBuf* rb) {
@@ -517,8 +558,13 @@ static void schur_op(wmg_ctx* c, int l, int prec, const EoTable& tb, const void*
   hop.parity = 1;
   hop.hop_only = 1;
   if (eo_mma(c, l, prec)) {
-    hop.inv = tb.inv;  // the tensor-core pass applies the block inverses in its epilogue
-    hop.inv_idx = tb.idx;
+    if (tb.B16) {  // -A_oo^-1 A_oe precomputed for the batch's one shift
+      hop.opB = tb.B16;
+      hop.sB = tb.sB;
+    } else {  // the tensor-core pass applies the block inverses in its epilogue
+      hop.inv = tb.inv;
+      hop.inv_idx = tb.idx;
+    }
     eo_stencil(c, l, prec, in, t, nrhs, dagger, hop, nullptr);
   } else {
     eo_stencil(c, l, prec, in, t, nrhs, dagger, hop, nullptr);
@@ -534,6 +580,7 @@ wmg_status schur_apply(wmg_ctx* c, int l, int prec, const void* in, void* out, i
   if (!eo_possible(c->L[l])) return WMG_EINVAL;
   EoTable tb;
   TRY(ensure_eo(c, l, prec, nrhs, &tb));
+  TRY(ensure_eoB(c, l, prec, nrhs, &tb));
   void* t;
   TRY(vec_ws(c, l, "eo_t", prec, nrhs, &t));
   blas_zero(prec, out, c->L[l].nvec_elems(), nrhs, c->stream);
@@ -600,6 +647,7 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
   if (eo) {
     TRY(ensure_eo(c, l, prec, nrhs, &tb));
     TRY(vec_ws(c, l, "eo_t", prec, nrhs, &t));
+    TRY(ensure_eoB(c, l, prec, nrhs, &tb));
   }
   // the operator of the CG: A, or the Schur complement S on the even sites
   auto op = [&](const void* in, void* out, bool dagger, const RedBuf* rb) {
@@ -673,9 +721,10 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
     // iterations followed by a check kernel that clears the loop condition once every
     // right-hand side has converged or coarse_maxit is reached.  Built once per argument set.
     char key[512];
-    std::snprintf(key, sizeof key, "cg%d/%d/%d/%p/%p/%p/%p/%p/%p/%p/%p/%p/%p/%.17g/%d/%d/%p/%p/%p", l, prec, nrhs,
-                  L.A[prec], (void*)L.A16, x, r, p, q, z, (void*)c->d_shift[l], (void*)c->red_partial, (void*)c->res,
-                  cg.tol2, c->prm.coarse_maxit * 64 + chunk, eo ? 1 : 0, tb.inv, (const void*)tb.idx, t);
+    std::snprintf(key, sizeof key, "cg%d/%d/%d/%p/%p/%p/%p/%p/%p/%p/%p/%p/%p/%.17g/%d/%d/%p/%p/%p/%p/%p", l, prec,
+                  nrhs, L.A[prec], (void*)L.A16, x, r, p, q, z, (void*)c->d_shift[l], (void*)c->red_partial,
+                  (void*)c->res, cg.tol2, c->prm.coarse_maxit * 64 + chunk, eo ? 1 : 0, tb.inv, (const void*)tb.idx,
+                  t, tb.B16, (const void*)tb.sB);
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
       if (c->graphs.size() > 64) TRY(clear_graphs(c));
