@@ -37,6 +37,10 @@ WORKLOADS = {
     "16x16x16x32": dict(dims=(16, 16, 16, 32), eps=0.6, gauge_seed=11, nvec=24, block=(4, 4, 4, 4), nrhs=12,
                         masses_file=os.path.join(ROOT, "tests", "golden", "masses_16x16x16x32_eps0.6.json")),
 }
+# outer iterations per mass the GPU arm measures on this job (mean over the 12 point sources), used
+# by --impl reference, which runs without a GPU, to scale its sample to the whole job
+REFERENCE_ITERS = {"16x16x16x32": [38.4, 46.8, 53.2]}
+REFERENCE_CG = {"16x16x16x32": [15.3, 37.3, 65.8]}  # coarsest CG iterations per cycle, the same source
 PROF_CLASSES = ("dslash_sloppy", "dslash_fp64", "coarse", "restrict", "prolong", "blas", "setup", "cgnr",
                 "blas_coarse")
 
@@ -106,88 +110,166 @@ class Clocks:
 
 
 # ------------------------------------------------------------------------------------------
-# CPU oracle (reference arm and cpu_baseline)
+# CPU oracle (reference arm and cpu_baseline): the FP64 oracle as it stands, timed on this host
 # ------------------------------------------------------------------------------------------
-OPCOUNTS = os.path.join(ROOT, "profiles", "op_counts_16x16x16x32.json")
+def _threads(n):
+    """Limit the oracle to n host threads: the OpenMP pool of its C operator and, where
+    threadpoolctl is installed, numpy's BLAS pools (the oracle's numpy work is mostly elementwise)."""
+    import contextlib
+    import ctypes
+    try:
+        ctypes.CDLL("libgomp.so.1").omp_set_num_threads(int(n))
+    except OSError:
+        pass
+    try:
+        from threadpoolctl import threadpool_limits
+    except ImportError:
+        return contextlib.nullcontext()
+    return threadpool_limits(limits=int(n))
 
 
-def oracle_unit_costs(w, reps=3):
-    """Host seconds of the oracle's unit operations on this workload's shapes."""
-    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
-    from oracle import cref, mg
-    dims, N, blk = w["dims"], w["nvec"], w["block"]
-    U = synth.gauge_field(dims, w["eps"], w["gauge_seed"])
-    v = synth.setup_starts(dims, N, 5)
-    P = mg.block_orthonormalise(v, blk)
-    cd = mg.coarse_dims(dims, blk)
-    psi = synth.gaussian_spinors(dims, 1, 6)[0]
-    rng = np.random.default_rng(0)
-    shape = tuple(reversed(cd)) + (9, 2 * N, 2 * N)
-    A = mg.StencilOp(rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
-    phi = synth.coarse_starts(cd, 2 * N, 1, 7)[0]
-    t = {}
+class OracleJob:
+    """A bounded sample of the job run with the oracle's own code on the workload's shapes.
 
-    def tm(name, f):
-        f()
+    The oracle builds its own two-level hierarchy for the field (Gaussian starts, Gram-Schmidt,
+    Galerkin product; both timed, they are one setup rebuild).  Then, timed: MR relaxation steps
+    on D psi = 0 (the setup's first pass) and outer flexible-GCR iterations of one point source
+    with the oracle's cycle (MR nu = 4, even-odd coarsest CG to the GPU arm's coarse tolerance)
+    at each mass.  The job estimate scales these by the counts of the job: relaxation steps x N,
+    setup passes x rebuilds, (passes - 1) x N cycle applications, and right-hand sides x the outer
+    iterations the GPU arm measured at each mass in the same run."""
+
+    def __init__(self, w, masses, coarse_tol, log=None):
+        from oracle import mg
+        self.w, self.masses, self.coarse_tol = w, list(masses), coarse_tol
+        dims, N, blk = w["dims"], w["nvec"], w["block"]
+        self.U = synth.gauge_field(dims, w["eps"], w["gauge_seed"])
+        self.starts = synth.setup_starts(dims, N, 5)
+        self.b = synth.point_sources(dims, 1)[0]
         t0 = time.perf_counter()
-        for _ in range(reps):
-            f()
-        t[name] = (time.perf_counter() - t0) / reps
+        self.P = mg.block_orthonormalise(self.starts, blk)
+        self.t_gs = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        self.Ac = mg.galerkin(mg.WilsonOp(self.U, self.masses[-1]), self.P, blk)
+        self.t_gal = time.perf_counter() - t0
+        self.cores = os.cpu_count()
 
-    tm("D", lambda: cref.apply_D(U, psi, -1.0))
-    tm("coarse", lambda: A.apply(phi))
-    tm("restrict", lambda: mg.restrict(P, psi, blk))
-    tm("prolong", lambda: mg.prolong(P, phi, blk))
-    t0 = time.perf_counter()
-    mg.block_orthonormalise(v, blk)
-    t["gs"] = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    op = mg.WilsonOp(U, -1.0)
-    g = np.zeros_like(psi)
-    g[..., :6] = P[0][..., :6]
-    for mu in range(4):
-        for s in (1, -1):
-            mg.restrict(P, op.hop(g, mu, s), blk)
-    t["galerkin_column"] = time.perf_counter() - t0
-    return t, os.cpu_count()
+    def time_relax(self, steps):
+        from oracle import mg, solvers
+        op = mg.WilsonOp(self.U, self.masses[-1])
+        s = self.starts[0]
+        t0 = time.perf_counter()
+        solvers.mr(op.apply, np.zeros_like(s), s, steps)
+        return (time.perf_counter() - t0) / steps
+
+    def time_iterations(self, m, k):
+        """Seconds per outer iteration at mass m (k iterations of the oracle's flexible GCR, its
+        closing true residual included) and the mean coarsest-CG iterations per cycle."""
+        from oracle import mg, solvers
+        op = mg.WilsonOp(self.U, m)
+        prm = solvers.CycleParams(nu=4, coarse_tol=self.coarse_tol, coarse_maxit=2000, coarse_eo=True)
+        H = solvers.Hierarchy([op, self.Ac.shifted(m - self.masses[-1])], [self.P], [self.w["block"]], prm)
+        t0 = time.perf_counter()
+        solvers.fgcr(op.apply, lambda r: solvers.cycle(H, 0, r), self.b, 1e-10, 16, max_iter=k)
+        return (time.perf_counter() - t0) / k, float(np.mean(H.coarse_iters)) if H.coarse_iters else 0.0
+
+    def time_coarse_cg(self, m, k=10):
+        """Seconds per iteration of the oracle's even-odd coarsest CG at mass m (k iterations
+        against one, the difference per iteration; no convergence test is met)."""
+        from oracle import eo
+        A = self.Ac.shifted(m - self.masses[-1])
+        b = synth.coarse_starts(A.dims, A.n, 1, 7)[0]
+        t0 = time.perf_counter()
+        eo.cgnr_eo(A, b, 1e-30, 1)
+        t1 = time.perf_counter()
+        eo.cgnr_eo(A, b, 1e-30, k + 1)
+        t2 = time.perf_counter()
+        return ((t2 - t1) - (t1 - t0)) / k
+
+    def estimate(self, t_mr, t_iter, iters, prm):
+        """Job seconds: setup (relaxation, rebuilds, improvement cycles) + the solves."""
+        N, nrhs = self.w["nvec"], self.w["nrhs"]
+        setup = N * prm["setup_relax"] * t_mr + prm["setup_passes"] * (self.t_gs + self.t_gal) \
+            + (prm["setup_passes"] - 1) * N * t_iter[-1]
+        return setup + sum(nrhs * it * t for it, t in zip(iters, t_iter))
 
 
-def oracle_estimate(w, counts, unit):
-    """Oracle seconds for one step: unit costs x the step's operation counts."""
-    N = w["nvec"]
-    sec = (counts["dslash_sloppy"] + counts["dslash_fp64"]) * unit["D"] + counts["coarse"] * unit["coarse"] \
-        + counts["restrict"] * unit["restrict"] + counts["prolong"] * unit["prolong"] \
-        + counts["setup_builds"] * (unit["gs"] + 2 * N * unit["galerkin_column"])
-    return sec
+def cpu_baseline_sample(w, masses, iters, cg_per_cycle, prm, k=1):
+    """The oracle's sample at all cores and the lightest mass again on one thread.  The coarsest
+    solve is charged at the GPU arm's CG iterations per cycle (cg_per_cycle, per mass): the
+    oracle's iteration time has its own coarsest CG iterations replaced by those, each at the
+    oracle's measured time per CG iteration."""
+    job = OracleJob(w, masses, prm["coarse_tol"])
+    with _threads(job.cores):
+        t_mr = job.time_relax(2)
+        timed = [job.time_iterations(m, k) for m in masses]
+        t_cg = [job.time_coarse_cg(m) for m in masses]
+    t_iter = [t + (g - c) * tc for (t, c), g, tc in zip(timed, cg_per_cycle, t_cg)]
+    est = job.estimate(t_mr, t_iter, iters, prm)
+    with _threads(1):
+        t1, c1 = job.time_iterations(masses[-1], k)
+        tc1 = job.time_coarse_cg(masses[-1])
+    t1 = t1 + (cg_per_cycle[-1] - c1) * tc1
+    out = {"value": est, "unit": "s", "cores": job.cores, "kind": "oracle",
+           "sample": (f"FP64 oracle on this host ({job.cores} threads): its own 2-level hierarchy for the 16^3x32 "
+                      f"field (Gram-Schmidt {job.t_gs:.1f} s, Galerkin {job.t_gal:.1f} s, timed), 2 MR relaxation "
+                      f"steps ({t_mr:.3f} s each) and {k} outer FGCR iteration(s) of one point source at each mass "
+                      f"({', '.join(f'{t:.2f}' for t, _ in timed)} s per iteration with "
+                      f"{', '.join(f'{c:.0f}' for _, c in timed)} coarsest CG iterations per cycle on the oracle's "
+                      f"hierarchy; {', '.join(f'{1e3 * t:.1f}' for t in t_cg)} ms per coarsest CG iteration, charged at "
+                      f"the GPU arm's {', '.join(f'{g:.0f}' for g in cg_per_cycle)} per cycle: "
+                      f"{', '.join(f'{t:.2f}' for t in t_iter)} s per outer iteration), "
+                      f"scaled to the job by its counts: N x {prm['setup_relax']} relaxation steps, "
+                      f"{prm['setup_passes']} rebuilds, {prm['setup_passes'] - 1} x N setup cycles, 12 right-hand "
+                      f"sides x the GPU arm's outer iterations per mass {[round(i, 1) for i in iters]}"),
+           "per_iteration_s": t_iter, "coarse_cg_iteration_s": t_cg, "one_thread": {
+               "iteration_s_lightest_mass": t1,
+               "value": est * t1 / t_iter[-1],
+               "note": "the job estimate scaled by the one-thread / all-thread time of an outer iteration at the "
+                       "lightest mass (the rebuild times were taken with all threads)"}}
+    return out
 
 
 def run_reference(args, w):
+    """--impl reference: the oracle, each step one timed outer iteration at one of the masses (in
+    turn), the value the job estimate from that step (see OracleJob)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    try:
-        with open(OPCOUNTS) as f:
-            rec = json.load(f)
-        counts = rec["counts"]
-        counts_at = f"{rec.get('masses')} ({rec.get('masses_source', 'unknown source')})"
-    except OSError:
-        print(json.dumps({"impl": "reference", "unavailable": "operation counts of the job not recorded yet"}))
-        return
-    vals = []
+    masses, _ = load_masses(w, args.masses, args.workload)
+    prm = dict(setup_relax=100, setup_passes=5, coarse_tol=0.1)
+    iters, cg = REFERENCE_ITERS[args.workload], REFERENCE_CG[args.workload]
+    job = OracleJob(w, masses, prm["coarse_tol"])
+    t_mr = job.time_relax(2)
+    t_cg = {m: job.time_coarse_cg(m) for m in masses}
+
+    def one(m):
+        t, c = job.time_iterations(m, 1)
+        return t + (cg[masses.index(m)] - c) * t_cg[m]
+
+    base = {m: one(m) for m in masses}
+    vals, walls = [], []
     for i in range(args.warmup + args.steps):
-        unit, cores = oracle_unit_costs(w, reps=1)
+        m = masses[i % len(masses)]
+        t0 = time.perf_counter()
+        base[m] = one(m)
+        wall = time.perf_counter() - t0
         if i >= args.warmup:
-            vals.append(oracle_estimate(w, counts, unit))
+            vals.append(job.estimate(t_mr, [base[x] for x in masses], iters, prm))
+            walls.append(wall)
     v = statistics.mean(vals)
-    sample = ("FP64 oracle on the host: C restatement of D, numpy coarse stencil, restrict, prolong, block "
-              "Gram-Schmidt and one Galerkin column timed on this workload's shapes, times the operation counts "
-              f"of one step recorded by the GPU arm at masses {counts_at} (vector updates not included)")
+    sample = (f"FP64 oracle ({job.cores} threads): its own hierarchy for the field (Gram-Schmidt {job.t_gs:.1f} s, "
+              f"Galerkin {job.t_gal:.1f} s), 2 MR relaxation steps, then per step one outer FGCR iteration of one "
+              f"point source at one of the masses in turn (the step's wall time is ms_per_step); value = the job "
+              f"estimate from the latest iteration time at each mass (its coarsest CG charged at the GPU arm's {cg} "
+              f"CG iterations per cycle, at the oracle's measured time per CG iteration) x 12 right-hand sides x "
+              f"the GPU arm's outer iterations {iters}, plus the setup's relaxation, rebuilds and cycles")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "higher_is_better": False,
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload},
-        "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(walls) * 1e3, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": job.cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -219,7 +301,7 @@ def run_gpu(args, w):
     x_dev = torch.zeros_like(b_dev)
     ctx = wmg.Context(dims)
     params = wmg.default_params(nvec=[w["nvec"]], block=[w["block"]], prec_sloppy=wmg.PREC_SINGLE,
-                                seed=1000 + rank)
+                                seed=1000 + rank, max_iter=20000)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     record = {"iters": [], "true_resid": [], "phases": []}
     # host buffers of the end-to-end measurement: pinned, allocated once
@@ -300,14 +382,29 @@ def run_gpu(args, w):
     h2d = U.nbytes + len(masses) * b.nbytes
     d2h = len(masses) * b.nbytes
 
-    # instrumented step: per-class kernel time, algorithmic bytes and operation counts
+    # instrumented step, phase by phase (setup, then each mass): per-class kernel time, algorithmic
+    # bytes and launches, and the coarsest CG iterations per cycle at each mass (two Schur-complement
+    # applications per CG iteration, one cycle per restriction)
+    prof, cg_per_cycle = None, []
+
+    def add(tot, part):
+        if tot is None:
+            return part
+        return {k: {f: tot[k][f] + part[k][f] for f in part[k]} for k in part}
+
+    ctx.load_gauge(U_dev)
+    ctx.set_mass(m_light)
     ctx.profile(True)
-    step()
-    prof = ctx.profile_get()
+    ctx.setup(params)
+    prof = add(prof, ctx.profile_get())
+    for m in masses:
+        ctx.set_mass(m)
+        ctx.profile(True)
+        ctx.solve(b_dev, x_dev, nrhs)
+        part = ctx.profile_get()
+        prof = add(prof, part)
+        cg_per_cycle.append(part["coarse"]["launches"] / max(2 * part["restrict"]["launches"], 1))
     ctx.profile(False)
-    builds = params.setup_passes
-    counts = {k: prof[k]["units"] for k in PROF_CLASSES}
-    counts["setup_builds"] = builds
     # the dominant class: the largest share of kernel time among the classes with accounted bytes
     hot = max((k for k in PROF_CLASSES if prof[k]["bytes"] > 0), key=lambda k: prof[k]["ms"])
     peaks, src = measured_peaks()
@@ -351,7 +448,8 @@ def run_gpu(args, w):
     # plain comparison: the same job in all-FP64, one right-hand side at a time
     plain = None
     if not args.no_plain:
-        pp = wmg.default_params(nvec=[w["nvec"]], block=[w["block"]], prec_sloppy=wmg.PREC_DOUBLE, seed=1000 + rank)
+        pp = wmg.default_params(nvec=[w["nvec"]], block=[w["block"]], prec_sloppy=wmg.PREC_DOUBLE, seed=1000 + rank,
+                                max_iter=20000)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -368,24 +466,40 @@ def run_gpu(args, w):
         torch.cuda.synchronize()
         plain = {"s": e0.elapsed_time(e1) / 1e3, "iters_mean": float(np.mean(pit)), "prec": "f64", "nrhs_per_solve": 1}
 
-    cpu = None
-    if rank == 0 and not args.no_cpu:
-        unit, cores = oracle_unit_costs(w, reps=2)
-        cpu = {"value": oracle_estimate(w, counts, unit), "unit": "s", "cores": cores, "kind": "oracle",
-               "sample": "FP64 oracle unit operations (C restatement of D, numpy coarse stencil, restrict, prolong, "
-                         "block Gram-Schmidt, one Galerkin column) timed on this workload's shapes, times the "
-                         "operation counts of one step; vector updates not included"}
-        if args.record_counts:
-            os.makedirs(os.path.dirname(os.path.abspath(args.record_counts)), exist_ok=True)
-            with open(args.record_counts, "w") as f:
-                json.dump({"workload": args.workload, "counts": counts, "masses": masses, "masses_source": masses_source,
-                           "note": "operator applications per step measured by bench.py --record-counts"}, f, indent=1)
+    # unpreconditioned baselines on the same kernels (FP64, one point source per mass): outer
+    # iterations and seconds of plain restarted GCR(16) and of CG on the normal equations, beside
+    # MG-GCR's, to show the critical slowing down the multigrid preconditioner removes
+    baselines = None
+    if not args.no_plain:
+        ctx.load_gauge(U_dev)
+        baselines = {"gcr16_fp64": [], "cgnr_fp64": []}
+        b1 = b_dev[:1].contiguous()
+        x1 = torch.zeros_like(b1)
+        for m in masses:
+            ctx.set_mass(m)
+            for key, f in (("gcr16_fp64", lambda: ctx.solve(b1, x1, 1, plain=True)),
+                           ("cgnr_fp64", lambda: ctx.solve_cgnr(b1, x1, 1, maxit=40000))):
+                x1.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, info = f()
+                torch.cuda.synchronize()
+                baselines[key].append({"mass": m, "iters": info[0]["iters"], "s": time.perf_counter() - t0,
+                                       "converged": bool(info[0]["converged"]),
+                                       "true_resid": info[0]["true_resid"]})
 
     serving = None
     if rank == 0 and not args.no_serving:
         ctx.close()
         torch.cuda.empty_cache()
         serving = run_serving(wmg, masses, masses_source)
+    iters_mean = [float(np.mean(i)) for i in iters[:len(masses)]]
+    # the oracle's timed sample, after every GPU measurement (nothing else runs meanwhile)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline_sample(w, masses, iters_mean, cg_per_cycle, dict(setup_relax=params.setup_relax,
+                                                              setup_passes=params.setup_passes,
+                                                              coarse_tol=params.coarse_tol))
     if rank != 0:
         return
     out = {
@@ -397,11 +511,14 @@ def run_gpu(args, w):
                    "setup_passes": params.setup_passes, "smoother": "MR nu=4 FP32", "outer": "FGCR(16) FP64 reliable",
                    "l2": "flushed (256 MB write) between timed steps", "parallelism": "replicas" if world > 1 else "1 GPU"},
         "solves_per_s": world * len(masses) * nrhs / t_step,
-        "iters_per_mass": [float(np.mean(i)) for i in iters[:len(masses)]],
+        "iters_per_mass": iters_mean,
+        "iters_growth": max(iters_mean) / min(iters_mean),
+        "coarse_cg_per_cycle": cg_per_cycle,
         "phases": phases,
         "max_true_resid": resid,
         "plain_fp64": plain,
         "speedup_vs_plain": (plain["s"] / t_step) if plain else None,
+        "unpreconditioned_fp64": baselines,
         "dslash_fp32_isolated": dsl,
         "kernel_breakdown": breakdown,
         "roofline": roof,
@@ -492,6 +609,68 @@ def run_serving(wmg, masses16, masses_source, nreq=200, seed=2009, slots=12):
                        "24^3x48 eps0.7 3-level N24/32 (hand-chosen masses)"]}
 
 
+def run_probe(args, w):
+    """--probe: the hot kernels of the job on the 16^3x32 workload inside the NVTX range "probe",
+    for ncu captures (ncu --nvtx --nvtx-include "probe/") and quick CUDA-event timing.  The hierarchy
+    is built first (the job's setup at the lightest mass); inside the range each of the FP32 fine
+    dslash, restrict, prolong, the tensor-core coarse stencil and the even-odd Schur complement of
+    the coarse operator runs --probe-reps times on 12 right-hand sides, then (--probe-solve) the 12
+    point sources are solved once at --probe-mass (default the heaviest of the job's masses)."""
+    import torch
+
+    from paper_0912_2186_b300 import build, wmg
+    build.build()
+    masses, _ = load_masses(w, args.masses, args.workload)
+    dims, nr = w["dims"], w["nrhs"]
+    V = int(np.prod(dims))
+    ctx = wmg.Context(dims)
+    ctx.load_gauge(torch.from_numpy(synth.gauge_field(dims, w["eps"], w["gauge_seed"])).cuda())
+    ctx.set_mass(masses[-1])
+    ctx.setup(wmg.default_params(nvec=[w["nvec"]], block=[w["block"]], prec_sloppy=wmg.PREC_SINGLE))
+    m = args.probe_mass if args.probe_mass is not None else masses[0]
+    ctx.set_mass(m)
+    nc, n = ctx.level_info(1)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    fi = torch.randn(nr * 12 * V, dtype=torch.complex64, device="cuda", generator=g)
+    fo = torch.zeros_like(fi)
+    ci = torch.randn(nr * nc * n, dtype=torch.complex64, device="cuda", generator=g)
+    co = torch.zeros_like(ci)
+    b = torch.from_numpy(synth.point_sources(dims, nr)).cuda()
+    x = torch.zeros_like(b)
+    ops = {
+        "dslash": lambda: ctx.apply_D(wmg.PREC_SINGLE, fi, fo, nr),
+        "restrict": lambda: ctx.restrict(0, wmg.PREC_SINGLE, fi, co, nr),
+        "prolong": lambda: ctx.prolong(0, wmg.PREC_SINGLE, ci, fo, nr),
+        "coarse": lambda: ctx.apply_coarse(1, wmg.PREC_HALF, ci, co, nr),
+        "schur": lambda: ctx.apply_coarse_schur(1, wmg.PREC_HALF, ci, co, nr),
+    }
+    for f in ops.values():
+        f()
+    if args.probe_solve:
+        ctx.solve(b, x, nr)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("probe")
+    for f in ops.values():
+        for _ in range(args.probe_reps):
+            f()
+    if args.probe_solve:
+        ctx.solve(b, x, nr)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    res = {"mass": m}
+    for k, f in ops.items():
+        reps = 50
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            f()
+        e1.record()
+        torch.cuda.synchronize()
+        res[k + "_us_per_call"] = e0.elapsed_time(e1) * 1e3 / reps
+    print(json.dumps(res))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -502,12 +681,16 @@ def main():
     ap.add_argument("--masses", default=None, help="comma-separated masses (default: the oracle's)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--record-counts", nargs="?", const=OPCOUNTS, default=None, metavar="PATH",
-                    help="write the step's operation counts (for --impl reference) to PATH")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--probe", action="store_true", help="run the hot kernels in an NVTX range (profiling)")
+    ap.add_argument("--probe-reps", type=int, default=2)
+    ap.add_argument("--probe-mass", type=float, default=None)
+    ap.add_argument("--probe-solve", action="store_true")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
-    if args.impl == "reference":
+    if args.probe:
+        run_probe(args, w)
+    elif args.impl == "reference":
         run_reference(args, w)
     else:
         run_gpu(args, w)

@@ -213,6 +213,15 @@ wmg_status wmg_solve(wmg_ctx* ctx, const double* b_host, double* x_host, int nrh
 wmg_status wmg_solve_dev(wmg_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, wmg_info* info);
 /* The same outer solver without preconditioner (FP64), for comparison. */
 wmg_status wmg_solve_plain_dev(wmg_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, wmg_info* info);
+/* Unpreconditioned baseline (the CG of Sec. 3's comparison, on the normal equations): CG on
+ * D^dag D x = D^dag b in FP64 (CGLS form; D^dag = gamma_5 D gamma_5) at the context's mass, each
+ * right-hand side to |b - D x| <= tol |b| (tol of the last setup, else 1e-10) with the true
+ * residual checked at the end and the iteration restarted from x while it is above tol.  Needs
+ * only the gauge field (no hierarchy).  b, x: canonical device spinors.  info[k].iters = CG
+ * iterations (two operator applications each), info[k].reliable_updates = true-residual
+ * evaluations.  maxit caps the CG iterations; WMG_ENOCONV if a right-hand side missed tol within
+ * it.  Synchronises. */
+wmg_status wmg_solve_cgnr_dev(wmg_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, int maxit, wmg_info* info);
 
 /* ---- operator-level entry points (native device layouts, stream-ordered) ---- */
 

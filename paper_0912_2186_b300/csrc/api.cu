@@ -473,6 +473,20 @@ wmg_status wmg_solve_plain_dev(wmg_ctx* c, const double* b, double* x, int nrhs,
   return solve_dev_impl(c, b, x, nrhs, info, false);
 }
 
+wmg_status wmg_solve_cgnr_dev(wmg_ctx* c, const double* b, double* x, int nrhs, int maxit, wmg_info* info) {
+  if (!c || !b || !x || nrhs < 1 || maxit < 1) return WMG_EINVAL;
+  if (!c->have_gauge) return WMG_ESTATE;
+  const size_t V = c->fine.V;
+  wmg_status worst = WMG_OK;
+  for (int r0 = 0; r0 < nrhs; r0 += kMaxRhs) {
+    const int nr = std::min(kMaxRhs, nrhs - r0);
+    const wmg_status st = cgnr_fine(c, b + V * 24 * r0, x + V * 24 * r0, nr, maxit, info ? info + r0 : nullptr);
+    if (st != WMG_OK && st != WMG_ENOCONV) return st;
+    if (st != WMG_OK) worst = st;
+  }
+  return worst;
+}
+
 wmg_status wmg_solve(wmg_ctx* c, const double* b_host, double* x_host, int nrhs, wmg_info* info) {
   if (!c || !b_host || !x_host || nrhs < 1) return WMG_EINVAL;
   const size_t bytes = (size_t)c->fine.V * 12 * sizeof(cd) * nrhs;

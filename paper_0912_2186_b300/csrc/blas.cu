@@ -100,6 +100,16 @@ __global__ void k_scale_inv_sqrt(void* x, size_t n, const double* nrm2, int stri
   WMG_GRID_LOOP(i) a[i] = s * a[i];
 }
 
+// y = gamma_5 x on native fine spinors: the components of spins 2 and 3 (chunks 3..5, the second
+// half of each right-hand side's n complex numbers) change sign
+template <typename R>
+__global__ void k_gamma5(const void* x_, void* y_, size_t n) {
+  const int r = blockIdx.y;
+  const cpx<R>* x = vec<R>(x_, n, r);
+  cpx<R>* y = vec<R>(y_, n, r);
+  WMG_GRID_LOOP(i) y[i] = i < n / 2 ? x[i] : -x[i];
+}
+
 // x += alpha r and (update_r) r -= alpha q, alpha = red[0..1] / red[2] per rhs
 template <typename R>
 __global__ void k_mr_update(void* x_, void* r_, const void* q_, size_t n, const double* red, const int* active,
@@ -422,6 +432,12 @@ void blas_norm2(int prec, const void* a, size_t n, int nrhs, const RedBuf& rb, c
   count_launch();
   dim3 g(blas_blocks(n), nrhs);
   WMG_BY_PREC(prec, k_norm2, <<<g, kBlasThreads, 0, s>>>(a, n, rb));
+}
+
+void blas_gamma5(int prec, const void* x, void* y, size_t n, int nrhs, cudaStream_t s) {
+  count_launch();
+  dim3 g(blas_blocks(n), nrhs);
+  WMG_BY_PREC(prec, k_gamma5, <<<g, kBlasThreads, 0, s>>>(x, y, n));
 }
 
 void blas_scale_inv_sqrt(int prec, void* x, size_t n, int nrhs, const double* nrm2, int stride, cudaStream_t s) {

@@ -46,10 +46,12 @@ struct LevelData {
   long long eo_version[2] = {-1, -1};
   std::vector<int> eo_idx_up[2];
   const void* eo_idx_ptr[2] = {nullptr, nullptr};
-  // precomputed odd-site pass -A_oo^-1 A_oe (FP16 tensor-core copy) for one mass shift
-  double eoB_shift = 0.0;
+  // precomputed odd-site pass -A_oo^-1 A_oe (FP16 tensor-core copies), one entry per mass shift
+  std::vector<double> eoB_shift;
   long long eoB_version = -1;
   const void* eoB_ptr = nullptr;
+  std::vector<int> eoB_mask_up;  // per-entry right-hand-side masks last uploaded
+  const void* eoB_mask_ptr = nullptr;
   size_t nvec_elems() const { return (size_t)g.V * ndof; }  // complex numbers per field
 };
 

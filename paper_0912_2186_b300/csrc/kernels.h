@@ -51,6 +51,8 @@ void blas_dot_norm(int prec, const void* a, const void* b, size_t n, int nrhs, c
 void blas_norm2(int prec, const void* a, size_t n, int nrhs, const RedBuf& rb, cudaStream_t s);
 // x[r] *= scale[r] (scale double, per rhs; skip where scale pointer entry is not finite)
 void blas_scale_inv_sqrt(int prec, void* x, size_t n, int nrhs, const double* norm2, int stride, cudaStream_t s);
+// y = gamma_5 x for native fine spinors (n = 12 V complex per rhs; y may alias x)
+void blas_gamma5(int prec, const void* x, void* y, size_t n, int nrhs, cudaStream_t s);
 // y = x - y  (y := x - y)
 void blas_xmy(int prec, const void* x, void* y, size_t n, int nrhs, cudaStream_t s);
 // y = x + y

@@ -427,8 +427,12 @@ static bool eo_usable(const wmg_ctx* c, int l) { return c->prm.coarse_eo && eo_p
 struct EoTable {
   const void* inv;
   const int* idx;
-  const void* B16 = nullptr;  // precomputed odd-site pass (single-shift batches) or null
-  const float* sB = nullptr;
+  int nB = 0;                   // entries of the precomputed odd-site pass in use (0: none)
+  const char* B16 = nullptr;    // entry e at B16 + e * Bstride
+  size_t Bstride = 0;
+  const float* sB = nullptr;    // entry e at sB + e * V / 2
+  const int* Bmask = nullptr;   // launch i's right-hand sides: Bmask[i * kMaxRhs + r] (null for one launch)
+  std::vector<int> order;       // launch i uses table entry order[i]
 };
 
 // the table entries for the shifts of right-hand sides 0 .. nrhs-1 (computed for shifts not
@@ -511,42 +515,84 @@ static void eo_stencil(wmg_ctx* c, int l, int prec, const void* in, void* out, i
     coarse_apply(prec, L.A[prec], L.g, L.ndof, in, out, nrhs, c->d_shift[l], dagger, nullptr, rb, c->stream, &eo);
 }
 
-// When every right-hand side of the call has the same mass shift and the parity passes run on
-// the tensor-core stencil, the odd-site pass t_o = -A_oo^-1 A_oe x_e is a plain hop stencil with
-// the blocks B_k = -A_oo^-1 A_oe,k, built once per operator and shift (FP32 product of the
-// table's inverse and the hop blocks, then the FP16 fragment copy); otherwise tb->B16 stays null
-// and the pass applies the inverses in its epilogue.
+// When the parity passes run on the tensor-core stencil, the odd-site pass t_o = -A_oo^-1 A_oe x_e
+// is a plain hop stencil with the blocks B_k = -A_oo^-1 A_oe,k of the right-hand side's mass
+// shift: one table entry per distinct shift of the call (FP32 product of the shift's inverse and
+// the hop blocks, then the FP16 fragment copy), built once per operator and shift, and one launch
+// per entry over the right-hand sides with that shift (a mask), so that a right-hand side's
+// arithmetic does not depend on the other shifts in its batch.
 static wmg_status ensure_eoB(wmg_ctx* c, int l, int prec, int nrhs, EoTable* tb) {
-  tb->B16 = nullptr;
-  tb->sB = nullptr;
+  tb->nB = 0;
   if (!c->use_eoB || !eo_mma(c, l, prec)) return WMG_OK;
-  const double sh = c->h_shift[0];
-  for (int r = 1; r < nrhs; ++r)
-    if (c->h_shift[r] != sh) return WMG_OK;
   LevelData& L = c->L[l];
   const int n = L.ndof, Vh = L.g.V / 2;
   const std::string tag = std::to_string(l);
+  std::vector<double> need;
+  for (int r = 0; r < nrhs; ++r)
+    if (std::find(need.begin(), need.end(), c->h_shift[r]) == need.end()) need.push_back(c->h_shift[r]);
+  const size_t eb = stencil_mma_words(Vh, n) * 16;
+  std::vector<double>& tab = L.eoB_shift;
+  if (L.eoB_version != L.op_version) tab.clear();
+  std::vector<double> missing;
+  for (double v : need)
+    if (std::find(tab.begin(), tab.end(), v) == tab.end()) missing.push_back(v);
+  auto it = c->ws.find("eoB16_" + tag);
+  const size_t cap = it == c->ws.end() ? 0 : it->second.second / eb;
+  if (tab.size() + missing.size() > cap) {
+    tab.clear();
+    missing = need;
+  }
+  const size_t want = std::max(cap, tab.size() + missing.size());
   void *B16, *sB;
-  TRY(ws_get(c, "eoB16_" + tag, stencil_mma_words(Vh, n) * 16, &B16));
-  TRY(ws_get(c, "eoBs_" + tag, (size_t)Vh * sizeof(float), &sB));
-  if (L.eoB_version != L.op_version || L.eoB_shift != sh || L.eoB_ptr != B16) {
+  TRY(ws_get(c, "eoB16_" + tag, want * eb, &B16));
+  TRY(ws_get(c, "eoBs_" + tag, want * Vh * sizeof(float), &sB));
+  if (B16 != L.eoB_ptr && !tab.empty()) {  // the buffer moved: rebuild what this call needs
+    tab.clear();
+    missing = need;
+  }
+  if (!missing.empty()) {
     void* Bt;
     TRY(ws_get(c, "eoBt_" + tag, (size_t)Vh * 9 * n * n * sizeof(cf), &Bt));
-    const std::vector<double>& tab = L.eo_shift[prec];
-    const size_t e = (size_t)(std::find(tab.begin(), tab.end(), sh) - tab.begin());
-    const void* inv_e = (const char*)tb->inv + e * eo_inverse_bytes(prec, L.g, n);
-    {
-      ProfScope ps(c, PROF_CGNR, 0);
+    const std::vector<double>& inv_tab = L.eo_shift[prec];
+    ProfScope ps(c, PROF_CGNR, 0);
+    for (double sh : missing) {
+      const size_t ei = (size_t)(std::find(inv_tab.begin(), inv_tab.end(), sh) - inv_tab.begin());
+      const void* inv_e = (const char*)tb->inv + ei * eo_inverse_bytes(prec, L.g, n);
+      const size_t e = tab.size();
       eo_hop_inverse(L.A[WMG_PREC_SINGLE], inv_e, L.g, n, Bt, c->stream);
-      stencil_to_mma(WMG_PREC_SINGLE, Bt, Vh, n, (float*)sB, B16, c->stream);
+      stencil_to_mma(WMG_PREC_SINGLE, Bt, Vh, n, (float*)sB + e * Vh, (char*)B16 + e * eb, c->stream);
+      tab.push_back(sh);
     }
-    TRY(check(c, "even-odd odd-site operator"));
-    L.eoB_version = L.op_version;
-    L.eoB_shift = sh;
-    L.eoB_ptr = B16;
   }
-  tb->B16 = B16;
+  TRY(check(c, "even-odd odd-site operator"));
+  L.eoB_version = L.op_version;
+  L.eoB_ptr = B16;
+  // the entries in the order of `need`, and their right-hand-side masks
+  std::vector<int> order(need.size());
+  for (size_t i = 0; i < need.size(); ++i)
+    order[i] = (int)(std::find(tab.begin(), tab.end(), need[i]) - tab.begin());
+  tb->nB = (int)need.size();
+  tb->B16 = (const char*)B16;
+  tb->Bstride = eb;
   tb->sB = (const float*)sB;
+  tb->Bmask = nullptr;
+  if (need.size() > 1) {
+    std::vector<int> mask((size_t)kMaxRhs * need.size(), 0);
+    for (size_t i = 0; i < need.size(); ++i)
+      for (int r = 0; r < nrhs; ++r) mask[i * kMaxRhs + r] = c->h_shift[r] == need[i];
+    int* dm;
+    TRY(ws_get(c, "eoBm_" + tag, (size_t)kMaxRhs * kMaxRhs * sizeof(int), (void**)&dm));
+    if (mask != L.eoB_mask_up || dm != L.eoB_mask_ptr) {
+      for (size_t off = 0; off < mask.size(); off += kRingInts) {
+        const size_t cnt = std::min(mask.size() - off, (size_t)kRingInts);
+        TRY(ring_upload(c, dm + off, mask.data() + off, cnt * sizeof(int)));
+      }
+      L.eoB_mask_up = mask;
+      L.eoB_mask_ptr = dm;
+    }
+    tb->Bmask = dm;
+  }
+  tb->order = order;
   return WMG_OK;
 }
 
@@ -557,14 +603,18 @@ static void schur_op(wmg_ctx* c, int l, int prec, const EoTable& tb, const void*
   StencilEo hop;  // t_o = -A_oo^-1 A_oe in_e
   hop.parity = 1;
   hop.hop_only = 1;
-  if (eo_mma(c, l, prec)) {
-    if (tb.B16) {  // -A_oo^-1 A_oe precomputed for the batch's one shift
-      hop.opB = tb.B16;
-      hop.sB = tb.sB;
-    } else {  // the tensor-core pass applies the block inverses in its epilogue
-      hop.inv = tb.inv;
-      hop.inv_idx = tb.idx;
+  if (eo_mma(c, l, prec) && tb.nB > 0) {
+    // -A_oo^-1 A_oe precomputed per shift: one launch per shift of the call
+    const int Vh = L.g.V / 2;
+    for (int i = 0; i < tb.nB; ++i) {
+      hop.opB = tb.B16 + (size_t)tb.order[i] * tb.Bstride;
+      hop.sB = tb.sB + (size_t)tb.order[i] * Vh;
+      coarse_apply_mma(L.A16, L.sA, L.g, L.ndof, in, t, nrhs, c->d_shift[l], dagger,
+                       tb.Bmask ? tb.Bmask + (size_t)i * kMaxRhs : nullptr, nullptr, c->stream, &hop, c->d_err);
     }
+  } else if (eo_mma(c, l, prec)) {
+    hop.inv = tb.inv;  // the tensor-core pass applies the block inverses in its epilogue
+    hop.inv_idx = tb.idx;
     eo_stencil(c, l, prec, in, t, nrhs, dagger, hop, nullptr);
   } else {
     eo_stencil(c, l, prec, in, t, nrhs, dagger, hop, nullptr);
@@ -724,8 +774,10 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
     std::snprintf(key, sizeof key, "cg%d/%d/%d/%p/%p/%p/%p/%p/%p/%p/%p/%p/%p/%.17g/%d/%d/%p/%p/%p/%p/%p", l, prec,
                   nrhs, L.A[prec], (void*)L.A16, x, r, p, q, z, (void*)c->d_shift[l], (void*)c->red_partial,
                   (void*)c->res, cg.tol2, c->prm.coarse_maxit * 64 + chunk, eo ? 1 : 0, tb.inv, (const void*)tb.idx,
-                  t, tb.B16, (const void*)tb.sB);
-    auto it = c->graphs.find(key);
+                  t, (const void*)tb.B16, (const void*)(size_t)(tb.nB * 1000 + (tb.Bmask ? 1 : 0)));
+    std::string gkey(key);
+    for (int e : tb.order) gkey += "/" + std::to_string(e);  // the odd-site launches' table entries
+    auto it = c->graphs.find(gkey);
     if (it == c->graphs.end()) {
       if (c->graphs.size() > 64) TRY(clear_graphs(c));
       cudaGraph_t parent;
@@ -757,7 +809,7 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
       if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, parent, 0);
       cudaGraphDestroy(parent);
       if (e != cudaSuccess) return fail(c, e, "cgnr graph capture");
-      it = c->graphs.emplace(key, std::make_pair(ge, 0LL)).first;
+      it = c->graphs.emplace(gkey, std::make_pair(ge, 0LL)).first;
     }
     CU(c, cudaGraphLaunch(it->second.first, s));
   } else {
@@ -1168,6 +1220,133 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
     }
   }
   return WMG_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// Unpreconditioned baseline (Sec. 3 compares MG with CG): CG on the normal equations of the fine
+// operator in FP64, the CGLS form of the coarsest solve applied to D with D^dag = gamma_5 D gamma_5:
+// x = 0, r = b, z = D^dag r, p = z; per iteration q = D p, alpha = |z|^2 / |q|^2, x += alpha p,
+// r -= alpha q, z = D^dag r, beta = |z'|^2 / |z|^2, p = z + beta p, until |r| <= tol |b| per
+// right-hand side.  Then the true residual b - D x; a right-hand side above tol restarts from its
+// x (the others keep theirs) while the iteration cap allows.  Every right-hand side is iterated
+// independently.  info.iters counts CG iterations (two operator applications each) and
+// info.reliable_updates the true-residual evaluations.
+// ------------------------------------------------------------------------------------
+wmg_status cgnr_fine(wmg_ctx* c, const double* b_canon, double* x_canon, int nrhs, int maxit, wmg_info* info) {
+  const int prec = WMG_PREC_DOUBLE;
+  const int V = c->fine.V;
+  const size_t n = (size_t)V * 12;
+  cudaStream_t s = c->stream;
+  auto t_start = std::chrono::steady_clock::now();
+  TRY(ensure_reductions(c, nrhs));
+  TRY(set_rhs_scalars(c, nullptr, nrhs));
+  void *b, *x, *r, *p, *q, *z, *t;
+  TRY(vec_ws(c, 0, "cgf_b", prec, nrhs, &b));
+  TRY(vec_ws(c, 0, "cgf_x", prec, nrhs, &x));
+  TRY(vec_ws(c, 0, "cgf_r", prec, nrhs, &r));
+  TRY(vec_ws(c, 0, "cgf_p", prec, nrhs, &p));
+  TRY(vec_ws(c, 0, "cgf_q", prec, nrhs, &q));
+  TRY(vec_ws(c, 0, "cgf_z", prec, nrhs, &z));
+  TRY(vec_ws(c, 0, "cgf_t", prec, nrhs, &t));
+  CgScalars cg;
+  cg.zz = res_slot(c, RES_CGZZ);
+  cg.rr = res_slot(c, RES_CGRR);
+  cg.qq = res_slot(c, RES_CGQQ);
+  cg.bb = res_slot(c, RES_CGBB);
+  cg.done = c->d_cgint;
+  cg.iters = c->d_cgint + kMaxRhs;
+  cg.tol2 = c->prm.tol * c->prm.tol;
+  pack_spinor(prec, b_canon, b, V, nrhs, s);
+  blas_zero(prec, x, n, nrhs, s);
+  blas_norm2(prec, b, n, nrhs, redbuf(c, RES_CGBB), s);
+  std::vector<double> bb, tr;
+  TRY(download(c, cg.bb, nrhs, bb));
+  // out = D^dag in = gamma_5 D gamma_5 in, |out|^2 per rhs (gamma_5 is unitary)
+  auto dag = [&](const void* in, void* out, const RedBuf* rb) {
+    blas_gamma5(prec, in, t, n, nrhs, s);
+    {
+      ProfScope ps(c, PROF_DSLASH_64, dslash_bytes(c, prec, nrhs, false), nrhs);
+      dslash(prec, out, t, nullptr, c->gauge[prec], c->fine, c->d_mass, nullptr, nrhs, 1, rb, s);
+    }
+    blas_gamma5(prec, out, out, n, nrhs, s);
+  };
+  RedBuf rqq{c->red_partial, c->red_counter, cg.qq}, rrr{c->red_partial, c->red_counter, cg.rr};
+  RedBuf rtr = redbuf(c, RES_R64);
+  std::vector<int> run(nrhs, 0), its(nrhs, 0), evals(nrhs, 0), conv(nrhs, 0);
+  for (int i = 0; i < nrhs; ++i) run[i] = bb[i] > 0.0, conv[i] = !(bb[i] > 0.0);
+  int total = 0;
+  while (true) {
+    bool any = false;
+    for (int i = 0; i < nrhs; ++i) any = any || run[i];
+    if (!any || total >= maxit) break;
+    // (re)start the running right-hand sides from x: r = b - D x, z = D^dag r, p = z
+    TRY(upload_ints(c, c->d_mask, run));
+    dslash(prec, r, x, b, c->gauge[prec], c->fine, c->d_mass, nullptr, nrhs, 0, nullptr, s);
+    RedBuf rzz0{c->red_partial, c->red_counter, cg.zz};
+    dag(r, z, &rzz0);
+    blas_convert(prec, p, prec, z, n, nrhs, nullptr, s);
+    k_cg_init<<<1, 64, 0, s>>>(cg.done, cg.iters, cg.bb, c->d_mask, nrhs, c->d_flag + 1);
+    count_launch();
+    const int chunk = 16;
+    bool all = false;
+    while (!all && total < maxit) {
+      for (int i = 0; i < chunk; ++i) {
+        const int parity = i & 1;
+        {
+          ProfScope ps(c, PROF_DSLASH_64, dslash_bytes(c, prec, nrhs, false), nrhs);
+          dslash(prec, q, p, nullptr, c->gauge[prec], c->fine, c->d_mass, nullptr, nrhs, 1, &rqq, s);
+        }
+        {
+          ProfScope ps(c, PROF_BLAS, vec_bytes(c, 0, prec, nrhs, 6), nrhs);
+          cg_update(prec, x, r, p, q, n, nrhs, cg, parity, rrr, s);
+        }
+        RedBuf rzz{c->red_partial, c->red_counter, cg.zz + (1 - parity) * nrhs};
+        dag(r, z, &rzz);
+        {
+          ProfScope ps(c, PROF_BLAS, vec_bytes(c, 0, prec, nrhs, 3), nrhs);
+          cg_xpay(prec, p, z, n, nrhs, cg, parity, s);
+        }
+      }
+      total += chunk;
+      CU(c, cudaMemcpyAsync(c->h_pin_i, cg.done, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CU(c, cudaStreamSynchronize(s));
+      all = true;
+      for (int i = 0; i < nrhs; ++i) all = all && c->h_pin_i[i];
+      TRY(check(c, "fine cgnr"));
+    }
+    CU(c, cudaMemcpyAsync(c->h_pin_i, cg.iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(c, cudaStreamSynchronize(s));
+    for (int i = 0; i < nrhs; ++i)
+      if (run[i]) its[i] += c->h_pin_i[i];
+    // true residuals of the running right-hand sides
+    {
+      ProfScope ps(c, PROF_DSLASH_64, dslash_bytes(c, prec, nrhs, true), nrhs);
+      dslash(prec, r, x, b, c->gauge[prec], c->fine, c->d_mass, nullptr, nrhs, 1, &rtr, s);
+    }
+    TRY(download(c, rtr.result, nrhs, tr));
+    for (int i = 0; i < nrhs; ++i) {
+      if (!run[i]) continue;
+      evals[i] += 1;
+      if (tr[i] <= cg.tol2 * bb[i]) run[i] = 0, conv[i] = 1;
+    }
+  }
+  unpack_spinor(prec, x, x_canon, V, nrhs, s);
+  CU(c, cudaStreamSynchronize(s));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  bool allc = true;
+  for (int i = 0; i < nrhs; ++i) {
+    if (info) {
+      info[i] = wmg_info{};
+      info[i].iters = its[i];
+      info[i].reliable_updates = evals[i];
+      info[i].converged = conv[i];
+      info[i].true_resid = bb[i] > 0.0 ? std::sqrt(std::max(tr.empty() ? 0.0 : tr[i], 0.0) / bb[i]) : 0.0;
+      info[i].seconds = secs;
+    }
+    allc = allc && conv[i];
+  }
+  TRY(check(c, "fine cgnr"));
+  return allc ? WMG_OK : WMG_ENOCONV;
 }
 
 // All right-hand sides of one call, admitted at once; results unpacked into x (canonical).

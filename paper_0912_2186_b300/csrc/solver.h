@@ -42,6 +42,8 @@ struct SlotSource {
 };
 wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg);
 // b_canon, x_canon: canonical device spinors, nrhs <= 64
+// unpreconditioned CG on the fine normal equations (FP64 baseline); maxit caps CG iterations
+wmg_status cgnr_fine(wmg_ctx* c, const double* b_canon, double* x_canon, int nrhs, int maxit, wmg_info* info);
 wmg_status fgcr(wmg_ctx* c, const double* b_canon, double* x_canon, int nrhs, const double* masses, wmg_info* info,
                 bool use_mg);
 

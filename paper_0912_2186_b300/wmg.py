@@ -98,6 +98,7 @@ def load():
         "wmg_solve": (i, [vp, vp, vp, i, P(Info)]),
         "wmg_solve_dev": (i, [vp, vp, vp, i, P(Info)]),
         "wmg_solve_plain_dev": (i, [vp, vp, vp, i, P(Info)]),
+        "wmg_solve_cgnr_dev": (i, [vp, vp, vp, i, i, P(Info)]),
         "wmg_pack_spinor": (i, [vp, i, vp, vp, i]),
         "wmg_unpack_spinor": (i, [vp, i, vp, vp, i]),
         "wmg_apply_D": (i, [vp, i, vp, vp, i]),
@@ -267,6 +268,13 @@ class Context:
         else:
             f = self.lib.wmg_solve_plain_dev if plain else self.lib.wmg_solve_dev
             st = f(self.h, _ptr(b), _ptr(x), int(nrhs), info)
+        self._check(st, allow=(ENOCONV,))
+        return st, [i.as_dict() for i in info]
+
+    def solve_cgnr(self, b, x, nrhs, maxit=100000):
+        """Unpreconditioned FP64 CG on the normal equations (baseline); b, x canonical CUDA tensors."""
+        info = (Info * nrhs)()
+        st = self.lib.wmg_solve_cgnr_dev(self.h, _ptr(b), _ptr(x), int(nrhs), int(maxit), info)
         self._check(st, allow=(ENOCONV,))
         return st, [i.as_dict() for i in info]
 

@@ -62,12 +62,12 @@ def test_setup_matches_oracle_setup(W):
     ctx = W.Context(dims)
     ctx.load_gauge(U)
     ctx.set_mass(m)
-    p = W.default_params(nvec=[N], prec_sloppy=W.PREC_DOUBLE, coarse_tol=1e-12, coarse_maxit=20000)
+    p = W.default_params(nvec=[N], prec_sloppy=W.PREC_DOUBLE, coarse_tol=1e-12, coarse_maxit=20000, setup_relax=20)
     ctx.setup(p, starts)
     Pg = ctx.export_nullvecs(0, N).reshape((N,) + starts.shape[1:])
     op = mg.WilsonOp(U, m)
     prm = solvers.CycleParams(coarse_tol=1e-12, coarse_maxit=20000, coarse_eo=True)
-    Po, Ao, _ = solvers.setup_level(op, block, starts, passes=5, relax=20, params=prm)
+    Po, Ao, _ = solvers.setup_level(op, block, starts, passes=p.setup_passes, relax=p.setup_relax, params=prm)
     sine = max_block_angle_sine(Pg, Po, block)
     assert sine < 1e-6, sine
     b = synth.gaussian_spinors(dims, 1, 13)

@@ -265,3 +265,23 @@ def test_even_odd_coarsest_solve(W, prec):
             _, i1 = ctx.solve(dev(b[2:3]), x1, 1)
             assert np.array_equal(host(x1)[0], xs[2]) and i1[0]["iters"] == info[2]["iters"]
     assert all(abs(a - b) <= 2 for a, b in zip(its[0], its[1]))
+
+
+def test_cgnr_fine_baseline(W):
+    """The unpreconditioned baseline: FP64 CG on the fine normal equations meets the 1e-10 true
+    residual with the oracle's operator, takes the oracle CGNR's iteration count to within 2 % (+2),
+    and many more iterations than MG-GCR."""
+    ctx, U, p = _ctx(W, CFG1, 0)
+    b = synth.gaussian_spinors(CFG1["dims"], 2, 19)
+    x = dev(np.zeros_like(b))
+    st, info = ctx.solve_cgnr(dev(b), x, 2)
+    xs = host(x)
+    op = mg.WilsonOp(U, CFG1["m"])
+    for r in range(2):
+        assert info[r]["converged"]
+        assert oracle_resid(U, CFG1["m"], b[r], xs[r]) <= 1.05e-10
+    _, it_o = solvers.cgnr(op, b[0], 1e-10, 100000)
+    assert abs(info[0]["iters"] - it_o) <= 2 + 0.02 * it_o, (info[0]["iters"], it_o)
+    xm = dev(np.zeros_like(b))
+    _, im = ctx.solve(dev(b), xm, 2)
+    assert info[0]["iters"] > 5 * im[0]["iters"]
