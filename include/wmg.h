@@ -170,6 +170,18 @@ wmg_status wmg_destroy(wmg_ctx* ctx);
 wmg_status wmg_load_gauge(wmg_ctx* ctx, const double* U_host);
 wmg_status wmg_load_gauge_dev(wmg_ctx* ctx, const double* U_dev);
 
+/* Link storage of the FP32 fine operator (the cycle's smoother and the sloppy Krylov operator):
+ * 12 reals (rows 0 and 1, row 2 = conj(row0 x row1); the default) or 8 reals (Table 2's "8
+ * floats"): elements (0,1), (0,2), (1,0) and the phases of (0,0) and (2,0), the rest rebuilt from
+ * unitarity and det U = 1 (moduli from the row-0 and column-0 norms, (1,1), (1,2), (2,1), (2,2) by
+ * Cramer's rule from row orthogonality and the cofactor relations of U^-1 = U^dag).  The 8-real
+ * links are made from the FP64 links at every gauge load; FP64 operators, the Galerkin product and
+ * the no-alloc residual keep 12 reals.  A field with a link whose (0,1) and (0,2) elements (nearly)
+ * vanish, |U_01|^2 + |U_02|^2 < 1e-6 (the free field, for one), is not representable that way: for
+ * such a field the FP32 operator keeps the 12-real links.  reals: 12 or 8, else WMG_EINVAL.
+ * Synchronises when a field is loaded. */
+wmg_status wmg_set_gauge_compression(wmg_ctx* ctx, int reals);
+
 /* Set the Wilson mass m (Sec. 2, the (4 + m) term).  An existing hierarchy's coarse
  * operators are shifted by (m - m_setup) on their diagonal blocks, which is exact
  * because P^dag P = 1. */
@@ -182,6 +194,20 @@ wmg_status wmg_set_mass(wmg_ctx* ctx, double m);
  * generator keyed by p->seed (p->seed + 1 for the second level; Box-Muller in FP32), real
  * and imaginary parts in canonical order.  Synchronises. */
 wmg_status wmg_setup(wmg_ctx* ctx, const wmg_params* p, const double* starts_host);
+
+/* Setup amortisation across gauge updates (Sec. 4: the coarse operators of a slowly evolving
+ * field, as in HMC, reuse the near-null subspace for several steps with an incremental update).
+ * wmg_update_gauge loads a new U (canonical layout, as wmg_load_gauge) but keeps the hierarchy's
+ * block-orthonormal vectors P of every level and rebuilds only the Galerkin coarse operators
+ * D^ = P^dag D(U_new) P (at the setup's mass).  wmg_refresh_setup then runs `passes` improvement
+ * passes of the adaptive setup on the current field, level by level, from the current subspace
+ * (the starting vectors are the N fields of P, field k holding basis vector k of every block):
+ * psi_k <- K(psi_k) with the two-level cycle of the current hierarchy, normalised, P and D^ rebuilt
+ * after each pass.  WMG_ESTATE without a hierarchy, or when only FP16 fine null vectors are kept
+ * (prec_nullvec HALF; set up again instead).  Both synchronise. */
+wmg_status wmg_update_gauge(wmg_ctx* ctx, const double* U_host);
+wmg_status wmg_update_gauge_dev(wmg_ctx* ctx, const double* U_dev);
+wmg_status wmg_refresh_setup(wmg_ctx* ctx, int passes);
 
 /* Replace the near-null vectors of `level` (0: fine spinors, canonical layout;
  * 1: coarse fields of the level-1 lattice) by the given host vectors, then

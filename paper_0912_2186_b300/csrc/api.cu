@@ -53,6 +53,7 @@ size_t context_device_bytes(const wmg_ctx* c) {
   const size_t V = c->fine.V;
   if (c->gauge[0]) b += V * 4 * 6 * sizeof(cd);
   if (c->gauge[1]) b += V * 4 * 6 * sizeof(cf);
+  if (c->gauge8) b += gauge8_bytes((int)V);
   for (int l = 0; l < WMG_MAX_LEVELS; ++l) {
     const LevelData& L = c->L[l];
     const size_t pe = L.P[0] ? L.nvec_elems() * L.bk.N : 0;
@@ -151,6 +152,17 @@ wmg_status trim_after_setup(wmg_ctx* c) {
     c->ws.clear();
   }
   return WMG_OK;
+}
+
+// 8-real links of the loaded field, and whether every link is representable (else the FP32
+// operator keeps the 12-real links for this field)
+wmg_status make_gauge8(wmg_ctx* c) {
+  CU(c, cudaMemsetAsync(c->d_flag + 2, 0, sizeof(int), c->stream));
+  pack_gauge8(c->gauge[0], c->gauge8, c->fine.V, c->d_flag + 2, c->stream);
+  CU(c, cudaMemcpyAsync(c->h_pin_i, c->d_flag + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(c, cudaStreamSynchronize(c->stream));
+  c->gauge8_ok = c->h_pin_i[0] == 0;
+  return check(c, "pack_gauge8");
 }
 
 }  // namespace
@@ -274,7 +286,7 @@ wmg_status wmg_destroy(wmg_ctx* c) {
   for (auto& kv : c->ws) cudaFree(kv.second.first);
   c->ws.clear();
   void* ptrs[] = {c->d_mass, c->d_shift[1], c->d_shift[2], c->d_active, c->d_mask, c->d_flag, c->d_cgint,
-                  c->red_counter, c->res, c->red_partial, c->gauge[0], c->gauge[1], c->d_err};
+                  c->red_counter, c->res, c->red_partial, c->gauge[0], c->gauge[1], c->d_err, c->gauge8};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pin) cudaFreeHost(c->h_pin);
@@ -292,6 +304,7 @@ wmg_status wmg_load_gauge_dev(wmg_ctx* c, const double* U) {
   free_hierarchy(c);
   pack_gauge(WMG_PREC_DOUBLE, U, c->gauge[0], c->fine.V, c->stream);
   pack_gauge(WMG_PREC_SINGLE, U, c->gauge[1], c->fine.V, c->stream);
+  if (c->gauge8) TRY(make_gauge8(c));
   TRY(check(c, "pack_gauge"));
   c->have_gauge = true;
   return WMG_OK;
@@ -305,6 +318,23 @@ wmg_status wmg_load_gauge(wmg_ctx* c, const double* U_host) {
   CU(c, cudaMemcpyAsync(st, U_host, bytes, cudaMemcpyHostToDevice, c->stream));
   TRY(wmg_load_gauge_dev(c, (const double*)st));
   CU(c, cudaStreamSynchronize(c->stream));
+  return WMG_OK;
+}
+
+wmg_status wmg_set_gauge_compression(wmg_ctx* c, int reals) {
+  if (!c || (reals != 12 && reals != 8)) return WMG_EINVAL;
+  if (reals == 8 && !c->gauge8) {
+    CU(c, cudaMalloc(&c->gauge8, gauge8_bytes(c->fine.V)));
+    c->gauge8_ok = false;
+    if (c->have_gauge) TRY(make_gauge8(c));
+  }
+  if (reals == 12 && c->gauge8) {
+    CU(c, cudaStreamSynchronize(c->stream));
+    cudaFree(c->gauge8);
+    c->gauge8 = nullptr;
+  }
+  c->gauge_compress = reals;
+  clear_graphs(c);
   return WMG_OK;
 }
 
@@ -352,6 +382,56 @@ wmg_status wmg_setup(wmg_ctx* c, const wmg_params* p, const double* starts_host)
   CU(c, cudaStreamSynchronize(c->stream));
   c->have_hier = true;
   TRY(trim_after_setup(c));
+  return WMG_OK;
+}
+
+wmg_status wmg_update_gauge_dev(wmg_ctx* c, const double* U) {
+  if (!c || !U) return WMG_EINVAL;
+  if (!c->have_hier) return WMG_ESTATE;
+  for (int l = 0; l + 1 < c->nlev; ++l)
+    if (!c->L[l].P[c->prm.prec_sloppy] || !c->L[l].P[0]) {
+      c->err = "update_gauge: the hierarchy keeps only FP16 fine null vectors (set up again instead)";
+      return WMG_ESTATE;
+    }
+  CU(c, cudaStreamSynchronize(c->stream));
+  pack_gauge(WMG_PREC_DOUBLE, U, c->gauge[0], c->fine.V, c->stream);
+  pack_gauge(WMG_PREC_SINGLE, U, c->gauge[1], c->fine.V, c->stream);
+  if (c->gauge8) TRY(make_gauge8(c));
+  TRY(check(c, "pack_gauge"));
+  // the kept near-null subspace, the coarse operators of the new field
+  for (int l = 0; l + 1 < c->nlev; ++l) TRY(galerkin(c, l, c->prm.prec_sloppy));
+  CU(c, cudaStreamSynchronize(c->stream));
+  return WMG_OK;
+}
+
+wmg_status wmg_update_gauge(wmg_ctx* c, const double* U_host) {
+  if (!c || !U_host) return WMG_EINVAL;
+  if (!c->have_hier) return WMG_ESTATE;
+  void* st;
+  const size_t bytes = (size_t)c->fine.V * 4 * 9 * sizeof(cd);
+  TRY(ws_get(c, "stage", bytes, &st));
+  CU(c, cudaMemcpyAsync(st, U_host, bytes, cudaMemcpyHostToDevice, c->stream));
+  return wmg_update_gauge_dev(c, (const double*)st);
+}
+
+wmg_status wmg_refresh_setup(wmg_ctx* c, int passes) {
+  if (!c || passes < 0) return WMG_EINVAL;
+  if (!c->have_hier) return WMG_ESTATE;
+  const int prec = c->prm.prec_sloppy;
+  for (int l = 0; l + 1 < c->nlev; ++l) {
+    LevelData& L = c->L[l];
+    if (!L.P[prec] || !L.P[0]) {
+      c->err = "refresh_setup: the hierarchy keeps only FP16 fine null vectors (set up again instead)";
+      return WMG_ESTATE;
+    }
+    // the starting vectors: the N fields of P (field k holds basis vector k of every block)
+    void* vecs;
+    TRY(vec_ws(c, l, "setup_vecs", prec, L.bk.N, &vecs));
+    blas_convert(prec, vecs, WMG_PREC_DOUBLE, L.P[0], L.nvec_elems(), L.bk.N, nullptr, c->stream);
+    if (l > 0) TRY(galerkin(c, l, prec));  // the level's operator follows the refreshed level above
+    TRY(improve_level(c, l, vecs, passes));
+  }
+  CU(c, cudaStreamSynchronize(c->stream));
   return WMG_OK;
 }
 
@@ -527,12 +607,15 @@ wmg_status wmg_apply_D(wmg_ctx* c, int prec, const void* in, void* out, int nrhs
     TRY(ws_get(c, "aD_n_in", (size_t)V * nrhs * sizeof(float), &n_in));
     TRY(ws_get(c, "aD_n_out", (size_t)V * nrhs * sizeof(float), &n_out));
     spinor_to_h(in, h_in, (float*)n_in, V, nrhs, c->stream);
-    dslash_h(1, h_out, (float*)n_out, h_in, (const float*)n_in, nullptr, c->gauge[1], c->fine, c->d_mass, nullptr,
-             nrhs, 0, nullptr, c->stream);
+    const bool g8 = c->gauge_compress == 8 && c->gauge8 && c->gauge8_ok;
+    dslash_h(1, h_out, (float*)n_out, h_in, (const float*)n_in, nullptr, g8 ? c->gauge8 : c->gauge[1], c->fine,
+             c->d_mass, nullptr, nrhs, 0, nullptr, c->stream, g8 ? 8 : 12);
     spinor_from_h(h_out, (const float*)n_out, out, V, nrhs, c->stream);
     return check(c, "apply_D (FP16 storage)");
   }
-  dslash(prec, out, in, nullptr, c->gauge[prec], c->fine, c->d_mass, nullptr, nrhs, 0, nullptr, c->stream);
+  const bool g8 = prec == WMG_PREC_SINGLE && c->gauge_compress == 8 && c->gauge8 && c->gauge8_ok;
+  dslash(prec, out, in, nullptr, g8 ? c->gauge8 : c->gauge[prec], c->fine, c->d_mass, nullptr, nrhs, 0, nullptr,
+         c->stream, g8 ? 8 : 12);
   return check(c, "apply_D");
 }
 

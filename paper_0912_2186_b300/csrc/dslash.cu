@@ -22,6 +22,22 @@ __global__ void k_pack_gauge(const double2* __restrict__ canon, void* __restrict
   }
 }
 
+// native FP64 12-real links -> 8-real FP32 (see load_link8): row 2 rebuilt in FP64, then
+// (a1, a2), (b0, arg a0, arg c0)
+__global__ void k_pack_gauge8(const void* __restrict__ g64, float4* __restrict__ out, int V, int* degenerate) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  for (int mu = 0; mu < 4; ++mu) {
+    cd u[9];
+    load_link<double>(g64, V, mu, v, u);
+    // the 8-real form divides by |a1|^2 + |a2|^2: links where it (nearly) vanishes are flagged
+    if (norm2(u[1]) + norm2(u[2]) < 1e-6) atomicExch(degenerate, 1);
+    out[(size_t)(mu * 2) * V + v] = make_float4((float)u[1].re, (float)u[1].im, (float)u[2].re, (float)u[2].im);
+    out[(size_t)(mu * 2 + 1) * V + v] =
+        make_float4((float)u[3].re, (float)u[3].im, (float)atan2(u[0].im, u[0].re), (float)atan2(u[6].im, u[6].re));
+  }
+}
+
 // canonical [rhs][V][12] <-> native [rhs][6][V][2]
 template <typename R>
 __global__ void k_pack_spinor(const double2* __restrict__ canon, void* __restrict__ out, int V, int nrhs) {
@@ -76,7 +92,7 @@ WMG_D void site_coords_fast(const Geom& g, const DslashDiv& d, int v, int c[4]) 
 // CTA per SM and keeps one block per CTA.)
 template <typename R, int RED> constexpr int dslash_spb() { return RED > 0 && sizeof(R) == 4 ? 4 : 1; }
 
-template <typename R, int RED>
+template <typename R, int RED, int GC>
 __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(void* __restrict__ out,
                                                                         const void* __restrict__ in,
                                                                         const void* __restrict__ b,
@@ -104,11 +120,11 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(void* __
     for (int mu = 0; mu < 4; ++mu) {
       cpx<R> u[9], nb[12];
       const int vf = neighbour(g, v, c, mu, +1);
-      load_link<R>(gauge, g.V, mu, v, u);
+      load_link_gc<R, GC>(gauge, g.V, mu, v, u);
       load_spinor<R>(inr, g.V, vf, nb);
       hop_accumulate<+1>(mu, u, nb, acc);
       const int vb = neighbour(g, v, c, mu, -1);
-      load_link<R>(gauge, g.V, mu, vb, u);
+      load_link_gc<R, GC>(gauge, g.V, mu, vb, u);
       load_spinor<R>(inr, g.V, vb, nb);
       hop_accumulate<-1>(mu, u, nb, acc);
     }
@@ -163,7 +179,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(void* __
 // FP16 neighbour enters the accumulation of its hop.  RED = 2: per rhs {<out, in>, |out|^2}
 // from the FP32 values before rounding.
 // ------------------------------------------------------------------------------------
-template <int IN16, int RED>
+template <int IN16, int RED, int GC>
 __global__ void __launch_bounds__(128) k_dslash_h(void* __restrict__ out16, float* __restrict__ out_norm,
                                                   const void* __restrict__ in, const float* __restrict__ in_norm,
                                                   const void* __restrict__ b, const void* __restrict__ gauge, Geom g,
@@ -187,7 +203,7 @@ __global__ void __launch_bounds__(128) k_dslash_h(void* __restrict__ out16, floa
     for (int mu = 0; mu < 4; ++mu) {
       cpx<float> u[9], nb[12];
       const int vf = neighbour(g, v, c, mu, +1);
-      load_link<float>(gauge, g.V, mu, v, u);
+      load_link_gc<float, GC>(gauge, g.V, mu, v, u);
       if (IN16) {
         load_spinor_h(inr, g.V, vf, nb);
         hop_accumulate_scaled<+1>(mu, u, nb, __ldg(inn + vf), acc);
@@ -196,7 +212,7 @@ __global__ void __launch_bounds__(128) k_dslash_h(void* __restrict__ out16, floa
         hop_accumulate<+1>(mu, u, nb, acc);
       }
       const int vb = neighbour(g, v, c, mu, -1);
-      load_link<float>(gauge, g.V, mu, vb, u);
+      load_link_gc<float, GC>(gauge, g.V, mu, vb, u);
       if (IN16) {
         load_spinor_h(inr, g.V, vb, nb);
         hop_accumulate_scaled<-1>(mu, u, nb, __ldg(inn + vb), acc);
@@ -310,6 +326,12 @@ void pack_gauge(int prec, const double* canon, void* out, int V, cudaStream_t s)
   else k_pack_gauge<float><<<B, T, 0, s>>>((const double2*)canon, out, V);
 }
 
+void pack_gauge8(const void* g64, void* out, int V, int* degenerate, cudaStream_t s) {
+  count_launch();
+  const int T = 256, B = (V + T - 1) / T;
+  k_pack_gauge8<<<B, T, 0, s>>>(g64, (float4*)out, V, degenerate);
+}
+
 void pack_spinor(int prec, const double* canon, void* out, int V, int nrhs, cudaStream_t s) {
   count_launch();
   const size_t n = (size_t)V * nrhs;
@@ -331,7 +353,8 @@ void unpack_spinor(int prec, const void* in, double* canon, int V, int nrhs, cud
 int dslash_blocks(int V) { return (V + kDslashThreads - 1) / kDslashThreads; }
 
 void dslash(int prec, void* out, const void* in, const void* b, const void* gauge, const Geom& g,
-            const double* mass_dev, const int* active, int nrhs, int red, const RedBuf* rb, cudaStream_t s) {
+            const double* mass_dev, const int* active, int nrhs, int red, const RedBuf* rb, cudaStream_t s,
+            int gc) {
   count_launch();
   const int nb = dslash_blocks(g.V);
   const int spb = prec == WMG_PREC_DOUBLE ? dslash_spb<double, 1>() : dslash_spb<float, 1>();
@@ -339,31 +362,40 @@ void dslash(int prec, void* out, const void* in, const void* b, const void* gaug
   const unsigned grid = (unsigned)nb * nrhs, gridr = (unsigned)nbr * nrhs;
   RedBuf r = rb ? *rb : RedBuf{nullptr, nullptr, nullptr};
   const DslashDiv dv{make_fastdiv(g.L[0]), make_fastdiv(g.L[1]), make_fastdiv(g.L[2])};
-#define WMG_DS(R)                                                                                             \
+#define WMG_DS(R, GC)                                                                                         \
   do {                                                                                                        \
-    if (red == 0) k_dslash<R, 0><<<grid, kDslashThreads, 0, s>>>(out, in, b, gauge, g, dv, mass_dev, active, nrhs, nb, r); \
-    else if (red == 1) k_dslash<R, 1><<<gridr, kDslashThreads, 0, s>>>(out, in, b, gauge, g, dv, mass_dev, active, nrhs, nbr, r); \
-    else k_dslash<R, 2><<<gridr, kDslashThreads, 0, s>>>(out, in, b, gauge, g, dv, mass_dev, active, nrhs, nbr, r); \
+    if (red == 0) k_dslash<R, 0, GC><<<grid, kDslashThreads, 0, s>>>(out, in, b, gauge, g, dv, mass_dev, active, nrhs, nb, r); \
+    else if (red == 1) k_dslash<R, 1, GC><<<gridr, kDslashThreads, 0, s>>>(out, in, b, gauge, g, dv, mass_dev, active, nrhs, nbr, r); \
+    else k_dslash<R, 2, GC><<<gridr, kDslashThreads, 0, s>>>(out, in, b, gauge, g, dv, mass_dev, active, nrhs, nbr, r); \
   } while (0)
-  if (prec == WMG_PREC_DOUBLE) WMG_DS(double);
-  else WMG_DS(float);
+  if (prec == WMG_PREC_DOUBLE) WMG_DS(double, 12);
+  else if (gc == 8) WMG_DS(float, 8);
+  else WMG_DS(float, 12);
 #undef WMG_DS
+}
+
+template <int GC>
+static void launch_dslash_h(int in16, void* out16, float* out_norm, const void* in, const float* in_norm,
+                            const void* b, const void* gauge, const Geom& g, const double* mass_dev,
+                            const int* active, int nrhs, int red, const RedBuf& r, cudaStream_t s) {
+  const int nb = dslash_blocks(g.V);
+  const unsigned grid = (unsigned)nb * nrhs;
+  if (in16) {
+    if (red == 2) k_dslash_h<1, 2, GC><<<grid, kDslashThreads, 0, s>>>(out16, out_norm, in, in_norm, b, gauge, g, mass_dev, active, nrhs, nb, r);
+    else k_dslash_h<1, 0, GC><<<grid, kDslashThreads, 0, s>>>(out16, out_norm, in, in_norm, b, gauge, g, mass_dev, active, nrhs, nb, r);
+  } else {
+    if (red == 2) k_dslash_h<0, 2, GC><<<grid, kDslashThreads, 0, s>>>(out16, out_norm, in, in_norm, b, gauge, g, mass_dev, active, nrhs, nb, r);
+    else k_dslash_h<0, 0, GC><<<grid, kDslashThreads, 0, s>>>(out16, out_norm, in, in_norm, b, gauge, g, mass_dev, active, nrhs, nb, r);
+  }
 }
 
 void dslash_h(int in16, void* out16, float* out_norm, const void* in, const float* in_norm, const void* b,
               const void* gauge, const Geom& g, const double* mass_dev, const int* active, int nrhs, int red,
-              const RedBuf* rb, cudaStream_t s) {
+              const RedBuf* rb, cudaStream_t s, int gc) {
   count_launch();
-  const int nb = dslash_blocks(g.V);
-  const unsigned grid = (unsigned)nb * nrhs;
   RedBuf r = rb ? *rb : RedBuf{nullptr, nullptr, nullptr};
-  if (in16) {
-    if (red == 2) k_dslash_h<1, 2><<<grid, kDslashThreads, 0, s>>>(out16, out_norm, in, in_norm, b, gauge, g, mass_dev, active, nrhs, nb, r);
-    else k_dslash_h<1, 0><<<grid, kDslashThreads, 0, s>>>(out16, out_norm, in, in_norm, b, gauge, g, mass_dev, active, nrhs, nb, r);
-  } else {
-    if (red == 2) k_dslash_h<0, 2><<<grid, kDslashThreads, 0, s>>>(out16, out_norm, in, in_norm, b, gauge, g, mass_dev, active, nrhs, nb, r);
-    else k_dslash_h<0, 0><<<grid, kDslashThreads, 0, s>>>(out16, out_norm, in, in_norm, b, gauge, g, mass_dev, active, nrhs, nb, r);
-  }
+  if (gc == 8) launch_dslash_h<8>(in16, out16, out_norm, in, in_norm, b, gauge, g, mass_dev, active, nrhs, red, r, s);
+  else launch_dslash_h<12>(in16, out16, out_norm, in, in_norm, b, gauge, g, mass_dev, active, nrhs, red, r, s);
 }
 
 void mr_update_h(void* x, void* r16, float* rn, const void* q16, const float* qn, int V, int nrhs, const double* red,

@@ -26,13 +26,18 @@ void unpack_spinor(int prec, const void* in, double* canon, int V, int nrhs, cud
 int dslash_blocks(int V);
 // out = D in, or out = b - D in when b != nullptr.  mass_dev[nrhs]: per-rhs Wilson mass.
 // red = 0: none; 1: |out|^2 per rhs into rb->result[rhs]; 2: {Re, Im <out,in>, |out|^2}.
+// gc = 8: FP32 only, `gauge` holds 8-real links (pack_gauge8)
 void dslash(int prec, void* out, const void* in, const void* b, const void* gauge, const Geom& g,
-            const double* mass_dev, const int* active, int nrhs, int red, const RedBuf* rb, cudaStream_t s);
+            const double* mass_dev, const int* active, int nrhs, int red, const RedBuf* rb, cudaStream_t s,
+            int gc = 12);
+// 8-real FP32 links from the native FP64 12-real links; *degenerate (device int) set to 1 if a
+// link has |U_01|^2 + |U_02|^2 < 1e-6 (the 8-real form cannot represent it accurately)
+void pack_gauge8(const void* g64, void* out, int V, int* degenerate, cudaStream_t s);
 // the smoother's FP16 storage (per-site norms, FP32 arithmetic): out16 = [b -] D in with in
 // FP32 native (in16 = 0) or FP16 (in16 = 1); red = 2 adds per-rhs {<out, in>, |out|^2}
 void dslash_h(int in16, void* out16, float* out_norm, const void* in, const float* in_norm, const void* b,
               const void* gauge, const Geom& g, const double* mass_dev, const int* active, int nrhs, int red,
-              const RedBuf* rb, cudaStream_t s);
+              const RedBuf* rb, cudaStream_t s, int gc = 12);
 // x += alpha r, r -= alpha q (update_r) with x FP32 native and r, q FP16
 void mr_update_h(void* x, void* r16, float* rn, const void* q16, const float* qn, int V, int nrhs, const double* red,
                  const int* active, bool update_r, cudaStream_t s);

@@ -217,7 +217,17 @@ struct ProfScope {
 static double rb_(int prec) { return prec == WMG_PREC_DOUBLE ? 8.0 : 4.0; }
 double dslash_bytes(const wmg_ctx* c, int prec, int nact, bool resid) {
   const double s = rb_(prec), V = c->fine.V;
-  return V * (48.0 * s) + (double)nact * V * 24.0 * s * (resid ? 3.0 : 2.0);
+  const double links = (prec == WMG_PREC_SINGLE && c->gauge_compress == 8 && c->gauge8_ok) ? 32.0 : 48.0;
+  return V * (links * s) + (double)nact * V * 24.0 * s * (resid ? 3.0 : 2.0);
+}
+// the links of the fine operator in precision prec: 12-real, or the 8-real FP32 links
+static const void* links(const wmg_ctx* c, int prec, int* gc) {
+  if (prec == WMG_PREC_SINGLE && c->gauge_compress == 8 && c->gauge8 && c->gauge8_ok) {
+    *gc = 8;
+    return c->gauge8;
+  }
+  *gc = 12;
+  return c->gauge[prec];
 }
 double coarse_bytes(const wmg_ctx* c, int l, int prec, int nact) {
   const double s = rb_(prec), V = c->L[l].g.V, n = c->L[l].ndof;
@@ -303,7 +313,9 @@ void level_apply(wmg_ctx* c, int l, int prec, const void* in, void* out, int nrh
   const int na = nact_of(c, active, nrhs);
   if (l == 0) {
     ProfScope ps(c, prec == WMG_PREC_DOUBLE ? PROF_DSLASH_64 : PROF_DSLASH_LO, dslash_bytes(c, prec, na, false), na);
-    dslash(prec, out, in, nullptr, c->gauge[prec], c->fine, c->d_mass, active, nrhs, red, rb, c->stream);
+    int gc;
+    const void* U = links(c, prec, &gc);
+    dslash(prec, out, in, nullptr, U, c->fine, c->d_mass, active, nrhs, red, rb, c->stream, gc);
   } else {
     ProfScope ps(c, PROF_COARSE, coarse_bytes(c, l, prec, na), na);
     coarse_op(c, l, prec, in, out, nrhs, false, active, red == 1 ? rb : nullptr);
@@ -320,16 +332,19 @@ static wmg_status mr_half(wmg_ctx* c, void* x, const void* b, int nrhs, int nu, 
   TRY(ws_get(c, "mr_qn", (size_t)V * nrhs * sizeof(float), &qn));
   RedBuf rb = redbuf(c, RES_MR);
   const int na = nact_of(c, active, nrhs);
-  const double hb = (double)V * (48.0 * 4.0) + (double)na * V * (96.0 + 52.0);  // gauge, x + b in, r out
+  int gc;
+  const void* U = links(c, WMG_PREC_SINGLE, &gc);
+  const double lb = gc == 8 ? 128.0 : 192.0;
+  const double hb = (double)V * lb + (double)na * V * (96.0 + 52.0);  // gauge, x + b in, r out
   {
     ProfScope ps(c, PROF_DSLASH_LO, hb + (double)na * V * 96.0, na);
-    dslash_h(0, r, (float*)rn, x, nullptr, b, c->gauge[1], c->fine, c->d_mass, active, nrhs, 0, nullptr, c->stream);
+    dslash_h(0, r, (float*)rn, x, nullptr, b, U, c->fine, c->d_mass, active, nrhs, 0, nullptr, c->stream, gc);
   }
   for (int i = 0; i < nu; ++i) {
     {
-      ProfScope ps(c, PROF_DSLASH_LO, (double)V * 192.0 + (double)na * V * 104.0, na);
-      dslash_h(1, q, (float*)qn, r, (const float*)rn, nullptr, c->gauge[1], c->fine, c->d_mass, active, nrhs, 2, &rb,
-               c->stream);
+      ProfScope ps(c, PROF_DSLASH_LO, (double)V * lb + (double)na * V * 104.0, na);
+      dslash_h(1, q, (float*)qn, r, (const float*)rn, nullptr, U, c->fine, c->d_mass, active, nrhs, 2, &rb,
+               c->stream, gc);
     }
     // x read + written (FP32), r16 read (+ written), q16 read when r is updated
     const double ub = (double)na * V * (192.0 + (i + 1 < nu ? 3.0 * 52.0 : 52.0));
@@ -350,9 +365,11 @@ wmg_status mr(wmg_ctx* c, int l, int prec, void* x, const void* b, int nrhs, int
   RedBuf rb = redbuf(c, RES_MR);
   const int na = nact_of(c, active, nrhs);
   const int dcls = prec == WMG_PREC_DOUBLE ? PROF_DSLASH_64 : PROF_DSLASH_LO;
+  int gc;
+  const void* U = links(c, prec, &gc);
   if (l == 0) {
     ProfScope ps(c, dcls, dslash_bytes(c, prec, na, true), na);
-    dslash(prec, r, x, b, c->gauge[prec], c->fine, c->d_mass, active, nrhs, 0, nullptr, c->stream);
+    dslash(prec, r, x, b, U, c->fine, c->d_mass, active, nrhs, 0, nullptr, c->stream, gc);
   } else {
     level_apply(c, l, prec, x, r, nrhs, active, 0, nullptr);
     ProfScope ps(c, blas_cls(l), vec_bytes(c, l, prec, na, 3), na);
@@ -361,7 +378,7 @@ wmg_status mr(wmg_ctx* c, int l, int prec, void* x, const void* b, int nrhs, int
   for (int i = 0; i < nu; ++i) {
     if (l == 0) {
       ProfScope ps(c, dcls, dslash_bytes(c, prec, na, false), na);
-      dslash(prec, q, r, nullptr, c->gauge[prec], c->fine, c->d_mass, active, nrhs, 2, &rb, c->stream);
+      dslash(prec, q, r, nullptr, U, c->fine, c->d_mass, active, nrhs, 2, &rb, c->stream, gc);
     } else {
       level_apply(c, l, prec, r, q, nrhs, active, 0, nullptr);
       ProfScope ps(c, blas_cls(l), vec_bytes(c, l, prec, na, 2), na);
@@ -979,15 +996,28 @@ wmg_status setup_level(wmg_ctx* c, int l, void* vecs) {
   TRY(normalise(c, l, prec, vecs, N));
   TRY(build_from_vectors(c, l, prec, vecs));
   // later passes: one cycle of the trial hierarchy as an approximate solve of A psi' = psi
+  return improve_level(c, l, vecs, c->prm.setup_passes - 1);
+}
+
+// `passes` improvement passes of level l's vectors (precision prec_sloppy, N fields): psi_k <-
+// K(psi_k) with the two-level cycle of the current hierarchy (coarse solve on level l + 1),
+// normalised; P and the coarse operator are rebuilt after each pass.
+wmg_status improve_level(wmg_ctx* c, int l, void* vecs, int passes) {
+  const int prec = c->prm.prec_sloppy;
+  const int N = c->L[l].bk.N;
+  TRY(ensure_reductions(c, N));
+  std::vector<double> m(N, c->mass_setup);
+  TRY(set_rhs_scalars(c, m.data(), N));
+  c->n_active = N;
   void* out;
   TRY(vec_ws(c, l, "setup_out", prec, N, &out));
-  for (int pass = 1; pass < c->prm.setup_passes; ++pass) {
+  for (int pass = 0; pass < passes; ++pass) {
     TRY(cycle(c, l, l + 1, prec, vecs, out, N, nullptr));
     blas_convert(prec, vecs, prec, out, c->L[l].nvec_elems(), N, nullptr, c->stream);
     TRY(normalise(c, l, prec, vecs, N));
     TRY(build_from_vectors(c, l, prec, vecs));
   }
-  return check(c, "setup_level");
+  return check(c, "improve_level");
 }
 
 // ------------------------------------------------------------------------------------
@@ -1126,7 +1156,9 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
     {
       ProfScope ps(c, lo == WMG_PREC_DOUBLE ? PROF_DSLASH_64 : PROF_DSLASH_LO, dslash_bytes(c, lo, c->n_active, false),
                    c->n_active);
-      dslash(lo, wk, zk, nullptr, c->gauge[lo], c->fine, c->d_mass, c->d_active, nslots, 0, nullptr, s);
+      int gc;
+      const void* U = links(c, lo, &gc);
+      dslash(lo, wk, zk, nullptr, U, c->fine, c->d_mass, c->d_active, nslots, 0, nullptr, s, gc);
     }
     {
       // multidot: W_0..W_{k-1} and w read; orth: W_0..W_{k-1}, r read, w read + written;

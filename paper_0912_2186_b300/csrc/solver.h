@@ -24,6 +24,7 @@ wmg_status galerkin(wmg_ctx* c, int l, int prec);
 wmg_status orthonormalise(wmg_ctx* c, int l);
 wmg_status build_from_vectors(wmg_ctx* c, int l, int prec, const void* vecs);
 wmg_status setup_level(wmg_ctx* c, int l, void* vecs);
+wmg_status improve_level(wmg_ctx* c, int l, void* vecs, int passes);
 void prof_flush(wmg_ctx* c);
 size_t context_device_bytes(const wmg_ctx* c);  // api.cu
 wmg_status clear_graphs(wmg_ctx* c);

@@ -230,6 +230,43 @@ WMG_D void load_link(const void* base, int V, int mu, int v, cpx<R> u[9]) {
   u[8] = conj(u[0] * u[4] - u[1] * u[3]);
 }
 
+// 8-real FP32 links (the "8 floats" gauge storage): [mu][2][V] float4, chunk 0 = (a1, a2) =
+// elements (0,1), (0,2); chunk 1 = (b0, theta_a0, theta_c0) = element (1,0) and the phases of
+// elements (0,0) and (2,0).  Rebuilt from unitarity with det U = 1: |a0|^2 = 1 - |a1|^2 - |a2|^2,
+// |c0|^2 = 1 - |a0|^2 - |b0|^2 (column 0), and, with n = |a1|^2 + |a2|^2, the 2 x 2 systems of
+// row 1 (resp. row 2) orthogonal to row 0 and the cofactor relations conj(c0) = a1 b2 - a2 b1,
+// conj(b0) = a2 c1 - a1 c2 (U^-1 = U^dag = adj U), solved by Cramer's rule:
+//   b1 = -(a1 b0 conj(a0) + conj(a2) conj(c0)) / n,  b2 = (conj(a1) conj(c0) - a2 b0 conj(a0)) / n,
+//   c1 = (conj(a2) conj(b0) - a1 c0 conj(a0)) / n,   c2 = -(a2 c0 conj(a0) + conj(a1) conj(b0)) / n.
+WMG_HD size_t gauge8_bytes(int V) { return (size_t)V * 4 * 2 * sizeof(float4); }
+WMG_D void load_link8(const void* base, int V, int mu, int v, cpx<float> u[9]) {
+  const float4 t0 = __ldg(reinterpret_cast<const float4*>(base) + (size_t)(mu * 2) * V + v);
+  const float4 t1 = __ldg(reinterpret_cast<const float4*>(base) + (size_t)(mu * 2 + 1) * V + v);
+  const cpx<float> a1{t0.x, t0.y}, a2{t0.z, t0.w}, b0{t1.x, t1.y};
+  const float n = a1.re * a1.re + a1.im * a1.im + a2.re * a2.re + a2.im * a2.im;
+  const float ra = sqrtf(fmaxf(1.f - n, 0.f));
+  const float rc = sqrtf(fmaxf(n - (b0.re * b0.re + b0.im * b0.im), 0.f));  // 1 - |a0|^2 - |b0|^2
+  float sa, ca, sc, cc;
+  __sincosf(t1.z, &sa, &ca);
+  __sincosf(t1.w, &sc, &cc);
+  const cpx<float> a0{ra * ca, ra * sa}, c0{rc * cc, rc * sc};
+  const float in = 1.f / n;
+  const cpx<float> b0a0 = b0 * conj(a0), c0a0 = c0 * conj(a0);
+  const cpx<float> b1 = -in * (a1 * b0a0 + conj(a2) * conj(c0));
+  const cpx<float> b2 = in * (conj(a1) * conj(c0) - a2 * b0a0);
+  const cpx<float> c1 = in * (conj(a2) * conj(b0) - a1 * c0a0);
+  const cpx<float> c2 = -in * (a2 * c0a0 + conj(a1) * conj(b0));
+  u[0] = a0, u[1] = a1, u[2] = a2;
+  u[3] = b0, u[4] = b1, u[5] = b2;
+  u[6] = c0, u[7] = c1, u[8] = c2;
+}
+// the link loader of a dslash kernel: 12-real in the kernel's precision, or 8-real FP32 (GC = 8)
+template <typename R, int GC>
+WMG_D void load_link_gc(const void* base, int V, int mu, int v, cpx<R> u[9]) {
+  if constexpr (GC == 8) load_link8(base, V, mu, v, u);
+  else load_link<R>(base, V, mu, v, u);
+}
+
 // ---------------------------------------------------------------------------------
 // deterministic reductions: each CTA writes its partial sums (double) for its rhs;
 // the last CTA of that rhs (counter) sums the partials in index order.

@@ -88,8 +88,12 @@ def load():
         "wmg_load_gauge": (i, [vp, vp]),
         "wmg_load_gauge_dev": (i, [vp, vp]),
         "wmg_set_mass": (i, [vp, d]),
+        "wmg_set_gauge_compression": (i, [vp, i]),
         "wmg_setup": (i, [vp, P(Params), vp]),
         "wmg_import_nullvecs": (i, [vp, P(Params), i, vp]),
+        "wmg_update_gauge": (i, [vp, vp]),
+        "wmg_update_gauge_dev": (i, [vp, vp]),
+        "wmg_refresh_setup": (i, [vp, i]),
         "wmg_export_nullvecs": (i, [vp, i, vp]),
         "wmg_export_coarse": (i, [vp, i, vp]),
         "wmg_level_info": (i, [vp, i, P(i), P(i)]),
@@ -217,12 +221,27 @@ class Context:
             return self._check(self.lib.wmg_load_gauge(self.h, _ptr(U)))
         return self._check(self.lib.wmg_load_gauge_dev(self.h, _ptr(U)))
 
+    def set_gauge_compression(self, reals):
+        """12 (default) or 8 reals per link in the FP32 fine operator."""
+        return self._check(self.lib.wmg_set_gauge_compression(self.h, int(reals)))
+
     def set_mass(self, m):
         return self._check(self.lib.wmg_set_mass(self.h, float(m)))
 
     def setup(self, params, starts=None):
         s = None if starts is None else np.ascontiguousarray(starts, dtype=np.complex128)
         return self._check(self.lib.wmg_setup(self.h, ctypes.byref(params), _ptr(s) if s is not None else None))
+
+    def update_gauge(self, U):
+        """New gauge field, same near-null subspace: only the coarse operators are rebuilt."""
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=np.complex128)
+            return self._check(self.lib.wmg_update_gauge(self.h, _ptr(U)))
+        return self._check(self.lib.wmg_update_gauge_dev(self.h, _ptr(U)))
+
+    def refresh_setup(self, passes=1):
+        """`passes` improvement passes of the adaptive setup from the current subspace."""
+        return self._check(self.lib.wmg_refresh_setup(self.h, int(passes)))
 
     def import_nullvecs(self, level, vecs, params=None):
         v = np.ascontiguousarray(vecs, dtype=np.complex128)

@@ -83,6 +83,16 @@ def gauge_field(dims, eps, seed, chunk_sites=1 << 18):
     return out.reshape(shape + (4, 3, 3))
 
 
+def evolved_gauge(U, eps, seed):
+    """A small step of the gauge field, as in a molecular-dynamics update: every link multiplied
+    from the left by exp(i eps H) with H the traceless Hermitian part of seeded Gaussian entries
+    (drawn in the [t][z][y][x][mu] order), re-unitarised."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    g = rng.standard_normal(size=U.shape + (2,))
+    R = _su3_exp(g[..., 0] + 1j * g[..., 1], eps)
+    return _reunitarise(R @ U)
+
+
 def unit_gauge(dims):
     """The free field U_mu(x) = 1."""
     shape = lex_shape(dims)

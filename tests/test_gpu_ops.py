@@ -257,3 +257,51 @@ def test_coarse_schur_apply(W, prec, dims, block, N):
             for r in range(nrhs):
                 assert rel_err(got[r], want[r]) < tol
                 assert np.all(got[r][odd] == 0)
+
+
+@pytest.mark.parametrize("dims", [(6, 4, 4, 6), (8, 8, 8, 8)])
+def test_dslash_8real_links_parity(W, dims):
+    """8-real FP32 links (Table 2's "8 floats"): the FP32 operator against the oracle at 1e-5 and
+    the FP16-storage path at 2e-3 (V = 576 leaves a ragged last CTA)."""
+    U = synth.gauge_field(dims, 0.6, 3)
+    m, nrhs = -0.27, 3
+    b = synth.gaussian_spinors(dims, nrhs, 4)
+    ctx = W.Context(dims)
+    ctx.set_gauge_compression(8)
+    ctx.load_gauge(U)
+    ctx.set_mass(m)
+    want = np.stack([dirac.apply_D(U, b[r], m) for r in range(nrhs)])
+    for prec, tol in ((1, TOL[1]), (2, 2e-3)):
+        xin, xout = native_fine(ctx.V, nrhs, 1), native_fine(ctx.V, nrhs, 1)
+        ctx.pack(1, dev(b), xin, nrhs)
+        ctx.apply_D(prec, xin, xout, nrhs)
+        canon = dev(np.zeros_like(b))
+        ctx.unpack(1, xout, canon, nrhs)
+        assert rel_err(host(canon), want) < tol, prec
+
+
+def test_8real_links_solve_and_free_field(W):
+    """A mixed-precision MG-GCR solve with 8-real FP32 links meets the 1e-10 true residual (oracle D);
+    on the free field, which the 8-real form cannot represent, the operator keeps 12-real links."""
+    dims, m = (8, 8, 8, 8), 0.05
+    U = synth.gauge_field(dims, 0.4, 11)
+    ctx = W.Context(dims)
+    ctx.set_gauge_compression(8)
+    ctx.load_gauge(U)
+    ctx.set_mass(m)
+    ctx.setup(W.default_params(nvec=[8], prec_sloppy=1), synth.setup_starts(dims, 8, 12))
+    b = synth.gaussian_spinors(dims, 2, 13)
+    x = dev(np.zeros_like(b))
+    st, info = ctx.solve(dev(b), x, 2)
+    xs = host(x)
+    for r in range(2):
+        assert info[r]["converged"]
+        assert np.linalg.norm(b[r] - dirac.apply_D(U, xs[r], m)) / np.linalg.norm(b[r]) <= 1.05e-10
+    ctx.load_gauge(synth.unit_gauge(dims))
+    xin, xout = native_fine(ctx.V, 1, 1), native_fine(ctx.V, 1, 1)
+    ctx.pack(1, dev(b[:1]), xin, 1)
+    ctx.apply_D(1, xin, xout, 1)
+    canon = dev(np.zeros_like(b[:1]))
+    ctx.unpack(1, xout, canon, 1)
+    want = dirac.apply_D(synth.unit_gauge(dims), b[0], m)
+    assert rel_err(host(canon)[0], want) < TOL[1]
