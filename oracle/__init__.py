@@ -16,6 +16,9 @@ paper computes:
 * ``solvers`` -- MR smoother, CGNR coarsest solve, the multigrid cycle with post
                  smoothing only, flexible GCR outer solver (Sec. 3) and the adaptive
                  near-null-vector setup (Sec. 2).
+* ``eo_fine`` -- the even-odd (red/black) form of the fine solve of Sec. 3: the Schur complement
+                 S = d - H_eo H_oe / d, the prepared right-hand side, the odd-site reconstruction
+                 and MG-GCR on S with the whole-lattice cycle as preconditioner.
 * ``eo``      -- the even-odd (Schur complement) form of the coarsest-level CG solve:
                  S = A_ee - A_eo A_oo^-1 A_oe, its adjoint, the prepared right-hand side
                  and the reconstruction of the odd sites.
@@ -25,4 +28,4 @@ no closed form, so the adaptive setup (``solvers.setup_level``) is pinned as an
 algorithm: against a dense restatement of its steps made of library routines on a tiny
 lattice, plus the indirect invariants (residual decrease, span, orthonormality).
 """
-from . import dirac, eo, mg, solvers  # noqa: F401
+from . import dirac, eo, eo_fine, mg, solvers  # noqa: F401

@@ -136,26 +136,46 @@ __global__ void k_mr_update(void* x_, void* r_, const void* q_, size_t n, const 
 
 // x += alpha p, r -= alpha q with alpha = zz[parity]/qq; |r|^2 reduced; the CTA that completes
 // the sum marks convergence (|r|^2 <= tol2 |b|^2) and counts the iteration (every other CTA of
-// the right-hand side has read done[r] by then).
+// the right-hand side has read done[r] by then).  A thread takes kBlasPerThread elements per
+// round, i0 + j blockDim (j < kBlasPerThread), and issues every load of the round before the
+// arithmetic (one memory round trip per round; the coarsest solve's vectors take one round).
 template <typename R>
-__global__ void k_cg_update(void* x_, void* r_, const void* p_, const void* q_, size_t n, CgScalars cg, int parity,
-                            int nrhs, RedBuf rb) {
+__global__ void k_cg_update(void* __restrict__ x_, void* __restrict__ r_, const void* __restrict__ p_,
+                            const void* __restrict__ q_, size_t n, CgScalars cg, int parity, int nrhs, RedBuf rb) {
+  constexpr int E = kBlasPerThread;
   const int r = blockIdx.y;
-  const bool on = !cg.done[r] && cg.qq[r] > 0.0;
-  const R al = on ? R(cg.zz[parity * nrhs + r] / cg.qq[r]) : R(0);
-  cpx<R>* x = vec<R>(x_, n, r);
-  cpx<R>* rr = vec<R>(r_, n, r);
-  const cpx<R>* p = vec<R>(p_, n, r);
-  const cpx<R>* q = vec<R>(q_, n, r);
+  const int done = cg.done[r];
+  const double qq = cg.qq[r], zz = cg.zz[parity * nrhs + r];
+  const bool on = !done && qq > 0.0;
+  const R al = on ? R(zz / qq) : R(0);
+  cpx<R>* __restrict__ x = vec<R>(x_, n, r);
+  cpx<R>* __restrict__ rr = vec<R>(r_, n, r);
+  const cpx<R>* __restrict__ p = vec<R>(p_, n, r);
+  const cpx<R>* __restrict__ q = vec<R>(q_, n, r);
   R t = 0;
-  WMG_GRID_LOOP(i) {
-    cpx<R> ri = rr[i];
-    if (on) {
-      x[i] += al * p[i];
-      ri = ri - al * q[i];
-      rr[i] = ri;
+  for (size_t i0 = (size_t)blockIdx.x * blockDim.x * E + threadIdx.x; i0 < n; i0 += (size_t)gridDim.x * blockDim.x * E) {
+    cpx<R> rv[E], xv[E], pv[E], qv[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const size_t i = i0 + (size_t)j * blockDim.x;
+      if (i < n) {
+        rv[j] = rr[i];
+        if (on) xv[j] = x[i], pv[j] = p[i], qv[j] = q[i];
+      }
     }
-    t += ri.re * ri.re + ri.im * ri.im;
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const size_t i = i0 + (size_t)j * blockDim.x;
+      if (i < n) {
+        if (on) {
+          xv[j] += al * pv[j];
+          rv[j] = rv[j] - al * qv[j];
+          x[i] = xv[j];
+          rr[i] = rv[j];
+        }
+        t += rv[j].re * rv[j].re + rv[j].im * rv[j].im;
+      }
+    }
   }
   double v[1] = {double(t)};
   __shared__ double sm[32];
@@ -170,16 +190,31 @@ __global__ void k_cg_update(void* x_, void* r_, const void* p_, const void* q_, 
   }
 }
 
-// p = z + beta p, beta = zz[1-parity]/zz[parity]
+// p = z + beta p, beta = zz[1-parity]/zz[parity] (loads of a round issued first, as above)
 template <typename R>
-__global__ void k_cg_xpay(void* p_, const void* z_, size_t n, CgScalars cg, int parity, int nrhs) {
+__global__ void k_cg_xpay(void* __restrict__ p_, const void* __restrict__ z_, size_t n, CgScalars cg, int parity,
+                          int nrhs) {
+  constexpr int E = kBlasPerThread;
   const int r = blockIdx.y;
-  if (cg.done[r]) return;
-  const double zo = cg.zz[parity * nrhs + r];
-  const R be = zo > 0.0 ? R(cg.zz[(1 - parity) * nrhs + r] / zo) : R(0);
-  cpx<R>* p = vec<R>(p_, n, r);
-  const cpx<R>* z = vec<R>(z_, n, r);
-  WMG_GRID_LOOP(i) p[i] = z[i] + be * p[i];
+  const int done = cg.done[r];
+  const double zo = cg.zz[parity * nrhs + r], zn = cg.zz[(1 - parity) * nrhs + r];
+  if (done) return;
+  const R be = zo > 0.0 ? R(zn / zo) : R(0);
+  cpx<R>* __restrict__ p = vec<R>(p_, n, r);
+  const cpx<R>* __restrict__ z = vec<R>(z_, n, r);
+  for (size_t i0 = (size_t)blockIdx.x * blockDim.x * E + threadIdx.x; i0 < n; i0 += (size_t)gridDim.x * blockDim.x * E) {
+    cpx<R> pv[E], zv[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const size_t i = i0 + (size_t)j * blockDim.x;
+      if (i < n) pv[j] = p[i], zv[j] = z[i];
+    }
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const size_t i = i0 + (size_t)j * blockDim.x;
+      if (i < n) p[i] = zv[j] + be * pv[j];
+    }
+  }
 }
 
 // coef_j = <W_j, w> for j = j0 .. j0+J-1 (j < kmax)

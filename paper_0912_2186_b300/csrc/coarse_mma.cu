@@ -16,6 +16,8 @@
 // shared memory with a per-(site, rhs) factor s_X.  The result is
 // rescaled by s_A s_X.  Relative error is about 1e-3 (FP16 operands), enough for the coarse
 // solve of a preconditioner.
+#include <cstdlib>
+
 #include <cuda_fp16.h>
 
 #include "kernels.h"
@@ -358,7 +360,11 @@ template <int NDOF>
 static void launch_mma_n(const void* A16, const float* sA, const Geom& g, const void* in, void* out, int nrhs,
                          const double* shift, bool dagger, const int* active, const RedBuf* rb, cudaStream_t s,
                          const StencilEo& eo, int* err) {
-  if (nrhs <= 8) launch_mma<NDOF, 1>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s, eo, err);
+  static const int nt_max = [] {
+    const char* e = std::getenv("WMG_MMA_NT");
+    return (e && e[0] == '1') ? 1 : 2;
+  }();
+  if (nrhs <= 8 || nt_max == 1) launch_mma<NDOF, 1>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s, eo, err);
   else launch_mma<NDOF, 2>(A16, sA, g, in, out, nrhs, shift, dagger, active, rb, s, eo, err);
 }
 

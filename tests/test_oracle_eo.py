@@ -5,7 +5,8 @@ true residual of the whole system."""
 import numpy as np
 import pytest
 
-from oracle import eo, mg
+import synth
+from oracle import dirac, eo, mg, solvers
 
 
 def random_stencil(dims, n, seed, diag=6.0):
@@ -134,3 +135,65 @@ def test_two_level_solve_with_even_odd_coarsest():
         assert np.linalg.norm(b - dirac.apply_D(U, x, 0.1)) <= 1.01e-10 * np.linalg.norm(b)
         its.append(info.iters)
     assert abs(its[0] - its[1]) <= 1
+
+
+# ---- the even-odd (red/black) form of the fine Wilson solve (oracle/eo_fine.py) ----
+from oracle import eo_fine  # noqa: E402
+
+
+def _fine_blocks(dims, U, m):
+    """Dense D from the loop-built matrix, split by site parity (dof index = site * 12 + k)."""
+    D = dirac.dense_D(U, m)
+    par = np.repeat(eo_fine.parity(dims).ravel(), 12)
+    e, o = np.nonzero(par == 0)[0], np.nonzero(par == 1)[0]
+    return D, e, o
+
+
+def test_fine_schur_against_dense_blocks():
+    dims, m = (4, 2, 2, 4), -0.3
+    U = synth.gauge_field(dims, 0.6, 120)
+    D, e, o = _fine_blocks(dims, U, m)
+    S = D[np.ix_(e, e)] - D[np.ix_(e, o)] @ np.linalg.solve(D[np.ix_(o, o)], D[np.ix_(o, e)])
+    x = synth.gaussian_spinors(dims, 1, 121)[0]
+    xe = x.ravel().copy()
+    xe[o] = 0
+    got = eo_fine.schur_apply(U, xe.reshape(x.shape), m).ravel()
+    assert np.abs(got[o]).max() == 0
+    assert np.abs(got[e] - S @ xe[e]).max() < 1e-13 * np.abs(S @ xe[e]).max()
+    # the odd-odd block is the scalar d = 4 + m (no hop stays on one parity)
+    assert np.abs(D[np.ix_(o, o)] - (4 + m) * np.eye(len(o))).max() < 1e-15
+    # S^dag = gamma_5 S gamma_5
+    g5 = np.where(np.arange(len(D)) % 12 < 6, 1.0, -1.0)[e]
+    assert np.abs(np.conj(S.T) - g5[:, None] * S * g5[None, :]).max() < 1e-13
+
+
+def test_fine_prepare_and_reconstruct_against_dense_solve():
+    dims, m = (4, 2, 2, 4), -0.3
+    U = synth.gauge_field(dims, 0.6, 122)
+    D, e, o = _fine_blocks(dims, U, m)
+    b = synth.gaussian_spinors(dims, 1, 123)[0]
+    bv = b.ravel()
+    S = D[np.ix_(e, e)] - D[np.ix_(e, o)] @ np.linalg.solve(D[np.ix_(o, o)], D[np.ix_(o, e)])
+    bh = eo_fine.prepare(U, b, m).ravel()
+    want_bh = bv[e] - D[np.ix_(e, o)] @ np.linalg.solve(D[np.ix_(o, o)], bv[o])
+    assert np.abs(bh[e] - want_bh).max() < 1e-13 * np.abs(want_bh).max() and np.abs(bh[o]).max() == 0
+    xe = np.zeros_like(bv)
+    xe[e] = np.linalg.solve(S, bh[e])
+    x = eo_fine.reconstruct(U, b, xe.reshape(b.shape), m).ravel()
+    want = np.linalg.solve(D, bv)
+    assert np.abs(x - want).max() < 1e-11 * np.abs(want).max()
+
+
+def test_fine_even_odd_mg_solve():
+    """MG-GCR on the even-odd system (the whole-lattice cycle on (r_e, 0) as preconditioner)
+    reaches the whole system's 1e-10 residual and the dense solution."""
+    dims, block, N = (4, 4, 2, 4), (2, 2, 2, 2), 3
+    U = synth.gauge_field(dims, 0.5, 124)
+    op = mg.WilsonOp(U, 0.02)
+    P = mg.block_orthonormalise(synth.setup_starts(dims, N, 125), block)
+    H = solvers.Hierarchy([op, mg.galerkin(op, P, block)], [P], [block], solvers.CycleParams(coarse_tol=1e-10))
+    b = synth.gaussian_spinors(dims, 1, 126)[0]
+    x, info = eo_fine.mg_solve_eo(H, b, 1e-10)
+    assert np.linalg.norm(b - dirac.apply_D(U, x, 0.02)) <= 1.01e-10 * np.linalg.norm(b)
+    want = np.linalg.solve(dirac.dense_D(U, 0.02), b.ravel())
+    assert np.abs(x.ravel() - want).max() < 1e-8 * np.abs(want).max()
