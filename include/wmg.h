@@ -134,6 +134,17 @@ typedef struct {
                                         test |b - A x| <= coarse_tol |b|; used where
                                         every extent of the coarsest lattice is even
                                         and 2N <= 64, else the plain CGNR; 0: plain  */
+  int fine_eo;                       /* 1: red/black preconditioning of the fine solve
+                                        (Sec. 3): the outer GCR runs on the even-site
+                                        Schur complement S = d - H_eo H_oe / d (d = 4 +
+                                        m, H the hopping term) with half-lattice Krylov
+                                        vectors, the cycle of the whole lattice applied
+                                        to (r_e, 0) as preconditioner, and the odd
+                                        sites reconstructed, x_o = (b_o - H_oe x_e) / d;
+                                        the stopping test stays |b - D x| <= tol |b|
+                                        (the residual vanishes on the odd sites).  The
+                                        x extent must be even.  0 (default): the whole
+                                        lattice                                       */
 } wmg_params;
 
 /* Per-right-hand-side result of a solve. */
@@ -260,6 +271,12 @@ wmg_status wmg_unpack_spinor(wmg_ctx* ctx, int prec, const void* native_dev, dou
  * the smoother's FP16 storage path: in rounded to FP16 with a per-site norm, D applied
  * in FP32 arithmetic, the result rounded to FP16 the same way and widened into out. */
 wmg_status wmg_apply_D(wmg_ctx* ctx, int prec, const void* in_dev, void* out_dev, int nrhs);
+
+/* out = S in on the even sites (odd sites of out set to 0, those of in not read): the even-site
+ * Schur complement S = d - H_eo H_oe / d of the fine operator (d = 4 + m at the context's mass, H
+ * the hopping term, parity (x + y + z + t) mod 2), the operator of the red/black solve (fine_eo);
+ * native fine spinors of precision prec (DOUBLE or SINGLE).  The x extent must be even. */
+wmg_status wmg_apply_D_eo(wmg_ctx* ctx, int prec, const void* in_dev, void* out_dev, int nrhs);
 
 /* out = K(in): one application of the multigrid preconditioner of the fine level (Sec. 3: the
  * cycle the outer GCR applies each iteration) to nrhs native fine spinors of precision prec

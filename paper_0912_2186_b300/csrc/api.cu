@@ -96,6 +96,8 @@ wmg_status alloc_hierarchy(wmg_ctx* c, const wmg_params* p) {
     return bad(c, "prec_smoother must be SINGLE, or HALF with prec_sloppy SINGLE");
   if (p->coarse_persistent != 0 && p->coarse_persistent != 1) return bad(c, "coarse_persistent must be 0 or 1");
   if (p->coarse_eo != 0 && p->coarse_eo != 1) return bad(c, "coarse_eo must be 0 or 1");
+  if (p->fine_eo != 0 && p->fine_eo != 1) return bad(c, "fine_eo must be 0 or 1");
+  if (p->fine_eo && c->fine.L[0] % 2) return bad(c, "fine_eo needs an even x extent");
   free_hierarchy(c);
   c->prm = *p;
   c->nlev = p->nlevels;
@@ -194,6 +196,7 @@ void wmg_default_params(wmg_params* p) {
   p->prec_smoother = WMG_PREC_SINGLE;
   p->coarse_persistent = 0;
   p->coarse_eo = 1;
+  p->fine_eo = 0;
 }
 
 const char* wmg_strerror(wmg_status s) {
@@ -617,6 +620,25 @@ wmg_status wmg_apply_D(wmg_ctx* c, int prec, const void* in, void* out, int nrhs
   dslash(prec, out, in, nullptr, g8 ? c->gauge8 : c->gauge[prec], c->fine, c->d_mass, nullptr, nrhs, 0, nullptr,
          c->stream, g8 ? 8 : 12);
   return check(c, "apply_D");
+}
+
+wmg_status wmg_apply_D_eo(wmg_ctx* c, int prec, const void* in, void* out, int nrhs) {
+  if (!c || !in || !out || nrhs < 1 || nrhs > kMaxRhs || in == out || !prec_ok(prec)) return WMG_EINVAL;
+  if (!c->have_gauge) return WMG_ESTATE;
+  if (c->fine.L[0] % 2) return bad(c, "apply_D_eo: the x extent must be even");
+  TRY(set_rhs_scalars(c, nullptr, nrhs));
+  void *he, *ht, *hs;
+  TRY(vec_ws(c, 0, "aDeo_e", prec, nrhs, &he));
+  TRY(vec_ws(c, 0, "aDeo_t", prec, nrhs, &ht));
+  TRY(vec_ws(c, 0, "aDeo_s", prec, nrhs, &hs));
+  const bool g8 = prec == WMG_PREC_SINGLE && c->gauge_compress == 8 && c->gauge8 && c->gauge8_ok;
+  const void* U = g8 ? c->gauge8 : c->gauge[prec];
+  eo_extract(prec, he, in, c->fine, 0, nrhs, c->stream);
+  dslash_eo(prec, 0, 1, ht, he, nullptr, nullptr, U, g8 ? 8 : 12, c->fine, c->d_mass, nullptr, nrhs, nullptr,
+            c->stream);
+  dslash_eo(prec, 1, 0, hs, ht, he, nullptr, U, g8 ? 8 : 12, c->fine, c->d_mass, nullptr, nrhs, nullptr, c->stream);
+  eo_embed(prec, out, hs, nullptr, c->fine, nrhs, c->stream);
+  return check(c, "apply_D_eo");
 }
 
 wmg_status wmg_apply_cycle(wmg_ctx* c, int prec, const void* in, void* out, int nrhs) {

@@ -44,6 +44,19 @@ void mr_update_h(void* x, void* r16, float* rn, const void* q16, const float* qn
 void spinor_to_h(const void* in, void* out16, float* norm, int V, int nrhs, cudaStream_t s);
 void spinor_from_h(const void* in16, const float* norm, void* out, int V, int nrhs, cudaStream_t s);
 
+// ---- even-odd fine operator (dslash_eo.cu): half-lattice fields [rhs][6][V/2], site v at v >> 1 ----
+// h = the raw hop sum onto the parity-p_out sites from the opposite-parity half field `in` (H = -h/2);
+// mode 0: out = h;  1: out = d self - h / (4 d);  2: out = self + h / (2 d);  3: out = (self + h / 2) / d,
+// d = 4 + m_r; with b: out = b - out; with rb: |out|^2 per rhs.  gc = 8: 8-real FP32 links.
+void dslash_eo(int prec, int mode, int p_out, void* out, const void* in, const void* self, const void* b,
+               const void* gauge, int gc, const Geom& g, const double* mass_dev, const int* active, int nrhs,
+               const RedBuf* rb, cudaStream_t s);
+int dslash_eo_blocks(int V);
+// whole-lattice native field <- even sites from half_e, odd sites from half_o (zeros for a null
+// one); and the half field of parity p from a whole-lattice one
+void eo_embed(int prec, void* full, const void* half_e, const void* half_o, const Geom& g, int nrhs, cudaStream_t s);
+void eo_extract(int prec, void* half, const void* full, const Geom& g, int p, int nrhs, cudaStream_t s);
+
 // ---- BLAS on flat complex vectors: n complex numbers per rhs, rhs stride n (blas.cu) ----
 int blas_blocks(size_t n);
 void blas_zero(int prec, void* x, size_t n, int nrhs, cudaStream_t s);

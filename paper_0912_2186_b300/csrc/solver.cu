@@ -1030,7 +1030,10 @@ wmg_status improve_level(wmg_ctx* c, int l, void* vecs, int passes) {
 // ------------------------------------------------------------------------------------
 wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
   const int lo = use_mg ? c->prm.prec_sloppy : WMG_PREC_DOUBLE;
-  const size_t n = (size_t)c->fine.V * 12;
+  // red/black: the Krylov vectors live on the even sites (half-lattice fields)
+  const bool eo = use_mg && c->prm.fine_eo && c->fine.L[0] % 2 == 0;
+  const size_t nfull = (size_t)c->fine.V * 12;
+  const size_t n = eo ? nfull / 2 : nfull;
   const int m = std::min(std::max(c->prm.gcr_restart, 1), kMaxKrylov);
   cudaStream_t s = c->stream;
   if (nslots < 1 || nslots > kMaxRhs) return WMG_EINVAL;
@@ -1047,6 +1050,40 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
   TRY(ws_get(c, std::string("gcr_W") + (lo ? "s" : "d"), slot * m, &W));
   const size_t f64 = n * sizeof(cd), flo = n * csize(lo);
   auto at = [](void* base, size_t bytes, int r) { return (void*)((char*)base + bytes * r); };
+  // red/black workspaces: the whole-lattice b (for the odd-site reconstruction), the halves of b,
+  // the odd-site intermediate of S in both precisions, the cycle's whole-lattice in / out, and
+  // the reconstructed whole-lattice solution of one slot
+  void *bfull = nullptr, *beh = nullptr, *boh = nullptr, *t64 = nullptr, *tlo = nullptr, *rfl = nullptr,
+       *zfl = nullptr, *xfull = nullptr, *xo = nullptr;
+  const size_t ffull = nfull * sizeof(cd);
+  if (eo) {
+    TRY(vec_ws(c, 0, "eo_bfull", WMG_PREC_DOUBLE, nslots, &bfull));
+    TRY(vec_ws(c, 0, "eo_beh", WMG_PREC_DOUBLE, nslots, &beh));
+    TRY(vec_ws(c, 0, "eo_boh", WMG_PREC_DOUBLE, nslots, &boh));
+    TRY(vec_ws(c, 0, "eo_t64", WMG_PREC_DOUBLE, nslots, &t64));
+    TRY(vec_ws(c, 0, "eo_tlo", lo, nslots, &tlo));
+    TRY(vec_ws(c, 0, "eo_rfl", lo, nslots, &rfl));
+    TRY(vec_ws(c, 0, "eo_zfl", lo, nslots, &zfl));
+    TRY(vec_ws(c, 0, "eo_xfull", WMG_PREC_DOUBLE, 1, &xfull));
+    TRY(vec_ws(c, 0, "eo_xo", WMG_PREC_DOUBLE, 1, &xo));
+  }
+  const Geom& fg = c->fine;
+  // the system's operator in the sloppy precision: D, or S = d - H_eo H_oe / d on half fields
+  auto sys_op = [&](const void* in, void* out) {
+    int gc;
+    const void* U = links(c, lo, &gc);
+    if (!eo) {
+      ProfScope ps(c, lo == WMG_PREC_DOUBLE ? PROF_DSLASH_64 : PROF_DSLASH_LO, dslash_bytes(c, lo, c->n_active, false),
+                   c->n_active);
+      dslash(lo, out, in, nullptr, U, fg, c->d_mass, c->d_active, nslots, 0, nullptr, s, gc);
+      return;
+    }
+    // two half-lattice passes: links once each, half fields in / out (+ the self term)
+    const double hb = 0.5 * dslash_bytes(c, lo, c->n_active, false) + 0.5 * dslash_bytes(c, lo, c->n_active, true);
+    ProfScope ps(c, lo == WMG_PREC_DOUBLE ? PROF_DSLASH_64 : PROF_DSLASH_LO, hb, c->n_active);
+    dslash_eo(lo, 0, 1, tlo, in, nullptr, nullptr, U, gc, fg, c->d_mass, c->d_active, nslots, nullptr, s);
+    dslash_eo(lo, 1, 0, out, tlo, in, nullptr, U, gc, fg, c->d_mass, c->d_active, nslots, nullptr, s);
+  };
   const double tol = c->prm.tol;
   const double delta = (lo == WMG_PREC_DOUBLE) ? 0.0 : c->prm.reliable_delta;
   std::vector<int> active(nslots, 0), rel(nslots, 0), iters(nslots, 0), relups(nslots, 0);
@@ -1104,7 +1141,12 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
     info.true_resid = tres[r];
     info.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0[r]).count();
     active[r] = 0;
-    return src.finish(c, r, at(x64, f64, r), info);
+    if (!eo) return src.finish(c, r, at(x64, f64, r), info);
+    // x_o = (b_o - H_oe x_e) / d, then the whole-lattice solution
+    dslash_eo(WMG_PREC_DOUBLE, 3, 1, xo, at(x64, f64, r), at(boh, f64, r), nullptr, c->gauge[0], 12, fg,
+              c->d_mass + r, nullptr, 1, nullptr, s);
+    eo_embed(WMG_PREC_DOUBLE, xfull, at(x64, f64, r), xo, fg, 1, s);
+    return src.finish(c, r, xfull, info);
   };
   TRY(set_rhs_scalars(c, mass.data(), nslots));
   CU(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
@@ -1120,19 +1162,31 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
       if (!adm.empty()) {
         std::vector<int> mask(nslots, 0);
         for (const Admission& a : adm) {
-          pack_spinor(WMG_PREC_DOUBLE, a.b_canon_dev, at(b64, f64, a.slot), c->fine.V, 1, s);
-          blas_zero(WMG_PREC_DOUBLE, at(x64, f64, a.slot), n, 1, s);
-          blas_zero(lo, at(xlo, flo, a.slot), n, 1, s);
-          blas_convert(WMG_PREC_DOUBLE, at(r64, f64, a.slot), WMG_PREC_DOUBLE, at(b64, f64, a.slot), n, 1, nullptr, s);
           mass[a.slot] = a.mass;
           mask[a.slot] = 1;
           iters[a.slot] = relups[a.slot] = 0;
           t0[a.slot] = std::chrono::steady_clock::now();
         }
-        blas_norm2(WMG_PREC_DOUBLE, b64, n, nslots, rb_bb, s);
+        TRY(set_rhs_scalars(c, mass.data(), nslots));
+        for (const Admission& a : adm) {
+          if (!eo) {
+            pack_spinor(WMG_PREC_DOUBLE, a.b_canon_dev, at(b64, f64, a.slot), fg.V, 1, s);
+          } else {
+            // b^_e = b_e - H_eo b_o / d
+            pack_spinor(WMG_PREC_DOUBLE, a.b_canon_dev, at(bfull, ffull, a.slot), fg.V, 1, s);
+            eo_extract(WMG_PREC_DOUBLE, at(beh, f64, a.slot), at(bfull, ffull, a.slot), fg, 0, 1, s);
+            eo_extract(WMG_PREC_DOUBLE, at(boh, f64, a.slot), at(bfull, ffull, a.slot), fg, 1, 1, s);
+            dslash_eo(WMG_PREC_DOUBLE, 2, 0, at(b64, f64, a.slot), at(boh, f64, a.slot), at(beh, f64, a.slot),
+                      nullptr, c->gauge[0], 12, fg, c->d_mass + a.slot, nullptr, 1, nullptr, s);
+          }
+          blas_zero(WMG_PREC_DOUBLE, at(x64, f64, a.slot), n, 1, s);
+          blas_zero(lo, at(xlo, flo, a.slot), n, 1, s);
+          blas_convert(WMG_PREC_DOUBLE, at(r64, f64, a.slot), WMG_PREC_DOUBLE, at(b64, f64, a.slot), n, 1, nullptr, s);
+        }
+        // |b| of the whole system: the stopping test is |b - D x| <= tol |b| in both forms
+        blas_norm2(WMG_PREC_DOUBLE, eo ? bfull : b64, eo ? nfull : n, nslots, rb_bb, s);
         std::vector<double> bb;
         TRY(download(c, rb_bb.result, nslots, bb));
-        TRY(set_rhs_scalars(c, mass.data(), nslots));
         TRY(upload_ints(c, c->d_mask, mask));
         blas_convert(lo, rlo, WMG_PREC_DOUBLE, r64, n, nslots, c->d_mask, s);
         for (const Admission& a : adm) {
@@ -1151,15 +1205,16 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
     }
     void* zk = (char*)Z + slot * k;
     void* wk = (char*)W + slot * k;
-    if (use_mg) TRY(cycle(c, 0, c->nlev - 1, lo, rlo, zk, nslots, c->d_active));
-    else blas_convert(lo, zk, lo, rlo, n, nslots, c->d_active, s);
-    {
-      ProfScope ps(c, lo == WMG_PREC_DOUBLE ? PROF_DSLASH_64 : PROF_DSLASH_LO, dslash_bytes(c, lo, c->n_active, false),
-                   c->n_active);
-      int gc;
-      const void* U = links(c, lo, &gc);
-      dslash(lo, wk, zk, nullptr, U, c->fine, c->d_mass, c->d_active, nslots, 0, nullptr, s, gc);
+    if (use_mg && eo) {  // the whole-lattice cycle on (r_e, 0); its even part preconditions S
+      eo_embed(lo, rfl, rlo, nullptr, fg, nslots, s);
+      TRY(cycle(c, 0, c->nlev - 1, lo, rfl, zfl, nslots, c->d_active));
+      eo_extract(lo, zk, zfl, fg, 0, nslots, s);
+    } else if (use_mg) {
+      TRY(cycle(c, 0, c->nlev - 1, lo, rlo, zk, nslots, c->d_active));
+    } else {
+      blas_convert(lo, zk, lo, rlo, n, nslots, c->d_active, s);
     }
+    sys_op(zk, wk);
     {
       // multidot: W_0..W_{k-1} and w read; orth: W_0..W_{k-1}, r read, w read + written;
       // update: r, w read + written
@@ -1198,7 +1253,14 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
       for (int r = 0; r < nslots; ++r) nrel += rel[r];
       {
         ProfScope ps(c, PROF_DSLASH_64, dslash_bytes(c, WMG_PREC_DOUBLE, nrel, true), nrel);
-        dslash(WMG_PREC_DOUBLE, r64, x64, b64, c->gauge[0], c->fine, c->d_mass, c->d_mask, nslots, 1, &rb_r64, s);
+        if (!eo) {
+          dslash(WMG_PREC_DOUBLE, r64, x64, b64, c->gauge[0], fg, c->d_mass, c->d_mask, nslots, 1, &rb_r64, s);
+        } else {  // r^_e = b^_e - S x_e (= the whole system's residual, zero on the odd sites)
+          dslash_eo(WMG_PREC_DOUBLE, 0, 1, t64, x64, nullptr, nullptr, c->gauge[0], 12, fg, c->d_mass, c->d_mask,
+                    nslots, nullptr, s);
+          dslash_eo(WMG_PREC_DOUBLE, 1, 0, r64, t64, x64, b64, c->gauge[0], 12, fg, c->d_mass, c->d_mask, nslots,
+                    &rb_r64, s);
+        }
       }
       TRY(download(c, rb_r64.result, nslots, t));
       blas_convert(lo, rlo, WMG_PREC_DOUBLE, r64, n, nslots, c->d_mask, s);

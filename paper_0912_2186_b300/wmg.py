@@ -49,6 +49,7 @@ class Params(ctypes.Structure):
         ("prec_smoother", ctypes.c_int),
         ("coarse_persistent", ctypes.c_int),
         ("coarse_eo", ctypes.c_int),
+        ("fine_eo", ctypes.c_int),
     ]
 
 
@@ -107,6 +108,7 @@ def load():
         "wmg_unpack_spinor": (i, [vp, i, vp, vp, i]),
         "wmg_apply_D": (i, [vp, i, vp, vp, i]),
         "wmg_apply_cycle": (i, [vp, i, vp, vp, i]),
+        "wmg_apply_D_eo": (i, [vp, i, vp, vp, i]),
         "wmg_smooth": (i, [vp, i, vp, vp, i, i]),
         "wmg_restrict": (i, [vp, i, i, vp, vp, i]),
         "wmg_prolong": (i, [vp, i, i, vp, vp, i]),
@@ -306,6 +308,10 @@ class Context:
 
     def apply_D(self, prec, inp, out, nrhs):
         return self._check(self.lib.wmg_apply_D(self.h, prec, _ptr(inp), _ptr(out), int(nrhs)))
+
+    def apply_D_eo(self, prec, inp, out, nrhs):
+        """out = S in on the even sites: the red/black Schur complement of the fine operator."""
+        return self._check(self.lib.wmg_apply_D_eo(self.h, prec, _ptr(inp), _ptr(out), int(nrhs)))
 
     def apply_cycle(self, prec, inp, out, nrhs):
         """out = K(in): one multigrid cycle of the fine level (native fine spinors)."""

@@ -344,3 +344,27 @@ def test_gauge_update_keeps_subspace_and_refresh(W):
           f"setup {t_full:.3f} s, refresh {t_ref:.3f} s")
     assert it_ref <= 1.1 * it_full + 2
     assert t_ref < t_full
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_fine_even_odd_solve(W, prec):
+    """fine_eo = 1 (red/black preconditioning of the fine solve): every solution meets the 1e-10
+    true residual of the whole system with the oracle's operator, in a number of iterations close
+    to the whole-lattice solve's, and a right-hand side's result is the same alone and in its batch."""
+    its = {}
+    for flag in (0, 1):
+        ctx, U, p = _ctx(W, CFG1, prec, fine_eo=flag)
+        b = synth.gaussian_spinors(CFG1["dims"], 3, 27)
+        x = dev(np.zeros_like(b))
+        st, info = ctx.solve(dev(b), x, 3)
+        xs = host(x)
+        for r in range(3):
+            assert info[r]["converged"]
+            assert oracle_resid(U, CFG1["m"], b[r], xs[r]) <= 1.05e-10
+        its[flag] = [i["iters"] for i in info]
+        if flag:
+            x1 = dev(np.zeros_like(b[1:2]))
+            _, i1 = ctx.solve(dev(b[1:2]), x1, 1)
+            assert np.array_equal(host(x1)[0], xs[1]) and i1[0]["iters"] == info[1]["iters"]
+    print(f"outer iterations whole lattice {its[0]}, red/black {its[1]}")
+    assert all(b <= 1.3 * a + 2 for a, b in zip(its[0], its[1]))
