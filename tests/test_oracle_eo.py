@@ -197,3 +197,28 @@ def test_fine_even_odd_mg_solve():
     assert np.linalg.norm(b - dirac.apply_D(U, x, 0.02)) <= 1.01e-10 * np.linalg.norm(b)
     want = np.linalg.solve(dirac.dense_D(U, 0.02), b.ravel())
     assert np.abs(x.ravel() - want).max() < 1e-8 * np.abs(want).max()
+
+
+def test_block_jacobi_schur_cg():
+    """Right block-Jacobi preconditioning of the coarsest CG: S's diagonal blocks against the
+    dense Schur complement (extent 2 included, where two hops return by either slot) and the
+    preconditioned CG's solution against a dense solve."""
+    for dims, seed in (((4, 4, 2, 2), 130), ((2, 2, 2, 4), 131)):
+        n = 4
+        A = random_stencil(dims, n, seed)
+        inv = eo.odd_block_inverse(A)
+        Sd = eo.schur_self_blocks(A, inv)
+        par = eo.parity(dims).ravel()
+        Ad = A.dense()
+        e = np.nonzero(np.repeat(par, n) == 0)[0]
+        o = np.nonzero(np.repeat(par, n) == 1)[0]
+        S = Ad[np.ix_(e, e)] - Ad[np.ix_(e, o)] @ np.linalg.solve(Ad[np.ix_(o, o)], Ad[np.ix_(o, e)])
+        ev_sites = np.nonzero(par == 0)[0]
+        flat = Sd.reshape(-1, n, n)
+        for i, site in enumerate(ev_sites):
+            blk = S[i * n:(i + 1) * n, i * n:(i + 1) * n]
+            assert np.abs(flat[site] - blk).max() < 1e-12 * np.abs(blk).max()
+        b = (np.random.default_rng(seed).standard_normal(A.D.shape[:4] + (n,)) + 0j)
+        x, it = eo.cgnr_eo_block_jacobi(A, b, 1e-12, 5000)
+        want = np.linalg.solve(Ad, b.ravel())
+        assert np.abs(x.ravel() - want).max() < 1e-9 * np.abs(want).max()
