@@ -26,30 +26,13 @@ WMG_D cd crecip(cd a) {
 
 }  // namespace
 
-// One CTA per (odd site k, table entry).  [M | W] = [A_kk + shift I | I] in FP64 in shared
-// memory (row-major); Gauss-Jordan elimination column by column with partial pivoting (the
-// largest |M_ij| of the rows i >= j, first on ties) leaves W = M^-1.
-template <typename R>
-__global__ void __launch_bounds__(kInvThreads) k_eo_invert(const cpx<R>* __restrict__ A, Geom g, int n,
-                                                           const double* __restrict__ shifts,
-                                                           cpx<R>* __restrict__ inv, int* __restrict__ singular) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  cd* M = reinterpret_cast<cd*>(smraw);  // [n][n]
-  cd* W = M + (size_t)n * n;             // [n][n]
-  cd* f = W + (size_t)n * n;             // [n] column j of M before its elimination
+// In-place inversion of the n x n matrix M (FP64, row-major, shared memory) by Gauss-Jordan
+// elimination on [M | W] with W = I on entry: column by column, partial pivoting (the largest |M_ij|
+// of the rows i >= j, first on ties); W = M^-1 on exit.  f: n scratch; *singular set on a zero pivot.
+// Called by the whole CTA.
+WMG_D void gauss_jordan(cd* M, cd* W, cd* f, int n, int* singular) {
   __shared__ int piv;
   __shared__ cd pivinv;
-  const int k = blockIdx.x, Vh = g.V / 2;
-  const int v = parity_site(g, k, 1);
-  const cpx<R>* a = A + (size_t)v * 9 * n * n;  // slot 0, [col][row]
-  const double sh = shifts[blockIdx.y];
-  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
-    const int col = i / n, row = i - col * n;
-    const cpx<R> x = a[i];
-    M[row * n + col] = cd{double(x.re) + (row == col ? sh : 0.0), double(x.im)};
-    W[row * n + col] = cd{row == col ? 1.0 : 0.0, 0.0};
-  }
-  __syncthreads();
   const int w2 = 2 * n;
   for (int j = 0; j < n; ++j) {
     if (threadIdx.x < 32) {
@@ -106,6 +89,29 @@ __global__ void __launch_bounds__(kInvThreads) k_eo_invert(const cpx<R>* __restr
     }
     __syncthreads();
   }
+}
+
+// One CTA per (odd site k, table entry): W = (A_kk + shift I)^-1 in FP64 in shared memory.
+template <typename R>
+__global__ void __launch_bounds__(kInvThreads) k_eo_invert(const cpx<R>* __restrict__ A, Geom g, int n,
+                                                           const double* __restrict__ shifts,
+                                                           cpx<R>* __restrict__ inv, int* __restrict__ singular) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cd* M = reinterpret_cast<cd*>(smraw);  // [n][n]
+  cd* W = M + (size_t)n * n;             // [n][n]
+  cd* f = W + (size_t)n * n;             // [n] column j of M before its elimination
+  const int k = blockIdx.x, Vh = g.V / 2;
+  const int v = parity_site(g, k, 1);
+  const cpx<R>* a = A + (size_t)v * 9 * n * n;  // slot 0, [col][row]
+  const double sh = shifts[blockIdx.y];
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+    const int col = i / n, row = i - col * n;
+    const cpx<R> x = a[i];
+    M[row * n + col] = cd{double(x.re) + (row == col ? sh : 0.0), double(x.im)};
+    W[row * n + col] = cd{row == col ? 1.0 : 0.0, 0.0};
+  }
+  __syncthreads();
+  gauss_jordan(M, W, f, n, singular);
   cpx<R>* o = inv + ((size_t)blockIdx.y * Vh + k) * n * n;
   for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
     const int col = i / n, row = i - col * n;
@@ -121,11 +127,11 @@ __global__ void __launch_bounds__(kInvThreads) k_eo_invert(const cpx<R>* __restr
 template <typename R>
 __global__ void k_eo_inv_apply(const cpx<R>* __restrict__ inv, const int* __restrict__ idx, Geom g, int n,
                                const cpx<R>* b, R bc, const cpx<R>* h, R hc, cpx<R>* out, int nrhs, int dagger,
-                               const int* __restrict__ active) {
+                               const int* __restrict__ active, int par) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<R>* xs = reinterpret_cast<cpx<R>*>(smraw);  // [kInvApplyRhs][n]
   const int k = blockIdx.x, Vh = g.V / 2, N = n / 2;
-  const int v = parity_site(g, k, 1);
+  const int v = parity_site(g, k, par);
   const int row = threadIdx.x % n, rr = threadIdx.x / n, r = blockIdx.y * kInvApplyRhs + rr;
   const bool ok = rr < kInvApplyRhs && r < nrhs;
   const size_t at = ((size_t)(ok ? r : 0) * g.V + v) * n + row;
@@ -185,6 +191,149 @@ void eo_hop_inverse(const void* A, const void* inv_entry, const Geom& g, int n, 
   k_eo_hop_inverse<<<dim3(g.V / 2, 8), 256, smem, s>>>((const cf*)A, (const cf*)inv_entry, g, n, (cf*)B);
 }
 
+// ---- right block-Jacobi preconditioning of the Schur complement: CG on T = S M, x_e = M y ----
+// M_x = (S_xx)^-1 at even site x (grid.x = its parity-site number) for one shift:
+//   S_xx = A_xx + shift I - sum over the two-hop paths x -> y = x + k1 -> x (every slot k2 of y that
+//          points back at x: both slots on an extent of 2) of A(x, k1) (A_yy + shift I)^-1 A(y, k2),
+// in FP64 (A: the FP64 stencil; the odd inverses: the shift's FP32 table entry, indexed by the odd
+// parity-site number y >> 1), then inverted by Gauss-Jordan.  Out: FP32 [k][col][row].
+__global__ void __launch_bounds__(kInvThreads) k_eo_schur_self_inv(const cd* __restrict__ A, const cf* __restrict__ inv,
+                                                                   Geom g, int n, double shift, cf* __restrict__ M,
+                                                                   int* __restrict__ singular) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cd* S = reinterpret_cast<cd*>(smraw);  // [n][n] row-major
+  cd* W = S + (size_t)n * n;
+  cd* Pm = W + (size_t)n * n;            // A(x, k1) (A_yy + shift)^-1, row-major
+  cd* f = Pm + (size_t)n * n;
+  const int k = blockIdx.x, nn = n * n;
+  const int x = parity_site(g, k, 0);
+  int cx[4];
+  site_coords(g, x, cx);
+  const cd* Ax = A + (size_t)x * 9 * nn;
+  for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+    const int col = i / n, row = i - col * n;
+    const cd a = Ax[i];
+    S[row * n + col] = cd{a.re + (row == col ? shift : 0.0), a.im};
+    W[row * n + col] = cd{row == col ? 1.0 : 0.0, 0.0};
+  }
+  __syncthreads();
+  for (int k1 = 1; k1 < 9; ++k1) {
+    const int y = neighbour(g, x, cx, (k1 - 1) >> 1, ((k1 - 1) & 1) ? -1 : +1);
+    const cf* iy = inv + (size_t)(y >> 1) * nn;  // [col][row]
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+      const int row = i / n, col = i - row * n;
+      cd acc{0.0, 0.0};
+      for (int j = 0; j < n; ++j) {
+        const cd a = Ax[((size_t)k1 * n + j) * n + row];
+        const cf b = iy[(size_t)col * n + j];
+        cfma(acc, a, cd{double(b.re), double(b.im)});
+      }
+      Pm[row * n + col] = acc;
+    }
+    __syncthreads();
+    int cy[4];
+    site_coords(g, y, cy);
+    const cd* Ay = A + (size_t)y * 9 * nn;
+    for (int k2 = 1; k2 < 9; ++k2) {
+      if (neighbour(g, y, cy, (k2 - 1) >> 1, ((k2 - 1) & 1) ? -1 : +1) != x) continue;
+      for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+        const int row = i / n, col = i - row * n;
+        cd acc{0.0, 0.0};
+        for (int j = 0; j < n; ++j) cfma(acc, Pm[row * n + j], Ay[((size_t)k2 * n + col) * n + j]);
+        S[row * n + col] -= acc;
+      }
+    }
+    __syncthreads();
+  }
+  gauss_jordan(S, W, f, n, singular);
+  cf* o = M + (size_t)k * nn;
+  for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+    const int col = i / n, row = i - col * n;
+    o[i] = cf{float(W[row * n + col].re), float(W[row * n + col].im)};
+  }
+}
+
+// Tables of the preconditioned passes, FP32 in the stencil layout [parity site][9][col][row]:
+//   mode 0 (odd site k, slot s = 1 + blockIdx.y): out = B[k][s] M(x + s), x odd, x + s even
+//   mode 1 (even site k, slot s = blockIdx.y): s = 0: (A_xx + shift I) M_x; s > 0: A(x, s)
+//   mode 2 (even site k, slot s = blockIdx.y): M_x X_s with X_0 = A_xx + shift I, X_s = A(x, s)
+// Both factors staged in shared memory; thread (row, col) forms the n-term product.
+__global__ void __launch_bounds__(256) k_eo_bj_table(int mode, const cf* __restrict__ A, const cf* __restrict__ B,
+                                                     const cf* __restrict__ M, Geom g, int n, float shift,
+                                                     cf* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cf* Ls = reinterpret_cast<cf*>(smraw);  // [col][row]
+  cf* Rs = Ls + (size_t)n * n;
+  const int k = blockIdx.x, nn = n * n;
+  const int s = mode == 0 ? 1 + (int)blockIdx.y : (int)blockIdx.y;
+  const int x = parity_site(g, k, mode == 0 ? 1 : 0);
+  const cf* Ax = A + ((size_t)x * 9 + s) * nn;
+  cf* o = out + ((size_t)k * 9 + s) * nn;
+  if (mode == 1 && s > 0) {
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) o[i] = Ax[i];
+    return;
+  }
+  const cf* L;
+  const cf* R;
+  bool shiftL = false, shiftR = false;
+  if (mode == 0) {
+    int c[4];
+    site_coords(g, x, c);
+    const int y = neighbour(g, x, c, (s - 1) >> 1, ((s - 1) & 1) ? -1 : +1);
+    L = B + ((size_t)k * 9 + s) * nn;
+    R = M + (size_t)(y >> 1) * nn;
+  } else if (mode == 1) {
+    L = Ax;
+    R = M + (size_t)k * nn;
+    shiftL = true;
+  } else {
+    L = M + (size_t)k * nn;
+    R = Ax;
+    shiftR = s == 0;
+  }
+  for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+    const int col = i / n, row = i - col * n;
+    cf l = L[i], r = R[i];
+    if (shiftL && row == col) l.re += shift;
+    if (shiftR && row == col) r.re += shift;
+    Ls[i] = l;
+    Rs[i] = r;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+    const int col = i / n, row = i - col * n;
+    cf acc{0.f, 0.f};
+    for (int j = 0; j < n; ++j) cfma(acc, Ls[(size_t)j * n + row], Rs[(size_t)col * n + j]);
+    o[i] = acc;
+  }
+}
+
+void eo_schur_self_inv(const void* A64, const void* inv_entry, const Geom& g, int n, double shift, void* M,
+                       int* singular, cudaStream_t s) {
+  count_launch();
+  const size_t smem = ((size_t)3 * n * n + n) * sizeof(cd);
+  static const bool attr = [] {
+    cudaFuncSetAttribute(k_eo_schur_self_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    return true;
+  }();
+  (void)attr;
+  k_eo_schur_self_inv<<<g.V / 2, kInvThreads, smem, s>>>((const cd*)A64, (const cf*)inv_entry, g, n, shift, (cf*)M,
+                                                          singular);
+}
+
+void eo_bj_table(int mode, const void* A32, const void* B, const void* M, const Geom& g, int n, double shift,
+                 void* out, cudaStream_t s) {
+  count_launch();
+  const size_t smem = (size_t)2 * n * n * sizeof(cf);
+  static const bool attr = [] {
+    cudaFuncSetAttribute(k_eo_bj_table, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    return true;
+  }();
+  (void)attr;
+  k_eo_bj_table<<<dim3(g.V / 2, mode == 0 ? 8 : 9), 256, smem, s>>>(mode, (const cf*)A32, (const cf*)B, (const cf*)M,
+                                                                   g, n, (float)shift, (cf*)out);
+}
+
 size_t eo_inverse_bytes(int prec, const Geom& g, int n) {
   return (size_t)(g.V / 2) * n * n * 2 * prec_real_bytes(prec);
 }
@@ -211,17 +360,18 @@ void eo_invert(int prec, const void* A, const Geom& g, int n, const double* shif
 }
 
 void eo_inv_apply(int prec, const void* inv, const int* idx, const Geom& g, int n, const void* b, double bc,
-                  const void* h, double hc, void* out, int nrhs, bool dagger, const int* active, cudaStream_t s) {
+                  const void* h, double hc, void* out, int nrhs, bool dagger, const int* active, cudaStream_t s,
+                  int par) {
   count_launch();
   const dim3 grid(g.V / 2, (nrhs + kInvApplyRhs - 1) / kInvApplyRhs);
   const int T = ((n * kInvApplyRhs + 31) / 32) * 32;
   const size_t smem = (size_t)kInvApplyRhs * n * 2 * prec_real_bytes(prec);
   if (prec == WMG_PREC_DOUBLE)
     k_eo_inv_apply<double><<<grid, T, smem, s>>>((const cd*)inv, idx, g, n, (const cd*)b, bc, (const cd*)h, hc,
-                                                 (cd*)out, nrhs, dagger ? 1 : 0, active);
+                                                 (cd*)out, nrhs, dagger ? 1 : 0, active, par);
   else
     k_eo_inv_apply<float><<<grid, T, smem, s>>>((const cf*)inv, idx, g, n, (const cf*)b, (float)bc, (const cf*)h,
-                                                (float)hc, (cf*)out, nrhs, dagger ? 1 : 0, active);
+                                                (float)hc, (cf*)out, nrhs, dagger ? 1 : 0, active, par);
 }
 
 }  // namespace wmg

@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
       const float yi = acc[0][1][e] + acc[1][0][e];
       const float sc = s_a * xmax[rr] * ((dagger && row >= N) ? -1.f : 1.f);
       cf o{yr * sc, yi * sc};
-      if (shift && !eo.hop_only) o += (float)shift[r] * in[((size_t)r * g.V + v) * n + row];
+      if (shift && !eo.hop_only && !eo.opB) o += (float)shift[r] * in[((size_t)r * g.V + v) * n + row];
       if (eo.add) o += reinterpret_cast<const cf*>(eo.add)[((size_t)r * g.V + v) * n + row];
       if (!active || active[r]) out[((size_t)r * g.V + v) * n + row] = o;
       nv2[e & 1] += double(o.re) * o.re + double(o.im) * o.im;
@@ -311,8 +311,9 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
     if (last) {
       __threadfence();
       const int nvals = min(R, nrhs - r0);
-      cta_multi_sum(rb.partial + (size_t)r0 * nblk, nvals, (size_t)nblk, nblk, 1,
-                    [&](int i, double s) { rb.result[r0 + i] = s; });
+      cta_multi_sum(rb.partial + (size_t)r0 * nblk, nvals, (size_t)nblk, nblk, 1, [&](int i, double s) {
+        if (!active || active[r0 + i]) rb.result[r0 + i] = s;  // a masked launch leaves the others' sums
+      });
       if (threadIdx.x == 0) rb.counter[blockIdx.y] = 0u;
     }
   }

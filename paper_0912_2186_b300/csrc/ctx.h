@@ -49,7 +49,11 @@ struct LevelData {
   // precomputed odd-site pass -A_oo^-1 A_oe (FP16 tensor-core copies), one entry per mass shift
   std::vector<double> eoB_shift;
   long long eoB_version = -1;
-  const void* eoB_ptr = nullptr;
+  bool eoB_bj = false;               // the entries include the block-Jacobi tables
+  bool eo_bj_singular = false;       // a diagonal block of S was singular: no block-Jacobi
+  std::vector<const void*> eoB_ptrs;
+  std::vector<int> eoB_idx_up;
+  const void* eoB_idx_ptr = nullptr;
   std::vector<int> eoB_mask_up;  // per-entry right-hand-side masks last uploaded
   const void* eoB_mask_ptr = nullptr;
   size_t nvec_elems() const { return (size_t)g.V * ndof; }  // complex numbers per field
@@ -91,7 +95,8 @@ struct wmg_ctx {
   bool use_graphs = true;                      // capture the coarsest CGNR iterations
   int cg_chunk = 2;                            // CGNR iterations between convergence checks (even)
   bool use_fused_galerkin = true;              // fused fine-level Galerkin kernel
-  bool use_eoB = true;                         // precomputed odd-site pass for single-shift batches
+  bool use_eoB = true;                         // precomputed odd-site pass of the coarse Schur complement
+  bool use_eobj = true;                        // block-Jacobi preconditioned coarsest CG (with use_eoB)
   int* d_pcg_err = nullptr;                    // sticky error flag of the persistent CGNR (per solve)
   int* d_err = nullptr;                        // error word of the tensor-core stencils' bounded waits
                                                // (cleared at the start of each solve)

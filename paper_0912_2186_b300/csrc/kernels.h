@@ -185,7 +185,17 @@ void eo_hop_inverse(const void* A, const void* inv_entry, const Geom& g, int n, 
 // out_o[r] = M_r (bc b_o[r] + hc h_o[r]) at the odd sites, M_r = inv[idx[r]] or, for dagger,
 // sigma_3 inv[idx[r]] sigma_3; b or h may be null; out may alias h (not b)
 void eo_inv_apply(int prec, const void* inv, const int* idx, const Geom& g, int n, const void* b, double bc,
-                  const void* h, double hc, void* out, int nrhs, bool dagger, const int* active, cudaStream_t s);
+                  const void* h, double hc, void* out, int nrhs, bool dagger, const int* active, cudaStream_t s,
+                  int par = 1);  // par = 0: the same at the even sites with a table of even-site blocks
+// right block-Jacobi preconditioning of the Schur complement (coarse_eo.cu): M = (S_xx)^-1 per even
+// site for one shift (FP32 [even site][col][row]; A64 the FP64 stencil, inv_entry the shift's FP32
+// odd-inverse table entry), and the FP32 tables of the preconditioned passes (stencil layout
+// [parity site][9][col][row]): mode 0 B M(x + s) (odd sites, B from eo_hop_inverse), mode 1 the
+// even pass of S M, mode 2 M times the even pass (for M S)
+void eo_schur_self_inv(const void* A64, const void* inv_entry, const Geom& g, int n, double shift, void* M,
+                       int* singular, cudaStream_t s);
+void eo_bj_table(int mode, const void* A32, const void* B, const void* M, const Geom& g, int n, double shift,
+                 void* out, cudaStream_t s);
 // Galerkin build helpers: split the operator applied to column vectors into 9 slot fields
 // fine level: g = column (s, alpha) of P, written for ncol columns starting at col0
 void hop_split_fine(int prec, const void* gauge, const void* P, const Blocking& bk, double mass, int col0,

@@ -448,6 +448,13 @@ struct EoTable {
   const char* B16 = nullptr;    // entry e at B16 + e * Bstride
   size_t Bstride = 0;
   const float* sB = nullptr;    // entry e at sB + e * V / 2
+  // right block-Jacobi preconditioning (CG on T = S M): the odd pass of S M (Bp), the even passes
+  // of S M (E) and of M S (F, for T^dag = sigma_3 M S sigma_3), M itself and the per-rhs entry
+  bool bj = false;
+  const char *Bp16 = nullptr, *E16 = nullptr, *F16 = nullptr;
+  const float *sBp = nullptr, *sE = nullptr, *sF = nullptr;
+  const void* M32 = nullptr;    // entry e at M32 + e * V / 2 * n^2 complex FP32
+  const int* bj_idx = nullptr;  // [kMaxRhs] table entry of each right-hand side
   const int* Bmask = nullptr;   // launch i's right-hand sides: Bmask[i * kMaxRhs + r] (null for one launch)
   std::vector<int> order;       // launch i uses table entry order[i]
 };
@@ -540,16 +547,18 @@ static void eo_stencil(wmg_ctx* c, int l, int prec, const void* in, void* out, i
 // arithmetic does not depend on the other shifts in its batch.
 static wmg_status ensure_eoB(wmg_ctx* c, int l, int prec, int nrhs, EoTable* tb) {
   tb->nB = 0;
+  tb->bj = false;
   if (!c->use_eoB || !eo_mma(c, l, prec)) return WMG_OK;
   LevelData& L = c->L[l];
   const int n = L.ndof, Vh = L.g.V / 2;
+  const bool bj = c->use_eobj && !L.eo_bj_singular;
   const std::string tag = std::to_string(l);
   std::vector<double> need;
   for (int r = 0; r < nrhs; ++r)
     if (std::find(need.begin(), need.end(), c->h_shift[r]) == need.end()) need.push_back(c->h_shift[r]);
-  const size_t eb = stencil_mma_words(Vh, n) * 16;
+  const size_t eb = stencil_mma_words(Vh, n) * 16, mb = (size_t)Vh * n * n * sizeof(cf);
   std::vector<double>& tab = L.eoB_shift;
-  if (L.eoB_version != L.op_version) tab.clear();
+  if (L.eoB_version != L.op_version || L.eoB_bj != bj) tab.clear();
   std::vector<double> missing;
   for (double v : need)
     if (std::find(tab.begin(), tab.end(), v) == tab.end()) missing.push_back(v);
@@ -560,39 +569,75 @@ static wmg_status ensure_eoB(wmg_ctx* c, int l, int prec, int nrhs, EoTable* tb)
     missing = need;
   }
   const size_t want = std::max(cap, tab.size() + missing.size());
-  void *B16, *sB;
-  TRY(ws_get(c, "eoB16_" + tag, want * eb, &B16));
-  TRY(ws_get(c, "eoBs_" + tag, want * Vh * sizeof(float), &sB));
-  if (B16 != L.eoB_ptr && !tab.empty()) {  // the buffer moved: rebuild what this call needs
+  // the tables: FP16 fragment copies with per-site scales, one entry per shift
+  const char* names[4] = {"eoB16_", "eoBp16_", "eoE16_", "eoF16_"};
+  void* t16[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* tsc[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* M32 = nullptr;
+  for (int t = 0; t < (bj ? 4 : 1); ++t) {
+    TRY(ws_get(c, names[t] + tag, want * eb, &t16[t]));
+    TRY(ws_get(c, std::string(names[t]) + "s" + tag, want * Vh * sizeof(float), &tsc[t]));
+  }
+  if (bj) TRY(ws_get(c, "eoM_" + tag, want * mb, &M32));
+  std::vector<const void*> ptrs{t16[0], t16[1], t16[2], t16[3], tsc[0], tsc[1], tsc[2], tsc[3], M32};
+  if (ptrs != L.eoB_ptrs && !tab.empty()) {  // a buffer moved: rebuild what this call needs
     tab.clear();
     missing = need;
   }
   if (!missing.empty()) {
-    void* Bt;
+    void *Bt, *Bt2;
     TRY(ws_get(c, "eoBt_" + tag, (size_t)Vh * 9 * n * n * sizeof(cf), &Bt));
+    if (bj) TRY(ws_get(c, "eoBt2_" + tag, (size_t)Vh * 9 * n * n * sizeof(cf), &Bt2));
     const std::vector<double>& inv_tab = L.eo_shift[prec];
     ProfScope ps(c, PROF_CGNR, 0);
+    // slot 0 of the odd-site tables is never read by the hop-only pass; zero it so that it does not
+    // enter the per-site scales
+    CU(c, cudaMemsetAsync(Bt, 0, (size_t)Vh * 9 * n * n * sizeof(cf), c->stream));
+    if (bj) CU(c, cudaMemsetAsync(c->d_flag + 3, 0, sizeof(int), c->stream));
     for (double sh : missing) {
       const size_t ei = (size_t)(std::find(inv_tab.begin(), inv_tab.end(), sh) - inv_tab.begin());
       const void* inv_e = (const char*)tb->inv + ei * eo_inverse_bytes(prec, L.g, n);
       const size_t e = tab.size();
       eo_hop_inverse(L.A[WMG_PREC_SINGLE], inv_e, L.g, n, Bt, c->stream);
-      stencil_to_mma(WMG_PREC_SINGLE, Bt, Vh, n, (float*)sB + e * Vh, (char*)B16 + e * eb, c->stream);
+      stencil_to_mma(WMG_PREC_SINGLE, Bt, Vh, n, (float*)tsc[0] + e * Vh, (char*)t16[0] + e * eb, c->stream);
+      if (bj) {
+        void* Me = (char*)M32 + e * mb;
+        eo_schur_self_inv(L.A[WMG_PREC_DOUBLE], inv_e, L.g, n, sh, Me, c->d_flag + 3, c->stream);
+        // slot 0 of the odd-site table must be zero for every entry (the even-site tables written
+        // before it fill slot 0): it enters the per-site scale of the FP16 copy
+        CU(c, cudaMemsetAsync(Bt2, 0, (size_t)Vh * 9 * n * n * sizeof(cf), c->stream));
+        for (int mode = 0; mode < 3; ++mode) {
+          eo_bj_table(mode, L.A[WMG_PREC_SINGLE], Bt, Me, L.g, n, sh, Bt2, c->stream);
+          stencil_to_mma(WMG_PREC_SINGLE, Bt2, Vh, n, (float*)tsc[1 + mode] + e * Vh, (char*)t16[1 + mode] + e * eb,
+                         c->stream);
+        }
+      }
       tab.push_back(sh);
+    }
+    if (bj) {
+      CU(c, cudaMemcpyAsync(c->h_pin_i, c->d_flag + 3, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+      CU(c, cudaStreamSynchronize(c->stream));
+      if (c->h_pin_i[0]) {  // a singular diagonal block of S: this operator runs without the preconditioner
+        L.eo_bj_singular = true;
+        L.eoB_shift.clear();
+        return ensure_eoB(c, l, prec, nrhs, tb);
+      }
     }
   }
   TRY(check(c, "even-odd odd-site operator"));
   L.eoB_version = L.op_version;
-  L.eoB_ptr = B16;
-  // the entries in the order of `need`, and their right-hand-side masks
+  L.eoB_bj = bj;
+  L.eoB_ptrs = ptrs;
+  // the entries in the order of `need`, their right-hand-side masks and each rhs's entry
   std::vector<int> order(need.size());
   for (size_t i = 0; i < need.size(); ++i)
     order[i] = (int)(std::find(tab.begin(), tab.end(), need[i]) - tab.begin());
   tb->nB = (int)need.size();
-  tb->B16 = (const char*)B16;
+  tb->B16 = (const char*)t16[0];
   tb->Bstride = eb;
-  tb->sB = (const float*)sB;
+  tb->sB = (const float*)tsc[0];
   tb->Bmask = nullptr;
+  tb->order = order;
   if (need.size() > 1) {
     std::vector<int> mask((size_t)kMaxRhs * need.size(), 0);
     for (size_t i = 0; i < need.size(); ++i)
@@ -609,7 +654,26 @@ static wmg_status ensure_eoB(wmg_ctx* c, int l, int prec, int nrhs, EoTable* tb)
     }
     tb->Bmask = dm;
   }
-  tb->order = order;
+  if (bj) {
+    tb->bj = true;
+    tb->Bp16 = (const char*)t16[1];
+    tb->E16 = (const char*)t16[2];
+    tb->F16 = (const char*)t16[3];
+    tb->sBp = (const float*)tsc[1];
+    tb->sE = (const float*)tsc[2];
+    tb->sF = (const float*)tsc[3];
+    tb->M32 = M32;
+    std::vector<int> idx(kMaxRhs, 0);
+    for (int r = 0; r < nrhs; ++r) idx[r] = (int)(std::find(tab.begin(), tab.end(), c->h_shift[r]) - tab.begin());
+    int* di;
+    TRY(ws_get(c, "eoBidx_" + tag, (size_t)kMaxRhs * sizeof(int), (void**)&di));
+    if (idx != L.eoB_idx_up || di != L.eoB_idx_ptr) {
+      TRY(upload_ints(c, di, idx));
+      L.eoB_idx_up = idx;
+      L.eoB_idx_ptr = di;
+    }
+    tb->bj_idx = di;
+  }
   return WMG_OK;
 }
 
@@ -621,13 +685,30 @@ static void schur_op(wmg_ctx* c, int l, int prec, const EoTable& tb, const void*
   hop.parity = 1;
   hop.hop_only = 1;
   if (eo_mma(c, l, prec) && tb.nB > 0) {
-    // -A_oo^-1 A_oe precomputed per shift: one launch per shift of the call
+    // -A_oo^-1 A_oe precomputed per shift: one launch per shift of the call.  With the block-Jacobi
+    // preconditioner the operator is T = S M (odd pass B M, even pass E = [(A_xx + s) M_x | A_eo])
+    // and its adjoint sigma_3 (M S) sigma_3 (odd pass B, even pass F = M_x [A_xx + s | A_eo]).
     const int Vh = L.g.V / 2;
+    const bool pre = tb.bj && !dagger;
     for (int i = 0; i < tb.nB; ++i) {
-      hop.opB = tb.B16 + (size_t)tb.order[i] * tb.Bstride;
-      hop.sB = tb.sB + (size_t)tb.order[i] * Vh;
+      const size_t e = (size_t)tb.order[i];
+      hop.opB = (pre ? tb.Bp16 : tb.B16) + e * tb.Bstride;
+      hop.sB = (pre ? tb.sBp : tb.sB) + e * Vh;
       coarse_apply_mma(L.A16, L.sA, L.g, L.ndof, in, t, nrhs, c->d_shift[l], dagger,
                        tb.Bmask ? tb.Bmask + (size_t)i * kMaxRhs : nullptr, nullptr, c->stream, &hop, c->d_err);
+    }
+    if (tb.bj) {
+      StencilEo ev;
+      ev.parity = 0;
+      ev.hop_in = t;
+      for (int i = 0; i < tb.nB; ++i) {
+        const size_t e = (size_t)tb.order[i];
+        ev.opB = (dagger ? tb.F16 : tb.E16) + e * tb.Bstride;
+        ev.sB = (dagger ? tb.sF : tb.sE) + e * Vh;
+        coarse_apply_mma(L.A16, L.sA, L.g, L.ndof, in, out, nrhs, nullptr, dagger,
+                         tb.Bmask ? tb.Bmask + (size_t)i * kMaxRhs : nullptr, rb, c->stream, &ev, c->d_err);
+      }
+      return;
     }
   } else if (eo_mma(c, l, prec)) {
     hop.inv = tb.inv;  // the tensor-core pass applies the block inverses in its epilogue
@@ -648,6 +729,7 @@ wmg_status schur_apply(wmg_ctx* c, int l, int prec, const void* in, void* out, i
   EoTable tb;
   TRY(ensure_eo(c, l, prec, nrhs, &tb));
   TRY(ensure_eoB(c, l, prec, nrhs, &tb));
+  tb.bj = false;  // this entry point applies S itself
   void* t;
   TRY(vec_ws(c, l, "eo_t", prec, nrhs, &t));
   blas_zero(prec, out, c->L[l].nvec_elems(), nrhs, c->stream);
@@ -794,6 +876,7 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
                   t, (const void*)tb.B16, (const void*)(size_t)(tb.nB * 1000 + (tb.Bmask ? 1 : 0)));
     std::string gkey(key);
     for (int e : tb.order) gkey += "/" + std::to_string(e);  // the odd-site launches' table entries
+    if (tb.bj) gkey += "/bj";
     auto it = c->graphs.find(gkey);
     if (it == c->graphs.end()) {
       if (c->graphs.size() > 64) TRY(clear_graphs(c));
@@ -837,6 +920,8 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
       if (all) break;
     }
   }
+  if (eo && tb.bj)  // the CG ran on T = S M: x_e = M y
+    eo_inv_apply(prec, tb.M32, tb.bj_idx, L.g, L.ndof, nullptr, 0.0, x, 1.0, x, nrhs, false, nullptr, s, 0);
   if (eo) {
     // x_o = A_oo^-1 (b_o - A_oe x_e)
     StencilEo hop;
@@ -941,6 +1026,7 @@ wmg_status galerkin(wmg_ctx* c, int l, int prec) {
     }
   }
   ++C.op_version;
+  C.eo_bj_singular = false;
   if (c->prm.coarse_tc == 3 && c->prm.prec_sloppy == WMG_PREC_SINGLE) TRY(tune_coarse(c, l + 1));
   return check(c, "galerkin");
 }
