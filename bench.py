@@ -39,8 +39,8 @@ WORKLOADS = {
 }
 # outer iterations per mass the GPU arm measures on this job (mean over the 12 point sources), used
 # by --impl reference, which runs without a GPU, to scale its sample to the whole job
-REFERENCE_ITERS = {"16x16x16x32": [38.4, 46.8, 53.2]}
-REFERENCE_CG = {"16x16x16x32": [15.3, 37.3, 65.8]}  # coarsest CG iterations per cycle, the same source
+REFERENCE_ITERS = {"16x16x16x32": [37.0, 43.9, 48.9]}
+REFERENCE_CG = {"16x16x16x32": [9.3, 23.9, 43.1]}  # coarsest CG iterations per cycle, the same source
 PROF_CLASSES = ("dslash_sloppy", "dslash_fp64", "coarse", "restrict", "prolong", "blas", "setup", "cgnr",
                 "blas_coarse")
 

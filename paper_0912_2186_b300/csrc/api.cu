@@ -241,6 +241,7 @@ wmg_status wmg_create(wmg_ctx** out, const int dims[4], void* stream) {
   if (const char* g = std::getenv("WMG_UNFUSED_GALERKIN")) c->use_fused_galerkin = !(g[0] == '1');
   if (const char* g = std::getenv("WMG_NO_EOB")) c->use_eoB = !(g[0] == '1');
   if (const char* g = std::getenv("WMG_NO_BJ")) c->use_eobj = !(g[0] == '1');
+  if (const char* g = std::getenv("WMG_MR_FUSE")) c->use_mr_fuse = g[0] == '1';
   c->L[0].g = c->fine;
   c->L[0].ndof = 12;
   cudaError_t e = cudaSuccess;

@@ -97,6 +97,8 @@ struct wmg_ctx {
   bool use_fused_galerkin = true;              // fused fine-level Galerkin kernel
   bool use_eoB = true;                         // precomputed odd-site pass of the coarse Schur complement
   bool use_eobj = true;                        // block-Jacobi preconditioned coarsest CG (with use_eoB)
+  bool use_mr_fuse = false;                    // fine MR steps fused with the previous step's update
+                                               // (WMG_MR_FUSE=1; measured no faster on the 16^3x32 job)
   int* d_pcg_err = nullptr;                    // sticky error flag of the persistent CGNR (per solve)
   int* d_err = nullptr;                        // error word of the tensor-core stencils' bounded waits
                                                // (cleared at the start of each solve)

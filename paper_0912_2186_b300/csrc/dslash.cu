@@ -174,6 +174,100 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(void* __
 }
 
 // ------------------------------------------------------------------------------------
+// One MR step with the previous step's update fused in (the smoother of Sec. 3): with r, q =
+// D r and alpha = <q, r> / |q|^2 of the previous step (red_prev, per rhs; 0 when |q| = 0),
+//   r' = r - alpha q  (own site written to r_out; at the neighbours formed on the fly),
+//   x += alpha r      (own site),
+//   q' = D r'         with the sums {Re, Im <q', r'>, |q'|^2} into rb,
+// so that the update costs no pass of its own.  r_out and out must not alias r or q (other CTAs
+// read them at their neighbours); rb.result must not be red_prev.  Same partition of sites into
+// CTAs as k_dslash<R, 2> (the order of the per-rhs sums depends on the volume only).
+// ------------------------------------------------------------------------------------
+template <typename R, int GC>
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_dslash_mr(void* __restrict__ out,
+                                                                           const void* __restrict__ in,
+                                                                           const void* __restrict__ qin,
+                                                                           void* __restrict__ rout,
+                                                                           void* __restrict__ x,
+                                                                           const double* __restrict__ red_prev,
+                                                                           const void* __restrict__ gauge, Geom g,
+                                                                           DslashDiv dv,
+                                                                           const double* __restrict__ mass,
+                                                                           const int* __restrict__ active, int nrhs,
+                                                                           int nblk_site, RedBuf rb) {
+  constexpr int SPB = dslash_spb<R, 2>();
+  const int rhs = blockIdx.x % nrhs;
+  const int sbe = blockIdx.x / nrhs;
+  if (active && !active[rhs]) return;  // whole CTA exits together (uniform per CTA)
+  const size_t fb = spinor_field_bytes<R>(g.V);
+  const char* inr = reinterpret_cast<const char*>(in) + fb * rhs;
+  const char* qr = reinterpret_cast<const char*>(qin) + fb * rhs;
+  const double qq = red_prev[rhs * 3 + 2];
+  const cpx<R> al = qq > 0.0 ? cpx<R>{R(red_prev[rhs * 3 + 0] / qq), R(red_prev[rhs * 3 + 1] / qq)}
+                             : cpx<R>{R(0), R(0)};
+  double red[3] = {0.0, 0.0, 0.0};
+#pragma unroll 1
+  for (int j = 0; j < SPB; ++j) {
+    const int v = (sbe * SPB + j) * blockDim.x + threadIdx.x;
+    if (v >= g.V) continue;
+    cpx<R> acc[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[i] = cpx<R>{R(0), R(0)};
+    int c[4];
+    site_coords_fast(g, dv, v, c);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      cpx<R> u[9], nb[12], nq[12];
+      const int vf = neighbour(g, v, c, mu, +1);
+      load_link_gc<R, GC>(gauge, g.V, mu, v, u);
+      load_spinor<R>(inr, g.V, vf, nb);
+      load_spinor<R>(qr, g.V, vf, nq);
+#pragma unroll
+      for (int i = 0; i < 12; ++i) nb[i] = nb[i] - al * nq[i];
+      hop_accumulate<+1>(mu, u, nb, acc);
+      const int vb = neighbour(g, v, c, mu, -1);
+      load_link_gc<R, GC>(gauge, g.V, mu, vb, u);
+      load_spinor<R>(inr, g.V, vb, nb);
+      load_spinor<R>(qr, g.V, vb, nq);
+#pragma unroll
+      for (int i = 0; i < 12; ++i) nb[i] = nb[i] - al * nq[i];
+      hop_accumulate<-1>(mu, u, nb, acc);
+    }
+    cpx<R> self[12], qs[12], xs[12];
+    load_spinor<R>(inr, g.V, v, self);
+    load_spinor<R>(qr, g.V, v, qs);
+    char* xr = reinterpret_cast<char*>(x) + fb * rhs;
+    load_spinor<R>(xr, g.V, v, xs);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      cfma(xs[i], al, self[i]);       // x += alpha r
+      self[i] = self[i] - al * qs[i];  // r' = r - alpha q
+    }
+    store_spinor<R>(xr, g.V, v, xs);
+    store_spinor<R>(reinterpret_cast<char*>(rout) + fb * rhs, g.V, v, self);
+    const R diag = R(4.0 + mass[rhs]);
+    const R half = R(-0.5);
+#pragma unroll
+    for (int i = 0; i < 12; ++i)
+      acc[i] = cpx<R>{diag * self[i].re + half * acc[i].re, diag * self[i].im + half * acc[i].im};
+    store_spinor<R>(reinterpret_cast<char*>(out) + fb * rhs, g.V, v, acc);
+    R a0 = 0, a1 = 0, nn = 0;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      a0 += acc[i].re * self[i].re + acc[i].im * self[i].im;
+      a1 += acc[i].re * self[i].im - acc[i].im * self[i].re;
+      nn += acc[i].re * acc[i].re + acc[i].im * acc[i].im;
+    }
+    red[0] += double(a0);
+    red[1] += double(a1);
+    red[2] += double(nn);
+  }
+  __shared__ double sm[32 * 3];
+  cta_reduce<3>(red, sm);
+  grid_finish<3>(rb, rhs, sbe, nblk_site, red);
+}
+
+// ------------------------------------------------------------------------------------
 // The smoother's FP16 storage (FP32 arithmetic).  out16 (+ per-site norms) = [b -] D in, with
 // in FP32 native (IN16 = 0) or FP16 with norms (IN16 = 1) and b FP32 native; the scale of an
 // FP16 neighbour enters the accumulation of its hop.  RED = 2: per rhs {<out, in>, |out|^2}
@@ -372,6 +466,26 @@ void dslash(int prec, void* out, const void* in, const void* b, const void* gaug
   else if (gc == 8) WMG_DS(float, 8);
   else WMG_DS(float, 12);
 #undef WMG_DS
+}
+
+void dslash_mr(int prec, void* out, const void* r, const void* q, void* r_out, void* x, const double* red_prev,
+               const void* gauge, const Geom& g, const double* mass_dev, const int* active, int nrhs,
+               const RedBuf& rb, cudaStream_t s, int gc) {
+  count_launch();
+  const int nb = dslash_blocks(g.V);
+  const int spb = prec == WMG_PREC_DOUBLE ? dslash_spb<double, 2>() : dslash_spb<float, 2>();
+  const int nbr = (nb + spb - 1) / spb;
+  const unsigned grid = (unsigned)nbr * nrhs;
+  const DslashDiv dv{make_fastdiv(g.L[0]), make_fastdiv(g.L[1]), make_fastdiv(g.L[2])};
+  if (prec == WMG_PREC_DOUBLE)
+    k_dslash_mr<double, 12><<<grid, kDslashThreads, 0, s>>>(out, r, q, r_out, x, red_prev, gauge, g, dv, mass_dev,
+                                                             active, nrhs, nbr, rb);
+  else if (gc == 8)
+    k_dslash_mr<float, 8><<<grid, kDslashThreads, 0, s>>>(out, r, q, r_out, x, red_prev, gauge, g, dv, mass_dev,
+                                                           active, nrhs, nbr, rb);
+  else
+    k_dslash_mr<float, 12><<<grid, kDslashThreads, 0, s>>>(out, r, q, r_out, x, red_prev, gauge, g, dv, mass_dev,
+                                                            active, nrhs, nbr, rb);
 }
 
 template <int GC>

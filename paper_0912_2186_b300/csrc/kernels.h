@@ -30,6 +30,12 @@ int dslash_blocks(int V);
 void dslash(int prec, void* out, const void* in, const void* b, const void* gauge, const Geom& g,
             const double* mass_dev, const int* active, int nrhs, int red, const RedBuf* rb, cudaStream_t s,
             int gc = 12);
+// one MR step with the previous update fused in: r_out = r - alpha q, x += alpha r, out = D r_out
+// with the sums {Re, Im <out, r_out>, |out|^2} per rhs into rb (alpha from red_prev[3 r ..]);
+// out and r_out must not alias r, q; rb.result must not alias red_prev
+void dslash_mr(int prec, void* out, const void* r, const void* q, void* r_out, void* x, const double* red_prev,
+               const void* gauge, const Geom& g, const double* mass_dev, const int* active, int nrhs,
+               const RedBuf& rb, cudaStream_t s, int gc = 12);
 // 8-real FP32 links from the native FP64 12-real links; *degenerate (device int) set to 1 if a
 // link has |U_01|^2 + |U_02|^2 < 1e-6 (the 8-real form cannot represent it accurately)
 void pack_gauge8(const void* g64, void* out, int V, int* degenerate, cudaStream_t s);

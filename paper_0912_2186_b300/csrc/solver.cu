@@ -84,7 +84,7 @@ wmg_status vec_ws(wmg_ctx* c, int l, const char* tag, int prec, int nrhs, void**
 
 static double* res_slot(wmg_ctx* c, int slot) { return c->res + (size_t)slot * kMaxRhs * 16; }
 enum { RES_MR = 0, RES_NORM, RES_WRED, RES_RN, RES_R64, RES_BB, RES_CGQQ, RES_CGRR, RES_CGBB, RES_CGZZ,
-       RES_SETUP, RES_COEF = 16, RES_SLOTS = 24 };
+       RES_SETUP, RES_MR2, RES_COEF = 16, RES_SLOTS = 24 };
 
 RedBuf redbuf(wmg_ctx* c, int slot) { return RedBuf{c->red_partial, c->red_counter, res_slot(c, slot)}; }
 
@@ -367,6 +367,37 @@ wmg_status mr(wmg_ctx* c, int l, int prec, void* x, const void* b, int nrhs, int
   const int dcls = prec == WMG_PREC_DOUBLE ? PROF_DSLASH_64 : PROF_DSLASH_LO;
   int gc;
   const void* U = links(c, prec, &gc);
+  if (l == 0 && c->use_mr_fuse && nu > 0) {
+    // r = b - D x; q = D r with the step's sums; then each later step fused with the previous
+    // step's update (r and q ping-pong between two buffers, the sums between two result slots);
+    // the last update (x += alpha r) on its own
+    void *r2, *q2;
+    TRY(vec_ws(c, l, "mr_r2", prec, nrhs, &r2));
+    TRY(vec_ws(c, l, "mr_q2", prec, nrhs, &q2));
+    RedBuf ra = rb, rbb = redbuf(c, RES_MR2);
+    {
+      ProfScope ps(c, dcls, dslash_bytes(c, prec, na, true), na);
+      dslash(prec, r, x, b, U, c->fine, c->d_mass, active, nrhs, 0, nullptr, c->stream, gc);
+    }
+    {
+      ProfScope ps(c, dcls, dslash_bytes(c, prec, na, false), na);
+      dslash(prec, q, r, nullptr, U, c->fine, c->d_mass, active, nrhs, 2, &ra, c->stream, gc);
+    }
+    // fused step: links + (x, r, q read; x, r', q' written) per rhs
+    const double fb = dslash_bytes(c, prec, na, false) + 4.0 * (double)na * c->fine.V * 24.0 * rb_(prec);
+    for (int i = 1; i < nu; ++i) {
+      {
+        ProfScope ps(c, dcls, fb, na);
+        dslash_mr(prec, q2, r, q, r2, x, ra.result, U, c->fine, c->d_mass, active, nrhs, rbb, c->stream, gc);
+      }
+      std::swap(r, r2);
+      std::swap(q, q2);
+      std::swap(ra, rbb);
+    }
+    ProfScope ps(c, PROF_BLAS, vec_bytes(c, l, prec, na, 3), na);
+    blas_mr_update(prec, x, r, q, n, nrhs, ra.result, false, active, c->stream);
+    return check(c, "mr (fused steps)");
+  }
   if (l == 0) {
     ProfScope ps(c, dcls, dslash_bytes(c, prec, na, true), na);
     dslash(prec, r, x, b, U, c->fine, c->d_mass, active, nrhs, 0, nullptr, c->stream, gc);

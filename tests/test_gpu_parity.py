@@ -151,13 +151,16 @@ def test_cycle_single_precision_matches_oracle(W):
     assert err < 1e-4, err
 
 
+@pytest.mark.parametrize("fused", [0, 1])
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("dims", [(6, 4, 4, 10), (8, 8, 8, 16)])
-def test_smoother_matches_oracle_mr(W, prec, dims):
+def test_smoother_matches_oracle_mr(W, prec, dims, fused, monkeypatch):
     """nu = 4 MR steps on D x = b from a random guess, 12 right-hand sides (the FP32 dslash with
-    fused <q, r>, |q|^2 sums over 4 site blocks per CTA); V = 960 leaves a ragged last CTA."""
+    fused <q, r>, |q|^2 sums over 4 site blocks per CTA; fused = 1: each later step fused with the
+    previous step's update, WMG_MR_FUSE=1); V = 960 leaves a ragged last CTA."""
     m = -0.4
     U = synth.gauge_field(dims, 0.6, 64)
+    monkeypatch.setenv("WMG_MR_FUSE", str(fused))
     ctx = W.Context(dims)
     ctx.load_gauge(U)
     ctx.set_mass(m)
