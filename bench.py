@@ -37,6 +37,15 @@ WORKLOADS = {
     "16x16x16x32": dict(dims=(16, 16, 16, 32), eps=0.6, gauge_seed=11, nvec=24, block=(4, 4, 4, 4), nrhs=12,
                         masses_file=os.path.join(ROOT, "tests", "golden", "masses_16x16x16x32_eps0.6.json")),
 }
+# The larger workloads (a line for the design notes, not the benchmark's job): 3 levels, Gaussian
+# right-hand sides, a hand-chosen mass near the field's critical region (no oracle mass search was
+# run on these volumes); the 48^3x96 one with FP16 null vectors and its device footprint.
+LARGE = {
+    "24x24x24x48": dict(dims=(24, 24, 24, 48), eps=0.7, gauge_seed=31, nvec=[24, 32],
+                        block=[(4, 4, 4, 4), (2, 2, 2, 2)], nrhs=12, mass=-1.2, prec_nullvec=1),
+    "48x48x48x96": dict(dims=(48, 48, 48, 96), eps=0.7, gauge_seed=51, nvec=[24, 32],
+                        block=[(4, 4, 4, 4), (2, 2, 2, 2)], nrhs=4, mass=-1.2, prec_nullvec=2),
+}
 # outer iterations per mass the GPU arm measures on this job (mean over the 12 point sources), used
 # by --impl reference, which runs without a GPU, to scale its sample to the whole job
 REFERENCE_ITERS = {"16x16x16x32": [37.0, 43.9, 48.9]}
@@ -647,7 +656,8 @@ def run_probe(args, w):
     is built first (the job's setup at the lightest mass); inside the range each of the FP32 fine
     dslash, restrict, prolong, the tensor-core coarse stencil and the even-odd Schur complement of
     the coarse operator runs --probe-reps times on 12 right-hand sides, then (--probe-solve) the 12
-    point sources are solved once at --probe-mass (default the heaviest of the job's masses)."""
+    point sources are solved once at --probe-mass (default the heaviest of the job's masses), with
+    the benchmark's setup and solver parameters."""
     import torch
 
     from paper_0912_2186_b300 import build, wmg
@@ -658,7 +668,8 @@ def run_probe(args, w):
     ctx = wmg.Context(dims)
     ctx.load_gauge(torch.from_numpy(synth.gauge_field(dims, w["eps"], w["gauge_seed"])).cuda())
     ctx.set_mass(masses[-1])
-    ctx.setup(wmg.default_params(nvec=[w["nvec"]], block=[w["block"]], prec_sloppy=wmg.PREC_SINGLE))
+    ctx.setup(wmg.default_params(nvec=[w["nvec"]], block=[w["block"]], prec_sloppy=wmg.PREC_SINGLE, setup_relax=200,
+                                 setup_passes=2, fine_eo=1))
     m = args.probe_mass if args.probe_mass is not None else masses[0]
     ctx.set_mass(m)
     nc, n = ctx.level_info(1)
@@ -703,6 +714,66 @@ def run_probe(args, w):
     ctx.close()
 
 
+def run_large(args):
+    """One setup and one batched solve on a larger workload: 3 levels (4^4 then 2^4 blocks, N = 24 and
+    32), FP16 smoother storage, tensor-core coarse stencils (autotuned), Gaussian right-hand sides;
+    time-to-solution (setup and solve), iterations, the library's FP64 true residuals, one of them
+    checked with the oracle's C operator, the isolated dslash and the device footprint."""
+    import torch
+
+    from paper_0912_2186_b300 import build, wmg
+    build.build()
+    w = LARGE[args.large]
+    dims, nrhs, m = w["dims"], w["nrhs"], w["mass"]
+    V = int(np.prod(dims))
+    U = synth.gauge_field(dims, w["eps"], w["gauge_seed"])
+    b = synth.gaussian_spinors(dims, nrhs, w["gauge_seed"] + 1)
+    ctx = wmg.Context(dims)
+    ctx.load_gauge(torch.from_numpy(U).cuda())
+    ctx.set_mass(m)
+    p = wmg.default_params(nlevels=3, block=w["block"], nvec=w["nvec"], prec_sloppy=wmg.PREC_SINGLE,
+                           prec_smoother=wmg.PREC_HALF, prec_nullvec=w["prec_nullvec"], coarse_tc=3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.setup(p)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    bytes_setup = ctx.device_bytes()
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    ctx.solve(bd, x, nrhs)  # warm: workspaces and graphs
+    x.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, info = ctx.solve(bd, x, nrhs)
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    from oracle import cref
+    x0 = x[0].cpu().numpy()
+    ores = float(np.linalg.norm(b[0] - cref.apply_D(U, x0, m)) / np.linalg.norm(b[0]))
+    impl = [ctx.coarse_impl(lv) for lv in (1, 2)]
+    xin = torch.zeros(nrhs * 12 * V, dtype=torch.complex64, device="cuda")
+    xout = torch.zeros_like(xin)
+    for _ in range(3):
+        ctx.apply_D(wmg.PREC_SINGLE, xin, xout, nrhs)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        ctx.apply_D(wmg.PREC_SINGLE, xin, xout, nrhs)
+    e1.record()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3 / 20
+    peaks, _ = measured_peaks()
+    by = V * 48 * 4 + nrhs * V * 48 * 4
+    print(json.dumps({
+        "workload": args.large, "mass": m, "mass_source": "hand-chosen", "nrhs": nrhs, "setup_s": t_setup,
+        "solve_s": t_solve, "iters": [i["iters"] for i in info], "max_true_resid": max(i["true_resid"] for i in info),
+        "oracle_resid_rhs0": ores, "status": int(st), "coarse_impl_and_tuner_ms": impl,
+        "device_bytes_after_setup": bytes_setup, "device_bytes_after_solve": ctx.device_bytes(),
+        "dslash_fp32": {"nrhs": nrhs, "us": sec * 1e6, "GB_s": by / sec / 1e9, "frac_hbm": by / sec / 1e9 / peaks["hbm_gbs"]},
+    }))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -718,9 +789,13 @@ def main():
     ap.add_argument("--probe-reps", type=int, default=2)
     ap.add_argument("--probe-mass", type=float, default=None)
     ap.add_argument("--probe-solve", action="store_true")
+    ap.add_argument("--large", default=None, choices=sorted(LARGE),
+                    help="one setup and solve on a larger workload (a line for the design notes)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
-    if args.probe:
+    if args.large:
+        run_large(args)
+    elif args.probe:
         run_probe(args, w)
     elif args.impl == "reference":
         run_reference(args, w)

@@ -1181,8 +1181,8 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
     TRY(vec_ws(c, 0, "eo_tlo", lo, nslots, &tlo));
     TRY(vec_ws(c, 0, "eo_rfl", lo, nslots, &rfl));
     TRY(vec_ws(c, 0, "eo_zfl", lo, nslots, &zfl));
-    TRY(vec_ws(c, 0, "eo_xfull", WMG_PREC_DOUBLE, 1, &xfull));
-    TRY(vec_ws(c, 0, "eo_xo", WMG_PREC_DOUBLE, 1, &xo));
+    TRY(vec_ws(c, 0, "eo_xfull", WMG_PREC_DOUBLE, nslots, &xfull));
+    TRY(vec_ws(c, 0, "eo_xo", WMG_PREC_DOUBLE, nslots, &xo));
   }
   const Geom& fg = c->fine;
   // the system's operator in the sloppy precision: D, or S = d - H_eo H_oe / d on half fields
@@ -1250,20 +1250,34 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
     c->n_active = 0;
     for (int r = 0; r < nslots; ++r) c->n_active += active[r];
   };
-  auto finish = [&](int r, bool conv) -> wmg_status {
-    wmg_info info{};
-    info.iters = iters[r];
-    info.reliable_updates = relups[r];
-    info.converged = conv;
-    info.true_resid = tres[r];
-    info.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0[r]).count();
-    active[r] = 0;
-    if (!eo) return src.finish(c, r, at(x64, f64, r), info);
-    // x_o = (b_o - H_oe x_e) / d, then the whole-lattice solution
-    dslash_eo(WMG_PREC_DOUBLE, 3, 1, xo, at(x64, f64, r), at(boh, f64, r), nullptr, c->gauge[0], 12, fg,
-              c->d_mass + r, nullptr, 1, nullptr, s);
-    eo_embed(WMG_PREC_DOUBLE, xfull, at(x64, f64, r), xo, fg, 1, s);
-    return src.finish(c, r, xfull, info);
+  // hand the finished slots (slot, converged) to the source; red/black: x_o = (b_o - H_oe x_e) / d
+  // for all of them in one launch, then each whole-lattice solution
+  auto finish_many = [&](const std::vector<std::pair<int, bool>>& fl) -> wmg_status {
+    if (fl.empty()) return WMG_OK;
+    if (eo) {
+      std::vector<int> m(nslots, 0);
+      for (const auto& f : fl) m[f.first] = 1;
+      TRY(upload_ints(c, c->d_mask, m));
+      dslash_eo(WMG_PREC_DOUBLE, 3, 1, xo, x64, boh, nullptr, c->gauge[0], 12, fg, c->d_mass, c->d_mask, nslots,
+                nullptr, s);
+    }
+    for (const auto& f : fl) {
+      const int r = f.first;
+      wmg_info info{};
+      info.iters = iters[r];
+      info.reliable_updates = relups[r];
+      info.converged = f.second;
+      info.true_resid = tres[r];
+      info.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0[r]).count();
+      active[r] = 0;
+      if (!eo) {
+        TRY(src.finish(c, r, at(x64, f64, r), info));
+      } else {
+        eo_embed(WMG_PREC_DOUBLE, at(xfull, ffull, r), at(x64, f64, r), at(xo, f64, r), fg, 1, s);
+        TRY(src.finish(c, r, at(xfull, ffull, r), info));
+      }
+    }
+    return WMG_OK;
   };
   TRY(set_rhs_scalars(c, mass.data(), nslots));
   CU(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
@@ -1285,17 +1299,18 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
           t0[a.slot] = std::chrono::steady_clock::now();
         }
         TRY(set_rhs_scalars(c, mass.data(), nslots));
+        for (const Admission& a : adm)
+          pack_spinor(WMG_PREC_DOUBLE, a.b_canon_dev, eo ? at(bfull, ffull, a.slot) : at(b64, f64, a.slot), fg.V, 1, s);
+        if (eo) {
+          // b^_e = b_e - H_eo b_o / d for the admitted slots in one launch (the halves of every slot's
+          // b are rewritten from its unchanged whole-lattice b)
+          TRY(upload_ints(c, c->d_mask, mask));
+          eo_extract(WMG_PREC_DOUBLE, beh, bfull, fg, 0, nslots, s);
+          eo_extract(WMG_PREC_DOUBLE, boh, bfull, fg, 1, nslots, s);
+          dslash_eo(WMG_PREC_DOUBLE, 2, 0, b64, boh, beh, nullptr, c->gauge[0], 12, fg, c->d_mass, c->d_mask, nslots,
+                    nullptr, s);
+        }
         for (const Admission& a : adm) {
-          if (!eo) {
-            pack_spinor(WMG_PREC_DOUBLE, a.b_canon_dev, at(b64, f64, a.slot), fg.V, 1, s);
-          } else {
-            // b^_e = b_e - H_eo b_o / d
-            pack_spinor(WMG_PREC_DOUBLE, a.b_canon_dev, at(bfull, ffull, a.slot), fg.V, 1, s);
-            eo_extract(WMG_PREC_DOUBLE, at(beh, f64, a.slot), at(bfull, ffull, a.slot), fg, 0, 1, s);
-            eo_extract(WMG_PREC_DOUBLE, at(boh, f64, a.slot), at(bfull, ffull, a.slot), fg, 1, 1, s);
-            dslash_eo(WMG_PREC_DOUBLE, 2, 0, at(b64, f64, a.slot), at(boh, f64, a.slot), at(beh, f64, a.slot),
-                      nullptr, c->gauge[0], 12, fg, c->d_mass + a.slot, nullptr, 1, nullptr, s);
-          }
           blas_zero(WMG_PREC_DOUBLE, at(x64, f64, a.slot), n, 1, s);
           blas_zero(lo, at(xlo, flo, a.slot), n, 1, s);
           blas_convert(WMG_PREC_DOUBLE, at(r64, f64, a.slot), WMG_PREC_DOUBLE, at(b64, f64, a.slot), n, 1, nullptr, s);
@@ -1311,7 +1326,7 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
           bnorm[r] = ref[r] = std::sqrt(bb[r]);
           tres[r] = 0.0;
           if (bb[r] > 0.0) active[r] = 1;
-          else TRY(finish(r, true));  // b = 0: x = 0 exactly
+          else TRY(finish_many({{r, true}}));  // b = 0: x = 0 exactly
         }
         TRY(upload_ints(c, c->d_active, active));
         count_active();
@@ -1381,21 +1396,18 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
       }
       TRY(download(c, rb_r64.result, nslots, t));
       blas_convert(lo, rlo, WMG_PREC_DOUBLE, r64, n, nslots, c->d_mask, s);
-      bool changed = false;
+      std::vector<std::pair<int, bool>> fin;
       for (int r = 0; r < nslots; ++r) {
         if (!rel[r]) continue;
         const double tr = std::sqrt(std::max(t[r], 0.0));
         tres[r] = tr / bnorm[r];
         ref[r] = tr;
         relups[r] += 1;
-        if (tr <= tol * bnorm[r]) {
-          TRY(finish(r, true));
-          changed = true;
-        } else if (iters[r] >= c->prm.max_iter || !(tr == tr)) {
-          TRY(finish(r, false));
-          changed = true;
-        }
+        if (tr <= tol * bnorm[r]) fin.push_back({r, true});
+        else if (iters[r] >= c->prm.max_iter || !(tr == tr)) fin.push_back({r, false});
       }
+      TRY(finish_many(fin));
+      const bool changed = !fin.empty();
       if (changed) {
         TRY(upload_ints(c, c->d_active, active));
         count_active();
