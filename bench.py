@@ -50,6 +50,10 @@ LARGE = {
 # by --impl reference, which runs without a GPU, to scale its sample to the whole job
 REFERENCE_ITERS = {"16x16x16x32": [37.0, 43.9, 48.9]}
 REFERENCE_CG = {"16x16x16x32": [9.3, 23.9, 43.1]}  # coarsest CG iterations per cycle, the same source
+# DRAM traffic per launch group of a class from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), taken with the committed command of the named profile; a group of the coarse
+# class is one application of the coarsest Schur complement (its odd-site and even-site passes)
+TRAFFIC = {"coarse": {"bytes_per_launch": 46.1e6, "profile": "profiles/coarse_schur_16x16x16x32_nrhs12.md"}}
 PROF_CLASSES = ("dslash_sloppy", "dslash_fp64", "coarse", "restrict", "prolong", "blas", "setup", "cgnr",
                 "blas_coarse")
 
@@ -421,8 +425,11 @@ def run_gpu(args, w):
     hot = max((k for k in PROF_CLASSES if prof[k]["bytes"] > 0), key=lambda k: prof[k]["ms"])
     peaks, src = measured_peaks()
     achieved = prof[hot]["bytes"] / (prof[hot]["ms"] * 1e-3) / 1e9 if prof[hot]["ms"] > 0 else 0.0
+    tr = TRAFFIC.get(hot)
     roof = {"bound": "hbm", "kernel": hot, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+            "frac": achieved / peaks["hbm_gbs"], "traffic": tr["bytes_per_launch"] if tr else None,
+            "traffic_profile": tr["profile"] if tr else None,
+            "bytes_per_launch": prof[hot]["bytes"] / max(prof[hot]["launches"], 1), "peak_source": src,
             "launches": prof[hot]["launches"], "ms_per_launch": prof[hot]["ms"] / max(prof[hot]["launches"], 1)}
     total_ms = sum(prof[k]["ms"] for k in PROF_CLASSES)
     breakdown = {k: {"ms": round(prof[k]["ms"], 3), "share": round(prof[k]["ms"] / total_ms, 4) if total_ms else 0,

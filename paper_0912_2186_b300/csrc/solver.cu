@@ -236,10 +236,13 @@ double coarse_bytes(const wmg_ctx* c, int l, int prec, int nact) {
 }
 // one application of the even-odd Schur complement: the odd-site pass (8 blocks per site and the
 // site's block inverse, in the vectors' precision) and the even-site pass (9 blocks per site)
-double coarse_bytes_eo(const wmg_ctx* c, int l, int prec, int nact) {
+// (with precomputed odd-site tables the odd pass reads its 8 table blocks instead of the 8 hop
+// blocks and the inverse)
+double coarse_bytes_eo(const wmg_ctx* c, int l, int prec, int nact, bool tables = false) {
   const double s = rb_(prec), V = c->L[l].g.V, n = c->L[l].ndof;
   const double sa = (prec == WMG_PREC_SINGLE && c->L[l].A16) ? 2.0 : s;
-  return V / 2 * 17.0 * n * n * 2.0 * sa + V / 2 * n * n * 2.0 * s + V * 4.0 + (double)nact * V * n * 2.0 * s * 2.0;
+  const double inv = tables ? 0.0 : V / 2 * n * n * 2.0 * s;
+  return V / 2 * 17.0 * n * n * 2.0 * sa + inv + V * 4.0 + (double)nact * V * n * 2.0 * s * 2.0;
 }
 double transfer_bytes(const wmg_ctx* c, int l, int prec, int nact) {
   const LevelData& L = c->L[l];
@@ -866,7 +869,7 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
   count_launch();
   RedBuf rqq{c->red_partial, c->red_counter, cg.qq};
   RedBuf rrr{c->red_partial, c->red_counter, cg.rr};
-  const double cb = eo ? coarse_bytes_eo(c, l, prec, nrhs) : coarse_bytes(c, l, prec, nrhs);
+  const double cb = eo ? coarse_bytes_eo(c, l, prec, nrhs, tb.nB > 0) : coarse_bytes(c, l, prec, nrhs);
   // one CGNR iteration: q = A p (|q|^2), x += alpha p, r -= alpha q (|r|^2, convergence flags),
   // z = A^dag r (|z|^2), p = z + beta p
   auto body = [&](int parity) {
