@@ -54,6 +54,7 @@ REFERENCE_CG = {"16x16x16x32": [9.3, 23.9, 43.1]}  # coarsest CG iterations per 
 # dram__bytes_write.sum), taken with the committed command of the named profile; a group of the coarse
 # class is one application of the coarsest Schur complement (its odd-site and even-site passes)
 TRAFFIC = {"coarse": {"bytes_per_launch": 46.1e6, "profile": "profiles/coarse_schur_16x16x16x32_nrhs12.md"}}
+GAUGE_REALS = 12  # reals per link of the FP32 fine operator in the job (wmg_set_gauge_compression)
 PROF_CLASSES = ("dslash_sloppy", "dslash_fp64", "coarse", "restrict", "prolong", "blas", "setup", "cgnr",
                 "blas_coarse")
 
@@ -313,6 +314,7 @@ def run_gpu(args, w):
     b_dev = torch.from_numpy(b).cuda()
     x_dev = torch.zeros_like(b_dev)
     ctx = wmg.Context(dims)
+    ctx.set_gauge_compression(GAUGE_REALS)
     # setup: 200 relaxation steps and one improvement pass (measured fastest for this field at
     # unchanged outer iteration counts; the library default is 100 steps and 5 passes); the fine
     # solve red/black preconditioned (Sec. 3: multigrid combined with red/black preconditioning)
@@ -443,9 +445,9 @@ def run_gpu(args, w):
         breakdown["dslash_fp64"].update({"GFLOP_s": round(gf, 1), "bound": "fp64 alu",
                                          "frac_of_probed_fp64": round(gf / (alu["fp64_tflops"] * 1e3), 3)})
 
-    # isolated dslash throughput (FP32, 12 right-hand sides and 1; 12-real links, then 8-real)
+    # isolated dslash throughput (FP32, 12 right-hand sides and 1; 12-real links, then 8- and 18-real)
     dsl = {}
-    for gc, nr in ((12, 1), (12, nrhs), (8, 1), (8, nrhs)):
+    for gc, nr in ((12, 1), (12, nrhs), (8, 1), (8, nrhs), (18, 1), (18, nrhs)):
         ctx.set_gauge_compression(gc)
         xin = torch.zeros(nr * 12 * V, dtype=torch.complex64, device="cuda")
         xout = torch.zeros_like(xin)
@@ -462,19 +464,21 @@ def run_gpu(args, w):
         e1.record()
         torch.cuda.synchronize()
         sec = e0.elapsed_time(e1) / 1e3 / reps
-        by = V * (48 if gc == 12 else 32) * 4 + nr * V * 48 * 4
-        dsl[f"nrhs{nr}" + ("" if gc == 12 else "_8real")] = {"us": sec * 1e6, "GB_s": by / sec / 1e9,
-                                                              "GFLOP_s": 1368 * V * nr / sec / 1e9}
-    # one job step with the 8-real links in the FP32 operator
-    ctx.set_gauge_compression(8)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    step()
-    e1.record()
-    torch.cuda.synchronize()
-    step8 = e0.elapsed_time(e1) / 1e3
-    ctx.set_gauge_compression(12)
+        by = V * 4 * gc * 4 + nr * V * 48 * 4
+        dsl[f"nrhs{nr}" + ("" if gc == 12 else f"_{gc}real")] = {"us": sec * 1e6, "GB_s": by / sec / 1e9,
+                                                                 "GFLOP_s": 1368 * V * nr / sec / 1e9}
+    # one job step each with the 8-real and the 18-real links in the FP32 operator
+    step_links = {}
+    for gc in (8, 18):
+        ctx.set_gauge_compression(gc)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        torch.cuda.synchronize()
+        step_links[gc] = e0.elapsed_time(e1) / 1e3
+    ctx.set_gauge_compression(GAUGE_REALS)
     # one job step without red/black preconditioning (the whole-lattice outer solve, fine_eo = 0)
     params.fine_eo = 0
     n_it = len(record["iters"])
@@ -566,7 +570,8 @@ def run_gpu(args, w):
         "speedup_vs_plain": (plain["s"] / t_step) if plain else None,
         "unpreconditioned_fp64": baselines,
         "dslash_fp32_isolated": dsl,
-        "step_s_8real_links": step8,
+        "step_s_8real_links": step_links[8],
+        "step_s_18real_links": step_links[18],
         "step_whole_lattice": step_eo,
         "kernel_breakdown": breakdown,
         "roofline": roof,
@@ -674,6 +679,7 @@ def run_probe(args, w):
     V = int(np.prod(dims))
     ctx = wmg.Context(dims)
     ctx.load_gauge(torch.from_numpy(synth.gauge_field(dims, w["eps"], w["gauge_seed"])).cuda())
+    ctx.set_gauge_compression(args.probe_gauge)
     ctx.set_mass(masses[-1])
     ctx.setup(wmg.default_params(nvec=[w["nvec"]], block=[w["block"]], prec_sloppy=wmg.PREC_SINGLE, setup_relax=200,
                                  setup_passes=2, fine_eo=1))
@@ -794,6 +800,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--probe", action="store_true", help="run the hot kernels in an NVTX range (profiling)")
     ap.add_argument("--probe-reps", type=int, default=2)
+    ap.add_argument("--probe-gauge", type=int, default=12, choices=(8, 12, 18),
+                    help="reals per link of the FP32 fine operator in --probe")
     ap.add_argument("--probe-mass", type=float, default=None)
     ap.add_argument("--probe-solve", action="store_true")
     ap.add_argument("--large", default=None, choices=sorted(LARGE),

@@ -189,8 +189,10 @@ wmg_status wmg_load_gauge_dev(wmg_ctx* ctx, const double* U_dev);
  * links are made from the FP64 links at every gauge load; FP64 operators, the Galerkin product and
  * the no-alloc residual keep 12 reals.  A field with a link whose (0,1) and (0,2) elements (nearly)
  * vanish, |U_01|^2 + |U_02|^2 < 1e-6 (the free field, for one), is not representable that way: for
- * such a field the FP32 operator keeps the 12-real links.  reals: 12 or 8, else WMG_EINVAL.
- * Synchronises when a field is loaded. */
+ * such a field the FP32 operator keeps the 12-real links.  reals = 18 stores all nine elements
+ * in FP32 (row 2 rebuilt once, in FP64, at the gauge load): 50 % more link bytes than 12 reals
+ * and no arithmetic on load.  reals: 18, 12 or 8, else WMG_EINVAL.  Synchronises when a field is
+ * loaded. */
 wmg_status wmg_set_gauge_compression(wmg_ctx* ctx, int reals);
 
 /* Set the Wilson mass m (Sec. 2, the (4 + m) term).  An existing hierarchy's coarse

@@ -54,6 +54,7 @@ size_t context_device_bytes(const wmg_ctx* c) {
   if (c->gauge[0]) b += V * 4 * 6 * sizeof(cd);
   if (c->gauge[1]) b += V * 4 * 6 * sizeof(cf);
   if (c->gauge8) b += gauge8_bytes((int)V);
+  if (c->gauge18) b += gauge18_bytes((int)V);
   for (int l = 0; l < WMG_MAX_LEVELS; ++l) {
     const LevelData& L = c->L[l];
     const size_t pe = L.P[0] ? L.nvec_elems() * L.bk.N : 0;
@@ -165,6 +166,14 @@ wmg_status make_gauge8(wmg_ctx* c) {
   CU(c, cudaStreamSynchronize(c->stream));
   c->gauge8_ok = c->h_pin_i[0] == 0;
   return check(c, "pack_gauge8");
+}
+
+// the FP32 links of the loaded field in the compressed (8-real) or uncompressed (18-real) form
+// that the context keeps
+wmg_status make_gauge_forms(wmg_ctx* c) {
+  if (c->gauge8) TRY(make_gauge8(c));
+  if (c->gauge18) pack_gauge18(c->gauge[0], c->gauge18, c->fine.V, c->stream);
+  return check(c, "pack_gauge18");
 }
 
 }  // namespace
@@ -291,7 +300,7 @@ wmg_status wmg_destroy(wmg_ctx* c) {
   for (auto& kv : c->ws) cudaFree(kv.second.first);
   c->ws.clear();
   void* ptrs[] = {c->d_mass, c->d_shift[1], c->d_shift[2], c->d_active, c->d_mask, c->d_flag, c->d_cgint,
-                  c->red_counter, c->res, c->red_partial, c->gauge[0], c->gauge[1], c->d_err, c->gauge8};
+                  c->red_counter, c->res, c->red_partial, c->gauge[0], c->gauge[1], c->d_err, c->gauge8, c->gauge18};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pin) cudaFreeHost(c->h_pin);
@@ -309,7 +318,7 @@ wmg_status wmg_load_gauge_dev(wmg_ctx* c, const double* U) {
   free_hierarchy(c);
   pack_gauge(WMG_PREC_DOUBLE, U, c->gauge[0], c->fine.V, c->stream);
   pack_gauge(WMG_PREC_SINGLE, U, c->gauge[1], c->fine.V, c->stream);
-  if (c->gauge8) TRY(make_gauge8(c));
+  TRY(make_gauge_forms(c));
   TRY(check(c, "pack_gauge"));
   c->have_gauge = true;
   return WMG_OK;
@@ -327,16 +336,28 @@ wmg_status wmg_load_gauge(wmg_ctx* c, const double* U_host) {
 }
 
 wmg_status wmg_set_gauge_compression(wmg_ctx* c, int reals) {
-  if (!c || (reals != 12 && reals != 8)) return WMG_EINVAL;
+  if (!c || (reals != 12 && reals != 8 && reals != 18)) return WMG_EINVAL;
+  if (reals != 8 && c->gauge8) {
+    CU(c, cudaStreamSynchronize(c->stream));
+    cudaFree(c->gauge8);
+    c->gauge8 = nullptr;
+  }
+  if (reals != 18 && c->gauge18) {
+    CU(c, cudaStreamSynchronize(c->stream));
+    cudaFree(c->gauge18);
+    c->gauge18 = nullptr;
+  }
   if (reals == 8 && !c->gauge8) {
     CU(c, cudaMalloc(&c->gauge8, gauge8_bytes(c->fine.V)));
     c->gauge8_ok = false;
     if (c->have_gauge) TRY(make_gauge8(c));
   }
-  if (reals == 12 && c->gauge8) {
-    CU(c, cudaStreamSynchronize(c->stream));
-    cudaFree(c->gauge8);
-    c->gauge8 = nullptr;
+  if (reals == 18 && !c->gauge18) {
+    CU(c, cudaMalloc(&c->gauge18, gauge18_bytes(c->fine.V)));
+    if (c->have_gauge) {
+      pack_gauge18(c->gauge[0], c->gauge18, c->fine.V, c->stream);
+      TRY(check(c, "pack_gauge18"));
+    }
   }
   c->gauge_compress = reals;
   clear_graphs(c);
@@ -401,7 +422,7 @@ wmg_status wmg_update_gauge_dev(wmg_ctx* c, const double* U) {
   CU(c, cudaStreamSynchronize(c->stream));
   pack_gauge(WMG_PREC_DOUBLE, U, c->gauge[0], c->fine.V, c->stream);
   pack_gauge(WMG_PREC_SINGLE, U, c->gauge[1], c->fine.V, c->stream);
-  if (c->gauge8) TRY(make_gauge8(c));
+  TRY(make_gauge_forms(c));
   TRY(check(c, "pack_gauge"));
   // the kept near-null subspace, the coarse operators of the new field
   for (int l = 0; l + 1 < c->nlev; ++l) TRY(galerkin(c, l, c->prm.prec_sloppy));
@@ -612,15 +633,16 @@ wmg_status wmg_apply_D(wmg_ctx* c, int prec, const void* in, void* out, int nrhs
     TRY(ws_get(c, "aD_n_in", (size_t)V * nrhs * sizeof(float), &n_in));
     TRY(ws_get(c, "aD_n_out", (size_t)V * nrhs * sizeof(float), &n_out));
     spinor_to_h(in, h_in, (float*)n_in, V, nrhs, c->stream);
-    const bool g8 = c->gauge_compress == 8 && c->gauge8 && c->gauge8_ok;
-    dslash_h(1, h_out, (float*)n_out, h_in, (const float*)n_in, nullptr, g8 ? c->gauge8 : c->gauge[1], c->fine,
-             c->d_mass, nullptr, nrhs, 0, nullptr, c->stream, g8 ? 8 : 12);
+    int gc;
+    const void* U = links(c, WMG_PREC_SINGLE, &gc);
+    dslash_h(1, h_out, (float*)n_out, h_in, (const float*)n_in, nullptr, U, c->fine, c->d_mass, nullptr, nrhs, 0,
+             nullptr, c->stream, gc);
     spinor_from_h(h_out, (const float*)n_out, out, V, nrhs, c->stream);
     return check(c, "apply_D (FP16 storage)");
   }
-  const bool g8 = prec == WMG_PREC_SINGLE && c->gauge_compress == 8 && c->gauge8 && c->gauge8_ok;
-  dslash(prec, out, in, nullptr, g8 ? c->gauge8 : c->gauge[prec], c->fine, c->d_mass, nullptr, nrhs, 0, nullptr,
-         c->stream, g8 ? 8 : 12);
+  int gc;
+  const void* U = links(c, prec, &gc);
+  dslash(prec, out, in, nullptr, U, c->fine, c->d_mass, nullptr, nrhs, 0, nullptr, c->stream, gc);
   return check(c, "apply_D");
 }
 
@@ -633,12 +655,11 @@ wmg_status wmg_apply_D_eo(wmg_ctx* c, int prec, const void* in, void* out, int n
   TRY(vec_ws(c, 0, "aDeo_e", prec, nrhs, &he));
   TRY(vec_ws(c, 0, "aDeo_t", prec, nrhs, &ht));
   TRY(vec_ws(c, 0, "aDeo_s", prec, nrhs, &hs));
-  const bool g8 = prec == WMG_PREC_SINGLE && c->gauge_compress == 8 && c->gauge8 && c->gauge8_ok;
-  const void* U = g8 ? c->gauge8 : c->gauge[prec];
+  int gc;
+  const void* U = links(c, prec, &gc);
   eo_extract(prec, he, in, c->fine, 0, nrhs, c->stream);
-  dslash_eo(prec, 0, 1, ht, he, nullptr, nullptr, U, g8 ? 8 : 12, c->fine, c->d_mass, nullptr, nrhs, nullptr,
-            c->stream);
-  dslash_eo(prec, 1, 0, hs, ht, he, nullptr, U, g8 ? 8 : 12, c->fine, c->d_mass, nullptr, nrhs, nullptr, c->stream);
+  dslash_eo(prec, 0, 1, ht, he, nullptr, nullptr, U, gc, c->fine, c->d_mass, nullptr, nrhs, nullptr, c->stream);
+  dslash_eo(prec, 1, 0, hs, ht, he, nullptr, U, gc, c->fine, c->d_mass, nullptr, nrhs, nullptr, c->stream);
   eo_embed(prec, out, hs, nullptr, c->fine, nrhs, c->stream);
   return check(c, "apply_D_eo");
 }

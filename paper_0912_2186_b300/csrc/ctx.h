@@ -66,8 +66,9 @@ struct wmg_ctx {
   cudaStream_t stream = nullptr;
   Geom fine{};
   void* gauge[2] = {nullptr, nullptr};  // native 12-real links, FP64 and FP32
-  int gauge_compress = 12;               // links of the FP32 sloppy operator: 12 or 8 reals
+  int gauge_compress = 12;               // links of the FP32 sloppy operator: 18, 12 or 8 reals
   void* gauge8 = nullptr;                // 8-real FP32 links (with gauge_compress 8)
+  void* gauge18 = nullptr;               // 18-real FP32 links (with gauge_compress 18)
   bool gauge8_ok = false;                // the loaded field is representable with 8 reals
   bool have_gauge = false;
   double mass = 0.0, mass_setup = 0.0;

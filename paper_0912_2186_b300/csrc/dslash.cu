@@ -38,6 +38,21 @@ __global__ void k_pack_gauge8(const void* __restrict__ g64, float4* __restrict__
   }
 }
 
+// native FP64 12-real links -> 18-real FP32 (see load_link18), row 2 rebuilt in FP64
+__global__ void k_pack_gauge18(const void* __restrict__ g64, float4* __restrict__ out, int V) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  float2* o8 = reinterpret_cast<float2*>(out + (size_t)16 * V);
+  for (int mu = 0; mu < 4; ++mu) {
+    cd u[9];
+    load_link<double>(g64, V, mu, v, u);
+    for (int c = 0; c < 4; ++c)
+      out[(size_t)(mu * 4 + c) * V + v] = make_float4((float)u[2 * c].re, (float)u[2 * c].im,
+                                                      (float)u[2 * c + 1].re, (float)u[2 * c + 1].im);
+    o8[(size_t)mu * V + v] = make_float2((float)u[8].re, (float)u[8].im);
+  }
+}
+
 // canonical [rhs][V][12] <-> native [rhs][6][V][2]
 template <typename R>
 __global__ void k_pack_spinor(const double2* __restrict__ canon, void* __restrict__ out, int V, int nrhs) {
@@ -426,6 +441,12 @@ void pack_gauge8(const void* g64, void* out, int V, int* degenerate, cudaStream_
   k_pack_gauge8<<<B, T, 0, s>>>(g64, (float4*)out, V, degenerate);
 }
 
+void pack_gauge18(const void* g64, void* out, int V, cudaStream_t s) {
+  count_launch();
+  const int T = 256, B = (V + T - 1) / T;
+  k_pack_gauge18<<<B, T, 0, s>>>(g64, (float4*)out, V);
+}
+
 void pack_spinor(int prec, const double* canon, void* out, int V, int nrhs, cudaStream_t s) {
   count_launch();
   const size_t n = (size_t)V * nrhs;
@@ -464,6 +485,7 @@ void dslash(int prec, void* out, const void* in, const void* b, const void* gaug
   } while (0)
   if (prec == WMG_PREC_DOUBLE) WMG_DS(double, 12);
   else if (gc == 8) WMG_DS(float, 8);
+  else if (gc == 18) WMG_DS(float, 18);
   else WMG_DS(float, 12);
 #undef WMG_DS
 }
@@ -483,6 +505,9 @@ void dslash_mr(int prec, void* out, const void* r, const void* q, void* r_out, v
   else if (gc == 8)
     k_dslash_mr<float, 8><<<grid, kDslashThreads, 0, s>>>(out, r, q, r_out, x, red_prev, gauge, g, dv, mass_dev,
                                                            active, nrhs, nbr, rb);
+  else if (gc == 18)
+    k_dslash_mr<float, 18><<<grid, kDslashThreads, 0, s>>>(out, r, q, r_out, x, red_prev, gauge, g, dv, mass_dev,
+                                                            active, nrhs, nbr, rb);
   else
     k_dslash_mr<float, 12><<<grid, kDslashThreads, 0, s>>>(out, r, q, r_out, x, red_prev, gauge, g, dv, mass_dev,
                                                             active, nrhs, nbr, rb);
@@ -509,6 +534,8 @@ void dslash_h(int in16, void* out16, float* out_norm, const void* in, const floa
   count_launch();
   RedBuf r = rb ? *rb : RedBuf{nullptr, nullptr, nullptr};
   if (gc == 8) launch_dslash_h<8>(in16, out16, out_norm, in, in_norm, b, gauge, g, mass_dev, active, nrhs, red, r, s);
+  else if (gc == 18)
+    launch_dslash_h<18>(in16, out16, out_norm, in, in_norm, b, gauge, g, mass_dev, active, nrhs, red, r, s);
   else launch_dslash_h<12>(in16, out16, out_norm, in, in_norm, b, gauge, g, mass_dev, active, nrhs, red, r, s);
 }
 

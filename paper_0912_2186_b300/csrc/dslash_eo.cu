@@ -150,6 +150,9 @@ void dslash_eo(int prec, int mode, int p_out, void* out, const void* in, const v
   } else if (gc == 8) {
     if (rb) WMG_EO(float, 1, 8);
     else WMG_EO(float, 0, 8);
+  } else if (gc == 18) {
+    if (rb) WMG_EO(float, 1, 18);
+    else WMG_EO(float, 0, 18);
   } else {
     if (rb) WMG_EO(float, 1, 12);
     else WMG_EO(float, 0, 12);

@@ -26,7 +26,7 @@ void unpack_spinor(int prec, const void* in, double* canon, int V, int nrhs, cud
 int dslash_blocks(int V);
 // out = D in, or out = b - D in when b != nullptr.  mass_dev[nrhs]: per-rhs Wilson mass.
 // red = 0: none; 1: |out|^2 per rhs into rb->result[rhs]; 2: {Re, Im <out,in>, |out|^2}.
-// gc = 8: FP32 only, `gauge` holds 8-real links (pack_gauge8)
+// gc = 8 / 18: FP32 only, `gauge` holds 8-real (pack_gauge8) or 18-real (pack_gauge18) links
 void dslash(int prec, void* out, const void* in, const void* b, const void* gauge, const Geom& g,
             const double* mass_dev, const int* active, int nrhs, int red, const RedBuf* rb, cudaStream_t s,
             int gc = 12);
@@ -39,6 +39,7 @@ void dslash_mr(int prec, void* out, const void* r, const void* q, void* r_out, v
 // 8-real FP32 links from the native FP64 12-real links; *degenerate (device int) set to 1 if a
 // link has |U_01|^2 + |U_02|^2 < 1e-6 (the 8-real form cannot represent it accurately)
 void pack_gauge8(const void* g64, void* out, int V, int* degenerate, cudaStream_t s);
+void pack_gauge18(const void* g64, void* out, int V, cudaStream_t s);
 // the smoother's FP16 storage (per-site norms, FP32 arithmetic): out16 = [b -] D in with in
 // FP32 native (in16 = 0) or FP16 (in16 = 1); red = 2 adds per-rhs {<out, in>, |out|^2}
 void dslash_h(int in16, void* out16, float* out_norm, const void* in, const float* in_norm, const void* b,
@@ -53,7 +54,7 @@ void spinor_from_h(const void* in16, const float* norm, void* out, int V, int nr
 // ---- even-odd fine operator (dslash_eo.cu): half-lattice fields [rhs][6][V/2], site v at v >> 1 ----
 // h = the raw hop sum onto the parity-p_out sites from the opposite-parity half field `in` (H = -h/2);
 // mode 0: out = h;  1: out = d self - h / (4 d);  2: out = self + h / (2 d);  3: out = (self + h / 2) / d,
-// d = 4 + m_r; with b: out = b - out; with rb: |out|^2 per rhs.  gc = 8: 8-real FP32 links.
+// d = 4 + m_r; with b: out = b - out; with rb: |out|^2 per rhs.  gc = 8 / 18: 8- or 18-real FP32 links.
 void dslash_eo(int prec, int mode, int p_out, void* out, const void* in, const void* self, const void* b,
                const void* gauge, int gc, const Geom& g, const double* mass_dev, const int* active, int nrhs,
                const RedBuf* rb, cudaStream_t s);

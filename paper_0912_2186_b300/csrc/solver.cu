@@ -217,14 +217,19 @@ struct ProfScope {
 static double rb_(int prec) { return prec == WMG_PREC_DOUBLE ? 8.0 : 4.0; }
 double dslash_bytes(const wmg_ctx* c, int prec, int nact, bool resid) {
   const double s = rb_(prec), V = c->fine.V;
-  const double links = (prec == WMG_PREC_SINGLE && c->gauge_compress == 8 && c->gauge8_ok) ? 32.0 : 48.0;
-  return V * (links * s) + (double)nact * V * 24.0 * s * (resid ? 3.0 : 2.0);
+  int gc;
+  links(c, prec, &gc);
+  return V * (4.0 * gc * s) + (double)nact * V * 24.0 * s * (resid ? 3.0 : 2.0);
 }
-// the links of the fine operator in precision prec: 12-real, or the 8-real FP32 links
-static const void* links(const wmg_ctx* c, int prec, int* gc) {
+// the links of the fine operator in precision prec: 12-real, or the 8- or 18-real FP32 links
+const void* links(const wmg_ctx* c, int prec, int* gc) {
   if (prec == WMG_PREC_SINGLE && c->gauge_compress == 8 && c->gauge8 && c->gauge8_ok) {
     *gc = 8;
     return c->gauge8;
+  }
+  if (prec == WMG_PREC_SINGLE && c->gauge_compress == 18 && c->gauge18) {
+    *gc = 18;
+    return c->gauge18;
   }
   *gc = 12;
   return c->gauge[prec];
@@ -337,7 +342,7 @@ static wmg_status mr_half(wmg_ctx* c, void* x, const void* b, int nrhs, int nu, 
   const int na = nact_of(c, active, nrhs);
   int gc;
   const void* U = links(c, WMG_PREC_SINGLE, &gc);
-  const double lb = gc == 8 ? 128.0 : 192.0;
+  const double lb = 4.0 * gc * 4.0;  // links per site, FP32
   const double hb = (double)V * lb + (double)na * V * (96.0 + 52.0);  // gauge, x + b in, r out
   {
     ProfScope ps(c, PROF_DSLASH_LO, hb + (double)na * V * 96.0, na);

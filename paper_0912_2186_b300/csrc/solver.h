@@ -13,6 +13,9 @@ wmg_status ws_get(wmg_ctx* c, const std::string& name, size_t bytes, void** out)
 wmg_status vec_ws(wmg_ctx* c, int l, const char* tag, int prec, int nrhs, void** out);
 wmg_status ensure_reductions(wmg_ctx* c, int nrhs);
 wmg_status set_rhs_scalars(wmg_ctx* c, const double* masses, int nrhs);
+// the links of the fine operator in precision prec and their form (gc: 12, or 8 / 18 for the
+// FP32 compressed or uncompressed links selected by wmg_set_gauge_compression)
+const void* links(const wmg_ctx* c, int prec, int* gc);
 void level_apply(wmg_ctx* c, int l, int prec, const void* in, void* out, int nrhs, const int* active, int red,
                  const RedBuf* rb);
 wmg_status mr(wmg_ctx* c, int l, int prec, void* x, const void* b, int nrhs, int nu, const int* active);

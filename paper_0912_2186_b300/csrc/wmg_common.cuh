@@ -260,10 +260,27 @@ WMG_D void load_link8(const void* base, int V, int mu, int v, cpx<float> u[9]) {
   u[3] = b0, u[4] = b1, u[5] = b2;
   u[6] = c0, u[7] = c1, u[8] = c2;
 }
-// the link loader of a dslash kernel: 12-real in the kernel's precision, or 8-real FP32 (GC = 8)
+// 18-real FP32 links (all nine elements stored; row 2 rebuilt once, in FP64, when packed):
+// [mu][4][V] float4 chunks of elements (0, 1), (2, 3), (4, 5), (6, 7), then [mu][V] float2 of
+// element 8 after the 16 V chunks.  Loading costs no arithmetic.
+WMG_HD size_t gauge18_bytes(int V) { return (size_t)V * 4 * (4 * sizeof(float4) + sizeof(float2)); }
+WMG_D void load_link18(const void* base, int V, int mu, int v, cpx<float> u[9]) {
+  const float4* q = reinterpret_cast<const float4*>(base);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float4 t = __ldg(q + (size_t)(mu * 4 + c) * V + v);
+    u[2 * c] = {t.x, t.y};
+    u[2 * c + 1] = {t.z, t.w};
+  }
+  const float2 t8 = __ldg(reinterpret_cast<const float2*>(q + (size_t)16 * V) + (size_t)mu * V + v);
+  u[8] = {t8.x, t8.y};
+}
+// the link loader of a dslash kernel: 12-real in the kernel's precision, or FP32 8-real (GC = 8)
+// or 18-real (GC = 18)
 template <typename R, int GC>
 WMG_D void load_link_gc(const void* base, int V, int mu, int v, cpx<R> u[9]) {
   if constexpr (GC == 8) load_link8(base, V, mu, v, u);
+  else if constexpr (GC == 18) load_link18(base, V, mu, v, u);
   else load_link<R>(base, V, mu, v, u);
 }
 

@@ -224,7 +224,7 @@ class Context:
         return self._check(self.lib.wmg_load_gauge_dev(self.h, _ptr(U)))
 
     def set_gauge_compression(self, reals):
-        """12 (default) or 8 reals per link in the FP32 fine operator."""
+        """18, 12 (default) or 8 reals per link in the FP32 fine operator."""
         return self._check(self.lib.wmg_set_gauge_compression(self.h, int(reals)))
 
     def set_mass(self, m):

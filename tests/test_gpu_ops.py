@@ -259,15 +259,17 @@ def test_coarse_schur_apply(W, prec, dims, block, N):
                 assert np.all(got[r][odd] == 0)
 
 
+@pytest.mark.parametrize("reals", [8, 18])
 @pytest.mark.parametrize("dims", [(6, 4, 4, 6), (8, 8, 8, 8)])
-def test_dslash_8real_links_parity(W, dims):
-    """8-real FP32 links (Table 2's "8 floats"): the FP32 operator against the oracle at 1e-5 and
-    the FP16-storage path at 2e-3 (V = 576 leaves a ragged last CTA)."""
+def test_dslash_link_forms_parity(W, dims, reals):
+    """8-real FP32 links (Table 2's "8 floats") and uncompressed 18-real FP32 links: the FP32
+    operator against the oracle at 1e-5 and the FP16-storage path at 2e-3 (V = 576 leaves a ragged
+    last CTA)."""
     U = synth.gauge_field(dims, 0.6, 3)
     m, nrhs = -0.27, 3
     b = synth.gaussian_spinors(dims, nrhs, 4)
     ctx = W.Context(dims)
-    ctx.set_gauge_compression(8)
+    ctx.set_gauge_compression(reals)
     ctx.load_gauge(U)
     ctx.set_mass(m)
     want = np.stack([dirac.apply_D(U, b[r], m) for r in range(nrhs)])
@@ -280,17 +282,26 @@ def test_dslash_8real_links_parity(W, dims):
         assert rel_err(host(canon), want) < tol, prec
 
 
-def test_8real_links_solve_and_free_field(W):
-    """A mixed-precision MG-GCR solve with 8-real FP32 links meets the 1e-10 true residual (oracle D);
-    on the free field, which the 8-real form cannot represent, the operator keeps 12-real links."""
+@pytest.mark.parametrize("reals", [8, 18])
+def test_link_forms_solve_and_free_field(W, reals):
+    """A mixed-precision MG-GCR solve (whole-lattice and red/black) with 8- or 18-real FP32 links
+    meets the 1e-10 true residual (oracle D); on the free field, which the 8-real form cannot
+    represent, the 8-real operator keeps 12-real links; the 18-real one represents it exactly."""
     dims, m = (8, 8, 8, 8), 0.05
     U = synth.gauge_field(dims, 0.4, 11)
     ctx = W.Context(dims)
-    ctx.set_gauge_compression(8)
+    ctx.set_gauge_compression(reals)
     ctx.load_gauge(U)
     ctx.set_mass(m)
     ctx.setup(W.default_params(nvec=[8], prec_sloppy=1), synth.setup_starts(dims, 8, 12))
     b = synth.gaussian_spinors(dims, 2, 13)
+    x = dev(np.zeros_like(b))
+    st, info = ctx.solve(dev(b), x, 2)
+    xs = host(x)
+    for r in range(2):
+        assert info[r]["converged"]
+        assert np.linalg.norm(b[r] - dirac.apply_D(U, xs[r], m)) / np.linalg.norm(b[r]) <= 1.05e-10
+    ctx.setup(W.default_params(nvec=[8], prec_sloppy=1, fine_eo=1), synth.setup_starts(dims, 8, 12))
     x = dev(np.zeros_like(b))
     st, info = ctx.solve(dev(b), x, 2)
     xs = host(x)
@@ -307,16 +318,18 @@ def test_8real_links_solve_and_free_field(W):
     assert rel_err(host(canon)[0], want) < TOL[1]
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec,reals", [(0, 12), (1, 12), (1, 8), (1, 18)])
 @pytest.mark.parametrize("dims", [(6, 4, 4, 6), (8, 8, 8, 8)])
-def test_fine_schur_parity(W, prec, dims):
+def test_fine_schur_parity(W, prec, reals, dims):
     """The red/black Schur complement S = d - H_eo H_oe / d of the fine operator against the oracle
-    (V / 2 = 288 leaves a ragged last CTA); odd sites of the result are zero."""
+    (V / 2 = 288 leaves a ragged last CTA), FP32 with each link form; odd sites of the result are
+    zero."""
     from oracle import eo_fine
     U = synth.gauge_field(dims, 0.6, 5)
     m, nrhs = -0.3, 3
     x = synth.gaussian_spinors(dims, nrhs, 6)
     ctx = W.Context(dims)
+    ctx.set_gauge_compression(reals)
     ctx.load_gauge(U)
     ctx.set_mass(m)
     xin, xout = native_fine(ctx.V, nrhs, prec), native_fine(ctx.V, nrhs, prec)
