@@ -42,9 +42,11 @@ WORKLOADS = {
 # run on these volumes); the 48^3x96 one with FP16 null vectors and its device footprint.
 LARGE = {
     "24x24x24x48": dict(dims=(24, 24, 24, 48), eps=0.7, gauge_seed=31, nvec=[24, 32],
-                        block=[(4, 4, 4, 4), (2, 2, 2, 2)], nrhs=12, mass=-1.2, prec_nullvec=1),
+                        block=[(4, 4, 4, 4), (2, 2, 2, 2)], nrhs=12, mass=-1.2, prec_nullvec=1, gcr_restart=16),
+    # FGCR(8) on the red/black system: its FP32 basis (2 x restart half-lattice vectors per rhs)
+    # is a quarter of FGCR(16) on the whole lattice
     "48x48x48x96": dict(dims=(48, 48, 48, 96), eps=0.7, gauge_seed=51, nvec=[24, 32],
-                        block=[(4, 4, 4, 4), (2, 2, 2, 2)], nrhs=4, mass=-1.2, prec_nullvec=2),
+                        block=[(4, 4, 4, 4), (2, 2, 2, 2)], nrhs=4, mass=-1.2, prec_nullvec=2, gcr_restart=8),
 }
 # outer iterations per mass the GPU arm measures on this job (mean over the 12 point sources), used
 # by --impl reference, which runs without a GPU, to scale its sample to the whole job
@@ -677,7 +679,10 @@ def run_probe(args, w):
     masses, _ = load_masses(w, args.masses, args.workload)
     dims, nr = w["dims"], w["nrhs"]
     V = int(np.prod(dims))
-    ctx = wmg.Context(dims)
+    # the library launches on this stream, so that CUDA graphs captured on it replay its kernels
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = wmg.Context(dims, stream=stream.cuda_stream)
     ctx.load_gauge(torch.from_numpy(synth.gauge_field(dims, w["eps"], w["gauge_seed"])).cuda())
     ctx.set_gauge_compression(args.probe_gauge)
     ctx.set_mass(masses[-1])
@@ -713,16 +718,23 @@ def run_probe(args, w):
         ctx.solve(b, x, nr)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
+    # device time per call: 20 calls captured in a CUDA graph, replayed 5 times between events on
+    # the library's stream (a host loop of short calls would time the host's issue rate instead)
     res = {"mass": m}
     for k, f in ops.items():
-        reps = 50
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            f()
-        e1.record()
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr, stream=stream, capture_error_mode="thread_local"):
+            for _ in range(20):
+                f()
+        gr.replay()
         torch.cuda.synchronize()
-        res[k + "_us_per_call"] = e0.elapsed_time(e1) * 1e3 / reps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            gr.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[k + "_us_per_call"] = e0.elapsed_time(e1) * 1e3 / 100
     print(json.dumps(res))
     ctx.close()
 
@@ -745,7 +757,8 @@ def run_large(args):
     ctx.load_gauge(torch.from_numpy(U).cuda())
     ctx.set_mass(m)
     p = wmg.default_params(nlevels=3, block=w["block"], nvec=w["nvec"], prec_sloppy=wmg.PREC_SINGLE,
-                           prec_smoother=wmg.PREC_HALF, prec_nullvec=w["prec_nullvec"], coarse_tc=3)
+                           prec_smoother=wmg.PREC_HALF, prec_nullvec=w["prec_nullvec"], coarse_tc=3,
+                           fine_eo=args.large_eo, gcr_restart=w["gcr_restart"])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ctx.setup(p)
@@ -779,7 +792,8 @@ def run_large(args):
     peaks, _ = measured_peaks()
     by = V * 48 * 4 + nrhs * V * 48 * 4
     print(json.dumps({
-        "workload": args.large, "mass": m, "mass_source": "hand-chosen", "nrhs": nrhs, "setup_s": t_setup,
+        "workload": args.large, "mass": m, "mass_source": "hand-chosen", "nrhs": nrhs,
+        "fine_eo": args.large_eo, "gcr_restart": w["gcr_restart"], "setup_s": t_setup,
         "solve_s": t_solve, "iters": [i["iters"] for i in info], "max_true_resid": max(i["true_resid"] for i in info),
         "oracle_resid_rhs0": ores, "status": int(st), "coarse_impl_and_tuner_ms": impl,
         "device_bytes_after_setup": bytes_setup, "device_bytes_after_solve": ctx.device_bytes(),
@@ -803,6 +817,8 @@ def main():
     ap.add_argument("--probe-gauge", type=int, default=12, choices=(8, 12, 18),
                     help="reals per link of the FP32 fine operator in --probe")
     ap.add_argument("--probe-mass", type=float, default=None)
+    ap.add_argument("--large-eo", type=int, default=1, choices=(0, 1),
+                    help="red/black outer solve in --large (fine_eo)")
     ap.add_argument("--probe-solve", action="store_true")
     ap.add_argument("--large", default=None, choices=sorted(LARGE),
                     help="one setup and solve on a larger workload (a line for the design notes)")
