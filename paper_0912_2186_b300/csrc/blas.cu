@@ -69,9 +69,9 @@ __global__ void k_dot_norm(const void* a_, const void* b_, size_t n, RedBuf rb) 
     t[1] += x.re * y.im - x.im * y.re;
     t[2] += x.re * x.re + x.im * x.im;
   }
-  double v[3] = {double(t[0]), double(t[1]), double(t[2])};
+  double v[3];
   __shared__ double sm[32 * 3];
-  cta_reduce<3>(v, sm);
+  cta_reduce_mixed<R, 3>(t, v, sm);
   grid_finish<3>(rb, r, blockIdx.x, gridDim.x, v);
 }
 
@@ -84,9 +84,10 @@ __global__ void k_norm2(const void* a_, size_t n, RedBuf rb) {
     cpx<R> x = a[i];
     t += x.re * x.re + x.im * x.im;
   }
-  double v[1] = {double(t)};
+  double v[1];
   __shared__ double sm[32];
-  cta_reduce<1>(v, sm);
+  R tv[1] = {t};
+  cta_reduce_mixed<R, 1>(tv, v, sm);
   grid_finish<1>(rb, r, blockIdx.x, gridDim.x, v);
 }
 
@@ -177,9 +178,10 @@ __global__ void k_cg_update(void* __restrict__ x_, void* __restrict__ r_, const 
       }
     }
   }
-  double v[1] = {double(t)};
+  double v[1];
   __shared__ double sm[32];
-  cta_reduce<1>(v, sm);
+  R tv[1] = {t};
+  cta_reduce_mixed<R, 1>(tv, v, sm);
   const bool last = grid_finish<1>(rb, r, blockIdx.x, gridDim.x, v);
   if (last) {
     __syncthreads();
@@ -239,10 +241,8 @@ __global__ void k_multidot(const void* W, size_t slot_stride, int j0, int kmax, 
     }
   }
   double v[2 * J];
-#pragma unroll
-  for (int j = 0; j < 2 * J; ++j) v[j] = double(t[j]);
   __shared__ double sm[32 * 2 * J];
-  cta_reduce<2 * J>(v, sm);
+  cta_reduce_mixed<R, 2 * J>(t, v, sm);
   grid_finish<2 * J>(rb, r, blockIdx.x, gridDim.x, v);
 }
 
@@ -278,9 +278,9 @@ __global__ void k_gcr_orth(const void* W, const void* Z, size_t slot_stride, int
     t[1] += wi.re * ri.re + wi.im * ri.im;
     t[2] += wi.re * ri.im - wi.im * ri.re;
   }
-  double v[3] = {double(t[0]), double(t[1]), double(t[2])};
+  double v[3];
   __shared__ double sm[32 * 3];
-  cta_reduce<3>(v, sm);
+  cta_reduce_mixed<R, 3>(t, v, sm);
   grid_finish<3>(rb, r, blockIdx.x, gridDim.x, v);
 }
 
@@ -311,9 +311,10 @@ __global__ void k_gcr_update(void* x_, void* r_, void* w_, void* z_, const doubl
     z[i] = inv * zi;
     t += ri.re * ri.re + ri.im * ri.im;
   }
-  double v[1] = {double(t)};
+  double v[1];
   __shared__ double sm[32];
-  cta_reduce<1>(v, sm);
+  R tv[1] = {t};
+  cta_reduce_mixed<R, 1>(tv, v, sm);
   grid_finish<1>(rb, r, blockIdx.x, gridDim.x, v);
 }
 
@@ -336,9 +337,10 @@ __global__ void k_gcr_update_r(void* r_, void* w_, const double* wred, size_t n,
     w[i] = inv * wi;
     t += ri.re * ri.re + ri.im * ri.im;
   }
-  double v[1] = {double(t)};
+  double v[1];
   __shared__ double sm[32];
-  cta_reduce<1>(v, sm);
+  R tv[1] = {t};
+  cta_reduce_mixed<R, 1>(tv, v, sm);
   grid_finish<1>(rb, r, blockIdx.x, gridDim.x, v);
 }
 

@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
     return;
   }
   // epilogue: thread holds rows 16 m + gq (+8) and right-hand sides 8 blk + 2q + (e & 1)
-  double nv2[2] = {0.0, 0.0};
+  float nv2[2] = {0.f, 0.f};  // the thread's sums in FP32, FP64 across lanes, warps and CTAs
   if (mma_warp) {
     const float s_a = s_site;
 #pragma unroll
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
       if (shift && !eo.hop_only && !eo.opB) o += (float)shift[r] * in[((size_t)r * g.V + v) * n + row];
       if (eo.add) o += reinterpret_cast<const cf*>(eo.add)[((size_t)r * g.V + v) * n + row];
       if (!active || active[r]) out[((size_t)r * g.V + v) * n + row] = o;
-      nv2[e & 1] += double(o.re) * o.re + double(o.im) * o.im;
+      nv2[e & 1] += o.re * o.re + o.im * o.im;
     }
   }
   if (want_norm) {

@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(void* __
   if (active && !active[rhs]) return;  // whole CTA exits together (uniform per CTA)
   const size_t fb = spinor_field_bytes<R>(g.V);
   const char* inr = reinterpret_cast<const char*>(in) + fb * rhs;
-  double red[3] = {0.0, 0.0, 0.0};
+  R red[3] = {R(0), R(0), R(0)};
 #pragma unroll 1
   for (int j = 0; j < SPB; ++j) {
   const int v = (sbe * SPB + j) * blockDim.x + threadIdx.x;
@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(void* __
       for (int i = 0; i < 12; ++i) acc[i] = bb[i] - acc[i];
     }
     store_spinor<R>(reinterpret_cast<char*>(out) + fb * rhs, g.V, v, acc);
-    // per-site sums in the field's precision; FP64 across threads and CTAs
+    // per-site sums and the thread's and warp's sums in the field's precision; FP64 across the
+    // warps and CTAs
     if (RED == 2) {
       R a0 = 0, a1 = 0;
 #pragma unroll
@@ -167,14 +168,14 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(void* __
         a0 += acc[i].re * self[i].re + acc[i].im * self[i].im;
         a1 += acc[i].re * self[i].im - acc[i].im * self[i].re;
       }
-      red[0] += double(a0);
-      red[1] += double(a1);
+      red[0] += a0;
+      red[1] += a1;
     }
     if (RED >= 1) {
       R nn = 0;
 #pragma unroll
       for (int i = 0; i < 12; ++i) nn += acc[i].re * acc[i].re + acc[i].im * acc[i].im;
-      red[RED == 2 ? 2 : 0] += double(nn);
+      red[RED == 2 ? 2 : 0] += nn;
     }
   }
   }
@@ -182,8 +183,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(void* __
     constexpr int NV = RED == 2 ? 3 : 1;
     __shared__ double sm[32 * 3];
     double vals[NV];
-    for (int i = 0; i < NV; ++i) vals[i] = red[i];
-    cta_reduce<NV>(vals, sm);
+    cta_reduce_mixed<R, NV>(red, vals, sm);
     grid_finish<NV>(rb, rhs, sbe, nblk_site, vals);
   }
 }
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_dslash_mr(void*
   const double qq = red_prev[rhs * 3 + 2];
   const cpx<R> al = qq > 0.0 ? cpx<R>{R(red_prev[rhs * 3 + 0] / qq), R(red_prev[rhs * 3 + 1] / qq)}
                              : cpx<R>{R(0), R(0)};
-  double red[3] = {0.0, 0.0, 0.0};
+  R red[3] = {R(0), R(0), R(0)};
 #pragma unroll 1
   for (int j = 0; j < SPB; ++j) {
     const int v = (sbe * SPB + j) * blockDim.x + threadIdx.x;
@@ -273,13 +273,14 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_dslash_mr(void*
       a1 += acc[i].re * self[i].im - acc[i].im * self[i].re;
       nn += acc[i].re * acc[i].re + acc[i].im * acc[i].im;
     }
-    red[0] += double(a0);
-    red[1] += double(a1);
-    red[2] += double(nn);
+    red[0] += a0;
+    red[1] += a1;
+    red[2] += nn;
   }
   __shared__ double sm[32 * 3];
-  cta_reduce<3>(red, sm);
-  grid_finish<3>(rb, rhs, sbe, nblk_site, red);
+  double vals[3];
+  cta_reduce_mixed<R, 3>(red, vals, sm);
+  grid_finish<3>(rb, rhs, sbe, nblk_site, vals);
 }
 
 // ------------------------------------------------------------------------------------
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(128) k_dslash_h(void* __restrict__ out16, floa
   const char* inr = reinterpret_cast<const char*>(in) + fbi * rhs;
   const float* inn = IN16 ? in_norm + (size_t)g.V * rhs : nullptr;
   cpx<float> acc[12];
-  double red[3] = {0.0, 0.0, 0.0};
+  float red[3] = {0.f, 0.f, 0.f};
   if (v < g.V) {
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc[i] = cpx<float>{0.f, 0.f};
@@ -359,15 +360,16 @@ __global__ void __launch_bounds__(128) k_dslash_h(void* __restrict__ out16, floa
         a1 += acc[i].re * self[i].im - acc[i].im * self[i].re;
         nn += acc[i].re * acc[i].re + acc[i].im * acc[i].im;
       }
-      red[0] = double(a0);
-      red[1] = double(a1);
-      red[2] = double(nn);
+      red[0] = a0;
+      red[1] = a1;
+      red[2] = nn;
     }
   }
   if constexpr (RED == 2) {
     __shared__ double sm[32 * 3];
-    cta_reduce<3>(red, sm);
-    grid_finish<3>(rb, rhs, sb, nblk_site, red);
+    double vals[3];
+    cta_reduce_mixed<float, 3>(red, vals, sm);
+    grid_finish<3>(rb, rhs, sb, nblk_site, vals);
   }
 }
 

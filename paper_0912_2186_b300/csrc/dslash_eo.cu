@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(128) k_dslash_eo(void* __restrict__ out, const
   const int k = sb * blockDim.x + threadIdx.x;
   const size_t fb = spinor_field_bytes<R>(Vh);
   const char* inr = reinterpret_cast<const char*>(in) + fb * rhs;
-  double red = 0.0;
+  R red = 0;
   if (k < Vh) {
     // coordinates of site 2k, then the site of parity p_out among 2k, 2k + 1
     const uint32_t v0 = 2u * (uint32_t)k;
@@ -81,13 +81,14 @@ __global__ void __launch_bounds__(128) k_dslash_eo(void* __restrict__ out, const
       R nn = 0;
 #pragma unroll
       for (int i = 0; i < 12; ++i) nn += acc[i].re * acc[i].re + acc[i].im * acc[i].im;
-      red = double(nn);
+      red = nn;
     }
   }
   if (RED) {
     __shared__ double sm[32];
-    double vals[1] = {red};
-    cta_reduce<1>(vals, sm);
+    double vals[1];
+    R rv[1] = {red};
+    cta_reduce_mixed<R, 1>(rv, vals, sm);
     grid_finish<1>(rb, rhs, sb, nblk, vals);
   }
 }

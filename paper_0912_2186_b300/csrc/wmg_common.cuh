@@ -321,6 +321,34 @@ WMG_D void cta_reduce(double v[NVAL], double* smem /* >= 32*NVAL */) {
   __syncthreads();
 }
 
+// As cta_reduce, for per-thread values in the kernel's own precision T: the tree within each warp
+// runs in T, the warps' results are summed in FP64 in index order (the same fixed shape), result
+// in out[] of thread 0.  An FP32 kernel so keeps its reductions off the FP64 pipe (1/64 of the
+// FP32 rate on B300) except for one sum per warp; for T = double it is cta_reduce.
+template <typename T, int NVAL>
+WMG_D void cta_reduce_mixed(T v[NVAL], double out[NVAL], double* smem /* >= 32*NVAL */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NVAL; ++i)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NVAL; ++i) smem[warp * NVAL + i] = double(v[i]);
+  __syncthreads();
+  double tot = 0.0;
+  if (threadIdx.x < NVAL) {
+    for (int w = 0; w < nw; ++w) tot += smem[w * NVAL + threadIdx.x];
+  }
+  __syncthreads();
+  if (threadIdx.x < NVAL) smem[threadIdx.x] = tot;
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int i = 0; i < NVAL; ++i) out[i] = smem[i];
+  __syncthreads();
+}
+
 // Sum p[b * stride], b < count, over the whole CTA in a fixed order (thread t takes
 // b = t, t + blockDim, ...; then the fixed-shape tree of cta_reduce).  Valid in thread 0.
 WMG_D double cta_sum_strided(const volatile double* p, int count, int stride, double* smem /* >= 32 */) {
