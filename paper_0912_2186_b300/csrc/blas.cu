@@ -96,7 +96,9 @@ __global__ void k_scale_inv_sqrt(void* x, size_t n, const double* nrm2, int stri
   const int r = blockIdx.y;
   const double q = nrm2[(size_t)r * stride];
   if (!(q > 0.0)) return;
-  const R s = R(1.0 / sqrt(q));
+  R sc[1];
+  cta_scalars<R, 1>(sc, [&](double* v) { v[0] = 1.0 / sqrt(q); });
+  const R s = sc[0];
   cpx<R>* a = vec<R>(x, n, r);
   WMG_GRID_LOOP(i) a[i] = s * a[i];
 }
@@ -119,7 +121,12 @@ __global__ void k_mr_update(void* x_, void* r_, const void* q_, size_t n, const 
   if (active && !active[r]) return;
   const double qq = red[r * 3 + 2];
   if (!(qq > 0.0)) return;
-  const cpx<R> al{R(red[r * 3 + 0] / qq), R(red[r * 3 + 1] / qq)};
+  R sc[2];
+  cta_scalars<R, 2>(sc, [&](double* v) {
+    v[0] = red[r * 3 + 0] / qq;
+    v[1] = red[r * 3 + 1] / qq;
+  });
+  const cpx<R> al{sc[0], sc[1]};
   cpx<R>* x = vec<R>(x_, n, r);
   cpx<R>* rr = vec<R>(r_, n, r);
   const cpx<R>* q = vec<R>(q_, n, r);
@@ -148,7 +155,9 @@ __global__ void k_cg_update(void* __restrict__ x_, void* __restrict__ r_, const 
   const int done = cg.done[r];
   const double qq = cg.qq[r], zz = cg.zz[parity * nrhs + r];
   const bool on = !done && qq > 0.0;
-  const R al = on ? R(zz / qq) : R(0);
+  R sc[1];
+  cta_scalars<R, 1>(sc, [&](double* v) { v[0] = on ? zz / qq : 0.0; });
+  const R al = sc[0];
   cpx<R>* __restrict__ x = vec<R>(x_, n, r);
   cpx<R>* __restrict__ rr = vec<R>(r_, n, r);
   const cpx<R>* __restrict__ p = vec<R>(p_, n, r);
@@ -201,7 +210,9 @@ __global__ void k_cg_xpay(void* __restrict__ p_, const void* __restrict__ z_, si
   const int done = cg.done[r];
   const double zo = cg.zz[parity * nrhs + r], zn = cg.zz[(1 - parity) * nrhs + r];
   if (done) return;
-  const R be = zo > 0.0 ? R(zn / zo) : R(0);
+  R sc[1];
+  cta_scalars<R, 1>(sc, [&](double* v) { v[0] = zo > 0.0 ? zn / zo : 0.0; });
+  const R be = sc[0];
   cpx<R>* __restrict__ p = vec<R>(p_, n, r);
   const cpx<R>* __restrict__ z = vec<R>(z_, n, r);
   for (size_t i0 = (size_t)blockIdx.x * blockDim.x * E + threadIdx.x; i0 < n; i0 += (size_t)gridDim.x * blockDim.x * E) {
@@ -293,8 +304,14 @@ __global__ void k_gcr_update(void* x_, void* r_, void* w_, void* z_, const doubl
   if (active && !active[r]) return;
   const double ww = wred[r * 3 + 0];
   const bool ok = ww > 0.0;
-  const R inv = R(ok ? 1.0 / sqrt(ww) : 0.0);
-  const cpx<R> al{R(ok ? wred[r * 3 + 1] / ww : 0.0), R(ok ? wred[r * 3 + 2] / ww : 0.0)};
+  R sc[3];
+  cta_scalars<R, 3>(sc, [&](double* v) {
+    v[0] = ok ? 1.0 / sqrt(ww) : 0.0;
+    v[1] = ok ? wred[r * 3 + 1] / ww : 0.0;
+    v[2] = ok ? wred[r * 3 + 2] / ww : 0.0;
+  });
+  const R inv = sc[0];
+  const cpx<R> al{sc[1], sc[2]};
   cpx<R>* x = vec<R>(x_, n, r);
   cpx<R>* rv = vec<R>(r_, n, r);
   cpx<R>* w = vec<R>(w_, n, r);
@@ -325,8 +342,14 @@ __global__ void k_gcr_update_r(void* r_, void* w_, const double* wred, size_t n,
   if (active && !active[r]) return;
   const double ww = wred[r * 3 + 0];
   const bool ok = ww > 0.0;
-  const R inv = R(ok ? 1.0 / sqrt(ww) : 0.0);
-  const cpx<R> al{R(ok ? wred[r * 3 + 1] / ww : 0.0), R(ok ? wred[r * 3 + 2] / ww : 0.0)};
+  R sc[3];
+  cta_scalars<R, 3>(sc, [&](double* v) {
+    v[0] = ok ? 1.0 / sqrt(ww) : 0.0;
+    v[1] = ok ? wred[r * 3 + 1] / ww : 0.0;
+    v[2] = ok ? wred[r * 3 + 2] / ww : 0.0;
+  });
+  const R inv = sc[0];
+  const cpx<R> al{sc[1], sc[2]};
   cpx<R>* rv = vec<R>(r_, n, r);
   cpx<R>* w = vec<R>(w_, n, r);
   R t = 0;

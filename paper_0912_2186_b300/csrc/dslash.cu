@@ -218,8 +218,12 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_dslash_mr(void*
   const char* inr = reinterpret_cast<const char*>(in) + fb * rhs;
   const char* qr = reinterpret_cast<const char*>(qin) + fb * rhs;
   const double qq = red_prev[rhs * 3 + 2];
-  const cpx<R> al = qq > 0.0 ? cpx<R>{R(red_prev[rhs * 3 + 0] / qq), R(red_prev[rhs * 3 + 1] / qq)}
-                             : cpx<R>{R(0), R(0)};
+  R sc[2];
+  cta_scalars<R, 2>(sc, [&](double* v) {
+    v[0] = qq > 0.0 ? red_prev[rhs * 3 + 0] / qq : 0.0;
+    v[1] = qq > 0.0 ? red_prev[rhs * 3 + 1] / qq : 0.0;
+  });
+  const cpx<R> al{sc[0], sc[1]};
   R red[3] = {R(0), R(0), R(0)};
 #pragma unroll 1
   for (int j = 0; j < SPB; ++j) {
@@ -382,9 +386,14 @@ __global__ void k_mr_update_h(void* __restrict__ x, void* __restrict__ r16, floa
   if (active && !active[rhs]) return;
   const double qq = red[rhs * 3 + 2];
   if (!(qq > 0.0)) return;
+  float sc[2];
+  cta_scalars<float, 2>(sc, [&](double* v) {
+    v[0] = red[rhs * 3 + 0] / qq;
+    v[1] = red[rhs * 3 + 1] / qq;
+  });
+  const cpx<float> al{sc[0], sc[1]};
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V) return;
-  const cpx<float> al{float(red[rhs * 3 + 0] / qq), float(red[rhs * 3 + 1] / qq)};
   const size_t fh = spinor_h_bytes(V), ff = spinor_field_bytes<float>(V);
   char* rr = reinterpret_cast<char*>(r16) + fh * rhs;
   char* xr = reinterpret_cast<char*>(x) + ff * rhs;

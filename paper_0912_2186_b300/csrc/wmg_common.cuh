@@ -349,6 +349,24 @@ WMG_D void cta_reduce_mixed(T v[NVAL], double out[NVAL], double* smem /* >= 32*N
   __syncthreads();
 }
 
+// NS per-rhs scalars of a vector kernel (f fills them in FP64), formed once per CTA by thread 0
+// and read by every thread from shared memory.  FP64 division and square root cost tens of
+// FP64-pipe operations on B300, which every thread would otherwise repeat.  The values are those
+// each thread would have formed itself.  Call once per kernel, from every thread of the CTA.
+template <typename R, int NS, typename F>
+WMG_D void cta_scalars(R out[NS], F f) {
+  __shared__ R sv[NS];
+  if (threadIdx.x == 0) {
+    double v[NS];
+    f(v);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) sv[i] = R(v[i]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NS; ++i) out[i] = sv[i];
+}
+
 // Sum p[b * stride], b < count, over the whole CTA in a fixed order (thread t takes
 // b = t, t + blockDim, ...; then the fixed-shape tree of cta_reduce).  Valid in thread 0.
 WMG_D double cta_sum_strided(const volatile double* p, int count, int stride, double* smem /* >= 32 */) {
