@@ -294,19 +294,56 @@ struct RedBuf {
   double* result;     // [nrhs][nval]
 };
 
+// Sum of NVAL values over a warp by recursive halving (NVAL <= 32, padded with zeros to P = 2^M):
+// at each of the first M levels a lane keeps the half of its values that the lane bit selects and
+// adds its partner's copy of that half, so the warp needs P - 1 + 5 - M additions and as many
+// shuffles per lane instead of 5 NVAL.  On return s is the warp's sum of value idx, held by the
+// 32 / P lanes with idx = lane >> (5 - M).  The order of the additions is fixed, and a + b = b + a,
+// so both partners hold identical sums.
+template <int NVAL>
+constexpr int warp_reduce_levels() {
+  return NVAL <= 1 ? 0 : NVAL <= 2 ? 1 : NVAL <= 4 ? 2 : NVAL <= 8 ? 3 : NVAL <= 16 ? 4 : 5;
+}
+template <typename T, int NVAL>
+WMG_D void warp_reduce_multi(const T v[NVAL], T& s, int& idx) {
+  constexpr int M = warp_reduce_levels<NVAL>();
+  constexpr int P = 1 << M;
+  static_assert(NVAL >= 1 && NVAL <= 32, "warp_reduce_multi: 1 <= NVAL <= 32");
+  const int lane = threadIdx.x & 31;
+  T w[P];
+#pragma unroll
+  for (int i = 0; i < P; ++i) w[i] = i < NVAL ? v[i] : T(0);
+#pragma unroll
+  for (int lev = 0; lev < 5; ++lev) {
+    const int o = 16 >> lev;
+    if (lev < M) {
+      const int h = P >> (lev + 1);
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int i = 0; i < h; ++i) {
+        const T send = up ? w[i] : w[i + h];
+        const T keep = up ? w[i + h] : w[i];
+        w[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      }
+    } else {
+      w[0] += __shfl_xor_sync(0xffffffffu, w[0], o);
+    }
+  }
+  s = w[0];
+  idx = (lane >> (5 - M)) & (P - 1);
+}
+
 // Reduce NVAL doubles across the CTA (blockDim.x a multiple of 32, <= 1024); the result is
-// valid in thread 0.  Fixed summation order: shuffle tree within each warp, then the warps in
+// valid in thread 0.  Fixed summation order: warp_reduce_multi within each warp, then the warps in
 // index order (thread i combines value i).
 template <int NVAL>
 WMG_D void cta_reduce(double v[NVAL], double* smem /* >= 32*NVAL */) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NVAL; ++i)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
-  if (lane == 0)
-#pragma unroll
-    for (int i = 0; i < NVAL; ++i) smem[warp * NVAL + i] = v[i];
+  double ws;
+  int idx;
+  warp_reduce_multi<double, NVAL>(v, ws, idx);
+  if (idx < NVAL && lane == (idx << (5 - warp_reduce_levels<NVAL>())))
+    smem[warp * NVAL + idx] = ws;
   __syncthreads();
   double tot = 0.0;
   if (threadIdx.x < NVAL) {
@@ -321,20 +358,18 @@ WMG_D void cta_reduce(double v[NVAL], double* smem /* >= 32*NVAL */) {
   __syncthreads();
 }
 
-// As cta_reduce, for per-thread values in the kernel's own precision T: the tree within each warp
-// runs in T, the warps' results are summed in FP64 in index order (the same fixed shape), result
+// As cta_reduce, for per-thread values in the kernel's own precision T: the sums within each warp
+// run in T, the warps' results are summed in FP64 in index order (the same fixed shape), result
 // in out[] of thread 0.  An FP32 kernel so keeps its reductions off the FP64 pipe (1/64 of the
 // FP32 rate on B300) except for one sum per warp; for T = double it is cta_reduce.
 template <typename T, int NVAL>
 WMG_D void cta_reduce_mixed(T v[NVAL], double out[NVAL], double* smem /* >= 32*NVAL */) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NVAL; ++i)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
-  if (lane == 0)
-#pragma unroll
-    for (int i = 0; i < NVAL; ++i) smem[warp * NVAL + i] = double(v[i]);
+  T ws;
+  int idx;
+  warp_reduce_multi<T, NVAL>(v, ws, idx);
+  if (idx < NVAL && lane == (idx << (5 - warp_reduce_levels<NVAL>())))
+    smem[warp * NVAL + idx] = double(ws);
   __syncthreads();
   double tot = 0.0;
   if (threadIdx.x < NVAL) {
