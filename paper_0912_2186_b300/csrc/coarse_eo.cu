@@ -19,35 +19,38 @@ namespace {
 constexpr int kInvThreads = 256;
 constexpr int kInvApplyRhs = 4;  // right-hand sides per CTA of the inverse application
 
-WMG_D cd crecip(cd a) {
-  const double d = a.re * a.re + a.im * a.im;
-  return cd{a.re / d, -a.im / d};
+template <typename R>
+WMG_D cpx<R> crecip(cpx<R> a) {
+  const R d = a.re * a.re + a.im * a.im;
+  return cpx<R>{a.re / d, -a.im / d};
 }
 
 }  // namespace
 
-// In-place inversion of the n x n matrix M (FP64, row-major, shared memory) by Gauss-Jordan
+// In-place inversion of the n x n matrix M (precision R, row-major, shared memory) by Gauss-Jordan
 // elimination on [M | W] with W = I on entry: column by column, partial pivoting (the largest |M_ij|
 // of the rows i >= j, first on ties); W = M^-1 on exit.  f: n scratch; *singular set on a zero pivot.
 // Called by the whole CTA.
-WMG_D void gauss_jordan(cd* M, cd* W, cd* f, int n, int* singular) {
+template <typename R>
+WMG_D void gauss_jordan(cpx<R>* M, cpx<R>* W, cpx<R>* f, int n, int* singular) {
+  using C = cpx<R>;
   __shared__ int piv;
-  __shared__ cd pivinv;
+  __shared__ C pivinv;
   const int w2 = 2 * n;
   for (int j = 0; j < n; ++j) {
     if (threadIdx.x < 32) {
-      double best = -1.0;
+      R best = R(-1);
       int bi = j;
       for (int i = j + (int)threadIdx.x; i < n; i += 32) {
-        const cd x = M[i * n + j];
-        const double m2 = x.re * x.re + x.im * x.im;
+        const C x = M[i * n + j];
+        const R m2 = x.re * x.re + x.im * x.im;
         if (m2 > best) {
           best = m2;
           bi = i;
         }
       }
       for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const R ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) {
           best = ob;
@@ -56,25 +59,25 @@ WMG_D void gauss_jordan(cd* M, cd* W, cd* f, int n, int* singular) {
       }
       if (threadIdx.x == 0) {
         piv = bi;
-        if (!(best > 0.0)) atomicExch(singular, 1);
+        if (!(best > R(0))) atomicExch(singular, 1);
       }
     }
     __syncthreads();
     const int p = piv;
     if (p != j)
       for (int c = threadIdx.x; c < w2; c += blockDim.x) {
-        cd* B = c < n ? M : W;
+        C* B = c < n ? M : W;
         const int cc = c < n ? c : c - n;
-        const cd t = B[j * n + cc];
+        const C t = B[j * n + cc];
         B[j * n + cc] = B[p * n + cc];
         B[p * n + cc] = t;
       }
     __syncthreads();
     if (threadIdx.x == 0) pivinv = crecip(M[j * n + j]);
     __syncthreads();
-    const cd s = pivinv;
+    const C s = pivinv;
     for (int c = threadIdx.x; c < w2; c += blockDim.x) {
-      cd* B = c < n ? M : W;
+      C* B = c < n ? M : W;
       const int cc = c < n ? c : c - n;
       B[j * n + cc] = s * B[j * n + cc];
     }
@@ -83,7 +86,7 @@ WMG_D void gauss_jordan(cd* M, cd* W, cd* f, int n, int* singular) {
     for (int t = threadIdx.x; t < n * w2; t += blockDim.x) {
       const int i = t / w2, c = t - i * w2;
       if (i == j) continue;
-      cd* B = c < n ? M : W;
+      C* B = c < n ? M : W;
       const int cc = c < n ? c : c - n;
       B[i * n + cc] -= f[i] * B[j * n + cc];
     }
@@ -91,15 +94,16 @@ WMG_D void gauss_jordan(cd* M, cd* W, cd* f, int n, int* singular) {
   }
 }
 
-// One CTA per (odd site k, table entry): W = (A_kk + shift I)^-1 in FP64 in shared memory.
+// One CTA per (odd site k, table entry): W = (A_kk + shift I)^-1 in shared memory, in the table's
+// precision R (FP64 for the FP64 coarsest solve; FP32 for the tables of the FP32 and FP16 passes).
 template <typename R>
 __global__ void __launch_bounds__(kInvThreads) k_eo_invert(const cpx<R>* __restrict__ A, Geom g, int n,
                                                            const double* __restrict__ shifts,
                                                            cpx<R>* __restrict__ inv, int* __restrict__ singular) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  cd* M = reinterpret_cast<cd*>(smraw);  // [n][n]
-  cd* W = M + (size_t)n * n;             // [n][n]
-  cd* f = W + (size_t)n * n;             // [n] column j of M before its elimination
+  cpx<R>* M = reinterpret_cast<cpx<R>*>(smraw);  // [n][n]
+  cpx<R>* W = M + (size_t)n * n;                 // [n][n]
+  cpx<R>* f = W + (size_t)n * n;                 // [n] column j of M before its elimination
   const int k = blockIdx.x, Vh = g.V / 2;
   const int v = parity_site(g, k, 1);
   const cpx<R>* a = A + (size_t)v * 9 * n * n;  // slot 0, [col][row]
@@ -107,16 +111,15 @@ __global__ void __launch_bounds__(kInvThreads) k_eo_invert(const cpx<R>* __restr
   for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
     const int col = i / n, row = i - col * n;
     const cpx<R> x = a[i];
-    M[row * n + col] = cd{double(x.re) + (row == col ? sh : 0.0), double(x.im)};
-    W[row * n + col] = cd{row == col ? 1.0 : 0.0, 0.0};
+    M[row * n + col] = cpx<R>{x.re + (row == col ? R(sh) : R(0)), x.im};
+    W[row * n + col] = cpx<R>{row == col ? R(1) : R(0), R(0)};
   }
   __syncthreads();
-  gauss_jordan(M, W, f, n, singular);
+  gauss_jordan<R>(M, W, f, n, singular);
   cpx<R>* o = inv + ((size_t)blockIdx.y * Vh + k) * n * n;
   for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
     const int col = i / n, row = i - col * n;
-    const cd x = W[row * n + col];
-    o[i] = cpx<R>{R(x.re), R(x.im)};
+    o[i] = W[row * n + col];
   }
 }
 
@@ -195,26 +198,28 @@ void eo_hop_inverse(const void* A, const void* inv_entry, const Geom& g, int n, 
 // M_x = (S_xx)^-1 at even site x (grid.x = its parity-site number) for one shift:
 //   S_xx = A_xx + shift I - sum over the two-hop paths x -> y = x + k1 -> x (every slot k2 of y that
 //          points back at x: both slots on an extent of 2) of A(x, k1) (A_yy + shift I)^-1 A(y, k2),
-// in FP64 (A: the FP64 stencil; the odd inverses: the shift's FP32 table entry, indexed by the odd
-// parity-site number y >> 1), then inverted by Gauss-Jordan.  Out: FP32 [k][col][row].
-__global__ void __launch_bounds__(kInvThreads) k_eo_schur_self_inv(const cd* __restrict__ A, const cf* __restrict__ inv,
+// in FP32 (A: the FP32 stencil; the odd inverses: the shift's FP32 table entry, indexed by the odd
+// parity-site number y >> 1), then inverted by Gauss-Jordan in FP32: the block-Jacobi preconditioner
+// of the FP32 / FP16 coarsest CG.  Out: FP32 [k][col][row].
+__global__ void __launch_bounds__(kInvThreads) k_eo_schur_self_inv(const cf* __restrict__ A, const cf* __restrict__ inv,
                                                                    Geom g, int n, double shift, cf* __restrict__ M,
                                                                    int* __restrict__ singular) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  cd* S = reinterpret_cast<cd*>(smraw);  // [n][n] row-major
-  cd* W = S + (size_t)n * n;
-  cd* Pm = W + (size_t)n * n;            // A(x, k1) (A_yy + shift)^-1, row-major
-  cd* f = Pm + (size_t)n * n;
+  cf* S = reinterpret_cast<cf*>(smraw);  // [n][n] row-major
+  cf* W = S + (size_t)n * n;
+  cf* Pm = W + (size_t)n * n;            // A(x, k1) (A_yy + shift)^-1, row-major
+  cf* f = Pm + (size_t)n * n;
+  const float shf = (float)shift;
   const int k = blockIdx.x, nn = n * n;
   const int x = parity_site(g, k, 0);
   int cx[4];
   site_coords(g, x, cx);
-  const cd* Ax = A + (size_t)x * 9 * nn;
+  const cf* Ax = A + (size_t)x * 9 * nn;
   for (int i = threadIdx.x; i < nn; i += blockDim.x) {
     const int col = i / n, row = i - col * n;
-    const cd a = Ax[i];
-    S[row * n + col] = cd{a.re + (row == col ? shift : 0.0), a.im};
-    W[row * n + col] = cd{row == col ? 1.0 : 0.0, 0.0};
+    const cf a = Ax[i];
+    S[row * n + col] = cf{a.re + (row == col ? shf : 0.f), a.im};
+    W[row * n + col] = cf{row == col ? 1.f : 0.f, 0.f};
   }
   __syncthreads();
   for (int k1 = 1; k1 < 9; ++k1) {
@@ -222,34 +227,30 @@ __global__ void __launch_bounds__(kInvThreads) k_eo_schur_self_inv(const cd* __r
     const cf* iy = inv + (size_t)(y >> 1) * nn;  // [col][row]
     for (int i = threadIdx.x; i < nn; i += blockDim.x) {
       const int row = i / n, col = i - row * n;
-      cd acc{0.0, 0.0};
-      for (int j = 0; j < n; ++j) {
-        const cd a = Ax[((size_t)k1 * n + j) * n + row];
-        const cf b = iy[(size_t)col * n + j];
-        cfma(acc, a, cd{double(b.re), double(b.im)});
-      }
+      cf acc{0.f, 0.f};
+      for (int j = 0; j < n; ++j) cfma(acc, Ax[((size_t)k1 * n + j) * n + row], iy[(size_t)col * n + j]);
       Pm[row * n + col] = acc;
     }
     __syncthreads();
     int cy[4];
     site_coords(g, y, cy);
-    const cd* Ay = A + (size_t)y * 9 * nn;
+    const cf* Ay = A + (size_t)y * 9 * nn;
     for (int k2 = 1; k2 < 9; ++k2) {
       if (neighbour(g, y, cy, (k2 - 1) >> 1, ((k2 - 1) & 1) ? -1 : +1) != x) continue;
       for (int i = threadIdx.x; i < nn; i += blockDim.x) {
         const int row = i / n, col = i - row * n;
-        cd acc{0.0, 0.0};
+        cf acc{0.f, 0.f};
         for (int j = 0; j < n; ++j) cfma(acc, Pm[row * n + j], Ay[((size_t)k2 * n + col) * n + j]);
         S[row * n + col] -= acc;
       }
     }
     __syncthreads();
   }
-  gauss_jordan(S, W, f, n, singular);
+  gauss_jordan<float>(S, W, f, n, singular);
   cf* o = M + (size_t)k * nn;
   for (int i = threadIdx.x; i < nn; i += blockDim.x) {
     const int col = i / n, row = i - col * n;
-    o[i] = cf{float(W[row * n + col].re), float(W[row * n + col].im)};
+    o[i] = W[row * n + col];
   }
 }
 
@@ -308,16 +309,16 @@ __global__ void __launch_bounds__(256) k_eo_bj_table(int mode, const cf* __restr
   }
 }
 
-void eo_schur_self_inv(const void* A64, const void* inv_entry, const Geom& g, int n, double shift, void* M,
+void eo_schur_self_inv(const void* A32, const void* inv_entry, const Geom& g, int n, double shift, void* M,
                        int* singular, cudaStream_t s) {
   count_launch();
-  const size_t smem = ((size_t)3 * n * n + n) * sizeof(cd);
+  const size_t smem = ((size_t)3 * n * n + n) * sizeof(cf);
   static const bool attr = [] {
     cudaFuncSetAttribute(k_eo_schur_self_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     return true;
   }();
   (void)attr;
-  k_eo_schur_self_inv<<<g.V / 2, kInvThreads, smem, s>>>((const cd*)A64, (const cf*)inv_entry, g, n, shift, (cf*)M,
+  k_eo_schur_self_inv<<<g.V / 2, kInvThreads, smem, s>>>((const cf*)A32, (const cf*)inv_entry, g, n, shift, (cf*)M,
                                                           singular);
 }
 
@@ -342,7 +343,7 @@ void eo_invert(int prec, const void* A, const Geom& g, int n, const double* shif
                int* singular, cudaStream_t s) {
   if (ne <= 0) return;
   count_launch();
-  const size_t smem = ((size_t)2 * n * n + n) * sizeof(cd);
+  const size_t smem = ((size_t)2 * n * n + n) * 2 * prec_real_bytes(prec);
   static const bool attr = [] {
     cudaFuncSetAttribute(k_eo_invert<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_eo_invert<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

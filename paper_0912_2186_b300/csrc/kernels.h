@@ -181,8 +181,8 @@ void coarse_apply(int prec, const void* A, const Geom& g, int n, const void* in,
                   const double* shift, bool dagger, const int* active, const RedBuf* rb_norm, cudaStream_t s,
                   const StencilEo* eo = nullptr);
 // A_oo^-1 for the even-odd coarsest solve (coarse_eo.cu): for table entries e0 + j, j < ne,
-// inv[e0 + j][k] = (A[odd site k][0] + shifts[j] I)^-1, FP64 Gauss-Jordan with partial
-// pivoting, stored [e][k][col][row] in precision prec; *singular set to 1 on a zero pivot.
+// inv[e0 + j][k] = (A[odd site k][0] + shifts[j] I)^-1, Gauss-Jordan with partial pivoting in
+// precision prec (A in that precision), stored [e][k][col][row]; *singular set to 1 on a zero pivot.
 void eo_invert(int prec, const void* A, const Geom& g, int n, const double* shifts, int e0, int ne, void* inv,
                int* singular, cudaStream_t s);
 size_t eo_inverse_bytes(int prec, const Geom& g, int n);  // one table entry
@@ -195,11 +195,11 @@ void eo_inv_apply(int prec, const void* inv, const int* idx, const Geom& g, int 
                   const void* h, double hc, void* out, int nrhs, bool dagger, const int* active, cudaStream_t s,
                   int par = 1);  // par = 0: the same at the even sites with a table of even-site blocks
 // right block-Jacobi preconditioning of the Schur complement (coarse_eo.cu): M = (S_xx)^-1 per even
-// site for one shift (FP32 [even site][col][row]; A64 the FP64 stencil, inv_entry the shift's FP32
-// odd-inverse table entry), and the FP32 tables of the preconditioned passes (stencil layout
+// site for one shift, formed and inverted in FP32 (FP32 [even site][col][row]; A32 the FP32
+// stencil, inv_entry the shift's FP32 odd-inverse table entry), and the FP32 tables of the preconditioned passes (stencil layout
 // [parity site][9][col][row]): mode 0 B M(x + s) (odd sites, B from eo_hop_inverse), mode 1 the
 // even pass of S M, mode 2 M times the even pass (for M S)
-void eo_schur_self_inv(const void* A64, const void* inv_entry, const Geom& g, int n, double shift, void* M,
+void eo_schur_self_inv(const void* A32, const void* inv_entry, const Geom& g, int n, double shift, void* M,
                        int* singular, cudaStream_t s);
 void eo_bj_table(int mode, const void* A32, const void* B, const void* M, const Geom& g, int n, double shift,
                  void* out, cudaStream_t s);

@@ -641,7 +641,7 @@ static wmg_status ensure_eoB(wmg_ctx* c, int l, int prec, int nrhs, EoTable* tb)
       stencil_to_mma(WMG_PREC_SINGLE, Bt, Vh, n, (float*)tsc[0] + e * Vh, (char*)t16[0] + e * eb, c->stream);
       if (bj) {
         void* Me = (char*)M32 + e * mb;
-        eo_schur_self_inv(L.A[WMG_PREC_DOUBLE], inv_e, L.g, n, sh, Me, c->d_flag + 3, c->stream);
+        eo_schur_self_inv(L.A[WMG_PREC_SINGLE], inv_e, L.g, n, sh, Me, c->d_flag + 3, c->stream);
         // slot 0 of the odd-site table must be zero for every entry (the even-site tables written
         // before it fill slot 0): it enters the per-site scale of the FP16 copy
         CU(c, cudaMemsetAsync(Bt2, 0, (size_t)Vh * 9 * n * n * sizeof(cf), c->stream));
