@@ -3,6 +3,7 @@
 // call share it).  Every scalar is per right-hand side and lives on the device; reductions
 // are deterministic (fixed-order two-stage sums in double precision).
 #include "kernels.h"
+#include "ptx.cuh"
 
 namespace wmg {
 
@@ -152,6 +153,7 @@ __global__ void k_cg_update(void* __restrict__ x_, void* __restrict__ r_, const 
                             const void* __restrict__ q_, size_t n, CgScalars cg, int parity, int nrhs, RedBuf rb) {
   constexpr int E = kBlasPerThread;
   const int r = blockIdx.y;
+  griddep_wait();  // everything below reads the previous kernel's results
   const int done = cg.done[r];
   const double qq = cg.qq[r], zz = cg.zz[parity * nrhs + r];
   const bool on = !done && qq > 0.0;
@@ -187,6 +189,7 @@ __global__ void k_cg_update(void* __restrict__ x_, void* __restrict__ r_, const 
       }
     }
   }
+  griddep_launch_dependents();
   double v[1];
   __shared__ double sm[32];
   R tv[1] = {t};
@@ -207,6 +210,7 @@ __global__ void k_cg_xpay(void* __restrict__ p_, const void* __restrict__ z_, si
                           int nrhs) {
   constexpr int E = kBlasPerThread;
   const int r = blockIdx.y;
+  griddep_wait();  // everything below reads the previous kernel's results
   const int done = cg.done[r];
   const double zo = cg.zz[parity * nrhs + r], zn = cg.zz[(1 - parity) * nrhs + r];
   if (done) return;
@@ -228,6 +232,7 @@ __global__ void k_cg_xpay(void* __restrict__ p_, const void* __restrict__ z_, si
       if (i < n) p[i] = zv[j] + be * pv[j];
     }
   }
+  griddep_launch_dependents();
 }
 
 // coef_j = <W_j, w> for j = j0 .. j0+J-1 (j < kmax)
@@ -516,14 +521,32 @@ void blas_mr_update(int prec, void* x, void* r, const void* q, size_t n, int nrh
 void cg_update(int prec, void* x, void* r, const void* p, const void* q, size_t n, int nrhs, const CgScalars& cg,
                int parity, const RedBuf& rb_rr, cudaStream_t s) {
   count_launch();
-  dim3 g(blas_blocks(n), nrhs);
-  WMG_BY_PREC(prec, k_cg_update, <<<g, kBlasThreads, 0, s>>>(x, r, p, q, n, cg, parity, nrhs, rb_rr));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blas_blocks(n), nrhs);
+  cfg.blockDim = dim3(kBlasThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_launches() ? 1 : 0;
+  if (prec == WMG_PREC_DOUBLE) cudaLaunchKernelEx(&cfg, k_cg_update<double>, x, r, p, q, n, cg, parity, nrhs, rb_rr);
+  else cudaLaunchKernelEx(&cfg, k_cg_update<float>, x, r, p, q, n, cg, parity, nrhs, rb_rr);
 }
 
 void cg_xpay(int prec, void* p, const void* z, size_t n, int nrhs, const CgScalars& cg, int parity, cudaStream_t s) {
   count_launch();
-  dim3 g(blas_blocks(n), nrhs);
-  WMG_BY_PREC(prec, k_cg_xpay, <<<g, kBlasThreads, 0, s>>>(p, z, n, cg, parity, nrhs));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blas_blocks(n), nrhs);
+  cfg.blockDim = dim3(kBlasThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_launches() ? 1 : 0;
+  if (prec == WMG_PREC_DOUBLE) cudaLaunchKernelEx(&cfg, k_cg_xpay<double>, p, z, n, cg, parity, nrhs);
+  else cudaLaunchKernelEx(&cfg, k_cg_xpay<float>, p, z, n, cg, parity, nrhs);
 }
 
 void gcr_multidot(int prec, const void* W, size_t slot_stride, int kmax, const void* w, size_t n, int nrhs,

@@ -159,6 +159,9 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
     }
   }
   const cf* hin = eo.hop_in ? reinterpret_cast<const cf*>(eo.hop_in) : in;
+  // everything above reads only the operator tables and the geometry: with a programmatic launch
+  // it overlaps the end of the previous kernel, whose results are read from here on
+  griddep_wait();
   // gather this warp's right-hand sides (all loads first), then per rhs the max |Re|, |Im| by
   // shuffles and the scaled FP16 copy in column layout [Xr 0..7 | Xi 0..7 | Xr 8..15 | Xi 8..15]
   cf xv[RPW][EPL];
@@ -228,6 +231,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
       }
     }
   }
+  griddep_launch_dependents();  // the next kernel may start its own table-only prologue
   // a tile whose wait expired: give its copies a second bounded chance to land before exit
   if (mma_warp && !ready) mbar_wait_bounded(smem_addr(&mbar[m]), 0, kMmaSpinLimit);
   if (eo.inv) {
@@ -352,9 +356,18 @@ static void launch_mma(const void* A16, const float* sA, const Geom& g, const vo
   (void)attr;
   dim3 grid(eo.parity < 0 ? g.V : g.V / 2, (nrhs + R - 1) / R);
   RedBuf r = rb ? *rb : RedBuf{nullptr, nullptr, nullptr};
-  k_coarse_apply_mma<NDOF, NT><<<grid, kMmaThreads, smem, s>>>((const uint4*)A16, sA, g, (const cf*)in, (cf*)out,
-                                                               nrhs, shift, dagger ? 1 : 0, active, r, rb ? 1 : 0,
-                                                               eo, err);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(kMmaThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_launches() ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k_coarse_apply_mma<NDOF, NT>, (const uint4*)A16, sA, g, (const cf*)in, (cf*)out, nrhs,
+                     shift, dagger ? 1 : 0, active, r, rb ? 1 : 0, eo, err);
 }
 
 template <int NDOF>

@@ -5,6 +5,11 @@
 namespace wmg {
 
 constexpr int kDslashThreads = 128;
+// whether the coarsest CG's kernels are launched with programmatic stream serialisation (each may
+// start while its predecessor finishes): inside pdl_scope(true) ... pdl_scope(false) only, and not
+// with WMG_PDL=0
+bool pdl_launches();
+void pdl_scope(bool on);
 constexpr int kBlasThreads = 256;
 constexpr int kMaxRhs = 64;          // right-hand sides per batched launch
 constexpr int kMaxKrylov = 32;       // outer GCR restart length limit

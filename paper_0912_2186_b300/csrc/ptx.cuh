@@ -10,6 +10,14 @@ namespace wmg {
 
 WMG_D uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// Programmatic dependent launch (sm_90 and later): a kernel launched with programmatic stream
+// serialisation may start while the previous kernel of the stream runs; griddep_wait blocks until
+// that kernel has completed and its memory operations are visible (a no-op without the launch
+// attribute), and griddep_launch_dependents lets the next such kernel start once every CTA of this
+// one has issued it or exited.
+WMG_D void griddep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+WMG_D void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 WMG_D void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
 }

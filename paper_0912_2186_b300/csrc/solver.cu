@@ -21,6 +21,17 @@ namespace wmg {
 static std::atomic<long long> g_launches{0};
 long long launch_count() { return g_launches.load(); }
 void count_launch(int n) { g_launches += n; }
+// Programmatic launches are used only inside the coarsest CG's loop (pdl_scope), where the
+// operator tables and masks that a pass reads before its griddep_wait are final.
+static thread_local bool t_pdl_scope = false;
+void pdl_scope(bool on) { t_pdl_scope = on; }
+bool pdl_launches() {
+  static const bool on = [] {
+    const char* e = getenv("WMG_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on && t_pdl_scope;
+}
 }  // namespace wmg
 
 wmg_status wmg_cuda_fail(cudaError_t e, const char* what) {
@@ -938,7 +949,9 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
       const long long l0 = launch_count();
       e = cudaStreamBeginCaptureToGraph(s, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
+        pdl_scope(true);
         for (int i = 0; i < chunk; ++i) body(i & 1);
+        pdl_scope(false);
         const int per = (int)(launch_count() - l0) + 1;
         k_cg_check<<<1, 32, 0, s>>>(cg.done, c->d_flag + 1, nrhs, chunk, c->prm.coarse_maxit, per, h);
         e = cudaStreamEndCapture(s, &bodyg);
@@ -953,7 +966,9 @@ wmg_status cgnr(wmg_ctx* c, int l, int prec, const void* b, void* x, int nrhs, c
     CU(c, cudaGraphLaunch(it->second.first, s));
   } else {
     for (int itr = 0; itr < c->prm.coarse_maxit; itr += chunk) {
+      pdl_scope(true);
       for (int i = 0; i < chunk; ++i) body(i & 1);
+      pdl_scope(false);
       bool all;
       TRY(all_done(&all));
       if (all) break;
