@@ -368,3 +368,25 @@ def test_fine_even_odd_solve(W, prec):
             assert np.array_equal(host(x1)[0], xs[1]) and i1[0]["iters"] == info[1]["iters"]
     print(f"outer iterations whole lattice {its[0]}, red/black {its[1]}")
     assert all(b <= 1.3 * a + 2 for a, b in zip(its[0], its[1]))
+
+
+def test_coarse_cg_graph_and_host_loop_identical(W, monkeypatch):
+    """The coarsest CG as a CUDA graph with a WHILE node and as the host-driven loop (a context
+    created with WMG_NO_GRAPHS=1, the form the instrumented benchmark step and the ncu launch lists
+    use) launch the same kernels in the same order, programmatic launches included: the solutions
+    are bit-identical and meet the 1e-10 true residual (oracle D)."""
+    b = synth.gaussian_spinors(CFG1["dims"], 3, 31)
+    xs, its = {}, {}
+    for flag in ("0", "1"):
+        monkeypatch.setenv("WMG_NO_GRAPHS", flag)
+        ctx, U, p = _ctx(W, CFG1, 1, fine_eo=1)
+        x = dev(np.zeros_like(b))
+        st, info = ctx.solve(dev(b), x, 3)
+        xs[flag] = host(x)
+        its[flag] = [i["iters"] for i in info]
+        for r in range(3):
+            assert info[r]["converged"]
+            assert oracle_resid(U, CFG1["m"], b[r], xs[flag][r]) <= 1.05e-10
+        ctx.close()
+    assert its["0"] == its["1"]
+    assert np.array_equal(xs["0"], xs["1"])
