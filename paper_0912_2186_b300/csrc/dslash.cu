@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(void* __
                                                                         const void* __restrict__ gauge, Geom g,
                                                                         DslashDiv dv, const double* __restrict__ mass,
                                                                         const int* __restrict__ active, int nrhs,
-                                                                        int nblk_site, RedBuf rb) {
+                                                                        int nblk_site, RedBuf rb, int b_half) {
   constexpr int SPB = dslash_spb<R, RED>();
   const int rhs = blockIdx.x % nrhs;
   const int sbe = blockIdx.x / nrhs;
@@ -153,8 +153,16 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(void* __
       acc[i] = o;
     }
     if (b) {
+      // b_half: b holds the even sites only (half-lattice fields, site v at v >> 1), zero elsewhere
       cpx<R> bb[12];
-      load_spinor<R>(reinterpret_cast<const char*>(b) + fb * rhs, g.V, v, bb);
+      if (!b_half) {
+        load_spinor<R>(reinterpret_cast<const char*>(b) + fb * rhs, g.V, v, bb);
+      } else if (((c[0] + c[1] + c[2] + c[3]) & 1) == 0) {
+        load_spinor<R>(reinterpret_cast<const char*>(b) + spinor_field_bytes<R>(g.V / 2) * rhs, g.V / 2, v >> 1, bb);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 12; ++i) bb[i] = cpx<R>{R(0), R(0)};
+      }
 #pragma unroll
       for (int i = 0; i < 12; ++i) acc[i] = bb[i] - acc[i];
     }
@@ -480,7 +488,7 @@ int dslash_blocks(int V) { return (V + kDslashThreads - 1) / kDslashThreads; }
 
 void dslash(int prec, void* out, const void* in, const void* b, const void* gauge, const Geom& g,
             const double* mass_dev, const int* active, int nrhs, int red, const RedBuf* rb, cudaStream_t s,
-            int gc) {
+            int gc, int b_half) {
   count_launch();
   const int nb = dslash_blocks(g.V);
   const int spb = prec == WMG_PREC_DOUBLE ? dslash_spb<double, 1>() : dslash_spb<float, 1>();
@@ -490,9 +498,9 @@ void dslash(int prec, void* out, const void* in, const void* b, const void* gaug
   const DslashDiv dv{make_fastdiv(g.L[0]), make_fastdiv(g.L[1]), make_fastdiv(g.L[2])};
 #define WMG_DS(R, GC)                                                                                         \
   do {                                                                                                        \
-    if (red == 0) k_dslash<R, 0, GC><<<grid, kDslashThreads, 0, s>>>(out, in, b, gauge, g, dv, mass_dev, active, nrhs, nb, r); \
-    else if (red == 1) k_dslash<R, 1, GC><<<gridr, kDslashThreads, 0, s>>>(out, in, b, gauge, g, dv, mass_dev, active, nrhs, nbr, r); \
-    else k_dslash<R, 2, GC><<<gridr, kDslashThreads, 0, s>>>(out, in, b, gauge, g, dv, mass_dev, active, nrhs, nbr, r); \
+    if (red == 0) k_dslash<R, 0, GC><<<grid, kDslashThreads, 0, s>>>(out, in, b, gauge, g, dv, mass_dev, active, nrhs, nb, r, b_half); \
+    else if (red == 1) k_dslash<R, 1, GC><<<gridr, kDslashThreads, 0, s>>>(out, in, b, gauge, g, dv, mass_dev, active, nrhs, nbr, r, b_half); \
+    else k_dslash<R, 2, GC><<<gridr, kDslashThreads, 0, s>>>(out, in, b, gauge, g, dv, mass_dev, active, nrhs, nbr, r, b_half); \
   } while (0)
   if (prec == WMG_PREC_DOUBLE) WMG_DS(double, 12);
   else if (gc == 8) WMG_DS(float, 8);

@@ -31,10 +31,11 @@ void unpack_spinor(int prec, const void* in, double* canon, int V, int nrhs, cud
 int dslash_blocks(int V);
 // out = D in, or out = b - D in when b != nullptr.  mass_dev[nrhs]: per-rhs Wilson mass.
 // red = 0: none; 1: |out|^2 per rhs into rb->result[rhs]; 2: {Re, Im <out,in>, |out|^2}.
-// gc = 8 / 18: FP32 only, `gauge` holds 8-real (pack_gauge8) or 18-real (pack_gauge18) links
+// gc = 8 / 18: FP32 only, `gauge` holds 8-real (pack_gauge8) or 18-real (pack_gauge18) links.
+// b_half = 1: b holds the even sites only, as half-lattice fields (zero on the odd sites).
 void dslash(int prec, void* out, const void* in, const void* b, const void* gauge, const Geom& g,
             const double* mass_dev, const int* active, int nrhs, int red, const RedBuf* rb, cudaStream_t s,
-            int gc = 12);
+            int gc = 12, int b_half = 0);
 // one MR step with the previous update fused in: r_out = r - alpha q, x += alpha r, out = D r_out
 // with the sums {Re, Im <out, r_out>, |out|^2} per rhs into rb (alpha from red_prev[3 r ..]);
 // out and r_out must not alias r, q; rb.result must not alias red_prev
@@ -140,14 +141,16 @@ struct Blocking {
   int N;         // vectors
   int nf;        // complex dof per fine site (12 on the fine lattice, 2N' on a coarse one)
 };
-// fine level: fine spinors (native) <-> coarse vectors; P = N native fine fields
+// fine level: fine spinors (native) <-> coarse vectors; P = N native fine fields.  half = 1 (N <= 64,
+// even block x extent): `in` holds the even sites only as half-lattice fields (zero on the odd
+// sites), and only the even sites' rows of P are read.
 void restrict_fine(int prec, const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
-                   const int* active, cudaStream_t s);
+                   const int* active, cudaStream_t s, int half = 0);
 void prolong_fine(int prec, const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
                   const int* active, cudaStream_t s);
 // FP32 vectors, FP16 null vectors (false: blocking not handled, use the FP32 copy)
 bool restrict_fine_h(const void* P16, const Blocking& bk, const void* in, void* out, int nrhs, const int* active,
-                     cudaStream_t s);
+                     cudaStream_t s, int half = 0);
 bool prolong_fine_h(const void* P16, const Blocking& bk, const void* in, void* out, int nrhs, const int* active,
                     cudaStream_t s);
 void convert_to_half2(const void* src64, void* dst16, size_t n, cudaStream_t s);  // complex FP64 -> (re, im) FP16

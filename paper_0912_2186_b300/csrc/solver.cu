@@ -260,9 +260,10 @@ double coarse_bytes_eo(const wmg_ctx* c, int l, int prec, int nact, bool tables 
   const double inv = tables ? 0.0 : V / 2 * n * n * 2.0 * s;
   return V / 2 * 17.0 * n * n * 2.0 * sa + inv + V * 4.0 + (double)nact * V * n * 2.0 * s * 2.0;
 }
-double transfer_bytes(const wmg_ctx* c, int l, int prec, int nact) {
+double transfer_bytes(const wmg_ctx* c, int l, int prec, int nact, bool half = false) {
   const LevelData& L = c->L[l];
-  const double s = rb_(prec), nf = (double)L.g.V * L.ndof, nc = (double)L.bk.coarse.V * 2.0 * L.bk.N;
+  const double s = rb_(prec), nf = (double)L.g.V * L.ndof * (half ? 0.5 : 1.0),
+               nc = (double)L.bk.coarse.V * 2.0 * L.bk.N;
   return (double)L.bk.N * nf * 2.0 * s + (double)nact * (nf + nc) * 2.0 * s;
 }
 static int nact_of(const wmg_ctx* c, const int* active, int nrhs) { return active ? c->n_active : nrhs; }
@@ -396,7 +397,7 @@ wmg_status mr(wmg_ctx* c, int l, int prec, void* x, const void* b, int nrhs, int
     RedBuf ra = rb, rbb = redbuf(c, RES_MR2);
     {
       ProfScope ps(c, dcls, dslash_bytes(c, prec, na, true), na);
-      dslash(prec, r, x, b, U, c->fine, c->d_mass, active, nrhs, 0, nullptr, c->stream, gc);
+      dslash(prec, r, x, b, U, c->fine, c->d_mass, active, nrhs, 0, nullptr, c->stream, gc, c->cyc_b_half ? 1 : 0);
     }
     {
       ProfScope ps(c, dcls, dslash_bytes(c, prec, na, false), na);
@@ -419,7 +420,7 @@ wmg_status mr(wmg_ctx* c, int l, int prec, void* x, const void* b, int nrhs, int
   }
   if (l == 0) {
     ProfScope ps(c, dcls, dslash_bytes(c, prec, na, true), na);
-    dslash(prec, r, x, b, U, c->fine, c->d_mass, active, nrhs, 0, nullptr, c->stream, gc);
+    dslash(prec, r, x, b, U, c->fine, c->d_mass, active, nrhs, 0, nullptr, c->stream, gc, c->cyc_b_half ? 1 : 0);
   } else {
     level_apply(c, l, prec, x, r, nrhs, active, 0, nullptr);
     ProfScope ps(c, blas_cls(l), vec_bytes(c, l, prec, na, 3), na);
@@ -1007,10 +1008,13 @@ wmg_status cycle(wmg_ctx* c, int l, int last, int prec, const void* r, void* e, 
       rin = t;
     }
     {
-      ProfScope ps(c, PROF_RESTRICT, transfer_bytes(c, l, prec, nact_of(c, active, nrhs)), nact_of(c, active, nrhs));
+      const int half = l == 0 && c->cyc_b_half ? 1 : 0;  // r: the even sites as half-lattice fields
+      ProfScope ps(c, PROF_RESTRICT, transfer_bytes(c, l, prec, nact_of(c, active, nrhs), half != 0),
+                   nact_of(c, active, nrhs));
       if (l == 0) {
-        if (!(prec == WMG_PREC_SINGLE && L.P16 && restrict_fine_h(L.P16, L.bk, rin, rc, nrhs, active, c->stream)))
-          restrict_fine(prec, L.P[prec], L.bk, rin, rc, nrhs, active, c->stream);
+        if (!(prec == WMG_PREC_SINGLE && L.P16 &&
+              restrict_fine_h(L.P16, L.bk, rin, rc, nrhs, active, c->stream, half)))
+          restrict_fine(prec, L.P[prec], L.bk, rin, rc, nrhs, active, c->stream, half);
       }
       else restrict_coarse(prec, L.P[prec], L.bk, rin, rc, nrhs, active, c->stream);
     }
@@ -1360,9 +1364,23 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
     }
     void* zk = (char*)Z + slot * k;
     void* wk = (char*)W + slot * k;
-    if (use_mg && eo) {  // the whole-lattice cycle on (r_e, 0); its even part preconditions S
-      eo_embed(lo, rfl, rlo, nullptr, fg, nslots, s);
-      TRY(cycle(c, 0, c->nlev - 1, lo, rfl, zfl, nslots, c->d_active));
+    if (use_mg && eo) {
+      // the whole-lattice cycle on (r_e, 0); its even part preconditions S.  Where the fine-level
+      // kernels that read the cycle's right-hand side (the restriction and the smoother's first
+      // residual) take the even sites as a half-lattice field, r_e goes in as it is; otherwise
+      // through its whole-lattice embedding
+      const LevelData& L0 = c->L[0];
+      const bool half = lo == WMG_PREC_SINGLE && c->prm.prec_smoother != WMG_PREC_HALF && L0.bk.N <= 64 &&
+                        L0.bk.b[0] % 2 == 0;
+      if (half) {
+        c->cyc_b_half = true;
+        const wmg_status st = cycle(c, 0, c->nlev - 1, lo, rlo, zfl, nslots, c->d_active);
+        c->cyc_b_half = false;
+        TRY(st);
+      } else {
+        eo_embed(lo, rfl, rlo, nullptr, fg, nslots, s);
+        TRY(cycle(c, 0, c->nlev - 1, lo, rfl, zfl, nslots, c->d_active));
+      }
       eo_extract(lo, zk, zfl, fg, 0, nslots, s);
     } else if (use_mg) {
       TRY(cycle(c, 0, c->nlev - 1, lo, rlo, zk, nslots, c->d_active));

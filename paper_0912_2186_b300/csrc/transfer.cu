@@ -84,6 +84,26 @@ WMG_D int block_site(const Blocking& bk, int xc, int e) {
   return site_index(bk.fine, f);
 }
 
+// The e-th even site of block xc, e < bs / 2.  The block's x extent is even, so its sites 2e and
+// 2e + 1 are neighbours in x and exactly one of them is even.
+WMG_D int even_block_site(const Blocking& bk, int xc, int e) {
+  int c[4];
+  site_coords(bk.coarse, xc, c);
+  const int e2 = 2 * e;
+  int o[4];
+  o[0] = e2 % bk.b[0];
+  int t = e2 / bk.b[0];
+  o[1] = t % bk.b[1];
+  t /= bk.b[1];
+  o[2] = t % bk.b[2];
+  o[3] = t / bk.b[2];
+  int f[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) f[i] = c[i] * bk.b[i] + o[i];
+  const int v = site_index(bk.fine, f);
+  return ((f[0] + f[1] + f[2] + f[3]) & 1) ? v + 1 : v;
+}
+
 // fine field element (site v, component k) inside one native field
 template <typename R>
 WMG_D cpx<R>* fine_elem(void* f, int V, int v, int k) {
@@ -272,7 +292,7 @@ constexpr int kRWarps = 8;  // warps of the restrict CTA
 template <typename R, typename PT, int TA, int TR, int S>
 __global__ void __launch_bounds__(kRWarps * 32) k_restrict_fine3(const void* __restrict__ P, Blocking bk,
                                                                  const void* __restrict__ in, void* __restrict__ out,
-                                                                 int nrhs, const int* __restrict__ active) {
+                                                                 int nrhs, const int* __restrict__ active, int half) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int NA = 8 * TA, RC = 4 * TR;
   constexpr int CB = 2 * sizeof(cpx<R>), CBP = PSt<PT>::kPair;  // bytes of a component pair: x, P
@@ -285,16 +305,19 @@ __global__ void __launch_bounds__(kRWarps * 32) k_restrict_fine3(const void* __r
   constexpr size_t stage = pbytes + (size_t)RC * Kp * sizeof(cpx<R>);
   const int xc = blockIdx.x, s = blockIdx.y, r0 = blockIdx.z * RC;
   const int N = bk.N, V = bk.fine.V, bs = bk.bs;
+  // half: `in` holds the even sites only (half-lattice fields, site v at v >> 1; zero on the odd
+  // sites), so only the block's bs / 2 even sites are read, of the vectors and of P
+  const int bsx = half ? bs / 2 : bs;
   auto Pbuf = [&](int q) { return reinterpret_cast<PT*>(smraw + (size_t)q * stage); };
   auto Xbuf = [&](int q) { return reinterpret_cast<cpx<R>*>(smraw + (size_t)q * stage + pbytes); };
   int* vsite = reinterpret_cast<int*>(smraw + 2 * stage);  // [bs] fine site of each block site
-  const size_t fb = spinor_field_bytes<R>(V), fbp = (size_t)V * 6 * CBP;  // vector / P field bytes
+  const size_t fb = spinor_field_bytes<R>(half ? V / 2 : V), fbp = (size_t)V * 6 * CBP;  // vector / P field bytes
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, ag = lane >> 2, rg = lane & 3;
   const int kb = warp * KW, ke = min(K, kb + KW);
   unsigned rmask = 0;  // right-hand sides of this chunk that are present and active
   for (int j = 0; j < RC; ++j)
     if (r0 + j < nrhs && (!active || active[r0 + j])) rmask |= 1u << j;
-  for (int e = threadIdx.x; e < bs; e += NT) vsite[e] = block_site(bk, xc, e);
+  for (int e = threadIdx.x; e < bsx; e += NT) vsite[e] = half ? even_block_site(bk, xc, e) : block_site(bk, xc, e);
   // P rows alpha >= N stay zero in both buffers
   for (int i = threadIdx.x; i < (NA - N) * Kp; i += NT) {
     Pbuf(0)[(size_t)N * Kp + i] = PSt<PT>::zero();
@@ -303,12 +326,13 @@ __global__ void __launch_bounds__(kRWarps * 32) k_restrict_fine3(const void* __r
   __syncthreads();
   // this thread stages item (cc, e) of rows row0, row0 + RSTEP, ...
   const int item = threadIdx.x % CE, row0 = threadIdx.x / CE, cc = item / S, e = item % S;
-  const size_t coff = (size_t)(3 * s + cc) * V;
-  const int nchunks = (bs + S - 1) / S;
+  const size_t coff = (size_t)(3 * s + cc) * V, xoff = half ? (size_t)(3 * s + cc) * (V / 2) : coff;
+  const int nchunks = (bsx + S - 1) / S;
   auto issue = [&](int q) {
     if (q < nchunks && row0 < RSTEP) {
-      const bool in_blk = q * S + e < bs;
-      const size_t site = coff + (in_blk ? vsite[q * S + e] : 0);
+      const bool in_blk = q * S + e < bsx;
+      const int vs = in_blk ? vsite[q * S + e] : 0;
+      const size_t site = coff + vs, xsite = xoff + (half ? vs >> 1 : vs);
       for (int row = row0; row < N + RC; row += RSTEP) {
         if (row < N) {
           PT* dst = Pbuf(q & 1) + (size_t)row * Kp + (cc * S + e) * 2;
@@ -317,7 +341,7 @@ __global__ void __launch_bounds__(kRWarps * 32) k_restrict_fine3(const void* __r
         } else {
           cpx<R>* dst = Xbuf(q & 1) + (size_t)(row - N) * Kp + (cc * S + e) * 2;
           if (in_blk && ((rmask >> (row - N)) & 1u)) {
-            const char* src = (const char*)in + fb * (r0 + row - N) + site * CB;
+            const char* src = (const char*)in + fb * (r0 + row - N) + xsite * CB;
 #pragma unroll
             for (int h = 0; h < CB / 16; ++h) cp_async16((char*)dst + 16 * h, src + 16 * h);
           } else {
@@ -384,44 +408,44 @@ static size_t restrict3_smem(int bs) {
 
 template <typename R, typename PT, int TA, int TR, int S>
 static void launch_restrict_fine3s(const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
-                                   const int* active, cudaStream_t s) {
+                                   const int* active, cudaStream_t s, int half) {
   constexpr int RC = 4 * TR;
   static const cudaError_t attr = cudaFuncSetAttribute(k_restrict_fine3<R, PT, TA, TR, S>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   (void)attr;
   dim3 g(bk.coarse.V, 2, (nrhs + RC - 1) / RC);
   k_restrict_fine3<R, PT, TA, TR, S><<<g, kRWarps * 32, restrict3_smem<R, PT, TA, TR, S>(bk.bs), s>>>(P, bk, in, out,
-                                                                                                      nrhs, active);
+                                                                                                      nrhs, active, half);
 }
 
 // sites per staged chunk: 16, or 8 when two 16-site stages would not fit in shared memory
 template <typename R, typename PT, int TA, int TR>
 static void launch_restrict_fine3(const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
-                                  const int* active, cudaStream_t s) {
+                                  const int* active, cudaStream_t s, int half) {
   if (restrict3_smem<R, PT, TA, TR, 16>(bk.bs) <= 200 * 1024)
-    launch_restrict_fine3s<R, PT, TA, TR, 16>(P, bk, in, out, nrhs, active, s);
+    launch_restrict_fine3s<R, PT, TA, TR, 16>(P, bk, in, out, nrhs, active, s, half);
   else
-    launch_restrict_fine3s<R, PT, TA, TR, 8>(P, bk, in, out, nrhs, active, s);
+    launch_restrict_fine3s<R, PT, TA, TR, 8>(P, bk, in, out, nrhs, active, s, half);
 }
 
 template <typename R, typename PT, int TA>
 static void restrict_fine3_tr(const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
-                              const int* active, cudaStream_t s) {
-  if (nrhs <= 4) launch_restrict_fine3<R, PT, TA, 1>(P, bk, in, out, nrhs, active, s);
-  else if (nrhs <= 8) launch_restrict_fine3<R, PT, TA, 2>(P, bk, in, out, nrhs, active, s);
-  else launch_restrict_fine3<R, PT, TA, 3>(P, bk, in, out, nrhs, active, s);
+                              const int* active, cudaStream_t s, int half) {
+  if (nrhs <= 4) launch_restrict_fine3<R, PT, TA, 1>(P, bk, in, out, nrhs, active, s, half);
+  else if (nrhs <= 8) launch_restrict_fine3<R, PT, TA, 2>(P, bk, in, out, nrhs, active, s, half);
+  else launch_restrict_fine3<R, PT, TA, 3>(P, bk, in, out, nrhs, active, s, half);
 }
 
 template <typename R, typename PT>
 static void restrict_fine3(const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
-                           const int* active, cudaStream_t s) {
+                           const int* active, cudaStream_t s, int half = 0) {
   const int ta = (bk.N + 7) / 8;
-  if (ta <= 1) restrict_fine3_tr<R, PT, 1>(P, bk, in, out, nrhs, active, s);
-  else if (ta <= 2) restrict_fine3_tr<R, PT, 2>(P, bk, in, out, nrhs, active, s);
-  else if (ta <= 3) restrict_fine3_tr<R, PT, 3>(P, bk, in, out, nrhs, active, s);
-  else if (ta <= 4) restrict_fine3_tr<R, PT, 4>(P, bk, in, out, nrhs, active, s);
-  else if (ta <= 6) restrict_fine3_tr<R, PT, 6>(P, bk, in, out, nrhs, active, s);
-  else restrict_fine3_tr<R, PT, 8>(P, bk, in, out, nrhs, active, s);
+  if (ta <= 1) restrict_fine3_tr<R, PT, 1>(P, bk, in, out, nrhs, active, s, half);
+  else if (ta <= 2) restrict_fine3_tr<R, PT, 2>(P, bk, in, out, nrhs, active, s, half);
+  else if (ta <= 3) restrict_fine3_tr<R, PT, 3>(P, bk, in, out, nrhs, active, s, half);
+  else if (ta <= 4) restrict_fine3_tr<R, PT, 4>(P, bk, in, out, nrhs, active, s, half);
+  else if (ta <= 6) restrict_fine3_tr<R, PT, 6>(P, bk, in, out, nrhs, active, s, half);
+  else restrict_fine3_tr<R, PT, 8>(P, bk, in, out, nrhs, active, s, half);
 }
 
 template <typename R, typename PT, int RC>
@@ -662,10 +686,10 @@ static void launch_restrict_fine(const void* P, const Blocking& bk, const void* 
 // FP32 vectors with FP16 null vectors (the native layout with __half2 elements); false when the
 // blocking is outside what the staged kernels handle (the caller then uses the FP32 copy).
 bool restrict_fine_h(const void* P16, const Blocking& bk, const void* in, void* out, int nrhs, const int* active,
-                     cudaStream_t s) {
+                     cudaStream_t s, int half) {
   if (bk.N > 64) return false;
   count_launch();
-  restrict_fine3<float, __half2>(P16, bk, in, out, nrhs, active, s);
+  restrict_fine3<float, __half2>(P16, bk, in, out, nrhs, active, s, half);
   return true;
 }
 bool prolong_fine_h(const void* P16, const Blocking& bk, const void* in, void* out, int nrhs, const int* active,
@@ -688,11 +712,11 @@ void convert_to_half2(const void* src64, void* dst16, size_t n, cudaStream_t s) 
 }
 
 void restrict_fine(int prec, const void* P, const Blocking& bk, const void* in, void* out, int nrhs,
-                   const int* active, cudaStream_t s) {
+                   const int* active, cudaStream_t s, int half) {
   count_launch();
   if (bk.N <= 64) {
-    if (prec == WMG_PREC_DOUBLE) restrict_fine3<double, cpx<double>>(P, bk, in, out, nrhs, active, s);
-    else restrict_fine3<float, cpx<float>>(P, bk, in, out, nrhs, active, s);
+    if (prec == WMG_PREC_DOUBLE) restrict_fine3<double, cpx<double>>(P, bk, in, out, nrhs, active, s, half);
+    else restrict_fine3<float, cpx<float>>(P, bk, in, out, nrhs, active, s, half);
     return;
   }
   if (prec == WMG_PREC_DOUBLE) {
