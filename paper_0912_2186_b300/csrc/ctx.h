@@ -96,6 +96,8 @@ struct wmg_ctx {
   bool use_graphs = true;                      // capture the coarsest CGNR iterations
   int cg_chunk = 2;                            // CGNR iterations between convergence checks (even)
   bool cyc_b_half = false;  // the fine-level cycle's right-hand side is an even half-lattice field
+  void* cyc_out_half = nullptr;  // non-null: the fine-level cycle's result goes here (even sites,
+                                 // half-lattice), from its last MR step
   bool use_fused_galerkin = true;              // fused fine-level Galerkin kernel
   bool use_eoB = true;                         // precomputed odd-site pass of the coarse Schur complement
   bool use_eobj = true;                        // block-Jacobi preconditioned coarsest CG (with use_eoB)

@@ -132,7 +132,52 @@ __global__ void k_eo_extract(void* __restrict__ half, const void* __restrict__ f
   }
 }
 
+// The last MR step of the red/black solve's cycle, restricted to what the outer solve uses:
+// out_e = x_e + alpha r_e at the even sites (alpha = red[0..1] / red[2] per rhs), written as
+// half-lattice fields; x, r whole-lattice.  One thread per (even site k, rhs).
+template <typename R>
+__global__ void k_mr_update_even(const void* __restrict__ x, const void* __restrict__ r, void* __restrict__ out,
+                                 Geom g, EoDiv dv, const double* __restrict__ red, const int* __restrict__ active) {
+  const int rhs = blockIdx.y;
+  if (active && !active[rhs]) return;
+  const double qq = red[rhs * 3 + 2];
+  R sc[2];
+  cta_scalars<R, 2>(sc, [&](double* v) {
+    v[0] = qq > 0.0 ? red[rhs * 3 + 0] / qq : 0.0;
+    v[1] = qq > 0.0 ? red[rhs * 3 + 1] / qq : 0.0;
+  });
+  const cpx<R> al{sc[0], sc[1]};
+  const int Vh = g.V / 2;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= Vh) return;
+  const uint32_t v0 = 2u * (uint32_t)k;
+  const uint32_t q0 = fdiv(v0, dv.dx), q1 = fdiv(q0, dv.dy), q2 = fdiv(q1, dv.dz);
+  const int odd0 = ((int)(v0 - q0 * g.L[0]) + (int)(q0 - q1 * g.L[1]) + (int)(q1 - q2 * g.L[2]) + (int)q2) & 1;
+  const int v = (int)v0 + odd0;  // the even one of the sites 2k, 2k + 1
+  const char* xr = reinterpret_cast<const char*>(x) + spinor_field_bytes<R>(g.V) * rhs;
+  const char* rr = reinterpret_cast<const char*>(r) + spinor_field_bytes<R>(g.V) * rhs;
+  char* o = reinterpret_cast<char*>(out) + spinor_field_bytes<R>(Vh) * rhs;
+#pragma unroll
+  for (int ch = 0; ch < 6; ++ch) {
+    cpx<R> a, b, ra, rb2;
+    Chunk2<R>::load(xr, (size_t)ch * g.V + v, a, b);
+    Chunk2<R>::load(rr, (size_t)ch * g.V + v, ra, rb2);
+    cfma(a, al, ra);
+    cfma(b, al, rb2);
+    Chunk2<R>::store(o, (size_t)ch * Vh + k, a, b);
+  }
+}
+
 int dslash_eo_blocks(int V) { return (V / 2 + kDslashThreads - 1) / kDslashThreads; }
+
+void mr_update_even(int prec, const void* x, const void* r, void* out_half, const Geom& g, int nrhs,
+                    const double* red, const int* active, cudaStream_t s) {
+  count_launch();
+  const dim3 grid((g.V / 2 + 255) / 256, nrhs);
+  const EoDiv dv{make_fastdiv(g.L[0]), make_fastdiv(g.L[1]), make_fastdiv(g.L[2])};
+  if (prec == WMG_PREC_DOUBLE) k_mr_update_even<double><<<grid, 256, 0, s>>>(x, r, out_half, g, dv, red, active);
+  else k_mr_update_even<float><<<grid, 256, 0, s>>>(x, r, out_half, g, dv, red, active);
+}
 
 void dslash_eo(int prec, int mode, int p_out, void* out, const void* in, const void* self, const void* b,
                const void* gauge, int gc, const Geom& g, const double* mass_dev, const int* active, int nrhs,

@@ -67,6 +67,10 @@ void dslash_eo(int prec, int mode, int p_out, void* out, const void* in, const v
 int dslash_eo_blocks(int V);
 // whole-lattice native field <- even sites from half_e, odd sites from half_o (zeros for a null
 // one); and the half field of parity p from a whole-lattice one
+// out_e = x_e + alpha r_e at the even sites as half-lattice fields (alpha = red[0..1] / red[2] per
+// rhs; x, r whole-lattice native fields): the last MR step of the red/black solve's cycle
+void mr_update_even(int prec, const void* x, const void* r, void* out_half, const Geom& g, int nrhs,
+                    const double* red, const int* active, cudaStream_t s);
 void eo_embed(int prec, void* full, const void* half_e, const void* half_o, const Geom& g, int nrhs, cudaStream_t s);
 void eo_extract(int prec, void* half, const void* full, const Geom& g, int p, int nrhs, cudaStream_t s);
 

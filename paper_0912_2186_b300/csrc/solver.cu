@@ -435,6 +435,12 @@ wmg_status mr(wmg_ctx* c, int l, int prec, void* x, const void* b, int nrhs, int
       ProfScope ps(c, blas_cls(l), vec_bytes(c, l, prec, na, 2), na);
       blas_dot_norm(prec, q, r, n, nrhs, rb, c->stream);
     }
+    if (l == 0 && c->cyc_out_half && i + 1 == nu) {
+      // the red/black solve uses only the even sites of the result: written as half-lattice fields
+      ProfScope ps(c, PROF_BLAS, vec_bytes(c, l, prec, na, 1.5), na);
+      mr_update_even(prec, x, r, c->cyc_out_half, c->fine, nrhs, rb.result, active, c->stream);
+      continue;
+    }
     // x read + written, r read (+ written), q read when r is updated
     ProfScope ps(c, blas_cls(l), vec_bytes(c, l, prec, na, i + 1 < nu ? 5 : 3), na);
     blas_mr_update(prec, x, r, q, n, nrhs, rb.result, i + 1 < nu, active, c->stream);  // last r unused
@@ -1372,16 +1378,21 @@ wmg_status fgcr_engine(wmg_ctx* c, int nslots, SlotSource& src, bool use_mg) {
       const LevelData& L0 = c->L[0];
       const bool half = lo == WMG_PREC_SINGLE && c->prm.prec_smoother != WMG_PREC_HALF && L0.bk.N <= 64 &&
                         L0.bk.b[0] % 2 == 0;
+      // ... and, when the cycle ends with FP32 MR steps of its own, its last step writes the even
+      // sites of the result straight into z_k
+      const bool out_half = half && c->prm.nu_post > 0 && !c->use_mr_fuse;
       if (half) {
         c->cyc_b_half = true;
+        c->cyc_out_half = out_half ? zk : nullptr;
         const wmg_status st = cycle(c, 0, c->nlev - 1, lo, rlo, zfl, nslots, c->d_active);
         c->cyc_b_half = false;
+        c->cyc_out_half = nullptr;
         TRY(st);
       } else {
         eo_embed(lo, rfl, rlo, nullptr, fg, nslots, s);
         TRY(cycle(c, 0, c->nlev - 1, lo, rfl, zfl, nslots, c->d_active));
       }
-      eo_extract(lo, zk, zfl, fg, 0, nslots, s);
+      if (!out_half) eo_extract(lo, zk, zfl, fg, 0, nslots, s);
     } else if (use_mg) {
       TRY(cycle(c, 0, c->nlev - 1, lo, rlo, zk, nslots, c->d_active));
     } else {
