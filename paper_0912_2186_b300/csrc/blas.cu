@@ -66,9 +66,8 @@ __global__ void k_dot_norm(const void* a_, const void* b_, size_t n, RedBuf rb) 
   R t[3] = {0, 0, 0};  // per-thread sums in the vectors' precision, FP64 across threads
   WMG_GRID_LOOP(i) {
     cpx<R> x = a[i], y = b[i];
-    t[0] += x.re * y.re + x.im * y.im;
-    t[1] += x.re * y.im - x.im * y.re;
-    t[2] += x.re * x.re + x.im * x.im;
+    cdot_acc(t[0], t[1], x, y);
+    norm2_acc(t[2], x);
   }
   double v[3];
   __shared__ double sm[32 * 3];
@@ -83,7 +82,7 @@ __global__ void k_norm2(const void* a_, size_t n, RedBuf rb) {
   R t = 0;
   WMG_GRID_LOOP(i) {
     cpx<R> x = a[i];
-    t += x.re * x.re + x.im * x.im;
+    norm2_acc(t, x);
   }
   double v[1];
   __shared__ double sm[32];
@@ -185,7 +184,7 @@ __global__ void k_cg_update(void* __restrict__ x_, void* __restrict__ r_, const 
           x[i] = xv[j];
           rr[i] = rv[j];
         }
-        t += rv[j].re * rv[j].re + rv[j].im * rv[j].im;
+        norm2_acc(t, rv[j]);
       }
     }
   }
@@ -251,8 +250,7 @@ __global__ void k_multidot(const void* W, size_t slot_stride, int j0, int kmax, 
     for (int j = 0; j < J; ++j) {
       if (j0 + j < kmax) {
         const cpx<R> a = vec<R>((const char*)W + (j0 + j) * slot_stride, n, r)[i];
-        t[2 * j] += a.re * b.re + a.im * b.im;
-        t[2 * j + 1] += a.re * b.im - a.im * b.re;
+        cdot_acc(t[2 * j], t[2 * j + 1], a, b);
       }
     }
   }
@@ -290,9 +288,8 @@ __global__ void k_gcr_orth(const void* W, const void* Z, size_t slot_stride, int
       z[i] = zi;
     }
     const cpx<R> ri = rv[i];
-    t[0] += wi.re * wi.re + wi.im * wi.im;
-    t[1] += wi.re * ri.re + wi.im * ri.im;
-    t[2] += wi.re * ri.im - wi.im * ri.re;
+    norm2_acc(t[0], wi);
+    cdot_acc(t[1], t[2], wi, ri);
   }
   double v[3];
   __shared__ double sm[32 * 3];
@@ -331,7 +328,7 @@ __global__ void k_gcr_update(void* x_, void* r_, void* w_, void* z_, const doubl
     rv[i] = ri;
     w[i] = inv * wi;
     z[i] = inv * zi;
-    t += ri.re * ri.re + ri.im * ri.im;
+    norm2_acc(t, ri);
   }
   double v[1];
   __shared__ double sm[32];
@@ -363,7 +360,7 @@ __global__ void k_gcr_update_r(void* r_, void* w_, const double* wred, size_t n,
     const cpx<R> ri = rv[i] - al * wi;
     rv[i] = ri;
     w[i] = inv * wi;
-    t += ri.re * ri.re + ri.im * ri.im;
+    norm2_acc(t, ri);
   }
   double v[1];
   __shared__ double sm[32];

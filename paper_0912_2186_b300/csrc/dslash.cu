@@ -173,8 +173,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(void* __
       R a0 = 0, a1 = 0;
 #pragma unroll
       for (int i = 0; i < 12; ++i) {
-        a0 += acc[i].re * self[i].re + acc[i].im * self[i].im;
-        a1 += acc[i].re * self[i].im - acc[i].im * self[i].re;
+        cdot_acc(a0, a1, acc[i], self[i]);
       }
       red[0] += a0;
       red[1] += a1;
@@ -182,7 +181,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(void* __
     if (RED >= 1) {
       R nn = 0;
 #pragma unroll
-      for (int i = 0; i < 12; ++i) nn += acc[i].re * acc[i].re + acc[i].im * acc[i].im;
+      for (int i = 0; i < 12; ++i) norm2_acc(nn, acc[i]);
       red[RED == 2 ? 2 : 0] += nn;
     }
   }
@@ -281,9 +280,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_dslash_mr(void*
     R a0 = 0, a1 = 0, nn = 0;
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
-      a0 += acc[i].re * self[i].re + acc[i].im * self[i].im;
-      a1 += acc[i].re * self[i].im - acc[i].im * self[i].re;
-      nn += acc[i].re * acc[i].re + acc[i].im * acc[i].im;
+      cdot_acc(a0, a1, acc[i], self[i]);
+      norm2_acc(nn, acc[i]);
     }
     red[0] += a0;
     red[1] += a1;
@@ -368,9 +366,8 @@ __global__ void __launch_bounds__(128) k_dslash_h(void* __restrict__ out16, floa
       float a0 = 0.f, a1 = 0.f, nn = 0.f;
 #pragma unroll
       for (int i = 0; i < 12; ++i) {
-        a0 += acc[i].re * self[i].re + acc[i].im * self[i].im;
-        a1 += acc[i].re * self[i].im - acc[i].im * self[i].re;
-        nn += acc[i].re * acc[i].re + acc[i].im * acc[i].im;
+        cdot_acc(a0, a1, acc[i], self[i]);
+        norm2_acc(nn, acc[i]);
       }
       red[0] = a0;
       red[1] = a1;

@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(128) k_dslash_eo(void* __restrict__ out, const
     if (RED) {
       R nn = 0;
 #pragma unroll
-      for (int i = 0; i < 12; ++i) nn += acc[i].re * acc[i].re + acc[i].im * acc[i].im;
+      for (int i = 0; i < 12; ++i) norm2_acc(nn, acc[i]);
       red = nn;
     }
   }

@@ -600,7 +600,7 @@ __global__ void __launch_bounds__(kGsThreads) k_block_gs(void* vecs, GsLayout L,
     double n0 = 0;
     {
       double t[1] = {0};
-      for (int i = 0; i < ne; ++i) t[0] += norm2(vk[i]);
+      for (int i = 0; i < ne; ++i) norm2_acc(t[0], vk[i]);
       cta_reduce<1>(t, sm);
       if (threadIdx.x == 0) coef[0] = t[0];
       __syncthreads();
@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(kGsThreads) k_block_gs(void* vecs, GsLayout L,
         // (Kahan-Parlett criterion: otherwise one classical pass is already orthogonal to
         // working precision)
         double t[1] = {0};
-        for (int i = 0; i < ne; ++i) t[0] += norm2(vk[i]);
+        for (int i = 0; i < ne; ++i) norm2_acc(t[0], vk[i]);
         cta_reduce<1>(t, sm);
         if (threadIdx.x == 0) coef[0] = t[0];
         __syncthreads();
@@ -631,9 +631,12 @@ __global__ void __launch_bounds__(kGsThreads) k_block_gs(void* vecs, GsLayout L,
           const int j = j0 + q;
           if (j < k)
             for (int i = 0; i < ne; ++i) {
+              // <v_j, v_k> as FMA chains: 4 FP64 operations per complex term instead of 6
               const cd a = base[fs * j + off[i]];
-              t[2 * q] += a.re * vk[i].re + a.im * vk[i].im;
-              t[2 * q + 1] += a.re * vk[i].im - a.im * vk[i].re;
+              t[2 * q] = fma(a.re, vk[i].re, t[2 * q]);
+              t[2 * q] = fma(a.im, vk[i].im, t[2 * q]);
+              t[2 * q + 1] = fma(a.re, vk[i].im, t[2 * q + 1]);
+              t[2 * q + 1] = fma(-a.im, vk[i].re, t[2 * q + 1]);
             }
         }
         cta_reduce<2 * kGsChunk>(t, sm);
@@ -643,14 +646,14 @@ __global__ void __launch_bounds__(kGsThreads) k_block_gs(void* vecs, GsLayout L,
       }
       for (int j = 0; j < k; ++j) {
         const cd cj{coef[2 * j], coef[2 * j + 1]};
-        for (int i = 0; i < ne; ++i) vk[i] = vk[i] - cj * base[fs * j + off[i]];
+        for (int i = 0; i < ne; ++i) cfms(vk[i], cj, base[fs * j + off[i]]);
       }
       __syncthreads();
     }
     double n1;
     {
       double t[1] = {0};
-      for (int i = 0; i < ne; ++i) t[0] += norm2(vk[i]);
+      for (int i = 0; i < ne; ++i) norm2_acc(t[0], vk[i]);
       cta_reduce<1>(t, sm);
       if (threadIdx.x == 0) coef[0] = t[0];
       __syncthreads();

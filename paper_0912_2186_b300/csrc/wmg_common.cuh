@@ -58,7 +58,26 @@ template <typename R> WMG_HD void cfmac(cpx<R>& acc, cpx<R> a, cpx<R> b) {
   acc.im = fma(a.re, b.im, acc.im);
   acc.im = fma(-a.im, b.re, acc.im);
 }
+// acc -= c * b
+template <typename R> WMG_HD void cfms(cpx<R>& acc, cpx<R> c, cpx<R> b) {
+  acc.re = fma(-c.re, b.re, acc.re);
+  acc.re = fma(c.im, b.im, acc.re);
+  acc.im = fma(-c.re, b.im, acc.im);
+  acc.im = fma(-c.im, b.re, acc.im);
+}
 template <typename R> WMG_HD R norm2(cpx<R> a) { return a.re * a.re + a.im * a.im; }
+// re += Re(conj(a) b), im += Im(conj(a) b) as FMA chains (4 operations instead of 6)
+template <typename R> WMG_HD void cdot_acc(R& re, R& im, cpx<R> a, cpx<R> b) {
+  re = fma(a.re, b.re, re);
+  re = fma(a.im, b.im, re);
+  im = fma(a.re, b.im, im);
+  im = fma(-a.im, b.re, im);
+}
+// t += |a|^2 as two FMAs (a.re * a.re + a.im * a.im, then the add, is three operations)
+template <typename R> WMG_HD void norm2_acc(R& t, cpx<R> a) {
+  t = fma(a.re, a.re, t);
+  t = fma(a.im, a.im, t);
+}
 template <typename T, typename R> WMG_HD cpx<T> ccast(cpx<R> a) { return {T(a.re), T(a.im)}; }
 
 // multiply by a unit phase: ph = 0 -> 1, 1 -> i, 2 -> -1, 3 -> -i
