@@ -337,6 +337,25 @@ __global__ void k_gcr_update(void* x_, void* r_, void* w_, void* z_, const doubl
   grid_finish<1>(rb, r, blockIdx.x, gridDim.x, v);
 }
 
+// r_out = r - alpha q (an MR step whose solution update is deferred)
+template <typename R>
+__global__ void k_mr_rnext(void* __restrict__ ro_, const void* __restrict__ r_, const void* __restrict__ q_, size_t n,
+                           const double* __restrict__ red, const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  const double qq = red[r * 3 + 2];
+  R sc[2];
+  cta_scalars<R, 2>(sc, [&](double* v) {
+    v[0] = qq > 0.0 ? red[r * 3 + 0] / qq : 0.0;
+    v[1] = qq > 0.0 ? red[r * 3 + 1] / qq : 0.0;
+  });
+  const cpx<R> al{sc[0], sc[1]};
+  cpx<R>* ro = vec<R>(ro_, n, r);
+  const cpx<R>* rv = vec<R>(r_, n, r);
+  const cpx<R>* q = vec<R>(q_, n, r);
+  WMG_GRID_LOOP(i) ro[i] = rv[i] - al * q[i];
+}
+
 // alpha = <w,r>/|w|^2, r -= alpha w, w /= |w|; red = |r|^2 (the solution update is deferred)
 template <typename R>
 __global__ void k_gcr_update_r(void* r_, void* w_, const double* wred, size_t n, const int* active, RedBuf rb) {
@@ -513,6 +532,13 @@ void blas_mr_update(int prec, void* x, void* r, const void* q, size_t n, int nrh
   count_launch();
   dim3 g(blas_blocks(n), nrhs);
   WMG_BY_PREC(prec, k_mr_update, <<<g, kBlasThreads, 0, s>>>(x, r, q, n, red, active, update_r ? 1 : 0));
+}
+
+void blas_mr_rnext(int prec, void* r_out, const void* r, const void* q, size_t n, int nrhs, const double* red,
+                   const int* active, cudaStream_t s) {
+  count_launch();
+  dim3 g(blas_blocks(n), nrhs);
+  WMG_BY_PREC(prec, k_mr_rnext, <<<g, kBlasThreads, 0, s>>>(r_out, r, q, n, red, active));
 }
 
 void cg_update(int prec, void* x, void* r, const void* p, const void* q, size_t n, int nrhs, const CgScalars& cg,

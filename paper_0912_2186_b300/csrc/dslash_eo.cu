@@ -168,7 +168,61 @@ __global__ void k_mr_update_even(const void* __restrict__ x, const void* __restr
   }
 }
 
+// The red/black cycle's MR smoother with its solution updates deferred: after steps 1..nsteps the
+// result at the even sites is out_e = x_e + alpha_1 r_1 + ... + alpha_n r_n (the residual of step
+// i in r.p[i], alpha_i = red[i][0..1] / red[i][2] per rhs, red[i] = red0 + i * rstride), formed
+// with the same FMA sequence as step-by-step updates of x; half-lattice output.
+template <typename R>
+__global__ void k_mr_combine_even(const void* __restrict__ x, MrSteps rs, void* __restrict__ out, Geom g, EoDiv dv,
+                                  const double* __restrict__ red0, int rstride, const int* __restrict__ active) {
+  const int rhs = blockIdx.y;
+  if (active && !active[rhs]) return;
+  R sc[2 * kMrMaxSteps];
+  cta_scalars<R, 2 * kMrMaxSteps>(sc, [&](double* v) {
+    for (int i = 0; i < kMrMaxSteps; ++i) {
+      const double* rd = red0 + (size_t)i * rstride + rhs * 3;
+      const bool ok = i < rs.n && rd[2] > 0.0;
+      v[2 * i] = ok ? rd[0] / rd[2] : 0.0;
+      v[2 * i + 1] = ok ? rd[1] / rd[2] : 0.0;
+    }
+  });
+  const int Vh = g.V / 2;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= Vh) return;
+  const uint32_t v0 = 2u * (uint32_t)k;
+  const uint32_t q0 = fdiv(v0, dv.dx), q1 = fdiv(q0, dv.dy), q2 = fdiv(q1, dv.dz);
+  const int odd0 = ((int)(v0 - q0 * g.L[0]) + (int)(q0 - q1 * g.L[1]) + (int)(q1 - q2 * g.L[2]) + (int)q2) & 1;
+  const int v = (int)v0 + odd0;  // the even one of the sites 2k, 2k + 1
+  const size_t fb = spinor_field_bytes<R>(g.V);
+  const char* xr = reinterpret_cast<const char*>(x) + fb * rhs;
+  char* o = reinterpret_cast<char*>(out) + spinor_field_bytes<R>(Vh) * rhs;
+#pragma unroll
+  for (int ch = 0; ch < 6; ++ch) {
+    cpx<R> a, b;
+    Chunk2<R>::load(xr, (size_t)ch * g.V + v, a, b);
+    for (int i = 0; i < rs.n; ++i) {
+      cpx<R> ra, rb2;
+      Chunk2<R>::load(reinterpret_cast<const char*>(rs.p[i]) + fb * rhs, (size_t)ch * g.V + v, ra, rb2);
+      const cpx<R> al{sc[2 * i], sc[2 * i + 1]};
+      cfma(a, al, ra);
+      cfma(b, al, rb2);
+    }
+    Chunk2<R>::store(o, (size_t)ch * Vh + k, a, b);
+  }
+}
+
 int dslash_eo_blocks(int V) { return (V / 2 + kDslashThreads - 1) / kDslashThreads; }
+
+void mr_combine_even(int prec, const void* x, const MrSteps& rs, void* out_half, const Geom& g, int nrhs,
+                     const double* red0, int rstride, const int* active, cudaStream_t s) {
+  count_launch();
+  const dim3 grid((g.V / 2 + 255) / 256, nrhs);
+  const EoDiv dv{make_fastdiv(g.L[0]), make_fastdiv(g.L[1]), make_fastdiv(g.L[2])};
+  if (prec == WMG_PREC_DOUBLE)
+    k_mr_combine_even<double><<<grid, 256, 0, s>>>(x, rs, out_half, g, dv, red0, rstride, active);
+  else
+    k_mr_combine_even<float><<<grid, 256, 0, s>>>(x, rs, out_half, g, dv, red0, rstride, active);
+}
 
 void mr_update_even(int prec, const void* x, const void* r, void* out_half, const Geom& g, int nrhs,
                     const double* red, const int* active, cudaStream_t s) {

@@ -67,6 +67,19 @@ void dslash_eo(int prec, int mode, int p_out, void* out, const void* in, const v
 int dslash_eo_blocks(int V);
 // whole-lattice native field <- even sites from half_e, odd sites from half_o (zeros for a null
 // one); and the half field of parity p from a whole-lattice one
+// the residuals r_1 .. r_n of the MR steps whose solution updates are deferred (n <= kMrMaxSteps)
+constexpr int kMrMaxSteps = 5;
+struct MrSteps {
+  const void* p[kMrMaxSteps];
+  int n;
+};
+// out_e = x_e + sum_i alpha_i r_i at the even sites as half-lattice fields (alpha_i =
+// red0[i * rstride + 3 r ..] per rhs, the sums {Re, Im <q_i, r_i>, |q_i|^2}; x, r_i whole-lattice)
+void mr_combine_even(int prec, const void* x, const MrSteps& rs, void* out_half, const Geom& g, int nrhs,
+                     const double* red0, int rstride, const int* active, cudaStream_t s);
+// r_out = r - alpha q, alpha = red[0..1] / red[2] per rhs (r_out may not alias r or q)
+void blas_mr_rnext(int prec, void* r_out, const void* r, const void* q, size_t n, int nrhs, const double* red,
+                   const int* active, cudaStream_t s);
 // out_e = x_e + alpha r_e at the even sites as half-lattice fields (alpha = red[0..1] / red[2] per
 // rhs; x, r whole-lattice native fields): the last MR step of the red/black solve's cycle
 void mr_update_even(int prec, const void* x, const void* r, void* out_half, const Geom& g, int nrhs,

@@ -387,6 +387,41 @@ wmg_status mr(wmg_ctx* c, int l, int prec, void* x, const void* b, int nrhs, int
   const int dcls = prec == WMG_PREC_DOUBLE ? PROF_DSLASH_64 : PROF_DSLASH_LO;
   int gc;
   const void* U = links(c, prec, &gc);
+  if (l == 0 && c->cyc_out_half && !c->use_mr_fuse && nu >= 1 && nu <= kMrMaxSteps) {
+    // the red/black cycle's smoother with its solution updates deferred: the residuals of the
+    // steps are kept (r_1 .. r_nu, each step r_{i+1} = r_i - alpha_i q_i) and the even sites of
+    // x + sum_i alpha_i r_i are formed once at the end, in the order of step-by-step updates
+    MrSteps rs{};
+    rs.n = nu;
+    void* rbuf[kMrMaxSteps];
+    rbuf[0] = r;
+    for (int i = 1; i < nu; ++i) {
+      char tag[16];
+      std::snprintf(tag, sizeof tag, "mr_rs%d", i);
+      TRY(vec_ws(c, l, tag, prec, nrhs, &rbuf[i]));
+    }
+    for (int i = 0; i < nu; ++i) rs.p[i] = rbuf[i];
+    {
+      ProfScope ps(c, dcls, dslash_bytes(c, prec, na, true), na);
+      dslash(prec, r, x, b, U, c->fine, c->d_mass, active, nrhs, 0, nullptr, c->stream, gc, c->cyc_b_half ? 1 : 0);
+    }
+    double* red0 = res_slot(c, RES_MR);  // step i's sums at red0 + i * 3 kMaxRhs (the slot holds 16 kMaxRhs)
+    const int rstride = 3 * kMaxRhs;
+    for (int i = 0; i < nu; ++i) {
+      RedBuf rbi{c->red_partial, c->red_counter, red0 + (size_t)i * rstride};
+      {
+        ProfScope ps(c, dcls, dslash_bytes(c, prec, na, false), na);
+        dslash(prec, q, rbuf[i], nullptr, U, c->fine, c->d_mass, active, nrhs, 2, &rbi, c->stream, gc);
+      }
+      if (i + 1 < nu) {
+        ProfScope ps(c, PROF_BLAS, vec_bytes(c, l, prec, na, 3), na);  // r_i, q read; r_{i+1} written
+        blas_mr_rnext(prec, rbuf[i + 1], rbuf[i], q, n, nrhs, rbi.result, active, c->stream);
+      }
+    }
+    ProfScope ps(c, PROF_BLAS, vec_bytes(c, l, prec, na, 0.5 * (nu + 2)), na);  // even halves: x, r_i in, out
+    mr_combine_even(prec, x, rs, c->cyc_out_half, c->fine, nrhs, red0, rstride, active, c->stream);
+    return check(c, "mr (deferred updates)");
+  }
   if (l == 0 && c->use_mr_fuse && nu > 0) {
     // r = b - D x; q = D r with the step's sums; then each later step fused with the previous
     // step's update (r and q ping-pong between two buffers, the sums between two result slots);
