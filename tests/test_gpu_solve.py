@@ -390,3 +390,37 @@ def test_coarse_cg_graph_and_host_loop_identical(W, monkeypatch):
         ctx.close()
     assert its["0"] == its["1"]
     assert np.array_equal(xs["0"], xs["1"])
+
+
+@pytest.mark.parametrize("gamma", [1, 2])
+def test_three_level_red_black_solve(W, gamma):
+    """3 levels (V- and W-cycle) with the red/black fine solve and the FP32 smoother, where the cycle
+    reads the half-lattice residual (restriction from the even sites, the smoother's first residual
+    with b on the even sites) and its smoother defers the solution updates: every solution meets
+    the 1e-10 true residual (oracle D) in about as many outer iterations as the whole-lattice
+    solve, and a right-hand side's result is the same alone and in its batch."""
+    dims, m = (8, 8, 8, 16), 0.0
+    U = synth.gauge_field(dims, 0.5, 91)
+    b = synth.gaussian_spinors(dims, 3, 92)
+    its = {}
+    for eo in (0, 1):
+        ctx = W.Context(dims)
+        ctx.load_gauge(U)
+        ctx.set_mass(m)
+        p = W.default_params(nlevels=3, block=[(2, 2, 2, 2), (2, 2, 2, 2)], nvec=[6, 8], prec_sloppy=1,
+                             cycle_gamma=gamma, fine_eo=eo)
+        ctx.setup(p, synth.setup_starts(dims, 6, 93))
+        x = dev(np.zeros_like(b))
+        _, info = ctx.solve(dev(b), x, 3)
+        xs = host(x)
+        for r in range(3):
+            assert info[r]["converged"]
+            assert oracle_resid(U, m, b[r], xs[r]) <= 1.05e-10
+        its[eo] = [i["iters"] for i in info]
+        if eo:
+            x1 = dev(np.zeros_like(b[2:3]))
+            _, i1 = ctx.solve(dev(b[2:3]), x1, 1)
+            assert np.array_equal(host(x1)[0], xs[2]) and i1[0]["iters"] == info[2]["iters"]
+        ctx.close()
+    print(f"outer iterations whole lattice {its[0]}, red/black {its[1]}")
+    assert all(e <= 1.3 * w + 2 for w, e in zip(its[0], its[1]))
