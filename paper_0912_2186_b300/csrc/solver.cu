@@ -387,7 +387,11 @@ wmg_status mr(wmg_ctx* c, int l, int prec, void* x, const void* b, int nrhs, int
   const int dcls = prec == WMG_PREC_DOUBLE ? PROF_DSLASH_64 : PROF_DSLASH_LO;
   int gc;
   const void* U = links(c, prec, &gc);
-  if (l == 0 && c->cyc_out_half && !c->use_mr_fuse && nu >= 1 && nu <= kMrMaxSteps) {
+  // deferred solution updates keep the step residuals: used while they fit in kMrDeferBytes
+  constexpr double kMrDeferBytes = 4.0e9;
+  const double rbytes = (double)nrhs * (double)n * (prec == WMG_PREC_DOUBLE ? 16.0 : 8.0);
+  if (l == 0 && c->cyc_out_half && !c->use_mr_fuse && nu >= 1 && nu <= kMrMaxSteps &&
+      (nu - 1) * rbytes <= kMrDeferBytes) {
     // the red/black cycle's smoother with its solution updates deferred: the residuals of the
     // steps are kept (r_1 .. r_nu, each step r_{i+1} = r_i - alpha_i q_i) and the even sites of
     // x + sum_i alpha_i r_i are formed once at the end, in the order of step-by-step updates
