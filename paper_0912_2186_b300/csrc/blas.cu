@@ -148,8 +148,11 @@ __global__ void k_mr_update(void* x_, void* r_, const void* q_, size_t n, const 
 // round, i0 + j blockDim (j < kBlasPerThread), and issues every load of the round before the
 // arithmetic (one memory round trip per round; the coarsest solve's vectors take one round).
 template <typename R>
-__global__ void k_cg_update(void* __restrict__ x_, void* __restrict__ r_, const void* __restrict__ p_,
-                            const void* __restrict__ q_, size_t n, CgScalars cg, int parity, int nrhs, RedBuf rb) {
+// (In the kernels launched with programmatic serialisation the vectors written by the previous
+// kernel are read through plain pointers: a const __restrict__ load may be taken as invariant over
+// the kernel and issued before griddepcontrol.wait, i.e. before the previous kernel has finished.)
+__global__ void k_cg_update(void* x_, void* r_, const void* p_, const void* q_, size_t n, CgScalars cg, int parity,
+                            int nrhs, RedBuf rb) {
   constexpr int E = kBlasPerThread;
   const int r = blockIdx.y;
   griddep_wait();  // everything below reads the previous kernel's results
@@ -159,10 +162,10 @@ __global__ void k_cg_update(void* __restrict__ x_, void* __restrict__ r_, const 
   R sc[1];
   cta_scalars<R, 1>(sc, [&](double* v) { v[0] = on ? zz / qq : 0.0; });
   const R al = sc[0];
-  cpx<R>* __restrict__ x = vec<R>(x_, n, r);
-  cpx<R>* __restrict__ rr = vec<R>(r_, n, r);
-  const cpx<R>* __restrict__ p = vec<R>(p_, n, r);
-  const cpx<R>* __restrict__ q = vec<R>(q_, n, r);
+  cpx<R>* x = vec<R>(x_, n, r);
+  cpx<R>* rr = vec<R>(r_, n, r);
+  const cpx<R>* p = vec<R>(p_, n, r);
+  const cpx<R>* q = vec<R>(q_, n, r);
   R t = 0;
   for (size_t i0 = (size_t)blockIdx.x * blockDim.x * E + threadIdx.x; i0 < n; i0 += (size_t)gridDim.x * blockDim.x * E) {
     cpx<R> rv[E], xv[E], pv[E], qv[E];
@@ -205,8 +208,7 @@ __global__ void k_cg_update(void* __restrict__ x_, void* __restrict__ r_, const 
 
 // p = z + beta p, beta = zz[1-parity]/zz[parity] (loads of a round issued first, as above)
 template <typename R>
-__global__ void k_cg_xpay(void* __restrict__ p_, const void* __restrict__ z_, size_t n, CgScalars cg, int parity,
-                          int nrhs) {
+__global__ void k_cg_xpay(void* p_, const void* z_, size_t n, CgScalars cg, int parity, int nrhs) {
   constexpr int E = kBlasPerThread;
   const int r = blockIdx.y;
   griddep_wait();  // everything below reads the previous kernel's results
@@ -216,8 +218,8 @@ __global__ void k_cg_xpay(void* __restrict__ p_, const void* __restrict__ z_, si
   R sc[1];
   cta_scalars<R, 1>(sc, [&](double* v) { v[0] = zo > 0.0 ? zn / zo : 0.0; });
   const R be = sc[0];
-  cpx<R>* __restrict__ p = vec<R>(p_, n, r);
-  const cpx<R>* __restrict__ z = vec<R>(z_, n, r);
+  cpx<R>* p = vec<R>(p_, n, r);
+  const cpx<R>* z = vec<R>(z_, n, r);
   for (size_t i0 = (size_t)blockIdx.x * blockDim.x * E + threadIdx.x; i0 < n; i0 += (size_t)gridDim.x * blockDim.x * E) {
     cpx<R> pv[E], zv[E];
 #pragma unroll

@@ -98,7 +98,7 @@ constexpr int kMmaThreads = 256;
 template <int NDOF, int NT>
 __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4* __restrict__ A16,
                                                                      const float* __restrict__ sA, Geom g,
-                                                                     const cf* __restrict__ in, cf* __restrict__ out,
+                                                                     const cf* in, cf* out,
                                                                      int nrhs, const double* __restrict__ shift,
                                                                      int dagger, const int* __restrict__ active,
                                                                      RedBuf rb, int want_norm, StencilEo eo,
@@ -160,7 +160,9 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_coarse_apply_mma(const uint4
   }
   const cf* hin = eo.hop_in ? reinterpret_cast<const cf*>(eo.hop_in) : in;
   // everything above reads only the operator tables and the geometry: with a programmatic launch
-  // it overlaps the end of the previous kernel, whose results are read from here on
+  // it overlaps the end of the previous kernel, whose results are read from here on (`in`, `out`
+  // and the vectors of eo are plain pointers, so that no load of them is taken as invariant and
+  // issued before the wait)
   griddep_wait();
   // gather this warp's right-hand sides (all loads first), then per rhs the max |Re|, |Im| by
   // shuffles and the scaled FP16 copy in column layout [Xr 0..7 | Xi 0..7 | Xr 8..15 | Xi 8..15]
