@@ -57,9 +57,7 @@ REFERENCE_CG = {"16x16x16x32": [9.1, 23.4, 43.0]}  # coarsest CG iterations per 
 # class is one application of the coarsest Schur complement (its odd-site and even-site passes).
 # "changed": the kernel changed after the capture, so the line reports no traffic (the last
 # capture's figure is kept beside it) until the capture is taken again.
-TRAFFIC = {"coarse": {"bytes_per_launch": 46.1e6, "profile": "profiles/coarse_schur_16x16x16x32_nrhs12.md",
-                      "changed": "vector loads of the passes through plain instead of const __restrict__ "
-                                 "pointers since the capture"}}
+TRAFFIC = {"coarse": {"bytes_per_launch": 46.1e6, "profile": "profiles/coarse_schur_16x16x16x32_nrhs12.md"}}
 GAUGE_REALS = 12  # reals per link of the FP32 fine operator in the job (wmg_set_gauge_compression)
 PROF_CLASSES = ("dslash_sloppy", "dslash_fp64", "coarse", "restrict", "prolong", "blas", "setup", "cgnr",
                 "blas_coarse")
