@@ -71,3 +71,18 @@ def test_the_check_sees_a_restrict_vector():
     (name, params, body), = _kernels(src)
     assert name == "k_demo" and "griddep_wait()" in body
     assert any("__restrict__" in p and p.strip().endswith("v") for p in params.split(","))
+
+
+def test_programmatic_launches_only_of_waiting_kernels():
+    # a kernel launched with programmatic stream serialisation that never waits could run
+    # entirely before its predecessor has finished: every such launch is of a waiting kernel
+    waiting = {k[1] for k in _waiting_kernels()}
+    launched = set()
+    for f in sorted(os.listdir(CSRC)):
+        if f.endswith(".cu"):
+            with open(os.path.join(CSRC, f)) as fh:
+                src = fh.read()
+            if "programmaticStreamSerializationAllowed" in src:
+                launched |= set(re.findall(r"cudaLaunchKernelEx\(\s*&\w+\s*,\s*(\w+)", src))
+    assert launched, "no programmatic launches found"
+    assert launched <= waiting, f"launched with programmatic serialisation without a wait: {launched - waiting}"
